@@ -1,0 +1,280 @@
+"""Seeded synthetic Wannier models and workloads.
+
+This module only BUILDS inputs: tight-binding hoppings H(R_e), mass-scaled force
+constants D(R_ph) and Wannier-space couplings g(R_e, R_ph), together with the mesh,
+temperature, chemical potential, window and delta-width of each workload.  It holds
+none of the method's arithmetic (no Fourier sums, no diagonalisation, no rates, no
+BTE); the CUDA path and the oracle both consume the arrays it returns.
+
+The materials of the paper (DFT/EPW silicon, Methods section) are not available;
+the models below stand in for them with the same shapes (bands, atoms, branches,
+R grids) and value structure (couplings decaying exponentially with |R|).
+
+Conventions shared by both consumers:
+  * lattice rows are a1, a2, a3 in Angstrom; R vectors are integer crystal
+    coordinates; k and q are reciprocal crystal coordinates (k.R = 2 pi sum k_i R_i).
+  * H_R[r, m, n] (eV), complex; H(k) = sum_r exp(i 2 pi k.R_r) H_R[r].
+  * D_R[r, a, b] (eV^2), mass-scaled so that the eigenvalues of D(q) are (hbar w)^2.
+  * g_R[re, rp, m', n', alpha] (eV), alpha = 3*atom + cartesian.
+  * sym_rot[s] integer 3x3 acting on reciprocal crystal coordinates of k,
+    sym_cart[s] the same operation acting on Cartesian vectors.
+"""
+from __future__ import annotations
+
+import dataclasses
+import itertools
+
+import numpy as np
+
+SEED_BASE = 2109085470
+
+
+@dataclasses.dataclass
+class WannierModel:
+    lattice: np.ndarray            # (3,3) Angstrom, rows a1..a3
+    mass_amu: np.ndarray           # (nat,)
+    tau_cart: np.ndarray           # (nat,3) Angstrom
+    nb: int
+    Re: np.ndarray                 # (nRe,3) int32
+    H_R: np.ndarray                # (nRe,nb,nb) complex128, eV
+    Rd: np.ndarray                 # (nRd,3) int32
+    D_R: np.ndarray                # (nRd,3nat,3nat) complex128, eV^2
+    Rge: np.ndarray                # (nRge,3) int32
+    Rgp: np.ndarray                # (nRgp,3) int32
+    g_R: np.ndarray                # (nRge,nRgp,nb,nb,3nat) complex128, eV
+    omega_ref_eV: float            # hbar*omega at which g_R is quoted
+    sym_rot: np.ndarray            # (nsym,3,3) int32
+    sym_cart: np.ndarray           # (nsym,3,3) float64
+    spin_deg: float = 2.0
+    bg_rate_coeff: float = 1.0e12  # 1/s, phonon background rate at omega_ref, T_ref
+    bg_omega_ref_eV: float = 0.03
+    bg_T_ref: float = 300.0
+
+    @property
+    def nat(self) -> int:
+        return int(self.mass_amu.shape[0])
+
+    @property
+    def nbranch(self) -> int:
+        return 3 * self.nat
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    model: WannierModel
+    kmesh: tuple
+    qmesh: tuple
+    T_K: float
+    mu_eV: float
+    window: tuple                  # absolute (lo_eV, hi_eV), inclusive
+    sigma_eV: float = 0.010
+    cutoff_sigmas: float = 8.0
+    omega_min_eV: float = 1.0e-4
+    degen_tol_eV: float = 1.0e-6
+    tol: float = 1.0e-10
+
+
+def oh_group() -> np.ndarray:
+    """The 48 signed permutation matrices (point group O_h of a cubic lattice)."""
+    ops = []
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product((1, -1), repeat=3):
+            m = np.zeros((3, 3), dtype=np.int32)
+            for i in range(3):
+                m[i, perm[i]] = signs[i]
+            ops.append(m)
+    ops.sort(key=lambda m: tuple(m.ravel()))
+    # identity first
+    ident = [i for i, m in enumerate(ops) if np.array_equal(m, np.eye(3, dtype=np.int32))][0]
+    ops.insert(0, ops.pop(ident))
+    return np.array(ops, dtype=np.int32)
+
+
+def identity_group() -> np.ndarray:
+    return np.eye(3, dtype=np.int32)[None]
+
+
+def cube_grid(half: int) -> np.ndarray:
+    """Integer vectors with every component in [-half, half], lexicographic order."""
+    r = range(-half, half + 1)
+    return np.array(list(itertools.product(r, r, r)), dtype=np.int32)
+
+
+def _index_of(grid: np.ndarray) -> dict:
+    return {tuple(v): i for i, v in enumerate(grid)}
+
+
+def hermitian_pair_symmetrise(g: np.ndarray, Rge: np.ndarray, Rgp: np.ndarray) -> np.ndarray:
+    """Impose g_{m'n'a}(Re,Rp) = conj(g_{n'm'a}(-Re, Rp-Re)) (the condition under which
+    |g_mn(k,q)| = |g_nm(k+q,-q)|, i.e. the absorption and emission vertices agree).
+    Pairs whose partner falls outside the grid are set to zero."""
+    ie = _index_of(Rge)
+    ip = _index_of(Rgp)
+    out = np.zeros_like(g)
+    for a, re in enumerate(Rge):
+        pe = ie.get(tuple(-re))
+        for b, rp in enumerate(Rgp):
+            pp = ip.get(tuple(rp - re))
+            if pe is None or pp is None:
+                continue
+            partner = np.conj(np.swapaxes(g[pe, pp], 0, 1))
+            out[a, b] = 0.5 * (g[a, b] + partner)
+    return out
+
+
+def hermitian_hoppings(h: np.ndarray, R: np.ndarray) -> np.ndarray:
+    """H(-R) = H(R)^dagger, so that H(k) is Hermitian."""
+    idx = _index_of(R)
+    out = np.empty_like(h)
+    for i, r in enumerate(R):
+        j = idx[tuple(-r)]
+        out[i] = 0.5 * (h[i] + np.conj(h[j].T))
+    return out
+
+
+# --------------------------------------------------------------------------------------
+# Model 1: simple cubic, one band, one atom (closed-form bands and phonons)
+# --------------------------------------------------------------------------------------
+
+def model_sc1(seed: int = SEED_BASE + 1, a: float = 3.0, t_eV: float = 1.0,
+              omega_max_eV: float = 0.030, g0_eV: float = 0.05, noise: float = 0.10) -> WannierModel:
+    """Nearest-neighbour tight binding eps = -2t sum cos(k_a a); nearest-neighbour
+    springs giving hbar*w_alpha(q) = w_max |sin(q_alpha a/2)| with Cartesian
+    eigenvectors; g(Re,Rp) = g0 exp(-(|Re|+|Rp|)/a) (1+xi) on 3^3 x 3^3 R grids, the
+    same for the three displacement directions.  xi is drawn once per O_h orbit of
+    the pair (Re,Rp) so the model keeps the full cubic symmetry."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lattice = a * np.eye(3)
+    nn = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]],
+                  dtype=np.int32)
+    H_R = np.zeros((7, 1, 1), dtype=np.complex128)
+    H_R[1:, 0, 0] = -t_eV
+    W2 = omega_max_eV ** 2
+    D_R = np.zeros((7, 3, 3), dtype=np.complex128)
+    D_R[0] = 0.5 * W2 * np.eye(3)
+    for i, r in enumerate(nn[1:], start=1):
+        ax = int(np.nonzero(r)[0][0])
+        D_R[i, ax, ax] = -0.25 * W2
+    grid = cube_grid(1)
+    ops = oh_group()
+    # noise per orbit of the pair under simultaneous rotation
+    keys = {}
+    for a_i, re in enumerate(grid):
+        for b_i, rp in enumerate(grid):
+            key = min((tuple(S @ re), tuple(S @ rp)) for S in ops)
+            keys[(a_i, b_i)] = key
+    orbit_list = sorted(set(keys.values()))
+    xi = dict(zip(orbit_list, rng.uniform(-noise, noise, size=len(orbit_list))))
+    g = np.zeros((27, 27, 1, 1, 3), dtype=np.complex128)
+    for (a_i, b_i), key in keys.items():
+        amp = g0_eV * np.exp(-(np.linalg.norm(grid[a_i]) + np.linalg.norm(grid[b_i]))) * (1.0 + xi[key])
+        g[a_i, b_i, 0, 0, :] = amp
+    g = hermitian_pair_symmetrise(g, grid, grid)
+    return WannierModel(lattice=lattice, mass_amu=np.array([28.0855]), tau_cart=np.zeros((1, 3)), nb=1,
+                        Re=nn.copy(), H_R=H_R, Rd=nn.copy(), D_R=D_R, Rge=grid, Rgp=grid.copy(), g_R=g,
+                        omega_ref_eV=omega_max_eV, sym_rot=ops, sym_cart=ops.astype(np.float64),
+                        bg_omega_ref_eV=omega_max_eV)
+
+
+# --------------------------------------------------------------------------------------
+# Model 2: 4-band seeded random Hamiltonian, 2-atom CsCl-type cubic basis, 6 branches
+# --------------------------------------------------------------------------------------
+
+def _cscl_force_constants(K1: float, K2A: float, K2B: float, mA: float, mB: float):
+    """Central springs on a CsCl-type lattice (A at 0, B at (1/2,1/2,1/2)a): K1 on the
+    8 A-B nearest bonds, K2A / K2B on the 6 A-A / B-B next-nearest bonds.  Returns the
+    R list and mass-scaled blocks D(R) (arbitrary energy^2 units, real)."""
+    Rd = cube_grid(1)
+    idx = _index_of(Rd)
+    D = np.zeros((27, 6, 6))
+    tau = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.5]])
+    masses = np.array([mA, mB])
+    Kmat = {(0, 1): K1, (1, 0): K1, (0, 0): K2A, (1, 1): K2B}
+    for i in range(2):
+        for j in range(2):
+            for R in Rd:
+                d = R + tau[j] - tau[i]
+                dist = np.linalg.norm(d)
+                if dist < 1e-12:
+                    continue
+                if i != j and abs(dist - np.sqrt(3) / 2) < 1e-9:
+                    K = Kmat[(i, j)]
+                elif i == j and abs(dist - 1.0) < 1e-9:
+                    K = Kmat[(i, j)]
+                else:
+                    continue
+                e = d / dist
+                blk = K * np.outer(e, e)
+                r = idx[tuple(R)]
+                D[r, 3 * i:3 * i + 3, 3 * j:3 * j + 3] -= blk / np.sqrt(masses[i] * masses[j])
+                D[idx[(0, 0, 0)], 3 * i:3 * i + 3, 3 * i:3 * i + 3] += blk / masses[i]
+    return Rd, D
+
+
+def model_cscl4(seed: int = SEED_BASE + 2, a: float = 3.0, omega_max_eV: float = 0.060,
+                g0_eV: float = 0.01, hop_eV: float = 1.0, nb: int = 4, r_half: int = 2) -> WannierModel:
+    """4-band Hamiltonian with seeded normal hoppings 1 eV exp(-|R|/a) on a 5^3 R grid
+    (H(-R) = H(R)^dagger, band centre at 0 eV), 2-atom CsCl-type basis (masses 28 and
+    16 amu) with seeded nearest / next-nearest central springs scaled so the
+    zone-centre optical phonon is omega_max, and normal couplings
+    g0 exp(-(|Re|+|Rp|)/a) on 5^3 x 5^3 R grids (stored complex128).
+
+    No point symmetry is kept, but the Wannier functions are taken real (real H(R)
+    and g), i.e. the model is time-reversal symmetric as every non-magnetic crystal
+    is: eps(-k) = eps(k), v(-k) = -v(k).  Without it the driving terms of the electron
+    BTE overlap the collision operator's number-conserving zero mode and the plain
+    iteration drifts instead of converging."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lattice = a * np.eye(3)
+    R = cube_grid(r_half)
+    nR = R.shape[0]
+    decay = np.exp(-np.linalg.norm(R, axis=1))
+    h = rng.standard_normal((nR, nb, nb)).astype(np.complex128)
+    h *= hop_eV * decay[:, None, None]
+    H_R = hermitian_hoppings(h, R)
+    i0 = _index_of(R)[(0, 0, 0)]
+    H_R[i0] -= (np.trace(H_R[i0]).real / nb) * np.eye(nb)
+    mA, mB = 28.0855, 15.999
+    K = rng.uniform(0.5, 1.5, size=3)
+    Rd, D = _cscl_force_constants(K[0], K[1], K[2], mA, mB)
+    # zone-centre optical frequency of the central-spring CsCl lattice: (8 K1/3)(1/mA+1/mB)
+    w2_opt = (8.0 * K[0] / 3.0) * (1.0 / mA + 1.0 / mB)
+    D_R = (D * (omega_max_eV ** 2 / w2_opt)).astype(np.complex128)
+    g = rng.standard_normal((nR, nR, nb, nb, 6)).astype(np.complex128)
+    g *= g0_eV * (decay[:, None] * decay[None, :])[:, :, None, None, None]
+    g = hermitian_pair_symmetrise(g, R, R)
+    return WannierModel(lattice=lattice, mass_amu=np.array([mA, mB]),
+                        tau_cart=np.array([[0.0, 0.0, 0.0], [0.5 * a, 0.5 * a, 0.5 * a]]), nb=nb,
+                        Re=R, H_R=H_R, Rd=Rd, D_R=D_R, Rge=R.copy(), Rgp=R.copy(), g_R=g,
+                        omega_ref_eV=omega_max_eV, sym_rot=identity_group(),
+                        sym_cart=identity_group().astype(np.float64), bg_omega_ref_eV=omega_max_eV)
+
+
+# --------------------------------------------------------------------------------------
+# Workloads
+# --------------------------------------------------------------------------------------
+
+def workload_sc1(n: int = 8, nsym_full: bool = True, T_K: float = 300.0) -> Workload:
+    """One-band simple-cubic case: 8^3 k and q meshes, mu = +0.3 eV, window mu +- 0.4 eV,
+    T = 300 K, Gaussian delta sigma = 10 meV."""
+    m = model_sc1()
+    if not nsym_full:
+        m = dataclasses.replace(m, sym_rot=identity_group(), sym_cart=identity_group().astype(np.float64))
+    mu = 0.3
+    return Workload(name=f"sc1-{n}^3", model=m, kmesh=(n, n, n), qmesh=(n, n, n), T_K=T_K, mu_eV=mu,
+                    window=(mu - 0.4, mu + 0.4), tol=1e-10)
+
+
+def workload_cscl4(n: int = 24, T_K: float = 300.0) -> Workload:
+    """Four-band, six-branch precision case: n^3 k and q meshes (24^3 at full size),
+    mu = 0 eV, window mu +- 0.3 eV, T = 300 K, sigma = 10 meV."""
+    m = model_cscl4()
+    mu = 0.0
+    return Workload(name=f"cscl4-{n}^3", model=m, kmesh=(n, n, n), qmesh=(n, n, n), T_K=T_K, mu_eV=mu,
+                    window=(mu - 0.3, mu + 0.3), tol=1e-10)
+
+
+def model_nbytes(m: WannierModel) -> int:
+    return int(sum(x.nbytes for x in (m.lattice, m.mass_amu, m.tau_cart, m.Re, m.H_R, m.Rd, m.D_R,
+                                       m.Rge, m.Rgp, m.g_R, m.sym_rot, m.sym_cart)))

@@ -1,0 +1,375 @@
+"""Pins of the FP64 oracle against things other than itself: closed forms, finite
+differences, unitarity, Hermiticity and symmetry identities, detailed balance, a
+brute-force full-BZ run, a dense direct solve of the same linear system, sum rules
+and the Kelvin-Onsager identity.  CPU only."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2109_08547_gb300 import synthetic as S
+
+HB = O.HBAR_EVS
+A_M = O.ANGSTROM
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+# ------------------------------------------------------------------ bands and phonons
+
+def test_sc1_bands_closed_form(sc1_prepared):
+    """Nearest-neighbour tight binding: eps = -2t sum cos(k_a a), v_a = (2ta/hbar) sin(k_a a)."""
+    P = sc1_prepared
+    kc = P.kidx / np.array(P.wl.kmesh)
+    eps = -2.0 * np.cos(2 * np.pi * kc).sum(axis=1)
+    np.testing.assert_allclose(P.eps[:, 0], eps, atol=1e-13)
+    v = (2.0 * 3.0 / HB) * np.sin(2 * np.pi * kc) * A_M
+    np.testing.assert_allclose(P.vel[:, 0, :], v, atol=1e-9 * np.abs(v).max())
+
+
+def test_sc1_phonons_closed_form(sc1_prepared):
+    """Nearest-neighbour springs: hbar w_a = w_max |sin(q_a a/2)| with Cartesian eigenvectors;
+    v = (w_max a / 2 hbar) cos(q_a a/2) sgn(sin) along a, zero across."""
+    P = sc1_prepared
+    W, a = 0.030, 3.0
+    qc = P.qidx / np.array(P.wl.qmesh)
+    w_exact = W * np.abs(np.sin(np.pi * qc))
+    np.testing.assert_allclose(P.w, np.sort(w_exact, axis=1), atol=1e-12)
+    for q in range(P.Nq):
+        order = np.argsort(w_exact[q], kind="stable")
+        we = w_exact[q, order]
+        if np.min(np.diff(we)) < 1e-6 or we[0] < 1e-4:
+            continue  # degenerate or Gamma-like: covered by averaging tests
+        for s, ax in enumerate(order):
+            v = np.zeros(3)
+            v[ax] = (W * a / (2 * HB)) * np.cos(np.pi * qc[q, ax]) * np.sign(np.sin(np.pi * qc[q, ax])) * A_M
+            np.testing.assert_allclose(P.vph[q, s], v, atol=1e-9 * abs(v[ax]))
+
+
+def test_multiband_velocity_matches_finite_difference():
+    """Hellmann-Feynman v = (1/hbar) d eps/dk against a central difference of the eigenvalues
+    (electrons) and of hbar w (phonons) of the 4-band / 6-branch model."""
+    m = S.model_cscl4()
+    rng = np.random.default_rng(7)
+    k = rng.random((12, 3))
+    h = 1e-5
+    e0, _, v = O.electron_bands(m, k, 1e-6)
+    w0, _, vp = O.phonon_modes(m, k, 1e-6, 1e-4)
+    a = 3.0
+    for d in range(3):
+        dk = np.zeros(3)
+        dk[d] = h
+        ep, _, _ = O.electron_bands(m, k + dk, 1e-6)
+        em, _, _ = O.electron_bands(m, k - dk, 1e-6)
+        wp, _, _ = O.phonon_modes(m, k + dk, 1e-6, 1e-4)
+        wm, _, _ = O.phonon_modes(m, k - dk, 1e-6, 1e-4)
+        dkc = 2 * np.pi * h / a   # cartesian step (1/Angstrom)
+        fd = (ep - em) / (2 * dkc) / HB * A_M
+        fdw = (wp - wm) / (2 * dkc) / HB * A_M
+        ok = np.min(np.abs(np.diff(e0, axis=1)), axis=1) > 1e-3
+        np.testing.assert_allclose(v[ok, :, d], fd[ok], rtol=1e-5, atol=1e-6 * np.abs(v).max())
+        okw = np.min(np.abs(np.diff(w0, axis=1)), axis=1) > 1e-4
+        np.testing.assert_allclose(vp[okw, :, d], fdw[okw], rtol=1e-5, atol=1e-6 * np.abs(vp).max())
+
+
+def test_acoustic_sum_rule_and_stability():
+    m = S.model_cscl4()
+    q = np.vstack([np.zeros((1, 3)), np.random.default_rng(3).random((50, 3))])
+    w, _, _ = O.phonon_modes(m, q, 1e-6, 1e-4)
+    assert np.all(w[0, :3] < 1e-8) and np.all(w[0, 3:] > 1e-3)
+    Dq = np.einsum("qr,rab->qab", np.exp(2j * np.pi * q @ m.Rd.T), m.D_R)
+    assert np.min(np.linalg.eigvalsh(Dq)) > -1e-12
+    # zone-centre optical frequency set by the model (0.060 eV)
+    np.testing.assert_allclose(w[0, 3:], 0.060, rtol=1e-12)
+
+
+# ------------------------------------------------------------------ Bloch vertex
+
+def _r0_only(m):
+    g = np.zeros_like(m.g_R)
+    ie = [i for i, r in enumerate(m.Rge) if not r.any()][0]
+    ip = [i for i, r in enumerate(m.Rgp) if not r.any()][0]
+    g[ie, ip] = m.g_R[ie, ip]
+    return dataclasses.replace(m, g_R=g), g[ie, ip]
+
+
+def test_vertex_unitarity_with_R0_couplings():
+    """Only g(0,0) nonzero => G(k,q) = g(0,0) for all k,q, and the band/branch rotations are
+    unitary: sum_{m,n,s} (w_s/w_ref) |g|^2 = sum_alpha (m_bar/m_alpha) ||g(0,0)_alpha||_F^2."""
+    wl = S.workload_cscl4(4)
+    m0, g00 = _r0_only(wl.model)
+    wl = dataclasses.replace(wl, model=m0, window=(-100.0, 100.0))
+    P = O.prepare(wl)
+    mass = np.repeat(m0.mass_amu, 3)
+    expect = np.sum(np.abs(g00) ** 2 * (mass.mean() / mass)[None, None, :])
+    k = 5
+    qs = np.array([1, 7, 22, 41, 63])
+    kps = O.kplusq(P, k, qs)
+    g2 = O.bloch_vertex_sq(P, k, qs, kps)
+    for i, q in enumerate(qs):
+        assert np.all(P.w[q] > 1e-4)
+        tot = np.sum(g2[i] * (P.w[q] / m0.omega_ref_eV)[None, None, :])
+        np.testing.assert_allclose(tot, expect, rtol=1e-12)
+
+
+def test_vertex_one_band_R0_is_constant(sc1_prepared):
+    """One band, Cartesian phonon eigenvectors: |g_s|^2 = (w_ref/w_s) |g(0,0)|^2 exactly."""
+    m0, g00 = _r0_only(sc1_prepared.wl.model)
+    P = O.prepare(dataclasses.replace(sc1_prepared.wl, model=m0))
+    k = 3
+    qs = np.arange(P.Nq)
+    kps = O.kplusq(P, k, qs)
+    g2 = O.bloch_vertex_sq(P, k, qs, kps)
+    ok = P.w > 1e-4
+    expect = (m0.omega_ref_eV / P.w[ok]) * np.abs(g00[0, 0, 0]) ** 2
+    np.testing.assert_allclose(g2[:, 0, 0, :][ok], expect, rtol=1e-12)
+
+
+@pytest.mark.parametrize("which", ["sc1", "cscl4"])
+def test_vertex_hermiticity(which):
+    """|g_mn(k,q)| = |g_nm(k+q,-q)| (absorption and emission share the vertex)."""
+    wl = S.workload_sc1() if which == "sc1" else S.workload_cscl4(4)
+    P = O.prepare(wl)
+    rng = np.random.default_rng(11)
+    for k in rng.integers(0, P.Nk, 4):
+        qs = rng.integers(0, P.Nq, 6)
+        kps = O.kplusq(P, k, qs)
+        g2 = O.bloch_vertex_sq(P, k, qs, kps)
+        mqs = O.minus_q(P, qs)
+        for i in range(len(qs)):
+            back = O.bloch_vertex_sq(P, kps[i], mqs[i:i + 1], np.array([k]))[0]
+            ok = P.w[qs[i]] > 1e-4
+            np.testing.assert_allclose(g2[i][:, :, ok], np.swapaxes(back, 0, 1)[:, :, ok],
+                                       rtol=1e-9, atol=1e-12 * g2.max())
+
+
+def test_vertex_cubic_symmetry(sc1_prepared):
+    """|g(Sk, Sq)|^2 = |g(k,q)|^2 for every O_h operation of the symmetric one-band model."""
+    P = sc1_prepared
+    nk = np.array(P.wl.kmesh)
+    rng = np.random.default_rng(5)
+    for k in rng.integers(0, P.Nk, 3):
+        qs = rng.integers(0, P.Nq, 5)
+        g2 = O.bloch_vertex_sq(P, k, qs, O.kplusq(P, k, qs))
+        for Sop in P.wl.model.sym_rot[::7]:
+            kS = O.flat_index(np.mod(Sop @ P.kidx[k], nk), P.wl.kmesh)
+            qS = O.flat_index(np.mod(P.qidx[qs] @ Sop.T, nk), P.wl.qmesh)
+            g2S = O.bloch_vertex_sq(P, kS, qS, O.kplusq(P, kS, qS))
+            np.testing.assert_allclose(g2S, g2, rtol=1e-10, atol=1e-14 * g2.max())
+
+
+def test_degenerate_average_is_gauge_invariant(sc1_prepared):
+    """Rotating phonon eigenvectors by a random unitary inside a degenerate subspace leaves
+    the subspace-averaged |g|^2 unchanged (q on the body diagonal: triply degenerate)."""
+    P = sc1_prepared
+    q = O.flat_index(np.array([1, 1, 1]), P.wl.qmesh)
+    k = 0
+    g_ref = O.bloch_vertex_sq(P, k, np.array([q]), O.kplusq(P, k, np.array([q])))
+    rng = np.random.default_rng(2)
+    Z = rng.standard_normal((3, 3)) + 1j * rng.standard_normal((3, 3))
+    Q, _ = np.linalg.qr(Z)
+    u2 = P.u.copy()
+    u2[q] = u2[q] @ Q
+    P2 = dataclasses.replace(P, u=u2)
+    g_rot = O.bloch_vertex_sq(P2, k, np.array([q]), O.kplusq(P2, k, np.array([q])))
+    np.testing.assert_allclose(g_rot, g_ref, rtol=1e-12)
+
+
+# ------------------------------------------------------------------ rates
+
+def test_sc1_counts(sc1_prepared, sc1_rates):
+    """Window/IBZ/cut bookkeeping of the one-band 8^3 case: 92 active FBZ states, 4 IBZ
+    points with an active band, 368 (k,q) pairs, 574 entries within the 8-sigma cut
+    (1148 when X+ and X- are counted separately)."""
+    assert sc1_prepared.active.sum() == 92
+    assert len(sc1_rates.ibz_win) == 4
+    assert sc1_rates.n_pairs == 368
+    assert len(sc1_rates.Xp) == 574
+
+
+def test_detailed_balance(sc1_full_prepared, sc1_full_rates):
+    """X+(mk -> nk' | q) / X-(nk' -> mk | -q) = exp(beta (eps_nk' - eps_mk - hbar w_sq))."""
+    P, R = sc1_full_prepared, sc1_full_rates
+    key = {(a, b, c, d, e): i for i, (a, b, c, d, e) in enumerate(zip(R.ik, R.m, R.iq, R.n, R.s))}
+    beta = 1.0 / (O.KB_EVK * P.wl.T_K)
+    checked = 0
+    mq = O.minus_q(P, R.iq)
+    for i in range(len(R.Xp)):
+        if R.Xp[i] <= 0:
+            continue
+        j = key.get((R.ikp[i], R.n[i], mq[i], R.m[i], R.s[i]))
+        assert j is not None
+        x = P.eps[R.ikp[i], R.n[i]] - P.eps[R.ik[i], R.m[i]] - P.w[R.iq[i], R.s[i]]
+        np.testing.assert_allclose(R.Xp[i] / R.Xm[j], np.exp(beta * x), rtol=1e-10)
+        checked += 1
+    assert checked > 100
+
+
+def test_rates_vanish_beyond_cut(sc1_rates, sc1_prepared):
+    P, R = sc1_prepared, sc1_rates
+    xp = P.eps[R.ikp, R.n] - P.eps[R.ik, R.m] - P.w[R.iq, R.s]
+    xm = xp + 2 * P.w[R.iq, R.s]
+    cut = P.wl.cutoff_sigmas * P.wl.sigma_eV
+    assert np.all(R.Xp[np.abs(xp) > cut] == 0) and np.all(R.Xm[np.abs(xm) > cut] == 0)
+    assert np.all((np.abs(xp) <= cut) | (np.abs(xm) <= cut))
+
+
+# ------------------------------------------------------------------ BTE and coefficients
+
+@pytest.mark.parametrize("level", ["rta", "dragless", "dragged"])
+def test_ibz_path_equals_full_bz(sc1_prepared, sc1_rates, sc1_full_prepared, sc1_full_rates, level):
+    """IBZ representatives + symmetry rotations + phonon fold reproduce the brute-force
+    full-BZ calculation (no symmetry) for RTA, dragless and dragged solutions."""
+    a = O.solve_coupled_bte(sc1_prepared, sc1_rates, level=level)
+    b = O.solve_coupled_bte(sc1_full_prepared, sc1_full_rates, level=level)
+    assert a.converged and b.converged
+    for key in ("sigma", "sigmaS", "alpha_el", "kappa0_el", "alpha_ph", "kappa_ph"):
+        np.testing.assert_allclose(a.coeffs[key], b.coeffs[key], rtol=1e-8,
+                                   atol=1e-8 * np.abs(b.coeffs[key]).max() + 1e-300)
+    # electron RTA rates agree state by state
+    full = {tuple(s): w for s, w in zip(b.states, b.W_e)}
+    for (k, m), w in zip(a.states, a.W_e):
+        np.testing.assert_allclose(w, full[(k, m)], rtol=1e-11)
+    np.testing.assert_allclose(a.W_ph, b.W_ph, rtol=1e-11)
+
+
+def test_cubic_tensors_are_isotropic(sc1_prepared, sc1_rates):
+    r = O.solve_coupled_bte(sc1_prepared, sc1_rates, level="dragged")
+    for key in ("sigma", "sigmaS", "kappa_el", "kappa_ph", "alpha_ph"):
+        t = r.coeffs[key]
+        d = np.diag(t)
+        np.testing.assert_allclose(d, d[0], rtol=1e-12)
+        assert np.max(np.abs(t - np.diag(d))) < 1e-12 * abs(d[0])
+    assert r.coeffs["S"][0, 0] < 0, "electron-like carriers above mid-band give S < 0"
+
+
+def test_rta_is_first_iterate(sc1_prepared, sc1_rates):
+    """Iteration 0 is the RTA: I = (eps-mu)/T v/W, J = v/W, F = (hbar w/T) v/W, G = 0."""
+    P = sc1_prepared
+    r = O.solve_coupled_bte(P, sc1_rates, level="rta")
+    ks, bs = r.states[:, 0], r.states[:, 1]
+    v = P.vel[ks, bs]
+    np.testing.assert_allclose(r.J, v / r.W_e[:, None], rtol=1e-15)
+    np.testing.assert_allclose(r.I, ((P.eps[ks, bs] - P.wl.mu_eV) / P.wl.T_K)[:, None] * v / r.W_e[:, None],
+                               rtol=1e-15)
+    ok = P.w > P.wl.omega_min_eV
+    np.testing.assert_allclose(r.F[ok], (P.w[ok] / P.wl.T_K)[:, None] * P.vph[ok] / r.W_ph[ok][:, None], rtol=1e-15)
+    assert np.all(r.G == 0)
+    d = O.solve_coupled_bte(P, sc1_rates, level="dragged")
+    for key in r.coeffs:
+        np.testing.assert_array_equal(d.rta_coeffs[key], r.coeffs[key])
+
+
+def test_kelvin_onsager_identity_after_correction(sc1_prepared, sc1_rates):
+    """After the correction sigma S = (alpha_el + alpha_ph)/T holds (isotropic case), and
+    sigmaS[I_diff] = alpha_el/T is an identity for I_diff = (eps-mu) J/(eT)."""
+    P = sc1_prepared
+    r = O.solve_coupled_bte(P, sc1_rates, level="dragged", ko=True)
+    c = r.coeffs
+    T = P.wl.T_K
+    np.testing.assert_allclose(c["sigmaS"], (c["alpha_el"] + c["alpha_ph"]) / T, rtol=1e-11,
+                               atol=1e-11 * np.abs(c["sigmaS"]).max())
+    sp = O.StateSpace(P, sc1_rates)
+    I_diff = ((sp.eps - P.wl.mu_eV) / T)[:, None] * r.J
+    np.testing.assert_allclose(sp.electron_tensors(I_diff, r.J)["sigmaS"], c["alpha_el"] / T, rtol=1e-13,
+                               atol=1e-13 * np.abs(c["alpha_el"]).max() / T)
+    assert 0.0 < r.lambdas[-1] < 2.0
+
+
+def test_sigma_f_sum_rule():
+    """Units and BZ weights of sigma: with a constant relaxation time tau (J = v tau) the
+    mesh sum sum_k f(1-f)/kT v_x^2 equals sum_k f d2eps/dk_x^2 / hbar^2 (integration by
+    parts over the periodic zone), so sigma_xx = d_s e tau 2 t a^2 <f cos(k_x a)> / (V hbar^2)
+    (t, hbar in eV units).  Hot, wide-window case on the O_h IBZ so that the symmetrisation
+    of the sums is pinned too."""
+    wl = S.workload_sc1(n=40)
+    wl = dataclasses.replace(wl, T_K=20000.0, mu_eV=-2.0, window=(-6.5, 6.5))
+    P = O.prepare(wl)
+    sp = O.StateSpace(P)
+    tau = 1e-14
+    J = sp.v * tau
+    I = ((sp.eps - wl.mu_eV) / wl.T_K)[:, None] * J
+    sig = sp.electron_tensors(I, J)["sigma"]
+    kc = P.kidx / np.array(wl.kmesh)
+    f = O.fermi(P.eps[:, 0], wl.mu_eV, wl.T_K)
+    a_m = 3.0 * A_M
+    V = (3.0 * A_M) ** 3
+    expect = 2.0 * O.E_CHARGE * tau * 2.0 * 1.0 * a_m ** 2 * np.mean(f * np.cos(2 * np.pi * kc[:, 0])) / (V * HB ** 2)
+    np.testing.assert_allclose(np.diag(sig), expect, rtol=1e-7)
+
+
+def test_kappa_ph_classical_limit():
+    """Units of kappa_ph: constant tau, k_B T >> hbar w, so (hbar w)^2 n(1+n) -> (k_B T)^2 and
+    kappa_xx = (k_B tau / V) (1/N) sum_qs v_x^2.  For the nearest-neighbour spring model the
+    x-polarised branch carries v_x = (w_max a/2 hbar) cos(q_x a/2); when it is degenerate with
+    d-1 other branches the subspace-averaged velocities give that branch's v_x^2 / d in
+    total.  Modes with w = 0 are excluded."""
+    n = 8
+    wl = dataclasses.replace(S.workload_sc1(n=n), T_K=3.0e5)
+    P = O.prepare(wl)
+    sp = O.StateSpace(P)
+    tau = 1e-12
+    F = (P.w / wl.T_K)[..., None] * P.vph * tau
+    kap = sp.phonon_tensors(F, np.zeros_like(F))["kappa_ph"]
+    kB = O.KB_EVK * O.E_CHARGE
+    vmax = 0.030 * 3.0 / (2 * HB) * A_M
+    qc = P.qidx / n
+    wa = 0.030 * np.abs(np.sin(np.pi * qc))
+    tot = 0.0
+    for q in range(P.Nq):
+        if wa[q, 0] <= 1e-4:
+            continue
+        d = np.count_nonzero(np.abs(wa[q] - wa[q, 0]) < 1e-6)
+        tot += np.cos(np.pi * qc[q, 0]) ** 2 / d
+    expect = kB * tau / (3.0 * A_M) ** 3 * vmax ** 2 * tot / P.Nq
+    np.testing.assert_allclose(np.diag(kap), expect, rtol=1e-6)
+
+
+def test_fixed_point_equals_dense_solve(sc1_full_prepared, sc1_full_rates):
+    """With the Kelvin-Onsager step off, the converged coupled iteration solves the linear
+    system of the four BTEs.  Assemble that system as a dense matrix from the rate list
+    and solve it directly (least squares: electron-number conservation makes it singular
+    along constant I), then compare the coefficients."""
+    P, R = sc1_full_prepared, sc1_full_rates
+    it = O.solve_coupled_bte(P, R, level="dragged", ko=False, tol=1e-12)
+    assert it.converged
+    sp = O.StateSpace(P, R)
+    ne, nq, nbr = len(sp.states), P.Nq, sp.nbr
+    nph = nq * nbr
+    ds = P.wl.model.spin_deg
+    W_e, W_ph = it.W_e, it.W_ph
+    ok = P.w.ravel() > P.wl.omega_min_eV
+    M = np.zeros((ne + nph, ne + nph))
+    for e in range(len(R.Xp)):
+        i, j = sp.row[e], sp.col[e]
+        qs = R.iq[e] * nbr + R.s[e]
+        mqs = sp.mq[e] * nbr + R.s[e]
+        c = 1.0 / (sp.ff[i] * W_e[i])
+        M[i, j] += c * (R.Xp[e] + R.Xm[e])
+        M[i, ne + qs] -= c * R.Xp[e]
+        M[i, ne + mqs] += c * R.Xm[e]
+        y = R.Xp[e] * P.Nq / P.Nk
+        cp = ds / (sp.nn1.ravel()[qs] * W_ph.ravel()[qs])
+        M[ne + qs, j] += cp * y
+        M[ne + qs, i] -= cp * y
+    A = np.eye(ne + nph) - M
+    keep = np.concatenate([np.ones(ne, bool), ok])
+    A = A[np.ix_(keep, keep)]
+    T, mu = P.wl.T_K, P.wl.mu_eV
+    I0 = ((sp.eps - mu) / T)[:, None] * sp.v / W_e[:, None]
+    J0 = sp.v / W_e[:, None]
+    F0 = ((P.w / T)[..., None] * P.vph / np.where(W_ph > 0, W_ph, 1.0)[..., None]).reshape(nph, 3)
+    bT = np.vstack([I0, F0[ok]])
+    bE = np.vstack([J0, np.zeros((ok.sum(), 3))])
+    xT = np.linalg.lstsq(A, bT, rcond=None)[0]
+    xE = np.linalg.lstsq(A, bE, rcond=None)[0]
+    F = np.zeros((nph, 3))
+    G = np.zeros((nph, 3))
+    F[ok] = xT[ne:]
+    G[ok] = xE[ne:]
+    c = O.coefficients_from_responses(sp, xT[:ne], xE[:ne], F.reshape(nq, nbr, 3), G.reshape(nq, nbr, 3))
+    for key in ("sigma", "sigmaS", "alpha_el", "kappa0_el", "alpha_ph", "kappa_ph"):
+        np.testing.assert_allclose(it.coeffs[key], c[key], rtol=1e-7, atol=1e-7 * np.abs(c[key]).max())
