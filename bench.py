@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark of the e-ph scattering + coupled-BTE hot path on GB300.
+
+One step = build_meshes_ibz + compute_transition_rates + solve_coupled_bte (dragged,
+tol 1e-10, Kelvin-Onsager on) + transport_coefficients for the 4-band / 6-branch model on
+24^3 k and q meshes, with the Wannier model already resident on the device.  L2 is
+flushed (256 MB write) before every step.  The metric is transition rates per second:
+(k m, q, n, s) tuples interpolated and delta-weighted per step / step time.
+
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU (the path
+needs no exchange on one device; the value is all ranks' tuples / the slowest rank).
+
+--impl reference times the FP64 CPU oracle on the host cores on bounded samples of the
+same workload (the slow reference arm)."""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "transition rates/s and s to converged σ,S,κ at 1e-6 rel: mixed+batched vs FP64"
+UNIT = "transition rates/s"
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (recipe table); no measured FP64 peak is provided
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=24, help="k and q mesh size per dimension")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def profile_traffic(kernel_tag, source_file):
+    """dram bytes per unit from a committed ncu summary, if it was taken on the current source."""
+    path = os.path.join(ROOT, "profiles", f"ncu_{kernel_tag}.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for ln in open(path):
+        if ":" in ln:
+            k, v = ln.split(":", 1)
+            kv[k.strip()] = v.strip()
+    src = os.path.join(ROOT, "paper_2109_08547_gb300", "csrc", source_file)
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if kv.get("source_sha256_16") != h:
+        return None
+    try:
+        return float(kv["dram_bytes_per_unit"]), kv.get("unit", "")
+    except (KeyError, ValueError):
+        return None
+
+
+def oracle_sample(wl, n_q=None, row_index=None):
+    """Time the oracle's transition rates for (part of) one irreducible row."""
+    import numpy as np
+    import oracle as O
+    P = O.prepare(wl)
+    ibzw = O.ibz_window_points(P)
+    row = int(ibzw[len(ibzw) // 2 if row_index is None else row_index])
+    t0 = time.perf_counter()
+    if n_q is None:
+        R = O.transition_rates(P, ks=[row])
+    else:
+        # restrict the row to its first n_q partner q points
+        allq = np.arange(P.Nq)
+        kps = O.kplusq(P, row, allq)
+        qs = allq[P.active[kps].any(axis=1)][:n_q]
+        mask = np.zeros(P.Nq, bool)
+        mask[qs] = True
+        P2 = P
+        R = _rates_subset(O, P2, row, mask)
+    dt = time.perf_counter() - t0
+    return R.n_tuples, dt, row
+
+
+def _rates_subset(O, P, row, qmask):
+    import dataclasses
+    import numpy as np
+    act = P.active.copy()
+    kps = O.kplusq(P, row, np.arange(P.Nq))
+    keep = np.zeros_like(act)
+    keep[kps[qmask]] = act[kps[qmask]]
+    keep[row] = act[row]
+    return O.transition_rates(dataclasses.replace(P, active=keep), ks=[row])
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2109_08547_gb300 import synthetic as S
+    wl = S.workload_cscl4(args.n)
+    steps = []
+    for i in range(args.warmup + args.steps):
+        nt, dt, row = oracle_sample(wl, n_q=256)
+        if i >= args.warmup:
+            steps.append((nt, dt))
+    tot = sum(s[0] for s in steps)
+    el = sum(s[1] for s in steps)
+    val = tot / el
+    cores = os.cpu_count()
+    out = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "model": "4-band/6-branch CsCl-type, 5^3 R grids", "kmesh": list(wl.kmesh),
+                   "qmesh": list(wl.qmesh), "T_K": wl.T_K, "mu_eV": wl.mu_eV, "window_eV": list(wl.window)},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "FP64 oracle transition rates of 256 (k,q) pairs of one irreducible row per step"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2109_08547_gb300 import binding as B
+    from paper_2109_08547_gb300 import synthetic as S
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    wl = S.workload_cscl4(args.n)
+    ctx = B.Context(local, stream=stream.cuda_stream)
+    B.set_wannier_model(ctx, wl.model)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def step():
+        return B.run_path(ctx, wl, level="dragged", ko_correction=True)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    results = []
+    l0 = B.kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        results.append(step())
+    torch.cuda.synchronize()
+    barrier()
+    el = time.perf_counter() - t0
+    launches = B.kernel_launches() - l0
+    clocks = sampler.stop()
+    el_t = torch.tensor([el], dtype=torch.float64, device=dev)
+    tup_t = torch.tensor([float(sum(r.rates["n_tuples"] for r in results))], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(el_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tup_t, op=dist.ReduceOp.SUM)
+    el_max = float(el_t.item())
+    value = float(tup_t.item()) / el_max
+    r0 = results[-1]
+
+    # dominant kernel and its roofline (device time measured with CUDA events in this run)
+    ms_b = statistics.mean(r.rates["ms_stage_b"] for r in results)
+    ms_e = statistics.mean(r.solve["ms_e_sweep"] for r in results)
+    peaks = measured_peaks()
+    if ms_b >= ms_e:
+        achieved = r0.rates["stage_b_flops"] / (ms_b * 1e-3) / 1e12
+        tr = profile_traffic("stage_b_rates", "vertex.cu")
+        roof = {"kernel": "k_stage_b_rates (R_ph contraction + rotations + rates, FP64)", "bound": "alu",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "nominal GB300 FP64 rate from the profiling recipe table (no measured FP64 peak)",
+                "traffic": (tr[0] * r0.rates["n_pairs"]) if tr else None,
+                "ms_per_step": ms_b, "share_of_step": ms_b / (1e3 * el_max / args.steps)}
+    else:
+        nsw = r0.solve["n_sweeps"]
+        achieved = r0.solve["e_sweep_bytes"] * nsw / (ms_e * 1e-3) / 1e9
+        pk = peaks.get("hbm_gbs", 6800.0)
+        tr = profile_traffic("e_sweep", "bte.cu")
+        roof = {"kernel": "k_e_sweep (electron gather sweep)", "bound": "hbm", "achieved": achieved, "peak": pk,
+                "unit": "GB/s", "frac": achieved / pk,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback",
+                "traffic": (tr[0] * r0.rates["n_entries"]) if tr else None,
+                "ms_per_step": ms_e, "share_of_step": ms_e / (1e3 * el_max / args.steps)}
+
+    # end-to-end through the C ABI with host buffers: model H2D (pinned) + path + coefficients D2H
+    e2e = None
+    if not args.no_e2e:
+        m = wl.model
+        pinned = {}
+        for name in ("H_R", "D_R", "g_R", "Re", "Rd", "Rge", "Rgp", "sym_rot", "sym_cart", "mass_amu", "tau_cart"):
+            a = np.ascontiguousarray(getattr(m, name))
+            t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+            t.numpy()[...] = a
+            pinned[name] = t
+        import dataclasses
+        mp = dataclasses.replace(m, **{k: v.numpy() for k, v in pinned.items()})
+        h2d = int(sum(v.numel() * v.element_size() for v in pinned.values()))
+        ctx2 = B.Context(local, stream=stream.cuda_stream)
+        barrier()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        tup = 0
+        for _ in range(args.steps):
+            flush.zero_()
+            B.set_wannier_model(ctx2, mp)
+            rr = B.run_path(ctx2, wl, level="dragged", ko_correction=True)
+            tup += rr.rates["n_tuples"]
+        torch.cuda.synchronize()
+        barrier()
+        el2 = time.perf_counter() - t1
+        e2_t = torch.tensor([el2], dtype=torch.float64, device=dev)
+        tu_t = torch.tensor([float(tup)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(e2_t, op=dist.ReduceOp.MAX)
+            dist.all_reduce(tu_t, op=dist.ReduceOp.SUM)
+        e2e = {"value": float(tu_t.item()) / float(e2_t.item()), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 8 * 9 * 8, "s_per_step": float(e2_t.item()) / args.steps}
+        ctx2.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nt, dt, row = oracle_sample(wl)
+        cpu = {"value": nt / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"FP64 oracle transition rates of one irreducible row (k index {row}, {nt} tuples, "
+                         f"{dt:.1f} s)"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "model": "4-band/6-branch CsCl-type cubic, 5^3 x 5^3 R grids (g 24 MB)",
+                       "kmesh": list(wl.kmesh), "qmesh": list(wl.qmesh), "T_K": wl.T_K, "mu_eV": wl.mu_eV,
+                       "window_eV": list(wl.window), "sigma_eV": wl.sigma_eV, "level": "dragged+KO",
+                       "tol": wl.tol, "l2": "256 MB buffer written before every step",
+                       "parallelism": f"replicas x{world}", "tuples_per_step": r0.rates["n_tuples"],
+                       "entries": r0.rates["n_entries"], "pairs": r0.rates["n_pairs"]},
+            "s_to_converged": 1e-3 * el_max / args.steps,
+            "phases_ms": {"rates": r0.rates["ms"], "stage_a": r0.rates["ms_stage_a"],
+                          "stage_b": r0.rates["ms_stage_b"], "solve": r0.solve["ms"],
+                          "e_sweeps": r0.solve["ms_e_sweep"], "ph_sweeps": r0.solve["ms_ph_sweep"],
+                          "n_sweeps": r0.solve["n_sweeps"], "outer_iters": r0.solve["outer_iters"]},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(out))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

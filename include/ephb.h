@@ -1,0 +1,248 @@
+/*
+ * ephb.h -- C ABI of the GB300 e-ph scattering + coupled-BTE library.
+ *
+ * The library computes, on one CUDA GPU, the hot path of the coupled electron-phonon
+ * Boltzmann transport method of arXiv 2109.08547:
+ *   - Wannier-to-Bloch interpolation of H, D and the e-ph vertex g (section
+ *     "Electrons, phonons, and interactions", Eqs. H_mn(k), D_ss'(q), g^smn_kq);
+ *   - transition rates X^+/X^- over irreducible k x full q inside the transport window
+ *     (Eq. X^e-ph) and the phonon-side rates Y (Eq. Y^ph-e);
+ *   - the RTA, self and drag terms and the unified single-iterator coupled solution with
+ *     the Kelvin-Onsager correction (section "Coupled and decoupled BTEs" and
+ *     "Transport coefficients");
+ *   - the transport coefficient tensors (Eqs. sigma/sigmaS, alpha_el/kappa0_el,
+ *     alpha_ph/kappa_ph).
+ *
+ * Conventions for every call:
+ *   - All pointers in argument structs are HOST pointers; the library copies what it
+ *     needs during the call and keeps no reference to caller memory.
+ *   - All device memory is owned by the context and released by ephb_destroy.
+ *   - Every kernel runs on the context's stream (the stream given to ephb_create, or a
+ *     stream the context creates when NULL is given).  Calls return after the work they
+ *     enqueue has completed, unless stated otherwise.
+ *   - No call aborts or throws; failures return a status and set a message readable with
+ *     ephb_last_error.  Calls made in the wrong order return EPHB_ESTATE.
+ *   - There is no CPU fallback: every numerical step runs in the library's CUDA kernels.
+ *
+ * Units: energies eV, lengths Angstrom, temperatures K, rates 1/s, velocities m/s,
+ * coefficient tensors SI (sigma S/m, S V/K, kappa W/(m K), alpha A/m), row-major 3x3.
+ */
+#ifndef EPHB_H
+#define EPHB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ephb_ctx ephb_ctx;
+
+typedef enum {
+  EPHB_OK = 0,
+  EPHB_EINVAL = 1,     /* bad argument (sizes, pointers, unsupported option)           */
+  EPHB_ENOMEM = 2,     /* device or host allocation failed                             */
+  EPHB_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed                  */
+  EPHB_ESTATE = 4,     /* call made before the calls it depends on                     */
+  EPHB_ENOCONV = 5,    /* iteration limit reached; outputs hold the last iterate       */
+  EPHB_ETIMEOUT = 6,   /* a bounded device-side wait gave up                           */
+  EPHB_EINTERNAL = 7
+} ephb_status;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t (or NULL
+ * for a context-owned stream).  On success *out receives the context. */
+ephb_status ephb_create(ephb_ctx **out, int device, void *cuda_stream);
+
+/* Release every device buffer of the context.  NULL is accepted. */
+void ephb_destroy(ephb_ctx *ctx);
+
+/* Message of the last failed call on ctx (valid until the next call on ctx). */
+const char *ephb_last_error(const ephb_ctx *ctx);
+
+/* ----------------------------------------------------------------------------------
+ * Wannier model (section "Electrons, phonons, and interactions").
+ *   H(k)   = sum_r exp(i 2pi k.Re[r]) H_R[r]                     (Eq. H_mn(k))
+ *   D(q)   = sum_r exp(i 2pi q.Rd[r]) D_R[r]                     (Eq. D_ss'(q), short range)
+ *   g^s_mn(k,q) = sqrt(omega_ref/hbar w_sq) sum_{m'n'alpha} c*_{n'n}(k') c_{m'm}(k)
+ *          [sum_{re,rp} exp(i 2pi (k.Rge[re] + q.Rgp[rp])) g_R[re][rp][m'][n'][alpha]]
+ *          u_{alpha s}(q) / sqrt(mass[alpha/3]/mean mass)          (Eq. g^smn_kq)
+ * with c the eigenvector columns of H (the paper's U_k = c^dagger) and u those of D.
+ * The 1/N_e, 1/N_ph and Wigner-Seitz weights are taken as already folded into the arrays.
+ * Complex arrays are interleaved (re, im) doubles, row-major in the order shown.
+ * --------------------------------------------------------------------------------*/
+typedef struct {
+  double lattice[3][3];        /* rows a1, a2, a3 (Angstrom)                               */
+  int nat;                     /* atoms per cell; branches = 3*nat (<= 12)                 */
+  const double *mass_amu;      /* [nat]                                                    */
+  const double *tau_cart;      /* [nat][3] Angstrom (informational)                        */
+  int nb;                      /* Wannier bands (<= 8)                                     */
+  int nRe;                     /* Hamiltonian R vectors                                    */
+  const int32_t *Re;           /* [nRe][3] integer crystal coordinates                     */
+  const double *H_R;           /* [nRe][nb][nb] complex, eV                                */
+  int nRd;
+  const int32_t *Rd;           /* [nRd][3]                                                 */
+  const double *D_R;           /* [nRd][3nat][3nat] complex, eV^2 (mass scaled)            */
+  int nRge, nRgp;
+  const int32_t *Rge;          /* [nRge][3]                                                */
+  const int32_t *Rgp;          /* [nRgp][3]                                                */
+  const double *g_R;           /* [nRge][nRgp][nb][nb][3nat] complex, eV                   */
+  double omega_ref_eV;         /* hbar*omega at which g_R is quoted                        */
+  int nsym;                    /* point operations (1..48); 1 = identity only              */
+  const int32_t *sym_rot;      /* [nsym][3][3] integer, acting on reciprocal crystal k     */
+  const double *sym_cart;      /* [nsym][3][3] the same operations on Cartesian vectors    */
+  double spin_deg;             /* d_s                                                      */
+  double bg_rate_coeff;        /* phonon background rate W_bg = coeff (w/w_bg)^2 (T/T_bg)  */
+  double bg_omega_ref_eV;
+  double bg_T_ref;
+} ephb_model;
+
+/* Validate and copy the model to the device.  Resets meshes, rates and solutions. */
+ephb_status ephb_set_wannier_model(ephb_ctx *ctx, const ephb_model *model);
+
+/* ----------------------------------------------------------------------------------
+ * Meshes, bands, phonons, irreducible wedge and transport window
+ * (Eqs. H_mn(k), v_mk, D_ss'(q), v_sq; section "Workflow and structure": symmetry,
+ * window-restricted IBZ).  Gamma-centred meshes; the k mesh must be an integer multiple
+ * of the q mesh per dimension, and cubic (n x n x n) when nsym > 1.  An electron state
+ * is active when window_lo <= eps <= window_hi.  Modes with hbar w <= omega_min are
+ * excluded from every rate and sum.  Velocities and |g|^2 are averaged over degenerate
+ * subspaces (|d eps| < degen_tol).
+ * --------------------------------------------------------------------------------*/
+typedef struct {
+  int kmesh[3];
+  int qmesh[3];
+  double window_lo_eV, window_hi_eV;
+  double degen_tol_eV;         /* default 1e-6 */
+  double omega_min_eV;         /* default 1e-4 */
+} ephb_mesh_opts;
+
+typedef struct {
+  int64_t nk, nq;              /* full mesh sizes                                          */
+  int64_t n_active_states;     /* active (k,m) on the full k mesh                          */
+  int64_t n_ibz;               /* irreducible points of the k mesh                         */
+  int64_t n_ibz_window;        /* irreducible points with an active band                   */
+  int64_t n_pairs;             /* (irreducible-window k, q) with an active band at k+q     */
+} ephb_mesh_info;
+
+ephb_status ephb_build_meshes_ibz(ephb_ctx *ctx, const ephb_mesh_opts *opts, ephb_mesh_info *out);
+
+/* ----------------------------------------------------------------------------------
+ * Transition rates (Eq. X^e-ph, with Y^ph-e = X^+ N_q/N_k for the phonon side):
+ *   X^+ = 2pi/(hbar N_q) |g|^2 f_mk (1-f_nk') n_sq     delta(eps_nk' - eps_mk - hbar w_sq)
+ *   X^- = 2pi/(hbar N_q) |g|^2 f_mk (1-f_nk') (1+n_sq) delta(eps_nk' - eps_mk + hbar w_sq)
+ * for every irreducible-window k, active m, q with k' = [k+q], active n and branch s.
+ * delta is a Gaussian of standard deviation sigma, exactly zero beyond cutoff*sigma; an
+ * entry is stored when either argument is within the cut.
+ * ninst must be 1.  precision must be EPHB_FP64 (the other modes return EPHB_EINVAL).
+ * --------------------------------------------------------------------------------*/
+typedef struct { double T_K, mu_eV; } ephb_thermo;
+typedef struct { double sigma_eV, cutoff_sigmas; } ephb_delta;
+typedef enum { EPHB_FP64 = 0, EPHB_SPLIT_TF32 = 1, EPHB_SPLIT_BF16 = 2 } ephb_precision;
+
+typedef struct {
+  int64_t n_tuples;            /* (k m, q, n, s) tuples interpolated and delta-weighted    */
+  int64_t n_entries;           /* stored electron-side entries (rows: k, m)                */
+  int64_t n_ph_entries;        /* stored phonon-side entries (rows: q, s)                  */
+  int64_t n_pairs;
+  double ms;                   /* device time of the call (CUDA events)                    */
+  double ms_stage_a;           /* device time of the R_e contraction kernels               */
+  double ms_stage_b;           /* device time of the R_ph contraction + rate kernels       */
+  double stage_a_flops;        /* algorithmic flops of the R_e contraction                 */
+  double stage_b_flops;        /* algorithmic flops of the R_ph contraction + rotations    */
+} ephb_rates_info;
+
+ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst, int ninst,
+                                          const ephb_delta *delta, ephb_precision precision,
+                                          ephb_rates_info *out);
+
+/* ----------------------------------------------------------------------------------
+ * Coupled BTE (section "Coupled and decoupled BTEs"; Kelvin-Onsager correction from
+ * "Transport coefficients").  Iteration 0 is the RTA.  Each later (phonon) iteration
+ * sets F = F0 + dF^D[I], G = dG^D[J]; iterates the electron equations
+ * I = I0 + dI^S[I] + dI^D[F], J = J0 + dJ^S[J] + dJ^D[G] until the electron tensors
+ * change by less than inner_tol; then (ko_correction) replaces I by I_diff + lambda I_drag
+ * with lambda the least-squares solution of sigmaS_drag[lambda I_drag] = alpha_ph/T.
+ * Convergence: max relative Frobenius change of the coefficient tensors < tol.
+ * The phonon background W_bg stands in for ph-ph and ph-isotope scattering, whose self
+ * terms are therefore absent.
+ * --------------------------------------------------------------------------------*/
+typedef enum { EPHB_RTA = 0, EPHB_PARTIAL = 1, EPHB_DRAGLESS = 2, EPHB_DRAGGED = 3 } ephb_level;
+
+typedef struct {
+  int level;                   /* ephb_level                                               */
+  double tol;                  /* outer tolerance (e.g. 1e-10)                             */
+  double inner_tol;            /* electron loop tolerance (<= 0: 0.1*tol)                  */
+  int max_outer, max_inner;
+  int ko_correction;           /* 1: apply the Kelvin-Onsager step (dragged levels)        */
+} ephb_solve_opts;
+
+typedef struct {
+  int outer_iters;
+  int inner_iters_total;
+  int converged;
+  int n_zero_rate_states;      /* active states without partners (I = J = 0)              */
+  double residual;             /* last outer residual                                      */
+  double lambda;               /* last Kelvin-Onsager scalar (1 if not applied)            */
+  int64_t n_sweeps;            /* electron sweeps performed                                */
+  double ms;                   /* device time of the call                                  */
+  double ms_e_sweep;           /* summed device time of the electron sweep kernels         */
+  double ms_ph_sweep;          /* summed device time of the phonon drag sweep kernels      */
+  double e_sweep_bytes;        /* algorithmic HBM bytes of one electron sweep              */
+} ephb_solve_info;
+
+ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *opts, ephb_solve_info *out);
+
+/* ----------------------------------------------------------------------------------
+ * Transport coefficients of the current responses (Eqs. sigma/sigmaS,
+ * alpha_el/kappa0_el, alpha_ph/kappa_ph with 1/N_k and 1/N_q on the zone sums):
+ *   sigma, sigmaS = d_s e/(V N_k k_B T) sum_{mk} f(1-f) v (x) {J, -I}
+ *   alpha_el, kappa0_el = -d_s/(V N_k k_B T) sum (eps-mu) f(1-f) v (x) {J, -I}
+ *   alpha_ph, kappa_ph = 1/(V N_q k_B T) sum_{sq} hbar w n(1+n) v (x) {-G, F}
+ *   S = sigma^-1 sigmaS, kappa_el = kappa0_el - alpha_el S.
+ * `out` is caller-owned host memory.  inst must be 0.
+ * --------------------------------------------------------------------------------*/
+typedef struct {
+  double sigma[9], sigmaS[9], S[9], alpha_el[9], kappa0_el[9], kappa_el[9], alpha_ph[9], kappa_ph[9];
+} ephb_coeffs;
+
+ephb_status ephb_transport_coefficients(ephb_ctx *ctx, int inst, ephb_coeffs *out);
+
+/* ----------------------------------------------------------------------------------
+ * Inspection: borrowed views of the context's device arrays (valid until the next call
+ * that rebuilds them) and a copy into caller host memory.  Shapes are reported in
+ * shape[0..3] (unused dimensions 1); dtype codes: 0 f64, 1 c128, 2 i32, 3 i64, 4 u32.
+ * --------------------------------------------------------------------------------*/
+typedef enum {
+  EPHB_ARR_EPS = 0,            /* [nk][nb] f64                                             */
+  EPHB_ARR_VEL = 1,            /* [nk][nb][3] f64                                          */
+  EPHB_ARR_OMEGA = 2,          /* [nq][nbr] f64                                            */
+  EPHB_ARR_VPH = 3,            /* [nq][nbr][3] f64                                         */
+  EPHB_ARR_IBZ_REP = 4,        /* [nk] i32 full index of the representative                */
+  EPHB_ARR_IBZ_OP = 5,         /* [nk] i32 first operation S with S<k> = k                 */
+  EPHB_ARR_IBZW_LIST = 6,      /* [n_ibz_window] i32 full index of each irreducible point  */
+  EPHB_ARR_ROW_PTR = 7,        /* [n_ibz_window*nb + 1] i64 electron rows (k,m)            */
+  EPHB_ARR_ENTRY_KPNS = 8,     /* [n_entries] u32: k' | n<<21 | s<<25                      */
+  EPHB_ARR_ENTRY_X = 9,        /* [n_entries][2] f64: X^+, X^-                             */
+  EPHB_ARR_PAIR_Q = 10,        /* [n_pairs] i32 q of each pair                             */
+  EPHB_ARR_W_E = 11,           /* [n_ibz_window*nb] f64 electron W^RTA (0 when inactive)   */
+  EPHB_ARR_W_PH = 12,          /* [nq][nbr] f64 phonon W^RTA                               */
+  EPHB_ARR_I = 13,             /* [n_ibz_window*nb][3] f64                                 */
+  EPHB_ARR_J = 14,
+  EPHB_ARR_F = 15,             /* [nq][nbr][3] f64                                         */
+  EPHB_ARR_G = 16,
+  EPHB_ARR_PAIR_PTR = 17,      /* [n_ibz_window + 1] i64                                   */
+  EPHB_ARR_ACTIVE = 18,        /* [nk] u32 bit mask of active bands                        */
+  EPHB_ARR_COUNT = 19
+} ephb_array;
+
+ephb_status ephb_get_device_array(ephb_ctx *ctx, int which, void **dptr, int64_t shape[4], int *dtype);
+ephb_status ephb_copy_array_to_host(ephb_ctx *ctx, int which, void *host_dst, int64_t nbytes);
+
+/* Number of CUDA kernels the library has launched in this process (all contexts). */
+int64_t ephb_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EPHB_H */

@@ -1,0 +1,291 @@
+"""Thin ctypes binding of the C ABI in include/ephb.h.
+
+Argument marshalling only: every numerical step runs in the CUDA library.  Loading
+fails loudly when the shared library cannot be built or opened; there is no CPU path.
+Function names follow the C entry points (set_wannier_model, build_meshes_ibz,
+compute_transition_rates, solve_coupled_bte, transport_coefficients).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, ENOCONV, ETIMEOUT, EINTERNAL = range(8)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ESTATE", "ENOCONV", "ETIMEOUT", "EINTERNAL"]
+FP64, SPLIT_TF32, SPLIT_BF16 = 0, 1, 2
+RTA, PARTIAL, DRAGLESS, DRAGGED = 0, 1, 2, 3
+LEVELS = {"rta": RTA, "partial": PARTIAL, "dragless": DRAGLESS, "dragged": DRAGGED}
+
+ARR = dict(eps=0, vel=1, omega=2, vph=3, ibz_rep=4, ibz_op=5, ibzw_list=6, row_ptr=7, entry_kpns=8, entry_x=9,
+           pair_q=10, w_e=11, w_ph=12, I=13, J=14, F=15, G=16, pair_ptr=17, active=18)
+_DT = {0: np.float64, 1: np.complex128, 2: np.int32, 3: np.int64, 4: np.uint32}
+
+EXPORTED = ["ephb_create", "ephb_destroy", "ephb_last_error", "ephb_set_wannier_model", "ephb_build_meshes_ibz",
+            "ephb_compute_transition_rates", "ephb_solve_coupled_bte", "ephb_transport_coefficients",
+            "ephb_get_device_array", "ephb_copy_array_to_host", "ephb_kernel_launches"]
+
+_pd = C.POINTER(C.c_double)
+_pi = C.POINTER(C.c_int32)
+
+
+class ModelC(C.Structure):
+    _fields_ = [("lattice", C.c_double * 9), ("nat", C.c_int), ("mass_amu", _pd), ("tau_cart", _pd),
+                ("nb", C.c_int), ("nRe", C.c_int), ("Re", _pi), ("H_R", _pd), ("nRd", C.c_int), ("Rd", _pi),
+                ("D_R", _pd), ("nRge", C.c_int), ("nRgp", C.c_int), ("Rge", _pi), ("Rgp", _pi), ("g_R", _pd),
+                ("omega_ref_eV", C.c_double), ("nsym", C.c_int), ("sym_rot", _pi), ("sym_cart", _pd),
+                ("spin_deg", C.c_double), ("bg_rate_coeff", C.c_double), ("bg_omega_ref_eV", C.c_double),
+                ("bg_T_ref", C.c_double)]
+
+
+class MeshOptsC(C.Structure):
+    _fields_ = [("kmesh", C.c_int * 3), ("qmesh", C.c_int * 3), ("window_lo_eV", C.c_double),
+                ("window_hi_eV", C.c_double), ("degen_tol_eV", C.c_double), ("omega_min_eV", C.c_double)]
+
+
+class MeshInfoC(C.Structure):
+    _fields_ = [("nk", C.c_int64), ("nq", C.c_int64), ("n_active_states", C.c_int64), ("n_ibz", C.c_int64),
+                ("n_ibz_window", C.c_int64), ("n_pairs", C.c_int64)]
+
+
+class ThermoC(C.Structure):
+    _fields_ = [("T_K", C.c_double), ("mu_eV", C.c_double)]
+
+
+class DeltaC(C.Structure):
+    _fields_ = [("sigma_eV", C.c_double), ("cutoff_sigmas", C.c_double)]
+
+
+class RatesInfoC(C.Structure):
+    _fields_ = [("n_tuples", C.c_int64), ("n_entries", C.c_int64), ("n_ph_entries", C.c_int64),
+                ("n_pairs", C.c_int64), ("ms", C.c_double), ("ms_stage_a", C.c_double), ("ms_stage_b", C.c_double),
+                ("stage_a_flops", C.c_double), ("stage_b_flops", C.c_double)]
+
+
+class SolveOptsC(C.Structure):
+    _fields_ = [("level", C.c_int), ("tol", C.c_double), ("inner_tol", C.c_double), ("max_outer", C.c_int),
+                ("max_inner", C.c_int), ("ko_correction", C.c_int)]
+
+
+class SolveInfoC(C.Structure):
+    _fields_ = [("outer_iters", C.c_int), ("inner_iters_total", C.c_int), ("converged", C.c_int),
+                ("n_zero_rate_states", C.c_int), ("residual", C.c_double), ("lambda_", C.c_double),
+                ("n_sweeps", C.c_int64), ("ms", C.c_double), ("ms_e_sweep", C.c_double),
+                ("ms_ph_sweep", C.c_double), ("e_sweep_bytes", C.c_double)]
+
+
+class CoeffsC(C.Structure):
+    _fields_ = [(n, C.c_double * 9) for n in
+                ("sigma", "sigmaS", "S", "alpha_el", "kappa0_el", "kappa_el", "alpha_ph", "kappa_ph")]
+
+
+class EphbError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+def load(path: str = None):
+    """Open (building first if sources changed) the CUDA library."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.build()
+    lib = C.CDLL(path)
+    lib.ephb_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_void_p]
+    lib.ephb_destroy.argtypes = [C.c_void_p]
+    lib.ephb_destroy.restype = None
+    lib.ephb_last_error.argtypes = [C.c_void_p]
+    lib.ephb_last_error.restype = C.c_char_p
+    lib.ephb_set_wannier_model.argtypes = [C.c_void_p, C.POINTER(ModelC)]
+    lib.ephb_build_meshes_ibz.argtypes = [C.c_void_p, C.POINTER(MeshOptsC), C.POINTER(MeshInfoC)]
+    lib.ephb_compute_transition_rates.argtypes = [C.c_void_p, C.POINTER(ThermoC), C.c_int, C.POINTER(DeltaC),
+                                                  C.c_int, C.POINTER(RatesInfoC)]
+    lib.ephb_solve_coupled_bte.argtypes = [C.c_void_p, C.POINTER(SolveOptsC), C.POINTER(SolveInfoC)]
+    lib.ephb_transport_coefficients.argtypes = [C.c_void_p, C.c_int, C.POINTER(CoeffsC)]
+    lib.ephb_get_device_array.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
+                                          C.POINTER(C.c_int)]
+    lib.ephb_copy_array_to_host.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]
+    lib.ephb_kernel_launches.argtypes = []
+    for name in EXPORTED:
+        if name not in ("ephb_destroy", "ephb_last_error", "ephb_kernel_launches"):
+            getattr(lib, name).restype = C.c_int
+    lib.ephb_kernel_launches.restype = C.c_int64
+    _lib = lib
+    return lib
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process."""
+    return int(load().ephb_kernel_launches())
+
+
+def _check(ctx, status, allow=()):
+    if status != OK and status not in allow:
+        msg = _lib.ephb_last_error(ctx.handle).decode() if ctx is not None and ctx.handle else ""
+        raise EphbError(status, msg)
+    return status
+
+
+class Context:
+    """Owns one ephb_ctx (device memory of one model / mesh / rate set)."""
+
+    def __init__(self, device: int = 0, stream: int = None):
+        lib = load()
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream(device).cuda_stream
+            except ImportError:
+                stream = None
+        h = C.c_void_p()
+        st = lib.ephb_create(C.byref(h), int(device), C.c_void_p(stream) if stream else None)
+        if st != OK:
+            raise EphbError(st, "ephb_create failed (is a CUDA device visible?)")
+        self.handle = h
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.ephb_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def _arr(x, dtype):
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a
+
+
+def set_wannier_model(ctx: Context, m) -> None:
+    """ephb_set_wannier_model from a WannierModel (numpy arrays)."""
+    keep = {
+        "mass": _arr(m.mass_amu, np.float64), "tau": _arr(m.tau_cart, np.float64), "Re": _arr(m.Re, np.int32),
+        "H": _arr(m.H_R, np.complex128), "Rd": _arr(m.Rd, np.int32), "D": _arr(m.D_R, np.complex128),
+        "Rge": _arr(m.Rge, np.int32), "Rgp": _arr(m.Rgp, np.int32), "g": _arr(m.g_R, np.complex128),
+        "rot": _arr(m.sym_rot, np.int32), "cart": _arr(m.sym_cart, np.float64),
+    }
+    mc = ModelC()
+    mc.lattice[:] = list(np.asarray(m.lattice, dtype=np.float64).ravel())
+    mc.nat = int(m.mass_amu.shape[0])
+    mc.mass_amu = keep["mass"].ctypes.data_as(_pd)
+    mc.tau_cart = keep["tau"].ctypes.data_as(_pd)
+    mc.nb = int(m.nb)
+    mc.nRe = int(keep["Re"].shape[0])
+    mc.Re = keep["Re"].ctypes.data_as(_pi)
+    mc.H_R = keep["H"].ctypes.data_as(_pd)
+    mc.nRd = int(keep["Rd"].shape[0])
+    mc.Rd = keep["Rd"].ctypes.data_as(_pi)
+    mc.D_R = keep["D"].ctypes.data_as(_pd)
+    mc.nRge = int(keep["Rge"].shape[0])
+    mc.nRgp = int(keep["Rgp"].shape[0])
+    mc.Rge = keep["Rge"].ctypes.data_as(_pi)
+    mc.Rgp = keep["Rgp"].ctypes.data_as(_pi)
+    mc.g_R = keep["g"].ctypes.data_as(_pd)
+    mc.omega_ref_eV = float(m.omega_ref_eV)
+    mc.nsym = int(keep["rot"].shape[0])
+    mc.sym_rot = keep["rot"].ctypes.data_as(_pi)
+    mc.sym_cart = keep["cart"].ctypes.data_as(_pd)
+    mc.spin_deg = float(m.spin_deg)
+    mc.bg_rate_coeff = float(m.bg_rate_coeff)
+    mc.bg_omega_ref_eV = float(m.bg_omega_ref_eV)
+    mc.bg_T_ref = float(m.bg_T_ref)
+    _check(ctx, _lib.ephb_set_wannier_model(ctx.handle, C.byref(mc)))
+
+
+def build_meshes_ibz(ctx: Context, kmesh, qmesh, window, degen_tol_eV=1e-6, omega_min_eV=1e-4) -> dict:
+    o = MeshOptsC()
+    o.kmesh[:] = [int(x) for x in kmesh]
+    o.qmesh[:] = [int(x) for x in qmesh]
+    o.window_lo_eV, o.window_hi_eV = float(window[0]), float(window[1])
+    o.degen_tol_eV = float(degen_tol_eV)
+    o.omega_min_eV = float(omega_min_eV)
+    info = MeshInfoC()
+    _check(ctx, _lib.ephb_build_meshes_ibz(ctx.handle, C.byref(o), C.byref(info)))
+    return {f: getattr(info, f) for f, _ in MeshInfoC._fields_}
+
+
+def compute_transition_rates(ctx: Context, T_K, mu_eV, sigma_eV=0.01, cutoff_sigmas=8.0, precision=FP64) -> dict:
+    th = ThermoC(float(T_K), float(mu_eV))
+    de = DeltaC(float(sigma_eV), float(cutoff_sigmas))
+    info = RatesInfoC()
+    _check(ctx, _lib.ephb_compute_transition_rates(ctx.handle, C.byref(th), 1, C.byref(de), int(precision),
+                                                   C.byref(info)))
+    return {f: getattr(info, f) for f, _ in RatesInfoC._fields_}
+
+
+def solve_coupled_bte(ctx: Context, level="dragged", tol=1e-10, inner_tol=0.0, max_outer=500, max_inner=5000,
+                      ko_correction=True, allow_noconv=False) -> dict:
+    o = SolveOptsC(LEVELS[level] if isinstance(level, str) else int(level), float(tol), float(inner_tol),
+                   int(max_outer), int(max_inner), 1 if ko_correction else 0)
+    info = SolveInfoC()
+    st = _check(ctx, _lib.ephb_solve_coupled_bte(ctx.handle, C.byref(o), C.byref(info)),
+                allow=(ENOCONV,) if allow_noconv else ())
+    d = {f: getattr(info, f) for f, _ in SolveInfoC._fields_}
+    d["lambda"] = d.pop("lambda_")
+    d["status"] = st
+    return d
+
+
+def transport_coefficients(ctx: Context, inst: int = 0) -> dict:
+    c = CoeffsC()
+    _check(ctx, _lib.ephb_transport_coefficients(ctx.handle, int(inst), C.byref(c)))
+    return {f: np.array(getattr(c, f)[:]).reshape(3, 3) for f, _ in CoeffsC._fields_}
+
+
+def get_array(ctx: Context, which: str) -> np.ndarray:
+    """Copy one of the context's device arrays into a new numpy array."""
+    p = C.c_void_p()
+    shape = (C.c_int64 * 4)()
+    dt = C.c_int()
+    _check(ctx, _lib.ephb_get_device_array(ctx.handle, ARR[which], C.byref(p), shape, C.byref(dt)))
+    shp = [int(s) for s in shape]
+    out = np.empty(shp, dtype=_DT[dt.value])
+    _check(ctx, _lib.ephb_copy_array_to_host(ctx.handle, ARR[which], out.ctypes.data_as(C.c_void_p), out.nbytes))
+    while out.ndim > 1 and out.shape[-1] == 1:
+        out = out.reshape(out.shape[:-1])
+    return out
+
+
+def device_array(ctx: Context, which: str):
+    """Borrowed device pointer, shape and numpy dtype of a context array."""
+    p = C.c_void_p()
+    shape = (C.c_int64 * 4)()
+    dt = C.c_int()
+    _check(ctx, _lib.ephb_get_device_array(ctx.handle, ARR[which], C.byref(p), shape, C.byref(dt)))
+    return p.value, tuple(int(s) for s in shape), _DT[dt.value]
+
+
+@dataclasses.dataclass
+class PathResult:
+    mesh: dict
+    rates: dict
+    solve: dict
+    coeffs: dict
+
+
+def run_path(ctx: Context, wl, level="dragged", ko_correction=True, tol=None, max_outer=500, max_inner=5000,
+             precision=FP64, allow_noconv=False) -> PathResult:
+    """The whole hot path for one workload on an existing context whose model is set."""
+    mesh = build_meshes_ibz(ctx, wl.kmesh, wl.qmesh, wl.window, wl.degen_tol_eV, wl.omega_min_eV)
+    rates = compute_transition_rates(ctx, wl.T_K, wl.mu_eV, wl.sigma_eV, wl.cutoff_sigmas, precision)
+    solve = solve_coupled_bte(ctx, level, wl.tol if tol is None else tol, 0.0, max_outer, max_inner, ko_correction,
+                              allow_noconv)
+    return PathResult(mesh, rates, solve, transport_coefficients(ctx))

@@ -1,0 +1,823 @@
+// Host runtime behind the C ABI (include/ephb.h): the context, its device buffers, the
+// call sequencing and the iteration control of the coupled BTE.  All numerical work is
+// enqueued as CUDA kernels on the context stream; the host only validates arguments,
+// sizes buffers and reads back scalars (counts, residuals) that steer the next launch.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ephb.h"
+#include "internal.h"
+
+using namespace ephb;
+
+namespace {
+std::atomic<long long> g_launches{0};
+}
+
+void ephb::note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+namespace {
+
+// Accumulates the device time between pairs of events recorded around one kind of kernel.
+struct EventTimer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  double ms = 0.0;
+  bool pending = false;
+  cudaError_t init() {
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    return e;
+  }
+  cudaError_t start(cudaStream_t s) { return cudaEventRecord(a, s); }
+  cudaError_t stop(cudaStream_t s) {
+    pending = true;
+    return cudaEventRecord(b, s);
+  }
+  // call after the stream has been synchronised past stop()
+  cudaError_t collect() {
+    if (!pending) return cudaSuccess;
+    float t = 0.f;
+    cudaError_t e = cudaEventElapsedTime(&t, a, b);
+    ms += t;
+    pending = false;
+    return e;
+  }
+  ~EventTimer() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+
+template <typename T>
+struct DBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  cudaError_t ensure(size_t count) {
+    if (count <= n && p) return cudaSuccess;
+    release();
+    size_t c = count ? count : 1;
+    cudaError_t e = cudaMalloc(&p, c * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      n = 0;
+      return e;
+    }
+    n = c;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+}  // namespace
+
+struct ephb_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  int stage = 0;   // 1 model, 2 meshes, 3 rates, 4 solved
+
+  ModelDev M;
+  DBuf<int> Re, Rd, Rge, Rgp, sym_rot, sym_inv;
+  DBuf<double2> H_R, D_R, g_R;
+  DBuf<double> sym_cart;
+
+  // meshes
+  Mesh km{}, qm{};
+  int ratio[3] = {1, 1, 1};
+  double lo = 0, hi = 0, degen_tol = 1e-6, omega_min = 1e-4;
+  int64_t n_ibzw = 0, n_pairs = 0;
+  ephb_mesh_info minfo{};
+  DBuf<double2> ktab, qtab, cvec, u;
+  DBuf<double> eps, vel, w, vph;
+  DBuf<uint8_t> egrp, pgrp;
+  DBuf<uint32_t> amask;
+  DBuf<int> rep, op, stab, flag, ibzw_list, ibzw_of, npairs, pair_q, pair_i, qcount, pq_rank;
+  DBuf<int64_t> pos, pair_ptr, qpair_ptr, scratch, scal;
+
+  // rates
+  double T = 300, mu = 0;
+  int64_t n_entries = 0, n_ph_entries = 0, n_tuples = 0;
+  DBuf<int> cntE, cntPh, ph_st;
+  DBuf<int64_t> escan, phscan, row_ptr, ph_row_ptr;
+  DBuf<uint32_t> e_kpns, ph_kpn;
+  DBuf<double2> e_X, Tbuf, Abuf;
+  DBuf<double> ph_Y;
+
+  // BTE
+  DBuf<double> st_eps, st_vel, st_ff, st_wt, W_e, inv_ffW, I0, J0, I, J, I2, J2, Bt, W_ph, inv_nnW, F0, F, G, Btv,
+      partial, res, prev_in, prev_out, prev_tmp;
+  DBuf<uint32_t> kcrd;
+  DBuf<int2> kinfo;
+  DBuf<unsigned long long> ucount;
+  double *host_res = nullptr;   // pinned
+  bool bte_ready = false;
+};
+
+namespace {
+
+ephb_status fail(ephb_ctx *ctx, ephb_status s, const std::string &msg) {
+  if (ctx) ctx->err = msg;
+  return s;
+}
+
+#define CK(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess)                                                                        \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? EPHB_ENOMEM : EPHB_ECUDA,                \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                            \
+  } while (0)
+
+template <typename T>
+cudaError_t upload(DBuf<T> &b, const T *src, size_t count, cudaStream_t st) {
+  cudaError_t e = b.ensure(count);
+  if (e != cudaSuccess) return e;
+  if (count == 0) return cudaSuccess;
+  e = cudaMemcpyAsync(b.p, src, count * sizeof(T), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(st);
+}
+
+int64_t read_i64(ephb_ctx *ctx, const int64_t *dptr, cudaError_t &e) {
+  int64_t v = 0;
+  e = cudaMemcpyAsync(&v, dptr, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  return v;
+}
+
+MeshDev mesh_view(ephb_ctx *c) {
+  MeshDev D;
+  D.km = c->km;
+  D.qm = c->qm;
+  for (int d = 0; d < 3; ++d) D.ratio[d] = c->ratio[d];
+  D.nk = c->km.size();
+  D.nq = c->qm.size();
+  D.ktab = c->ktab.p;
+  D.qtab = c->qtab.p;
+  D.eps = c->eps.p;
+  D.cvec = c->cvec.p;
+  D.vel = c->vel.p;
+  D.egrp = c->egrp.p;
+  D.amask = c->amask.p;
+  D.w = c->w.p;
+  D.u = c->u.p;
+  D.vph = c->vph.p;
+  D.pgrp = c->pgrp.p;
+  D.rep = c->rep.p;
+  D.op = c->op.p;
+  D.stab = c->stab.p;
+  D.ibzw_of = c->ibzw_of.p;
+  D.ibzw_list = c->ibzw_list.p;
+  D.n_ibzw = c->n_ibzw;
+  D.pair_ptr = c->pair_ptr.p;
+  D.pair_q = c->pair_q.p;
+  D.pair_i = c->pair_i.p;
+  D.qpair_ptr = c->qpair_ptr.p;
+  D.pq_rank = c->pq_rank.p;
+  D.n_pairs = c->n_pairs;
+  D.omega_min = c->omega_min;
+  D.degen_tol = c->degen_tol;
+  return D;
+}
+
+BteDev bte_view(ephb_ctx *c) {
+  BteDev B;
+  B.nb = c->M.nb;
+  B.nbr = c->M.nbr;
+  B.nsym = c->M.nsym;
+  B.nst = c->n_ibzw * c->M.nb;
+  B.nq = c->qm.size();
+  B.T = c->T;
+  B.mu = c->mu;
+  B.spin_deg = c->M.spin_deg;
+  const double *L = c->M.lattice;
+  double V = fabs(L[0] * (L[4] * L[8] - L[5] * L[7]) - L[1] * (L[3] * L[8] - L[5] * L[6]) +
+                  L[2] * (L[3] * L[7] - L[4] * L[6])) *
+             kAngstrom * kAngstrom * kAngstrom;
+  double kT = kKbEVK * c->T;
+  B.Pe = c->M.spin_deg * kECharge / (V * double(c->km.size()) * kT);
+  B.Pph = kECharge / (V * double(c->qm.size()) * kT);
+  B.row_ptr = c->row_ptr.p;
+  B.e_kpns = c->e_kpns.p;
+  B.e_X = c->e_X.p;
+  B.ph_row_ptr = c->ph_row_ptr.p;
+  B.ph_st = c->ph_st.p;
+  B.ph_kpn = c->ph_kpn.p;
+  B.ph_Y = c->ph_Y.p;
+  B.kcrd = c->kcrd.p;
+  B.st_eps = c->st_eps.p;
+  B.st_vel = c->st_vel.p;
+  B.st_ff = c->st_ff.p;
+  B.st_wt = c->st_wt.p;
+  return B;
+}
+
+}  // namespace
+
+extern "C" {
+
+ephb_status ephb_create(ephb_ctx **out, int device, void *cuda_stream) {
+  if (!out) return EPHB_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return EPHB_ECUDA;
+  if (device < 0 || device >= ndev) return EPHB_EINVAL;
+  ephb_ctx *ctx = new (std::nothrow) ephb_ctx();
+  if (!ctx) return EPHB_ENOMEM;
+  ctx->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete ctx;
+    return EPHB_ECUDA;
+  }
+  if (cuda_stream) {
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return EPHB_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  if (cudaMallocHost(&ctx->host_res, kResLen * sizeof(double)) != cudaSuccess) {
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return EPHB_ENOMEM;
+  }
+  *out = ctx;
+  return EPHB_OK;
+}
+
+void ephb_destroy(ephb_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  ctx->Re.release(); ctx->Rd.release(); ctx->Rge.release(); ctx->Rgp.release(); ctx->sym_rot.release();
+  ctx->sym_inv.release(); ctx->H_R.release(); ctx->D_R.release(); ctx->g_R.release(); ctx->sym_cart.release();
+  ctx->ktab.release(); ctx->qtab.release(); ctx->cvec.release(); ctx->u.release(); ctx->eps.release();
+  ctx->vel.release(); ctx->w.release(); ctx->vph.release(); ctx->egrp.release(); ctx->pgrp.release();
+  ctx->amask.release(); ctx->rep.release(); ctx->op.release(); ctx->stab.release(); ctx->flag.release();
+  ctx->ibzw_list.release(); ctx->ibzw_of.release(); ctx->npairs.release(); ctx->pair_q.release();
+  ctx->pair_i.release(); ctx->qcount.release(); ctx->pq_rank.release(); ctx->pos.release();
+  ctx->pair_ptr.release(); ctx->qpair_ptr.release(); ctx->scratch.release(); ctx->scal.release();
+  ctx->cntE.release(); ctx->cntPh.release(); ctx->ph_st.release(); ctx->escan.release(); ctx->phscan.release();
+  ctx->row_ptr.release(); ctx->ph_row_ptr.release(); ctx->e_kpns.release(); ctx->ph_kpn.release();
+  ctx->e_X.release(); ctx->Tbuf.release(); ctx->Abuf.release(); ctx->ph_Y.release();
+  ctx->st_eps.release(); ctx->st_vel.release(); ctx->st_ff.release(); ctx->st_wt.release(); ctx->W_e.release();
+  ctx->inv_ffW.release(); ctx->I0.release(); ctx->J0.release(); ctx->I.release(); ctx->J.release();
+  ctx->I2.release(); ctx->J2.release(); ctx->Bt.release(); ctx->W_ph.release(); ctx->inv_nnW.release();
+  ctx->F0.release(); ctx->F.release(); ctx->G.release(); ctx->Btv.release(); ctx->partial.release();
+  ctx->res.release(); ctx->prev_in.release(); ctx->prev_out.release(); ctx->prev_tmp.release();
+  ctx->kcrd.release(); ctx->kinfo.release(); ctx->ucount.release();
+  if (ctx->host_res) cudaFreeHost(ctx->host_res);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char *ephb_last_error(const ephb_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+// ---------------------------------------------------------------------------------------
+ephb_status ephb_set_wannier_model(ephb_ctx *ctx, const ephb_model *m) {
+  if (!ctx) return EPHB_EINVAL;
+  if (!m) return fail(ctx, EPHB_EINVAL, "model is NULL");
+  CK(cudaSetDevice(ctx->device));
+  if (m->nb < 1 || m->nb > kMaxBands) return fail(ctx, EPHB_EINVAL, "nb must be in [1, 8]");
+  if (m->nat < 1 || 3 * m->nat > kMaxBranches) return fail(ctx, EPHB_EINVAL, "nat must be in [1, 4]");
+  if (m->nRe < 1 || m->nRd < 1 || m->nRge < 1 || m->nRgp < 1) return fail(ctx, EPHB_EINVAL, "empty R list");
+  if (m->nRge > 4096) return fail(ctx, EPHB_EINVAL, "nRge > 4096 not supported");
+  if (m->nsym < 1 || m->nsym > kMaxSym) return fail(ctx, EPHB_EINVAL, "nsym must be in [1, 48]");
+  if (!m->mass_amu || !m->Re || !m->H_R || !m->Rd || !m->D_R || !m->Rge || !m->Rgp || !m->g_R || !m->sym_rot ||
+      !m->sym_cart)
+    return fail(ctx, EPHB_EINVAL, "NULL array in model");
+  if (!(m->omega_ref_eV > 0) || !(m->spin_deg > 0) || !(m->bg_omega_ref_eV > 0) || !(m->bg_T_ref > 0) ||
+      m->bg_rate_coeff < 0)
+    return fail(ctx, EPHB_EINVAL, "bad scalar model parameter");
+  for (int a = 0; a < m->nat; ++a)
+    if (!(m->mass_amu[a] > 0)) return fail(ctx, EPHB_EINVAL, "masses must be positive");
+  // the operation list must be a group closed under inversion: find S^-1 for each S
+  std::vector<int> inv(m->nsym, -1);
+  for (int s = 0; s < m->nsym; ++s) {
+    const int32_t *A = m->sym_rot + 9 * s;
+    for (int t = 0; t < m->nsym && inv[s] < 0; ++t) {
+      const int32_t *B = m->sym_rot + 9 * t;
+      bool id = true;
+      for (int i = 0; i < 3 && id; ++i)
+        for (int j = 0; j < 3 && id; ++j) {
+          int v = 0;
+          for (int l = 0; l < 3; ++l) v += A[3 * i + l] * B[3 * l + j];
+          id = v == (i == j ? 1 : 0);
+        }
+      if (id) inv[s] = t;
+    }
+    if (inv[s] < 0) return fail(ctx, EPHB_EINVAL, "symmetry operations are not closed under inversion");
+  }
+  ModelDev &M = ctx->M;
+  M = ModelDev();
+  M.nat = m->nat;
+  M.nb = m->nb;
+  M.nbr = 3 * m->nat;
+  M.nRe = m->nRe;
+  M.nRd = m->nRd;
+  M.nRge = m->nRge;
+  M.nRgp = m->nRgp;
+  M.nsym = m->nsym;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) M.lattice[3 * i + j] = m->lattice[i][j];
+  M.omega_ref = m->omega_ref_eV;
+  M.spin_deg = m->spin_deg;
+  M.bg_coeff = m->bg_rate_coeff;
+  M.bg_w = m->bg_omega_ref_eV;
+  M.bg_T = m->bg_T_ref;
+  double msum = 0;
+  for (int a = 0; a < m->nat; ++a) {
+    M.mass[a] = m->mass_amu[a];
+    msum += m->mass_amu[a];
+  }
+  M.mass_mean = msum / m->nat;
+  cudaStream_t st = ctx->stream;
+  const size_t nb2 = size_t(m->nb) * m->nb, nbr2 = size_t(M.nbr) * M.nbr;
+  CK(upload(ctx->Re, m->Re, size_t(m->nRe) * 3, st));
+  CK(upload(ctx->Rd, m->Rd, size_t(m->nRd) * 3, st));
+  CK(upload(ctx->Rge, m->Rge, size_t(m->nRge) * 3, st));
+  CK(upload(ctx->Rgp, m->Rgp, size_t(m->nRgp) * 3, st));
+  CK(upload(ctx->H_R, reinterpret_cast<const double2 *>(m->H_R), size_t(m->nRe) * nb2, st));
+  CK(upload(ctx->D_R, reinterpret_cast<const double2 *>(m->D_R), size_t(m->nRd) * nbr2, st));
+  CK(upload(ctx->g_R, reinterpret_cast<const double2 *>(m->g_R), size_t(m->nRge) * m->nRgp * nb2 * M.nbr, st));
+  CK(upload(ctx->sym_rot, m->sym_rot, size_t(m->nsym) * 9, st));
+  CK(upload(ctx->sym_cart, m->sym_cart, size_t(m->nsym) * 9, st));
+  CK(upload(ctx->sym_inv, inv.data(), inv.size(), st));
+  M.Re = ctx->Re.p;
+  M.Rd = ctx->Rd.p;
+  M.Rge = ctx->Rge.p;
+  M.Rgp = ctx->Rgp.p;
+  M.H_R = ctx->H_R.p;
+  M.D_R = ctx->D_R.p;
+  M.g_R = ctx->g_R.p;
+  M.sym_rot = ctx->sym_rot.p;
+  M.sym_cart = ctx->sym_cart.p;
+  M.sym_inv = ctx->sym_inv.p;
+  ctx->stage = 1;
+  ctx->bte_ready = false;
+  return EPHB_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+ephb_status ephb_build_meshes_ibz(ephb_ctx *ctx, const ephb_mesh_opts *o, ephb_mesh_info *out) {
+  if (!ctx) return EPHB_EINVAL;
+  if (ctx->stage < 1) return fail(ctx, EPHB_ESTATE, "set_wannier_model must come first");
+  if (!o) return fail(ctx, EPHB_EINVAL, "opts is NULL");
+  CK(cudaSetDevice(ctx->device));
+  for (int d = 0; d < 3; ++d) {
+    if (o->kmesh[d] < 1 || o->qmesh[d] < 1 || o->kmesh[d] > 1023)
+      return fail(ctx, EPHB_EINVAL, "mesh dimensions must be in [1, 1023]");
+    if (o->kmesh[d] % o->qmesh[d] != 0) return fail(ctx, EPHB_EINVAL, "k mesh must be a multiple of the q mesh");
+  }
+  Mesh km{{o->kmesh[0], o->kmesh[1], o->kmesh[2]}}, qm{{o->qmesh[0], o->qmesh[1], o->qmesh[2]}};
+  if (km.size() > (int64_t(1) << kKpBits)) return fail(ctx, EPHB_EINVAL, "k mesh larger than 2^21 points");
+  if (ctx->M.nsym > 1 && !(km.n[0] == km.n[1] && km.n[1] == km.n[2] && qm.n[0] == qm.n[1] && qm.n[1] == qm.n[2]))
+    return fail(ctx, EPHB_EINVAL, "symmetry reduction needs cubic (n x n x n) meshes");
+  if (!(o->window_hi_eV >= o->window_lo_eV)) return fail(ctx, EPHB_EINVAL, "empty window");
+  ctx->km = km;
+  ctx->qm = qm;
+  for (int d = 0; d < 3; ++d) ctx->ratio[d] = km.n[d] / qm.n[d];
+  ctx->lo = o->window_lo_eV;
+  ctx->hi = o->window_hi_eV;
+  ctx->degen_tol = o->degen_tol_eV > 0 ? o->degen_tol_eV : 1e-6;
+  ctx->omega_min = o->omega_min_eV > 0 ? o->omega_min_eV : 1e-4;
+  const ModelDev &M = ctx->M;
+  const int64_t nk = km.size(), nq = qm.size();
+  const int nb = M.nb, nbr = M.nbr;
+  cudaStream_t st = ctx->stream;
+  CK(ctx->ktab.ensure(km.n[0] + km.n[1] + km.n[2]));
+  CK(ctx->qtab.ensure(qm.n[0] + qm.n[1] + qm.n[2]));
+  CK(ctx->eps.ensure(nk * nb));
+  CK(ctx->cvec.ensure(nk * nb * nb));
+  CK(ctx->vel.ensure(nk * nb * 3));
+  CK(ctx->egrp.ensure(nk * nb * 2));
+  CK(ctx->amask.ensure(nk));
+  CK(ctx->w.ensure(nq * nbr));
+  CK(ctx->u.ensure(nq * nbr * nbr));
+  CK(ctx->vph.ensure(nq * nbr * 3));
+  CK(ctx->pgrp.ensure(nq * nbr * 2));
+  CK(ctx->rep.ensure(nk));
+  CK(ctx->op.ensure(nk));
+  CK(ctx->stab.ensure(nk));
+  CK(ctx->flag.ensure(nk));
+  CK(ctx->pos.ensure(nk));
+  CK(ctx->ibzw_of.ensure(nk));
+  CK(ctx->scal.ensure(16));
+  int64_t scr = scan_scratch_elems(nk > nq ? nk : nq);
+  CK(ctx->scratch.ensure(scr));
+  CK(launch_phase_tables(ctx->ktab.p, km, st));
+  CK(launch_phase_tables(ctx->qtab.p, qm, st));
+  CK(launch_electron_bands(M, km, ctx->ktab.p, ctx->degen_tol, ctx->lo, ctx->hi, ctx->eps.p, ctx->cvec.p,
+                           ctx->vel.p, ctx->egrp.p, ctx->amask.p, st));
+  CK(launch_phonon_modes(M, qm, ctx->qtab.p, ctx->degen_tol, ctx->omega_min, ctx->w.p, ctx->u.p, ctx->vph.p,
+                         ctx->pgrp.p, st));
+  CK(launch_ibz(M, km, ctx->rep.p, ctx->op.p, ctx->stab.p, ctx->flag.p, ctx->amask.p, st));
+  CK(exclusive_scan<int>(ctx->flag.p, ctx->pos.p, nk, ctx->scal.p + 0, ctx->scratch.p, ctx->scratch.n, st));
+  CK(launch_count_bits(ctx->amask.p, nk, ctx->scal.p + 1, st));
+  CK(launch_count_reps(ctx->rep.p, nk, ctx->scal.p + 2, st));
+  int64_t host_scal[3];
+  CK(cudaMemcpyAsync(host_scal, ctx->scal.p, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  ctx->n_ibzw = host_scal[0];
+  CK(ctx->ibzw_list.ensure(ctx->n_ibzw));
+  CK(launch_ibzw_fill(nk, ctx->flag.p, ctx->pos.p, ctx->ibzw_list.p, ctx->ibzw_of.p, st));
+  // pairs (k, q) with an active band at k+q, sorted by q within each k
+  CK(ctx->npairs.ensure(ctx->n_ibzw));
+  CK(ctx->pair_ptr.ensure(ctx->n_ibzw + 1));
+  MeshDev D = mesh_view(ctx);
+  CK(launch_pair_count(D, ctx->npairs.p, st));
+  CK(ctx->scratch.ensure(scan_scratch_elems(ctx->n_ibzw > nk ? ctx->n_ibzw : nk)));
+  CK(exclusive_scan<int>(ctx->npairs.p, ctx->pair_ptr.p, ctx->n_ibzw, ctx->pair_ptr.p + ctx->n_ibzw,
+                         ctx->scratch.p, ctx->scratch.n, st));
+  cudaError_t e;
+  ctx->n_pairs = read_i64(ctx, ctx->pair_ptr.p + ctx->n_ibzw, e);
+  CK(e);
+  CK(ctx->pair_q.ensure(ctx->n_pairs));
+  CK(ctx->pair_i.ensure(ctx->n_pairs));
+  CK(ctx->pq_rank.ensure(ctx->n_pairs));
+  D = mesh_view(ctx);
+  CK(launch_pair_fill(D, ctx->pair_q.p, ctx->pair_i.p, st));
+  CK(ctx->qcount.ensure(nq));
+  CK(ctx->qpair_ptr.ensure(nq + 1));
+  CK(launch_qpair_count(D, ctx->qcount.p, st));
+  CK(exclusive_scan<int>(ctx->qcount.p, ctx->qpair_ptr.p, nq, ctx->qpair_ptr.p + nq, ctx->scratch.p,
+                         ctx->scratch.n, st));
+  D = mesh_view(ctx);
+  CK(launch_qpair_fill(D, ctx->pq_rank.p, st));
+  CK(cudaStreamSynchronize(st));
+  ephb_mesh_info info;
+  info.nk = nk;
+  info.nq = nq;
+  info.n_active_states = host_scal[1];
+  info.n_ibz = host_scal[2];
+  info.n_ibz_window = ctx->n_ibzw;
+  info.n_pairs = ctx->n_pairs;
+  ctx->minfo = info;
+  if (out) *out = info;
+  ctx->stage = 2;
+  ctx->bte_ready = false;
+  return EPHB_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst, int ninst, const ephb_delta *delta,
+                                          ephb_precision precision, ephb_rates_info *out) {
+  if (!ctx) return EPHB_EINVAL;
+  if (ctx->stage < 2) return fail(ctx, EPHB_ESTATE, "build_meshes_ibz must come first");
+  if (!inst || !delta) return fail(ctx, EPHB_EINVAL, "NULL argument");
+  if (ninst != 1) return fail(ctx, EPHB_EINVAL, "only one (T, mu) instance per call is supported");
+  if (precision != EPHB_FP64) return fail(ctx, EPHB_EINVAL, "only EPHB_FP64 is available");
+  if (!(inst->T_K > 0) || !(delta->sigma_eV > 0) || !(delta->cutoff_sigmas > 0))
+    return fail(ctx, EPHB_EINVAL, "T, sigma and cutoff must be positive");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  const ModelDev &M = ctx->M;
+  const int nb = M.nb, nbr = M.nbr;
+  const int64_t nq = ctx->qm.size();
+  ctx->T = inst->T_K;
+  ctx->mu = inst->mu_eV;
+  cudaEvent_t ev0, ev1;
+  CK(cudaEventCreate(&ev0));
+  CK(cudaEventCreate(&ev1));
+  CK(cudaEventRecord(ev0, st));
+  RateParams rp;
+  rp.T = inst->T_K;
+  rp.mu = inst->mu_eV;
+  rp.sigma = delta->sigma_eV;
+  rp.cut = delta->cutoff_sigmas * delta->sigma_eV;
+  rp.inv_Nq_pref = 2.0 * kPi / (kHbarEVs * double(nq));
+  rp.y_scale = double(nq) / double(ctx->km.size());
+  const int64_t np = ctx->n_pairs;
+  CK(ctx->cntE.ensure(np * nb));
+  CK(ctx->cntPh.ensure(np * nbr));
+  CK(ctx->escan.ensure(np * nb));
+  CK(ctx->phscan.ensure(np * nbr));
+  CK(ctx->ucount.ensure(4));
+  MeshDev D = mesh_view(ctx);
+  CK(launch_rate_count(M, D, rp, ctx->cntE.p, ctx->cntPh.p, ctx->ucount.p, st));
+  int64_t big = np * (nb > nbr ? nb : nbr);
+  CK(ctx->scratch.ensure(scan_scratch_elems(big)));
+  CK(exclusive_scan<int>(ctx->cntE.p, ctx->escan.p, np * nb, ctx->scal.p + 3, ctx->scratch.p, ctx->scratch.n, st));
+  CK(exclusive_scan<int>(ctx->cntPh.p, ctx->phscan.p, np * nbr, ctx->scal.p + 4, ctx->scratch.p, ctx->scratch.n,
+                         st));
+  int64_t hs[2];
+  unsigned long long ntup = 0;
+  CK(cudaMemcpyAsync(hs, ctx->scal.p + 3, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&ntup, ctx->ucount.p, sizeof(ntup), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  ctx->n_entries = hs[0];
+  ctx->n_ph_entries = hs[1];
+  ctx->n_tuples = int64_t(ntup);
+  CK(ctx->e_kpns.ensure(ctx->n_entries));
+  CK(ctx->e_X.ensure(ctx->n_entries));
+  CK(ctx->ph_st.ensure(ctx->n_ph_entries));
+  CK(ctx->ph_kpn.ensure(ctx->n_ph_entries));
+  CK(ctx->ph_Y.ensure(ctx->n_ph_entries));
+  CK(ctx->row_ptr.ensure(ctx->n_ibzw * nb + 1));
+  CK(ctx->ph_row_ptr.ensure(nq * nbr + 1));
+  CK(launch_row_ptrs(D, nb, nbr, ctx->escan.p, ctx->phscan.p, ctx->n_entries, ctx->n_ph_entries, ctx->row_ptr.p,
+                     ctx->ph_row_ptr.p, st));
+  // stage A / B in chunks of irreducible-window k points
+  const size_t per_k = stage_a_T_elems(M);
+  int64_t chunk = int64_t((size_t(3) << 29) / (2 * per_k * sizeof(double2)));
+  if (chunk < 1) chunk = 1;
+  if (chunk > ctx->n_ibzw) chunk = ctx->n_ibzw;
+  if (chunk > 0) {
+    CK(ctx->Tbuf.ensure(size_t(chunk) * per_k));
+    CK(ctx->Abuf.ensure(size_t(chunk) * stage_a_A_elems(M)));
+  }
+  EventTimer ta, tb;
+  CK(ta.init());
+  CK(tb.init());
+  for (int64_t i0 = 0; i0 < ctx->n_ibzw; i0 += chunk) {
+    int64_t nkc = ctx->n_ibzw - i0 < chunk ? ctx->n_ibzw - i0 : chunk;
+    CK(ta.start(st));
+    CK(launch_stage_a(M, D, i0, nkc, ctx->Tbuf.p, ctx->Abuf.p, st));
+    CK(ta.stop(st));
+    CK(tb.start(st));
+    CK(launch_stage_b_rates(M, D, rp, i0, nkc, ctx->Abuf.p, ctx->escan.p, ctx->phscan.p, ctx->e_kpns.p, ctx->e_X.p,
+                            ctx->ph_st.p, ctx->ph_kpn.p, ctx->ph_Y.p, st));
+    CK(tb.stop(st));
+    CK(cudaStreamSynchronize(st));
+    CK(ta.collect());
+    CK(tb.collect());
+  }
+  unsigned long long cnt[4];
+  CK(cudaMemcpyAsync(cnt, ctx->ucount.p, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+  CK(cudaEventRecord(ev1, st));
+  CK(cudaEventSynchronize(ev1));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, ev0, ev1));
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  if (out) {
+    out->n_tuples = ctx->n_tuples;
+    out->n_entries = ctx->n_entries;
+    out->n_ph_entries = ctx->n_ph_entries;
+    out->n_pairs = np;
+    out->ms = ms;
+    out->ms_stage_a = ta.ms;
+    out->ms_stage_b = tb.ms;
+    const double ncol = double(M.nRgp) * M.nb * M.nb * M.nbr;
+    out->stage_a_flops = 8.0 * double(ctx->n_ibzw) * M.nRge * ncol + 8.0 * double(cnt[3]) * ncol;
+    out->stage_b_flops = double(cnt[2]);
+  }
+  ctx->stage = 3;
+  ctx->bte_ready = false;
+  return EPHB_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+namespace {
+
+ephb_status bte_setup(ephb_ctx *ctx) {
+  const ModelDev &M = ctx->M;
+  cudaStream_t st = ctx->stream;
+  const int64_t nst = ctx->n_ibzw * M.nb, nph = ctx->qm.size() * M.nbr, nk = ctx->km.size();
+  CK(ctx->st_eps.ensure(nst));
+  CK(ctx->st_vel.ensure(nst * 3));
+  CK(ctx->st_ff.ensure(nst));
+  CK(ctx->st_wt.ensure(nst));
+  CK(ctx->kcrd.ensure(nk));
+  CK(ctx->kinfo.ensure(nk));
+  CK(ctx->W_e.ensure(nst));
+  CK(ctx->inv_ffW.ensure(nst));
+  for (auto *b : {&ctx->I0, &ctx->J0, &ctx->I, &ctx->J, &ctx->I2, &ctx->J2}) CK(b->ensure(nst * 3));
+  CK(ctx->Bt.ensure(nph));
+  CK(ctx->W_ph.ensure(nph));
+  CK(ctx->inv_nnW.ensure(nph));
+  for (auto *b : {&ctx->F0, &ctx->F, &ctx->G}) CK(b->ensure(nph * 3));
+  CK(ctx->Btv.ensure(nph * 6));
+  CK(ctx->partial.ensure(size_t(coeff_partials()) * 64));
+  for (auto *b : {&ctx->res, &ctx->prev_in, &ctx->prev_out, &ctx->prev_tmp}) CK(b->ensure(kResLen));
+  MeshDev D = mesh_view(ctx);
+  CK(launch_state_setup(M, D, ctx->T, ctx->mu, ctx->st_eps.p, ctx->st_vel.p, ctx->st_ff.p, ctx->st_wt.p,
+                        ctx->kcrd.p, ctx->kinfo.p, st));
+  BteDev B = bte_view(ctx);
+  CK(launch_rta_electron(B, ctx->W_e.p, ctx->inv_ffW.p, ctx->I0.p, ctx->J0.p, ctx->ucount.p + 1, st));
+  CK(launch_ph_rowsum(B, ctx->Bt.p, st));
+  CK(launch_rta_phonon(M, D, B, ctx->Bt.p, ctx->W_ph.p, ctx->inv_nnW.p, ctx->F0.p, st));
+  ctx->bte_ready = true;
+  return EPHB_OK;
+}
+
+ephb_status coefficients_to_host(ephb_ctx *ctx, double *prev) {
+  MeshDev D = mesh_view(ctx);
+  BteDev B = bte_view(ctx);
+  CK(launch_coefficients(ctx->M, D, B, ctx->I.p, ctx->J.p, ctx->F.p, ctx->G.p, ctx->partial.p, coeff_partials(),
+                         ctx->res.p, prev, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->host_res, ctx->res.p, kResLen * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return EPHB_OK;
+}
+
+}  // namespace
+
+ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *out) {
+  if (!ctx) return EPHB_EINVAL;
+  if (ctx->stage < 3) return fail(ctx, EPHB_ESTATE, "compute_transition_rates must come first");
+  if (!o) return fail(ctx, EPHB_EINVAL, "opts is NULL");
+  if (o->level < EPHB_RTA || o->level > EPHB_DRAGGED) return fail(ctx, EPHB_EINVAL, "bad level");
+  if (!(o->tol > 0) || o->max_outer < 1 || o->max_inner < 1) return fail(ctx, EPHB_EINVAL, "bad tolerances");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  cudaEvent_t ev0, ev1;
+  CK(cudaEventCreate(&ev0));
+  CK(cudaEventCreate(&ev1));
+  CK(cudaEventRecord(ev0, st));
+  ephb_status s = bte_setup(ctx);
+  if (s != EPHB_OK) return s;
+  const ModelDev &M = ctx->M;
+  const int64_t nst = ctx->n_ibzw * M.nb, nph = ctx->qm.size() * M.nbr;
+  const double tol = o->tol, inner_tol = o->inner_tol > 0 ? o->inner_tol : 0.1 * o->tol;
+  CK(cudaMemcpyAsync(ctx->I.p, ctx->I0.p, nst * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(ctx->J.p, ctx->J0.p, nst * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(ctx->F.p, ctx->F0.p, nph * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(ctx->G.p, 0, nph * 3 * sizeof(double), st));
+  CK(cudaMemsetAsync(ctx->prev_out.p, 0, kResLen * sizeof(double), st));
+  s = coefficients_to_host(ctx, ctx->prev_out.p);   // RTA; prev_out <- RTA tensors
+  if (s != EPHB_OK) return s;
+  MeshDev D = mesh_view(ctx);
+  BteDev B = bte_view(ctx);
+  int outer = 0, inner_total = 0;
+  int64_t sweeps = 0;
+  bool converged = o->level == EPHB_RTA;
+  double residual = 0.0, lambda = 1.0;
+  EventTimer te, tp;
+  CK(te.init());
+  CK(tp.init());
+
+  auto inner_loop = [&](int drag, bool &ok) -> ephb_status {
+    ok = false;
+    CK(cudaMemsetAsync(ctx->prev_in.p, 0, kResLen * sizeof(double), st));
+    ephb_status r = coefficients_to_host(ctx, ctx->prev_in.p);
+    if (r != EPHB_OK) return r;
+    for (int it = 1; it <= o->max_inner; ++it) {
+      CK(te.start(st));
+      CK(launch_e_sweep(M, D, B, ctx->kinfo.p, ctx->I0.p, ctx->J0.p, ctx->inv_ffW.p, ctx->I.p, ctx->J.p, ctx->F.p,
+                        ctx->G.p, drag, ctx->I2.p, ctx->J2.p, st));
+      CK(te.stop(st));
+      std::swap(ctx->I.p, ctx->I2.p);
+      std::swap(ctx->J.p, ctx->J2.p);
+      ++sweeps;
+      ++inner_total;
+      B = bte_view(ctx);
+      r = coefficients_to_host(ctx, ctx->prev_in.p);
+      if (r != EPHB_OK) return r;
+      CK(te.collect());
+      if (ctx->host_res[72] < inner_tol) {
+        ok = true;
+        return EPHB_OK;
+      }
+    }
+    return EPHB_OK;
+  };
+
+  if (o->level == EPHB_DRAGLESS) {
+    bool ok;
+    s = inner_loop(0, ok);
+    if (s != EPHB_OK) return s;
+    converged = ok;
+    outer = 1;
+    residual = ctx->host_res[72];
+  } else if (o->level == EPHB_DRAGGED || o->level == EPHB_PARTIAL) {
+    for (outer = 1; outer <= o->max_outer; ++outer) {
+      CK(tp.start(st));
+      CK(launch_ph_sweep(M, D, B, ctx->kinfo.p, ctx->I.p, ctx->J.p, ctx->Btv.p, st));
+      CK(tp.stop(st));
+      CK(launch_ph_update(M, D, B, ctx->Btv.p, ctx->F0.p, ctx->inv_nnW.p, ctx->F.p, ctx->G.p, st));
+      bool ok;
+      s = inner_loop(1, ok);
+      if (s != EPHB_OK) return s;
+      CK(tp.collect());
+      if (o->ko_correction) {
+        CK(launch_ko(M, D, B, ctx->I.p, ctx->J.p, ctx->partial.p, coeff_partials(), ctx->res.p, st));
+        CK(cudaMemcpyAsync(ctx->host_res + 74, ctx->res.p + 74, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (ctx->host_res[75] != 0.0) lambda = ctx->host_res[74];
+      }
+      s = coefficients_to_host(ctx, ctx->prev_out.p);
+      if (s != EPHB_OK) return s;
+      residual = ctx->host_res[73];
+      if (o->level == EPHB_PARTIAL || residual < tol) {
+        converged = true;
+        break;
+      }
+    }
+    if (outer > o->max_outer) outer = o->max_outer;
+  }
+  unsigned long long nzero = 0;
+  CK(cudaMemcpyAsync(&nzero, ctx->ucount.p + 1, sizeof(nzero), cudaMemcpyDeviceToHost, st));
+  CK(cudaEventRecord(ev1, st));
+  CK(cudaEventSynchronize(ev1));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, ev0, ev1));
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  if (out) {
+    out->outer_iters = outer;
+    out->inner_iters_total = inner_total;
+    out->converged = converged ? 1 : 0;
+    out->n_zero_rate_states = int(nzero);
+    out->residual = residual;
+    out->lambda = lambda;
+    out->n_sweeps = sweeps;
+    out->ms = ms;
+    out->ms_e_sweep = te.ms;
+    out->ms_ph_sweep = tp.ms;
+    // per electron sweep: the entry stream (k'|n|s word + X+,X-) plus the per-row arrays
+    out->e_sweep_bytes = 20.0 * double(ctx->n_entries) + double(nst) * (8.0 + 13.0 * 8.0);
+  }
+  ctx->stage = 4;
+  if (!converged) return fail(ctx, EPHB_ENOCONV, "iteration limit reached before the tolerance");
+  return EPHB_OK;
+}
+
+ephb_status ephb_transport_coefficients(ephb_ctx *ctx, int inst, ephb_coeffs *out) {
+  if (!ctx) return EPHB_EINVAL;
+  if (ctx->stage < 4 || !ctx->bte_ready) return fail(ctx, EPHB_ESTATE, "solve_coupled_bte must come first");
+  if (inst != 0) return fail(ctx, EPHB_EINVAL, "inst must be 0");
+  if (!out) return fail(ctx, EPHB_EINVAL, "out is NULL");
+  CK(cudaSetDevice(ctx->device));
+  ephb_status s = coefficients_to_host(ctx, ctx->prev_tmp.p);
+  if (s != EPHB_OK) return s;
+  const double *r = ctx->host_res;
+  std::memcpy(out->sigma, r + 0, 9 * sizeof(double));
+  std::memcpy(out->sigmaS, r + 9, 9 * sizeof(double));
+  std::memcpy(out->alpha_el, r + 18, 9 * sizeof(double));
+  std::memcpy(out->kappa0_el, r + 27, 9 * sizeof(double));
+  std::memcpy(out->alpha_ph, r + 36, 9 * sizeof(double));
+  std::memcpy(out->kappa_ph, r + 45, 9 * sizeof(double));
+  std::memcpy(out->S, r + 54, 9 * sizeof(double));
+  std::memcpy(out->kappa_el, r + 63, 9 * sizeof(double));
+  return EPHB_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+ephb_status ephb_get_device_array(ephb_ctx *ctx, int which, void **dptr, int64_t shape[4], int *dtype) {
+  if (!ctx || !dptr || !shape || !dtype) return EPHB_EINVAL;
+  const int64_t nk = ctx->km.size(), nq = ctx->qm.size(), nb = ctx->M.nb, nbr = ctx->M.nbr;
+  const int64_t nst = ctx->n_ibzw * nb;
+  for (int d = 0; d < 4; ++d) shape[d] = 1;
+  int need = 2;
+  void *p = nullptr;
+  int dt = 0;
+  switch (which) {
+    case EPHB_ARR_EPS: p = ctx->eps.p; shape[0] = nk; shape[1] = nb; break;
+    case EPHB_ARR_VEL: p = ctx->vel.p; shape[0] = nk; shape[1] = nb; shape[2] = 3; break;
+    case EPHB_ARR_OMEGA: p = ctx->w.p; shape[0] = nq; shape[1] = nbr; break;
+    case EPHB_ARR_VPH: p = ctx->vph.p; shape[0] = nq; shape[1] = nbr; shape[2] = 3; break;
+    case EPHB_ARR_IBZ_REP: p = ctx->rep.p; shape[0] = nk; dt = 2; break;
+    case EPHB_ARR_IBZ_OP: p = ctx->op.p; shape[0] = nk; dt = 2; break;
+    case EPHB_ARR_IBZW_LIST: p = ctx->ibzw_list.p; shape[0] = ctx->n_ibzw; dt = 2; break;
+    case EPHB_ARR_ACTIVE: p = ctx->amask.p; shape[0] = nk; dt = 4; break;
+    case EPHB_ARR_PAIR_PTR: p = ctx->pair_ptr.p; shape[0] = ctx->n_ibzw + 1; dt = 3; break;
+    case EPHB_ARR_PAIR_Q: p = ctx->pair_q.p; shape[0] = ctx->n_pairs; dt = 2; break;
+    case EPHB_ARR_ROW_PTR: p = ctx->row_ptr.p; shape[0] = nst + 1; dt = 3; need = 3; break;
+    case EPHB_ARR_ENTRY_KPNS: p = ctx->e_kpns.p; shape[0] = ctx->n_entries; dt = 4; need = 3; break;
+    case EPHB_ARR_ENTRY_X: p = ctx->e_X.p; shape[0] = ctx->n_entries; shape[1] = 2; need = 3; break;
+    case EPHB_ARR_W_E: p = ctx->W_e.p; shape[0] = nst; need = 4; break;
+    case EPHB_ARR_W_PH: p = ctx->W_ph.p; shape[0] = nq; shape[1] = nbr; need = 4; break;
+    case EPHB_ARR_I: p = ctx->I.p; shape[0] = nst; shape[1] = 3; need = 4; break;
+    case EPHB_ARR_J: p = ctx->J.p; shape[0] = nst; shape[1] = 3; need = 4; break;
+    case EPHB_ARR_F: p = ctx->F.p; shape[0] = nq; shape[1] = nbr; shape[2] = 3; need = 4; break;
+    case EPHB_ARR_G: p = ctx->G.p; shape[0] = nq; shape[1] = nbr; shape[2] = 3; need = 4; break;
+    default: return fail(ctx, EPHB_EINVAL, "unknown array id");
+  }
+  if (ctx->stage < need || (need == 4 && !ctx->bte_ready)) return fail(ctx, EPHB_ESTATE, "array not computed yet");
+  *dptr = p;
+  *dtype = dt;
+  return EPHB_OK;
+}
+
+int64_t ephb_kernel_launches(void) { return g_launches.load(); }
+
+ephb_status ephb_copy_array_to_host(ephb_ctx *ctx, int which, void *host_dst, int64_t nbytes) {
+  if (!ctx || !host_dst) return EPHB_EINVAL;
+  void *p;
+  int64_t shape[4];
+  int dt;
+  ephb_status s = ephb_get_device_array(ctx, which, &p, shape, &dt);
+  if (s != EPHB_OK) return s;
+  const int64_t esz[5] = {8, 16, 4, 8, 4};
+  int64_t need = shape[0] * shape[1] * shape[2] * shape[3] * esz[dt];
+  if (nbytes < need) return fail(ctx, EPHB_EINVAL, "destination too small");
+  CK(cudaSetDevice(ctx->device));
+  if (need > 0) {
+    CK(cudaMemcpyAsync(host_dst, p, size_t(need), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return EPHB_OK;
+}
+
+}  // extern "C"

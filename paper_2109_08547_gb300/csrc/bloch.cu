@@ -1,0 +1,400 @@
+// Wannier-to-Bloch interpolation of H(k) and D(q), their diagonalisation, Hellmann-Feynman
+// velocities (Eqs. H_mn(k), v_mk, D_ss'(q), v_sq of arXiv 2109.08547), the transport
+// window, the irreducible wedge of the k mesh and the (k, q) pair lists.
+#include "internal.h"
+#include "jacobi.cuh"
+
+namespace ephb {
+
+namespace {
+
+__global__ void k_phase_tables(double2 *tab, Mesh m) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int total = m.n[0] + m.n[1] + m.n[2];
+  if (t >= total) return;
+  int d = t < m.n[0] ? 0 : (t < m.n[0] + m.n[1] ? 1 : 2);
+  int j = t - (d == 0 ? 0 : (d == 1 ? m.n[0] : m.n[0] + m.n[1]));
+  double s, c;
+  sincospi(2.0 * double(j) / double(m.n[d]), &s, &c);
+  tab[t] = cmk(c, s);
+}
+
+// One thread per k point: H(k), grad_k H(k), eigen-decomposition, velocities.
+template <int NB>
+__global__ void __launch_bounds__(128) k_electron_bands(ModelDev M, Mesh km, const double2 *__restrict__ ktab,
+                                                        double degen_tol, double lo, double hi, double *eps,
+                                                        double2 *cvec, double *vel, uint8_t *egrp,
+                                                        uint32_t *amask) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= km.size()) return;
+  const int nb = M.nb;
+  int i0, i1, i2;
+  km.unflat(k, i0, i1, i2);
+  double2 H[NB * NB], dH[3][NB * NB], V[NB * NB];
+  double e[NB];
+  for (int t = 0; t < NB * NB; ++t) {
+    H[t] = cmk(0, 0);
+    dH[0][t] = dH[1][t] = dH[2][t] = cmk(0, 0);
+  }
+  for (int r = 0; r < M.nRe; ++r) {
+    const int r0 = M.Re[3 * r], r1 = M.Re[3 * r + 1], r2 = M.Re[3 * r + 2];
+    double2 ph = mesh_phase(ktab, km, i0, i1, i2, r0, r1, r2);
+    double Rc[3];
+    for (int a = 0; a < 3; ++a) Rc[a] = r0 * M.lattice[a] + r1 * M.lattice[3 + a] + r2 * M.lattice[6 + a];
+    const double2 *h = M.H_R + size_t(r) * nb * nb;
+    for (int i = 0; i < nb; ++i)
+      for (int j = 0; j < nb; ++j) {
+        double2 t = cmul(ph, h[i * nb + j]);
+        H[i * NB + j] = cadd(H[i * NB + j], t);
+        for (int a = 0; a < 3; ++a) {  // i R_a t
+          dH[a][i * NB + j].x -= Rc[a] * t.y;
+          dH[a][i * NB + j].y += Rc[a] * t.x;
+        }
+      }
+  }
+  herm_jacobi<NB>(H, V, e, nb);
+  double vd[NB][3];
+  for (int m = 0; m < nb; ++m)
+    for (int a = 0; a < 3; ++a) {
+      double acc = 0.0;
+      for (int i = 0; i < nb; ++i) {
+        double2 row = cmk(0, 0);
+        for (int j = 0; j < nb; ++j) cfma(row, dH[a][i * NB + j], V[j * NB + m]);
+        acc += V[i * NB + m].x * row.x + V[i * NB + m].y * row.y;   // Re(conj(V_im) row_i)
+      }
+      vd[m][a] = acc;
+    }
+  uint8_t grp[2 * NB];
+  degenerate_groups(e, nb, degen_tol, grp);
+  const double conv = kAngstrom / kHbarEVs;
+  uint32_t mask = 0;
+  for (int m = 0; m < nb; ++m) {
+    int g0 = grp[2 * m], g1 = grp[2 * m + 1];
+    for (int a = 0; a < 3; ++a) {
+      double s = 0.0;
+      for (int j = g0; j < g1; ++j) s += vd[j][a];
+      vel[(size_t(k) * nb + m) * 3 + a] = s / double(g1 - g0) * conv;
+    }
+    eps[size_t(k) * nb + m] = e[m];
+    egrp[(size_t(k) * nb + m) * 2] = grp[2 * m];
+    egrp[(size_t(k) * nb + m) * 2 + 1] = grp[2 * m + 1];
+    if (e[m] >= lo && e[m] <= hi) mask |= 1u << m;
+    for (int i = 0; i < nb; ++i) cvec[(size_t(k) * nb + i) * nb + m] = V[i * NB + m];
+  }
+  amask[k] = mask;
+}
+
+// One thread per q point: D(q), eigen-decomposition, hbar w = sqrt(max(lambda,0)), velocities.
+template <int NB>
+__global__ void __launch_bounds__(128) k_phonon_modes(ModelDev M, Mesh qm, const double2 *__restrict__ qtab,
+                                                      double degen_tol, double omega_min, double *w, double2 *u,
+                                                      double *vph, uint8_t *pgrp) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= qm.size()) return;
+  const int nb = M.nbr;
+  int i0, i1, i2;
+  qm.unflat(q, i0, i1, i2);
+  double2 D[NB * NB], dD[3][NB * NB], V[NB * NB];
+  double e[NB];
+  for (int t = 0; t < NB * NB; ++t) {
+    D[t] = cmk(0, 0);
+    dD[0][t] = dD[1][t] = dD[2][t] = cmk(0, 0);
+  }
+  for (int r = 0; r < M.nRd; ++r) {
+    const int r0 = M.Rd[3 * r], r1 = M.Rd[3 * r + 1], r2 = M.Rd[3 * r + 2];
+    double2 ph = mesh_phase(qtab, qm, i0, i1, i2, r0, r1, r2);
+    double Rc[3];
+    for (int a = 0; a < 3; ++a) Rc[a] = r0 * M.lattice[a] + r1 * M.lattice[3 + a] + r2 * M.lattice[6 + a];
+    const double2 *h = M.D_R + size_t(r) * nb * nb;
+    for (int i = 0; i < nb; ++i)
+      for (int j = 0; j < nb; ++j) {
+        double2 t = cmul(ph, h[i * nb + j]);
+        D[i * NB + j] = cadd(D[i * NB + j], t);
+        for (int a = 0; a < 3; ++a) {
+          dD[a][i * NB + j].x -= Rc[a] * t.y;
+          dD[a][i * NB + j].y += Rc[a] * t.x;
+        }
+      }
+  }
+  herm_jacobi<NB>(D, V, e, nb);
+  double om[NB];
+  for (int s = 0; s < nb; ++s) om[s] = sqrt(fmax(e[s], 0.0));
+  double vd[NB][3];
+  for (int s = 0; s < nb; ++s)
+    for (int a = 0; a < 3; ++a) {
+      double acc = 0.0;
+      for (int i = 0; i < nb; ++i) {
+        double2 row = cmk(0, 0);
+        for (int j = 0; j < nb; ++j) cfma(row, dD[a][i * NB + j], V[j * NB + s]);
+        acc += V[i * NB + s].x * row.x + V[i * NB + s].y * row.y;
+      }
+      vd[s][a] = acc;
+    }
+  uint8_t grp[2 * NB];
+  degenerate_groups(om, nb, degen_tol, grp);
+  const double conv = kAngstrom / kHbarEVs;
+  for (int s = 0; s < nb; ++s) {
+    int g0 = grp[2 * s], g1 = grp[2 * s + 1];
+    for (int a = 0; a < 3; ++a) {
+      double v = 0.0;
+      if (om[s] > omega_min) {
+        double acc = 0.0;
+        for (int j = g0; j < g1; ++j) acc += vd[j][a];
+        v = acc / double(g1 - g0) / (2.0 * om[s]) * conv;
+      }
+      vph[(size_t(q) * nb + s) * 3 + a] = v;
+    }
+    w[size_t(q) * nb + s] = om[s];
+    pgrp[(size_t(q) * nb + s) * 2] = grp[2 * s];
+    pgrp[(size_t(q) * nb + s) * 2 + 1] = grp[2 * s + 1];
+    for (int i = 0; i < nb; ++i) u[(size_t(q) * nb + i) * nb + s] = V[i * NB + s];
+  }
+}
+
+// Irreducible wedge: representative = smallest image index, first op S with S<k> = k,
+// stabiliser size.  Also flags representatives holding an active band.
+__global__ void k_ibz(ModelDev M, Mesh km, int *rep, int *op, int *stab, int *flag, const uint32_t *amask) {
+  __shared__ int rot[kMaxSym * 9];
+  for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) rot[t] = M.sym_rot[t];
+  __syncthreads();
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= km.size()) return;
+  int i[3];
+  km.unflat(k, i[0], i[1], i[2]);
+  int best = k;
+  for (int s = 0; s < M.nsym; ++s) {
+    const int *S = rot + 9 * s;
+    int j0 = pmod(S[0] * i[0] + S[1] * i[1] + S[2] * i[2], km.n[0]);
+    int j1 = pmod(S[3] * i[0] + S[4] * i[1] + S[5] * i[2], km.n[1]);
+    int j2 = pmod(S[6] * i[0] + S[7] * i[1] + S[8] * i[2], km.n[2]);
+    int img = km.flat(j0, j1, j2);
+    best = img < best ? img : best;
+  }
+  int r[3];
+  km.unflat(best, r[0], r[1], r[2]);
+  int first = -1, ns = 0;
+  for (int s = 0; s < M.nsym; ++s) {
+    const int *S = rot + 9 * s;
+    int j0 = pmod(S[0] * r[0] + S[1] * r[1] + S[2] * r[2], km.n[0]);
+    int j1 = pmod(S[3] * r[0] + S[4] * r[1] + S[5] * r[2], km.n[1]);
+    int j2 = pmod(S[6] * r[0] + S[7] * r[1] + S[8] * r[2], km.n[2]);
+    int img = km.flat(j0, j1, j2);
+    if (img == k && first < 0) first = s;
+    if (img == best) ++ns;
+  }
+  rep[k] = best;
+  op[k] = first;
+  stab[k] = ns;
+  flag[k] = (best == k && amask[k] != 0u) ? 1 : 0;
+}
+
+__global__ void k_ibzw_fill(int64_t nk, const int *flag, const int64_t *pos, int *list, int *of) {
+  int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (k >= nk) return;
+  if (flag[k]) {
+    list[pos[k]] = int(k);
+    of[k] = int(pos[k]);
+  } else {
+    of[k] = -1;
+  }
+}
+
+__device__ inline int kplusq(const MeshDev &D, int k, int q) {
+  int a0, a1, a2, b0, b1, b2;
+  D.km.unflat(k, a0, a1, a2);
+  D.qm.unflat(q, b0, b1, b2);
+  return D.km.flat(pmod(a0 + D.ratio[0] * b0, D.km.n[0]), pmod(a1 + D.ratio[1] * b1, D.km.n[1]),
+                   pmod(a2 + D.ratio[2] * b2, D.km.n[2]));
+}
+
+// block per irreducible-window k: number of q with an active band at k+q
+__global__ void k_pair_count(MeshDev D, int *npairs) {
+  __shared__ int red[32];
+  int i = blockIdx.x;
+  int k = D.ibzw_list[i];
+  int c = 0;
+  for (int q = threadIdx.x; q < D.nq; q += blockDim.x) c += D.amask[kplusq(D, k, q)] != 0u;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) npairs[i] = v;
+  }
+}
+
+// ordered compaction helper: exclusive rank of `flag` within the block (blockDim = 256)
+__device__ inline int block_rank(int flag, int *warp_tot, int &total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned b = __ballot_sync(0xffffffffu, flag);
+  int r = __popc(b & ((1u << lane) - 1u));
+  if (lane == 0) warp_tot[wid] = __popc(b);
+  __syncthreads();
+  int off = 0;
+  total = 0;
+  for (int w = 0; w < nw; ++w) {
+    if (w < wid) off += warp_tot[w];
+    total += warp_tot[w];
+  }
+  __syncthreads();
+  return off + r;
+}
+
+__global__ void k_pair_fill(MeshDev D, int *pair_q, int *pair_i) {
+  __shared__ int wt[32];
+  int i = blockIdx.x;
+  int k = D.ibzw_list[i];
+  int64_t base = D.pair_ptr[i];
+  for (int q0 = 0; q0 < D.nq; q0 += blockDim.x) {
+    int q = q0 + threadIdx.x;
+    int f = q < D.nq ? (D.amask[kplusq(D, k, q)] != 0u) : 0;
+    int total;
+    int r = block_rank(f, wt, total);
+    if (f) {
+      pair_q[base + r] = q;
+      pair_i[base + r] = i;
+    }
+    base += total;
+  }
+}
+
+// block per q: how many irreducible-window k pair with it
+__global__ void k_qpair_count(MeshDev D, int *qcount) {
+  __shared__ int red[32];
+  int q = blockIdx.x;
+  int c = 0;
+  for (int i = threadIdx.x; i < D.n_ibzw; i += blockDim.x) c += D.amask[kplusq(D, D.ibzw_list[i], q)] != 0u;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) qcount[q] = v;
+  }
+}
+
+// block per q: rank of each pair (i, q) among the pairs of q, in increasing i
+__global__ void k_qpair_fill(MeshDev D, int *pq_rank) {
+  __shared__ int wt[32];
+  int q = blockIdx.x;
+  int base = 0;
+  for (int i0 = 0; i0 < D.n_ibzw; i0 += blockDim.x) {
+    int i = i0 + threadIdx.x;
+    int f = i < D.n_ibzw ? (D.amask[kplusq(D, D.ibzw_list[i], q)] != 0u) : 0;
+    int total;
+    int r = block_rank(f, wt, total);
+    if (f) {
+      // pair index of (i, q): binary search in the q-sorted list of i
+      int64_t lo = D.pair_ptr[i], hi = D.pair_ptr[i + 1];
+      while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (D.pair_q[mid] <= q) lo = mid; else hi = mid;
+      }
+      pq_rank[lo] = base + r;
+    }
+    base += total;
+  }
+}
+
+__global__ void k_count_bits(const uint32_t *m, int64_t n, unsigned long long *out) {
+  unsigned long long c = 0;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x)
+    c += __popc(m[t]);
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, c);
+}
+
+__global__ void k_count_reps(const int *rep, int64_t n, unsigned long long *out) {
+  unsigned long long c = 0;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x)
+    c += rep[t] == int(t);
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, c);
+}
+
+}  // namespace
+
+cudaError_t launch_phase_tables(double2 *tab, Mesh m, cudaStream_t st) {
+  int total = m.n[0] + m.n[1] + m.n[2];
+  EPHB_LAUNCH(k_phase_tables, (total + 127) / 128, 128, 0, st, tab, m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_electron_bands(const ModelDev &M, Mesh km, const double2 *ktab, double degen_tol, double lo,
+                                  double hi, double *eps, double2 *cvec, double *vel, uint8_t *egrp,
+                                  uint32_t *amask, cudaStream_t st) {
+  int64_t n = km.size();
+  int grid = int((n + 127) / 128);
+  if (M.nb <= 1)
+    EPHB_LAUNCH(k_electron_bands<1>, grid, 128, 0, st, M, km, ktab, degen_tol, lo, hi, eps, cvec, vel, egrp, amask);
+  else if (M.nb <= 4)
+    EPHB_LAUNCH(k_electron_bands<4>, grid, 128, 0, st, M, km, ktab, degen_tol, lo, hi, eps, cvec, vel, egrp, amask);
+  else
+    EPHB_LAUNCH(k_electron_bands<8>, grid, 128, 0, st, M, km, ktab, degen_tol, lo, hi, eps, cvec, vel, egrp, amask);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phonon_modes(const ModelDev &M, Mesh qm, const double2 *qtab, double degen_tol, double omega_min,
+                                double *w, double2 *u, double *vph, uint8_t *pgrp, cudaStream_t st) {
+  int64_t n = qm.size();
+  int grid = int((n + 127) / 128);
+  if (M.nbr <= 3)
+    EPHB_LAUNCH(k_phonon_modes<3>, grid, 128, 0, st, M, qm, qtab, degen_tol, omega_min, w, u, vph, pgrp);
+  else if (M.nbr <= 6)
+    EPHB_LAUNCH(k_phonon_modes<6>, grid, 128, 0, st, M, qm, qtab, degen_tol, omega_min, w, u, vph, pgrp);
+  else
+    EPHB_LAUNCH(k_phonon_modes<12>, grid, 128, 0, st, M, qm, qtab, degen_tol, omega_min, w, u, vph, pgrp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ibz(const ModelDev &M, Mesh km, int *rep, int *op, int *stab, int *flag, const uint32_t *amask,
+                       cudaStream_t st) {
+  int64_t n = km.size();
+  EPHB_LAUNCH(k_ibz, int((n + 127) / 128), 128, 0, st, M, km, rep, op, stab, flag, amask);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ibzw_fill(int64_t nk, const int *flag, const int64_t *pos, int *list, int *of, cudaStream_t st) {
+  EPHB_LAUNCH(k_ibzw_fill, int((nk + 255) / 256), 256, 0, st, nk, flag, pos, list, of);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_count(const MeshDev &D, int *npairs, cudaStream_t st) {
+  if (D.n_ibzw == 0) return cudaSuccess;
+  EPHB_LAUNCH(k_pair_count, int(D.n_ibzw), 256, 0, st, D, npairs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_fill(const MeshDev &D, int *pair_q, int *pair_i, cudaStream_t st) {
+  if (D.n_ibzw == 0) return cudaSuccess;
+  EPHB_LAUNCH(k_pair_fill, int(D.n_ibzw), 256, 0, st, D, pair_q, pair_i);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qpair_count(const MeshDev &D, int *qcount, cudaStream_t st) {
+  EPHB_LAUNCH(k_qpair_count, int(D.nq), 256, 0, st, D, qcount);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qpair_fill(const MeshDev &D, int *pq_rank, cudaStream_t st) {
+  EPHB_LAUNCH(k_qpair_fill, int(D.nq), 256, 0, st, D, pq_rank);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_bits(const uint32_t *amask, int64_t n, int64_t *out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int64_t), st);
+  if (e != cudaSuccess) return e;
+  EPHB_LAUNCH(k_count_bits, 152, 256, 0, st, amask, n, reinterpret_cast<unsigned long long *>(out));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_reps(const int *rep, int64_t n, int64_t *out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int64_t), st);
+  if (e != cudaSuccess) return e;
+  EPHB_LAUNCH(k_count_reps, 152, 256, 0, st, rep, n, reinterpret_cast<unsigned long long *>(out));
+  return cudaGetLastError();
+}
+
+}  // namespace ephb

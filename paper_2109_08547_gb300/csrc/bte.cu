@@ -1,0 +1,531 @@
+// Coupled electron-phonon BTE sweeps (section "Coupled and decoupled BTEs" of arXiv
+// 2109.08547): RTA rates and terms, the electron gather sweep (self + drag terms), the
+// phonon drag scatter over the (q,s) rows with the symmetry fold, the transport-coefficient
+// reductions and the Kelvin-Onsager correction.  Every reduction runs in a fixed order,
+// so repeated runs give bit-identical results.
+#include "internal.h"
+
+namespace ephb {
+
+namespace {
+
+__device__ inline double fermi_b(double e, double mu, double kT) { return 1.0 / (exp((e - mu) / kT) + 1.0); }
+__device__ inline double bose_b(double w, double kT) { return w > 0.0 ? 1.0 / expm1(w / kT) : 0.0; }
+
+__device__ inline double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ inline void rot3(const double *C, const double *x, double *y) {
+  y[0] = C[0] * x[0] + C[1] * x[1] + C[2] * x[2];
+  y[1] = C[3] * x[0] + C[4] * x[1] + C[5] * x[2];
+  y[2] = C[6] * x[0] + C[7] * x[1] + C[8] * x[2];
+}
+
+// image of q (flat) under operation s (integer rotation on reciprocal crystal coords)
+__device__ inline int q_image(const Mesh &qm, const int *rot, int q) {
+  int b0, b1, b2;
+  qm.unflat(q, b0, b1, b2);
+  return qm.flat(pmod(rot[0] * b0 + rot[1] * b1 + rot[2] * b2, qm.n[0]),
+                 pmod(rot[3] * b0 + rot[4] * b1 + rot[5] * b2, qm.n[1]),
+                 pmod(rot[6] * b0 + rot[7] * b1 + rot[8] * b2, qm.n[2]));
+}
+
+__global__ void k_state_setup(ModelDev M, MeshDev D, double T, double mu, double *st_eps, double *st_vel,
+                              double *st_ff, double *st_wt, uint32_t *kcrd, int2 *kinfo) {
+  int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int nb = M.nb;
+  if (t < D.n_ibzw * nb) {
+    int64_t i = t / nb;
+    int m = int(t % nb);
+    int k = D.ibzw_list[i];
+    bool act = (D.amask[k] >> m) & 1u;
+    double e = D.eps[size_t(k) * nb + m];
+    double f = fermi_b(e, mu, kKbEVK * T);
+    st_eps[t] = e;
+    for (int a = 0; a < 3; ++a) st_vel[t * 3 + a] = D.vel[(size_t(k) * nb + m) * 3 + a];
+    st_ff[t] = act ? f * (1.0 - f) : 0.0;
+    st_wt[t] = act ? 1.0 / double(D.stab[k]) : 0.0;
+  }
+  if (t < D.nk) {
+    int a0, a1, a2;
+    D.km.unflat(int(t), a0, a1, a2);
+    kcrd[t] = uint32_t(a0) | (uint32_t(a1) << 10) | (uint32_t(a2) << 20);
+    int r = D.rep[t];
+    int iw = D.ibzw_of[r];
+    kinfo[t] = make_int2(iw >= 0 ? iw * nb : -1, D.op[t]);
+  }
+}
+
+// W_e = sum_row (X+ + X-) / (f(1-f)); I0 = (eps-mu)/T v/W; J0 = v/W   (Eqs. W^RTA_mk, I0/J0)
+__global__ void k_rta_electron(BteDev B, double *W_e, double *inv_ffW, double *I0, double *J0,
+                               unsigned long long *n_zero) {
+  int64_t st = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (st >= B.nst) return;
+  double s = 0.0;
+  for (int64_t e = B.row_ptr[st] + lane; e < B.row_ptr[st + 1]; e += 32) {
+    double2 x = B.e_X[e];
+    s += x.x + x.y;
+  }
+  s = warp_sum(s);
+  if (lane == 0) {
+    double ff = B.st_ff[st];
+    double W = 0.0, inv = 0.0;
+    if (ff > 0.0 && s > 0.0) {
+      W = s / ff;
+      inv = 1.0 / (ff * W);
+    } else if (ff > 0.0) {
+      atomicAdd(n_zero, 1ull);
+    }
+    W_e[st] = W;
+    inv_ffW[st] = inv;
+    double c = W > 0.0 ? (B.st_eps[st] - B.mu) / B.T : 0.0;
+    for (int a = 0; a < 3; ++a) {
+      double v = W > 0.0 ? B.st_vel[st * 3 + a] / W : 0.0;
+      I0[st * 3 + a] = c * v;
+      J0[st * 3 + a] = v;
+    }
+  }
+}
+
+// Bt(q,s) = sum over the phonon row of Y/|stab|
+__global__ void k_ph_rowsum(BteDev B, double *Bt) {
+  int64_t row = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (row >= B.nq * B.nbr) return;
+  double s = 0.0;
+  for (int64_t e = B.ph_row_ptr[row] + lane; e < B.ph_row_ptr[row + 1]; e += 32) s += B.ph_Y[e];
+  s = warp_sum(s);
+  if (lane == 0) Bt[row] = s;
+}
+
+// W_ph = d_s sum_S Bt(S^-1 q) / (n(1+n)) + W_bg; F0 = (hbar w/T) v / W   (Eqs. W^RTA_sq, F0/G0)
+__global__ void k_rta_phonon(ModelDev M, MeshDev D, BteDev B, const double *Bt, double *W_ph, double *inv_nnW,
+                             double *F0) {
+  __shared__ int rot[kMaxSym * 9];
+  __shared__ int inv[kMaxSym];
+  for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) rot[t] = M.sym_rot[t];
+  for (int t = threadIdx.x; t < M.nsym; t += blockDim.x) inv[t] = M.sym_inv[t];
+  __syncthreads();
+  int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int nbr = M.nbr;
+  if (t >= D.nq * nbr) return;
+  int q = int(t / nbr), s = int(t % nbr);
+  double w = D.w[t];
+  double kT = kKbEVK * B.T;
+  double W = 0.0, invw = 0.0;
+  if (w > D.omega_min) {
+    double sum = 0.0;
+    for (int o = 0; o < M.nsym; ++o) sum += Bt[size_t(q_image(D.qm, rot + 9 * inv[o], q)) * nbr + s];
+    double n = bose_b(w, kT);
+    double nn1 = n * (1.0 + n);
+    double wr = w / M.bg_w;
+    W = M.spin_deg * sum / nn1 + M.bg_coeff * wr * wr * (B.T / M.bg_T);
+    invw = 1.0 / (nn1 * W);
+  }
+  W_ph[t] = W;
+  inv_nnW[t] = invw;
+  for (int a = 0; a < 3; ++a) F0[t * 3 + a] = W > 0.0 ? (w / B.T) * D.vph[t * 3 + a] / W : 0.0;
+}
+
+// One warp per electron row (k,m):
+//   I_out = I0 + [sum (X+ + X-) S_k' I_<k'>n  (- F_qs X+ + F_-qs X-)] / (f(1-f) W)   (Eqs. dI^S, dI^D)
+// and the same for J with G.
+__global__ void __launch_bounds__(256) k_e_sweep(ModelDev M, MeshDev D, BteDev B, const int2 *__restrict__ kinfo,
+                                                 const double *__restrict__ I0, const double *__restrict__ J0,
+                                                 const double *__restrict__ inv_ffW, const double *__restrict__ I,
+                                                 const double *__restrict__ J, const double *__restrict__ F,
+                                                 const double *__restrict__ G, int drag, double *I_out,
+                                                 double *J_out) {
+  __shared__ double C[kMaxSym * 9];
+  for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) C[t] = M.sym_cart[t];
+  __syncthreads();
+  int64_t st = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (st >= B.nst) return;
+  const int nb = B.nb, nbr = B.nbr;
+  const int k = D.ibzw_list[st / nb];
+  const uint32_t kc = B.kcrd[k];
+  const int k0 = kc & 1023u, k1 = (kc >> 10) & 1023u, k2 = kc >> 20;
+  double aI[3] = {0, 0, 0}, aJ[3] = {0, 0, 0};
+  for (int64_t e = B.row_ptr[st] + lane; e < B.row_ptr[st + 1]; e += 32) {
+    uint32_t pk = B.e_kpns[e];
+    double2 X = B.e_X[e];
+    int kp = unpack_kp(pk), n = unpack_n(pk), s = unpack_s(pk);
+    int2 inf = kinfo[kp];
+    int64_t st2 = inf.x + n;
+    const double *Cs = C + 9 * inf.y;
+    double r[3];
+    double xs = X.x + X.y;
+    rot3(Cs, I + st2 * 3, r);
+    for (int a = 0; a < 3; ++a) aI[a] += xs * r[a];
+    rot3(Cs, J + st2 * 3, r);
+    for (int a = 0; a < 3; ++a) aJ[a] += xs * r[a];
+    if (drag) {
+      uint32_t pc = B.kcrd[kp];
+      int d0 = pmod(int(pc & 1023u) - k0, D.km.n[0]) / D.ratio[0];
+      int d1 = pmod(int((pc >> 10) & 1023u) - k1, D.km.n[1]) / D.ratio[1];
+      int d2 = pmod(int(pc >> 20) - k2, D.km.n[2]) / D.ratio[2];
+      int64_t q = D.qm.flat(d0, d1, d2);
+      int64_t mq = D.qm.flat(pmod(-d0, D.qm.n[0]), pmod(-d1, D.qm.n[1]), pmod(-d2, D.qm.n[2]));
+      const double *Fq = F + (q * nbr + s) * 3, *Fm = F + (mq * nbr + s) * 3;
+      const double *Gq = G + (q * nbr + s) * 3, *Gm = G + (mq * nbr + s) * 3;
+      for (int a = 0; a < 3; ++a) {
+        aI[a] += -Fq[a] * X.x + Fm[a] * X.y;
+        aJ[a] += -Gq[a] * X.x + Gm[a] * X.y;
+      }
+    }
+  }
+  for (int a = 0; a < 3; ++a) {
+    aI[a] = warp_sum(aI[a]);
+    aJ[a] = warp_sum(aJ[a]);
+  }
+  if (lane == 0) {
+    double c = inv_ffW[st];
+    for (int a = 0; a < 3; ++a) {
+      I_out[st * 3 + a] = I0[st * 3 + a] + aI[a] * c;
+      J_out[st * 3 + a] = J0[st * 3 + a] + aJ[a] * c;
+    }
+  }
+}
+
+// One warp per phonon row (q,s): Btv = sum Y/|stab| (S_k' I_<k'>n - I_km), fields I and J.
+__global__ void __launch_bounds__(256) k_ph_sweep(ModelDev M, MeshDev D, BteDev B, const int2 *__restrict__ kinfo,
+                                                  const double *__restrict__ I, const double *__restrict__ J,
+                                                  double *Btv) {
+  __shared__ double C[kMaxSym * 9];
+  for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) C[t] = M.sym_cart[t];
+  __syncthreads();
+  int64_t row = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (row >= B.nq * B.nbr) return;
+  double aI[3] = {0, 0, 0}, aJ[3] = {0, 0, 0};
+  for (int64_t e = B.ph_row_ptr[row] + lane; e < B.ph_row_ptr[row + 1]; e += 32) {
+    int st = B.ph_st[e];
+    uint32_t pk = B.ph_kpn[e];
+    double y = B.ph_Y[e];
+    int kp = unpack_kp(pk), n = unpack_n(pk);
+    int2 inf = kinfo[kp];
+    int64_t st2 = inf.x + n;
+    const double *Cs = C + 9 * inf.y;
+    double r[3];
+    rot3(Cs, I + st2 * 3, r);
+    for (int a = 0; a < 3; ++a) aI[a] += y * (r[a] - I[int64_t(st) * 3 + a]);
+    rot3(Cs, J + st2 * 3, r);
+    for (int a = 0; a < 3; ++a) aJ[a] += y * (r[a] - J[int64_t(st) * 3 + a]);
+  }
+  for (int a = 0; a < 3; ++a) {
+    aI[a] = warp_sum(aI[a]);
+    aJ[a] = warp_sum(aJ[a]);
+  }
+  if (lane == 0)
+    for (int a = 0; a < 3; ++a) {
+      Btv[row * 6 + a] = aI[a];
+      Btv[row * 6 + 3 + a] = aJ[a];
+    }
+}
+
+// F = F0 + d_s/(n(1+n)W) sum_S C_S Btv_I(S^-1 q); G = d_s/(n(1+n)W) sum_S C_S Btv_J(S^-1 q)   (Eq. dF^D)
+__global__ void k_ph_update(ModelDev M, MeshDev D, BteDev B, const double *Btv, const double *F0,
+                            const double *inv_nnW, double *F, double *G) {
+  __shared__ int rot[kMaxSym * 9];
+  __shared__ int inv[kMaxSym];
+  __shared__ double C[kMaxSym * 9];
+  for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) {
+    rot[t] = M.sym_rot[t];
+    C[t] = M.sym_cart[t];
+  }
+  for (int t = threadIdx.x; t < M.nsym; t += blockDim.x) inv[t] = M.sym_inv[t];
+  __syncthreads();
+  int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int nbr = M.nbr;
+  if (t >= D.nq * nbr) return;
+  int q = int(t / nbr), s = int(t % nbr);
+  double aI[3] = {0, 0, 0}, aJ[3] = {0, 0, 0};
+  for (int o = 0; o < M.nsym; ++o) {
+    int64_t src = int64_t(q_image(D.qm, rot + 9 * inv[o], q)) * nbr + s;
+    double r[3];
+    rot3(C + 9 * o, Btv + src * 6, r);
+    for (int a = 0; a < 3; ++a) aI[a] += r[a];
+    rot3(C + 9 * o, Btv + src * 6 + 3, r);
+    for (int a = 0; a < 3; ++a) aJ[a] += r[a];
+  }
+  double c = M.spin_deg * inv_nnW[t];
+  for (int a = 0; a < 3; ++a) {
+    F[t * 3 + a] = F0[t * 3 + a] + c * aI[a];
+    G[t * 3 + a] = c * aJ[a];
+  }
+}
+
+// ---------------------------------------------------------------- coefficient reductions
+constexpr int kNPart = 304;     // fixed number of partial-sum blocks (2 per SM)
+constexpr int kCT = 256;
+constexpr int kNAcc = 54;       // 4 electron + 2 phonon 3x3 sums
+
+__device__ inline void block_reduce_store(double *acc, int nacc, double *out) {
+  __shared__ double wsum[kCT / 32][kNAcc];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int j = 0; j < nacc; ++j) {
+    double v = warp_sum(acc[j]);
+    if (lane == 0) wsum[wid][j] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nacc) {
+    double s = 0.0;
+    for (int w = 0; w < kCT / 32; ++w) s += wsum[w][threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kCT) k_coeff_partial(MeshDev D, BteDev B, const double *I, const double *J,
+                                                       const double *F, const double *G, double *partial) {
+  double acc[kNAcc];
+  for (int j = 0; j < kNAcc; ++j) acc[j] = 0.0;
+  const int64_t stride = int64_t(gridDim.x) * kCT;
+  for (int64_t st = blockIdx.x * int64_t(kCT) + threadIdx.x; st < B.nst; st += stride) {
+    double wff = B.st_wt[st] * B.st_ff[st];
+    if (wff == 0.0) continue;
+    double d = B.st_eps[st] - B.mu;
+    const double *v = B.st_vel + st * 3;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        double vj = wff * v[a] * J[st * 3 + b];
+        double vi = -wff * v[a] * I[st * 3 + b];
+        acc[a * 3 + b] += vj;
+        acc[9 + a * 3 + b] += vi;
+        acc[18 + a * 3 + b] += d * vj;
+        acc[27 + a * 3 + b] += d * vi;
+      }
+  }
+  const double kT = kKbEVK * B.T;
+  for (int64_t t = blockIdx.x * int64_t(kCT) + threadIdx.x; t < B.nq * B.nbr; t += stride) {
+    double w = D.w[t];
+    if (!(w > D.omega_min)) continue;
+    double n = bose_b(w, kT);
+    double wt = w * n * (1.0 + n);
+    const double *v = D.vph + t * 3;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        acc[36 + a * 3 + b] += -wt * v[a] * G[t * 3 + b];
+        acc[45 + a * 3 + b] += wt * v[a] * F[t * 3 + b];
+      }
+  }
+  block_reduce_store(acc, kNAcc, partial + size_t(blockIdx.x) * kNAcc);
+}
+
+__device__ inline void symmetrise(const double *C, int nsym, const double *M, double *out) {
+  for (int j = 0; j < 9; ++j) out[j] = 0.0;
+  for (int o = 0; o < nsym; ++o) {
+    const double *S = C + 9 * o;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        double s = 0.0;
+        for (int c = 0; c < 3; ++c)
+          for (int d = 0; d < 3; ++d) s += S[a * 3 + c] * M[c * 3 + d] * S[b * 3 + d];
+        out[a * 3 + b] += s;
+      }
+  }
+}
+
+__device__ inline double fro2(const double *a) {
+  double s = 0.0;
+  for (int j = 0; j < 9; ++j) s += a[j] * a[j];
+  return s;
+}
+
+__device__ inline double rel_change(const double *a, const double *b) {
+  double n = fro2(a);
+  if (n == 0.0) return 0.0;
+  double d = 0.0;
+  for (int j = 0; j < 9; ++j) d += (a[j] - b[j]) * (a[j] - b[j]);
+  return sqrt(d) / sqrt(n);
+}
+
+// res: [0] sigma [9] sigmaS [18] alpha_el [27] kappa0_el [36] alpha_ph [45] kappa_ph [54] S [63] kappa_el
+//      [72] residual_e [73] residual_all
+__global__ void k_coeff_final(ModelDev M, BteDev B, const double *partial, int npart, double *res, double *prev) {
+  __shared__ double Ms[kNAcc];
+  if (threadIdx.x < kNAcc) {
+    double s = 0.0;
+    for (int b = 0; b < npart; ++b) s += partial[size_t(b) * kNAcc + threadIdx.x];
+    Ms[threadIdx.x] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double t[9];
+  const double sg[4] = {1.0, 1.0, -1.0, -1.0};
+  for (int c = 0; c < 4; ++c) {
+    symmetrise(M.sym_cart, M.nsym, Ms + 9 * c, t);
+    for (int j = 0; j < 9; ++j) res[9 * c + j] = sg[c] * B.Pe * t[j];
+  }
+  for (int j = 0; j < 9; ++j) {
+    res[36 + j] = B.Pph * Ms[36 + j];
+    res[45 + j] = B.Pph * Ms[45 + j];
+  }
+  // S = sigma^-1 sigmaS (adjugate inverse), kappa_el = kappa0_el - alpha_el S
+  const double *s = res;
+  double inv[9];
+  inv[0] = s[4] * s[8] - s[5] * s[7];
+  inv[1] = s[2] * s[7] - s[1] * s[8];
+  inv[2] = s[1] * s[5] - s[2] * s[4];
+  inv[3] = s[5] * s[6] - s[3] * s[8];
+  inv[4] = s[0] * s[8] - s[2] * s[6];
+  inv[5] = s[2] * s[3] - s[0] * s[5];
+  inv[6] = s[3] * s[7] - s[4] * s[6];
+  inv[7] = s[1] * s[6] - s[0] * s[7];
+  inv[8] = s[0] * s[4] - s[1] * s[3];
+  double det = s[0] * inv[0] + s[1] * inv[3] + s[2] * inv[6];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double v = 0.0;
+      for (int c = 0; c < 3; ++c) v += inv[a * 3 + c] * res[9 + c * 3 + b];
+      res[54 + a * 3 + b] = det != 0.0 ? v / det : 0.0;
+    }
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double v = 0.0;
+      for (int c = 0; c < 3; ++c) v += res[18 + a * 3 + c] * res[54 + c * 3 + b];
+      res[63 + a * 3 + b] = res[27 + a * 3 + b] - v;
+    }
+  double re = 0.0, ra = 0.0;
+  for (int c = 0; c < 6; ++c) {
+    double r = rel_change(res + 9 * c, prev + 9 * c);
+    if (c < 4) re = fmax(re, r);
+    ra = fmax(ra, r);
+  }
+  res[72] = re;
+  res[73] = ra;
+  for (int j = 0; j < 54; ++j) prev[j] = res[j];
+}
+
+// Kelvin-Onsager step: B = sigmaS[I_drag], A = alpha_ph / T, lambda = <A,B>/<B,B>
+__global__ void __launch_bounds__(kCT) k_ko_partial(BteDev B, const double *I, const double *J, double *partial) {
+  double acc[9];
+  for (int j = 0; j < 9; ++j) acc[j] = 0.0;
+  const int64_t stride = int64_t(gridDim.x) * kCT;
+  for (int64_t st = blockIdx.x * int64_t(kCT) + threadIdx.x; st < B.nst; st += stride) {
+    double wff = B.st_wt[st] * B.st_ff[st];
+    if (wff == 0.0) continue;
+    double d = (B.st_eps[st] - B.mu) / B.T;
+    const double *v = B.st_vel + st * 3;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) acc[a * 3 + b] += -wff * v[a] * (I[st * 3 + b] - d * J[st * 3 + b]);
+  }
+  block_reduce_store(acc, 9, partial + size_t(blockIdx.x) * kNAcc);
+}
+
+__global__ void k_ko_final(ModelDev M, BteDev B, const double *partial, int npart, double *res) {
+  __shared__ double Ms[9];
+  if (threadIdx.x < 9) {
+    double s = 0.0;
+    for (int b = 0; b < npart; ++b) s += partial[size_t(b) * kNAcc + threadIdx.x];
+    Ms[threadIdx.x] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double t[9];
+  symmetrise(M.sym_cart, M.nsym, Ms, t);
+  double bb = 0.0, ab = 0.0;
+  for (int j = 0; j < 9; ++j) {
+    double b = B.Pe * t[j];
+    double a = res[36 + j] / B.T;
+    bb += b * b;
+    ab += a * b;
+  }
+  if (sqrt(bb) > 1e-30) {
+    res[74] = ab / bb;
+    res[75] = 1.0;
+  } else {
+    res[75] = 0.0;
+  }
+}
+
+__global__ void k_ko_apply(BteDev B, double *I, const double *J, const double *res) {
+  if (res[75] == 0.0) return;
+  double lam = res[74];
+  int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= B.nst * 3) return;
+  int64_t st = t / 3;
+  double d = (B.st_eps[st] - B.mu) / B.T;
+  double idiff = d * J[t];
+  I[t] = idiff + lam * (I[t] - idiff);
+}
+
+}  // namespace
+
+int coeff_partials() { return kNPart; }
+
+cudaError_t launch_state_setup(const ModelDev &M, const MeshDev &D, double T, double mu, double *st_eps,
+                               double *st_vel, double *st_ff, double *st_wt, uint32_t *kcrd, int2 *kinfo,
+                               cudaStream_t st) {
+  int64_t n = D.n_ibzw * M.nb > D.nk ? D.n_ibzw * M.nb : D.nk;
+  EPHB_LAUNCH(k_state_setup, unsigned((n + 255) / 256), 256, 0, st, M, D, T, mu, st_eps, st_vel, st_ff, st_wt, kcrd, kinfo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rta_electron(const BteDev &B, double *W_e, double *inv_ffW, double *I0, double *J0,
+                                unsigned long long *n_zero, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(n_zero, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess || B.nst == 0) return e;
+  EPHB_LAUNCH(k_rta_electron, unsigned((B.nst * 32 + 255) / 256), 256, 0, st, B, W_e, inv_ffW, I0, J0, n_zero);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ph_rowsum(const BteDev &B, double *Bt, cudaStream_t st) {
+  EPHB_LAUNCH(k_ph_rowsum, unsigned((B.nq * B.nbr * 32 + 255) / 256), 256, 0, st, B, Bt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rta_phonon(const ModelDev &M, const MeshDev &D, const BteDev &B, const double *Bt, double *W_ph,
+                              double *inv_nnW, double *F0, cudaStream_t st) {
+  EPHB_LAUNCH(k_rta_phonon, unsigned((D.nq * M.nbr + 255) / 256), 256, 0, st, M, D, B, Bt, W_ph, inv_nnW, F0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_e_sweep(const ModelDev &M, const MeshDev &D, const BteDev &B, const int2 *kinfo, const double *I0,
+                           const double *J0, const double *inv_ffW, const double *I, const double *J,
+                           const double *F, const double *G, int drag, double *I_out, double *J_out,
+                           cudaStream_t st) {
+  if (B.nst == 0) return cudaSuccess;
+  EPHB_LAUNCH(k_e_sweep, unsigned((B.nst * 32 + 255) / 256), 256, 0, st, M, D, B, kinfo, I0, J0, inv_ffW, I, J, F, G, drag,
+                                                                 I_out, J_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ph_sweep(const ModelDev &M, const MeshDev &D, const BteDev &B, const int2 *kinfo, const double *I,
+                            const double *J, double *Btv, cudaStream_t st) {
+  EPHB_LAUNCH(k_ph_sweep, unsigned((B.nq * B.nbr * 32 + 255) / 256), 256, 0, st, M, D, B, kinfo, I, J, Btv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ph_update(const ModelDev &M, const MeshDev &D, const BteDev &B, const double *Btv,
+                             const double *F0, const double *inv_nnW, double *F, double *G, cudaStream_t st) {
+  EPHB_LAUNCH(k_ph_update, unsigned((D.nq * M.nbr + 255) / 256), 256, 0, st, M, D, B, Btv, F0, inv_nnW, F, G);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coefficients(const ModelDev &M, const MeshDev &D, const BteDev &B, const double *I,
+                                const double *J, const double *F, const double *G, double *partial,
+                                int npartial, double *res, double *prev, cudaStream_t st) {
+  EPHB_LAUNCH(k_coeff_partial, npartial, kCT, 0, st, D, B, I, J, F, G, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  EPHB_LAUNCH(k_coeff_final, 1, 64, 0, st, M, B, partial, npartial, res, prev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ko(const ModelDev &M, const MeshDev &D, const BteDev &B, double *I, const double *J,
+                      double *partial, int npartial, double *res, cudaStream_t st) {
+  EPHB_LAUNCH(k_ko_partial, npartial, kCT, 0, st, B, I, J, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  EPHB_LAUNCH(k_ko_final, 1, 32, 0, st, M, B, partial, npartial, res);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || B.nst == 0) return e;
+  EPHB_LAUNCH(k_ko_apply, unsigned((B.nst * 3 + 255) / 256), 256, 0, st, B, I, J, res);
+  return cudaGetLastError();
+}
+
+}  // namespace ephb

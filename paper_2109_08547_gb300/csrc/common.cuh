@@ -1,0 +1,93 @@
+// Shared device helpers of the CUDA path: complex arithmetic on double2, physical
+// constants, mesh index arithmetic and the plain-old-data views the kernels receive.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ephb {
+
+// Process-wide count of kernels launched by the library (defined in api.cu).
+void note_launches(int n);
+
+}  // namespace ephb
+
+// Every kernel launch of the library goes through this macro so that launches are counted.
+#define EPHB_LAUNCH(kernel, grid, block, smem, stream, ...) \
+  (::ephb::note_launches(1), kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__))
+
+namespace ephb {
+
+// Physical constants (CODATA 2018 / SI 2019), eV, K, s, C.
+constexpr double kHbarEVs = 6.582119569e-16;
+constexpr double kKbEVK = 8.617333262e-5;
+constexpr double kECharge = 1.602176634e-19;
+constexpr double kAngstrom = 1.0e-10;
+constexpr double kPi = 3.14159265358979323846;
+
+constexpr int kMaxBands = 8;       // electron Wannier bands
+constexpr int kMaxBranches = 12;   // phonon branches (4 atoms)
+constexpr int kMaxSym = 48;
+
+// entry packing of the electron-side rate list: k' (21 bits) | n (4 bits) | s (6 bits)
+constexpr int kKpBits = 21;
+constexpr uint32_t kKpMask = (1u << kKpBits) - 1u;
+__host__ __device__ inline uint32_t pack_kpns(int kp, int n, int s) {
+  return uint32_t(kp) | (uint32_t(n) << kKpBits) | (uint32_t(s) << (kKpBits + 4));
+}
+__host__ __device__ inline int unpack_kp(uint32_t v) { return int(v & kKpMask); }
+__host__ __device__ inline int unpack_n(uint32_t v) { return int((v >> kKpBits) & 15u); }
+__host__ __device__ inline int unpack_s(uint32_t v) { return int(v >> (kKpBits + 4)); }
+
+// complex helpers ------------------------------------------------------------------------
+__host__ __device__ inline double2 cmk(double r, double i) { return make_double2(r, i); }
+__host__ __device__ inline double2 cadd(double2 a, double2 b) { return cmk(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 csub(double2 a, double2 b) { return cmk(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline double2 cmul(double2 a, double2 b) {
+  return cmk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline double2 cconj(double2 a) { return cmk(a.x, -a.y); }
+__host__ __device__ inline double2 cscale(double2 a, double s) { return cmk(a.x * s, a.y * s); }
+// acc += a * b
+__host__ __device__ inline void cfma(double2 &acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+__host__ __device__ inline void cfma_conj(double2 &acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+__host__ __device__ inline double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+// mesh helpers -----------------------------------------------------------------------------
+struct Mesh {
+  int n[3];
+  __host__ __device__ int64_t size() const { return int64_t(n[0]) * n[1] * n[2]; }
+  __host__ __device__ int flat(int i0, int i1, int i2) const { return (i0 * n[1] + i1) * n[2] + i2; }
+  __host__ __device__ void unflat(int k, int &i0, int &i1, int &i2) const {
+    i2 = k % n[2];
+    int t = k / n[2];
+    i1 = t % n[1];
+    i0 = t / n[1];
+  }
+};
+
+__host__ __device__ inline int pmod(long long a, int n) {
+  long long r = a % n;
+  return int(r < 0 ? r + n : r);
+}
+
+// exp(i 2 pi sum_d i_d R_d / n_d) from per-dimension tables tab[off_d + j] = exp(i 2 pi j / n_d)
+__device__ inline double2 mesh_phase(const double2 *__restrict__ tab, const Mesh &m, int i0, int i1, int i2,
+                                     int r0, int r1, int r2) {
+  double2 p0 = tab[pmod((long long)i0 * r0, m.n[0])];
+  double2 p1 = tab[m.n[0] + pmod((long long)i1 * r1, m.n[1])];
+  double2 p2 = tab[m.n[0] + m.n[1] + pmod((long long)i2 * r2, m.n[2])];
+  return cmul(cmul(p0, p1), p2);
+}
+
+}  // namespace ephb

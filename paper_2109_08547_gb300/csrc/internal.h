@@ -1,0 +1,141 @@
+// Internal declarations shared by the translation units of the CUDA library.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace ephb {
+
+// Device copy of the Wannier model (pointers are device pointers).
+struct ModelDev {
+  int nat = 0, nb = 0, nbr = 0, nRe = 0, nRd = 0, nRge = 0, nRgp = 0, nsym = 0;
+  double lattice[9] = {0};
+  double omega_ref = 0, spin_deg = 2, bg_coeff = 0, bg_w = 1, bg_T = 300;
+  double mass[4] = {0};
+  double mass_mean = 1;
+  const int *Re = nullptr, *Rd = nullptr, *Rge = nullptr, *Rgp = nullptr;
+  const double2 *H_R = nullptr, *D_R = nullptr, *g_R = nullptr;
+  const int *sym_rot = nullptr;       // [nsym][9]
+  const double *sym_cart = nullptr;   // [nsym][9]
+  const int *sym_inv = nullptr;       // [nsym]
+};
+
+// Views of the mesh-level arrays.
+struct MeshDev {
+  Mesh km, qm;
+  int ratio[3];
+  int64_t nk, nq;
+  const double2 *ktab, *qtab;         // per-dimension phase tables
+  const double *eps;                  // [nk][nb]
+  const double2 *cvec;                // [nk][nb][nb]  c[k][row][col]
+  const double *vel;                  // [nk][nb][3]
+  const uint8_t *egrp;                // [nk][nb][2] degenerate group [lo, hi)
+  const uint32_t *amask;              // [nk]
+  const double *w;                    // [nq][nbr]
+  const double2 *u;                   // [nq][nbr][nbr]
+  const double *vph;                  // [nq][nbr][3]
+  const uint8_t *pgrp;                // [nq][nbr][2]
+  const int *rep, *op, *stab;         // [nk]
+  const int *ibzw_of;                 // [nk] index in the irreducible-window list or -1
+  const int *ibzw_list;               // [n_ibzw]
+  int64_t n_ibzw;
+  const int64_t *pair_ptr;            // [n_ibzw+1]
+  const int *pair_q;                  // [n_pairs]
+  const int *pair_i;                  // [n_pairs]
+  const int64_t *qpair_ptr;           // [nq+1]
+  const int *pq_rank;                 // [n_pairs] rank of pair among the pairs of its q
+  int64_t n_pairs;
+  double omega_min, degen_tol;
+};
+
+// ---- scan.cu
+// out[i] = sum_{j<i} in[j]; returns the total through *total_dev (device int64).
+template <typename T>
+cudaError_t exclusive_scan(const T *in, int64_t *out, int64_t n, int64_t *total_dev, int64_t *scratch,
+                           int64_t scratch_elems, cudaStream_t st);
+int64_t scan_scratch_elems(int64_t n);
+
+// ---- bloch.cu
+cudaError_t launch_phase_tables(double2 *tab, Mesh m, cudaStream_t st);
+cudaError_t launch_electron_bands(const ModelDev &M, Mesh km, const double2 *ktab, double degen_tol, double lo,
+                                  double hi, double *eps, double2 *cvec, double *vel, uint8_t *egrp,
+                                  uint32_t *amask, cudaStream_t st);
+cudaError_t launch_phonon_modes(const ModelDev &M, Mesh qm, const double2 *qtab, double degen_tol, double omega_min,
+                                double *w, double2 *u, double *vph, uint8_t *pgrp, cudaStream_t st);
+cudaError_t launch_ibz(const ModelDev &M, Mesh km, int *rep, int *op, int *stab, int *ibzw_flag,
+                       const uint32_t *amask, cudaStream_t st);
+cudaError_t launch_ibzw_fill(int64_t nk, const int *flag, const int64_t *pos, int *ibzw_list, int *ibzw_of,
+                             cudaStream_t st);
+cudaError_t launch_pair_count(const MeshDev &D, int *npairs, cudaStream_t st);
+cudaError_t launch_pair_fill(const MeshDev &D, int *pair_q, int *pair_i, cudaStream_t st);
+cudaError_t launch_qpair_count(const MeshDev &D, int *qcount, cudaStream_t st);
+cudaError_t launch_qpair_fill(const MeshDev &D, int *pq_rank, cudaStream_t st);
+cudaError_t launch_count_bits(const uint32_t *amask, int64_t n, int64_t *out, cudaStream_t st);
+cudaError_t launch_count_reps(const int *rep, int64_t n, int64_t *out, cudaStream_t st);
+
+// ---- vertex.cu
+struct RateParams {
+  double T, mu, sigma, cut, inv_Nq_pref;   // inv_Nq_pref = 2 pi / (hbar N_q)
+  double y_scale;                          // N_q / N_k
+};
+cudaError_t launch_rate_count(const ModelDev &M, const MeshDev &D, RateParams rp, int *cntE, int *cntPh,
+                              unsigned long long *n_tuples, cudaStream_t st);
+cudaError_t launch_row_ptrs(const MeshDev &D, int nb, int nbr, const int64_t *escan, const int64_t *phscan,
+                            int64_t e_total, int64_t ph_total, int64_t *row_ptr, int64_t *ph_row_ptr,
+                            cudaStream_t st);
+cudaError_t launch_stage_a(const ModelDev &M, const MeshDev &D, int64_t i0, int64_t nkc, double2 *T, double2 *A,
+                           cudaStream_t st);
+cudaError_t launch_stage_b_rates(const ModelDev &M, const MeshDev &D, RateParams rp, int64_t i0, int64_t nkc,
+                                 const double2 *A, const int64_t *escan, const int64_t *phscan, uint32_t *e_kpns,
+                                 double2 *e_X, int *ph_st, uint32_t *ph_kpn, double *ph_Y, cudaStream_t st);
+size_t stage_a_T_elems(const ModelDev &M);
+size_t stage_a_A_elems(const ModelDev &M);
+
+// ---- bte.cu
+struct BteDev {
+  int nb, nbr, nsym;
+  int64_t nst, nq;
+  double T, mu, spin_deg, Pe, Pph;
+  const int64_t *row_ptr;
+  const uint32_t *e_kpns;
+  const double2 *e_X;
+  const int64_t *ph_row_ptr;
+  const int *ph_st;
+  const uint32_t *ph_kpn;
+  const double *ph_Y;
+  const uint32_t *kcrd;    // packed k coordinates (10 bits each)
+  const double *st_eps;    // [nst]
+  const double *st_vel;    // [nst][3]
+  const double *st_ff;     // [nst] f(1-f)
+  const double *st_wt;     // [nst] 1/|stab| (0 for inactive)
+};
+// kinfo[k] = (state base of the representative <k> = ibzw index * nb (or -1), op taking <k> to k)
+cudaError_t launch_state_setup(const ModelDev &M, const MeshDev &D, double T, double mu, double *st_eps,
+                               double *st_vel, double *st_ff, double *st_wt, uint32_t *kcrd, int2 *kinfo,
+                               cudaStream_t st);
+cudaError_t launch_rta_electron(const BteDev &B, double *W_e, double *inv_ffW, double *I0, double *J0,
+                                unsigned long long *n_zero, cudaStream_t st);
+cudaError_t launch_ph_rowsum(const BteDev &B, double *Bt, cudaStream_t st);
+cudaError_t launch_rta_phonon(const ModelDev &M, const MeshDev &D, const BteDev &B, const double *Bt, double *W_ph,
+                              double *inv_nnW, double *F0, cudaStream_t st);
+cudaError_t launch_e_sweep(const ModelDev &M, const MeshDev &D, const BteDev &B, const int2 *kinfo, const double *I0,
+                           const double *J0, const double *inv_ffW, const double *I, const double *J,
+                           const double *F, const double *G, int drag, double *I_out, double *J_out,
+                           cudaStream_t st);
+cudaError_t launch_ph_sweep(const ModelDev &M, const MeshDev &D, const BteDev &B, const int2 *kinfo, const double *I,
+                            const double *J, double *Btv, cudaStream_t st);
+cudaError_t launch_ph_update(const ModelDev &M, const MeshDev &D, const BteDev &B, const double *Btv,
+                             const double *F0, const double *inv_nnW, double *F, double *G, cudaStream_t st);
+// Coefficient tensors: partial sums then a single-block finalisation into `res`.
+//   res layout: [0] sigma [9] sigmaS [18] alpha_el [27] kappa0_el [36] alpha_ph [45] kappa_ph
+//               [54] S [63] kappa_el [72] residual_e [73] residual_all [74] lambda [75] ko_valid
+constexpr int kResLen = 80;
+cudaError_t launch_coefficients(const ModelDev &M, const MeshDev &D, const BteDev &B, const double *I,
+                                const double *J, const double *F, const double *G, double *partial,
+                                int npartial, double *res, double *prev, cudaStream_t st);
+cudaError_t launch_ko(const ModelDev &M, const MeshDev &D, const BteDev &B, double *I, const double *J,
+                      double *partial, int npartial, double *res, cudaStream_t st);
+int coeff_partials();
+
+}  // namespace ephb

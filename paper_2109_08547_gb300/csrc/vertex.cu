@@ -1,0 +1,458 @@
+// e-ph vertex interpolation (Eq. g^smn_kq of arXiv 2109.08547) fused with the transition
+// rates (Eq. X^e-ph; Y^ph-e as the same + process on the phonon side).
+//
+// The double Fourier sum over (R_e, R_ph) is evaluated in two contractions:
+//   stage A, per irreducible-window k:  A[rp][m,n',a] = sum_m' c_{m'm}(k) sum_re e^{ik.Re} gW[re][rp][m'][n'][a]
+//   stage B, per (k, q) pair:           B[m,n',a]    = sum_rp e^{iq.Rp} A[rp][m,n',a]
+// followed, in the same kernel, by the final-band and branch rotations, |g|^2, the
+// degenerate-subspace average, occupations, the Gaussian delta and the compacted writes
+// into the electron rows (k,m) and the phonon rows (q,s).
+#include "internal.h"
+
+namespace ephb {
+
+namespace {
+
+__device__ inline int kplusq_d(const MeshDev &D, int k, int q) {
+  int a0, a1, a2, b0, b1, b2;
+  D.km.unflat(k, a0, a1, a2);
+  D.qm.unflat(q, b0, b1, b2);
+  return D.km.flat(pmod(a0 + D.ratio[0] * b0, D.km.n[0]), pmod(a1 + D.ratio[1] * b1, D.km.n[1]),
+                   pmod(a2 + D.ratio[2] * b2, D.km.n[2]));
+}
+
+__device__ inline int nth_bit(uint32_t m, int n) {
+  for (int b = 0; b < 32; ++b)
+    if ((m >> b) & 1u) {
+      if (n == 0) return b;
+      --n;
+    }
+  return -1;
+}
+
+__device__ inline double fermi_d(double e, double mu, double kT) { return 1.0 / (exp((e - mu) / kT) + 1.0); }
+__device__ inline double bose_d(double w, double kT) { return w > 0.0 ? 1.0 / expm1(w / kT) : 0.0; }
+__device__ inline double gauss_d(double x, double sigma, double cut) {
+  if (fabs(x) > cut) return 0.0;
+  double r = x / sigma;
+  return exp(-0.5 * r * r) / (sigma * 2.5066282746310002);   // sqrt(2 pi)
+}
+
+// ------------------------------------------------------------------------ count pass
+__global__ void k_rate_count(ModelDev M, MeshDev D, RateParams rp, int *cntE, int *cntPh,
+                             unsigned long long *n_tuples) {
+  int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  unsigned long long nt = 0, fl = 0, ns = 0;
+  if (p < D.n_pairs) {
+    const int nb = M.nb, nbr = M.nbr;
+    int i = D.pair_i[p], q = D.pair_q[p];
+    int k = D.ibzw_list[i];
+    int kp = kplusq_d(D, k, q);
+    uint32_t am = D.amask[k], an = D.amask[kp];
+    int64_t p0 = D.pair_ptr[i];
+    int64_t npl = D.pair_ptr[i + 1] - p0, pl = p - p0;
+    // algorithmic flops of stage B for this pair: R_ph sum, branch rotation, band rotation
+    const unsigned long long na = __popc(am), nap = __popc(an);
+    fl = 8ull * (na * nb * nbr * (unsigned long long)M.nRgp + na * nb * nbr * nbr + na * nap * nb * nbr);
+    if (pl == 0) ns = na;
+    const double *ek = D.eps + size_t(k) * nb, *ekp = D.eps + size_t(kp) * nb, *wq = D.w + size_t(q) * nbr;
+    for (int m = 0; m < nb; ++m) {
+      int c = 0;
+      if ((am >> m) & 1u)
+        for (int n = 0; n < nb; ++n) {
+          if (!((an >> n) & 1u)) continue;
+          for (int s = 0; s < nbr; ++s) {
+            if (!(wq[s] > D.omega_min)) continue;
+            ++nt;
+            double xp = ekp[n] - ek[m] - wq[s];
+            double xm = ekp[n] - ek[m] + wq[s];
+            c += (fabs(xp) <= rp.cut || fabs(xm) <= rp.cut);
+          }
+        }
+      cntE[p0 * nb + m * npl + pl] = c;
+    }
+    int64_t qb = D.qpair_ptr[q];
+    int64_t npq = D.qpair_ptr[q + 1] - qb;
+    for (int s = 0; s < nbr; ++s) {
+      int c = 0;
+      if (wq[s] > D.omega_min)
+        for (int m = 0; m < nb; ++m) {
+          if (!((am >> m) & 1u)) continue;
+          for (int n = 0; n < nb; ++n) {
+            if (!((an >> n) & 1u)) continue;
+            double xp = ekp[n] - ek[m] - wq[s];
+            c += fabs(xp) <= rp.cut;
+          }
+        }
+      cntPh[qb * nbr + s * npq + D.pq_rank[p]] = c;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    nt += __shfl_down_sync(0xffffffffu, nt, o);
+    fl += __shfl_down_sync(0xffffffffu, fl, o);
+    ns += __shfl_down_sync(0xffffffffu, ns, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (nt) atomicAdd(n_tuples, nt);
+    if (fl) atomicAdd(n_tuples + 2, fl);
+    if (ns) atomicAdd(n_tuples + 3, ns);
+  }
+}
+
+// electron row starts (k,m) and phonon row starts (q,s) from the scanned count layouts
+__global__ void k_row_ptrs(MeshDev D, int nb, int nbr, const int64_t *escan, const int64_t *phscan,
+                           int64_t e_total, int64_t ph_total, int64_t *row_ptr, int64_t *ph_row_ptr) {
+  int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  int64_t ne = D.n_ibzw * nb, nph = D.nq * nbr;
+  if (t < ne) {
+    int64_t i = t / nb, m = t % nb;
+    int64_t p0 = D.pair_ptr[i], npl = D.pair_ptr[i + 1] - p0;
+    int64_t idx = p0 * nb + m * npl;
+    row_ptr[t] = idx < D.n_pairs * nb ? escan[idx] : e_total;
+  }
+  if (t == ne) row_ptr[ne] = e_total;
+  if (t < nph) {
+    int64_t q = t / nbr, s = t % nbr;
+    int64_t qb = D.qpair_ptr[q], npq = D.qpair_ptr[q + 1] - qb;
+    int64_t idx = qb * nbr + s * npq;
+    ph_row_ptr[t] = idx < D.n_pairs * nbr ? phscan[idx] : ph_total;
+  }
+  if (t == nph) ph_row_ptr[nph] = ph_total;
+}
+
+// ------------------------------------------------------------------------ stage A
+constexpr int kAKT = 8;   // k points per block
+
+// T[kc][col] = sum_re e^{i k.Re} gW[re][col], col = (rp, m', n', a)
+__global__ void __launch_bounds__(256) k_stage_a1(ModelDev M, MeshDev D, int64_t i0, int64_t nkc, double2 *T) {
+  extern __shared__ double2 sph[];   // [kAKT][nRge]
+  const int64_t ncol = int64_t(M.nRgp) * M.nb * M.nb * M.nbr;
+  const int64_t kc0 = int64_t(blockIdx.y) * kAKT;
+  for (int t = threadIdx.x; t < kAKT * M.nRge; t += blockDim.x) {
+    int kk = t / M.nRge, re = t % M.nRge;
+    double2 ph = cmk(0, 0);
+    if (kc0 + kk < nkc) {
+      int k = D.ibzw_list[i0 + kc0 + kk];
+      int a0, a1, a2;
+      D.km.unflat(k, a0, a1, a2);
+      ph = mesh_phase(D.ktab, D.km, a0, a1, a2, M.Rge[3 * re], M.Rge[3 * re + 1], M.Rge[3 * re + 2]);
+    }
+    sph[t] = ph;
+  }
+  __syncthreads();
+  int64_t col = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (col >= ncol) return;
+  double2 acc[kAKT];
+  for (int kk = 0; kk < kAKT; ++kk) acc[kk] = cmk(0, 0);
+  for (int re = 0; re < M.nRge; ++re) {
+    double2 g = M.g_R[re * ncol + col];
+    for (int kk = 0; kk < kAKT; ++kk) cfma(acc[kk], sph[kk * M.nRge + re], g);
+  }
+  for (int kk = 0; kk < kAKT; ++kk)
+    if (kc0 + kk < nkc) T[(kc0 + kk) * ncol + col] = acc[kk];
+}
+
+// A[kc][rp][j], j = ml*(nb*nbr) + n'*nbr + a over the active bands m of k:
+//   A = sum_m' c_{m'm}(k) T[kc][rp][m'][n'][a]
+__global__ void k_stage_a2(ModelDev M, MeshDev D, int64_t i0, int64_t nkc, const double2 *T, double2 *A) {
+  const int nb = M.nb, nbr = M.nbr;
+  const int64_t jmax = int64_t(nb) * nb * nbr;
+  const int64_t per_k = int64_t(M.nRgp) * jmax;
+  int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= nkc * per_k) return;
+  int64_t kc = t / per_k, r = t % per_k;
+  int rp = int(r / jmax), j = int(r % jmax);
+  int ml = j / (nb * nbr), na = j % (nb * nbr);
+  int k = D.ibzw_list[i0 + kc];
+  uint32_t am = D.amask[k];
+  double2 acc = cmk(0, 0);
+  if (ml < __popc(am)) {
+    int m = nth_bit(am, ml);
+    const double2 *Tk = T + kc * per_k + int64_t(rp) * jmax;
+    const double2 *ck = D.cvec + size_t(k) * nb * nb;
+    for (int mp = 0; mp < nb; ++mp) cfma(acc, ck[mp * nb + m], Tk[mp * nb * nbr + na]);
+  }
+  A[t] = acc;
+}
+
+// ------------------------------------------------------------------------ stage B + rates
+constexpr int kBT = 256;       // threads
+constexpr int kNR = 12;        // complex accumulators per thread
+constexpr int kRC = 16;        // R_ph chunk
+constexpr int kTPMax = 64;     // pairs per tile
+
+struct StageBSmem {
+  int jmax, tpmax, rc;
+  size_t off_B, off_ph, off_A, off_w, per_warp, total;
+};
+
+__host__ __device__ inline StageBSmem stage_b_layout(int nb, int nbr) {
+  StageBSmem L;
+  L.jmax = nb * nb * nbr;
+  L.tpmax = kTPMax;
+  L.rc = L.jmax > 192 ? 8 : kRC;
+  L.off_B = 0;
+  L.off_ph = L.off_B + size_t(kBT) * kNR * sizeof(double2);
+  L.off_A = L.off_ph + size_t(L.tpmax) * L.rc * sizeof(double2);
+  L.off_w = L.off_A + size_t(L.rc) * L.jmax * sizeof(double2);
+  L.per_warp = size_t(L.jmax) * sizeof(double2) + 3 * size_t(nb) * nb * nbr * sizeof(double);
+  L.total = L.off_w + (kBT / 32) * L.per_warp;
+  return L;
+}
+
+__global__ void __launch_bounds__(kBT) k_stage_b_rates(ModelDev M, MeshDev D, RateParams rp, int64_t i0,
+                                                       const double2 *__restrict__ A,
+                                                       const int64_t *__restrict__ escan,
+                                                       const int64_t *__restrict__ phscan, uint32_t *e_kpns,
+                                                       double2 *e_X, int *ph_st, uint32_t *ph_kpn, double *ph_Y) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nb = M.nb, nbr = M.nbr;
+  const StageBSmem L = stage_b_layout(nb, nbr);
+  double2 *Bsh = reinterpret_cast<double2 *>(smem + L.off_B);
+  double2 *phs = reinterpret_cast<double2 *>(smem + L.off_ph);
+  double2 *Ash = reinterpret_cast<double2 *>(smem + L.off_A);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned char *wscr = smem + L.off_w + wid * L.per_warp;
+  double2 *Zs = reinterpret_cast<double2 *>(wscr);
+  double *g2s = reinterpret_cast<double *>(wscr + size_t(L.jmax) * sizeof(double2));
+  double *Xps = g2s + nb * nb * nbr;
+  double *Xms = Xps + nb * nb * nbr;
+
+  const int64_t i = i0 + blockIdx.x;
+  const int k = D.ibzw_list[i];
+  const uint32_t am = D.amask[k];
+  const int nact = __popc(am);
+  const int Jk = nact * nb * nbr;
+  const int64_t p0 = D.pair_ptr[i];
+  const int64_t npl = D.pair_ptr[i + 1] - p0;
+  const double2 *Ak = A + size_t(blockIdx.x) * M.nRgp * L.jmax;
+  int TP = (kBT * kNR) / Jk;
+  TP = TP > L.tpmax ? L.tpmax : TP;
+  const double kT = kKbEVK * rp.T;
+  const double *ek = D.eps + size_t(k) * nb;
+  const double inv_stab = 1.0 / double(D.stab[k]);
+  double mscale[kMaxBranches];
+  for (int a = 0; a < nbr; ++a) mscale[a] = 1.0 / sqrt(M.mass[a / 3] / M.mass_mean);
+
+  for (int64_t t0 = 0; t0 < npl; t0 += TP) {
+    const int npt = int((npl - t0) < TP ? (npl - t0) : TP);
+    double2 acc[kNR];
+#pragma unroll
+    for (int r = 0; r < kNR; ++r) acc[r] = cmk(0, 0);
+    for (int r0 = 0; r0 < M.nRgp; r0 += L.rc) {
+      const int rc = (M.nRgp - r0) < L.rc ? (M.nRgp - r0) : L.rc;
+      __syncthreads();
+      for (int t = threadIdx.x; t < rc * Jk; t += kBT) {
+        int rr = t / Jk, j = t % Jk;
+        Ash[rr * L.jmax + j] = Ak[size_t(r0 + rr) * L.jmax + j];
+      }
+      for (int t = threadIdx.x; t < npt * L.rc; t += kBT) {
+        int p = t / L.rc, rr = t % L.rc;
+        double2 ph = cmk(0, 0);
+        if (rr < rc) {
+          int q = D.pair_q[p0 + t0 + p];
+          int b0, b1, b2;
+          D.qm.unflat(q, b0, b1, b2);
+          const int *R = M.Rgp + 3 * (r0 + rr);
+          ph = mesh_phase(D.qtab, D.qm, b0, b1, b2, R[0], R[1], R[2]);
+        }
+        phs[t] = ph;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < kNR; ++r) {
+        int o = threadIdx.x + kBT * r;
+        if (o < npt * Jk) {
+          int p = o / Jk, j = o - p * Jk;
+          const double2 *php = phs + p * L.rc;
+          for (int rr = 0; rr < rc; ++rr) cfma(acc[r], php[rr], Ash[rr * L.jmax + j]);
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kNR; ++r) {
+      int o = threadIdx.x + kBT * r;
+      if (o < npt * Jk) Bsh[o] = acc[r];
+    }
+    __syncthreads();
+
+    // ---- epilogue: one warp per pair
+    for (int p = wid; p < npt; p += kBT / 32) {
+      const int64_t pg = p0 + t0 + p;
+      const int q = D.pair_q[pg];
+      const int kp = kplusq_d(D, k, q);
+      const uint32_t an = D.amask[kp];
+      const int nactp = __popc(an);
+      const double2 *uq = D.u + size_t(q) * nbr * nbr;
+      const double *wq = D.w + size_t(q) * nbr;
+      const double2 *ckp = D.cvec + size_t(kp) * nb * nb;
+      const double *ekp = D.eps + size_t(kp) * nb;
+      const double2 *Bp = Bsh + p * Jk;
+      // Z[ml][n'][s] = sum_a B[ml][n'][a] u_{a s}(q) / sqrt(m_a / m_bar)
+      for (int t = lane; t < Jk; t += 32) {
+        int ml = t / (nb * nbr), np_ = (t / nbr) % nb, s = t % nbr;
+        double2 z = cmk(0, 0);
+        for (int a = 0; a < nbr; ++a)
+          cfma(z, Bp[(ml * nb + np_) * nbr + a], cscale(uq[a * nbr + s], mscale[a]));
+        Zs[t] = z;
+      }
+      __syncwarp();
+      // g[ml][nl][s] = sqrt(w_ref / w_s) sum_n' conj(c_{n'n}(k')) Z[ml][n'][s]
+      const int ntup = nact * nactp * nbr;
+      for (int t = lane; t < ntup; t += 32) {
+        int ml = t / (nactp * nbr), nl = (t / nbr) % nactp, s = t % nbr;
+        int n = nth_bit(an, nl);
+        double v = 0.0;
+        if (wq[s] > D.omega_min) {
+          double2 g = cmk(0, 0);
+          for (int np_ = 0; np_ < nb; ++np_) cfma_conj(g, ckp[np_ * nb + n], Zs[(ml * nb + np_) * nbr + s]);
+          v = cabs2(g) * (M.omega_ref / wq[s]);
+        }
+        g2s[t] = v;
+      }
+      __syncwarp();
+      // degenerate averages, occupations, delta; pass flags go to the (now free) Z scratch
+      int *flg = reinterpret_cast<int *>(Zs);
+      const uint8_t *gk = D.egrp + size_t(k) * nb * 2, *gkp = D.egrp + size_t(kp) * nb * 2;
+      const uint8_t *gq = D.pgrp + size_t(q) * nbr * 2;
+      for (int t = lane; t < ntup; t += 32) {
+        int ml = t / (nactp * nbr), nl = (t / nbr) % nactp, s = t % nbr;
+        int m = nth_bit(am, ml), n = nth_bit(an, nl);
+        double xp = 0.0, xm = 0.0;
+        if (wq[s] > D.omega_min) {
+          double sum = 0.0;
+          int cnt = 0;
+          for (int a = gk[2 * m]; a < gk[2 * m + 1]; ++a) {
+            if (!((am >> a) & 1u)) continue;
+            int al = __popc(am & ((1u << a) - 1u));
+            for (int b = gkp[2 * n]; b < gkp[2 * n + 1]; ++b) {
+              if (!((an >> b) & 1u)) continue;
+              int bl = __popc(an & ((1u << b) - 1u));
+              for (int c = gq[2 * s]; c < gq[2 * s + 1]; ++c) {
+                sum += g2s[(al * nactp + bl) * nbr + c];
+                ++cnt;
+              }
+            }
+          }
+          double g2 = sum / double(cnt);
+          double dxp = ekp[n] - ek[m] - wq[s];
+          double dxm = ekp[n] - ek[m] + wq[s];
+          double fm = fermi_d(ek[m], rp.mu, kT), fn = fermi_d(ekp[n], rp.mu, kT), nq = bose_d(wq[s], kT);
+          double occ = rp.inv_Nq_pref * g2 * fm * (1.0 - fn);
+          xp = occ * nq * gauss_d(dxp, rp.sigma, rp.cut);
+          xm = occ * (1.0 + nq) * gauss_d(dxm, rp.sigma, rp.cut);
+          Xps[t] = xp;
+          Xms[t] = xm;
+          flg[t] = (fabs(dxp) <= rp.cut ? 1 : 0) | (fabs(dxm) <= rp.cut ? 2 : 0);
+        } else {
+          Xps[t] = 0.0;
+          Xms[t] = 0.0;
+          flg[t] = 0;
+        }
+      }
+      __syncwarp();
+      // electron rows (k, m): entries ordered (n, s)
+      const int64_t pl = pg - p0;
+      for (int ml = 0; ml < nact; ++ml) {
+        const int m = nth_bit(am, ml);
+        int64_t base = escan[p0 * nb + m * npl + pl];
+        const int nit = nactp * nbr;
+        for (int c0 = 0; c0 < nit; c0 += 32) {
+          int t = c0 + lane;
+          int flag = 0, idx = 0;
+          if (t < nit) {
+            idx = ml * nit + t;
+            flag = flg[idx] != 0;
+          }
+          unsigned b = __ballot_sync(0xffffffffu, flag);
+          if (flag) {
+            int64_t pos = base + __popc(b & ((1u << lane) - 1u));
+            int nl = t / nbr, s = t % nbr;
+            e_kpns[pos] = pack_kpns(kp, nth_bit(an, nl), s);
+            e_X[pos] = cmk(Xps[idx], Xms[idx]);
+          }
+          base += __popc(b);
+        }
+      }
+      // phonon rows (q, s): entries ordered (m, n), absorption (+) processes only
+      const int64_t qb = D.qpair_ptr[q];
+      const int64_t npq = D.qpair_ptr[q + 1] - qb;
+      const int rk = D.pq_rank[pg];
+      for (int s = 0; s < nbr; ++s) {
+        if (!(wq[s] > D.omega_min)) continue;
+        int64_t base = phscan[qb * nbr + s * npq + rk];
+        const int nit = nact * nactp;
+        for (int c0 = 0; c0 < nit; c0 += 32) {
+          int t = c0 + lane;
+          int flag = 0, idx = 0;
+          if (t < nit) {
+            idx = t * nbr + s;
+            flag = (flg[idx] & 1) != 0;
+          }
+          unsigned b = __ballot_sync(0xffffffffu, flag);
+          if (flag) {
+            int64_t pos = base + __popc(b & ((1u << lane) - 1u));
+            int ml = t / nactp, nl = t % nactp;
+            ph_st[pos] = int(i) * nb + nth_bit(am, ml);
+            ph_kpn[pos] = pack_kpns(kp, nth_bit(an, nl), 0);
+            ph_Y[pos] = Xps[idx] * rp.y_scale * inv_stab;
+          }
+          base += __popc(b);
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+}  // namespace
+
+size_t stage_a_T_elems(const ModelDev &M) { return size_t(M.nRgp) * M.nb * M.nb * M.nbr; }
+size_t stage_a_A_elems(const ModelDev &M) { return size_t(M.nRgp) * M.nb * M.nb * M.nbr; }
+
+cudaError_t launch_rate_count(const ModelDev &M, const MeshDev &D, RateParams rp, int *cntE, int *cntPh,
+                              unsigned long long *n_tuples, cudaStream_t st) {
+  // counters: [0] tuples, [2] stage-B flops, [3] active states in irreducible rows
+  cudaError_t e = cudaMemsetAsync(n_tuples, 0, 4 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess || D.n_pairs == 0) return e;
+  EPHB_LAUNCH(k_rate_count, unsigned((D.n_pairs + 127) / 128), 128, 0, st, M, D, rp, cntE, cntPh, n_tuples);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_ptrs(const MeshDev &D, int nb, int nbr, const int64_t *escan, const int64_t *phscan,
+                            int64_t e_total, int64_t ph_total, int64_t *row_ptr, int64_t *ph_row_ptr,
+                            cudaStream_t st) {
+  int64_t n = (D.n_ibzw * nb > D.nq * nbr ? D.n_ibzw * nb : D.nq * nbr) + 1;
+  EPHB_LAUNCH(k_row_ptrs, unsigned((n + 255) / 256), 256, 0, st, D, nb, nbr, escan, phscan, e_total, ph_total, row_ptr,
+                                                        ph_row_ptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stage_a(const ModelDev &M, const MeshDev &D, int64_t i0, int64_t nkc, double2 *T, double2 *A,
+                           cudaStream_t st) {
+  const int64_t ncol = int64_t(M.nRgp) * M.nb * M.nb * M.nbr;
+  size_t smem = size_t(kAKT) * M.nRge * sizeof(double2);
+  cudaError_t e = cudaFuncSetAttribute(k_stage_a1, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  dim3 g1(unsigned((ncol + 255) / 256), unsigned((nkc + kAKT - 1) / kAKT));
+  EPHB_LAUNCH(k_stage_a1, g1, 256, smem, st, M, D, i0, nkc, T);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int64_t n2 = nkc * ncol;
+  EPHB_LAUNCH(k_stage_a2, unsigned((n2 + 255) / 256), 256, 0, st, M, D, i0, nkc, T, A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stage_b_rates(const ModelDev &M, const MeshDev &D, RateParams rp, int64_t i0, int64_t nkc,
+                                 const double2 *A, const int64_t *escan, const int64_t *phscan, uint32_t *e_kpns,
+                                 double2 *e_X, int *ph_st, uint32_t *ph_kpn, double *ph_Y, cudaStream_t st) {
+  StageBSmem L = stage_b_layout(M.nb, M.nbr);
+  cudaError_t e = cudaFuncSetAttribute(k_stage_b_rates, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L.total));
+  if (e != cudaSuccess) return e;
+  EPHB_LAUNCH(k_stage_b_rates, unsigned(nkc), kBT, L.total, st, M, D, rp, i0, A, escan, phscan, e_kpns, e_X, ph_st, ph_kpn,
+                                                       ph_Y);
+  return cudaGetLastError();
+}
+
+}  // namespace ephb
