@@ -290,6 +290,8 @@ ephb_status ephb_set_wannier_model(ephb_ctx *ctx, const ephb_model *m) {
   CK(cudaSetDevice(ctx->device));
   if (m->nb < 1 || m->nb > kMaxBands) return fail(ctx, EPHB_EINVAL, "nb must be in [1, 8]");
   if (m->nat < 1 || 3 * m->nat > kMaxBranches) return fail(ctx, EPHB_EINVAL, "nat must be in [1, 4]");
+  if (m->nb * m->nb * 3 * m->nat > 384)
+    return fail(ctx, EPHB_EINVAL, "nb^2 * 3 nat must not exceed 384 (vertex tile of one k point)");
   if (m->nRe < 1 || m->nRd < 1 || m->nRge < 1 || m->nRgp < 1) return fail(ctx, EPHB_EINVAL, "empty R list");
   if (m->nRge > 4096) return fail(ctx, EPHB_EINVAL, "nRge > 4096 not supported");
   if (m->nsym < 1 || m->nsym > kMaxSym) return fail(ctx, EPHB_EINVAL, "nsym must be in [1, 48]");

@@ -196,6 +196,7 @@ __host__ __device__ inline StageBSmem stage_b_layout(int nb, int nbr) {
   L.off_A = L.off_ph + size_t(L.tpmax) * L.rc * sizeof(double2);
   L.off_w = L.off_A + size_t(L.rc) * L.jmax * sizeof(double2);
   L.per_warp = size_t(L.jmax) * sizeof(double2) + 3 * size_t(nb) * nb * nbr * sizeof(double);
+  L.per_warp = (L.per_warp + 15) & ~size_t(15);   // every warp's double2 scratch stays 16-byte aligned
   L.total = L.off_w + (kBT / 32) * L.per_warp;
   return L;
 }

