@@ -113,7 +113,10 @@ struct ephb_ctx {
 
   // BTE
   DBuf<double> st_eps, st_vel, st_ff, st_wt, W_e, inv_ffW, I0, J0, I, J, I2, J2, Bt, W_ph, inv_nnW, F0, F, G, Btv,
-      partial, res, prev_in, prev_out, prev_tmp;
+      seg_part, epart, ppart, kpart, res, prev_in, prev_out, prev_tmp;
+  DBuf<int> nseg_row, seg_row;
+  DBuf<int64_t> seg_ptr, seg_begin;
+  int64_t nseg = 0;
   DBuf<uint32_t> kcrd;
   DBuf<int2> kinfo;
   DBuf<unsigned long long> ucount;
@@ -273,7 +276,9 @@ void ephb_destroy(ephb_ctx *ctx) {
   ctx->st_eps.release(); ctx->st_vel.release(); ctx->st_ff.release(); ctx->st_wt.release(); ctx->W_e.release();
   ctx->inv_ffW.release(); ctx->I0.release(); ctx->J0.release(); ctx->I.release(); ctx->J.release();
   ctx->I2.release(); ctx->J2.release(); ctx->Bt.release(); ctx->W_ph.release(); ctx->inv_nnW.release();
-  ctx->F0.release(); ctx->F.release(); ctx->G.release(); ctx->Btv.release(); ctx->partial.release();
+  ctx->F0.release(); ctx->F.release(); ctx->G.release(); ctx->Btv.release(); ctx->seg_part.release();
+  ctx->epart.release(); ctx->ppart.release(); ctx->kpart.release(); ctx->nseg_row.release();
+  ctx->seg_row.release(); ctx->seg_ptr.release(); ctx->seg_begin.release();
   ctx->res.release(); ctx->prev_in.release(); ctx->prev_out.release(); ctx->prev_tmp.release();
   ctx->kcrd.release(); ctx->kinfo.release(); ctx->ucount.release();
   if (ctx->host_res) cudaFreeHost(ctx->host_res);
@@ -600,7 +605,9 @@ ephb_status bte_setup(ephb_ctx *ctx) {
   CK(ctx->inv_nnW.ensure(nph));
   for (auto *b : {&ctx->F0, &ctx->F, &ctx->G}) CK(b->ensure(nph * 3));
   CK(ctx->Btv.ensure(nph * 6));
-  CK(ctx->partial.ensure(size_t(coeff_partials()) * 64));
+  CK(ctx->epart.ensure(size_t(coeff_partials()) * 36));
+  CK(ctx->ppart.ensure(size_t(coeff_partials()) * 18));
+  CK(ctx->kpart.ensure(size_t(coeff_partials()) * 9));
   for (auto *b : {&ctx->res, &ctx->prev_in, &ctx->prev_out, &ctx->prev_tmp}) CK(b->ensure(kResLen));
   MeshDev D = mesh_view(ctx);
   CK(launch_state_setup(M, D, ctx->T, ctx->mu, ctx->st_eps.p, ctx->st_vel.p, ctx->st_ff.p, ctx->st_wt.p,
@@ -609,15 +616,36 @@ ephb_status bte_setup(ephb_ctx *ctx) {
   CK(launch_rta_electron(B, ctx->W_e.p, ctx->inv_ffW.p, ctx->I0.p, ctx->J0.p, ctx->ucount.p + 1, st));
   CK(launch_ph_rowsum(B, ctx->Bt.p, st));
   CK(launch_rta_phonon(M, D, B, ctx->Bt.p, ctx->W_ph.p, ctx->inv_nnW.p, ctx->F0.p, st));
+  // segments of the electron entry stream for the sweep kernel
+  CK(ctx->nseg_row.ensure(nst));
+  CK(ctx->seg_ptr.ensure(nst + 1));
+  CK(ctx->scratch.ensure(scan_scratch_elems(nst)));
+  CK(launch_build_segments(B, ctx->nseg_row.p, ctx->seg_ptr.p, nullptr, nullptr, ctx->scratch.p, ctx->scratch.n,
+                           nullptr, ctx->nseg, st));
+  CK(ctx->seg_row.ensure(ctx->nseg));
+  CK(ctx->seg_begin.ensure(ctx->nseg));
+  CK(ctx->seg_part.ensure(size_t(ctx->nseg) * 6));
+  CK(launch_fill_segments(B, ctx->seg_ptr.p, ctx->seg_row.p, ctx->seg_begin.p, st));
   ctx->bte_ready = true;
   return EPHB_OK;
 }
 
-ephb_status coefficients_to_host(ephb_ctx *ctx, double *prev) {
+SweepSegs segs_view(ephb_ctx *c) {
+  SweepSegs S;
+  S.nseg = c->nseg;
+  S.seg_row = c->seg_row.p;
+  S.seg_begin = c->seg_begin.p;
+  S.seg_ptr = c->seg_ptr.p;
+  return S;
+}
+
+// Recompute the requested partial sums, finalise the tensors against `prev` and read `res`.
+ephb_status coefficients_to_host(ephb_ctx *ctx, double *prev, bool electron = true, bool phonon = true) {
   MeshDev D = mesh_view(ctx);
   BteDev B = bte_view(ctx);
-  CK(launch_coefficients(ctx->M, D, B, ctx->I.p, ctx->J.p, ctx->F.p, ctx->G.p, ctx->partial.p, coeff_partials(),
-                         ctx->res.p, prev, ctx->stream));
+  if (electron) CK(launch_e_partial(B, ctx->I.p, ctx->J.p, ctx->epart.p, ctx->stream));
+  if (phonon) CK(launch_ph_partial(D, B, ctx->F.p, ctx->G.p, ctx->ppart.p, ctx->stream));
+  CK(launch_coeff_final(ctx->M, B, ctx->epart.p, ctx->ppart.p, ctx->res.p, prev, ctx->stream));
   CK(cudaMemcpyAsync(ctx->host_res, ctx->res.p, kResLen * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return EPHB_OK;
@@ -662,19 +690,21 @@ ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb
   auto inner_loop = [&](int drag, bool &ok) -> ephb_status {
     ok = false;
     CK(cudaMemsetAsync(ctx->prev_in.p, 0, kResLen * sizeof(double), st));
-    ephb_status r = coefficients_to_host(ctx, ctx->prev_in.p);
+    ephb_status r = coefficients_to_host(ctx, ctx->prev_in.p, true, true);
     if (r != EPHB_OK) return r;
+    const SweepSegs S = segs_view(ctx);
     for (int it = 1; it <= o->max_inner; ++it) {
       CK(te.start(st));
-      CK(launch_e_sweep(M, D, B, ctx->kinfo.p, ctx->I0.p, ctx->J0.p, ctx->inv_ffW.p, ctx->I.p, ctx->J.p, ctx->F.p,
-                        ctx->G.p, drag, ctx->I2.p, ctx->J2.p, st));
+      CK(launch_e_sweep(M, D, B, S, ctx->kinfo.p, ctx->I0.p, ctx->J0.p, ctx->inv_ffW.p, ctx->I.p, ctx->J.p,
+                        ctx->F.p, ctx->G.p, drag, ctx->seg_part.p, ctx->I2.p, ctx->J2.p, ctx->epart.p, st));
       CK(te.stop(st));
       std::swap(ctx->I.p, ctx->I2.p);
       std::swap(ctx->J.p, ctx->J2.p);
       ++sweeps;
       ++inner_total;
       B = bte_view(ctx);
-      r = coefficients_to_host(ctx, ctx->prev_in.p);
+      // the sweep already wrote the electron partial sums; the phonon ones are unchanged
+      r = coefficients_to_host(ctx, ctx->prev_in.p, false, false);
       if (r != EPHB_OK) return r;
       CK(te.collect());
       if (ctx->host_res[72] < inner_tol) {
@@ -703,7 +733,7 @@ ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb
       if (s != EPHB_OK) return s;
       CK(tp.collect());
       if (o->ko_correction) {
-        CK(launch_ko(M, D, B, ctx->I.p, ctx->J.p, ctx->partial.p, coeff_partials(), ctx->res.p, st));
+        CK(launch_ko(M, D, B, ctx->I.p, ctx->J.p, ctx->kpart.p, ctx->res.p, st));
         CK(cudaMemcpyAsync(ctx->host_res + 74, ctx->res.p + 74, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         if (ctx->host_res[75] != 0.0) lambda = ctx->host_res[74];

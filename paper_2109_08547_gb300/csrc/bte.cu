@@ -130,65 +130,112 @@ __global__ void k_rta_phonon(ModelDev M, MeshDev D, BteDev B, const double *Bt, 
   for (int a = 0; a < 3; ++a) F0[t * 3 + a] = W > 0.0 ? (w / B.T) * D.vph[t * 3 + a] / W : 0.0;
 }
 
-// One warp per electron row (k,m):
-//   I_out = I0 + [sum (X+ + X-) S_k' I_<k'>n  (- F_qs X+ + F_-qs X-)] / (f(1-f) W)   (Eqs. dI^S, dI^D)
-// and the same for J with G.
-__global__ void __launch_bounds__(256) k_e_sweep(ModelDev M, MeshDev D, BteDev B, const int2 *__restrict__ kinfo,
-                                                 const double *__restrict__ I0, const double *__restrict__ J0,
-                                                 const double *__restrict__ inv_ffW, const double *__restrict__ I,
-                                                 const double *__restrict__ J, const double *__restrict__ F,
-                                                 const double *__restrict__ G, int drag, double *I_out,
-                                                 double *J_out) {
+// ---------------------------------------------------------------- electron sweep
+// The entry stream of the electron rows is cut into segments of at most kSeg entries
+// (never crossing a row).  One warp reduces one segment into 6 partial sums; a second
+// kernel adds a row's segment partials in segment order, so the result does not depend
+// on scheduling.  Per entry (Eqs. dI^S, dI^D):
+//   (X+ + X-) S_k' I_<k'>n  - F_qs X+ + F_-qs X-     and the same for J with G.
+constexpr int kSeg = 1024;
+constexpr int kUnroll = 4;
+
+__global__ void k_seg_count(int64_t nst, const int64_t *row_ptr, int *nseg) {
+  int64_t st = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (st >= nst) return;
+  int64_t len = row_ptr[st + 1] - row_ptr[st];
+  nseg[st] = int((len + kSeg - 1) / kSeg);
+}
+
+__global__ void k_seg_fill(int64_t nst, const int64_t *row_ptr, const int64_t *seg_ptr, int *seg_row,
+                           int64_t *seg_begin) {
+  int64_t st = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (st >= nst) return;
+  int64_t g = seg_ptr[st];
+  for (int64_t b = row_ptr[st]; b < row_ptr[st + 1]; b += kSeg, ++g) {
+    seg_row[g] = int(st);
+    seg_begin[g] = b;
+  }
+}
+
+template <bool SYM, bool DRAG>
+__global__ void __launch_bounds__(256) k_e_sweep_seg(ModelDev M, MeshDev D, BteDev B, SweepSegs S,
+                                                     const int2 *__restrict__ kinfo, const double *__restrict__ I,
+                                                     const double *__restrict__ J, const double *__restrict__ F,
+                                                     const double *__restrict__ G, double *__restrict__ part) {
   __shared__ double C[kMaxSym * 9];
-  for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) C[t] = M.sym_cart[t];
-  __syncthreads();
-  int64_t st = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (st >= B.nst) return;
-  const int nb = B.nb, nbr = B.nbr;
-  const int k = D.ibzw_list[st / nb];
-  const uint32_t kc = B.kcrd[k];
-  const int k0 = kc & 1023u, k1 = (kc >> 10) & 1023u, k2 = kc >> 20;
-  double aI[3] = {0, 0, 0}, aJ[3] = {0, 0, 0};
-  for (int64_t e = B.row_ptr[st] + lane; e < B.row_ptr[st + 1]; e += 32) {
-    uint32_t pk = B.e_kpns[e];
-    double2 X = B.e_X[e];
-    int kp = unpack_kp(pk), n = unpack_n(pk), s = unpack_s(pk);
-    int2 inf = kinfo[kp];
-    int64_t st2 = inf.x + n;
-    const double *Cs = C + 9 * inf.y;
-    double r[3];
-    double xs = X.x + X.y;
-    rot3(Cs, I + st2 * 3, r);
-    for (int a = 0; a < 3; ++a) aI[a] += xs * r[a];
-    rot3(Cs, J + st2 * 3, r);
-    for (int a = 0; a < 3; ++a) aJ[a] += xs * r[a];
-    if (drag) {
-      uint32_t pc = B.kcrd[kp];
-      int d0 = pmod(int(pc & 1023u) - k0, D.km.n[0]) / D.ratio[0];
-      int d1 = pmod(int((pc >> 10) & 1023u) - k1, D.km.n[1]) / D.ratio[1];
-      int d2 = pmod(int(pc >> 20) - k2, D.km.n[2]) / D.ratio[2];
-      int64_t q = D.qm.flat(d0, d1, d2);
-      int64_t mq = D.qm.flat(pmod(-d0, D.qm.n[0]), pmod(-d1, D.qm.n[1]), pmod(-d2, D.qm.n[2]));
-      const double *Fq = F + (q * nbr + s) * 3, *Fm = F + (mq * nbr + s) * 3;
-      const double *Gq = G + (q * nbr + s) * 3, *Gm = G + (mq * nbr + s) * 3;
-      for (int a = 0; a < 3; ++a) {
-        aI[a] += -Fq[a] * X.x + Fm[a] * X.y;
-        aJ[a] += -Gq[a] * X.x + Gm[a] * X.y;
+  if (SYM) {
+    for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) C[t] = M.sym_cart[t];
+    __syncthreads();
+  }
+  const int64_t g = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= S.nseg) return;
+  const int st = S.seg_row[g];
+  const int64_t b = S.seg_begin[g];
+  const int64_t rend = B.row_ptr[st + 1];
+  const int64_t e_end = b + kSeg < rend ? b + kSeg : rend;
+  const int nbr = B.nbr;
+  int k0 = 0, k1 = 0, k2 = 0;
+  if (DRAG) {
+    const uint32_t kc = B.kcrd[D.ibzw_list[st / B.nb]];
+    k0 = kc & 1023u;
+    k1 = (kc >> 10) & 1023u;
+    k2 = kc >> 20;
+  }
+  double a[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t e0 = b + lane; e0 < e_end; e0 += 32 * kUnroll) {
+    uint32_t pk[kUnroll];
+    double2 X[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t e = e0 + 32 * u;
+      pk[u] = e < e_end ? __ldcs(B.e_kpns + e) : 0u;
+      X[u] = e < e_end ? __ldcs(B.e_X + e) : make_double2(0.0, 0.0);
+    }
+    int2 inf[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) inf[u] = kinfo[unpack_kp(pk[u])];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      // inf.x < 0 would mean k' active but its representative not (a state within rounding
+      // of a window edge); such a partner contributes nothing rather than reading out of range
+      if (e0 + 32 * u >= e_end || inf[u].x < 0) continue;
+      const int64_t st2 = inf[u].x + unpack_n(pk[u]);
+      const double xs = X[u].x + X[u].y;
+      double vi[3] = {I[st2 * 3], I[st2 * 3 + 1], I[st2 * 3 + 2]};
+      double vj[3] = {J[st2 * 3], J[st2 * 3 + 1], J[st2 * 3 + 2]};
+      if (SYM) {
+        double r[3];
+        const double *Cs = C + 9 * inf[u].y;
+        rot3(Cs, vi, r);
+        vi[0] = r[0]; vi[1] = r[1]; vi[2] = r[2];
+        rot3(Cs, vj, r);
+        vj[0] = r[0]; vj[1] = r[1]; vj[2] = r[2];
+      }
+      for (int c = 0; c < 3; ++c) {
+        a[c] += xs * vi[c];
+        a[3 + c] += xs * vj[c];
+      }
+      if (DRAG) {
+        const int kp = unpack_kp(pk[u]), s = unpack_s(pk[u]);
+        const uint32_t pc = B.kcrd[kp];
+        const int d0 = pmod(int(pc & 1023u) - k0, D.km.n[0]) / D.ratio[0];
+        const int d1 = pmod(int((pc >> 10) & 1023u) - k1, D.km.n[1]) / D.ratio[1];
+        const int d2 = pmod(int(pc >> 20) - k2, D.km.n[2]) / D.ratio[2];
+        const int64_t q = D.qm.flat(d0, d1, d2);
+        const int64_t mq = D.qm.flat(pmod(-d0, D.qm.n[0]), pmod(-d1, D.qm.n[1]), pmod(-d2, D.qm.n[2]));
+        const double *Fq = F + (q * nbr + s) * 3, *Fm = F + (mq * nbr + s) * 3;
+        const double *Gq = G + (q * nbr + s) * 3, *Gm = G + (mq * nbr + s) * 3;
+        for (int c = 0; c < 3; ++c) {
+          a[c] += -Fq[c] * X[u].x + Fm[c] * X[u].y;
+          a[3 + c] += -Gq[c] * X[u].x + Gm[c] * X[u].y;
+        }
       }
     }
   }
-  for (int a = 0; a < 3; ++a) {
-    aI[a] = warp_sum(aI[a]);
-    aJ[a] = warp_sum(aJ[a]);
-  }
-  if (lane == 0) {
-    double c = inv_ffW[st];
-    for (int a = 0; a < 3; ++a) {
-      I_out[st * 3 + a] = I0[st * 3 + a] + aI[a] * c;
-      J_out[st * 3 + a] = J0[st * 3 + a] + aJ[a] * c;
-    }
-  }
+  for (int c = 0; c < 6; ++c) a[c] = warp_sum(a[c]);
+  if (lane == 0)
+    for (int c = 0; c < 6; ++c) part[g * 6 + c] = a[c];
 }
 
 // One warp per phonon row (q,s): Btv = sum Y/|stab| (S_k' I_<k'>n - I_km), fields I and J.
@@ -208,12 +255,12 @@ __global__ void __launch_bounds__(256) k_ph_sweep(ModelDev M, MeshDev D, BteDev 
     double y = B.ph_Y[e];
     int kp = unpack_kp(pk), n = unpack_n(pk);
     int2 inf = kinfo[kp];
-    int64_t st2 = inf.x + n;
-    const double *Cs = C + 9 * inf.y;
-    double r[3];
-    rot3(Cs, I + st2 * 3, r);
+    double r[3] = {0.0, 0.0, 0.0};
+    const double *Cs = C + 9 * (inf.y > 0 ? inf.y : 0);
+    const int64_t st2 = inf.x + n;
+    if (inf.x >= 0) rot3(Cs, I + st2 * 3, r);   // inf.x < 0: see the electron sweep
     for (int a = 0; a < 3; ++a) aI[a] += y * (r[a] - I[int64_t(st) * 3 + a]);
-    rot3(Cs, J + st2 * 3, r);
+    if (inf.x >= 0) rot3(Cs, J + st2 * 3, r);
     for (int a = 0; a < 3; ++a) aJ[a] += y * (r[a] - J[int64_t(st) * 3 + a]);
   }
   for (int a = 0; a < 3; ++a) {
@@ -260,12 +307,13 @@ __global__ void k_ph_update(ModelDev M, MeshDev D, BteDev B, const double *Btv, 
 }
 
 // ---------------------------------------------------------------- coefficient reductions
-constexpr int kNPart = 304;     // fixed number of partial-sum blocks (2 per SM)
+constexpr int kNPart = 152;     // fixed number of partial-sum blocks (one per SM)
 constexpr int kCT = 256;
-constexpr int kNAcc = 54;       // 4 electron + 2 phonon 3x3 sums
+constexpr int kNE = 36;         // electron sums: sigma, sigmaS, alpha_el, kappa0_el (3x3 each)
+constexpr int kNP = 18;         // phonon sums: alpha_ph, kappa_ph
 
 __device__ inline void block_reduce_store(double *acc, int nacc, double *out) {
-  __shared__ double wsum[kCT / 32][kNAcc];
+  __shared__ double wsum[kCT / 32][kNE];
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int j = 0; j < nacc; ++j) {
     double v = warp_sum(acc[j]);
@@ -279,26 +327,63 @@ __device__ inline void block_reduce_store(double *acc, int nacc, double *out) {
   }
 }
 
-__global__ void __launch_bounds__(kCT) k_coeff_partial(MeshDev D, BteDev B, const double *I, const double *J,
-                                                       const double *F, const double *G, double *partial) {
-  double acc[kNAcc];
-  for (int j = 0; j < kNAcc; ++j) acc[j] = 0.0;
+// f(1-f)/|stab| weighted v (x) {J, -I} and (eps-mu) v (x) {J, -I} of one state
+__device__ inline void e_tensor_acc(const BteDev &B, int64_t st, const double *Is, const double *Js, double *acc) {
+  const double wff = B.st_wt[st] * B.st_ff[st];
+  if (wff == 0.0) return;
+  const double d = B.st_eps[st] - B.mu;
+  const double *v = B.st_vel + st * 3;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double vj = wff * v[a] * Js[b];
+      double vi = -wff * v[a] * Is[b];
+      acc[a * 3 + b] += vj;
+      acc[9 + a * 3 + b] += vi;
+      acc[18 + a * 3 + b] += d * vj;
+      acc[27 + a * 3 + b] += d * vi;
+    }
+}
+
+// I = I0 + (sum of the row's segment partials) / (f(1-f) W), same for J; plus the electron
+// coefficient partial sums of the new responses.
+__global__ void __launch_bounds__(kCT) k_e_finalize(BteDev B, SweepSegs S, const double *__restrict__ part,
+                                                    const double *__restrict__ I0, const double *__restrict__ J0,
+                                                    const double *__restrict__ inv_ffW, double *I_out,
+                                                    double *J_out, double *epart) {
+  double acc[kNE];
+  for (int j = 0; j < kNE; ++j) acc[j] = 0.0;
   const int64_t stride = int64_t(gridDim.x) * kCT;
   for (int64_t st = blockIdx.x * int64_t(kCT) + threadIdx.x; st < B.nst; st += stride) {
-    double wff = B.st_wt[st] * B.st_ff[st];
-    if (wff == 0.0) continue;
-    double d = B.st_eps[st] - B.mu;
-    const double *v = B.st_vel + st * 3;
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) {
-        double vj = wff * v[a] * J[st * 3 + b];
-        double vi = -wff * v[a] * I[st * 3 + b];
-        acc[a * 3 + b] += vj;
-        acc[9 + a * 3 + b] += vi;
-        acc[18 + a * 3 + b] += d * vj;
-        acc[27 + a * 3 + b] += d * vi;
-      }
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t g = S.seg_ptr[st]; g < S.seg_ptr[st + 1]; ++g)
+      for (int c = 0; c < 6; ++c) s[c] += part[g * 6 + c];
+    const double c0 = inv_ffW[st];
+    double In[3], Jn[3];
+    for (int c = 0; c < 3; ++c) {
+      In[c] = I0[st * 3 + c] + s[c] * c0;
+      Jn[c] = J0[st * 3 + c] + s[3 + c] * c0;
+      I_out[st * 3 + c] = In[c];
+      J_out[st * 3 + c] = Jn[c];
+    }
+    e_tensor_acc(B, st, In, Jn, acc);
   }
+  block_reduce_store(acc, kNE, epart + size_t(blockIdx.x) * kNE);
+}
+
+__global__ void __launch_bounds__(kCT) k_e_partial(BteDev B, const double *I, const double *J, double *epart) {
+  double acc[kNE];
+  for (int j = 0; j < kNE; ++j) acc[j] = 0.0;
+  const int64_t stride = int64_t(gridDim.x) * kCT;
+  for (int64_t st = blockIdx.x * int64_t(kCT) + threadIdx.x; st < B.nst; st += stride)
+    e_tensor_acc(B, st, I + st * 3, J + st * 3, acc);
+  block_reduce_store(acc, kNE, epart + size_t(blockIdx.x) * kNE);
+}
+
+__global__ void __launch_bounds__(kCT) k_ph_partial(MeshDev D, BteDev B, const double *F, const double *G,
+                                                    double *ppart) {
+  double acc[kNP];
+  for (int j = 0; j < kNP; ++j) acc[j] = 0.0;
+  const int64_t stride = int64_t(gridDim.x) * kCT;
   const double kT = kKbEVK * B.T;
   for (int64_t t = blockIdx.x * int64_t(kCT) + threadIdx.x; t < B.nq * B.nbr; t += stride) {
     double w = D.w[t];
@@ -308,11 +393,11 @@ __global__ void __launch_bounds__(kCT) k_coeff_partial(MeshDev D, BteDev B, cons
     const double *v = D.vph + t * 3;
     for (int a = 0; a < 3; ++a)
       for (int b = 0; b < 3; ++b) {
-        acc[36 + a * 3 + b] += -wt * v[a] * G[t * 3 + b];
-        acc[45 + a * 3 + b] += wt * v[a] * F[t * 3 + b];
+        acc[a * 3 + b] += -wt * v[a] * G[t * 3 + b];
+        acc[9 + a * 3 + b] += wt * v[a] * F[t * 3 + b];
       }
   }
-  block_reduce_store(acc, kNAcc, partial + size_t(blockIdx.x) * kNAcc);
+  block_reduce_store(acc, kNP, ppart + size_t(blockIdx.x) * kNP);
 }
 
 __device__ inline void symmetrise(const double *C, int nsym, const double *M, double *out) {
@@ -343,15 +428,24 @@ __device__ inline double rel_change(const double *a, const double *b) {
   return sqrt(d) / sqrt(n);
 }
 
+// column sums of the partial-sum blocks, one warp per column (fixed order)
+__device__ inline void sum_columns(const double *epart, const double *ppart, int npart, double *Ms) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = wid; j < kNE + kNP; j += nw) {
+    double s = 0.0;
+    for (int b = lane; b < npart; b += 32)
+      s += j < kNE ? epart[size_t(b) * kNE + j] : ppart[size_t(b) * kNP + (j - kNE)];
+    s = warp_sum(s);
+    if (lane == 0) Ms[j] = s;
+  }
+}
+
 // res: [0] sigma [9] sigmaS [18] alpha_el [27] kappa0_el [36] alpha_ph [45] kappa_ph [54] S [63] kappa_el
 //      [72] residual_e [73] residual_all
-__global__ void k_coeff_final(ModelDev M, BteDev B, const double *partial, int npart, double *res, double *prev) {
-  __shared__ double Ms[kNAcc];
-  if (threadIdx.x < kNAcc) {
-    double s = 0.0;
-    for (int b = 0; b < npart; ++b) s += partial[size_t(b) * kNAcc + threadIdx.x];
-    Ms[threadIdx.x] = s;
-  }
+__global__ void k_coeff_final(ModelDev M, BteDev B, const double *epart, const double *ppart, int npart,
+                              double *res, double *prev) {
+  __shared__ double Ms[kNE + kNP];
+  sum_columns(epart, ppart, npart, Ms);
   __syncthreads();
   if (threadIdx.x != 0) return;
   double t[9];
@@ -401,7 +495,7 @@ __global__ void k_coeff_final(ModelDev M, BteDev B, const double *partial, int n
 }
 
 // Kelvin-Onsager step: B = sigmaS[I_drag], A = alpha_ph / T, lambda = <A,B>/<B,B>
-__global__ void __launch_bounds__(kCT) k_ko_partial(BteDev B, const double *I, const double *J, double *partial) {
+__global__ void __launch_bounds__(kCT) k_ko_partial(BteDev B, const double *I, const double *J, double *kpart) {
   double acc[9];
   for (int j = 0; j < 9; ++j) acc[j] = 0.0;
   const int64_t stride = int64_t(gridDim.x) * kCT;
@@ -413,15 +507,17 @@ __global__ void __launch_bounds__(kCT) k_ko_partial(BteDev B, const double *I, c
     for (int a = 0; a < 3; ++a)
       for (int b = 0; b < 3; ++b) acc[a * 3 + b] += -wff * v[a] * (I[st * 3 + b] - d * J[st * 3 + b]);
   }
-  block_reduce_store(acc, 9, partial + size_t(blockIdx.x) * kNAcc);
+  block_reduce_store(acc, 9, kpart + size_t(blockIdx.x) * 9);
 }
 
-__global__ void k_ko_final(ModelDev M, BteDev B, const double *partial, int npart, double *res) {
+__global__ void k_ko_final(ModelDev M, BteDev B, const double *kpart, int npart, double *res) {
   __shared__ double Ms[9];
-  if (threadIdx.x < 9) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = wid; j < 9; j += nw) {
     double s = 0.0;
-    for (int b = 0; b < npart; ++b) s += partial[size_t(b) * kNAcc + threadIdx.x];
-    Ms[threadIdx.x] = s;
+    for (int b = lane; b < npart; b += 32) s += kpart[size_t(b) * 9 + j];
+    s = warp_sum(s);
+    if (lane == 0) Ms[j] = s;
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
@@ -456,6 +552,7 @@ __global__ void k_ko_apply(BteDev B, double *I, const double *J, const double *r
 }  // namespace
 
 int coeff_partials() { return kNPart; }
+int sweep_segment_len() { return kSeg; }
 
 cudaError_t launch_state_setup(const ModelDev &M, const MeshDev &D, double T, double mu, double *st_eps,
                                double *st_vel, double *st_ff, double *st_wt, uint32_t *kcrd, int2 *kinfo,
@@ -484,13 +581,52 @@ cudaError_t launch_rta_phonon(const ModelDev &M, const MeshDev &D, const BteDev 
   return cudaGetLastError();
 }
 
-cudaError_t launch_e_sweep(const ModelDev &M, const MeshDev &D, const BteDev &B, const int2 *kinfo, const double *I0,
-                           const double *J0, const double *inv_ffW, const double *I, const double *J,
-                           const double *F, const double *G, int drag, double *I_out, double *J_out,
-                           cudaStream_t st) {
+
+cudaError_t launch_build_segments(const BteDev &B, int *nseg_row, int64_t *seg_ptr, int *seg_row,
+                                  int64_t *seg_begin, int64_t *scratch, int64_t scratch_elems, int64_t *total_dev,
+                                  int64_t &nseg_host, cudaStream_t st) {
+  if (B.nst == 0) {
+    nseg_host = 0;
+    return cudaMemsetAsync(seg_ptr, 0, sizeof(int64_t), st);
+  }
+  unsigned grid = unsigned((B.nst + 255) / 256);
+  EPHB_LAUNCH(k_seg_count, grid, 256, 0, st, B.nst, B.row_ptr, nseg_row);
+  cudaError_t e = exclusive_scan<int>(nseg_row, seg_ptr, B.nst, seg_ptr + B.nst, scratch, scratch_elems, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(&nseg_host, seg_ptr + B.nst, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  (void)total_dev;
+  return cudaSuccess;
+}
+
+cudaError_t launch_fill_segments(const BteDev &B, const int64_t *seg_ptr, int *seg_row, int64_t *seg_begin,
+                                 cudaStream_t st) {
   if (B.nst == 0) return cudaSuccess;
-  EPHB_LAUNCH(k_e_sweep, unsigned((B.nst * 32 + 255) / 256), 256, 0, st, M, D, B, kinfo, I0, J0, inv_ffW, I, J, F, G, drag,
-                                                                 I_out, J_out);
+  EPHB_LAUNCH(k_seg_fill, unsigned((B.nst + 255) / 256), 256, 0, st, B.nst, B.row_ptr, seg_ptr, seg_row, seg_begin);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_e_sweep(const ModelDev &M, const MeshDev &D, const BteDev &B, const SweepSegs &S,
+                           const int2 *kinfo, const double *I0, const double *J0, const double *inv_ffW,
+                           const double *I, const double *J, const double *F, const double *G, int drag,
+                           double *part, double *I_out, double *J_out, double *epart, cudaStream_t st) {
+  if (S.nseg > 0) {
+    unsigned grid = unsigned((S.nseg * 32 + 255) / 256);
+    const bool sym = M.nsym > 1;
+    if (sym && drag)
+      EPHB_LAUNCH((k_e_sweep_seg<true, true>), grid, 256, 0, st, M, D, B, S, kinfo, I, J, F, G, part);
+    else if (sym)
+      EPHB_LAUNCH((k_e_sweep_seg<true, false>), grid, 256, 0, st, M, D, B, S, kinfo, I, J, F, G, part);
+    else if (drag)
+      EPHB_LAUNCH((k_e_sweep_seg<false, true>), grid, 256, 0, st, M, D, B, S, kinfo, I, J, F, G, part);
+    else
+      EPHB_LAUNCH((k_e_sweep_seg<false, false>), grid, 256, 0, st, M, D, B, S, kinfo, I, J, F, G, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  EPHB_LAUNCH(k_e_finalize, kNPart, kCT, 0, st, B, S, part, I0, J0, inv_ffW, I_out, J_out, epart);
   return cudaGetLastError();
 }
 
@@ -506,22 +642,31 @@ cudaError_t launch_ph_update(const ModelDev &M, const MeshDev &D, const BteDev &
   return cudaGetLastError();
 }
 
-cudaError_t launch_coefficients(const ModelDev &M, const MeshDev &D, const BteDev &B, const double *I,
-                                const double *J, const double *F, const double *G, double *partial,
-                                int npartial, double *res, double *prev, cudaStream_t st) {
-  EPHB_LAUNCH(k_coeff_partial, npartial, kCT, 0, st, D, B, I, J, F, G, partial);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  EPHB_LAUNCH(k_coeff_final, 1, 64, 0, st, M, B, partial, npartial, res, prev);
+
+cudaError_t launch_e_partial(const BteDev &B, const double *I, const double *J, double *epart, cudaStream_t st) {
+  EPHB_LAUNCH(k_e_partial, kNPart, kCT, 0, st, B, I, J, epart);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ph_partial(const MeshDev &D, const BteDev &B, const double *F, const double *G, double *ppart,
+                              cudaStream_t st) {
+  EPHB_LAUNCH(k_ph_partial, kNPart, kCT, 0, st, D, B, F, G, ppart);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coeff_final(const ModelDev &M, const BteDev &B, const double *epart, const double *ppart,
+                               double *res, double *prev, cudaStream_t st) {
+  EPHB_LAUNCH(k_coeff_final, 1, 512, 0, st, M, B, epart, ppart, kNPart, res, prev);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ko(const ModelDev &M, const MeshDev &D, const BteDev &B, double *I, const double *J,
-                      double *partial, int npartial, double *res, cudaStream_t st) {
-  EPHB_LAUNCH(k_ko_partial, npartial, kCT, 0, st, B, I, J, partial);
+                      double *kpart, double *res, cudaStream_t st) {
+  (void)D;
+  EPHB_LAUNCH(k_ko_partial, kNPart, kCT, 0, st, B, I, J, kpart);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  EPHB_LAUNCH(k_ko_final, 1, 32, 0, st, M, B, partial, npartial, res);
+  EPHB_LAUNCH(k_ko_final, 1, 288, 0, st, M, B, kpart, kNPart, res);
   e = cudaGetLastError();
   if (e != cudaSuccess || B.nst == 0) return e;
   EPHB_LAUNCH(k_ko_apply, unsigned((B.nst * 3 + 255) / 256), 256, 0, st, B, I, J, res);

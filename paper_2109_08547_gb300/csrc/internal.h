@@ -119,23 +119,41 @@ cudaError_t launch_rta_electron(const BteDev &B, double *W_e, double *inv_ffW, d
 cudaError_t launch_ph_rowsum(const BteDev &B, double *Bt, cudaStream_t st);
 cudaError_t launch_rta_phonon(const ModelDev &M, const MeshDev &D, const BteDev &B, const double *Bt, double *W_ph,
                               double *inv_nnW, double *F0, cudaStream_t st);
-cudaError_t launch_e_sweep(const ModelDev &M, const MeshDev &D, const BteDev &B, const int2 *kinfo, const double *I0,
-                           const double *J0, const double *inv_ffW, const double *I, const double *J,
-                           const double *F, const double *G, int drag, double *I_out, double *J_out,
-                           cudaStream_t st);
+// Segments of the electron entry stream (at most sweep_segment_len() entries, within one row).
+struct SweepSegs {
+  int64_t nseg = 0;
+  const int *seg_row = nullptr;       // [nseg] state (row) of the segment
+  const int64_t *seg_begin = nullptr; // [nseg] first entry
+  const int64_t *seg_ptr = nullptr;   // [nst+1] first segment of each row
+};
+int sweep_segment_len();
+cudaError_t launch_build_segments(const BteDev &B, int *nseg_row, int64_t *seg_ptr, int *seg_row,
+                                  int64_t *seg_begin, int64_t *scratch, int64_t scratch_elems, int64_t *total_dev,
+                                  int64_t &nseg_host, cudaStream_t st);
+cudaError_t launch_fill_segments(const BteDev &B, const int64_t *seg_ptr, int *seg_row, int64_t *seg_begin,
+                                 cudaStream_t st);
+// One electron sweep: segment partials, then per-row finalisation I = I0 + ..., which also
+// writes the electron coefficient partial sums (epart) of the new responses.
+cudaError_t launch_e_sweep(const ModelDev &M, const MeshDev &D, const BteDev &B, const SweepSegs &S,
+                           const int2 *kinfo, const double *I0, const double *J0, const double *inv_ffW,
+                           const double *I, const double *J, const double *F, const double *G, int drag,
+                           double *part, double *I_out, double *J_out, double *epart, cudaStream_t st);
 cudaError_t launch_ph_sweep(const ModelDev &M, const MeshDev &D, const BteDev &B, const int2 *kinfo, const double *I,
                             const double *J, double *Btv, cudaStream_t st);
 cudaError_t launch_ph_update(const ModelDev &M, const MeshDev &D, const BteDev &B, const double *Btv,
                              const double *F0, const double *inv_nnW, double *F, double *G, cudaStream_t st);
-// Coefficient tensors: partial sums then a single-block finalisation into `res`.
+// Coefficient tensors: fixed-count partial sums (electron: 36 per block, phonon: 18 per
+// block) and a single-block finalisation into `res`.
 //   res layout: [0] sigma [9] sigmaS [18] alpha_el [27] kappa0_el [36] alpha_ph [45] kappa_ph
 //               [54] S [63] kappa_el [72] residual_e [73] residual_all [74] lambda [75] ko_valid
 constexpr int kResLen = 80;
-cudaError_t launch_coefficients(const ModelDev &M, const MeshDev &D, const BteDev &B, const double *I,
-                                const double *J, const double *F, const double *G, double *partial,
-                                int npartial, double *res, double *prev, cudaStream_t st);
-cudaError_t launch_ko(const ModelDev &M, const MeshDev &D, const BteDev &B, double *I, const double *J,
-                      double *partial, int npartial, double *res, cudaStream_t st);
 int coeff_partials();
+cudaError_t launch_e_partial(const BteDev &B, const double *I, const double *J, double *epart, cudaStream_t st);
+cudaError_t launch_ph_partial(const MeshDev &D, const BteDev &B, const double *F, const double *G, double *ppart,
+                              cudaStream_t st);
+cudaError_t launch_coeff_final(const ModelDev &M, const BteDev &B, const double *epart, const double *ppart,
+                               double *res, double *prev, cudaStream_t st);
+cudaError_t launch_ko(const ModelDev &M, const MeshDev &D, const BteDev &B, double *I, const double *J,
+                      double *kpart, double *res, cudaStream_t st);
 
 }  // namespace ephb
