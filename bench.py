@@ -29,7 +29,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "transition rates/s and s to converged σ,S,κ at 1e-6 rel: mixed+batched vs FP64"
 UNIT = "transition rates/s"
-FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (recipe table); no measured FP64 peak is provided
+# FP64 FMA throughput of the GB300s, measured with `bench.py --fp64-peak`
+# (profiles/fp64_peak_gb300.txt); the nominal figure is 1.25 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.188
 
 
 def parse():
@@ -41,7 +43,56 @@ def parse():
     p.add_argument("--n", type=int, default=24, help="k and q mesh size per dimension")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--fp64-peak", action="store_true",
+                   help="measure FP64 and FP32 FMA throughput with a small probe kernel and exit")
     return p.parse_args()
+
+
+FMA_PROBE = r"""
+#include <cstdio>
+#include <cuda_runtime.h>
+template <typename T> __global__ void probe(T *out, int iters, T a, T b) {
+  T x[8];
+  for (int j = 0; j < 8; ++j) x[j] = T(threadIdx.x) * T(1e-3) + T(j);
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = x[j] * a + b;
+  T s = 0; for (int j = 0; j < 8; ++j) s += x[j];
+  if (s == T(12345.678)) out[0] = s;
+}
+template <typename T> double run(int iters) {
+  T *d; cudaMalloc(&d, sizeof(T));
+  int sms; cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  int grid = sms * 8, block = 256;
+  cudaEvent_t a, b; cudaEventCreate(&a); cudaEventCreate(&b);
+  probe<T><<<grid, block>>>(d, iters, T(0.999999), T(1e-7));
+  float best = 1e30f;
+  for (int r = 0; r < 5; ++r) {
+    cudaEventRecord(a); probe<T><<<grid, block>>>(d, iters, T(0.999999), T(1e-7)); cudaEventRecord(b);
+    cudaEventSynchronize(b); float ms; cudaEventElapsedTime(&ms, a, b); best = ms < best ? ms : best;
+  }
+  cudaFree(d);
+  return 2.0 * 8 * iters * double(grid) * block / (best * 1e-3) / 1e12;
+}
+int main() {
+  printf("fp64_fma_tflops %.4f\nfp32_fma_tflops %.4f\n", run<double>(4096), run<float>(16384));
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+"""
+
+
+def fp64_peak():
+    """Compile and run the FMA probe (nvcc, sm_103a); prints TFLOP/s for FP64 and FP32."""
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "probe.cu")
+        exe = os.path.join(d, "probe")
+        with open(src, "w") as f:
+            f.write(FMA_PROBE)
+        subprocess.run(["nvcc", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-o", exe, src], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    vals = dict(line.split() for line in out.strip().splitlines())
+    print(json.dumps({k: float(v) for k, v in vals.items()}))
 
 
 def dist_env():
@@ -195,6 +246,9 @@ def reference_arm(args):
 
 def main():
     args = parse()
+    if args.fp64_peak:
+        fp64_peak()
+        return
     if args.impl == "reference":
         reference_arm(args)
         return
@@ -262,7 +316,7 @@ def main():
         roof = {"kernel": "k_stage_b_rates (R_ph contraction + rotations + rates, FP64)", "bound": "alu",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS,
-                "peak_source": "nominal GB300 FP64 rate from the profiling recipe table (no measured FP64 peak)",
+                "peak_source": "measured FP64 FMA rate (bench.py --fp64-peak, profiles/fp64_peak_gb300.txt)",
                 "traffic": (tr[0] * r0.rates["n_pairs"]) if tr else None,
                 "ms_per_step": ms_b, "share_of_step": ms_b / (1e3 * el_max / args.steps)}
     else:
