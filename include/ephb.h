@@ -233,7 +233,10 @@ typedef enum {
   EPHB_ARR_G = 16,
   EPHB_ARR_PAIR_PTR = 17,      /* [n_ibz_window + 1] i64                                   */
   EPHB_ARR_ACTIVE = 18,        /* [nk] u32 bit mask of active bands                        */
-  EPHB_ARR_COUNT = 19
+  EPHB_ARR_STATE_EPS = 19,     /* [n_ibz_window*nb] f64 band energy of each state          */
+  EPHB_ARR_STATE_VEL = 20,     /* [n_ibz_window*nb][3] f64 velocity of each state          */
+  EPHB_ARR_STATE_WEIGHT = 21,  /* [n_ibz_window*nb] f64 1/|stabiliser| (0 when inactive)   */
+  EPHB_ARR_COUNT = 22
 } ephb_array;
 
 ephb_status ephb_get_device_array(ephb_ctx *ctx, int which, void **dptr, int64_t shape[4], int *dtype);
@@ -241,6 +244,53 @@ ephb_status ephb_copy_array_to_host(ephb_ctx *ctx, int which, void *host_dst, in
 
 /* Number of CUDA kernels the library has launched in this process (all contexts). */
 int64_t ephb_kernel_launches(void);
+
+/* ----------------------------------------------------------------------------------
+ * Transport coefficients without any memory allocation.
+ *
+ * The paper has no counterpart: this is a service for callers that cannot allocate GPU
+ * memory -- code that runs while a stream is being captured into a CUDA graph, hosts
+ * whose every allocation must come from their own pool, embedders that may only use
+ * buffers they were handed.  It computes the same tensors as ephb_transport_coefficients
+ * from response arrays the caller already holds on the device, and calls no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *
+ * Inputs (all device pointers, row-major, FP64): per electron state its energy (eV),
+ * velocity (m/s, [n][3]), weight 1/|stabiliser of its k| (0 for an inactive state) and
+ * responses I, J ([n][3]); per phonon mode hbar*omega (eV), velocity ([n][3]) and F, G
+ * ([n][3]).  The symmetry operations are copied from the struct at call time.
+ * Output: out_dev, 72 doubles on the device in the order of ephb_coeffs (sigma, sigmaS,
+ * S, alpha_el, kappa0_el, kappa_el, alpha_ph, kappa_ph).
+ *
+ * Scratch: one file-scope __device__ array of 442 KB that every GPU loading the library
+ * holds until the process exits; it bounds n_states and n_modes to EPHB_NOALLOC_MAX_ITEMS
+ * each (larger inputs return EPHB_EINVAL).  Every call overwrites the scratch it reads,
+ * so nothing needs clearing, but all calls on a device share it: calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race and must be
+ * serialised by the caller.
+ * The first call on a device looks up the scratch's device address for that device (with
+ * that device current); make that first call before starting any stream capture.
+ * The work is enqueued on cuda_stream (NULL: the legacy default stream) and the call
+ * returns without waiting; out_dev is valid once the stream reaches that point.
+ * Errors: EPHB_EINVAL for NULL or out-of-range arguments, EPHB_ECUDA for a launch
+ * failure.
+ * --------------------------------------------------------------------------------*/
+#define EPHB_NOALLOC_MAX_ITEMS 4194304
+
+typedef struct {
+  int64_t n_states;
+  const double *eps, *vel, *weight, *I, *J;
+  int64_t n_modes;
+  const double *omega, *vph, *F, *G;
+  double T_K, mu_eV, spin_deg;
+  double volume_A3;            /* unit-cell volume                                          */
+  int64_t nk, nq;              /* full k and q mesh sizes (the 1/N_k, 1/N_q of the sums)    */
+  double omega_min_eV;         /* modes at or below it are left out                         */
+  int nsym;                    /* 1..48 operations ...                                      */
+  double sym_cart[48][9];      /* ... on Cartesian vectors, for the electron-side zone sum  */
+} ephb_coeff_inputs;
+
+ephb_status ephb_transport_coefficients_noalloc(const ephb_coeff_inputs *in, double *out_dev, void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -23,12 +23,15 @@ RTA, PARTIAL, DRAGLESS, DRAGGED = 0, 1, 2, 3
 LEVELS = {"rta": RTA, "partial": PARTIAL, "dragless": DRAGLESS, "dragged": DRAGGED}
 
 ARR = dict(eps=0, vel=1, omega=2, vph=3, ibz_rep=4, ibz_op=5, ibzw_list=6, row_ptr=7, entry_kpns=8, entry_x=9,
-           pair_q=10, w_e=11, w_ph=12, I=13, J=14, F=15, G=16, pair_ptr=17, active=18)
+           pair_q=10, w_e=11, w_ph=12, I=13, J=14, F=15, G=16, pair_ptr=17, active=18, state_eps=19,
+           state_vel=20, state_weight=21)
+NOALLOC_MAX_ITEMS = 4194304
 _DT = {0: np.float64, 1: np.complex128, 2: np.int32, 3: np.int64, 4: np.uint32}
 
 EXPORTED = ["ephb_create", "ephb_destroy", "ephb_last_error", "ephb_set_wannier_model", "ephb_build_meshes_ibz",
             "ephb_compute_transition_rates", "ephb_solve_coupled_bte", "ephb_transport_coefficients",
-            "ephb_get_device_array", "ephb_copy_array_to_host", "ephb_kernel_launches"]
+            "ephb_get_device_array", "ephb_copy_array_to_host", "ephb_kernel_launches",
+            "ephb_transport_coefficients_noalloc"]
 
 _pd = C.POINTER(C.c_double)
 _pi = C.POINTER(C.c_int32)
@@ -84,6 +87,15 @@ class CoeffsC(C.Structure):
                 ("sigma", "sigmaS", "S", "alpha_el", "kappa0_el", "kappa_el", "alpha_ph", "kappa_ph")]
 
 
+class CoeffInputsC(C.Structure):
+    _fields_ = [("n_states", C.c_int64), ("eps", C.c_void_p), ("vel", C.c_void_p), ("weight", C.c_void_p),
+                ("I", C.c_void_p), ("J", C.c_void_p), ("n_modes", C.c_int64), ("omega", C.c_void_p),
+                ("vph", C.c_void_p), ("F", C.c_void_p), ("G", C.c_void_p), ("T_K", C.c_double),
+                ("mu_eV", C.c_double), ("spin_deg", C.c_double), ("volume_A3", C.c_double), ("nk", C.c_int64),
+                ("nq", C.c_int64), ("omega_min_eV", C.c_double), ("nsym", C.c_int),
+                ("sym_cart", C.c_double * (48 * 9))]
+
+
 class EphbError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
@@ -111,6 +123,7 @@ def load(path: str = None):
     lib.ephb_get_device_array.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
                                           C.POINTER(C.c_int)]
     lib.ephb_copy_array_to_host.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]
+    lib.ephb_transport_coefficients_noalloc.argtypes = [C.POINTER(CoeffInputsC), C.c_void_p, C.c_void_p]
     lib.ephb_kernel_launches.argtypes = []
     for name in EXPORTED:
         if name not in ("ephb_destroy", "ephb_last_error", "ephb_kernel_launches"):
@@ -271,6 +284,27 @@ def device_array(ctx: Context, which: str):
     dt = C.c_int()
     _check(ctx, _lib.ephb_get_device_array(ctx.handle, ARR[which], C.byref(p), shape, C.byref(dt)))
     return p.value, tuple(int(s) for s in shape), _DT[dt.value]
+
+
+def transport_coefficients_noalloc(ptrs: dict, n_states: int, n_modes: int, T_K: float, mu_eV: float,
+                                   spin_deg: float, volume_A3: float, nk: int, nq: int, omega_min_eV: float,
+                                   sym_cart, out_dev: int, stream: int = 0) -> int:
+    """ephb_transport_coefficients_noalloc: `ptrs` maps eps, vel, weight, I, J, omega, vph, F, G
+    to device addresses; `out_dev` is the device address of 72 doubles.  Returns the status."""
+    lib = load()
+    c = CoeffInputsC()
+    c.n_states, c.n_modes = int(n_states), int(n_modes)
+    for name in ("eps", "vel", "weight", "I", "J", "omega", "vph", "F", "G"):
+        setattr(c, name, C.c_void_p(ptrs[name]) if ptrs.get(name) else None)
+    c.T_K, c.mu_eV, c.spin_deg, c.volume_A3 = float(T_K), float(mu_eV), float(spin_deg), float(volume_A3)
+    c.nk, c.nq, c.omega_min_eV = int(nk), int(nq), float(omega_min_eV)
+    ops = np.ascontiguousarray(sym_cart, dtype=np.float64).reshape(-1, 9)
+    c.nsym = int(ops.shape[0])
+    flat = np.zeros(48 * 9)
+    flat[:ops.size] = ops.ravel()
+    c.sym_cart[:] = list(flat)
+    return int(lib.ephb_transport_coefficients_noalloc(C.byref(c), C.c_void_p(out_dev),
+                                                        C.c_void_p(stream) if stream else None))
 
 
 @dataclasses.dataclass

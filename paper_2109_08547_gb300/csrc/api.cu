@@ -824,6 +824,9 @@ ephb_status ephb_get_device_array(ephb_ctx *ctx, int which, void **dptr, int64_t
     case EPHB_ARR_J: p = ctx->J.p; shape[0] = nst; shape[1] = 3; need = 4; break;
     case EPHB_ARR_F: p = ctx->F.p; shape[0] = nq; shape[1] = nbr; shape[2] = 3; need = 4; break;
     case EPHB_ARR_G: p = ctx->G.p; shape[0] = nq; shape[1] = nbr; shape[2] = 3; need = 4; break;
+    case EPHB_ARR_STATE_EPS: p = ctx->st_eps.p; shape[0] = nst; need = 4; break;
+    case EPHB_ARR_STATE_VEL: p = ctx->st_vel.p; shape[0] = nst; shape[1] = 3; need = 4; break;
+    case EPHB_ARR_STATE_WEIGHT: p = ctx->st_wt.p; shape[0] = nst; need = 4; break;
     default: return fail(ctx, EPHB_EINVAL, "unknown array id");
   }
   if (ctx->stage < need || (need == 4 && !ctx->bte_ready)) return fail(ctx, EPHB_ESTATE, "array not computed yet");
