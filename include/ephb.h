@@ -189,6 +189,8 @@ typedef struct {
   double ms_e_sweep;           /* summed device time of the electron sweep kernels         */
   double ms_ph_sweep;          /* summed device time of the phonon drag sweep kernels      */
   double e_sweep_bytes;        /* algorithmic HBM bytes of one electron sweep              */
+  double ms_drag;              /* summed device time of the electron drag-term kernels     */
+  int64_t n_runs;              /* partner runs: entries of a row merged over branches      */
 } ephb_solve_info;
 
 ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *opts, ephb_solve_info *out);

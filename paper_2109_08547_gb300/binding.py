@@ -79,7 +79,8 @@ class SolveInfoC(C.Structure):
     _fields_ = [("outer_iters", C.c_int), ("inner_iters_total", C.c_int), ("converged", C.c_int),
                 ("n_zero_rate_states", C.c_int), ("residual", C.c_double), ("lambda_", C.c_double),
                 ("n_sweeps", C.c_int64), ("ms", C.c_double), ("ms_e_sweep", C.c_double),
-                ("ms_ph_sweep", C.c_double), ("e_sweep_bytes", C.c_double)]
+                ("ms_ph_sweep", C.c_double), ("e_sweep_bytes", C.c_double), ("ms_drag", C.c_double),
+                ("n_runs", C.c_int64)]
 
 
 class CoeffsC(C.Structure):

@@ -113,10 +113,12 @@ struct ephb_ctx {
 
   // BTE
   DBuf<double> st_eps, st_vel, st_ff, st_wt, W_e, inv_ffW, I0, J0, I, J, I2, J2, Bt, W_ph, inv_nnW, F0, F, G, Btv,
-      seg_part, epart, ppart, kpart, res, prev_in, prev_out, prev_tmp;
-  DBuf<int> nseg_row, seg_row;
-  DBuf<int64_t> seg_ptr, seg_begin;
-  int64_t nseg = 0;
+      seg_part, epart, ppart, kpart, res, prev_in, prev_out, prev_tmp, Dterm, run_w;
+  // segments of the entry stream (drag term) and of the partner runs (self term)
+  DBuf<int> nseg_row, eseg_row, rseg_row, run_flag;
+  DBuf<int64_t> eseg_ptr, eseg_begin, rseg_ptr, rseg_begin, run_ptr, run_idx;
+  DBuf<uint32_t> run_col;
+  int64_t neseg = 0, nrseg = 0, nruns = 0;
   DBuf<uint32_t> kcrd;
   DBuf<int2> kinfo;
   DBuf<unsigned long long> ucount;
@@ -278,7 +280,9 @@ void ephb_destroy(ephb_ctx *ctx) {
   ctx->I2.release(); ctx->J2.release(); ctx->Bt.release(); ctx->W_ph.release(); ctx->inv_nnW.release();
   ctx->F0.release(); ctx->F.release(); ctx->G.release(); ctx->Btv.release(); ctx->seg_part.release();
   ctx->epart.release(); ctx->ppart.release(); ctx->kpart.release(); ctx->nseg_row.release();
-  ctx->seg_row.release(); ctx->seg_ptr.release(); ctx->seg_begin.release();
+  ctx->eseg_row.release(); ctx->rseg_row.release(); ctx->run_flag.release(); ctx->eseg_ptr.release();
+  ctx->eseg_begin.release(); ctx->rseg_ptr.release(); ctx->rseg_begin.release(); ctx->run_ptr.release();
+  ctx->run_idx.release(); ctx->run_col.release(); ctx->Dterm.release(); ctx->run_w.release();
   ctx->res.release(); ctx->prev_in.release(); ctx->prev_out.release(); ctx->prev_tmp.release();
   ctx->kcrd.release(); ctx->kinfo.release(); ctx->ucount.release();
   if (ctx->host_res) cudaFreeHost(ctx->host_res);
@@ -616,26 +620,56 @@ ephb_status bte_setup(ephb_ctx *ctx) {
   CK(launch_rta_electron(B, ctx->W_e.p, ctx->inv_ffW.p, ctx->I0.p, ctx->J0.p, ctx->ucount.p + 1, st));
   CK(launch_ph_rowsum(B, ctx->Bt.p, st));
   CK(launch_rta_phonon(M, D, B, ctx->Bt.p, ctx->W_ph.p, ctx->inv_nnW.p, ctx->F0.p, st));
-  // segments of the electron entry stream for the sweep kernel
+  // partner runs of the electron rows (self term), then segments of the entry stream
+  // (drag term) and of the run stream (self term)
+  const int64_t ne = ctx->n_entries;
+  CK(ctx->run_flag.ensure(ne));
+  CK(ctx->run_idx.ensure(ne));
+  CK(ctx->run_ptr.ensure(nst + 1));
+  CK(ctx->scratch.ensure(scan_scratch_elems(ne > nst ? ne : nst)));
+  CK(launch_build_runs(B, ne, ctx->kinfo.p, ctx->run_flag.p, ctx->run_idx.p, ctx->scratch.p, ctx->scratch.n,
+                       ctx->run_ptr.p, nullptr, nullptr, ctx->nruns, ctx->scal.p + 5, st));
+  CK(ctx->run_col.ensure(ctx->nruns));
+  CK(ctx->run_w.ensure(ctx->nruns));
+  CK(launch_fill_runs(B, ne, ctx->nruns, ctx->kinfo.p, ctx->run_flag.p, ctx->run_idx.p, ctx->run_ptr.p,
+                      ctx->run_col.p, ctx->run_w.p, st));
   CK(ctx->nseg_row.ensure(nst));
-  CK(ctx->seg_ptr.ensure(nst + 1));
-  CK(ctx->scratch.ensure(scan_scratch_elems(nst)));
-  CK(launch_build_segments(B, ctx->nseg_row.p, ctx->seg_ptr.p, nullptr, nullptr, ctx->scratch.p, ctx->scratch.n,
-                           nullptr, ctx->nseg, st));
-  CK(ctx->seg_row.ensure(ctx->nseg));
-  CK(ctx->seg_begin.ensure(ctx->nseg));
-  CK(ctx->seg_part.ensure(size_t(ctx->nseg) * 6));
-  CK(launch_fill_segments(B, ctx->seg_ptr.p, ctx->seg_row.p, ctx->seg_begin.p, st));
+  CK(ctx->eseg_ptr.ensure(nst + 1));
+  CK(ctx->rseg_ptr.ensure(nst + 1));
+  CK(launch_build_segments(nst, ctx->row_ptr.p, ctx->nseg_row.p, ctx->eseg_ptr.p, ctx->scratch.p, ctx->scratch.n,
+                           ctx->neseg, st));
+  CK(ctx->eseg_row.ensure(ctx->neseg));
+  CK(ctx->eseg_begin.ensure(ctx->neseg));
+  CK(launch_fill_segments(nst, ctx->row_ptr.p, ctx->eseg_ptr.p, ctx->eseg_row.p, ctx->eseg_begin.p, st));
+  CK(launch_build_segments(nst, ctx->run_ptr.p, ctx->nseg_row.p, ctx->rseg_ptr.p, ctx->scratch.p, ctx->scratch.n,
+                           ctx->nrseg, st));
+  CK(ctx->rseg_row.ensure(ctx->nrseg));
+  CK(ctx->rseg_begin.ensure(ctx->nrseg));
+  CK(launch_fill_segments(nst, ctx->run_ptr.p, ctx->rseg_ptr.p, ctx->rseg_row.p, ctx->rseg_begin.p, st));
+  CK(ctx->seg_part.ensure(size_t(ctx->neseg > ctx->nrseg ? ctx->neseg : ctx->nrseg) * 6));
+  CK(ctx->Dterm.ensure(nst * 6));
+  CK(cudaMemsetAsync(ctx->Dterm.p, 0, nst * 6 * sizeof(double), st));
   ctx->bte_ready = true;
   return EPHB_OK;
 }
 
-SweepSegs segs_view(ephb_ctx *c) {
+SweepSegs entry_segs(ephb_ctx *c) {
   SweepSegs S;
-  S.nseg = c->nseg;
-  S.seg_row = c->seg_row.p;
-  S.seg_begin = c->seg_begin.p;
-  S.seg_ptr = c->seg_ptr.p;
+  S.nseg = c->neseg;
+  S.seg_row = c->eseg_row.p;
+  S.seg_begin = c->eseg_begin.p;
+  S.seg_ptr = c->eseg_ptr.p;
+  S.row_ptr = c->row_ptr.p;
+  return S;
+}
+
+SweepSegs run_segs(ephb_ctx *c) {
+  SweepSegs S;
+  S.nseg = c->nrseg;
+  S.seg_row = c->rseg_row.p;
+  S.seg_begin = c->rseg_begin.p;
+  S.seg_ptr = c->rseg_ptr.p;
+  S.row_ptr = c->run_ptr.p;
   return S;
 }
 
@@ -683,20 +717,27 @@ ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb
   int64_t sweeps = 0;
   bool converged = o->level == EPHB_RTA;
   double residual = 0.0, lambda = 1.0;
-  EventTimer te, tp;
+  EventTimer te, tp, td;
   CK(te.init());
   CK(tp.init());
+  CK(td.init());
 
   auto inner_loop = [&](int drag, bool &ok) -> ephb_status {
     ok = false;
     CK(cudaMemsetAsync(ctx->prev_in.p, 0, kResLen * sizeof(double), st));
     ephb_status r = coefficients_to_host(ctx, ctx->prev_in.p, true, true);
     if (r != EPHB_OK) return r;
-    const SweepSegs S = segs_view(ctx);
+    if (drag) {   // F, G are fixed for this electron loop: its drag term is computed once
+      CK(td.start(st));
+      CK(launch_drag_term(D, B, entry_segs(ctx), ctx->F.p, ctx->G.p, ctx->seg_part.p, ctx->Dterm.p, st));
+      CK(td.stop(st));
+    }
+    const SweepSegs S = run_segs(ctx);
     for (int it = 1; it <= o->max_inner; ++it) {
       CK(te.start(st));
-      CK(launch_e_sweep(M, D, B, S, ctx->kinfo.p, ctx->I0.p, ctx->J0.p, ctx->inv_ffW.p, ctx->I.p, ctx->J.p,
-                        ctx->F.p, ctx->G.p, drag, ctx->seg_part.p, ctx->I2.p, ctx->J2.p, ctx->epart.p, st));
+      CK(launch_self_sweep(M, B, S, ctx->run_col.p, ctx->run_w.p, ctx->I0.p, ctx->J0.p, ctx->inv_ffW.p, ctx->I.p,
+                           ctx->J.p, drag ? ctx->Dterm.p : nullptr, ctx->seg_part.p, ctx->I2.p, ctx->J2.p,
+                           ctx->epart.p, st));
       CK(te.stop(st));
       std::swap(ctx->I.p, ctx->I2.p);
       std::swap(ctx->J.p, ctx->J2.p);
@@ -707,6 +748,7 @@ ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb
       r = coefficients_to_host(ctx, ctx->prev_in.p, false, false);
       if (r != EPHB_OK) return r;
       CK(te.collect());
+      CK(td.collect());
       if (ctx->host_res[72] < inner_tol) {
         ok = true;
         return EPHB_OK;
@@ -768,7 +810,11 @@ ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb
     out->ms_e_sweep = te.ms;
     out->ms_ph_sweep = tp.ms;
     // per electron sweep: the entry stream (k'|n|s word + X+,X-) plus the per-row arrays
-    out->e_sweep_bytes = 20.0 * double(ctx->n_entries) + double(nst) * (8.0 + 13.0 * 8.0);
+    // per electron sweep: the run stream (partner word + weight) plus the per-row arrays
+    // (segment pointer, I0, J0, 1/(f(1-f)W), drag term, new I, J)
+    out->e_sweep_bytes = 12.0 * double(ctx->nruns) + double(nst) * (8.0 + 20.0 * 8.0);
+    out->ms_drag = td.ms;
+    out->n_runs = ctx->nruns;
   }
   ctx->stage = 4;
   if (!converged) return fail(ctx, EPHB_ENOCONV, "iteration limit reached before the tolerance");

@@ -130,38 +130,82 @@ __global__ void k_rta_phonon(ModelDev M, MeshDev D, BteDev B, const double *Bt, 
   for (int a = 0; a < 3; ++a) F0[t * 3 + a] = W > 0.0 ? (w / B.T) * D.vph[t * 3 + a] / W : 0.0;
 }
 
-// ---------------------------------------------------------------- electron sweep
-// The entry stream of the electron rows is cut into segments of at most kSeg entries
-// (never crossing a row).  One warp reduces one segment into 6 partial sums; a second
-// kernel adds a row's segment partials in segment order, so the result does not depend
-// on scheduling.  Per entry (Eqs. dI^S, dI^D):
-//   (X+ + X-) S_k' I_<k'>n  - F_qs X+ + F_-qs X-     and the same for J with G.
+// ---------------------------------------------------------------- electron sweeps
+// Entry streams (the rate entries of the electron rows, or the partner runs below) are
+// cut into segments of at most kSeg items that never cross a row.  One warp reduces one
+// segment into 6 partial sums; a finalisation kernel adds a row's segment partials in
+// segment order, so results do not depend on scheduling.
+//
+// Self term (Eq. dI^S): sum_{n k' s} (X+ + X-) S_k' I_<k'>n.  The entries of one row that
+// share the partner state (k', n) differ only in the branch s, so their weights are merged
+// once per rate build into "runs" {partner state, rotation, w = sum_s (X+ + X-)}; every
+// inner sweep then streams runs (12 B) instead of entries (20 B) and does a third of the
+// FP64 work.
+// Drag term (Eq. dI^D): sum (-F_qs X+ + F_-qs X-).  It depends on F, G only, which are
+// fixed during the electron iteration, so it is evaluated once per phonon iteration.
 constexpr int kSeg = 1024;
 constexpr int kUnroll = 4;
+constexpr uint32_t kRunColMask = (1u << 26) - 1u;
+constexpr uint32_t kRunNone = kRunColMask;      // partner without a representative row
 
-__global__ void k_seg_count(int64_t nst, const int64_t *row_ptr, int *nseg) {
-  int64_t st = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (st >= nst) return;
-  int64_t len = row_ptr[st + 1] - row_ptr[st];
-  nseg[st] = int((len + kSeg - 1) / kSeg);
+__global__ void k_seg_count(int64_t nrow, const int64_t *row_ptr, int *nseg) {
+  int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (r >= nrow) return;
+  int64_t len = row_ptr[r + 1] - row_ptr[r];
+  nseg[r] = int((len + kSeg - 1) / kSeg);
 }
 
-__global__ void k_seg_fill(int64_t nst, const int64_t *row_ptr, const int64_t *seg_ptr, int *seg_row,
+__global__ void k_seg_fill(int64_t nrow, const int64_t *row_ptr, const int64_t *seg_ptr, int *seg_row,
                            int64_t *seg_begin) {
-  int64_t st = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (st >= nst) return;
-  int64_t g = seg_ptr[st];
-  for (int64_t b = row_ptr[st]; b < row_ptr[st + 1]; b += kSeg, ++g) {
-    seg_row[g] = int(st);
+  int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (r >= nrow) return;
+  int64_t g = seg_ptr[r];
+  for (int64_t b = row_ptr[r]; b < row_ptr[r + 1]; b += kSeg, ++g) {
+    seg_row[g] = int(r);
     seg_begin[g] = b;
   }
 }
 
-template <bool SYM, bool DRAG>
-__global__ void __launch_bounds__(256) k_e_sweep_seg(ModelDev M, MeshDev D, BteDev B, SweepSegs S,
-                                                     const int2 *__restrict__ kinfo, const double *__restrict__ I,
-                                                     const double *__restrict__ J, const double *__restrict__ F,
-                                                     const double *__restrict__ G, double *__restrict__ part) {
+// run starts: an entry whose (k', n) differs from the previous entry's, or a row's first entry
+__global__ void k_run_flags(int64_t n, const uint32_t *kpns, int *flag) {
+  int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (e >= n) return;
+  const uint32_t key = kpns[e] & ((1u << (kKpBits + 4)) - 1u);   // k' and n, without s
+  flag[e] = (e == 0 || (kpns[e - 1] & ((1u << (kKpBits + 4)) - 1u)) != key) ? 1 : 0;
+}
+
+__global__ void k_run_rowstarts(int64_t nrow, const int64_t *row_ptr, int *flag) {
+  int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (r >= nrow) return;
+  if (row_ptr[r + 1] > row_ptr[r]) flag[row_ptr[r]] = 1;
+}
+
+__global__ void k_run_fill(int64_t n, const uint32_t *kpns, const double2 *X, const int *flag,
+                           const int64_t *runidx, const int2 *kinfo, uint32_t *run_col, double *run_w) {
+  int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (e >= n || !flag[e]) return;
+  double w = 0.0;
+  for (int64_t f = e; f < n && (f == e || !flag[f]); ++f) w += X[f].x + X[f].y;
+  const int2 inf = kinfo[unpack_kp(kpns[e])];
+  const uint32_t col = inf.x >= 0 ? uint32_t(inf.x + unpack_n(kpns[e])) : kRunNone;
+  run_col[runidx[e]] = col | (uint32_t(inf.y) << 26);
+  run_w[runidx[e]] = w;
+}
+
+__global__ void k_run_ptr(int64_t nrow, const int64_t *row_ptr, const int64_t *runidx, int64_t n_entries,
+                          int64_t nruns, int64_t *run_ptr) {
+  int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (r > nrow) return;
+  const int64_t e = row_ptr[r];
+  run_ptr[r] = e < n_entries ? runidx[e] : nruns;
+}
+
+// self term over the runs of one segment
+template <bool SYM>
+__global__ void __launch_bounds__(256) k_self_sweep_seg(ModelDev M, SweepSegs S, const uint32_t *__restrict__ run_col,
+                                                        const double *__restrict__ run_w,
+                                                        const double *__restrict__ I, const double *__restrict__ J,
+                                                        double *__restrict__ part) {
   __shared__ double C[kMaxSym * 9];
   if (SYM) {
     for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) C[t] = M.sym_cart[t];
@@ -170,72 +214,90 @@ __global__ void __launch_bounds__(256) k_e_sweep_seg(ModelDev M, MeshDev D, BteD
   const int64_t g = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (g >= S.nseg) return;
-  const int st = S.seg_row[g];
+  const int row = S.seg_row[g];
   const int64_t b = S.seg_begin[g];
-  const int64_t rend = B.row_ptr[st + 1];
+  const int64_t rend = S.row_ptr[row + 1];
   const int64_t e_end = b + kSeg < rend ? b + kSeg : rend;
-  const int nbr = B.nbr;
-  int k0 = 0, k1 = 0, k2 = 0;
-  if (DRAG) {
-    const uint32_t kc = B.kcrd[D.ibzw_list[st / B.nb]];
-    k0 = kc & 1023u;
-    k1 = (kc >> 10) & 1023u;
-    k2 = kc >> 20;
-  }
   double a[6] = {0, 0, 0, 0, 0, 0};
   for (int64_t e0 = b + lane; e0 < e_end; e0 += 32 * kUnroll) {
-    uint32_t pk[kUnroll];
-    double2 X[kUnroll];
+    uint32_t pc[kUnroll];
+    double w[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const int64_t e = e0 + 32 * u;
-      pk[u] = e < e_end ? __ldcs(B.e_kpns + e) : 0u;
-      X[u] = e < e_end ? __ldcs(B.e_X + e) : make_double2(0.0, 0.0);
+      pc[u] = e < e_end ? __ldcs(run_col + e) : kRunNone;
+      w[u] = e < e_end ? __ldcs(run_w + e) : 0.0;
     }
-    int2 inf[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) inf[u] = kinfo[unpack_kp(pk[u])];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      // inf.x < 0 would mean k' active but its representative not (a state within rounding
-      // of a window edge); such a partner contributes nothing rather than reading out of range
-      if (e0 + 32 * u >= e_end || inf[u].x < 0) continue;
-      const int64_t st2 = inf[u].x + unpack_n(pk[u]);
-      const double xs = X[u].x + X[u].y;
-      double vi[3] = {I[st2 * 3], I[st2 * 3 + 1], I[st2 * 3 + 2]};
-      double vj[3] = {J[st2 * 3], J[st2 * 3 + 1], J[st2 * 3 + 2]};
+      const uint32_t col = pc[u] & kRunColMask;
+      if (col == kRunNone) continue;
+      double vi[3] = {I[int64_t(col) * 3], I[int64_t(col) * 3 + 1], I[int64_t(col) * 3 + 2]};
+      double vj[3] = {J[int64_t(col) * 3], J[int64_t(col) * 3 + 1], J[int64_t(col) * 3 + 2]};
       if (SYM) {
         double r[3];
-        const double *Cs = C + 9 * inf[u].y;
+        const double *Cs = C + 9 * (pc[u] >> 26);
         rot3(Cs, vi, r);
         vi[0] = r[0]; vi[1] = r[1]; vi[2] = r[2];
         rot3(Cs, vj, r);
         vj[0] = r[0]; vj[1] = r[1]; vj[2] = r[2];
       }
       for (int c = 0; c < 3; ++c) {
-        a[c] += xs * vi[c];
-        a[3 + c] += xs * vj[c];
-      }
-      if (DRAG) {
-        const int kp = unpack_kp(pk[u]), s = unpack_s(pk[u]);
-        const uint32_t pc = B.kcrd[kp];
-        const int d0 = pmod(int(pc & 1023u) - k0, D.km.n[0]) / D.ratio[0];
-        const int d1 = pmod(int((pc >> 10) & 1023u) - k1, D.km.n[1]) / D.ratio[1];
-        const int d2 = pmod(int(pc >> 20) - k2, D.km.n[2]) / D.ratio[2];
-        const int64_t q = D.qm.flat(d0, d1, d2);
-        const int64_t mq = D.qm.flat(pmod(-d0, D.qm.n[0]), pmod(-d1, D.qm.n[1]), pmod(-d2, D.qm.n[2]));
-        const double *Fq = F + (q * nbr + s) * 3, *Fm = F + (mq * nbr + s) * 3;
-        const double *Gq = G + (q * nbr + s) * 3, *Gm = G + (mq * nbr + s) * 3;
-        for (int c = 0; c < 3; ++c) {
-          a[c] += -Fq[c] * X[u].x + Fm[c] * X[u].y;
-          a[3 + c] += -Gq[c] * X[u].x + Gm[c] * X[u].y;
-        }
+        a[c] += w[u] * vi[c];
+        a[3 + c] += w[u] * vj[c];
       }
     }
   }
   for (int c = 0; c < 6; ++c) a[c] = warp_sum(a[c]);
   if (lane == 0)
     for (int c = 0; c < 6; ++c) part[g * 6 + c] = a[c];
+}
+
+// drag term over the rate entries of one segment
+__global__ void __launch_bounds__(256) k_drag_sweep_seg(MeshDev D, BteDev B, SweepSegs S,
+                                                        const double *__restrict__ F, const double *__restrict__ G,
+                                                        double *__restrict__ part) {
+  const int64_t g = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= S.nseg) return;
+  const int st = S.seg_row[g];
+  const int64_t b = S.seg_begin[g];
+  const int64_t rend = S.row_ptr[st + 1];
+  const int64_t e_end = b + kSeg < rend ? b + kSeg : rend;
+  const int nbr = B.nbr;
+  const uint32_t kc = B.kcrd[D.ibzw_list[st / B.nb]];
+  const int k0 = kc & 1023u, k1 = (kc >> 10) & 1023u, k2 = kc >> 20;
+  double a[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t e = b + lane; e < e_end; e += 32) {
+    const uint32_t pk = __ldcs(B.e_kpns + e);
+    const double2 X = __ldcs(B.e_X + e);
+    const int kp = unpack_kp(pk), s = unpack_s(pk);
+    const uint32_t pc = B.kcrd[kp];
+    const int d0 = pmod(int(pc & 1023u) - k0, D.km.n[0]) / D.ratio[0];
+    const int d1 = pmod(int((pc >> 10) & 1023u) - k1, D.km.n[1]) / D.ratio[1];
+    const int d2 = pmod(int(pc >> 20) - k2, D.km.n[2]) / D.ratio[2];
+    const int64_t q = D.qm.flat(d0, d1, d2);
+    const int64_t mq = D.qm.flat(pmod(-d0, D.qm.n[0]), pmod(-d1, D.qm.n[1]), pmod(-d2, D.qm.n[2]));
+    const double *Fq = F + (q * nbr + s) * 3, *Fm = F + (mq * nbr + s) * 3;
+    const double *Gq = G + (q * nbr + s) * 3, *Gm = G + (mq * nbr + s) * 3;
+    for (int c = 0; c < 3; ++c) {
+      a[c] += -Fq[c] * X.x + Fm[c] * X.y;
+      a[3 + c] += -Gq[c] * X.x + Gm[c] * X.y;
+    }
+  }
+  for (int c = 0; c < 6; ++c) a[c] = warp_sum(a[c]);
+  if (lane == 0)
+    for (int c = 0; c < 6; ++c) part[g * 6 + c] = a[c];
+}
+
+// Dterm[st] = sum of the row's drag segment partials (in segment order)
+__global__ void k_drag_finalize(int64_t nst, SweepSegs S, const double *part, double *Dterm) {
+  int64_t st = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (st >= nst) return;
+  double s[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t g = S.seg_ptr[st]; g < S.seg_ptr[st + 1]; ++g)
+    for (int c = 0; c < 6; ++c) s[c] += part[g * 6 + c];
+  for (int c = 0; c < 6; ++c) Dterm[st * 6 + c] = s[c];
 }
 
 // One warp per phonon row (q,s): Btv = sum Y/|stab| (S_k' I_<k'>n - I_km), fields I and J.
@@ -344,12 +406,12 @@ __device__ inline void e_tensor_acc(const BteDev &B, int64_t st, const double *I
     }
 }
 
-// I = I0 + (sum of the row's segment partials) / (f(1-f) W), same for J; plus the electron
+// I = I0 + (self partials + drag term) / (f(1-f) W), same for J; plus the electron
 // coefficient partial sums of the new responses.
 __global__ void __launch_bounds__(kCT) k_e_finalize(BteDev B, SweepSegs S, const double *__restrict__ part,
-                                                    const double *__restrict__ I0, const double *__restrict__ J0,
-                                                    const double *__restrict__ inv_ffW, double *I_out,
-                                                    double *J_out, double *epart) {
+                                                    const double *__restrict__ Dterm, const double *__restrict__ I0,
+                                                    const double *__restrict__ J0, const double *__restrict__ inv_ffW,
+                                                    double *I_out, double *J_out, double *epart) {
   double acc[kNE];
   for (int j = 0; j < kNE; ++j) acc[j] = 0.0;
   const int64_t stride = int64_t(gridDim.x) * kCT;
@@ -357,6 +419,8 @@ __global__ void __launch_bounds__(kCT) k_e_finalize(BteDev B, SweepSegs S, const
     double s[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t g = S.seg_ptr[st]; g < S.seg_ptr[st + 1]; ++g)
       for (int c = 0; c < 6; ++c) s[c] += part[g * 6 + c];
+    if (Dterm)
+      for (int c = 0; c < 6; ++c) s[c] += Dterm[st * 6 + c];
     const double c0 = inv_ffW[st];
     double In[3], Jn[3];
     for (int c = 0; c < 3; ++c) {
@@ -400,36 +464,15 @@ __global__ void __launch_bounds__(kCT) k_ph_partial(MeshDev D, BteDev B, const d
   block_reduce_store(acc, kNP, ppart + size_t(blockIdx.x) * kNP);
 }
 
-__device__ inline void symmetrise(const double *C, int nsym, const double *M, double *out) {
-  for (int j = 0; j < 9; ++j) out[j] = 0.0;
-  for (int o = 0; o < nsym; ++o) {
-    const double *S = C + 9 * o;
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) {
-        double s = 0.0;
-        for (int c = 0; c < 3; ++c)
-          for (int d = 0; d < 3; ++d) s += S[a * 3 + c] * M[c * 3 + d] * S[b * 3 + d];
-        out[a * 3 + b] += s;
-      }
-  }
-}
-
-__device__ inline double fro2(const double *a) {
-  double s = 0.0;
-  for (int j = 0; j < 9; ++j) s += a[j] * a[j];
-  return s;
-}
-
-__device__ inline double rel_change(const double *a, const double *b) {
-  double n = fro2(a);
-  if (n == 0.0) return 0.0;
-  double d = 0.0;
-  for (int j = 0; j < 9; ++j) d += (a[j] - b[j]) * (a[j] - b[j]);
-  return sqrt(d) / sqrt(n);
-}
-
-// column sums of the partial-sum blocks, one warp per column (fixed order)
-__device__ inline void sum_columns(const double *epart, const double *ppart, int npart, double *Ms) {
+// Final assembly, spread over threads (single-thread FP64 chains are slow on this GPU).
+// res: [0] sigma [9] sigmaS [18] alpha_el [27] kappa0_el [36] alpha_ph [45] kappa_ph [54] S [63] kappa_el
+//      [72] residual_e [73] residual_all
+__global__ void __launch_bounds__(512) k_coeff_final(ModelDev M, BteDev B, const double *epart,
+                                                     const double *ppart, int npart, double *res, double *prev) {
+  __shared__ double Ms[kNE + kNP];
+  __shared__ double R[72];
+  __shared__ double inv[10];
+  __shared__ double rc[6];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = wid; j < kNE + kNP; j += nw) {
     double s = 0.0;
@@ -438,60 +481,67 @@ __device__ inline void sum_columns(const double *epart, const double *ppart, int
     s = warp_sum(s);
     if (lane == 0) Ms[j] = s;
   }
-}
-
-// res: [0] sigma [9] sigmaS [18] alpha_el [27] kappa0_el [36] alpha_ph [45] kappa_ph [54] S [63] kappa_el
-//      [72] residual_e [73] residual_all
-__global__ void k_coeff_final(ModelDev M, BteDev B, const double *epart, const double *ppart, int npart,
-                              double *res, double *prev) {
-  __shared__ double Ms[kNE + kNP];
-  sum_columns(epart, ppart, npart, Ms);
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  double t[9];
-  const double sg[4] = {1.0, 1.0, -1.0, -1.0};
-  for (int c = 0; c < 4; ++c) {
-    symmetrise(M.sym_cart, M.nsym, Ms + 9 * c, t);
-    for (int j = 0; j < 9; ++j) res[9 * c + j] = sg[c] * B.Pe * t[j];
-  }
-  for (int j = 0; j < 9; ++j) {
-    res[36 + j] = B.Pph * Ms[36 + j];
-    res[45 + j] = B.Pph * Ms[45 + j];
-  }
-  // S = sigma^-1 sigmaS (adjugate inverse), kappa_el = kappa0_el - alpha_el S
-  const double *s = res;
-  double inv[9];
-  inv[0] = s[4] * s[8] - s[5] * s[7];
-  inv[1] = s[2] * s[7] - s[1] * s[8];
-  inv[2] = s[1] * s[5] - s[2] * s[4];
-  inv[3] = s[5] * s[6] - s[3] * s[8];
-  inv[4] = s[0] * s[8] - s[2] * s[6];
-  inv[5] = s[2] * s[3] - s[0] * s[5];
-  inv[6] = s[3] * s[7] - s[4] * s[6];
-  inv[7] = s[1] * s[6] - s[0] * s[7];
-  inv[8] = s[0] * s[4] - s[1] * s[3];
-  double det = s[0] * inv[0] + s[1] * inv[3] + s[2] * inv[6];
-  for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b) {
-      double v = 0.0;
-      for (int c = 0; c < 3; ++c) v += inv[a * 3 + c] * res[9 + c * 3 + b];
-      res[54 + a * 3 + b] = det != 0.0 ? v / det : 0.0;
+  const int t = threadIdx.x;
+  if (t < 36) {   // symmetrised electron tensors: sum_S S M S^T
+    const int c = t / 9, a = (t % 9) / 3, b = t % 3;
+    const double *Mc = Ms + 9 * c;
+    double s = 0.0;
+    for (int o = 0; o < M.nsym; ++o) {
+      const double *S = M.sym_cart + 9 * o;
+      for (int e = 0; e < 3; ++e)
+        for (int f = 0; f < 3; ++f) s += S[a * 3 + e] * Mc[e * 3 + f] * S[b * 3 + f];
     }
-  for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b) {
-      double v = 0.0;
-      for (int c = 0; c < 3; ++c) v += res[18 + a * 3 + c] * res[54 + c * 3 + b];
-      res[63 + a * 3 + b] = res[27 + a * 3 + b] - v;
-    }
-  double re = 0.0, ra = 0.0;
-  for (int c = 0; c < 6; ++c) {
-    double r = rel_change(res + 9 * c, prev + 9 * c);
-    if (c < 4) re = fmax(re, r);
-    ra = fmax(ra, r);
+    R[t] = (c < 2 ? 1.0 : -1.0) * B.Pe * s;
+  } else if (t < 54) {
+    R[t] = B.Pph * Ms[t];
   }
-  res[72] = re;
-  res[73] = ra;
-  for (int j = 0; j < 54; ++j) prev[j] = res[j];
+  __syncthreads();
+  if (t < 9) {    // adjugate of sigma
+    const double *s = R;
+    const int i0 = t / 3, j0 = t % 3;
+    // inv[j0][i0] = cofactor(i0, j0)
+    const int r1 = (i0 + 1) % 3, r2 = (i0 + 2) % 3, c1 = (j0 + 1) % 3, c2 = (j0 + 2) % 3;
+    inv[j0 * 3 + i0] = s[r1 * 3 + c1] * s[r2 * 3 + c2] - s[r1 * 3 + c2] * s[r2 * 3 + c1];
+  }
+  __syncthreads();
+  if (t == 0) inv[9] = R[0] * inv[0] + R[1] * inv[3] + R[2] * inv[6];
+  __syncthreads();
+  if (t < 9) {    // S = sigma^-1 sigmaS
+    const int a = t / 3, b = t % 3;
+    double v = 0.0;
+    for (int c = 0; c < 3; ++c) v += inv[a * 3 + c] * R[9 + c * 3 + b];
+    R[54 + t] = inv[9] != 0.0 ? v / inv[9] : 0.0;
+  }
+  __syncthreads();
+  if (t < 9) {    // kappa_el = kappa0_el - alpha_el S
+    const int a = t / 3, b = t % 3;
+    double v = 0.0;
+    for (int c = 0; c < 3; ++c) v += R[18 + a * 3 + c] * R[54 + c * 3 + b];
+    R[63 + t] = R[27 + t] - v;
+  }
+  if (t >= 32 && t < 38) {   // relative change of each of the six tensors
+    const int c = t - 32;
+    double n = 0.0, d = 0.0;
+    for (int j = 0; j < 9; ++j) {
+      const double x = R[9 * c + j], y = prev[9 * c + j];
+      n += x * x;
+      d += (x - y) * (x - y);
+    }
+    rc[c] = n == 0.0 ? 0.0 : sqrt(d) / sqrt(n);
+  }
+  __syncthreads();
+  if (t < 72) res[t] = R[t];
+  if (t < 54) prev[t] = R[t];
+  if (t == 0) {
+    double re = 0.0, ra = 0.0;
+    for (int c = 0; c < 6; ++c) {
+      if (c < 4) re = fmax(re, rc[c]);
+      ra = fmax(ra, rc[c]);
+    }
+    res[72] = re;
+    res[73] = ra;
+  }
 }
 
 // Kelvin-Onsager step: B = sigmaS[I_drag], A = alpha_ph / T, lambda = <A,B>/<B,B>
@@ -512,6 +562,7 @@ __global__ void __launch_bounds__(kCT) k_ko_partial(BteDev B, const double *I, c
 
 __global__ void k_ko_final(ModelDev M, BteDev B, const double *kpart, int npart, double *res) {
   __shared__ double Ms[9];
+  __shared__ double Bt[9];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = wid; j < 9; j += nw) {
     double s = 0.0;
@@ -520,15 +571,24 @@ __global__ void k_ko_final(ModelDev M, BteDev B, const double *kpart, int npart,
     if (lane == 0) Ms[j] = s;
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  double t[9];
-  symmetrise(M.sym_cart, M.nsym, Ms, t);
+  const int t = threadIdx.x;
+  if (t < 9) {
+    const int a = t / 3, b = t % 3;
+    double s = 0.0;
+    for (int o = 0; o < M.nsym; ++o) {
+      const double *S = M.sym_cart + 9 * o;
+      for (int e = 0; e < 3; ++e)
+        for (int f = 0; f < 3; ++f) s += S[a * 3 + e] * Ms[e * 3 + f] * S[b * 3 + f];
+    }
+    Bt[t] = B.Pe * s;
+  }
+  __syncthreads();
+  if (t != 0) return;
   double bb = 0.0, ab = 0.0;
   for (int j = 0; j < 9; ++j) {
-    double b = B.Pe * t[j];
     double a = res[36 + j] / B.T;
-    bb += b * b;
-    ab += a * b;
+    bb += Bt[j] * Bt[j];
+    ab += a * Bt[j];
   }
   if (sqrt(bb) > 1e-30) {
     res[74] = ab / bb;
@@ -582,51 +642,78 @@ cudaError_t launch_rta_phonon(const ModelDev &M, const MeshDev &D, const BteDev 
 }
 
 
-cudaError_t launch_build_segments(const BteDev &B, int *nseg_row, int64_t *seg_ptr, int *seg_row,
-                                  int64_t *seg_begin, int64_t *scratch, int64_t scratch_elems, int64_t *total_dev,
-                                  int64_t &nseg_host, cudaStream_t st) {
-  if (B.nst == 0) {
+cudaError_t launch_build_segments(int64_t nrow, const int64_t *row_ptr, int *nseg_row, int64_t *seg_ptr,
+                                  int64_t *scratch, int64_t scratch_elems, int64_t &nseg_host, cudaStream_t st) {
+  if (nrow == 0) {
     nseg_host = 0;
     return cudaMemsetAsync(seg_ptr, 0, sizeof(int64_t), st);
   }
-  unsigned grid = unsigned((B.nst + 255) / 256);
-  EPHB_LAUNCH(k_seg_count, grid, 256, 0, st, B.nst, B.row_ptr, nseg_row);
-  cudaError_t e = exclusive_scan<int>(nseg_row, seg_ptr, B.nst, seg_ptr + B.nst, scratch, scratch_elems, st);
+  EPHB_LAUNCH(k_seg_count, unsigned((nrow + 255) / 256), 256, 0, st, nrow, row_ptr, nseg_row);
+  cudaError_t e = exclusive_scan<int>(nseg_row, seg_ptr, nrow, seg_ptr + nrow, scratch, scratch_elems, st);
   if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(&nseg_host, seg_ptr + B.nst, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  e = cudaMemcpyAsync(&nseg_host, seg_ptr + nrow, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return e;
-  e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return e;
-  (void)total_dev;
-  return cudaSuccess;
+  return cudaStreamSynchronize(st);
 }
 
-cudaError_t launch_fill_segments(const BteDev &B, const int64_t *seg_ptr, int *seg_row, int64_t *seg_begin,
-                                 cudaStream_t st) {
-  if (B.nst == 0) return cudaSuccess;
-  EPHB_LAUNCH(k_seg_fill, unsigned((B.nst + 255) / 256), 256, 0, st, B.nst, B.row_ptr, seg_ptr, seg_row, seg_begin);
+cudaError_t launch_fill_segments(int64_t nrow, const int64_t *row_ptr, const int64_t *seg_ptr, int *seg_row,
+                                 int64_t *seg_begin, cudaStream_t st) {
+  if (nrow == 0) return cudaSuccess;
+  EPHB_LAUNCH(k_seg_fill, unsigned((nrow + 255) / 256), 256, 0, st, nrow, row_ptr, seg_ptr, seg_row, seg_begin);
   return cudaGetLastError();
 }
 
-cudaError_t launch_e_sweep(const ModelDev &M, const MeshDev &D, const BteDev &B, const SweepSegs &S,
-                           const int2 *kinfo, const double *I0, const double *J0, const double *inv_ffW,
-                           const double *I, const double *J, const double *F, const double *G, int drag,
-                           double *part, double *I_out, double *J_out, double *epart, cudaStream_t st) {
+cudaError_t launch_build_runs(const BteDev &B, int64_t n_entries, const int2 *kinfo, int *flag, int64_t *runidx,
+                              int64_t *scratch, int64_t scratch_elems, int64_t *run_ptr, uint32_t *run_col,
+                              double *run_w, int64_t &nruns, int64_t *total_dev, cudaStream_t st) {
+  nruns = 0;
+  if (n_entries > 0) {
+    const unsigned ge = unsigned((n_entries + 255) / 256);
+    EPHB_LAUNCH(k_run_flags, ge, 256, 0, st, n_entries, B.e_kpns, flag);
+    EPHB_LAUNCH(k_run_rowstarts, unsigned((B.nst + 255) / 256), 256, 0, st, B.nst, B.row_ptr, flag);
+    cudaError_t e = exclusive_scan<int>(flag, runidx, n_entries, total_dev, scratch, scratch_elems, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(&nruns, total_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_runs(const BteDev &B, int64_t n_entries, int64_t nruns, const int2 *kinfo, const int *flag,
+                             const int64_t *runidx, int64_t *run_ptr, uint32_t *run_col, double *run_w,
+                             cudaStream_t st) {
+  if (n_entries > 0)
+    EPHB_LAUNCH(k_run_fill, unsigned((n_entries + 255) / 256), 256, 0, st, n_entries, B.e_kpns, B.e_X, flag, runidx,
+                kinfo, run_col, run_w);
+  EPHB_LAUNCH(k_run_ptr, unsigned((B.nst + 1 + 255) / 256), 256, 0, st, B.nst, B.row_ptr, runidx, n_entries, nruns,
+              run_ptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_self_sweep(const ModelDev &M, const BteDev &B, const SweepSegs &S, const uint32_t *run_col,
+                              const double *run_w, const double *I0, const double *J0, const double *inv_ffW,
+                              const double *I, const double *J, const double *Dterm, double *part, double *I_out,
+                              double *J_out, double *epart, cudaStream_t st) {
   if (S.nseg > 0) {
-    unsigned grid = unsigned((S.nseg * 32 + 255) / 256);
-    const bool sym = M.nsym > 1;
-    if (sym && drag)
-      EPHB_LAUNCH((k_e_sweep_seg<true, true>), grid, 256, 0, st, M, D, B, S, kinfo, I, J, F, G, part);
-    else if (sym)
-      EPHB_LAUNCH((k_e_sweep_seg<true, false>), grid, 256, 0, st, M, D, B, S, kinfo, I, J, F, G, part);
-    else if (drag)
-      EPHB_LAUNCH((k_e_sweep_seg<false, true>), grid, 256, 0, st, M, D, B, S, kinfo, I, J, F, G, part);
+    const unsigned grid = unsigned((S.nseg * 32 + 255) / 256);
+    if (M.nsym > 1)
+      EPHB_LAUNCH(k_self_sweep_seg<true>, grid, 256, 0, st, M, S, run_col, run_w, I, J, part);
     else
-      EPHB_LAUNCH((k_e_sweep_seg<false, false>), grid, 256, 0, st, M, D, B, S, kinfo, I, J, F, G, part);
+      EPHB_LAUNCH(k_self_sweep_seg<false>, grid, 256, 0, st, M, S, run_col, run_w, I, J, part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  EPHB_LAUNCH(k_e_finalize, kNPart, kCT, 0, st, B, S, part, I0, J0, inv_ffW, I_out, J_out, epart);
+  EPHB_LAUNCH(k_e_finalize, kNPart, kCT, 0, st, B, S, part, Dterm, I0, J0, inv_ffW, I_out, J_out, epart);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_drag_term(const MeshDev &D, const BteDev &B, const SweepSegs &S, const double *F, const double *G,
+                             double *part, double *Dterm, cudaStream_t st) {
+  if (B.nst == 0) return cudaSuccess;
+  if (S.nseg > 0) EPHB_LAUNCH(k_drag_sweep_seg, unsigned((S.nseg * 32 + 255) / 256), 256, 0, st, D, B, S, F, G, part);
+  EPHB_LAUNCH(k_drag_finalize, unsigned((B.nst + 255) / 256), 256, 0, st, B.nst, S, part, Dterm);
   return cudaGetLastError();
 }
 
@@ -641,7 +728,6 @@ cudaError_t launch_ph_update(const ModelDev &M, const MeshDev &D, const BteDev &
   EPHB_LAUNCH(k_ph_update, unsigned((D.nq * M.nbr + 255) / 256), 256, 0, st, M, D, B, Btv, F0, inv_nnW, F, G);
   return cudaGetLastError();
 }
-
 
 cudaError_t launch_e_partial(const BteDev &B, const double *I, const double *J, double *epart, cudaStream_t st) {
   EPHB_LAUNCH(k_e_partial, kNPart, kCT, 0, st, B, I, J, epart);

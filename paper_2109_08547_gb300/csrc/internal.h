@@ -119,25 +119,35 @@ cudaError_t launch_rta_electron(const BteDev &B, double *W_e, double *inv_ffW, d
 cudaError_t launch_ph_rowsum(const BteDev &B, double *Bt, cudaStream_t st);
 cudaError_t launch_rta_phonon(const ModelDev &M, const MeshDev &D, const BteDev &B, const double *Bt, double *W_ph,
                               double *inv_nnW, double *F0, cudaStream_t st);
-// Segments of the electron entry stream (at most sweep_segment_len() entries, within one row).
+// Segments of a row-structured stream (at most sweep_segment_len() items, within one row).
 struct SweepSegs {
   int64_t nseg = 0;
-  const int *seg_row = nullptr;       // [nseg] state (row) of the segment
-  const int64_t *seg_begin = nullptr; // [nseg] first entry
-  const int64_t *seg_ptr = nullptr;   // [nst+1] first segment of each row
+  const int *seg_row = nullptr;       // [nseg] row of the segment
+  const int64_t *seg_begin = nullptr; // [nseg] first item
+  const int64_t *seg_ptr = nullptr;   // [nrow+1] first segment of each row
+  const int64_t *row_ptr = nullptr;   // [nrow+1] items of each row
 };
 int sweep_segment_len();
-cudaError_t launch_build_segments(const BteDev &B, int *nseg_row, int64_t *seg_ptr, int *seg_row,
-                                  int64_t *seg_begin, int64_t *scratch, int64_t scratch_elems, int64_t *total_dev,
-                                  int64_t &nseg_host, cudaStream_t st);
-cudaError_t launch_fill_segments(const BteDev &B, const int64_t *seg_ptr, int *seg_row, int64_t *seg_begin,
-                                 cudaStream_t st);
-// One electron sweep: segment partials, then per-row finalisation I = I0 + ..., which also
-// writes the electron coefficient partial sums (epart) of the new responses.
-cudaError_t launch_e_sweep(const ModelDev &M, const MeshDev &D, const BteDev &B, const SweepSegs &S,
-                           const int2 *kinfo, const double *I0, const double *J0, const double *inv_ffW,
-                           const double *I, const double *J, const double *F, const double *G, int drag,
-                           double *part, double *I_out, double *J_out, double *epart, cudaStream_t st);
+cudaError_t launch_build_segments(int64_t nrow, const int64_t *row_ptr, int *nseg_row, int64_t *seg_ptr,
+                                  int64_t *scratch, int64_t scratch_elems, int64_t &nseg_host, cudaStream_t st);
+cudaError_t launch_fill_segments(int64_t nrow, const int64_t *row_ptr, const int64_t *seg_ptr, int *seg_row,
+                                 int64_t *seg_begin, cudaStream_t st);
+// Partner runs: the entries of a row sharing (k', n), merged over branches.
+cudaError_t launch_build_runs(const BteDev &B, int64_t n_entries, const int2 *kinfo, int *flag, int64_t *runidx,
+                              int64_t *scratch, int64_t scratch_elems, int64_t *run_ptr, uint32_t *run_col,
+                              double *run_w, int64_t &nruns, int64_t *total_dev, cudaStream_t st);
+cudaError_t launch_fill_runs(const BteDev &B, int64_t n_entries, int64_t nruns, const int2 *kinfo, const int *flag,
+                             const int64_t *runidx, int64_t *run_ptr, uint32_t *run_col, double *run_w,
+                             cudaStream_t st);
+// One electron sweep (self term over the runs) and the per-row finalisation
+// I = I0 + (self + Dterm)/(f(1-f)W), which also writes the electron coefficient partials.
+cudaError_t launch_self_sweep(const ModelDev &M, const BteDev &B, const SweepSegs &S, const uint32_t *run_col,
+                              const double *run_w, const double *I0, const double *J0, const double *inv_ffW,
+                              const double *I, const double *J, const double *Dterm, double *part, double *I_out,
+                              double *J_out, double *epart, cudaStream_t st);
+// Drag term of every row for the current F, G: Dterm[st][6].
+cudaError_t launch_drag_term(const MeshDev &D, const BteDev &B, const SweepSegs &S, const double *F, const double *G,
+                             double *part, double *Dterm, cudaStream_t st);
 cudaError_t launch_ph_sweep(const ModelDev &M, const MeshDev &D, const BteDev &B, const int2 *kinfo, const double *I,
                             const double *J, double *Btv, cudaStream_t st);
 cudaError_t launch_ph_update(const ModelDev &M, const MeshDev &D, const BteDev &B, const double *Btv,
