@@ -31,7 +31,7 @@ METRIC = "transition rates/s and s to converged σ,S,κ at 1e-6 rel: mixed+batch
 UNIT = "transition rates/s"
 # FP64 FMA throughput of the GB300s, measured with `bench.py --fp64-peak`
 # (profiles/fp64_peak_gb300.txt); the nominal figure is 1.25 TFLOP/s.
-FP64_PEAK_TFLOPS = 1.188
+FP64_PEAK_TFLOPS = 1.188  # lower of two measurements (1.188, 1.255)
 
 
 def parse():
