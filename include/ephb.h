@@ -138,7 +138,19 @@ ephb_status ephb_build_meshes_ibz(ephb_ctx *ctx, const ephb_mesh_opts *opts, eph
  * --------------------------------------------------------------------------------*/
 typedef struct { double T_K, mu_eV; } ephb_thermo;
 typedef struct { double sigma_eV, cutoff_sigmas; } ephb_delta;
-typedef enum { EPHB_FP64 = 0, EPHB_SPLIT_TF32 = 1, EPHB_SPLIT_BF16 = 2 } ephb_precision;
+/* Precision of the R_ph contraction of the vertex (the largest part of the work):
+ *   EPHB_FP64         FP64 on the CUDA cores.
+ *   EPHB_FP64_SLICED  tensor cores (tcgen05, BF16 in, FP32 accumulate) on exact fixed-point
+ *                     slices: operands split into 5 slices of 8 bits, the 15 slice products
+ *                     of the leading diagonals, the two largest diagonals each kept in an
+ *                     accumulator where the FP32 sums are exact; FP64-grade results
+ *                     (relative error ~1e-12).
+ *   EPHB_SPLIT_BF16   the same with 3 slices and one FP32 accumulator (mixed precision,
+ *                     ~1e-7 relative).
+ *   EPHB_SPLIT_TF32   not available (EPHB_EINVAL).
+ * The stage-A contraction, the rotations, |g|^2, occupations and delta stay FP64 in every
+ * mode. */
+typedef enum { EPHB_FP64 = 0, EPHB_SPLIT_TF32 = 1, EPHB_SPLIT_BF16 = 2, EPHB_FP64_SLICED = 3 } ephb_precision;
 
 typedef struct {
   int64_t n_tuples;            /* (k m, q, n, s) tuples interpolated and delta-weighted    */
@@ -150,6 +162,8 @@ typedef struct {
   double ms_stage_b;           /* device time of the R_ph contraction + rate kernels       */
   double stage_a_flops;        /* algorithmic flops of the R_e contraction                 */
   double stage_b_flops;        /* algorithmic flops of the R_ph contraction + rotations    */
+  double ms_epilogue;          /* tensor-core modes: device time of the rotation/rate kernel */
+  double tensor_flops;         /* tensor-core modes: flops issued as tcgen05.mma           */
 } ephb_rates_info;
 
 ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst, int ninst,

@@ -18,7 +18,8 @@ _lib = None
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ENOCONV, ETIMEOUT, EINTERNAL = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ESTATE", "ENOCONV", "ETIMEOUT", "EINTERNAL"]
-FP64, SPLIT_TF32, SPLIT_BF16 = 0, 1, 2
+FP64, SPLIT_TF32, SPLIT_BF16, FP64_SLICED = 0, 1, 2, 3
+PRECISIONS = {"fp64": FP64, "fp64-sliced": FP64_SLICED, "split-bf16": SPLIT_BF16}
 RTA, PARTIAL, DRAGLESS, DRAGGED = 0, 1, 2, 3
 LEVELS = {"rta": RTA, "partial": PARTIAL, "dragless": DRAGLESS, "dragged": DRAGGED}
 
@@ -67,7 +68,8 @@ class DeltaC(C.Structure):
 class RatesInfoC(C.Structure):
     _fields_ = [("n_tuples", C.c_int64), ("n_entries", C.c_int64), ("n_ph_entries", C.c_int64),
                 ("n_pairs", C.c_int64), ("ms", C.c_double), ("ms_stage_a", C.c_double), ("ms_stage_b", C.c_double),
-                ("stage_a_flops", C.c_double), ("stage_b_flops", C.c_double)]
+                ("stage_a_flops", C.c_double), ("stage_b_flops", C.c_double), ("ms_epilogue", C.c_double),
+                ("tensor_flops", C.c_double)]
 
 
 class SolveOptsC(C.Structure):

@@ -2,6 +2,7 @@
 // call sequencing and the iteration control of the coupled BTE.  All numerical work is
 // enqueued as CUDA kernels on the context stream; the host only validates arguments,
 // sizes buffers and reads back scalars (counts, residuals) that steer the next launch.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
@@ -109,6 +110,11 @@ struct ephb_ctx {
   DBuf<int64_t> escan, phscan, row_ptr, ph_row_ptr;
   DBuf<uint32_t> e_kpns, ph_kpn;
   DBuf<double2> e_X, Tbuf, Abuf;
+  // tensor-core contraction: phase slices, B' slices and scales, work items, output scratch
+  DBuf<__nv_bfloat16> phis, bslices;
+  DBuf<double> bscale, Cbuf;
+  DBuf<int> nitem, tc_err;
+  DBuf<int64_t> item_ptr;
   DBuf<double> ph_Y;
 
   // BTE
@@ -275,6 +281,8 @@ void ephb_destroy(ephb_ctx *ctx) {
   ctx->cntE.release(); ctx->cntPh.release(); ctx->ph_st.release(); ctx->escan.release(); ctx->phscan.release();
   ctx->row_ptr.release(); ctx->ph_row_ptr.release(); ctx->e_kpns.release(); ctx->ph_kpn.release();
   ctx->e_X.release(); ctx->Tbuf.release(); ctx->Abuf.release(); ctx->ph_Y.release();
+  ctx->phis.release(); ctx->bslices.release(); ctx->bscale.release(); ctx->Cbuf.release(); ctx->nitem.release();
+  ctx->tc_err.release(); ctx->item_ptr.release();
   ctx->st_eps.release(); ctx->st_vel.release(); ctx->st_ff.release(); ctx->st_wt.release(); ctx->W_e.release();
   ctx->inv_ffW.release(); ctx->I0.release(); ctx->J0.release(); ctx->I.release(); ctx->J.release();
   ctx->I2.release(); ctx->J2.release(); ctx->Bt.release(); ctx->W_ph.release(); ctx->inv_nnW.release();
@@ -487,7 +495,8 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
   if (ctx->stage < 2) return fail(ctx, EPHB_ESTATE, "build_meshes_ibz must come first");
   if (!inst || !delta) return fail(ctx, EPHB_EINVAL, "NULL argument");
   if (ninst != 1) return fail(ctx, EPHB_EINVAL, "only one (T, mu) instance per call is supported");
-  if (precision != EPHB_FP64) return fail(ctx, EPHB_EINVAL, "only EPHB_FP64 is available");
+  if (precision != EPHB_FP64 && precision != EPHB_FP64_SLICED && precision != EPHB_SPLIT_BF16)
+    return fail(ctx, EPHB_EINVAL, "precision must be EPHB_FP64, EPHB_FP64_SLICED or EPHB_SPLIT_BF16");
   if (!(inst->T_K > 0) || !(delta->sigma_eV > 0) || !(delta->cutoff_sigmas > 0))
     return fail(ctx, EPHB_EINVAL, "T, sigma and cutoff must be positive");
   CK(cudaSetDevice(ctx->device));
@@ -547,21 +556,74 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     CK(ctx->Tbuf.ensure(size_t(chunk) * per_k));
     CK(ctx->Abuf.ensure(size_t(chunk) * stage_a_A_elems(M)));
   }
-  EventTimer ta, tb;
+  EventTimer ta, tb, tc;
   CK(ta.init());
   CK(tb.init());
-  for (int64_t i0 = 0; i0 < ctx->n_ibzw; i0 += chunk) {
+  CK(tc.init());
+  const bool tensor = precision != EPHB_FP64;
+  const int ns = precision == EPHB_FP64_SLICED ? 5 : 3;
+  std::vector<int64_t> hpp;
+  int Nmax = 0;
+  const int64_t kMaxChunkPairs = 1 << 20;   // bound of the contraction scratch (pairs x Nmax doubles)
+  if (tensor) {
+    // phase slices of the whole q mesh, the pair pointers (to bound chunks by pairs) and scratch
+    Nmax = tc_nmax(M);
+    const int Kp = tc_kp(M);
+    CK(ctx->phis.ensure(size_t(nq) * ns * Kp));
+    CK(launch_phase_slices(M, D, ns, ctx->phis.p, st));
+    hpp.resize(ctx->n_ibzw + 1);
+    CK(cudaMemcpyAsync(hpp.data(), ctx->pair_ptr.p, hpp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(ctx->bslices.ensure(size_t(chunk) * ns * Nmax * Kp));
+    CK(ctx->bscale.ensure(size_t(chunk) * Nmax));
+    CK(ctx->nitem.ensure(chunk));
+    CK(ctx->item_ptr.ensure(chunk));
+    CK(ctx->Cbuf.ensure(size_t(std::min<int64_t>(np, kMaxChunkPairs)) * Nmax));
+    CK(ctx->tc_err.ensure(1));
+    CK(cudaMemsetAsync(ctx->tc_err.p, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(ctx->scal.p + 7, 0, sizeof(int64_t), st));
+    CK(ctx->scratch.ensure(scan_scratch_elems(chunk > big ? chunk : big)));
+  }
+  for (int64_t i0 = 0; i0 < ctx->n_ibzw;) {
     int64_t nkc = ctx->n_ibzw - i0 < chunk ? ctx->n_ibzw - i0 : chunk;
+    if (tensor) {   // also keep the chunk's pairs within the contraction scratch
+      while (nkc > 1 && hpp[i0 + nkc] - hpp[i0] > kMaxChunkPairs) nkc = (nkc + 1) / 2;
+      if (hpp[i0 + nkc] - hpp[i0] > kMaxChunkPairs)
+        return fail(ctx, EPHB_EINVAL, "one irreducible k has more pairs than the contraction scratch holds");
+    }
     CK(ta.start(st));
     CK(launch_stage_a(M, D, i0, nkc, ctx->Tbuf.p, ctx->Abuf.p, st));
     CK(ta.stop(st));
     CK(tb.start(st));
-    CK(launch_stage_b_rates(M, D, rp, i0, nkc, ctx->Abuf.p, ctx->escan.p, ctx->phscan.p, ctx->e_kpns.p, ctx->e_X.p,
-                            ctx->ph_st.p, ctx->ph_kpn.p, ctx->ph_Y.p, st));
-    CK(tb.stop(st));
+    if (!tensor) {
+      CK(launch_stage_b_rates(M, D, rp, i0, nkc, ctx->Abuf.p, ctx->escan.p, ctx->phscan.p, ctx->e_kpns.p,
+                              ctx->e_X.p, ctx->ph_st.p, ctx->ph_kpn.p, ctx->ph_Y.p, st));
+      CK(tb.stop(st));
+    } else {
+      CK(launch_vertex_tc(M, D, ns, i0, nkc, hpp[i0], ctx->Abuf.p, ctx->phis.p, ctx->bslices.p, ctx->bscale.p,
+                          ctx->nitem.p, ctx->item_ptr.p, ctx->scratch.p, ctx->scratch.n, ctx->scal.p + 6,
+                          ctx->Cbuf.p, ctx->tc_err.p, st));
+      CK(tb.stop(st));
+      CK(tc.start(st));
+      CK(launch_vertex_epilogue(M, D, rp, i0, nkc, hpp[i0], ctx->Cbuf.p, Nmax, ctx->escan.p, ctx->phscan.p,
+                                ctx->e_kpns.p, ctx->e_X.p, ctx->ph_st.p, ctx->ph_kpn.p, ctx->ph_Y.p, st));
+      CK(tc.stop(st));
+    }
     CK(cudaStreamSynchronize(st));
     CK(ta.collect());
     CK(tb.collect());
+    CK(tc.collect());
+    i0 += nkc;
+  }
+  double tensor_flops = 0.0;
+  if (tensor) {
+    int herr = 0;
+    int64_t tfl = 0;
+    CK(cudaMemcpyAsync(&herr, ctx->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&tfl, ctx->scal.p + 7, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (herr) return fail(ctx, EPHB_ETIMEOUT, "a tensor-core wait gave up (vertex contraction)");
+    tensor_flops = double(tfl);
   }
   unsigned long long cnt[4];
   CK(cudaMemcpyAsync(cnt, ctx->ucount.p, sizeof(cnt), cudaMemcpyDeviceToHost, st));
@@ -582,6 +644,8 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     const double ncol = double(M.nRgp) * M.nb * M.nb * M.nbr;
     out->stage_a_flops = 8.0 * double(ctx->n_ibzw) * M.nRge * ncol + 8.0 * double(cnt[3]) * ncol;
     out->stage_b_flops = double(cnt[2]);
+    out->ms_epilogue = tc.ms;
+    out->tensor_flops = tensor_flops;
   }
   ctx->stage = 3;
   ctx->bte_ready = false;

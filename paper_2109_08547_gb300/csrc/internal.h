@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of the CUDA library.
 #pragma once
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -91,6 +92,20 @@ cudaError_t launch_stage_b_rates(const ModelDev &M, const MeshDev &D, RateParams
                                  double2 *e_X, int *ph_st, uint32_t *ph_kpn, double *ph_Y, cudaStream_t st);
 size_t stage_a_T_elems(const ModelDev &M);
 size_t stage_a_A_elems(const ModelDev &M);
+// Rates from a contraction already in Cbuf[pair - pair_base][Nmax] (tensor-core path).
+cudaError_t launch_vertex_epilogue(const ModelDev &M, const MeshDev &D, RateParams rp, int64_t i0, int64_t nkc,
+                                   int64_t pair_base, const double *Cbuf, int Nmax, const int64_t *escan,
+                                   const int64_t *phscan, uint32_t *e_kpns, double2 *e_X, int *ph_st,
+                                   uint32_t *ph_kpn, double *ph_Y, cudaStream_t st);
+
+// ---- vertex_tc.cu (tcgen05 R_ph contraction with exact BF16 fixed-point slices)
+int tc_kp(const ModelDev &M);     // padded K = 2 nRgp rounded up to the K block
+int tc_nmax(const ModelDev &M);   // column stride of B' = 2 nb^2 nbr rounded up to 16
+cudaError_t launch_phase_slices(const ModelDev &M, const MeshDev &D, int ns, __nv_bfloat16 *phis, cudaStream_t st);
+cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_t i0, int64_t nkc, int64_t pair_base,
+                             const double2 *A, const __nv_bfloat16 *phis, __nv_bfloat16 *bs, double *bscale,
+                             int *nitem, int64_t *item_ptr, int64_t *scratch, int64_t scratch_elems,
+                             int64_t *total_dev, double *Cbuf, int *err, cudaStream_t st);
 
 // ---- bte.cu
 struct BteDev {

@@ -201,6 +201,139 @@ __host__ __device__ inline StageBSmem stage_b_layout(int nb, int nbr) {
   return L;
 }
 
+// Rotations, |g|^2, degenerate average, occupations, delta and the compacted writes of one
+// (k, q) pair, executed by one warp.  Bp holds B[ml][n'][alpha] = sum_Rp e^{iq.Rp} A (complex).
+__device__ void pair_epilogue(const ModelDev &M, const MeshDev &D, const RateParams &rp, int64_t i, int k,
+                              uint32_t am, int nact, int Jk, int64_t p0, int64_t npl, int64_t pg,
+                              const double2 *Bp, double2 *Zs, double *g2s, double *Xps, double *Xms,
+                              const double *mscale, double inv_stab, const double *ek, double kT,
+                              const int64_t *__restrict__ escan, const int64_t *__restrict__ phscan,
+                              uint32_t *e_kpns, double2 *e_X, int *ph_st, uint32_t *ph_kpn, double *ph_Y) {
+  const int nb = M.nb, nbr = M.nbr;
+  const int lane = threadIdx.x & 31;
+  const int q = D.pair_q[pg];
+  const int kp = kplusq_d(D, k, q);
+  const uint32_t an = D.amask[kp];
+  const int nactp = __popc(an);
+  const double2 *uq = D.u + size_t(q) * nbr * nbr;
+  const double *wq = D.w + size_t(q) * nbr;
+  const double2 *ckp = D.cvec + size_t(kp) * nb * nb;
+  const double *ekp = D.eps + size_t(kp) * nb;
+    // Z[ml][n'][s] = sum_a B[ml][n'][a] u_{a s}(q) / sqrt(m_a / m_bar)
+  for (int t = lane; t < Jk; t += 32) {
+    int ml = t / (nb * nbr), np_ = (t / nbr) % nb, s = t % nbr;
+    double2 z = cmk(0, 0);
+    for (int a = 0; a < nbr; ++a)
+      cfma(z, Bp[(ml * nb + np_) * nbr + a], cscale(uq[a * nbr + s], mscale[a]));
+    Zs[t] = z;
+  }
+  __syncwarp();
+  // g[ml][nl][s] = sqrt(w_ref / w_s) sum_n' conj(c_{n'n}(k')) Z[ml][n'][s]
+  const int ntup = nact * nactp * nbr;
+  for (int t = lane; t < ntup; t += 32) {
+    int ml = t / (nactp * nbr), nl = (t / nbr) % nactp, s = t % nbr;
+    int n = nth_bit(an, nl);
+    double v = 0.0;
+    if (wq[s] > D.omega_min) {
+      double2 g = cmk(0, 0);
+      for (int np_ = 0; np_ < nb; ++np_) cfma_conj(g, ckp[np_ * nb + n], Zs[(ml * nb + np_) * nbr + s]);
+      v = cabs2(g) * (M.omega_ref / wq[s]);
+    }
+    g2s[t] = v;
+  }
+  __syncwarp();
+  // degenerate averages, occupations, delta; pass flags go to the (now free) Z scratch
+  int *flg = reinterpret_cast<int *>(Zs);
+  const uint8_t *gk = D.egrp + size_t(k) * nb * 2, *gkp = D.egrp + size_t(kp) * nb * 2;
+  const uint8_t *gq = D.pgrp + size_t(q) * nbr * 2;
+  for (int t = lane; t < ntup; t += 32) {
+    int ml = t / (nactp * nbr), nl = (t / nbr) % nactp, s = t % nbr;
+    int m = nth_bit(am, ml), n = nth_bit(an, nl);
+    double xp = 0.0, xm = 0.0;
+    if (wq[s] > D.omega_min) {
+      double sum = 0.0;
+      int cnt = 0;
+      for (int a = gk[2 * m]; a < gk[2 * m + 1]; ++a) {
+        if (!((am >> a) & 1u)) continue;
+        int al = __popc(am & ((1u << a) - 1u));
+        for (int b = gkp[2 * n]; b < gkp[2 * n + 1]; ++b) {
+          if (!((an >> b) & 1u)) continue;
+          int bl = __popc(an & ((1u << b) - 1u));
+          for (int c = gq[2 * s]; c < gq[2 * s + 1]; ++c) {
+            sum += g2s[(al * nactp + bl) * nbr + c];
+            ++cnt;
+          }
+        }
+      }
+      double g2 = sum / double(cnt);
+      double dxp = ekp[n] - ek[m] - wq[s];
+      double dxm = ekp[n] - ek[m] + wq[s];
+      double fm = fermi_d(ek[m], rp.mu, kT), fn = fermi_d(ekp[n], rp.mu, kT), nq = bose_d(wq[s], kT);
+      double occ = rp.inv_Nq_pref * g2 * fm * (1.0 - fn);
+      xp = occ * nq * gauss_d(dxp, rp.sigma, rp.cut);
+      xm = occ * (1.0 + nq) * gauss_d(dxm, rp.sigma, rp.cut);
+      Xps[t] = xp;
+      Xms[t] = xm;
+      flg[t] = (fabs(dxp) <= rp.cut ? 1 : 0) | (fabs(dxm) <= rp.cut ? 2 : 0);
+    } else {
+      Xps[t] = 0.0;
+      Xms[t] = 0.0;
+      flg[t] = 0;
+    }
+  }
+  __syncwarp();
+  // electron rows (k, m): entries ordered (n, s)
+  const int64_t pl = pg - p0;
+  for (int ml = 0; ml < nact; ++ml) {
+    const int m = nth_bit(am, ml);
+    int64_t base = escan[p0 * nb + m * npl + pl];
+    const int nit = nactp * nbr;
+    for (int c0 = 0; c0 < nit; c0 += 32) {
+      int t = c0 + lane;
+      int flag = 0, idx = 0;
+      if (t < nit) {
+        idx = ml * nit + t;
+        flag = flg[idx] != 0;
+      }
+      unsigned b = __ballot_sync(0xffffffffu, flag);
+      if (flag) {
+        int64_t pos = base + __popc(b & ((1u << lane) - 1u));
+        int nl = t / nbr, s = t % nbr;
+        e_kpns[pos] = pack_kpns(kp, nth_bit(an, nl), s);
+        e_X[pos] = cmk(Xps[idx], Xms[idx]);
+      }
+      base += __popc(b);
+    }
+  }
+  // phonon rows (q, s): entries ordered (m, n), absorption (+) processes only
+  const int64_t qb = D.qpair_ptr[q];
+  const int64_t npq = D.qpair_ptr[q + 1] - qb;
+  const int rk = D.pq_rank[pg];
+  for (int s = 0; s < nbr; ++s) {
+    if (!(wq[s] > D.omega_min)) continue;
+    int64_t base = phscan[qb * nbr + s * npq + rk];
+    const int nit = nact * nactp;
+    for (int c0 = 0; c0 < nit; c0 += 32) {
+      int t = c0 + lane;
+      int flag = 0, idx = 0;
+      if (t < nit) {
+        idx = t * nbr + s;
+        flag = (flg[idx] & 1) != 0;
+      }
+      unsigned b = __ballot_sync(0xffffffffu, flag);
+      if (flag) {
+        int64_t pos = base + __popc(b & ((1u << lane) - 1u));
+        int ml = t / nactp, nl = t % nactp;
+        ph_st[pos] = int(i) * nb + nth_bit(am, ml);
+        ph_kpn[pos] = pack_kpns(kp, nth_bit(an, nl), 0);
+        ph_Y[pos] = Xps[idx] * rp.y_scale * inv_stab;
+      }
+      base += __popc(b);
+    }
+  }
+  __syncwarp();
+}
+
 __global__ void __launch_bounds__(kBT) k_stage_b_rates(ModelDev M, MeshDev D, RateParams rp, int64_t i0,
                                                        const double2 *__restrict__ A,
                                                        const int64_t *__restrict__ escan,
@@ -279,135 +412,75 @@ __global__ void __launch_bounds__(kBT) k_stage_b_rates(ModelDev M, MeshDev D, Ra
     __syncthreads();
 
     // ---- epilogue: one warp per pair
-    for (int p = wid; p < npt; p += kBT / 32) {
-      const int64_t pg = p0 + t0 + p;
-      const int q = D.pair_q[pg];
-      const int kp = kplusq_d(D, k, q);
-      const uint32_t an = D.amask[kp];
-      const int nactp = __popc(an);
-      const double2 *uq = D.u + size_t(q) * nbr * nbr;
-      const double *wq = D.w + size_t(q) * nbr;
-      const double2 *ckp = D.cvec + size_t(kp) * nb * nb;
-      const double *ekp = D.eps + size_t(kp) * nb;
-      const double2 *Bp = Bsh + p * Jk;
-      // Z[ml][n'][s] = sum_a B[ml][n'][a] u_{a s}(q) / sqrt(m_a / m_bar)
-      for (int t = lane; t < Jk; t += 32) {
-        int ml = t / (nb * nbr), np_ = (t / nbr) % nb, s = t % nbr;
-        double2 z = cmk(0, 0);
-        for (int a = 0; a < nbr; ++a)
-          cfma(z, Bp[(ml * nb + np_) * nbr + a], cscale(uq[a * nbr + s], mscale[a]));
-        Zs[t] = z;
-      }
-      __syncwarp();
-      // g[ml][nl][s] = sqrt(w_ref / w_s) sum_n' conj(c_{n'n}(k')) Z[ml][n'][s]
-      const int ntup = nact * nactp * nbr;
-      for (int t = lane; t < ntup; t += 32) {
-        int ml = t / (nactp * nbr), nl = (t / nbr) % nactp, s = t % nbr;
-        int n = nth_bit(an, nl);
-        double v = 0.0;
-        if (wq[s] > D.omega_min) {
-          double2 g = cmk(0, 0);
-          for (int np_ = 0; np_ < nb; ++np_) cfma_conj(g, ckp[np_ * nb + n], Zs[(ml * nb + np_) * nbr + s]);
-          v = cabs2(g) * (M.omega_ref / wq[s]);
-        }
-        g2s[t] = v;
-      }
-      __syncwarp();
-      // degenerate averages, occupations, delta; pass flags go to the (now free) Z scratch
-      int *flg = reinterpret_cast<int *>(Zs);
-      const uint8_t *gk = D.egrp + size_t(k) * nb * 2, *gkp = D.egrp + size_t(kp) * nb * 2;
-      const uint8_t *gq = D.pgrp + size_t(q) * nbr * 2;
-      for (int t = lane; t < ntup; t += 32) {
-        int ml = t / (nactp * nbr), nl = (t / nbr) % nactp, s = t % nbr;
-        int m = nth_bit(am, ml), n = nth_bit(an, nl);
-        double xp = 0.0, xm = 0.0;
-        if (wq[s] > D.omega_min) {
-          double sum = 0.0;
-          int cnt = 0;
-          for (int a = gk[2 * m]; a < gk[2 * m + 1]; ++a) {
-            if (!((am >> a) & 1u)) continue;
-            int al = __popc(am & ((1u << a) - 1u));
-            for (int b = gkp[2 * n]; b < gkp[2 * n + 1]; ++b) {
-              if (!((an >> b) & 1u)) continue;
-              int bl = __popc(an & ((1u << b) - 1u));
-              for (int c = gq[2 * s]; c < gq[2 * s + 1]; ++c) {
-                sum += g2s[(al * nactp + bl) * nbr + c];
-                ++cnt;
-              }
-            }
-          }
-          double g2 = sum / double(cnt);
-          double dxp = ekp[n] - ek[m] - wq[s];
-          double dxm = ekp[n] - ek[m] + wq[s];
-          double fm = fermi_d(ek[m], rp.mu, kT), fn = fermi_d(ekp[n], rp.mu, kT), nq = bose_d(wq[s], kT);
-          double occ = rp.inv_Nq_pref * g2 * fm * (1.0 - fn);
-          xp = occ * nq * gauss_d(dxp, rp.sigma, rp.cut);
-          xm = occ * (1.0 + nq) * gauss_d(dxm, rp.sigma, rp.cut);
-          Xps[t] = xp;
-          Xms[t] = xm;
-          flg[t] = (fabs(dxp) <= rp.cut ? 1 : 0) | (fabs(dxm) <= rp.cut ? 2 : 0);
-        } else {
-          Xps[t] = 0.0;
-          Xms[t] = 0.0;
-          flg[t] = 0;
-        }
-      }
-      __syncwarp();
-      // electron rows (k, m): entries ordered (n, s)
-      const int64_t pl = pg - p0;
-      for (int ml = 0; ml < nact; ++ml) {
-        const int m = nth_bit(am, ml);
-        int64_t base = escan[p0 * nb + m * npl + pl];
-        const int nit = nactp * nbr;
-        for (int c0 = 0; c0 < nit; c0 += 32) {
-          int t = c0 + lane;
-          int flag = 0, idx = 0;
-          if (t < nit) {
-            idx = ml * nit + t;
-            flag = flg[idx] != 0;
-          }
-          unsigned b = __ballot_sync(0xffffffffu, flag);
-          if (flag) {
-            int64_t pos = base + __popc(b & ((1u << lane) - 1u));
-            int nl = t / nbr, s = t % nbr;
-            e_kpns[pos] = pack_kpns(kp, nth_bit(an, nl), s);
-            e_X[pos] = cmk(Xps[idx], Xms[idx]);
-          }
-          base += __popc(b);
-        }
-      }
-      // phonon rows (q, s): entries ordered (m, n), absorption (+) processes only
-      const int64_t qb = D.qpair_ptr[q];
-      const int64_t npq = D.qpair_ptr[q + 1] - qb;
-      const int rk = D.pq_rank[pg];
-      for (int s = 0; s < nbr; ++s) {
-        if (!(wq[s] > D.omega_min)) continue;
-        int64_t base = phscan[qb * nbr + s * npq + rk];
-        const int nit = nact * nactp;
-        for (int c0 = 0; c0 < nit; c0 += 32) {
-          int t = c0 + lane;
-          int flag = 0, idx = 0;
-          if (t < nit) {
-            idx = t * nbr + s;
-            flag = (flg[idx] & 1) != 0;
-          }
-          unsigned b = __ballot_sync(0xffffffffu, flag);
-          if (flag) {
-            int64_t pos = base + __popc(b & ((1u << lane) - 1u));
-            int ml = t / nactp, nl = t % nactp;
-            ph_st[pos] = int(i) * nb + nth_bit(am, ml);
-            ph_kpn[pos] = pack_kpns(kp, nth_bit(an, nl), 0);
-            ph_Y[pos] = Xps[idx] * rp.y_scale * inv_stab;
-          }
-          base += __popc(b);
-        }
-      }
-      __syncwarp();
+    for (int p = wid; p < npt; p += kBT / 32)
+      pair_epilogue(M, D, rp, i, k, am, nact, Jk, p0, npl, p0 + t0 + p, Bsh + p * Jk, Zs, g2s, Xps, Xms, mscale,
+                    inv_stab, ek, kT, escan, phscan, e_kpns, e_X, ph_st, ph_kpn, ph_Y);
+  }
+}
+
+// Rates from the tensor-core contraction: C'[pair][j'] with j' = ml*(2 nb nbr) + part*(nb nbr)
+// + n'*nbr + a (part 0: real, 1: imaginary).  One block per irreducible-window k, one warp per
+// pair; the per-pair work is the same epilogue as above.
+__global__ void __launch_bounds__(kBT) k_vertex_epilogue(ModelDev M, MeshDev D, RateParams rp, int64_t i0,
+                                                         int64_t pair_base, const double *__restrict__ Cbuf,
+                                                         int Nmax, const int64_t *__restrict__ escan,
+                                                         const int64_t *__restrict__ phscan, uint32_t *e_kpns,
+                                                         double2 *e_X, int *ph_st, uint32_t *ph_kpn, double *ph_Y) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nb = M.nb, nbr = M.nbr;
+  const int jmax = nb * nb * nbr;
+  size_t per_warp = size_t(jmax) * sizeof(double2) * 2 + 3 * size_t(jmax) * sizeof(double);
+  per_warp = (per_warp + 15) & ~size_t(15);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned char *wscr = smem + wid * per_warp;
+  double2 *Bp = reinterpret_cast<double2 *>(wscr);
+  double2 *Zs = Bp + jmax;
+  double *g2s = reinterpret_cast<double *>(Zs + jmax);
+  double *Xps = g2s + jmax;
+  double *Xms = Xps + jmax;
+  const int64_t i = i0 + blockIdx.x;
+  const int k = D.ibzw_list[i];
+  const uint32_t am = D.amask[k];
+  const int nact = __popc(am);
+  const int Jk = nact * nb * nbr;
+  const int64_t p0 = D.pair_ptr[i];
+  const int64_t npl = D.pair_ptr[i + 1] - p0;
+  const double kT = kKbEVK * rp.T;
+  const double *ek = D.eps + size_t(k) * nb;
+  const double inv_stab = 1.0 / double(D.stab[k]);
+  double mscale[kMaxBranches];
+  for (int a = 0; a < nbr; ++a) mscale[a] = 1.0 / sqrt(M.mass[a / 3] / M.mass_mean);
+  const int nbnbr = nb * nbr;
+  for (int64_t p = wid; p < npl; p += kBT / 32) {
+    const double *crow = Cbuf + (p0 + p - pair_base) * Nmax;
+    for (int t = lane; t < Jk; t += 32) {
+      const int ml = t / nbnbr, rest = t % nbnbr;
+      Bp[t] = cmk(crow[ml * 2 * nbnbr + rest], crow[ml * 2 * nbnbr + nbnbr + rest]);
     }
+    __syncwarp();
+    pair_epilogue(M, D, rp, i, k, am, nact, Jk, p0, npl, p0 + p, Bp, Zs, g2s, Xps, Xms, mscale, inv_stab, ek, kT,
+                  escan, phscan, e_kpns, e_X, ph_st, ph_kpn, ph_Y);
+    __syncwarp();
   }
 }
 
 }  // namespace
+
+cudaError_t launch_vertex_epilogue(const ModelDev &M, const MeshDev &D, RateParams rp, int64_t i0, int64_t nkc,
+                                   int64_t pair_base, const double *Cbuf, int Nmax, const int64_t *escan,
+                                   const int64_t *phscan, uint32_t *e_kpns, double2 *e_X, int *ph_st,
+                                   uint32_t *ph_kpn, double *ph_Y, cudaStream_t st) {
+  if (nkc <= 0) return cudaSuccess;
+  const int jmax = M.nb * M.nb * M.nbr;
+  size_t per_warp = size_t(jmax) * sizeof(double2) * 2 + 3 * size_t(jmax) * sizeof(double);
+  per_warp = (per_warp + 15) & ~size_t(15);
+  const size_t smem = per_warp * (kBT / 32);
+  cudaError_t e = cudaFuncSetAttribute(k_vertex_epilogue, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  EPHB_LAUNCH(k_vertex_epilogue, unsigned(nkc), kBT, smem, st, M, D, rp, i0, pair_base, Cbuf, Nmax, escan, phscan,
+              e_kpns, e_X, ph_st, ph_kpn, ph_Y);
+  return cudaGetLastError();
+}
 
 size_t stage_a_T_elems(const ModelDev &M) { return size_t(M.nRgp) * M.nb * M.nb * M.nbr; }
 size_t stage_a_A_elems(const ModelDev &M) { return size_t(M.nRgp) * M.nb * M.nb * M.nbr; }

@@ -1,0 +1,359 @@
+// Tensor-core (tcgen05) form of the R_ph contraction of the vertex (Eq. g^smn_kq):
+//   B[p][m n' a] = sum_Rp e^{i q_p.Rp} A_k[Rp][m n' a]
+// written as a real GEMM C'[p][j'] = sum_r Phi'[p][r] B'[r][j'] with
+//   Phi'[p][r] = (cos, sin)(2 pi q_p.Rp_r) for r < R and R <= r < 2R,
+//   B'(Re columns) = (Re A; -Im A),  B'(Im columns) = (Im A; Re A).
+//
+// Exact fixed-point slicing.  Every operand x in [-1, 1] (the phases as they are, each B'
+// column divided by a power of two sigma_j >= its largest entry) is split as
+//   x = sum_i s_i,  s_i = n_i 2^(-7-8(i-1)),  |n_i| <= 128,
+// so each slice is an exact BF16 number.  A product of two slices is an integer multiple of
+// 2^(-14-8(i+l-2)) below 2^(-8(i+l-2)) in size, and a K = 256 sum of such products (or the
+// two products of the second diagonal) fits the 24-bit FP32 significand: the tensor core
+// computes those diagonals exactly.  FP64-grade mode: 5 slices, products with i + l <= 6,
+// accumulators (i+l = 2), (i+l = 3) and (i+l >= 4); the last one rounds at 2^-24 of a term
+// that is itself below 2^-30 of the result.  Mixed mode: 3 slices, products with
+// i + l <= 4, one FP32 accumulator (about 1e-7 relative).
+//
+// The GEMM runs on 5th-generation tensor cores: operands in shared memory in the
+// no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix), accumulators in
+// tensor memory, one thread issuing tcgen05.mma, completion through tcgen05.commit on an
+// mbarrier, results read back with tcgen05.ld.  All waits are bounded; on expiry the CTA
+// records an error code, still waits (bounded) for its MMAs, frees its tensor memory and
+// returns.
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace ephb {
+
+namespace {
+
+constexpr int kTcM = 128;        // pairs per tile (tensor-memory lanes)
+constexpr int kTcKc = 64;        // K per shared-memory stage (4 MMA K-steps of 16)
+constexpr int kTcThreads = 128;  // 4 warps: one per tensor-memory lane quadrant
+constexpr long kSpinLimit = 400000000L;
+
+__host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// split x in [-1,1] into ns exact BF16 fixed-point slices
+__device__ inline void fixed_slices(double x, int ns, __nv_bfloat16 *out, size_t stride) {
+  double r = x;
+  double scale = 128.0;   // 2^7
+  for (int i = 0; i < ns; ++i) {
+    const double n = rint(r * scale);
+    const double s = n / scale;
+    out[i * stride] = __double2bfloat16(s);
+    r -= s;
+    scale *= 256.0;
+  }
+}
+
+// Phase slices of every q of the phonon mesh: PhiS[q][slice][Kp] (BF16)
+__global__ void k_phase_slices(ModelDev M, MeshDev D, int ns, int Kp, __nv_bfloat16 *phis) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int R = M.nRgp;
+  if (t >= D.nq * int64_t(Kp)) return;
+  const int q = int(t / Kp), r = int(t % Kp);
+  double x = 0.0;
+  if (r < 2 * R) {
+    const int rr = r < R ? r : r - R;
+    int b0, b1, b2;
+    D.qm.unflat(q, b0, b1, b2);
+    const int *Rv = M.Rgp + 3 * rr;
+    const double2 ph = mesh_phase(D.qtab, D.qm, b0, b1, b2, Rv[0], Rv[1], Rv[2]);
+    x = r < R ? ph.x : ph.y;
+  }
+  fixed_slices(x, ns, phis + (size_t(q) * ns) * Kp + r, size_t(Kp));
+}
+
+// B' slices of the k points of a chunk: BS[kc][slice][Nmax][Kp] (BF16) and column scales.
+// One warp per column j' = ml*(2 nb nbr) + part*(nb nbr) + n'*nbr + a.
+__global__ void k_b_slices(ModelDev M, MeshDev D, int64_t i0, int64_t nkc, const double2 *A, int ns, int Kp,
+                           int Nmax, __nv_bfloat16 *bs, double *bscale) {
+  const int64_t w = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= nkc * Nmax) return;
+  const int64_t kc = w / Nmax;
+  const int jp = int(w % Nmax);
+  const int nb = M.nb, nbr = M.nbr, R = M.nRgp;
+  const int nbnbr = nb * nbr;
+  const int jmax = nb * nb * nbr;
+  const int k = D.ibzw_list[i0 + kc];
+  const int nact = __popc(D.amask[k]);
+  const int ml = jp / (2 * nbnbr), part = (jp / nbnbr) & 1, rest = jp % nbnbr;
+  const bool live = ml < nact;
+  const int j = ml * nbnbr + rest;    // column of the stage-A tile
+  const double2 *Ak = A + size_t(kc) * R * jmax;
+  // largest magnitude of the column
+  double mx = 0.0;
+  for (int r = lane; r < 2 * R; r += 32) {
+    if (!live) break;
+    const double2 a = Ak[size_t(r < R ? r : r - R) * jmax + j];
+    const double v = r < R ? (part == 0 ? a.x : a.y) : (part == 0 ? -a.y : a.x);
+    mx = fmax(mx, fabs(v));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  int ex = 0;
+  if (mx > 0.0) {
+    frexp(mx, &ex);          // mx = f 2^ex, f in [0.5, 1): 2^ex >= mx
+  }
+  const double sigma = mx > 0.0 ? ldexp(1.0, ex) : 1.0;
+  if (lane == 0) bscale[kc * Nmax + jp] = sigma;
+  __nv_bfloat16 *dst = bs + (size_t(kc) * ns * Nmax + jp) * Kp;
+  const size_t sstride = size_t(Nmax) * Kp;
+  for (int r = lane; r < Kp; r += 32) {
+    double v = 0.0;
+    if (live && r < 2 * R) {
+      const double2 a = Ak[size_t(r < R ? r : r - R) * jmax + j];
+      v = r < R ? (part == 0 ? a.x : a.y) : (part == 0 ? -a.y : a.x);
+    }
+    fixed_slices(v / sigma, ns, dst + r, sstride);
+  }
+}
+
+// work items of a chunk: (k, 128-pair tile, column chunk); per k: ceil(npl/128) * nchunk(k)
+// (also accumulates the issued tensor-core flops: 2 * 128 * columns * Kp per slice product)
+__global__ void k_tc_items(ModelDev M, MeshDev D, int64_t i0, int64_t nkc, int nc_max, int Kp, int nprod,
+                           int *nitem, unsigned long long *flops) {
+  const int64_t kc = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (kc >= nkc) return;
+  const int64_t i = i0 + kc;
+  const int64_t npl = D.pair_ptr[i + 1] - D.pair_ptr[i];
+  const int nk = round_up(2 * __popc(D.amask[D.ibzw_list[i]]) * M.nb * M.nbr, 16);
+  const int nch = (nk + nc_max - 1) / nc_max;
+  const int ntile = int((npl + kTcM - 1) / kTcM);
+  nitem[kc] = ntile * nch;
+  atomicAdd(flops, 2ull * kTcM * (unsigned long long)nk * Kp * nprod * ntile);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+// shared-memory matrix descriptor: no swizzle, K-major; LBO = K-direction core-matrix stride,
+// SBO = stride between 8-row groups (validated on sm_103a)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= uint64_t((addr & 0x3FFFFu) >> 4);
+  d |= uint64_t((lbo >> 4) & 0x3FFFu) << 16;
+  d |= uint64_t((sbo >> 4) & 0x3FFFu) << 32;
+  d |= uint64_t(1) << 46;
+  return d;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+  uint32_t done = 0;
+  for (long it = 0; it < kSpinLimit && !done; ++it)
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done) : "r"(mbar), "r"(phase) : "memory");
+  return done != 0;
+}
+
+// core-matrix offset (bytes) of element (row, k) in a [rows x kTcKc] K-major tile
+__device__ __forceinline__ uint32_t core_off(int row, int kgroup) {
+  return uint32_t(((row >> 3) * (kTcKc / 8) + kgroup) * 128 + (row & 7) * 16);
+}
+
+struct TcParams {
+  int ns, nacc, Kp, Nmax, nc_max;
+  int64_t i0, nkc, pair_base;   // first pair of the chunk
+};
+
+template <int NS, int NACC>
+__global__ void __launch_bounds__(kTcThreads, 1) k_vertex_gemm(ModelDev M, MeshDev D, TcParams P,
+                                                               const int64_t *__restrict__ item_ptr,
+                                                               const __nv_bfloat16 *__restrict__ phis,
+                                                               const __nv_bfloat16 *__restrict__ bs,
+                                                               const double *__restrict__ bscale, double *Cbuf,
+                                                               int *err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // which (k, tile, column chunk)
+  const int64_t item = blockIdx.x;
+  int64_t lo = 0, hi = P.nkc;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (item_ptr[mid] <= item) lo = mid; else hi = mid;
+  }
+  const int64_t kc = lo;
+  const int64_t i = P.i0 + kc;
+  const int k = D.ibzw_list[i];
+  const int nb = M.nb, nbr = M.nbr;
+  const int nk = round_up(2 * __popc(D.amask[k]) * nb * nbr, 16);
+  const int nch = (nk + P.nc_max - 1) / P.nc_max;
+  const int nc = round_up((nk + nch - 1) / nch, 16);        // balanced chunk width
+  const int64_t local = item - item_ptr[kc];
+  const int tile = int(local / nch), chunk = int(local % nch);
+  const int n0 = chunk * nc;
+  const int ncw = nk - n0 < nc ? nk - n0 : nc;              // columns of this chunk (multiple of 16)
+  const int64_t p0 = D.pair_ptr[i];
+  const int64_t npl = D.pair_ptr[i + 1] - p0;
+  const int64_t t0 = int64_t(tile) * kTcM;
+  const int npt = int(npl - t0 < kTcM ? npl - t0 : kTcM);
+
+  unsigned char *sA = smem;                                   // NS x [128 x Kc]
+  unsigned char *sB = smem + size_t(NS) * kTcM * kTcKc * 2;   // NS x [nc_max x Kc]
+  const size_t a_slice = size_t(kTcM) * kTcKc * 2, b_slice = size_t(P.nc_max) * kTcKc * 2;
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  const uint32_t ncols_alloc = NACC * nc <= 32 ? 32u : (NACC * nc <= 64 ? 64u : (NACC * nc <= 128 ? 128u :
+                               (NACC * nc <= 256 ? 256u : 512u)));
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(&tslot)),
+                 "r"(ncols_alloc));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t taddr = tslot;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(ncw >> 3) << 17) | (uint32_t(kTcM >> 4) << 24);
+  const int q_row = tid < npt ? D.pair_q[p0 + t0 + tid] : -1;
+  const __nv_bfloat16 *bsk = bs + size_t(kc) * NS * P.Nmax * P.Kp;
+  bool ok = true;
+  uint32_t phase = 0;
+  for (int kb = 0; kb < P.Kp; kb += kTcKc) {
+    // stage the A rows (gathered phase slices) and the B rows of this K block
+    for (int s = 0; s < NS; ++s) {
+      unsigned char *dst = sA + s * a_slice;
+      const uint4 *src = q_row >= 0 ? reinterpret_cast<const uint4 *>(phis + (size_t(q_row) * NS + s) * P.Kp + kb)
+                                    : nullptr;
+      for (int g = 0; g < kTcKc / 8; ++g) {
+        const uint4 v = src ? src[g] : make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4 *>(dst + core_off(tid, g)) = v;
+      }
+    }
+    for (int t = tid; t < NS * ncw * (kTcKc / 8); t += kTcThreads) {
+      const int s = t / (ncw * (kTcKc / 8));
+      const int rem = t % (ncw * (kTcKc / 8));
+      const int row = rem / (kTcKc / 8), g = rem % (kTcKc / 8);
+      const uint4 v = reinterpret_cast<const uint4 *>(bsk + (size_t(s) * P.Nmax + n0 + row) * P.Kp + kb)[g];
+      *reinterpret_cast<uint4 *>(sB + s * b_slice + core_off(row, g)) = v;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      for (int is = 0; is < NS; ++is)
+        for (int ls = 0; ls + is < NS + 1 - 0 && ls < NS; ++ls) {
+          const int d = is + ls;                  // diagonal (0-based: slices is, ls)
+          if (d > NS - 1) continue;               // products with i + l <= NS + 1
+          const int acc = NACC == 1 ? 0 : (d < NACC - 1 ? d : NACC - 1);
+          const uint32_t dtm = taddr + uint32_t(acc * nc);
+          for (int ks = 0; ks < kTcKc / 16; ++ks) {
+            const uint64_t ad = smem_desc(smem_u32(sA + is * a_slice) + ks * 256, 128u, (kTcKc / 8) * 128u);
+            const uint64_t bd = smem_desc(smem_u32(sB + ls * b_slice) + ks * 256, 128u, (kTcKc / 8) * 128u);
+            // the first product into each accumulator (first K block, first K step) overwrites it
+            const bool first = kb == 0 && ks == 0 &&
+                               (NACC == 1 ? (is == 0 && ls == 0) :
+                                (acc < NACC - 1 ? (is == 0) : (is == 0 && ls == NACC - 1)));
+            const uint32_t en = first ? 0u : 1u;
+            asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                         :: "r"(dtm), "l"(ad), "l"(bd), "r"(idesc), "r"(en));
+          }
+        }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   :: "r"(smem_u32(&mbar)) : "memory");
+    }
+    // the MMAs read the staged operands: wait before overwriting them (the block agrees on
+    // the outcome, so a timeout leaves the loop on every thread together)
+    const bool waited = mbar_wait(smem_u32(&mbar), phase);
+    if (!__syncthreads_and(waited ? 1 : 0)) {
+      ok = false;
+      break;
+    }
+    phase ^= 1u;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (!ok) {
+    atomicExch(err, 1);
+    mbar_wait(smem_u32(&mbar), phase);   // bounded second wait for the MMAs in flight
+  } else {
+    // accumulators -> FP64 combination -> C'[pair][n0 + j]
+    const int row = warp * 32 + lane;
+    const double *sc = bscale + kc * P.Nmax + n0;
+    double *crow = Cbuf + (p0 + t0 + row - P.pair_base) * P.Nmax + n0;
+    for (int c0 = 0; c0 < ncw; c0 += 16) {
+      double sum[16];
+      for (int j = 0; j < 16; ++j) sum[j] = 0.0;
+      for (int a = 0; a < NACC; ++a) {
+        uint32_t v[16];
+        const uint32_t ta = taddr + (uint32_t(warp * 32) << 16) + uint32_t(a * nc + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(ta));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        for (int j = 0; j < 16; ++j) sum[j] += double(__uint_as_float(v[j]));
+      }
+      if (row < npt)
+        for (int j = 0; j < 16; ++j) crow[c0 + j] = sc[c0 + j] * sum[j];
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(ncols_alloc));
+}
+
+}  // namespace
+
+int tc_kp(const ModelDev &M) { return round_up(2 * M.nRgp, kTcKc); }
+int tc_nmax(const ModelDev &M) { return round_up(2 * M.nb * M.nb * M.nbr, 16); }
+int tc_nc_max(int ns) { return ns == 5 ? 160 : 256; }
+size_t tc_smem_bytes(int ns) { return size_t(ns) * kTcM * kTcKc * 2 + size_t(ns) * tc_nc_max(ns) * kTcKc * 2; }
+
+cudaError_t launch_phase_slices(const ModelDev &M, const MeshDev &D, int ns, __nv_bfloat16 *phis, cudaStream_t st) {
+  const int Kp = tc_kp(M);
+  const int64_t n = D.nq * int64_t(Kp);
+  EPHB_LAUNCH(k_phase_slices, unsigned((n + 255) / 256), 256, 0, st, M, D, ns, Kp, phis);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_t i0, int64_t nkc, int64_t pair_base,
+                             const double2 *A, const __nv_bfloat16 *phis, __nv_bfloat16 *bs, double *bscale,
+                             int *nitem, int64_t *item_ptr, int64_t *scratch, int64_t scratch_elems,
+                             int64_t *total_dev, double *Cbuf, int *err, cudaStream_t st) {
+  if (nkc <= 0) return cudaSuccess;
+  const int Kp = tc_kp(M), Nmax = tc_nmax(M), ncm = tc_nc_max(ns);
+  const int64_t nw = nkc * Nmax;
+  EPHB_LAUNCH(k_b_slices, unsigned((nw * 32 + 255) / 256), 256, 0, st, M, D, i0, nkc, A, ns, Kp, Nmax, bs, bscale);
+  const int nprod = ns * (ns + 1) / 2;
+  EPHB_LAUNCH(k_tc_items, unsigned((nkc + 255) / 256), 256, 0, st, M, D, i0, nkc, ncm, Kp, nprod, nitem,
+              reinterpret_cast<unsigned long long *>(total_dev + 1));
+  cudaError_t e = exclusive_scan<int>(nitem, item_ptr, nkc, total_dev, scratch, scratch_elems, st);
+  if (e != cudaSuccess) return e;
+  int64_t nitems = 0;
+  e = cudaMemcpyAsync(&nitems, total_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess || nitems == 0) return e;
+  TcParams P;
+  P.ns = ns;
+  P.nacc = ns == 5 ? 3 : 1;
+  P.Kp = Kp;
+  P.Nmax = Nmax;
+  P.nc_max = ncm;
+  P.i0 = i0;
+  P.nkc = nkc;
+  P.pair_base = pair_base;
+  const size_t smem = tc_smem_bytes(ns);
+  if (ns == 5) {
+    e = cudaFuncSetAttribute(k_vertex_gemm<5, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    EPHB_LAUNCH((k_vertex_gemm<5, 3>), unsigned(nitems), kTcThreads, smem, st, M, D, P, item_ptr, phis, bs, bscale,
+                Cbuf, err);
+  } else {
+    e = cudaFuncSetAttribute(k_vertex_gemm<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    EPHB_LAUNCH((k_vertex_gemm<3, 1>), unsigned(nitems), kTcThreads, smem, st, M, D, P, item_ptr, phis, bs, bscale,
+                Cbuf, err);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ephb

@@ -196,3 +196,35 @@ def test_call_order_and_arguments():
     info = B.solve_coupled_bte(ctx, "dragged", 1e-14, max_outer=2, max_inner=3, allow_noconv=True)
     assert info["status"] == B.ENOCONV and info["converged"] == 0
     ctx.close()
+
+
+# ----------------------------------------------------------------- tensor-core contraction
+# FP64-grade slicing must meet the FP64 tolerances; the 3-slice mixed mode is held to 1e-5
+# (its error, ~1e-7, is reported by the benchmark per coefficient).
+MIXED_RTOL = 1e-5
+
+
+@pytest.mark.parametrize("mode", ["fp64-sliced", "split-bf16"])
+def test_tensor_core_contraction(case, mode):
+    wl, P, R, ctx = case["wl"], case["P"], case["R"], case["ctx"]
+    info = B.compute_transition_rates(ctx, wl.T_K, wl.mu_eV, wl.sigma_eV, wl.cutoff_sigmas,
+                                      precision=B.PRECISIONS[mode])
+    assert info["n_entries"] == len(R.Xp)
+    assert info["tensor_flops"] > 0
+    gpu = gpu_rate_table(ctx, wl)
+    ora = oracle_rate_table(R)
+    if mode == "fp64-sliced":
+        compare_rates(gpu, ora, P)
+    else:
+        xmax = max(max(abs(v[0]), abs(v[1])) for v in ora.values())
+        worst = max(max(abs(gpu[k][0] - v[0]), abs(gpu[k][1] - v[1])) / max(abs(v[0]) + abs(v[1]), 1e-6 * xmax)
+                    for k, v in ora.items())
+        assert worst <= MIXED_RTOL, f"mixed-precision rate error {worst:.3e}"
+    caps = CAPS.get(case["name"], {})
+    ref = O.solve_coupled_bte(P, R, level="dragged", **caps)
+    B.solve_coupled_bte(ctx, "dragged", wl.tol, allow_noconv=bool(caps), **caps)
+    got = B.transport_coefficients(ctx)
+    tol = COEFF_RTOL if mode == "fp64-sliced" else MIXED_RTOL
+    for key in TENSORS:
+        err = rel_fro(got[key], ref.coeffs[key])
+        assert err <= tol, f"{mode} {key}: {err:.3e}"
