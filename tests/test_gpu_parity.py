@@ -187,7 +187,7 @@ def test_call_order_and_arguments():
     assert e.value.status == B.EINVAL
     B.build_meshes_ibz(ctx, wl.kmesh, wl.qmesh, wl.window)
     with pytest.raises(B.EphbError) as e:
-        B.compute_transition_rates(ctx, wl.T_K, wl.mu_eV, precision=B.SPLIT_BF16)
+        B.compute_transition_rates(ctx, wl.T_K, wl.mu_eV, precision=B.SPLIT_TF32)
     assert e.value.status == B.EINVAL
     with pytest.raises(B.EphbError) as e:
         B.solve_coupled_bte(ctx)
