@@ -561,7 +561,7 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
   CK(tb.init());
   CK(tc.init());
   const bool tensor = precision != EPHB_FP64;
-  const int ns = precision == EPHB_FP64_SLICED ? 5 : 3;
+  const int ns = precision == EPHB_FP64_SLICED ? 7 : 3;
   std::vector<int64_t> hpp;
   int Nmax = 0;
   const int64_t kMaxChunkPairs = 1 << 20;   // bound of the contraction scratch (pairs x Nmax doubles)

@@ -10,10 +10,12 @@
 // so each slice is an exact BF16 number.  A product of two slices is an integer multiple of
 // 2^(-14-8(i+l-2)) below 2^(-8(i+l-2)) in size, and a K = 256 sum of such products (or the
 // two products of the second diagonal) fits the 24-bit FP32 significand: the tensor core
-// computes those diagonals exactly.  FP64-grade mode: 5 slices, products with i + l <= 6,
-// accumulators (i+l = 2), (i+l = 3) and (i+l >= 4); the last one rounds at 2^-24 of a term
-// that is itself below 2^-30 of the result.  Mixed mode: 3 slices, products with
-// i + l <= 4, one FP32 accumulator (about 1e-7 relative).
+// computes those diagonals exactly.  FP64-grade mode: 7 slices (inputs to 2^-55 of the
+// column scale, which the Fourier sums need because they cancel: a result 1e-3 of its
+// column scale keeps ~1e-14 relative accuracy), the 28 products with i + l <= 8,
+// accumulators (i+l = 2), (i+l = 3) and (i+l >= 4); the last one rounds at 2^-24 of a sum
+// that is itself below 2^-14 of the column scale.  Mixed mode: 3 slices, products with
+// i + l <= 4, one FP32 accumulator.
 //
 // The GEMM runs on 5th-generation tensor cores: operands in shared memory in the
 // no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix), accumulators in
@@ -305,7 +307,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vertex_gemm(ModelDev M, MeshD
 
 int tc_kp(const ModelDev &M) { return round_up(2 * M.nRgp, kTcKc); }
 int tc_nmax(const ModelDev &M) { return round_up(2 * M.nb * M.nb * M.nbr, 16); }
-int tc_nc_max(int ns) { return ns == 5 ? 160 : 256; }
+int tc_nc_max(int ns) { return ns == 7 ? 96 : 256; }
 size_t tc_smem_bytes(int ns) { return size_t(ns) * kTcM * kTcKc * 2 + size_t(ns) * tc_nc_max(ns) * kTcKc * 2; }
 
 cudaError_t launch_phase_slices(const ModelDev &M, const MeshDev &D, int ns, __nv_bfloat16 *phis, cudaStream_t st) {
@@ -334,7 +336,7 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
   if (e != cudaSuccess || nitems == 0) return e;
   TcParams P;
   P.ns = ns;
-  P.nacc = ns == 5 ? 3 : 1;
+  P.nacc = ns == 7 ? 3 : 1;
   P.Kp = Kp;
   P.Nmax = Nmax;
   P.nc_max = ncm;
@@ -342,10 +344,10 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
   P.nkc = nkc;
   P.pair_base = pair_base;
   const size_t smem = tc_smem_bytes(ns);
-  if (ns == 5) {
-    e = cudaFuncSetAttribute(k_vertex_gemm<5, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (ns == 7) {
+    e = cudaFuncSetAttribute(k_vertex_gemm<7, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    EPHB_LAUNCH((k_vertex_gemm<5, 3>), unsigned(nitems), kTcThreads, smem, st, M, D, P, item_ptr, phis, bs, bscale,
+    EPHB_LAUNCH((k_vertex_gemm<7, 3>), unsigned(nitems), kTcThreads, smem, st, M, D, P, item_ptr, phis, bs, bscale,
                 Cbuf, err);
   } else {
     e = cudaFuncSetAttribute(k_vertex_gemm<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
