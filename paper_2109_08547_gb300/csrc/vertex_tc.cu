@@ -13,9 +13,11 @@
 // computes those diagonals exactly.  FP64-grade mode: 7 slices (inputs to 2^-55 of the
 // column scale, which the Fourier sums need because they cancel: a result 1e-3 of its
 // column scale keeps ~1e-14 relative accuracy), the 28 products with i + l <= 8,
-// accumulators (i+l = 2), (i+l = 3) and (i+l >= 4); the last one rounds at 2^-24 of a sum
-// that is itself below 2^-14 of the column scale.  Mixed mode: 3 slices, products with
-// i + l <= 4, one FP32 accumulator.
+// accumulators (i+l = 2), (i+l = 3), (i+l = 4) -- each summed exactly -- and (i+l >= 5),
+// which rounds at 2^-24 of a sum that is itself below 2^-22 of the column scale.  (With the
+// third diagonal merged into the tail, its rounding, ~2^-40 of the column scale, showed up as
+// 1e-8 relative errors on the smallest rates.)  Mixed mode: 3 slices, the 6 products with
+// i + l <= 4, accumulators (i+l = 2) (exact) and (i+l >= 3).
 //
 // The GEMM runs on 5th-generation tensor cores: operands in shared memory in the
 // no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix), accumulators in
@@ -336,7 +338,7 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
   if (e != cudaSuccess || nitems == 0) return e;
   TcParams P;
   P.ns = ns;
-  P.nacc = ns == 7 ? 3 : 1;
+  P.nacc = ns == 7 ? 4 : 2;
   P.Kp = Kp;
   P.Nmax = Nmax;
   P.nc_max = ncm;
@@ -345,14 +347,14 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
   P.pair_base = pair_base;
   const size_t smem = tc_smem_bytes(ns);
   if (ns == 7) {
-    e = cudaFuncSetAttribute(k_vertex_gemm<7, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    e = cudaFuncSetAttribute(k_vertex_gemm<7, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    EPHB_LAUNCH((k_vertex_gemm<7, 3>), unsigned(nitems), kTcThreads, smem, st, M, D, P, item_ptr, phis, bs, bscale,
+    EPHB_LAUNCH((k_vertex_gemm<7, 4>), unsigned(nitems), kTcThreads, smem, st, M, D, P, item_ptr, phis, bs, bscale,
                 Cbuf, err);
   } else {
-    e = cudaFuncSetAttribute(k_vertex_gemm<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    e = cudaFuncSetAttribute(k_vertex_gemm<3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    EPHB_LAUNCH((k_vertex_gemm<3, 1>), unsigned(nitems), kTcThreads, smem, st, M, D, P, item_ptr, phis, bs, bscale,
+    EPHB_LAUNCH((k_vertex_gemm<3, 2>), unsigned(nitems), kTcThreads, smem, st, M, D, P, item_ptr, phis, bs, bscale,
                 Cbuf, err);
   }
   return cudaGetLastError();
