@@ -32,6 +32,9 @@ UNIT = "transition rates/s"
 # FP64 FMA throughput of the GB300s, measured with `bench.py --fp64-peak`
 # (profiles/fp64_peak_gb300.txt); the nominal figure is 1.25 TFLOP/s.
 FP64_PEAK_TFLOPS = 1.188  # lower of two measurements (1.188, 1.255)
+# arithmetic of the vertex contraction per precision mode (everything else is FP64)
+DTYPES = {"fp64": "f64", "fp64-sliced": "f64 (tcgen05 bf16 x7 exact fixed-point slices, f32 accumulate)",
+          "split-bf16": "bf16 x3 slices, f32 accumulate (mixed)"}
 
 
 def parse():
@@ -43,6 +46,9 @@ def parse():
     p.add_argument("--n", type=int, default=24, help="k and q mesh size per dimension")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--precision", default="fp64-sliced", choices=["fp64", "fp64-sliced", "split-bf16"],
+                   help="vertex contraction: FP64 CUDA cores, FP64-grade tensor-core slices, or mixed precision")
+    p.add_argument("--no-variants", action="store_true", help="skip the one-step timings of the other precisions")
     p.add_argument("--fp64-peak", action="store_true",
                    help="measure FP64 and FP32 FMA throughput with a small probe kernel and exit")
     return p.parse_args()
@@ -270,8 +276,10 @@ def main():
     B.set_wannier_model(ctx, wl.model)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
 
-    def step():
-        return B.run_path(ctx, wl, level="dragged", ko_correction=True)
+    prec = B.PRECISIONS[args.precision]
+
+    def step(p=prec):
+        return B.run_path(ctx, wl, level="dragged", ko_correction=True, precision=p)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -308,9 +316,12 @@ def main():
 
     # dominant kernel and its roofline (device time measured with CUDA events in this run)
     ms_b = statistics.mean(r.rates["ms_stage_b"] for r in results)
+    ms_ep = statistics.mean(r.rates["ms_epilogue"] for r in results)
     ms_e = statistics.mean(r.solve["ms_e_sweep"] for r in results)
     peaks = measured_peaks()
-    if ms_b >= ms_e:
+    step_ms = 1e3 * el_max / args.steps
+    dominant = max((("stage_b", ms_b), ("epilogue", ms_ep), ("e_sweep", ms_e)), key=lambda x: x[1])[0]
+    if dominant == "stage_b" and args.precision == "fp64":
         achieved = r0.rates["stage_b_flops"] / (ms_b * 1e-3) / 1e12
         tr = profile_traffic("stage_b_rates", "vertex.cu")
         roof = {"kernel": "k_stage_b_rates (R_ph contraction + rotations + rates, FP64)", "bound": "alu",
@@ -318,7 +329,25 @@ def main():
                 "frac": achieved / FP64_PEAK_TFLOPS,
                 "peak_source": "measured FP64 FMA rate (bench.py --fp64-peak, profiles/fp64_peak_gb300.txt)",
                 "traffic": (tr[0] * r0.rates["n_pairs"]) if tr else None,
-                "ms_per_step": ms_b, "share_of_step": ms_b / (1e3 * el_max / args.steps)}
+                "ms_per_step": ms_b, "share_of_step": ms_b / step_ms}
+    elif dominant == "stage_b":
+        # tensor-core contraction: the MMA work the slicing issues, against the measured BF16 peak
+        pk = peaks.get("bf16_tflops", 1900.0)
+        achieved = r0.rates["tensor_flops"] / (ms_b * 1e-3) / 1e12
+        tr = profile_traffic("vertex_gemm", "vertex_tc.cu")
+        roof = {"kernel": f"k_vertex_gemm (tcgen05 R_ph contraction, {args.precision})", "bound": "tensor",
+                "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured burst)" if "bf16_tflops" in peaks
+                else "fallback", "traffic": (tr[0] * r0.rates["n_pairs"]) if tr else None,
+                "algorithmic_tflops": r0.rates["stage_b_flops"] / (ms_b * 1e-3) / 1e12,
+                "ms_per_step": ms_b, "share_of_step": ms_b / step_ms}
+    elif dominant == "epilogue":
+        achieved = r0.rates["rot_flops"] / (ms_ep * 1e-3) / 1e12
+        roof = {"kernel": "k_vertex_epilogue (rotations, |g|^2, occupations, delta, writes; FP64)", "bound": "alu",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "measured FP64 FMA rate (bench.py --fp64-peak, profiles/fp64_peak_gb300.txt)",
+                "traffic": None, "ms_per_step": ms_ep, "share_of_step": ms_ep / step_ms}
     else:
         nsw = r0.solve["n_sweeps"]
         achieved = r0.solve["e_sweep_bytes"] * nsw / (ms_e * 1e-3) / 1e9
@@ -328,7 +357,7 @@ def main():
                 "unit": "GB/s", "frac": achieved / pk,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback",
                 "traffic": (tr[0] * r0.rates["n_entries"]) if tr else None,
-                "ms_per_step": ms_e, "share_of_step": ms_e / (1e3 * el_max / args.steps)}
+                "ms_per_step": ms_e, "share_of_step": ms_e / step_ms}
 
     # end-to-end through the C ABI with host buffers: model H2D (pinned) + path + coefficients D2H
     e2e = None
@@ -351,7 +380,7 @@ def main():
         for _ in range(args.steps):
             flush.zero_()
             B.set_wannier_model(ctx2, mp)
-            rr = B.run_path(ctx2, wl, level="dragged", ko_correction=True)
+            rr = B.run_path(ctx2, wl, level="dragged", ko_correction=True, precision=prec)
             tup += rr.rates["n_tuples"]
         torch.cuda.synchronize()
         barrier()
@@ -365,6 +394,30 @@ def main():
                "d2h_bytes_per_step": 8 * 9 * 8, "s_per_step": float(e2_t.item()) / args.steps}
         ctx2.close()
 
+    # one step of each other precision of the vertex contraction: time to converged
+    # coefficients and each coefficient's relative (Frobenius) difference from this run's
+    # result (which itself matches the FP64 oracle to 1e-8 in the parity tests)
+    variants = {}
+    if not args.no_variants:
+        for name, p in B.PRECISIONS.items():
+            if name == args.precision:
+                continue
+            flush.zero_()
+            step(p)                       # warm-up of this mode
+            flush.zero_()
+            torch.cuda.synchronize()
+            tv = time.perf_counter()
+            rv = step(p)
+            torch.cuda.synchronize()
+            sv = time.perf_counter() - tv
+            err = {}
+            for key, ref in r0.coeffs.items():
+                nrm = float(np.linalg.norm(ref))
+                err[key] = float(np.linalg.norm(rv.coeffs[key] - ref) / nrm) if nrm > 0 else 0.0
+            variants[name] = {"s_to_converged": sv, "value": rv.rates["n_tuples"] / sv,
+                              "rates_ms": rv.rates["ms"], "stage_b_ms": rv.rates["ms_stage_b"],
+                              "coeff_rel_err": err}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nt, dt, row = oracle_sample(wl)
@@ -376,18 +429,20 @@ def main():
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
             "config": {"workload": wl.name, "model": "4-band/6-branch CsCl-type cubic, 5^3 x 5^3 R grids (g 24 MB)",
                        "kmesh": list(wl.kmesh), "qmesh": list(wl.qmesh), "T_K": wl.T_K, "mu_eV": wl.mu_eV,
                        "window_eV": list(wl.window), "sigma_eV": wl.sigma_eV, "level": "dragged+KO",
-                       "tol": wl.tol, "l2": "256 MB buffer written before every step",
+                       "tol": wl.tol, "precision": args.precision, "l2": "256 MB buffer written before every step",
                        "parallelism": f"replicas x{world}", "tuples_per_step": r0.rates["n_tuples"],
                        "entries": r0.rates["n_entries"], "pairs": r0.rates["n_pairs"]},
             "s_to_converged": 1e-3 * el_max / args.steps,
             "phases_ms": {"rates": r0.rates["ms"], "stage_a": r0.rates["ms_stage_a"],
-                          "stage_b": r0.rates["ms_stage_b"], "solve": r0.solve["ms"],
-                          "e_sweeps": r0.solve["ms_e_sweep"], "ph_sweeps": r0.solve["ms_ph_sweep"],
+                          "stage_b": r0.rates["ms_stage_b"], "rate_epilogue": r0.rates["ms_epilogue"],
+                          "solve": r0.solve["ms"], "e_sweeps": r0.solve["ms_e_sweep"],
+                          "drag_terms": r0.solve["ms_drag"], "ph_sweeps": r0.solve["ms_ph_sweep"],
                           "n_sweeps": r0.solve["n_sweeps"], "outer_iters": r0.solve["outer_iters"]},
+            "variants": variants,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(out))

@@ -163,6 +163,7 @@ typedef struct {
   double stage_b_flops;        /* algorithmic flops of the R_ph contraction + rotations    */
   double ms_epilogue;          /* tensor-core modes: device time of the rotation/rate kernel */
   double tensor_flops;         /* tensor-core modes: flops issued as tcgen05.mma           */
+  double rot_flops;            /* algorithmic flops of the band and branch rotations       */
 } ephb_rates_info;
 
 ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst, int ninst,

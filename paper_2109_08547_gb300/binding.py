@@ -69,7 +69,7 @@ class RatesInfoC(C.Structure):
     _fields_ = [("n_tuples", C.c_int64), ("n_entries", C.c_int64), ("n_ph_entries", C.c_int64),
                 ("n_pairs", C.c_int64), ("ms", C.c_double), ("ms_stage_a", C.c_double), ("ms_stage_b", C.c_double),
                 ("stage_a_flops", C.c_double), ("stage_b_flops", C.c_double), ("ms_epilogue", C.c_double),
-                ("tensor_flops", C.c_double)]
+                ("tensor_flops", C.c_double), ("rot_flops", C.c_double)]
 
 
 class SolveOptsC(C.Structure):

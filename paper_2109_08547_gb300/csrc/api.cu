@@ -522,7 +522,7 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
   CK(ctx->cntPh.ensure(np * nbr));
   CK(ctx->escan.ensure(np * nb));
   CK(ctx->phscan.ensure(np * nbr));
-  CK(ctx->ucount.ensure(4));
+  CK(ctx->ucount.ensure(8));
   MeshDev D = mesh_view(ctx);
   CK(launch_rate_count(M, D, rp, ctx->cntE.p, ctx->cntPh.p, ctx->ucount.p, st));
   int64_t big = np * (nb > nbr ? nb : nbr);
@@ -625,7 +625,7 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     if (herr) return fail(ctx, EPHB_ETIMEOUT, "a tensor-core wait gave up (vertex contraction)");
     tensor_flops = double(tfl);
   }
-  unsigned long long cnt[4];
+  unsigned long long cnt[5];
   CK(cudaMemcpyAsync(cnt, ctx->ucount.p, sizeof(cnt), cudaMemcpyDeviceToHost, st));
   CK(cudaEventRecord(ev1, st));
   CK(cudaEventSynchronize(ev1));
@@ -646,6 +646,7 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     out->stage_b_flops = double(cnt[2]);
     out->ms_epilogue = tc.ms;
     out->tensor_flops = tensor_flops;
+    out->rot_flops = double(cnt[4]);
   }
   ctx->stage = 3;
   ctx->bte_ready = false;

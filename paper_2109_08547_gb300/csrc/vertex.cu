@@ -42,7 +42,7 @@ __device__ inline double gauss_d(double x, double sigma, double cut) {
 __global__ void k_rate_count(ModelDev M, MeshDev D, RateParams rp, int *cntE, int *cntPh,
                              unsigned long long *n_tuples) {
   int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  unsigned long long nt = 0, fl = 0, ns = 0;
+  unsigned long long nt = 0, fl = 0, ns = 0, rf = 0;
   if (p < D.n_pairs) {
     const int nb = M.nb, nbr = M.nbr;
     int i = D.pair_i[p], q = D.pair_q[p];
@@ -55,6 +55,7 @@ __global__ void k_rate_count(ModelDev M, MeshDev D, RateParams rp, int *cntE, in
     const unsigned long long na = __popc(am), nap = __popc(an);
     fl = 8ull * (na * nb * nbr * (unsigned long long)M.nRgp + na * nb * nbr * nbr + na * nap * nb * nbr);
     if (pl == 0) ns = na;
+    rf = 8ull * (na * nb * nbr * nbr + na * nap * nb * nbr);   // rotations only
     const double *ek = D.eps + size_t(k) * nb, *ekp = D.eps + size_t(kp) * nb, *wq = D.w + size_t(q) * nbr;
     for (int m = 0; m < nb; ++m) {
       int c = 0;
@@ -90,11 +91,13 @@ __global__ void k_rate_count(ModelDev M, MeshDev D, RateParams rp, int *cntE, in
   for (int o = 16; o > 0; o >>= 1) {
     nt += __shfl_down_sync(0xffffffffu, nt, o);
     fl += __shfl_down_sync(0xffffffffu, fl, o);
+    rf += __shfl_down_sync(0xffffffffu, rf, o);
     ns += __shfl_down_sync(0xffffffffu, ns, o);
   }
   if ((threadIdx.x & 31) == 0) {
     if (nt) atomicAdd(n_tuples, nt);
     if (fl) atomicAdd(n_tuples + 2, fl);
+    if (rf) atomicAdd(n_tuples + 4, rf);
     if (ns) atomicAdd(n_tuples + 3, ns);
   }
 }
@@ -488,7 +491,7 @@ size_t stage_a_A_elems(const ModelDev &M) { return size_t(M.nRgp) * M.nb * M.nb 
 cudaError_t launch_rate_count(const ModelDev &M, const MeshDev &D, RateParams rp, int *cntE, int *cntPh,
                               unsigned long long *n_tuples, cudaStream_t st) {
   // counters: [0] tuples, [2] stage-B flops, [3] active states in irreducible rows
-  cudaError_t e = cudaMemsetAsync(n_tuples, 0, 4 * sizeof(unsigned long long), st);
+  cudaError_t e = cudaMemsetAsync(n_tuples, 0, 5 * sizeof(unsigned long long), st);
   if (e != cudaSuccess || D.n_pairs == 0) return e;
   EPHB_LAUNCH(k_rate_count, unsigned((D.n_pairs + 127) / 128), 128, 0, st, M, D, rp, cntE, cntPh, n_tuples);
   return cudaGetLastError();
