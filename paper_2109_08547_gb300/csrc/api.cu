@@ -115,6 +115,8 @@ struct ephb_ctx {
   DBuf<double> bscale, Cbuf;
   DBuf<int> nitem, tc_err;
   DBuf<int64_t> item_ptr;
+  DBuf<double> fk, nbq, wr;
+  DBuf<double2> ut;
   DBuf<double> ph_Y;
 
   // BTE
@@ -282,7 +284,8 @@ void ephb_destroy(ephb_ctx *ctx) {
   ctx->row_ptr.release(); ctx->ph_row_ptr.release(); ctx->e_kpns.release(); ctx->ph_kpn.release();
   ctx->e_X.release(); ctx->Tbuf.release(); ctx->Abuf.release(); ctx->ph_Y.release();
   ctx->phis.release(); ctx->bslices.release(); ctx->bscale.release(); ctx->Cbuf.release(); ctx->nitem.release();
-  ctx->tc_err.release(); ctx->item_ptr.release();
+  ctx->tc_err.release(); ctx->item_ptr.release(); ctx->fk.release(); ctx->nbq.release(); ctx->wr.release();
+  ctx->ut.release();
   ctx->st_eps.release(); ctx->st_vel.release(); ctx->st_ff.release(); ctx->st_wt.release(); ctx->W_e.release();
   ctx->inv_ffW.release(); ctx->I0.release(); ctx->J0.release(); ctx->I.release(); ctx->J.release();
   ctx->I2.release(); ctx->J2.release(); ctx->Bt.release(); ctx->W_ph.release(); ctx->inv_nnW.release();
@@ -583,6 +586,12 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     CK(cudaMemsetAsync(ctx->tc_err.p, 0, sizeof(int), st));
     CK(cudaMemsetAsync(ctx->scal.p + 7, 0, sizeof(int64_t), st));
     CK(ctx->scratch.ensure(scan_scratch_elems(chunk > big ? chunk : big)));
+    // occupation / prefactor / eigenvector tables of the rate epilogue
+    CK(ctx->fk.ensure(size_t(ctx->km.size()) * nb));
+    CK(ctx->nbq.ensure(size_t(nq) * nbr));
+    CK(ctx->wr.ensure(size_t(nq) * nbr));
+    CK(ctx->ut.ensure(size_t(nq) * nbr * nbr));
+    CK(launch_epi_tables(M, D, rp.T, rp.mu, ctx->fk.p, ctx->nbq.p, ctx->wr.p, ctx->ut.p, st));
   }
   for (int64_t i0 = 0; i0 < ctx->n_ibzw;) {
     int64_t nkc = ctx->n_ibzw - i0 < chunk ? ctx->n_ibzw - i0 : chunk;
@@ -605,8 +614,9 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
                           ctx->Cbuf.p, ctx->tc_err.p, st));
       CK(tb.stop(st));
       CK(tc.start(st));
-      CK(launch_vertex_epilogue(M, D, rp, i0, nkc, hpp[i0], ctx->Cbuf.p, Nmax, ctx->escan.p, ctx->phscan.p,
-                                ctx->e_kpns.p, ctx->e_X.p, ctx->ph_st.p, ctx->ph_kpn.p, ctx->ph_Y.p, st));
+      CK(launch_vertex_epilogue(M, D, rp, hpp[i0], hpp[i0 + nkc], hpp[i0], ctx->Cbuf.p, Nmax, ctx->fk.p,
+                                ctx->nbq.p, ctx->wr.p, ctx->ut.p, ctx->escan.p, ctx->phscan.p, ctx->e_kpns.p,
+                                ctx->e_X.p, ctx->ph_st.p, ctx->ph_kpn.p, ctx->ph_Y.p, st));
       CK(tc.stop(st));
     }
     CK(cudaStreamSynchronize(st));

@@ -92,9 +92,15 @@ cudaError_t launch_stage_b_rates(const ModelDev &M, const MeshDev &D, RateParams
                                  double2 *e_X, int *ph_st, uint32_t *ph_kpn, double *ph_Y, cudaStream_t st);
 size_t stage_a_T_elems(const ModelDev &M);
 size_t stage_a_A_elems(const ModelDev &M);
-// Rates from a contraction already in Cbuf[pair - pair_base][Nmax] (tensor-core path).
-cudaError_t launch_vertex_epilogue(const ModelDev &M, const MeshDev &D, RateParams rp, int64_t i0, int64_t nkc,
-                                   int64_t pair_base, const double *Cbuf, int Nmax, const int64_t *escan,
+// Tables of the rate epilogue: fk [nk][nb] Fermi, nbq [nq][nbr] Bose, wr [nq][nbr] w_ref/w,
+// ut [nq][nbr][nbr] mass-scaled phonon eigenvectors.
+cudaError_t launch_epi_tables(const ModelDev &M, const MeshDev &D, double T, double mu, double *fk, double *nbq,
+                              double *wr, double2 *ut, cudaStream_t st);
+// Rates of pairs [pbeg, pend) from a contraction already in Cbuf[pair - pair_base][Nmax]
+// (tensor-core path), one thread per pair.
+cudaError_t launch_vertex_epilogue(const ModelDev &M, const MeshDev &D, RateParams rp, int64_t pbeg, int64_t pend,
+                                   int64_t pair_base, const double *Cbuf, int Nmax, const double *fk,
+                                   const double *nbq, const double *wr, const double2 *ut, const int64_t *escan,
                                    const int64_t *phscan, uint32_t *e_kpns, double2 *e_X, int *ph_st,
                                    uint32_t *ph_kpn, double *ph_Y, cudaStream_t st);
 

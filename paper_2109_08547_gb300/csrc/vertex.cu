@@ -421,67 +421,166 @@ __global__ void __launch_bounds__(kBT) k_stage_b_rates(ModelDev M, MeshDev D, Ra
   }
 }
 
-// Rates from the tensor-core contraction: C'[pair][j'] with j' = ml*(2 nb nbr) + part*(nb nbr)
-// + n'*nbr + a (part 0: real, 1: imaginary).  One block per irreducible-window k, one warp per
-// pair; the per-pair work is the same epilogue as above.
-__global__ void __launch_bounds__(kBT) k_vertex_epilogue(ModelDev M, MeshDev D, RateParams rp, int64_t i0,
-                                                         int64_t pair_base, const double *__restrict__ Cbuf,
-                                                         int Nmax, const int64_t *__restrict__ escan,
-                                                         const int64_t *__restrict__ phscan, uint32_t *e_kpns,
-                                                         double2 *e_X, int *ph_st, uint32_t *ph_kpn, double *ph_Y) {
-  extern __shared__ __align__(16) unsigned char smem[];
+// Per-rate-build tables of the rate epilogue: Fermi occupation of every (k, band); Bose
+// occupation, w_ref/w prefactor (0 for excluded modes) and mass-scaled eigenvectors
+// u_{a s}(q) / sqrt(m_a / m_bar) of every (q, branch).
+__global__ void k_epi_tables(ModelDev M, MeshDev D, double T, double mu, double *fk, double *nbq, double *wr,
+                             double2 *ut) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   const int nb = M.nb, nbr = M.nbr;
-  const int jmax = nb * nb * nbr;
-  size_t per_warp = size_t(jmax) * sizeof(double2) * 2 + 3 * size_t(jmax) * sizeof(double);
-  per_warp = (per_warp + 15) & ~size_t(15);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  unsigned char *wscr = smem + wid * per_warp;
-  double2 *Bp = reinterpret_cast<double2 *>(wscr);
-  double2 *Zs = Bp + jmax;
-  double *g2s = reinterpret_cast<double *>(Zs + jmax);
-  double *Xps = g2s + jmax;
-  double *Xms = Xps + jmax;
-  const int64_t i = i0 + blockIdx.x;
+  const double kT = kKbEVK * T;
+  if (t < D.nk * nb) fk[t] = fermi_d(D.eps[t], mu, kT);
+  if (t < D.nq * nbr) {
+    const double w = D.w[t];
+    nbq[t] = bose_d(w, kT);
+    wr[t] = w > D.omega_min ? M.omega_ref / w : 0.0;
+  }
+  if (t < D.nq * nbr * nbr) {
+    const int a = int((t / nbr) % nbr);
+    ut[t] = cscale(D.u[t], 1.0 / sqrt(M.mass[a / 3] / M.mass_mean));
+  }
+}
+
+// Rates from a contraction held in Cbuf: C'[pair][j'] with j' = ml*(2 nb nbr) + part*(nb nbr)
+// + n'*nbr + a (part 0: real, 1: imaginary).  One thread per (k, q) pair, so every lane works
+// even when a pair has only a handful of (m, n, s) tuples.  The final-band index is contracted
+// before the branch index, W[m n a] = sum_n' conj(c_{n'n}(k')) B[m n' a], then
+// g[m n s] = sqrt(w_ref/w_s) sum_a W[m n a] u_{a s}(q)/sqrt(m_a/m_bar): the same product as
+// the fused kernel, with nact' instead of nb final-band rows in the branch rotation.
+template <int NBM, int NBRM>
+__global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, RateParams rp, int64_t pbeg,
+                                                       int64_t pend, int64_t pair_base, const double *__restrict__ Cbuf,
+                                                       int Nmax, const double *__restrict__ fk,
+                                                       const double *__restrict__ nbq, const double *__restrict__ wr,
+                                                       const double2 *__restrict__ ut,
+                                                       const int64_t *__restrict__ escan,
+                                                       const int64_t *__restrict__ phscan, uint32_t *e_kpns,
+                                                       double2 *e_X, int *ph_st, uint32_t *ph_kpn, double *ph_Y) {
+  const int64_t pg = pbeg + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (pg >= pend) return;
+  const int nb = M.nb, nbr = M.nbr, nbnbr = nb * nbr;
+  const int i = D.pair_i[pg], q = D.pair_q[pg];
   const int k = D.ibzw_list[i];
-  const uint32_t am = D.amask[k];
-  const int nact = __popc(am);
-  const int Jk = nact * nb * nbr;
+  const int kp = kplusq_d(D, k, q);
+  const uint32_t am = D.amask[k], an = D.amask[kp];
+  const int nact = __popc(am), nactp = __popc(an);
   const int64_t p0 = D.pair_ptr[i];
   const int64_t npl = D.pair_ptr[i + 1] - p0;
-  const double kT = kKbEVK * rp.T;
-  const double *ek = D.eps + size_t(k) * nb;
-  const double inv_stab = 1.0 / double(D.stab[k]);
-  double mscale[kMaxBranches];
-  for (int a = 0; a < nbr; ++a) mscale[a] = 1.0 / sqrt(M.mass[a / 3] / M.mass_mean);
-  const int nbnbr = nb * nbr;
-  for (int64_t p = wid; p < npl; p += kBT / 32) {
-    const double *crow = Cbuf + (p0 + p - pair_base) * Nmax;
-    for (int t = lane; t < Jk; t += 32) {
-      const int ml = t / nbnbr, rest = t % nbnbr;
-      Bp[t] = cmk(crow[ml * 2 * nbnbr + rest], crow[ml * 2 * nbnbr + nbnbr + rest]);
+  const double *crow = Cbuf + (pg - pair_base) * Nmax;
+  const double2 *ckp = D.cvec + size_t(kp) * nb * nb;
+  const double2 *uq = ut + size_t(q) * nbr * nbr;
+  const double *wrq = wr + size_t(q) * nbr;
+  double g2[NBM * NBM * NBRM];
+  for (int ml = 0; ml < nact; ++ml)
+    for (int nl = 0; nl < nactp; ++nl) {
+      const int n = nth_bit(an, nl);
+      double2 W[NBRM];
+      for (int a = 0; a < nbr; ++a) W[a] = cmk(0, 0);
+      for (int np_ = 0; np_ < nb; ++np_) {
+        const double2 cc = ckp[np_ * nb + n];
+        const double *re = crow + ml * 2 * nbnbr + np_ * nbr;
+        for (int a = 0; a < nbr; ++a) cfma_conj(W[a], cc, cmk(re[a], re[nbnbr + a]));
+      }
+      for (int s = 0; s < nbr; ++s) {
+        double2 g = cmk(0, 0);
+        for (int a = 0; a < nbr; ++a) cfma(g, W[a], uq[a * nbr + s]);
+        g2[(ml * nactp + nl) * nbr + s] = cabs2(g) * wrq[s];
+      }
     }
-    __syncwarp();
-    pair_epilogue(M, D, rp, i, k, am, nact, Jk, p0, npl, p0 + p, Bp, Zs, g2s, Xps, Xms, mscale, inv_stab, ek, kT,
-                  escan, phscan, e_kpns, e_X, ph_st, ph_kpn, ph_Y);
-    __syncwarp();
+  // degenerate averages, occupations (tables), delta
+  const double *ek = D.eps + size_t(k) * nb, *ekp = D.eps + size_t(kp) * nb, *wq = D.w + size_t(q) * nbr;
+  const uint8_t *gk = D.egrp + size_t(k) * nb * 2, *gkp = D.egrp + size_t(kp) * nb * 2;
+  const uint8_t *gq = D.pgrp + size_t(q) * nbr * 2;
+  double Xp[NBM * NBM * NBRM], Xm[NBM * NBM * NBRM];
+  uint8_t flg[NBM * NBM * NBRM];
+  const int ntup = nact * nactp * nbr;
+  for (int t = 0; t < ntup; ++t) {
+    const int ml = t / (nactp * nbr), nl = (t / nbr) % nactp, s = t % nbr;
+    const int m = nth_bit(am, ml), n = nth_bit(an, nl);
+    Xp[t] = 0.0;
+    Xm[t] = 0.0;
+    flg[t] = 0;
+    if (!(wq[s] > D.omega_min)) continue;
+    double sum = 0.0;
+    int cnt = 0;
+    for (int a = gk[2 * m]; a < gk[2 * m + 1]; ++a) {
+      if (!((am >> a) & 1u)) continue;
+      const int al = __popc(am & ((1u << a) - 1u));
+      for (int b = gkp[2 * n]; b < gkp[2 * n + 1]; ++b) {
+        if (!((an >> b) & 1u)) continue;
+        const int bl = __popc(an & ((1u << b) - 1u));
+        for (int c = gq[2 * s]; c < gq[2 * s + 1]; ++c) {
+          sum += g2[(al * nactp + bl) * nbr + c];
+          ++cnt;
+        }
+      }
+    }
+    const double dxp = ekp[n] - ek[m] - wq[s];
+    const double dxm = ekp[n] - ek[m] + wq[s];
+    const double nqs = nbq[size_t(q) * nbr + s];
+    const double occ = rp.inv_Nq_pref * (sum / double(cnt)) * fk[size_t(k) * nb + m] * (1.0 - fk[size_t(kp) * nb + n]);
+    Xp[t] = occ * nqs * gauss_d(dxp, rp.sigma, rp.cut);
+    Xm[t] = occ * (1.0 + nqs) * gauss_d(dxm, rp.sigma, rp.cut);
+    flg[t] = uint8_t((fabs(dxp) <= rp.cut ? 1 : 0) | (fabs(dxm) <= rp.cut ? 2 : 0));
+  }
+  // electron rows (k, m): entries ordered (n, s)
+  const int64_t pl = pg - p0;
+  for (int ml = 0; ml < nact; ++ml) {
+    const int m = nth_bit(am, ml);
+    int64_t pos = escan[p0 * nb + m * npl + pl];
+    for (int u = 0; u < nactp * nbr; ++u) {
+      const int t = ml * nactp * nbr + u;
+      if (!flg[t]) continue;
+      e_kpns[pos] = pack_kpns(kp, nth_bit(an, u / nbr), u % nbr);
+      e_X[pos] = cmk(Xp[t], Xm[t]);
+      ++pos;
+    }
+  }
+  // phonon rows (q, s): entries ordered (m, n), absorption (+) processes only
+  const int64_t qb = D.qpair_ptr[q];
+  const int64_t npq = D.qpair_ptr[q + 1] - qb;
+  const int rk = D.pq_rank[pg];
+  const double ysc = rp.y_scale / double(D.stab[k]);
+  for (int s = 0; s < nbr; ++s) {
+    if (!(wq[s] > D.omega_min)) continue;
+    int64_t pos = phscan[qb * nbr + s * npq + rk];
+    for (int u = 0; u < nact * nactp; ++u) {
+      const int t = u * nbr + s;
+      if (!(flg[t] & 1)) continue;
+      ph_st[pos] = i * nb + nth_bit(am, u / nactp);
+      ph_kpn[pos] = pack_kpns(kp, nth_bit(an, u % nactp), 0);
+      ph_Y[pos] = Xp[t] * ysc;
+      ++pos;
+    }
   }
 }
 
 }  // namespace
 
-cudaError_t launch_vertex_epilogue(const ModelDev &M, const MeshDev &D, RateParams rp, int64_t i0, int64_t nkc,
-                                   int64_t pair_base, const double *Cbuf, int Nmax, const int64_t *escan,
+cudaError_t launch_epi_tables(const ModelDev &M, const MeshDev &D, double T, double mu, double *fk, double *nbq,
+                              double *wr, double2 *ut, cudaStream_t st) {
+  int64_t n = D.nk * M.nb;
+  if (D.nq * M.nbr * M.nbr > n) n = D.nq * M.nbr * M.nbr;
+  EPHB_LAUNCH(k_epi_tables, unsigned((n + 255) / 256), 256, 0, st, M, D, T, mu, fk, nbq, wr, ut);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vertex_epilogue(const ModelDev &M, const MeshDev &D, RateParams rp, int64_t pbeg, int64_t pend,
+                                   int64_t pair_base, const double *Cbuf, int Nmax, const double *fk,
+                                   const double *nbq, const double *wr, const double2 *ut, const int64_t *escan,
                                    const int64_t *phscan, uint32_t *e_kpns, double2 *e_X, int *ph_st,
                                    uint32_t *ph_kpn, double *ph_Y, cudaStream_t st) {
-  if (nkc <= 0) return cudaSuccess;
-  const int jmax = M.nb * M.nb * M.nbr;
-  size_t per_warp = size_t(jmax) * sizeof(double2) * 2 + 3 * size_t(jmax) * sizeof(double);
-  per_warp = (per_warp + 15) & ~size_t(15);
-  const size_t smem = per_warp * (kBT / 32);
-  cudaError_t e = cudaFuncSetAttribute(k_vertex_epilogue, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
-  EPHB_LAUNCH(k_vertex_epilogue, unsigned(nkc), kBT, smem, st, M, D, rp, i0, pair_base, Cbuf, Nmax, escan, phscan,
-              e_kpns, e_X, ph_st, ph_kpn, ph_Y);
+  if (pend <= pbeg) return cudaSuccess;
+  const unsigned grid = unsigned((pend - pbeg + 127) / 128);
+  if (M.nb <= 1 && M.nbr <= 3)
+    EPHB_LAUNCH((k_rate_epilogue<1, 3>), grid, 128, 0, st, M, D, rp, pbeg, pend, pair_base, Cbuf, Nmax, fk, nbq, wr,
+                ut, escan, phscan, e_kpns, e_X, ph_st, ph_kpn, ph_Y);
+  else if (M.nb <= 4 && M.nbr <= 6)
+    EPHB_LAUNCH((k_rate_epilogue<4, 6>), grid, 128, 0, st, M, D, rp, pbeg, pend, pair_base, Cbuf, Nmax, fk, nbq, wr,
+                ut, escan, phscan, e_kpns, e_X, ph_st, ph_kpn, ph_Y);
+  else
+    EPHB_LAUNCH((k_rate_epilogue<kMaxBands, kMaxBranches>), grid, 128, 0, st, M, D, rp, pbeg, pend, pair_base, Cbuf,
+                Nmax, fk, nbq, wr, ut, escan, phscan, e_kpns, e_X, ph_st, ph_kpn, ph_Y);
   return cudaGetLastError();
 }
 
