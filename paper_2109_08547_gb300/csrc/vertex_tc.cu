@@ -34,9 +34,9 @@ namespace ephb {
 namespace {
 
 constexpr int kTcM = 128;        // pairs per tile (tensor-memory lanes)
-constexpr int kTcKc = 64;        // K per shared-memory stage (4 MMA K-steps of 16)
+constexpr int kTcKc = 32;        // K per shared-memory stage (2 MMA K-steps of 16)
 constexpr int kTcThreads = 128;  // 4 warps: one per tensor-memory lane quadrant
-constexpr long kSpinLimit = 400000000L;
+constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s bound on any wait
 
 __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
@@ -144,12 +144,27 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
   return d;
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// wait for the completion of phase `phase` of an mbarrier; gives up after kWaitNs
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
-  uint32_t done = 0;
-  for (long it = 0; it < kSpinLimit && !done; ++it)
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    uint32_t done = 0;
     asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
                  : "=r"(done) : "r"(mbar), "r"(phase) : "memory");
-  return done != 0;
+    if (done) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+}
+
+// 16-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
 
 // core-matrix offset (bytes) of element (row, k) in a [rows x kTcKc] K-major tile
@@ -170,9 +185,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vertex_gemm(ModelDev M, MeshD
                                                                const double *__restrict__ bscale, double *Cbuf,
                                                                int *err) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tslot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // once a CTA has recorded a timeout the remaining ones return without waiting in turn
+  if (*reinterpret_cast<volatile int *>(err)) return;
   // which (k, tile, column chunk)
   const int64_t item = blockIdx.x;
   int64_t lo = 0, hi = P.nkc;
@@ -196,12 +213,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vertex_gemm(ModelDev M, MeshD
   const int64_t t0 = int64_t(tile) * kTcM;
   const int npt = int(npl - t0 < kTcM ? npl - t0 : kTcM);
 
-  unsigned char *sA = smem;                                   // NS x [128 x Kc]
-  unsigned char *sB = smem + size_t(NS) * kTcM * kTcKc * 2;   // NS x [nc_max x Kc]
+  // two shared-memory stages, each NS x [128 x Kc] (A) followed by NS x [nc_max x Kc] (B)
   const size_t a_slice = size_t(kTcM) * kTcKc * 2, b_slice = size_t(P.nc_max) * kTcKc * 2;
+  const size_t stage_bytes = size_t(NS) * (a_slice + b_slice);
 
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[1])));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   const uint32_t ncols_alloc = NACC * nc <= 32 ? 32u : (NACC * nc <= 64 ? 64u : (NACC * nc <= 128 ? 128u :
@@ -218,41 +236,52 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vertex_gemm(ModelDev M, MeshD
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(ncw >> 3) << 17) | (uint32_t(kTcM >> 4) << 24);
   const int q_row = tid < npt ? D.pair_q[p0 + t0 + tid] : -1;
   const __nv_bfloat16 *bsk = bs + size_t(kc) * NS * P.Nmax * P.Kp;
-  bool ok = true;
-  uint32_t phase = 0;
-  for (int kb = 0; kb < P.Kp; kb += kTcKc) {
-    // stage the A rows (gathered phase slices) and the B rows of this K block
-    for (int s = 0; s < NS; ++s) {
-      unsigned char *dst = sA + s * a_slice;
-      const uint4 *src = q_row >= 0 ? reinterpret_cast<const uint4 *>(phis + (size_t(q_row) * NS + s) * P.Kp + kb)
-                                    : nullptr;
-      for (int g = 0; g < kTcKc / 8; ++g) {
-        const uint4 v = src ? src[g] : make_uint4(0u, 0u, 0u, 0u);
-        *reinterpret_cast<uint4 *>(dst + core_off(tid, g)) = v;
-      }
-    }
+  const __nv_bfloat16 *arow = phis + size_t(q_row < 0 ? 0 : q_row) * NS * P.Kp;
+  const uint32_t abytes = q_row >= 0 ? 16u : 0u;   // rows past the tile are zero-filled
+
+  // asynchronous copies of the operands of K block kb into stage buf (one commit group)
+  auto stage_load = [&](int buf, int kb) {
+    unsigned char *sA = smem + buf * stage_bytes;
+    unsigned char *sB = sA + NS * a_slice;
+    for (int s = 0; s < NS; ++s)
+      for (int g = 0; g < kTcKc / 8; ++g)
+        cp_async16(smem_u32(sA + s * a_slice + core_off(tid, g)), arow + size_t(s) * P.Kp + kb + g * 8, abytes);
     for (int t = tid; t < NS * ncw * (kTcKc / 8); t += kTcThreads) {
       const int s = t / (ncw * (kTcKc / 8));
       const int rem = t % (ncw * (kTcKc / 8));
       const int row = rem / (kTcKc / 8), g = rem % (kTcKc / 8);
-      const uint4 v = reinterpret_cast<const uint4 *>(bsk + (size_t(s) * P.Nmax + n0 + row) * P.Kp + kb)[g];
-      *reinterpret_cast<uint4 *>(sB + s * b_slice + core_off(row, g)) = v;
+      cp_async16(smem_u32(sB + s * b_slice + core_off(row, g)),
+                 bsk + (size_t(s) * P.Nmax + n0 + row) * P.Kp + kb + g * 8, 16u);
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
+  // Pipeline: the MMAs of block b are issued as soon as its operands have landed; the copies
+  // of block b + 1 go into the other stage once the MMAs of block b - 1 (its last readers)
+  // have completed, so they overlap the MMAs of block b.
+  const int nkb = P.Kp / kTcKc;
+  bool ok = true;
+  int issued = -1;    // last K block whose MMAs were committed
+  stage_load(0, 0);
+  for (int b = 0; b < nkb && ok; ++b) {
+    const int buf = b & 1;
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
+      const unsigned char *sA = smem + buf * stage_bytes;
+      const unsigned char *sB = sA + NS * a_slice;
       for (int is = 0; is < NS; ++is)
-        for (int ls = 0; ls + is < NS + 1 - 0 && ls < NS; ++ls) {
-          const int d = is + ls;                  // diagonal (0-based: slices is, ls)
-          if (d > NS - 1) continue;               // products with i + l <= NS + 1
+        for (int ls = 0; ls < NS - is; ++ls) {   // diagonal d = is + ls <= NS - 1 (i + l <= NS + 1)
+          const int d = is + ls;
           const int acc = NACC == 1 ? 0 : (d < NACC - 1 ? d : NACC - 1);
           const uint32_t dtm = taddr + uint32_t(acc * nc);
           for (int ks = 0; ks < kTcKc / 16; ++ks) {
             const uint64_t ad = smem_desc(smem_u32(sA + is * a_slice) + ks * 256, 128u, (kTcKc / 8) * 128u);
             const uint64_t bd = smem_desc(smem_u32(sB + ls * b_slice) + ks * 256, 128u, (kTcKc / 8) * 128u);
             // the first product into each accumulator (first K block, first K step) overwrites it
-            const bool first = kb == 0 && ks == 0 &&
+            const bool first = b == 0 && ks == 0 &&
                                (NACC == 1 ? (is == 0 && ls == 0) :
                                 (acc < NACC - 1 ? (is == 0) : (is == 0 && ls == NACC - 1)));
             const uint32_t en = first ? 0u : 1u;
@@ -262,21 +291,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vertex_gemm(ModelDev M, MeshD
           }
         }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   :: "r"(smem_u32(&mbar)) : "memory");
+                   :: "r"(smem_u32(&mbar[buf])) : "memory");
     }
-    // the MMAs read the staged operands: wait before overwriting them (the block agrees on
-    // the outcome, so a timeout leaves the loop on every thread together)
-    const bool waited = mbar_wait(smem_u32(&mbar), phase);
-    if (!__syncthreads_and(waited ? 1 : 0)) {
-      ok = false;
-      break;
+    issued = b;
+    if (b + 1 < nkb) {
+      if (b >= 1) {
+        // stage buf ^ 1 was read by the MMAs of block b - 1 (use (b - 1) / 2 of its barrier);
+        // the block agrees on the outcome, so a timeout leaves the loop on every thread together
+        const bool waited = mbar_wait(smem_u32(&mbar[buf ^ 1]), uint32_t(((b - 1) >> 1) & 1));
+        ok = __syncthreads_and(waited ? 1 : 0) != 0;
+      }
+      if (ok) stage_load(buf ^ 1, (b + 1) * kTcKc);
     }
-    phase ^= 1u;
+  }
+  // the last commit tracks every MMA issued before it (after a timeout: the bounded second wait)
+  {
+    const bool waited = mbar_wait(smem_u32(&mbar[issued & 1]), uint32_t((issued >> 1) & 1));
+    if (!__syncthreads_and(waited ? 1 : 0)) ok = false;
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (!ok) {
-    atomicExch(err, 1);
-    mbar_wait(smem_u32(&mbar), phase);   // bounded second wait for the MMAs in flight
+    if (tid == 0) atomicExch(err, 1);
   } else {
     // accumulators -> FP64 combination -> C'[pair][n0 + j]
     const int row = warp * 32 + lane;
@@ -310,7 +345,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vertex_gemm(ModelDev M, MeshD
 int tc_kp(const ModelDev &M) { return round_up(2 * M.nRgp, kTcKc); }
 int tc_nmax(const ModelDev &M) { return round_up(2 * M.nb * M.nb * M.nbr, 16); }
 int tc_nc_max(int ns) { return ns == 7 ? 96 : 256; }
-size_t tc_smem_bytes(int ns) { return size_t(ns) * kTcM * kTcKc * 2 + size_t(ns) * tc_nc_max(ns) * kTcKc * 2; }
+size_t tc_smem_bytes(int ns) { return 2 * (size_t(ns) * kTcM * kTcKc * 2 + size_t(ns) * tc_nc_max(ns) * kTcKc * 2); }
 
 cudaError_t launch_phase_slices(const ModelDev &M, const MeshDev &D, int ns, __nv_bfloat16 *phis, cudaStream_t st) {
   const int Kp = tc_kp(M);
