@@ -130,7 +130,8 @@ struct ephb_ctx {
   DBuf<uint32_t> kcrd;
   DBuf<int2> kinfo;
   DBuf<unsigned long long> ucount;
-  double *host_res = nullptr;   // pinned
+  DBuf<int> sctl;               // device-driven sweep loop: stop flag, sweeps done, converged
+  double *host_res = nullptr;   // pinned: kResLen doubles, then the sweep-loop control (4 ints)
   bool bte_ready = false;
 };
 
@@ -259,7 +260,7 @@ ephb_status ephb_create(ephb_ctx **out, int device, void *cuda_stream) {
     }
     ctx->own_stream = true;
   }
-  if (cudaMallocHost(&ctx->host_res, kResLen * sizeof(double)) != cudaSuccess) {
+  if (cudaMallocHost(&ctx->host_res, (kResLen + 2) * sizeof(double)) != cudaSuccess) {
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return EPHB_ENOMEM;
@@ -295,7 +296,7 @@ void ephb_destroy(ephb_ctx *ctx) {
   ctx->eseg_begin.release(); ctx->rseg_ptr.release(); ctx->rseg_begin.release(); ctx->run_ptr.release();
   ctx->run_idx.release(); ctx->run_col.release(); ctx->Dterm.release(); ctx->run_w.release();
   ctx->res.release(); ctx->prev_in.release(); ctx->prev_out.release(); ctx->prev_tmp.release();
-  ctx->kcrd.release(); ctx->kinfo.release(); ctx->ucount.release();
+  ctx->kcrd.release(); ctx->kinfo.release(); ctx->ucount.release(); ctx->sctl.release();
   if (ctx->host_res) cudaFreeHost(ctx->host_res);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -688,6 +689,7 @@ ephb_status bte_setup(ephb_ctx *ctx) {
   CK(ctx->ppart.ensure(size_t(coeff_partials()) * 18));
   CK(ctx->kpart.ensure(size_t(coeff_partials()) * 9));
   for (auto *b : {&ctx->res, &ctx->prev_in, &ctx->prev_out, &ctx->prev_tmp}) CK(b->ensure(kResLen));
+  CK(ctx->sctl.ensure(4));
   MeshDev D = mesh_view(ctx);
   CK(launch_state_setup(M, D, ctx->T, ctx->mu, ctx->st_eps.p, ctx->st_vel.p, ctx->st_ff.p, ctx->st_wt.p,
                         ctx->kcrd.p, ctx->kinfo.p, st));
@@ -762,6 +764,8 @@ ephb_status coefficients_to_host(ephb_ctx *ctx, double *prev, bool electron = tr
 
 }  // namespace
 
+constexpr int kSweepBatch = 8;   // electron sweeps queued per host round trip
+
 ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *out) {
   if (!ctx) return EPHB_EINVAL;
   if (ctx->stage < 3) return fail(ctx, EPHB_ESTATE, "compute_transition_rates must come first");
@@ -807,28 +811,42 @@ ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb
       CK(launch_drag_term(D, B, entry_segs(ctx), ctx->F.p, ctx->G.p, ctx->seg_part.p, ctx->Dterm.p, st));
       CK(td.stop(st));
     }
+    // Sweeps are queued in batches without a host round trip each: the coefficient kernel
+    // advances the sweep counter and sets the stop flag (converged or max_inner reached), after
+    // which the queued kernels return at once.
     const SweepSegs S = run_segs(ctx);
-    for (int it = 1; it <= o->max_inner; ++it) {
+    int *hctl = reinterpret_cast<int *>(ctx->host_res + kResLen);
+    CK(cudaMemsetAsync(ctx->sctl.p, 0, 4 * sizeof(int), st));
+    int queued = 0;
+    for (;;) {
+      const int nb = std::min(kSweepBatch, o->max_inner - queued);
       CK(te.start(st));
-      CK(launch_self_sweep(M, B, S, ctx->run_col.p, ctx->run_w.p, ctx->I0.p, ctx->J0.p, ctx->inv_ffW.p, ctx->I.p,
-                           ctx->J.p, drag ? ctx->Dterm.p : nullptr, ctx->seg_part.p, ctx->I2.p, ctx->J2.p,
-                           ctx->epart.p, st));
+      for (int j = 0; j < nb; ++j) {
+        CK(launch_self_sweep(M, B, S, ctx->run_col.p, ctx->run_w.p, ctx->I0.p, ctx->J0.p, ctx->inv_ffW.p, ctx->I.p,
+                             ctx->J.p, ctx->I2.p, ctx->J2.p, drag ? ctx->Dterm.p : nullptr, ctx->seg_part.p,
+                             ctx->epart.p, ctx->sctl.p, st));
+        // the sweep already wrote the electron partial sums; the phonon ones are unchanged
+        CK(launch_coeff_final(ctx->M, B, ctx->epart.p, ctx->ppart.p, ctx->res.p, ctx->prev_in.p, st, ctx->sctl.p,
+                              o->max_inner, inner_tol));
+      }
       CK(te.stop(st));
-      std::swap(ctx->I.p, ctx->I2.p);
-      std::swap(ctx->J.p, ctx->J2.p);
-      ++sweeps;
-      ++inner_total;
-      B = bte_view(ctx);
-      // the sweep already wrote the electron partial sums; the phonon ones are unchanged
-      r = coefficients_to_host(ctx, ctx->prev_in.p, false, false);
-      if (r != EPHB_OK) return r;
+      queued += nb;
+      CK(cudaMemcpyAsync(ctx->host_res, ctx->res.p, kResLen * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(hctl, ctx->sctl.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
       CK(te.collect());
       CK(td.collect());
-      if (ctx->host_res[72] < inner_tol) {
-        ok = true;
-        return EPHB_OK;
-      }
+      if (hctl[0] || queued >= o->max_inner) break;
     }
+    const int done = hctl[1];
+    sweeps += done;
+    inner_total += done;
+    if (done & 1) {   // the last sweep wrote the second buffer pair
+      std::swap(ctx->I.p, ctx->I2.p);
+      std::swap(ctx->J.p, ctx->J2.p);
+    }
+    B = bte_view(ctx);
+    ok = hctl[2] != 0;
     return EPHB_OK;
   };
 

@@ -205,7 +205,16 @@ template <bool SYM>
 __global__ void __launch_bounds__(256) k_self_sweep_seg(ModelDev M, SweepSegs S, const uint32_t *__restrict__ run_col,
                                                         const double *__restrict__ run_w,
                                                         const double *__restrict__ I, const double *__restrict__ J,
-                                                        double *__restrict__ part) {
+                                                        const double *__restrict__ I2, const double *__restrict__ J2,
+                                                        const int *__restrict__ ctl, double *__restrict__ part) {
+  // device-driven loop: skip once stopped; odd sweeps read the second buffer pair
+  if (ctl) {
+    if (ctl[0]) return;
+    if (ctl[1] & 1) {
+      I = I2;
+      J = J2;
+    }
+  }
   __shared__ double C[kMaxSym * 9];
   if (SYM) {
     for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) C[t] = M.sym_cart[t];
@@ -411,7 +420,15 @@ __device__ inline void e_tensor_acc(const BteDev &B, int64_t st, const double *I
 __global__ void __launch_bounds__(kCT) k_e_finalize(BteDev B, SweepSegs S, const double *__restrict__ part,
                                                     const double *__restrict__ Dterm, const double *__restrict__ I0,
                                                     const double *__restrict__ J0, const double *__restrict__ inv_ffW,
-                                                    double *I_out, double *J_out, double *epart) {
+                                                    double *I_out, double *J_out, double *I_alt, double *J_alt,
+                                                    const int *__restrict__ ctl, double *epart) {
+  if (ctl) {
+    if (ctl[0]) return;
+    if (ctl[1] & 1) {
+      I_out = I_alt;
+      J_out = J_alt;
+    }
+  }
   double acc[kNE];
   for (int j = 0; j < kNE; ++j) acc[j] = 0.0;
   const int64_t stride = int64_t(gridDim.x) * kCT;
@@ -468,7 +485,10 @@ __global__ void __launch_bounds__(kCT) k_ph_partial(MeshDev D, BteDev B, const d
 // res: [0] sigma [9] sigmaS [18] alpha_el [27] kappa0_el [36] alpha_ph [45] kappa_ph [54] S [63] kappa_el
 //      [72] residual_e [73] residual_all
 __global__ void __launch_bounds__(512) k_coeff_final(ModelDev M, BteDev B, const double *epart,
-                                                     const double *ppart, int npart, double *res, double *prev) {
+                                                     const double *ppart, int npart, double *res, double *prev,
+                                                     int *ctl, int max_sweeps, double tol) {
+  // device-driven loop (ctl != nullptr): ctl[0] stop flag, ctl[1] sweeps done, ctl[2] converged
+  if (ctl && ctl[0]) return;
   __shared__ double Ms[kNE + kNP];
   __shared__ double R[72];
   __shared__ double inv[10];
@@ -541,6 +561,13 @@ __global__ void __launch_bounds__(512) k_coeff_final(ModelDev M, BteDev B, const
     }
     res[72] = re;
     res[73] = ra;
+    if (ctl) {
+      const int n = ctl[1] + 1;
+      ctl[1] = n;
+      const bool conv = re < tol;
+      if (conv) ctl[2] = 1;
+      if (conv || n >= max_sweeps) ctl[0] = 1;
+    }
   }
 }
 
@@ -694,18 +721,18 @@ cudaError_t launch_fill_runs(const BteDev &B, int64_t n_entries, int64_t nruns, 
 
 cudaError_t launch_self_sweep(const ModelDev &M, const BteDev &B, const SweepSegs &S, const uint32_t *run_col,
                               const double *run_w, const double *I0, const double *J0, const double *inv_ffW,
-                              const double *I, const double *J, const double *Dterm, double *part, double *I_out,
-                              double *J_out, double *epart, cudaStream_t st) {
+                              double *Ia, double *Ja, double *Ib, double *Jb, const double *Dterm, double *part,
+                              double *epart, const int *ctl, cudaStream_t st) {
   if (S.nseg > 0) {
     const unsigned grid = unsigned((S.nseg * 32 + 255) / 256);
     if (M.nsym > 1)
-      EPHB_LAUNCH(k_self_sweep_seg<true>, grid, 256, 0, st, M, S, run_col, run_w, I, J, part);
+      EPHB_LAUNCH(k_self_sweep_seg<true>, grid, 256, 0, st, M, S, run_col, run_w, Ia, Ja, Ib, Jb, ctl, part);
     else
-      EPHB_LAUNCH(k_self_sweep_seg<false>, grid, 256, 0, st, M, S, run_col, run_w, I, J, part);
+      EPHB_LAUNCH(k_self_sweep_seg<false>, grid, 256, 0, st, M, S, run_col, run_w, Ia, Ja, Ib, Jb, ctl, part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  EPHB_LAUNCH(k_e_finalize, kNPart, kCT, 0, st, B, S, part, Dterm, I0, J0, inv_ffW, I_out, J_out, epart);
+  EPHB_LAUNCH(k_e_finalize, kNPart, kCT, 0, st, B, S, part, Dterm, I0, J0, inv_ffW, Ib, Jb, Ia, Ja, ctl, epart);
   return cudaGetLastError();
 }
 
@@ -741,8 +768,8 @@ cudaError_t launch_ph_partial(const MeshDev &D, const BteDev &B, const double *F
 }
 
 cudaError_t launch_coeff_final(const ModelDev &M, const BteDev &B, const double *epart, const double *ppart,
-                               double *res, double *prev, cudaStream_t st) {
-  EPHB_LAUNCH(k_coeff_final, 1, 512, 0, st, M, B, epart, ppart, kNPart, res, prev);
+                               double *res, double *prev, cudaStream_t st, int *ctl, int max_sweeps, double tol) {
+  EPHB_LAUNCH(k_coeff_final, 1, 512, 0, st, M, B, epart, ppart, kNPart, res, prev, ctl, max_sweeps, tol);
   return cudaGetLastError();
 }
 

@@ -162,10 +162,13 @@ cudaError_t launch_fill_runs(const BteDev &B, int64_t n_entries, int64_t nruns, 
                              cudaStream_t st);
 // One electron sweep (self term over the runs) and the per-row finalisation
 // I = I0 + (self + Dterm)/(f(1-f)W), which also writes the electron coefficient partials.
+// ctl == nullptr: reads (Ia, Ja), writes (Ib, Jb).  Otherwise the loop is driven on the device:
+// nothing runs once ctl[0] is set, and sweep number ctl[1] reads (Ia, Ja) when even and
+// (Ib, Jb) when odd and writes the other pair (ctl[1] is advanced by launch_coeff_final).
 cudaError_t launch_self_sweep(const ModelDev &M, const BteDev &B, const SweepSegs &S, const uint32_t *run_col,
                               const double *run_w, const double *I0, const double *J0, const double *inv_ffW,
-                              const double *I, const double *J, const double *Dterm, double *part, double *I_out,
-                              double *J_out, double *epart, cudaStream_t st);
+                              double *Ia, double *Ja, double *Ib, double *Jb, const double *Dterm, double *part,
+                              double *epart, const int *ctl, cudaStream_t st);
 // Drag term of every row for the current F, G: Dterm[st][6].
 cudaError_t launch_drag_term(const MeshDev &D, const BteDev &B, const SweepSegs &S, const double *F, const double *G,
                              double *part, double *Dterm, cudaStream_t st);
@@ -183,7 +186,8 @@ cudaError_t launch_e_partial(const BteDev &B, const double *I, const double *J, 
 cudaError_t launch_ph_partial(const MeshDev &D, const BteDev &B, const double *F, const double *G, double *ppart,
                               cudaStream_t st);
 cudaError_t launch_coeff_final(const ModelDev &M, const BteDev &B, const double *epart, const double *ppart,
-                               double *res, double *prev, cudaStream_t st);
+                               double *res, double *prev, cudaStream_t st, int *ctl = nullptr, int max_sweeps = 0,
+                               double tol = 0.0);
 cudaError_t launch_ko(const ModelDev &M, const MeshDev &D, const BteDev &B, double *I, const double *J,
                       double *kpart, double *res, cudaStream_t st);
 
