@@ -315,49 +315,62 @@ def main():
     r0 = results[-1]
 
     # dominant kernel and its roofline (device time measured with CUDA events in this run)
-    ms_b = statistics.mean(r.rates["ms_stage_b"] for r in results)
-    ms_ep = statistics.mean(r.rates["ms_epilogue"] for r in results)
-    ms_e = statistics.mean(r.solve["ms_e_sweep"] for r in results)
+    mean = lambda f: statistics.mean(f(r) for r in results)
+    ms_b = mean(lambda r: r.rates["ms_stage_b"])
+    ms_g = mean(lambda r: r.rates["ms_gemm"])
+    ms_a = mean(lambda r: r.rates["ms_stage_a"])
+    ms_ep = mean(lambda r: r.rates["ms_epilogue"])
+    ms_self = mean(lambda r: r.solve["ms_self_kernel"])
     peaks = measured_peaks()
     step_ms = 1e3 * el_max / args.steps
-    dominant = max((("stage_b", ms_b), ("epilogue", ms_ep), ("e_sweep", ms_e)), key=lambda x: x[1])[0]
-    if dominant == "stage_b" and args.precision == "fp64":
+    fp64_src = "measured FP64 FMA rate (bench.py --fp64-peak, profiles/fp64_peak_gb300.txt)"
+    cands = [("stage_a", ms_a), ("epilogue", ms_ep), ("self_sweep", ms_self)]
+    cands.append(("stage_b", ms_b) if args.precision == "fp64" else ("gemm", ms_g))
+    dominant = max(cands, key=lambda x: x[1])[0]
+    if dominant == "stage_b":
         achieved = r0.rates["stage_b_flops"] / (ms_b * 1e-3) / 1e12
         tr = profile_traffic("stage_b_rates", "vertex.cu")
         roof = {"kernel": "k_stage_b_rates (R_ph contraction + rotations + rates, FP64)", "bound": "alu",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS,
-                "peak_source": "measured FP64 FMA rate (bench.py --fp64-peak, profiles/fp64_peak_gb300.txt)",
+                "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": fp64_src,
                 "traffic": (tr[0] * r0.rates["n_pairs"]) if tr else None,
                 "ms_per_step": ms_b, "share_of_step": ms_b / step_ms}
-    elif dominant == "stage_b":
+    elif dominant == "gemm":
         # tensor-core contraction: the MMA work the slicing issues, against the measured BF16 peak
         pk = peaks.get("bf16_tflops", 1900.0)
-        achieved = r0.rates["tensor_flops"] / (ms_b * 1e-3) / 1e12
+        achieved = r0.rates["tensor_flops"] / (ms_g * 1e-3) / 1e12
         tr = profile_traffic("vertex_gemm", "vertex_tc.cu")
         roof = {"kernel": f"k_vertex_gemm (tcgen05 R_ph contraction, {args.precision})", "bound": "tensor",
                 "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured burst)" if "bf16_tflops" in peaks
                 else "fallback", "traffic": (tr[0] * r0.rates["n_pairs"]) if tr else None,
-                "algorithmic_tflops": r0.rates["stage_b_flops"] / (ms_b * 1e-3) / 1e12,
-                "ms_per_step": ms_b, "share_of_step": ms_b / step_ms}
+                "ms_per_step": ms_g, "share_of_step": ms_g / step_ms}
+    elif dominant == "stage_a":
+        achieved = r0.rates["stage_a_flops"] / (ms_a * 1e-3) / 1e12
+        roof = {"kernel": "k_stage_a1/a2 (R_e contraction and band rotation, FP64)", "bound": "alu",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": fp64_src, "traffic": None,
+                "ms_per_step": ms_a, "share_of_step": ms_a / step_ms}
     elif dominant == "epilogue":
         achieved = r0.rates["rot_flops"] / (ms_ep * 1e-3) / 1e12
-        roof = {"kernel": "k_vertex_epilogue (rotations, |g|^2, occupations, delta, writes; FP64)", "bound": "alu",
+        tr = profile_traffic("rate_epilogue", "vertex.cu")
+        roof = {"kernel": "k_rate_epilogue (rotations, |g|^2, occupations, delta, writes; FP64)", "bound": "alu",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS,
-                "peak_source": "measured FP64 FMA rate (bench.py --fp64-peak, profiles/fp64_peak_gb300.txt)",
-                "traffic": None, "ms_per_step": ms_ep, "share_of_step": ms_ep / step_ms}
+                "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": fp64_src,
+                "traffic": (tr[0] * r0.rates["n_pairs"]) if tr else None,
+                "ms_per_step": ms_ep, "share_of_step": ms_ep / step_ms}
     else:
+        # the self-term gather sweep: 6 FP64 multiply-adds per partner run; the run stream
+        # (12 B per run) sits in L2 between sweeps, so the FP64 pipe is the bound
         nsw = r0.solve["n_sweeps"]
-        achieved = r0.solve["e_sweep_bytes"] * nsw / (ms_e * 1e-3) / 1e9
-        pk = peaks.get("hbm_gbs", 6800.0)
-        tr = profile_traffic("e_sweep", "bte.cu")
-        roof = {"kernel": "k_e_sweep (electron gather sweep)", "bound": "hbm", "achieved": achieved, "peak": pk,
-                "unit": "GB/s", "frac": achieved / pk,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback",
-                "traffic": (tr[0] * r0.rates["n_entries"]) if tr else None,
-                "ms_per_step": ms_e, "share_of_step": ms_e / step_ms}
+        achieved = r0.solve["e_sweep_flops"] * nsw / (ms_self * 1e-3) / 1e12
+        tr = profile_traffic("self_sweep", "bte.cu")
+        roof = {"kernel": "k_self_sweep_seg (electron self-term gather sweep, FP64)", "bound": "alu",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": fp64_src,
+                "traffic": (tr[0] * r0.solve["n_runs"]) if tr else None,
+                "hbm_gbs_algorithmic": r0.solve["e_sweep_bytes"] * nsw / (ms_self * 1e-3) / 1e9,
+                "ms_per_step": ms_self, "share_of_step": ms_self / step_ms}
 
     # end-to-end through the C ABI with host buffers: model H2D (pinned) + path + coefficients D2H
     e2e = None
@@ -438,8 +451,10 @@ def main():
                        "entries": r0.rates["n_entries"], "pairs": r0.rates["n_pairs"]},
             "s_to_converged": 1e-3 * el_max / args.steps,
             "phases_ms": {"rates": r0.rates["ms"], "stage_a": r0.rates["ms_stage_a"],
-                          "stage_b": r0.rates["ms_stage_b"], "rate_epilogue": r0.rates["ms_epilogue"],
+                          "stage_b": r0.rates["ms_stage_b"], "tensor_gemm": r0.rates["ms_gemm"],
+                          "rate_epilogue": r0.rates["ms_epilogue"],
                           "solve": r0.solve["ms"], "e_sweeps": r0.solve["ms_e_sweep"],
+                          "self_sweep_kernel": r0.solve["ms_self_kernel"], "n_runs": r0.solve["n_runs"],
                           "drag_terms": r0.solve["ms_drag"], "ph_sweeps": r0.solve["ms_ph_sweep"],
                           "n_sweeps": r0.solve["n_sweeps"], "outer_iters": r0.solve["outer_iters"]},
             "variants": variants,

@@ -134,9 +134,25 @@ ephb_status ephb_build_meshes_ibz(ephb_ctx *ctx, const ephb_mesh_opts *opts, eph
  * for every irreducible-window k, active m, q with k' = [k+q], active n and branch s.
  * delta is a Gaussian of standard deviation sigma, exactly zero beyond cutoff*sigma; an
  * entry is stored when either argument is within the cut.
- * ninst must be 1.  precision must be EPHB_FP64 (the other modes return EPHB_EINVAL).
+ *
+ * Instances.  inst[0..ninst-1] (1 <= ninst <= EPHB_MAX_INSTANCES) are (T, mu, window)
+ * right-hand sides on the same meshes.  An instance's window [window_lo_eV, window_hi_eV] is
+ * clipped to the mesh window; window_lo_eV >= window_hi_eV means the mesh window.  A state is
+ * active for an instance when it is active on the meshes and its energy lies in the instance
+ * window.  With one instance on the mesh window the rates are computed directly.  Otherwise
+ * |g|^2 and delta (which do not depend on T or mu) are interpolated once, over the mesh window,
+ * as V+- = 2pi/(hbar N_q)|g|^2 delta(...), and every instance keeps the entries whose two
+ * states lie in its window, with X+- = V+- f (1-f') {n, 1+n} from its own T and mu (the
+ * vertex reuse across temperatures and chemical potentials of section "Workflow and
+ * structure").  Degenerate averages of |g|^2 are then taken over the bands active on the
+ * meshes.  Every later call acts on all instances (solve) or names one (coefficients,
+ * ephb_select_instance for the array views).
  * --------------------------------------------------------------------------------*/
-typedef struct { double T_K, mu_eV; } ephb_thermo;
+typedef struct {
+  double T_K, mu_eV;
+  double window_lo_eV, window_hi_eV;   /* instance window; lo >= hi: the mesh window           */
+} ephb_thermo;
+#define EPHB_MAX_INSTANCES 64
 typedef struct { double sigma_eV, cutoff_sigmas; } ephb_delta;
 /* Precision of the R_ph contraction of the vertex (the largest part of the work):
  *   EPHB_FP64         FP64 on the CUDA cores.
@@ -164,6 +180,7 @@ typedef struct {
   double ms_epilogue;          /* tensor-core modes: device time of the rotation/rate kernel */
   double tensor_flops;         /* tensor-core modes: flops issued as tcgen05.mma           */
   double rot_flops;            /* algorithmic flops of the band and branch rotations       */
+  double ms_gemm;              /* tensor-core modes: device time of the tcgen05 GEMM kernel  */
 } ephb_rates_info;
 
 ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst, int ninst,
@@ -205,9 +222,16 @@ typedef struct {
   double e_sweep_bytes;        /* algorithmic HBM bytes of one electron sweep              */
   double ms_drag;              /* summed device time of the electron drag-term kernels     */
   int64_t n_runs;              /* partner runs: entries of a row merged over branches      */
+  double ms_self_kernel;       /* summed device time of the self-term gather kernel alone  */
+  double e_sweep_flops;        /* algorithmic FP64 flops of one self-term sweep            */
 } ephb_solve_info;
 
+/* Solves every instance.  `out` (optional) sums the counts and device times over the
+ * instances and keeps the largest residual and outer-iteration count; converged is 1 only if
+ * every instance converged, else the call returns EPHB_ENOCONV after solving all of them. */
 ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *opts, ephb_solve_info *out);
+/* The last solve of one instance. */
+ephb_status ephb_instance_solve_info(ephb_ctx *ctx, int inst, ephb_solve_info *out);
 
 /* ----------------------------------------------------------------------------------
  * Transport coefficients of the current responses (Eqs. sigma/sigmaS,
@@ -216,7 +240,7 @@ ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *opts, e
  *   alpha_el, kappa0_el = -d_s/(V N_k k_B T) sum (eps-mu) f(1-f) v (x) {J, -I}
  *   alpha_ph, kappa_ph = 1/(V N_q k_B T) sum_{sq} hbar w n(1+n) v (x) {-G, F}
  *   S = sigma^-1 sigmaS, kappa_el = kappa0_el - alpha_el S.
- * `out` is caller-owned host memory.  inst must be 0.
+ * `out` is caller-owned host memory.  inst selects the instance (0 <= inst < ninst).
  * --------------------------------------------------------------------------------*/
 typedef struct {
   double sigma[9], sigmaS[9], S[9], alpha_el[9], kappa0_el[9], kappa_el[9], alpha_ph[9], kappa_ph[9];
@@ -255,6 +279,11 @@ typedef enum {
   EPHB_ARR_COUNT = 22
 } ephb_array;
 
+/* Make instance inst the one whose arrays the views and copies below return (and the one
+ * whose solution a later solve leaves in place).  EPHB_EINVAL if inst is out of range. */
+ephb_status ephb_select_instance(ephb_ctx *ctx, int inst);
+/* Number of instances of the last compute_transition_rates call (1 before any). */
+int ephb_num_instances(const ephb_ctx *ctx);
 ephb_status ephb_get_device_array(ephb_ctx *ctx, int which, void **dptr, int64_t shape[4], int *dtype);
 ephb_status ephb_copy_array_to_host(ephb_ctx *ctx, int which, void *host_dst, int64_t nbytes);
 

@@ -32,7 +32,8 @@ _DT = {0: np.float64, 1: np.complex128, 2: np.int32, 3: np.int64, 4: np.uint32}
 EXPORTED = ["ephb_create", "ephb_destroy", "ephb_last_error", "ephb_set_wannier_model", "ephb_build_meshes_ibz",
             "ephb_compute_transition_rates", "ephb_solve_coupled_bte", "ephb_transport_coefficients",
             "ephb_get_device_array", "ephb_copy_array_to_host", "ephb_kernel_launches",
-            "ephb_transport_coefficients_noalloc"]
+            "ephb_transport_coefficients_noalloc", "ephb_select_instance", "ephb_num_instances",
+            "ephb_instance_solve_info"]
 
 _pd = C.POINTER(C.c_double)
 _pi = C.POINTER(C.c_int32)
@@ -58,7 +59,8 @@ class MeshInfoC(C.Structure):
 
 
 class ThermoC(C.Structure):
-    _fields_ = [("T_K", C.c_double), ("mu_eV", C.c_double)]
+    _fields_ = [("T_K", C.c_double), ("mu_eV", C.c_double), ("window_lo_eV", C.c_double),
+                ("window_hi_eV", C.c_double)]
 
 
 class DeltaC(C.Structure):
@@ -69,7 +71,7 @@ class RatesInfoC(C.Structure):
     _fields_ = [("n_tuples", C.c_int64), ("n_entries", C.c_int64), ("n_ph_entries", C.c_int64),
                 ("n_pairs", C.c_int64), ("ms", C.c_double), ("ms_stage_a", C.c_double), ("ms_stage_b", C.c_double),
                 ("stage_a_flops", C.c_double), ("stage_b_flops", C.c_double), ("ms_epilogue", C.c_double),
-                ("tensor_flops", C.c_double), ("rot_flops", C.c_double)]
+                ("tensor_flops", C.c_double), ("rot_flops", C.c_double), ("ms_gemm", C.c_double)]
 
 
 class SolveOptsC(C.Structure):
@@ -82,7 +84,7 @@ class SolveInfoC(C.Structure):
                 ("n_zero_rate_states", C.c_int), ("residual", C.c_double), ("lambda_", C.c_double),
                 ("n_sweeps", C.c_int64), ("ms", C.c_double), ("ms_e_sweep", C.c_double),
                 ("ms_ph_sweep", C.c_double), ("e_sweep_bytes", C.c_double), ("ms_drag", C.c_double),
-                ("n_runs", C.c_int64)]
+                ("n_runs", C.c_int64), ("ms_self_kernel", C.c_double), ("e_sweep_flops", C.c_double)]
 
 
 class CoeffsC(C.Structure):
@@ -128,6 +130,9 @@ def load(path: str = None):
     lib.ephb_copy_array_to_host.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]
     lib.ephb_transport_coefficients_noalloc.argtypes = [C.POINTER(CoeffInputsC), C.c_void_p, C.c_void_p]
     lib.ephb_kernel_launches.argtypes = []
+    lib.ephb_select_instance.argtypes = [C.c_void_p, C.c_int]
+    lib.ephb_num_instances.argtypes = [C.c_void_p]
+    lib.ephb_instance_solve_info.argtypes = [C.c_void_p, C.c_int, C.POINTER(SolveInfoC)]
     for name in EXPORTED:
         if name not in ("ephb_destroy", "ephb_last_error", "ephb_kernel_launches"):
             getattr(lib, name).restype = C.c_int
@@ -238,13 +243,37 @@ def build_meshes_ibz(ctx: Context, kmesh, qmesh, window, degen_tol_eV=1e-6, omeg
     return {f: getattr(info, f) for f, _ in MeshInfoC._fields_}
 
 
-def compute_transition_rates(ctx: Context, T_K, mu_eV, sigma_eV=0.01, cutoff_sigmas=8.0, precision=FP64) -> dict:
-    th = ThermoC(float(T_K), float(mu_eV))
+def compute_transition_rates(ctx: Context, T_K, mu_eV, sigma_eV=0.01, cutoff_sigmas=8.0, precision=FP64,
+                             instances=None) -> dict:
+    """One (T_K, mu_eV) instance on the mesh window, or ``instances``: a list of
+    (T_K, mu_eV) or (T_K, mu_eV, window_lo_eV, window_hi_eV) tuples (T_K, mu_eV ignored)."""
+    if instances is None:
+        instances = [(T_K, mu_eV)]
+    arr = (ThermoC * len(instances))()
+    for i, t in enumerate(instances):
+        lo, hi = (t[2], t[3]) if len(t) > 2 else (0.0, 0.0)
+        arr[i] = ThermoC(float(t[0]), float(t[1]), float(lo), float(hi))
     de = DeltaC(float(sigma_eV), float(cutoff_sigmas))
     info = RatesInfoC()
-    _check(ctx, _lib.ephb_compute_transition_rates(ctx.handle, C.byref(th), 1, C.byref(de), int(precision),
+    _check(ctx, _lib.ephb_compute_transition_rates(ctx.handle, arr, len(instances), C.byref(de), int(precision),
                                                    C.byref(info)))
     return {f: getattr(info, f) for f, _ in RatesInfoC._fields_}
+
+
+def select_instance(ctx: Context, inst: int) -> None:
+    _check(ctx, _lib.ephb_select_instance(ctx.handle, int(inst)))
+
+
+def num_instances(ctx: Context) -> int:
+    return int(_lib.ephb_num_instances(ctx.handle))
+
+
+def instance_solve_info(ctx: Context, inst: int) -> dict:
+    info = SolveInfoC()
+    _check(ctx, _lib.ephb_instance_solve_info(ctx.handle, int(inst), C.byref(info)))
+    d = {f: getattr(info, f) for f, _ in SolveInfoC._fields_}
+    d["lambda"] = d.pop("lambda_")
+    return d
 
 
 def solve_coupled_bte(ctx: Context, level="dragged", tol=1e-10, inner_tol=0.0, max_outer=500, max_inner=5000,

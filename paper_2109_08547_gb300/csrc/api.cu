@@ -78,7 +78,49 @@ struct DBuf {
 
 }  // namespace
 
-struct ephb_ctx {
+namespace {
+
+// Everything that belongs to one (T, mu, window) instance: its rate lists and its BTE state.
+struct InstState {
+  double T = 300, mu = 0, win_lo = 0, win_hi = 0;
+  int64_t n_entries = 0, n_ph_entries = 0, n_tuples = 0;
+  DBuf<int64_t> row_ptr, ph_row_ptr;
+  DBuf<uint32_t> e_kpns, ph_kpn;
+  DBuf<double2> e_X;
+  DBuf<int> ph_st;
+  DBuf<double> ph_Y;
+  // BTE
+  DBuf<double> st_eps, st_vel, st_ff, st_wt, W_e, inv_ffW, I0, J0, I, J, I2, J2, Bt, W_ph, inv_nnW, F0, F, G, Btv,
+      seg_part, epart, ppart, kpart, res, prev_in, prev_out, prev_tmp, Dterm, run_w;
+  // segments of the entry stream (drag term) and of the partner runs (self term)
+  DBuf<int> nseg_row, eseg_row, rseg_row, run_flag;
+  DBuf<int64_t> eseg_ptr, eseg_begin, rseg_ptr, rseg_begin, run_ptr, run_idx;
+  DBuf<uint32_t> run_col;
+  int64_t neseg = 0, nrseg = 0, nruns = 0;
+  DBuf<uint32_t> kcrd;
+  DBuf<int2> kinfo;
+  DBuf<int> sctl;               // device-driven sweep loop: stop flag, sweeps done, converged
+  DBuf<unsigned long long> nzero;
+  bool bte_ready = false;
+  ephb_solve_info last{};       // the instance's last solve
+
+  void release_all() {
+    row_ptr.release(); ph_row_ptr.release(); e_kpns.release(); ph_kpn.release(); e_X.release(); ph_st.release();
+    ph_Y.release();
+    for (auto *b : {&st_eps, &st_vel, &st_ff, &st_wt, &W_e, &inv_ffW, &I0, &J0, &I, &J, &I2, &J2, &Bt, &W_ph,
+                    &inv_nnW, &F0, &F, &G, &Btv, &seg_part, &epart, &ppart, &kpart, &res, &prev_in, &prev_out,
+                    &prev_tmp, &Dterm, &run_w})
+      b->release();
+    nseg_row.release(); eseg_row.release(); rseg_row.release(); run_flag.release(); eseg_ptr.release();
+    eseg_begin.release(); rseg_ptr.release(); rseg_begin.release(); run_ptr.release(); run_idx.release();
+    run_col.release(); kcrd.release(); kinfo.release(); sctl.release(); nzero.release();
+    bte_ready = false;
+  }
+};
+
+}  // namespace
+
+struct ephb_ctx : InstState {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -103,13 +145,10 @@ struct ephb_ctx {
   DBuf<int> rep, op, stab, flag, ibzw_list, ibzw_of, npairs, pair_q, pair_i, qcount, pq_rank;
   DBuf<int64_t> pos, pair_ptr, qpair_ptr, scratch, scal;
 
-  // rates
-  double T = 300, mu = 0;
-  int64_t n_entries = 0, n_ph_entries = 0, n_tuples = 0;
-  DBuf<int> cntE, cntPh, ph_st;
-  DBuf<int64_t> escan, phscan, row_ptr, ph_row_ptr;
-  DBuf<uint32_t> e_kpns, ph_kpn;
-  DBuf<double2> e_X, Tbuf, Abuf;
+  // rates (scratch shared by the instances)
+  DBuf<int> cntE, cntPh;
+  DBuf<int64_t> escan, phscan;
+  DBuf<double2> Tbuf, Abuf;
   // tensor-core contraction: phase slices, B' slices and scales, work items, output scratch
   DBuf<__nv_bfloat16> phis, bslices;
   DBuf<double> bscale, Cbuf;
@@ -117,22 +156,20 @@ struct ephb_ctx {
   DBuf<int64_t> item_ptr;
   DBuf<double> fk, nbq, wr;
   DBuf<double2> ut;
-  DBuf<double> ph_Y;
-
-  // BTE
-  DBuf<double> st_eps, st_vel, st_ff, st_wt, W_e, inv_ffW, I0, J0, I, J, I2, J2, Bt, W_ph, inv_nnW, F0, F, G, Btv,
-      seg_part, epart, ppart, kpart, res, prev_in, prev_out, prev_tmp, Dterm, run_w;
-  // segments of the entry stream (drag term) and of the partner runs (self term)
-  DBuf<int> nseg_row, eseg_row, rseg_row, run_flag;
-  DBuf<int64_t> eseg_ptr, eseg_begin, rseg_ptr, rseg_begin, run_ptr, run_idx;
-  DBuf<uint32_t> run_col;
-  int64_t neseg = 0, nrseg = 0, nruns = 0;
-  DBuf<uint32_t> kcrd;
-  DBuf<int2> kinfo;
   DBuf<unsigned long long> ucount;
-  DBuf<int> sctl;               // device-driven sweep loop: stop flag, sweeps done, converged
+
+  // T-independent vertex lists over the union of the instance windows (several instances)
+  int64_t u_entries = 0, u_ph_entries = 0;
+  DBuf<int64_t> u_row_ptr, u_ph_row_ptr;
+  DBuf<uint32_t> u_kpns, u_ph_kpn;
+  DBuf<double2> u_X;
+  DBuf<int> u_ph_st;
+  DBuf<double> u_ph_V;
+
+  // instances: the one in use lives in the InstState base, the others in slots
+  int ninst = 1, cur = 0;
+  std::vector<InstState> slots = std::vector<InstState>(1);
   double *host_res = nullptr;   // pinned: kResLen doubles, then the sweep-loop control (4 ints)
-  bool bte_ready = false;
 };
 
 namespace {
@@ -281,22 +318,15 @@ void ephb_destroy(ephb_ctx *ctx) {
   ctx->ibzw_list.release(); ctx->ibzw_of.release(); ctx->npairs.release(); ctx->pair_q.release();
   ctx->pair_i.release(); ctx->qcount.release(); ctx->pq_rank.release(); ctx->pos.release();
   ctx->pair_ptr.release(); ctx->qpair_ptr.release(); ctx->scratch.release(); ctx->scal.release();
-  ctx->cntE.release(); ctx->cntPh.release(); ctx->ph_st.release(); ctx->escan.release(); ctx->phscan.release();
-  ctx->row_ptr.release(); ctx->ph_row_ptr.release(); ctx->e_kpns.release(); ctx->ph_kpn.release();
-  ctx->e_X.release(); ctx->Tbuf.release(); ctx->Abuf.release(); ctx->ph_Y.release();
+  ctx->cntE.release(); ctx->cntPh.release(); ctx->escan.release(); ctx->phscan.release();
+  ctx->Tbuf.release(); ctx->Abuf.release();
   ctx->phis.release(); ctx->bslices.release(); ctx->bscale.release(); ctx->Cbuf.release(); ctx->nitem.release();
   ctx->tc_err.release(); ctx->item_ptr.release(); ctx->fk.release(); ctx->nbq.release(); ctx->wr.release();
-  ctx->ut.release();
-  ctx->st_eps.release(); ctx->st_vel.release(); ctx->st_ff.release(); ctx->st_wt.release(); ctx->W_e.release();
-  ctx->inv_ffW.release(); ctx->I0.release(); ctx->J0.release(); ctx->I.release(); ctx->J.release();
-  ctx->I2.release(); ctx->J2.release(); ctx->Bt.release(); ctx->W_ph.release(); ctx->inv_nnW.release();
-  ctx->F0.release(); ctx->F.release(); ctx->G.release(); ctx->Btv.release(); ctx->seg_part.release();
-  ctx->epart.release(); ctx->ppart.release(); ctx->kpart.release(); ctx->nseg_row.release();
-  ctx->eseg_row.release(); ctx->rseg_row.release(); ctx->run_flag.release(); ctx->eseg_ptr.release();
-  ctx->eseg_begin.release(); ctx->rseg_ptr.release(); ctx->rseg_begin.release(); ctx->run_ptr.release();
-  ctx->run_idx.release(); ctx->run_col.release(); ctx->Dterm.release(); ctx->run_w.release();
-  ctx->res.release(); ctx->prev_in.release(); ctx->prev_out.release(); ctx->prev_tmp.release();
-  ctx->kcrd.release(); ctx->kinfo.release(); ctx->ucount.release(); ctx->sctl.release();
+  ctx->ut.release(); ctx->ucount.release();
+  ctx->u_row_ptr.release(); ctx->u_ph_row_ptr.release(); ctx->u_kpns.release(); ctx->u_ph_kpn.release();
+  ctx->u_X.release(); ctx->u_ph_st.release(); ctx->u_ph_V.release();
+  ctx->release_all();
+  for (auto &sl : ctx->slots) sl.release_all();
   if (ctx->host_res) cudaFreeHost(ctx->host_res);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -493,23 +523,124 @@ ephb_status ephb_build_meshes_ibz(ephb_ctx *ctx, const ephb_mesh_opts *o, ephb_m
 }
 
 // ---------------------------------------------------------------------------------------
+namespace {
+
+// Put instance i in the InstState base; the one there goes back to its slot.
+void select_instance(ephb_ctx *ctx, int i) {
+  if (i == ctx->cur) return;
+  InstState &base = *ctx;
+  std::swap(base, ctx->slots[ctx->cur]);
+  std::swap(base, ctx->slots[i]);
+  ctx->cur = i;
+}
+
+// n instances, every one without a solution; instance 0 in the base
+void set_instances(ephb_ctx *ctx, int n) {
+  select_instance(ctx, 0);
+  while (int(ctx->slots.size()) > n) {
+    ctx->slots.back().release_all();
+    ctx->slots.pop_back();
+  }
+  ctx->slots.resize(n);
+  ctx->ninst = n;
+  ctx->bte_ready = false;
+  for (int i = 1; i < n; ++i) ctx->slots[i].bte_ready = false;
+}
+
+// The lists just computed (vertex-only) become the union lists; each instance then takes the
+// entries of its window with its occupation factors.
+ephb_status derive_instances(ephb_ctx *ctx, const ephb_thermo *inst, int ninst) {
+  cudaStream_t st = ctx->stream;
+  const ModelDev &M = ctx->M;
+  const int64_t nst = ctx->n_ibzw * M.nb, nph = ctx->qm.size() * M.nbr;
+  std::swap(ctx->u_row_ptr, ctx->row_ptr);
+  std::swap(ctx->u_ph_row_ptr, ctx->ph_row_ptr);
+  std::swap(ctx->u_kpns, ctx->e_kpns);
+  std::swap(ctx->u_ph_kpn, ctx->ph_kpn);
+  std::swap(ctx->u_X, ctx->e_X);
+  std::swap(ctx->u_ph_st, ctx->ph_st);
+  std::swap(ctx->u_ph_V, ctx->ph_Y);
+  ctx->u_entries = ctx->n_entries;
+  ctx->u_ph_entries = ctx->n_ph_entries;
+  const int64_t n_tuples = ctx->n_tuples;
+  CK(ctx->cntE.ensure(nst > 0 ? nst : 1));
+  CK(ctx->cntPh.ensure(nph > 0 ? nph : 1));
+  CK(ctx->scratch.ensure(scan_scratch_elems(nst > nph ? nst : nph)));
+  CK(ctx->fk.ensure(size_t(ctx->km.size()) * M.nb));
+  CK(ctx->nbq.ensure(size_t(nph)));
+  CK(ctx->wr.ensure(size_t(nph)));
+  CK(ctx->ut.ensure(size_t(nph) * M.nbr));
+  for (int i = 0; i < ninst; ++i) {
+    select_instance(ctx, i);
+    ctx->T = inst[i].T_K;
+    ctx->mu = inst[i].mu_eV;
+    const bool own = inst[i].window_lo_eV < inst[i].window_hi_eV;
+    ctx->win_lo = own ? std::max(inst[i].window_lo_eV, ctx->lo) : ctx->lo;
+    ctx->win_hi = own ? std::min(inst[i].window_hi_eV, ctx->hi) : ctx->hi;
+    ctx->n_tuples = n_tuples;
+    ctx->bte_ready = false;
+    MeshDev D = mesh_view(ctx);
+    const InstWindow w{ctx->win_lo, ctx->win_hi};
+    CK(launch_epi_tables(M, D, ctx->T, ctx->mu, ctx->fk.p, ctx->nbq.p, ctx->wr.p, ctx->ut.p, st));
+    CK(launch_inst_count(M, D, w, ctx->u_row_ptr.p, ctx->u_kpns.p, ctx->u_ph_row_ptr.p, ctx->u_ph_st.p,
+                         ctx->u_ph_kpn.p, ctx->cntE.p, ctx->cntPh.p, st));
+    CK(ctx->row_ptr.ensure(nst + 1));
+    CK(ctx->ph_row_ptr.ensure(nph + 1));
+    CK(exclusive_scan<int>(ctx->cntE.p, ctx->row_ptr.p, nst, ctx->scal.p + 3, ctx->scratch.p, ctx->scratch.n, st));
+    CK(exclusive_scan<int>(ctx->cntPh.p, ctx->ph_row_ptr.p, nph, ctx->scal.p + 4, ctx->scratch.p, ctx->scratch.n,
+                           st));
+    CK(cudaMemcpyAsync(ctx->row_ptr.p + nst, ctx->scal.p + 3, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ctx->ph_row_ptr.p + nph, ctx->scal.p + 4, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    int64_t hs[2];
+    CK(cudaMemcpyAsync(hs, ctx->scal.p + 3, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    ctx->n_entries = hs[0];
+    ctx->n_ph_entries = hs[1];
+    CK(ctx->e_kpns.ensure(ctx->n_entries));
+    CK(ctx->e_X.ensure(ctx->n_entries));
+    CK(ctx->ph_st.ensure(ctx->n_ph_entries));
+    CK(ctx->ph_kpn.ensure(ctx->n_ph_entries));
+    CK(ctx->ph_Y.ensure(ctx->n_ph_entries));
+    CK(launch_inst_fill(M, D, w, ctx->fk.p, ctx->nbq.p, ctx->u_row_ptr.p, ctx->u_kpns.p, ctx->u_X.p,
+                        ctx->u_ph_row_ptr.p, ctx->u_ph_st.p, ctx->u_ph_kpn.p, ctx->u_ph_V.p, ctx->row_ptr.p,
+                        ctx->ph_row_ptr.p, ctx->e_kpns.p, ctx->e_X.p, ctx->ph_st.p, ctx->ph_kpn.p, ctx->ph_Y.p, st));
+  }
+  select_instance(ctx, 0);
+  return EPHB_OK;
+}
+
+}  // namespace
+
 ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst, int ninst, const ephb_delta *delta,
                                           ephb_precision precision, ephb_rates_info *out) {
   if (!ctx) return EPHB_EINVAL;
   if (ctx->stage < 2) return fail(ctx, EPHB_ESTATE, "build_meshes_ibz must come first");
   if (!inst || !delta) return fail(ctx, EPHB_EINVAL, "NULL argument");
-  if (ninst != 1) return fail(ctx, EPHB_EINVAL, "only one (T, mu) instance per call is supported");
+  if (ninst < 1 || ninst > EPHB_MAX_INSTANCES) return fail(ctx, EPHB_EINVAL, "ninst out of range");
   if (precision != EPHB_FP64 && precision != EPHB_FP64_SLICED && precision != EPHB_SPLIT_BF16)
     return fail(ctx, EPHB_EINVAL, "precision must be EPHB_FP64, EPHB_FP64_SLICED or EPHB_SPLIT_BF16");
-  if (!(inst->T_K > 0) || !(delta->sigma_eV > 0) || !(delta->cutoff_sigmas > 0))
-    return fail(ctx, EPHB_EINVAL, "T, sigma and cutoff must be positive");
+  if (!(delta->sigma_eV > 0) || !(delta->cutoff_sigmas > 0))
+    return fail(ctx, EPHB_EINVAL, "sigma and cutoff must be positive");
+  bool windowed = false;
+  for (int i = 0; i < ninst; ++i) {
+    if (!(inst[i].T_K > 0)) return fail(ctx, EPHB_EINVAL, "T must be positive");
+    if (inst[i].window_lo_eV < inst[i].window_hi_eV &&
+        (inst[i].window_lo_eV > ctx->lo || inst[i].window_hi_eV < ctx->hi))
+      windowed = true;
+  }
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
   const ModelDev &M = ctx->M;
   const int nb = M.nb, nbr = M.nbr;
   const int64_t nq = ctx->qm.size();
+  // several instances (or a window narrower than the meshes'): one T-independent vertex pass
+  // over the mesh window, then the rate lists of every instance from it
+  const bool multi = ninst > 1 || windowed;
+  set_instances(ctx, ninst);
   ctx->T = inst->T_K;
   ctx->mu = inst->mu_eV;
+  ctx->win_lo = ctx->lo;
+  ctx->win_hi = ctx->hi;
   cudaEvent_t ev0, ev1;
   CK(cudaEventCreate(&ev0));
   CK(cudaEventCreate(&ev1));
@@ -521,6 +652,7 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
   rp.cut = delta->cutoff_sigmas * delta->sigma_eV;
   rp.inv_Nq_pref = 2.0 * kPi / (kHbarEVs * double(nq));
   rp.y_scale = double(nq) / double(ctx->km.size());
+  rp.vertex_only = multi ? 1 : 0;
   const int64_t np = ctx->n_pairs;
   CK(ctx->cntE.ensure(np * nb));
   CK(ctx->cntPh.ensure(np * nbr));
@@ -560,10 +692,11 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     CK(ctx->Tbuf.ensure(size_t(chunk) * per_k));
     CK(ctx->Abuf.ensure(size_t(chunk) * stage_a_A_elems(M)));
   }
-  EventTimer ta, tb, tc;
+  EventTimer ta, tb, tc, tg;
   CK(ta.init());
   CK(tb.init());
   CK(tc.init());
+  CK(tg.init());
   const bool tensor = precision != EPHB_FP64;
   const int ns = precision == EPHB_FP64_SLICED ? 7 : 3;
   std::vector<int64_t> hpp;
@@ -612,7 +745,8 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     } else {
       CK(launch_vertex_tc(M, D, ns, i0, nkc, hpp[i0], ctx->Abuf.p, ctx->phis.p, ctx->bslices.p, ctx->bscale.p,
                           ctx->nitem.p, ctx->item_ptr.p, ctx->scratch.p, ctx->scratch.n, ctx->scal.p + 6,
-                          ctx->Cbuf.p, ctx->tc_err.p, st));
+                          ctx->Cbuf.p, ctx->tc_err.p, st, tg.a, tg.b));
+      tg.pending = true;
       CK(tb.stop(st));
       CK(tc.start(st));
       CK(launch_vertex_epilogue(M, D, rp, hpp[i0], hpp[i0 + nkc], hpp[i0], ctx->Cbuf.p, Nmax, ctx->fk.p,
@@ -624,6 +758,7 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     CK(ta.collect());
     CK(tb.collect());
     CK(tc.collect());
+    CK(tg.collect());
     i0 += nkc;
   }
   double tensor_flops = 0.0;
@@ -638,6 +773,10 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
   }
   unsigned long long cnt[5];
   CK(cudaMemcpyAsync(cnt, ctx->ucount.p, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+  if (multi) {
+    ephb_status r = derive_instances(ctx, inst, ninst);
+    if (r != EPHB_OK) return r;
+  }
   CK(cudaEventRecord(ev1, st));
   CK(cudaEventSynchronize(ev1));
   float ms = 0;
@@ -658,9 +797,9 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     out->ms_epilogue = tc.ms;
     out->tensor_flops = tensor_flops;
     out->rot_flops = double(cnt[4]);
+    out->ms_gemm = tg.ms;
   }
   ctx->stage = 3;
-  ctx->bte_ready = false;
   return EPHB_OK;
 }
 
@@ -691,10 +830,12 @@ ephb_status bte_setup(ephb_ctx *ctx) {
   for (auto *b : {&ctx->res, &ctx->prev_in, &ctx->prev_out, &ctx->prev_tmp}) CK(b->ensure(kResLen));
   CK(ctx->sctl.ensure(4));
   MeshDev D = mesh_view(ctx);
-  CK(launch_state_setup(M, D, ctx->T, ctx->mu, ctx->st_eps.p, ctx->st_vel.p, ctx->st_ff.p, ctx->st_wt.p,
+  CK(launch_state_setup(M, D, ctx->T, ctx->mu, ctx->win_lo, ctx->win_hi, ctx->st_eps.p, ctx->st_vel.p, ctx->st_ff.p, ctx->st_wt.p,
                         ctx->kcrd.p, ctx->kinfo.p, st));
   BteDev B = bte_view(ctx);
-  CK(launch_rta_electron(B, ctx->W_e.p, ctx->inv_ffW.p, ctx->I0.p, ctx->J0.p, ctx->ucount.p + 1, st));
+  CK(ctx->nzero.ensure(1));
+  CK(cudaMemsetAsync(ctx->nzero.p, 0, sizeof(unsigned long long), st));
+  CK(launch_rta_electron(B, ctx->W_e.p, ctx->inv_ffW.p, ctx->I0.p, ctx->J0.p, ctx->nzero.p, st));
   CK(launch_ph_rowsum(B, ctx->Bt.p, st));
   CK(launch_rta_phonon(M, D, B, ctx->Bt.p, ctx->W_ph.p, ctx->inv_nnW.p, ctx->F0.p, st));
   // partner runs of the electron rows (self term), then segments of the entry stream
@@ -766,13 +907,10 @@ ephb_status coefficients_to_host(ephb_ctx *ctx, double *prev, bool electron = tr
 
 constexpr int kSweepBatch = 8;   // electron sweeps queued per host round trip
 
-ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *out) {
-  if (!ctx) return EPHB_EINVAL;
-  if (ctx->stage < 3) return fail(ctx, EPHB_ESTATE, "compute_transition_rates must come first");
-  if (!o) return fail(ctx, EPHB_EINVAL, "opts is NULL");
-  if (o->level < EPHB_RTA || o->level > EPHB_DRAGGED) return fail(ctx, EPHB_EINVAL, "bad level");
-  if (!(o->tol > 0) || o->max_outer < 1 || o->max_inner < 1) return fail(ctx, EPHB_EINVAL, "bad tolerances");
-  CK(cudaSetDevice(ctx->device));
+namespace {
+
+// The coupled solve of the instance in the InstState base.
+ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *out) {
   cudaStream_t st = ctx->stream;
   cudaEvent_t ev0, ev1;
   CK(cudaEventCreate(&ev0));
@@ -797,9 +935,11 @@ ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb
   bool converged = o->level == EPHB_RTA;
   double residual = 0.0, lambda = 1.0;
   EventTimer te, tp, td;
+  EventTimer tsw[kSweepBatch];   // the self-term kernel of each queued sweep
   CK(te.init());
   CK(tp.init());
   CK(td.init());
+  for (auto &t : tsw) CK(t.init());
 
   auto inner_loop = [&](int drag, bool &ok) -> ephb_status {
     ok = false;
@@ -824,7 +964,8 @@ ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb
       for (int j = 0; j < nb; ++j) {
         CK(launch_self_sweep(M, B, S, ctx->run_col.p, ctx->run_w.p, ctx->I0.p, ctx->J0.p, ctx->inv_ffW.p, ctx->I.p,
                              ctx->J.p, ctx->I2.p, ctx->J2.p, drag ? ctx->Dterm.p : nullptr, ctx->seg_part.p,
-                             ctx->epart.p, ctx->sctl.p, st));
+                             ctx->epart.p, ctx->sctl.p, st, tsw[j].a, tsw[j].b));
+        tsw[j].pending = true;
         // the sweep already wrote the electron partial sums; the phonon ones are unchanged
         CK(launch_coeff_final(ctx->M, B, ctx->epart.p, ctx->ppart.p, ctx->res.p, ctx->prev_in.p, st, ctx->sctl.p,
                               o->max_inner, inner_tol));
@@ -836,6 +977,7 @@ ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb
       CK(cudaStreamSynchronize(st));
       CK(te.collect());
       CK(td.collect());
+      for (int j = 0; j < nb; ++j) CK(tsw[j].collect());
       if (hctl[0] || queued >= o->max_inner) break;
     }
     const int done = hctl[1];
@@ -884,7 +1026,7 @@ ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb
     if (outer > o->max_outer) outer = o->max_outer;
   }
   unsigned long long nzero = 0;
-  CK(cudaMemcpyAsync(&nzero, ctx->ucount.p + 1, sizeof(nzero), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&nzero, ctx->nzero.p, sizeof(nzero), cudaMemcpyDeviceToHost, st));
   CK(cudaEventRecord(ev1, st));
   CK(cudaEventSynchronize(ev1));
   float ms = 0;
@@ -901,6 +1043,11 @@ ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb
     out->n_sweeps = sweeps;
     out->ms = ms;
     out->ms_e_sweep = te.ms;
+    double ms_self = 0.0;
+    for (auto &t : tsw) ms_self += t.ms;
+    out->ms_self_kernel = ms_self;
+    // FP64 work of one self-term sweep: 6 multiply-adds per run (+ two 3x3 rotations with symmetry)
+    out->e_sweep_flops = double(ctx->nruns) * (ctx->M.nsym > 1 ? 12.0 + 36.0 : 12.0);
     out->ms_ph_sweep = tp.ms;
     // per electron sweep: the entry stream (k'|n|s word + X+,X-) plus the per-row arrays
     // per electron sweep: the run stream (partner word + weight) plus the per-row arrays
@@ -909,16 +1056,60 @@ ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb
     out->ms_drag = td.ms;
     out->n_runs = ctx->nruns;
   }
-  ctx->stage = 4;
   if (!converged) return fail(ctx, EPHB_ENOCONV, "iteration limit reached before the tolerance");
+  return EPHB_OK;
+}
+
+}  // namespace
+
+ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *out) {
+  if (!ctx) return EPHB_EINVAL;
+  if (ctx->stage < 3) return fail(ctx, EPHB_ESTATE, "compute_transition_rates must come first");
+  if (!o) return fail(ctx, EPHB_EINVAL, "opts is NULL");
+  if (o->level < EPHB_RTA || o->level > EPHB_DRAGGED) return fail(ctx, EPHB_EINVAL, "bad level");
+  if (!(o->tol > 0) || o->max_outer < 1 || o->max_inner < 1) return fail(ctx, EPHB_EINVAL, "bad tolerances");
+  CK(cudaSetDevice(ctx->device));
+  // every instance in turn; the summary adds up counts and times and keeps the worst residual
+  ephb_solve_info sum{};
+  sum.converged = 1;
+  sum.lambda = 1.0;
+  bool noconv = false;
+  for (int i = 0; i < ctx->ninst; ++i) {
+    select_instance(ctx, i);
+    ephb_solve_info one{};
+    const ephb_status r = solve_one(ctx, o, &one);
+    if (r != EPHB_OK && r != EPHB_ENOCONV) return r;
+    noconv = noconv || r == EPHB_ENOCONV;
+    ctx->last = one;
+    sum.outer_iters = std::max(sum.outer_iters, one.outer_iters);
+    sum.inner_iters_total += one.inner_iters_total;
+    sum.converged = sum.converged && one.converged;
+    sum.n_zero_rate_states += one.n_zero_rate_states;
+    sum.residual = std::max(sum.residual, one.residual);
+    sum.lambda = one.lambda;
+    sum.n_sweeps += one.n_sweeps;
+    sum.ms += one.ms;
+    sum.ms_e_sweep += one.ms_e_sweep;
+    sum.ms_ph_sweep += one.ms_ph_sweep;
+    sum.e_sweep_bytes += one.e_sweep_bytes;
+    sum.ms_drag += one.ms_drag;
+    sum.n_runs += one.n_runs;
+    sum.ms_self_kernel += one.ms_self_kernel;
+    sum.e_sweep_flops += one.e_sweep_flops;
+  }
+  select_instance(ctx, 0);
+  if (out) *out = sum;
+  ctx->stage = 4;
+  if (noconv) return fail(ctx, EPHB_ENOCONV, "iteration limit reached before the tolerance");
   return EPHB_OK;
 }
 
 ephb_status ephb_transport_coefficients(ephb_ctx *ctx, int inst, ephb_coeffs *out) {
   if (!ctx) return EPHB_EINVAL;
-  if (ctx->stage < 4 || !ctx->bte_ready) return fail(ctx, EPHB_ESTATE, "solve_coupled_bte must come first");
-  if (inst != 0) return fail(ctx, EPHB_EINVAL, "inst must be 0");
+  if (inst < 0 || inst >= ctx->ninst) return fail(ctx, EPHB_EINVAL, "inst out of range");
   if (!out) return fail(ctx, EPHB_EINVAL, "out is NULL");
+  select_instance(ctx, inst);
+  if (ctx->stage < 4 || !ctx->bte_ready) return fail(ctx, EPHB_ESTATE, "solve_coupled_bte must come first");
   CK(cudaSetDevice(ctx->device));
   ephb_status s = coefficients_to_host(ctx, ctx->prev_tmp.p);
   if (s != EPHB_OK) return s;
@@ -935,6 +1126,22 @@ ephb_status ephb_transport_coefficients(ephb_ctx *ctx, int inst, ephb_coeffs *ou
 }
 
 // ---------------------------------------------------------------------------------------
+ephb_status ephb_instance_solve_info(ephb_ctx *ctx, int inst, ephb_solve_info *out) {
+  if (!ctx || !out) return EPHB_EINVAL;
+  if (inst < 0 || inst >= ctx->ninst) return fail(ctx, EPHB_EINVAL, "inst out of range");
+  *out = inst == ctx->cur ? ctx->last : ctx->slots[inst].last;
+  return EPHB_OK;
+}
+
+ephb_status ephb_select_instance(ephb_ctx *ctx, int inst) {
+  if (!ctx) return EPHB_EINVAL;
+  if (inst < 0 || inst >= ctx->ninst) return fail(ctx, EPHB_EINVAL, "inst out of range");
+  select_instance(ctx, inst);
+  return EPHB_OK;
+}
+
+int ephb_num_instances(const ephb_ctx *ctx) { return ctx ? ctx->ninst : 0; }
+
 ephb_status ephb_get_device_array(ephb_ctx *ctx, int which, void **dptr, int64_t shape[4], int *dtype) {
   if (!ctx || !dptr || !shape || !dtype) return EPHB_EINVAL;
   const int64_t nk = ctx->km.size(), nq = ctx->qm.size(), nb = ctx->M.nb, nbr = ctx->M.nbr;

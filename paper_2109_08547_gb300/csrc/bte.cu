@@ -32,16 +32,16 @@ __device__ inline int q_image(const Mesh &qm, const int *rot, int q) {
                  pmod(rot[6] * b0 + rot[7] * b1 + rot[8] * b2, qm.n[2]));
 }
 
-__global__ void k_state_setup(ModelDev M, MeshDev D, double T, double mu, double *st_eps, double *st_vel,
-                              double *st_ff, double *st_wt, uint32_t *kcrd, int2 *kinfo) {
+__global__ void k_state_setup(ModelDev M, MeshDev D, double T, double mu, double lo, double hi, double *st_eps,
+                              double *st_vel, double *st_ff, double *st_wt, uint32_t *kcrd, int2 *kinfo) {
   int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   const int nb = M.nb;
   if (t < D.n_ibzw * nb) {
     int64_t i = t / nb;
     int m = int(t % nb);
     int k = D.ibzw_list[i];
-    bool act = (D.amask[k] >> m) & 1u;
     double e = D.eps[size_t(k) * nb + m];
+    bool act = ((D.amask[k] >> m) & 1u) && e >= lo && e <= hi;
     double f = fermi_b(e, mu, kKbEVK * T);
     st_eps[t] = e;
     for (int a = 0; a < 3; ++a) st_vel[t * 3 + a] = D.vel[(size_t(k) * nb + m) * 3 + a];
@@ -641,11 +641,12 @@ __global__ void k_ko_apply(BteDev B, double *I, const double *J, const double *r
 int coeff_partials() { return kNPart; }
 int sweep_segment_len() { return kSeg; }
 
-cudaError_t launch_state_setup(const ModelDev &M, const MeshDev &D, double T, double mu, double *st_eps,
-                               double *st_vel, double *st_ff, double *st_wt, uint32_t *kcrd, int2 *kinfo,
-                               cudaStream_t st) {
+cudaError_t launch_state_setup(const ModelDev &M, const MeshDev &D, double T, double mu, double lo, double hi,
+                               double *st_eps, double *st_vel, double *st_ff, double *st_wt, uint32_t *kcrd,
+                               int2 *kinfo, cudaStream_t st) {
   int64_t n = D.n_ibzw * M.nb > D.nk ? D.n_ibzw * M.nb : D.nk;
-  EPHB_LAUNCH(k_state_setup, unsigned((n + 255) / 256), 256, 0, st, M, D, T, mu, st_eps, st_vel, st_ff, st_wt, kcrd, kinfo);
+  EPHB_LAUNCH(k_state_setup, unsigned((n + 255) / 256), 256, 0, st, M, D, T, mu, lo, hi, st_eps, st_vel, st_ff, st_wt,
+              kcrd, kinfo);
   return cudaGetLastError();
 }
 
@@ -722,7 +723,11 @@ cudaError_t launch_fill_runs(const BteDev &B, int64_t n_entries, int64_t nruns, 
 cudaError_t launch_self_sweep(const ModelDev &M, const BteDev &B, const SweepSegs &S, const uint32_t *run_col,
                               const double *run_w, const double *I0, const double *J0, const double *inv_ffW,
                               double *Ia, double *Ja, double *Ib, double *Jb, const double *Dterm, double *part,
-                              double *epart, const int *ctl, cudaStream_t st) {
+                              double *epart, const int *ctl, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
+  if (ev0) {
+    cudaError_t e = cudaEventRecord(ev0, st);
+    if (e != cudaSuccess) return e;
+  }
   if (S.nseg > 0) {
     const unsigned grid = unsigned((S.nseg * 32 + 255) / 256);
     if (M.nsym > 1)
@@ -730,6 +735,10 @@ cudaError_t launch_self_sweep(const ModelDev &M, const BteDev &B, const SweepSeg
     else
       EPHB_LAUNCH(k_self_sweep_seg<false>, grid, 256, 0, st, M, S, run_col, run_w, Ia, Ja, Ib, Jb, ctl, part);
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (ev1) {
+    cudaError_t e = cudaEventRecord(ev1, st);
     if (e != cudaSuccess) return e;
   }
   EPHB_LAUNCH(k_e_finalize, kNPart, kCT, 0, st, B, S, part, Dterm, I0, J0, inv_ffW, Ib, Jb, Ia, Ja, ctl, epart);

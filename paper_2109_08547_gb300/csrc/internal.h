@@ -79,6 +79,7 @@ cudaError_t launch_count_reps(const int *rep, int64_t n, int64_t *out, cudaStrea
 struct RateParams {
   double T, mu, sigma, cut, inv_Nq_pref;   // inv_Nq_pref = 2 pi / (hbar N_q)
   double y_scale;                          // N_q / N_k
+  int vertex_only;                         // 1: store V+- = 2pi/(hbar N_q)|g|^2 delta (no occupations)
 };
 cudaError_t launch_rate_count(const ModelDev &M, const MeshDev &D, RateParams rp, int *cntE, int *cntPh,
                               unsigned long long *n_tuples, cudaStream_t st);
@@ -111,7 +112,8 @@ cudaError_t launch_phase_slices(const ModelDev &M, const MeshDev &D, int ns, __n
 cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_t i0, int64_t nkc, int64_t pair_base,
                              const double2 *A, const __nv_bfloat16 *phis, __nv_bfloat16 *bs, double *bscale,
                              int *nitem, int64_t *item_ptr, int64_t *scratch, int64_t scratch_elems,
-                             int64_t *total_dev, double *Cbuf, int *err, cudaStream_t st);
+                             int64_t *total_dev, double *Cbuf, int *err, cudaStream_t st,
+                             cudaEvent_t gemm0 = nullptr, cudaEvent_t gemm1 = nullptr);
 
 // ---- bte.cu
 struct BteDev {
@@ -132,9 +134,23 @@ struct BteDev {
   const double *st_wt;     // [nst] 1/|stab| (0 for inactive)
 };
 // kinfo[k] = (state base of the representative <k> = ibzw index * nb (or -1), op taking <k> to k)
-cudaError_t launch_state_setup(const ModelDev &M, const MeshDev &D, double T, double mu, double *st_eps,
-                               double *st_vel, double *st_ff, double *st_wt, uint32_t *kcrd, int2 *kinfo,
-                               cudaStream_t st);
+// States active for the BTE: active on the meshes and lo <= eps <= hi (the instance window).
+cudaError_t launch_state_setup(const ModelDev &M, const MeshDev &D, double T, double mu, double lo, double hi,
+                               double *st_eps, double *st_vel, double *st_ff, double *st_wt, uint32_t *kcrd,
+                               int2 *kinfo, cudaStream_t st);
+// Rate lists of one (T, mu, window) instance from the T-independent vertex lists (V+-, V+ Y-scaled):
+// count the kept entries of every electron row (k, m) and phonon row (q, s), then write them
+// (order kept) with X+- = V+- f(1-f') {n, 1+n} and Y = V f(1-f') n.  fk, nbq: occupation tables.
+struct InstWindow { double lo, hi; };
+cudaError_t launch_inst_count(const ModelDev &M, const MeshDev &D, InstWindow w, const int64_t *u_row_ptr,
+                              const uint32_t *u_kpns, const int64_t *u_ph_row_ptr, const int *u_ph_st,
+                              const uint32_t *u_ph_kpn, int *cnt_e, int *cnt_ph, cudaStream_t st);
+cudaError_t launch_inst_fill(const ModelDev &M, const MeshDev &D, InstWindow w, const double *fk, const double *nbq,
+                             const int64_t *u_row_ptr, const uint32_t *u_kpns, const double2 *u_X,
+                             const int64_t *u_ph_row_ptr, const int *u_ph_st, const uint32_t *u_ph_kpn,
+                             const double *u_ph_V, const int64_t *row_ptr, const int64_t *ph_row_ptr,
+                             uint32_t *e_kpns, double2 *e_X, int *ph_st, uint32_t *ph_kpn, double *ph_Y,
+                             cudaStream_t st);
 cudaError_t launch_rta_electron(const BteDev &B, double *W_e, double *inv_ffW, double *I0, double *J0,
                                 unsigned long long *n_zero, cudaStream_t st);
 cudaError_t launch_ph_rowsum(const BteDev &B, double *Bt, cudaStream_t st);
@@ -168,7 +184,8 @@ cudaError_t launch_fill_runs(const BteDev &B, int64_t n_entries, int64_t nruns, 
 cudaError_t launch_self_sweep(const ModelDev &M, const BteDev &B, const SweepSegs &S, const uint32_t *run_col,
                               const double *run_w, const double *I0, const double *J0, const double *inv_ffW,
                               double *Ia, double *Ja, double *Ib, double *Jb, const double *Dterm, double *part,
-                              double *epart, const int *ctl, cudaStream_t st);
+                              double *epart, const int *ctl, cudaStream_t st, cudaEvent_t ev0 = nullptr,
+                              cudaEvent_t ev1 = nullptr);   // events around the self-term kernel
 // Drag term of every row for the current F, G: Dterm[st][6].
 cudaError_t launch_drag_term(const MeshDev &D, const BteDev &B, const SweepSegs &S, const double *F, const double *G,
                              double *part, double *Dterm, cudaStream_t st);

@@ -271,10 +271,16 @@ __device__ void pair_epilogue(const ModelDev &M, const MeshDev &D, const RatePar
       double g2 = sum / double(cnt);
       double dxp = ekp[n] - ek[m] - wq[s];
       double dxm = ekp[n] - ek[m] + wq[s];
-      double fm = fermi_d(ek[m], rp.mu, kT), fn = fermi_d(ekp[n], rp.mu, kT), nq = bose_d(wq[s], kT);
-      double occ = rp.inv_Nq_pref * g2 * fm * (1.0 - fn);
-      xp = occ * nq * gauss_d(dxp, rp.sigma, rp.cut);
-      xm = occ * (1.0 + nq) * gauss_d(dxm, rp.sigma, rp.cut);
+      if (rp.vertex_only) {   // T-independent vertex weights V+-: occupation factors left out
+        const double v = rp.inv_Nq_pref * g2;
+        xp = v * gauss_d(dxp, rp.sigma, rp.cut);
+        xm = v * gauss_d(dxm, rp.sigma, rp.cut);
+      } else {
+        double fm = fermi_d(ek[m], rp.mu, kT), fn = fermi_d(ekp[n], rp.mu, kT), nq = bose_d(wq[s], kT);
+        double occ = rp.inv_Nq_pref * g2 * fm * (1.0 - fn);
+        xp = occ * nq * gauss_d(dxp, rp.sigma, rp.cut);
+        xm = occ * (1.0 + nq) * gauss_d(dxm, rp.sigma, rp.cut);
+      }
       Xps[t] = xp;
       Xms[t] = xm;
       flg[t] = (fabs(dxp) <= rp.cut ? 1 : 0) | (fabs(dxm) <= rp.cut ? 2 : 0);
@@ -517,10 +523,17 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
     }
     const double dxp = ekp[n] - ek[m] - wq[s];
     const double dxm = ekp[n] - ek[m] + wq[s];
-    const double nqs = nbq[size_t(q) * nbr + s];
-    const double occ = rp.inv_Nq_pref * (sum / double(cnt)) * fk[size_t(k) * nb + m] * (1.0 - fk[size_t(kp) * nb + n]);
-    Xp[t] = occ * nqs * gauss_d(dxp, rp.sigma, rp.cut);
-    Xm[t] = occ * (1.0 + nqs) * gauss_d(dxm, rp.sigma, rp.cut);
+    if (rp.vertex_only) {   // T-independent vertex weights V+-: occupation factors left out
+      const double v = rp.inv_Nq_pref * (sum / double(cnt));
+      Xp[t] = v * gauss_d(dxp, rp.sigma, rp.cut);
+      Xm[t] = v * gauss_d(dxm, rp.sigma, rp.cut);
+    } else {
+      const double nqs = nbq[size_t(q) * nbr + s];
+      const double occ =
+          rp.inv_Nq_pref * (sum / double(cnt)) * fk[size_t(k) * nb + m] * (1.0 - fk[size_t(kp) * nb + n]);
+      Xp[t] = occ * nqs * gauss_d(dxp, rp.sigma, rp.cut);
+      Xm[t] = occ * (1.0 + nqs) * gauss_d(dxm, rp.sigma, rp.cut);
+    }
     flg[t] = uint8_t((fabs(dxp) <= rp.cut ? 1 : 0) | (fabs(dxm) <= rp.cut ? 2 : 0));
   }
   // electron rows (k, m): entries ordered (n, s)

@@ -5,7 +5,8 @@
 //   B'(Re columns) = (Re A; -Im A),  B'(Im columns) = (Im A; Re A).
 //
 // Exact fixed-point slicing.  Every operand x in [-1, 1] (the phases as they are, each B'
-// column divided by a power of two sigma_j >= its largest entry) is split as
+// column divided by a power of two sigma_j >= its largest entry) is rounded to a multiple of
+// 2^(-7-8(ns-1)) and split as
 //   x = sum_i s_i,  s_i = n_i 2^(-7-8(i-1)),  |n_i| <= 128,
 // so each slice is an exact BF16 number.  A product of two slices is an integer multiple of
 // 2^(-14-8(i+l-2)) below 2^(-8(i+l-2)) in size, and a K = 256 sum of such products (or the
@@ -40,17 +41,19 @@ constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s bound on any wait
 
 __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-// split x in [-1,1] into ns exact BF16 fixed-point slices
+// Split x in [-1,1] into ns exact BF16 fixed-point slices.  x is rounded once to the 64-bit
+// integer N = rint(x 2^(7+8(ns-1))); N is cut into balanced base-256 digits from the bottom
+// (each in [-128, 127], the top one within [-128, 128]) and digit i becomes the BF16 number
+// n_i 2^(-7-8(i-1)), which is exact.  Two FP64 operations per element; the rest is integer.
 __device__ inline void fixed_slices(double x, int ns, __nv_bfloat16 *out, size_t stride) {
-  double r = x;
-  double scale = 128.0;   // 2^7
-  for (int i = 0; i < ns; ++i) {
-    const double n = rint(r * scale);
-    const double s = n / scale;
-    out[i * stride] = __double2bfloat16(s);
-    r -= s;
-    scale *= 256.0;
+  const int top = 7 + 8 * (ns - 1);
+  long long N = __double2ll_rn(ldexp(x, top));
+  for (int i = ns - 1; i >= 1; --i) {
+    const long long d = ((N + 128) & 255) - 128;   // balanced digit, N - d divisible by 256
+    N = (N - d) >> 8;
+    out[i * stride] = __float2bfloat16_rn(ldexpf(float(d), -7 - 8 * i));
   }
+  out[0] = __float2bfloat16_rn(ldexpf(float(N), -7));
 }
 
 // Phase slices of every q of the phonon mesh: PhiS[q][slice][Kp] (BF16)
@@ -103,6 +106,7 @@ __global__ void k_b_slices(ModelDev M, MeshDev D, int64_t i0, int64_t nkc, const
     frexp(mx, &ex);          // mx = f 2^ex, f in [0.5, 1): 2^ex >= mx
   }
   const double sigma = mx > 0.0 ? ldexp(1.0, ex) : 1.0;
+  const double inv_sigma = mx > 0.0 ? ldexp(1.0, -ex) : 1.0;
   if (lane == 0) bscale[kc * Nmax + jp] = sigma;
   __nv_bfloat16 *dst = bs + (size_t(kc) * ns * Nmax + jp) * Kp;
   const size_t sstride = size_t(Nmax) * Kp;
@@ -112,7 +116,7 @@ __global__ void k_b_slices(ModelDev M, MeshDev D, int64_t i0, int64_t nkc, const
       const double2 a = Ak[size_t(r < R ? r : r - R) * jmax + j];
       v = r < R ? (part == 0 ? a.x : a.y) : (part == 0 ? -a.y : a.x);
     }
-    fixed_slices(v / sigma, ns, dst + r, sstride);
+    fixed_slices(v * inv_sigma, ns, dst + r, sstride);   // sigma is a power of two: exact
   }
 }
 
@@ -357,7 +361,8 @@ cudaError_t launch_phase_slices(const ModelDev &M, const MeshDev &D, int ns, __n
 cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_t i0, int64_t nkc, int64_t pair_base,
                              const double2 *A, const __nv_bfloat16 *phis, __nv_bfloat16 *bs, double *bscale,
                              int *nitem, int64_t *item_ptr, int64_t *scratch, int64_t scratch_elems,
-                             int64_t *total_dev, double *Cbuf, int *err, cudaStream_t st) {
+                             int64_t *total_dev, double *Cbuf, int *err, cudaStream_t st, cudaEvent_t gemm0,
+                             cudaEvent_t gemm1) {
   if (nkc <= 0) return cudaSuccess;
   const int Kp = tc_kp(M), Nmax = tc_nmax(M), ncm = tc_nc_max(ns);
   const int64_t nw = nkc * Nmax;
@@ -381,6 +386,10 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
   P.nkc = nkc;
   P.pair_base = pair_base;
   const size_t smem = tc_smem_bytes(ns);
+  if (gemm0) {
+    e = cudaEventRecord(gemm0, st);
+    if (e != cudaSuccess) return e;
+  }
   if (ns == 7) {
     e = cudaFuncSetAttribute(k_vertex_gemm<7, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
@@ -392,7 +401,9 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
     EPHB_LAUNCH((k_vertex_gemm<3, 2>), unsigned(nitems), kTcThreads, smem, st, M, D, P, item_ptr, phis, bs, bscale,
                 Cbuf, err);
   }
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e == cudaSuccess && gemm1) e = cudaEventRecord(gemm1, st);
+  return e;
 }
 
 }  // namespace ephb

@@ -17,7 +17,7 @@ HEADER = os.path.join(ROOT, "include", "ephb.h")
 
 def _declared():
     txt = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:ephb_status|void|int64_t|const char \*)\s*(ephb_\w+)\s*\(", txt, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:ephb_status|void|int64_t|int|const char \*)\s*(ephb_\w+)\s*\(", txt, re.M)))
 
 
 def test_header_declares_the_five_calls():
