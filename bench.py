@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--precision", default="fp64-sliced", choices=["fp64", "fp64-sliced", "split-bf16"],
                    help="vertex contraction: FP64 CUDA cores, FP64-grade tensor-core slices, or mixed precision")
     p.add_argument("--no-variants", action="store_true", help="skip the one-step timings of the other precisions")
+    p.add_argument("--instances", type=int, default=8,
+                   help="(T, mu, window) instances of the batched-vs-sequential comparison (0: skip it)")
     p.add_argument("--fp64-peak", action="store_true",
                    help="measure FP64 and FP32 FMA throughput with a small probe kernel and exit")
     return p.parse_args()
@@ -220,6 +222,58 @@ def _rates_subset(O, P, row, qmask):
     keep[kps[qmask]] = act[kps[qmask]]
     keep[row] = act[row]
     return O.transition_rates(dataclasses.replace(P, active=keep), ks=[row])
+
+
+def batched_block(B, ctx, wl, args, flush, torch, np):
+    """The batched form against sequential plain FP64 runs on the same meshes.
+
+    Instances: synthetic.instance_grid (T in [100, 500] K, mu0 +- 0.2 eV, windows mu +- 0.25 eV).
+    Sequential: for each instance the whole FP64 path on its own window (meshes, rates, solve,
+    coefficients).  Batched: meshes on the union window, one rates call for all instances in
+    this run's precision (the vertex interpolated once), one solve, the coefficients.  Both are
+    wall times between device synchronisations; errors are per-coefficient relative Frobenius
+    differences of the batched result from the sequential FP64 one."""
+    import dataclasses
+    from paper_2109_08547_gb300 import synthetic as S
+    insts = S.instance_grid(args.instances, wl.mu_eV)
+    union = (min(i[2] for i in insts), max(i[3] for i in insts))
+    seq_coeffs, seq_s = [], 0.0
+    for T, mu, lo, hi in insts:
+        w1 = dataclasses.replace(wl, T_K=T, mu_eV=mu, window=(lo, hi))
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = B.run_path(ctx, w1, level="dragged", ko_correction=True, precision=B.FP64)
+        torch.cuda.synchronize()
+        seq_s += time.perf_counter() - t0
+        seq_coeffs.append(r.coeffs)
+
+    def batched_run():
+        B.build_meshes_ibz(ctx, wl.kmesh, wl.qmesh, union, wl.degen_tol_eV, wl.omega_min_eV)
+        rates = B.compute_transition_rates(ctx, 0.0, 0.0, wl.sigma_eV, wl.cutoff_sigmas,
+                                           B.PRECISIONS[args.precision], instances=insts)
+        solve = B.solve_coupled_bte(ctx, "dragged", wl.tol)
+        return rates, solve, [B.transport_coefficients(ctx, i) for i in range(len(insts))]
+
+    flush.zero_()
+    batched_run()                     # warm-up (allocations)
+    flush.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rates, solve, coeffs = batched_run()
+    torch.cuda.synchronize()
+    bat_s = time.perf_counter() - t0
+    worst = {}
+    for c, ref in zip(coeffs, seq_coeffs):
+        for key, v in ref.items():
+            nrm = float(np.linalg.norm(v))
+            e = float(np.linalg.norm(c[key] - v) / nrm) if nrm > 0 else 0.0
+            worst[key] = max(worst.get(key, 0.0), e)
+    return {"instances": len(insts), "union_window_eV": list(union), "T_K_range": [100.0, 500.0],
+            "s_sequential_fp64": seq_s, "s_batched": bat_s, "speedup": seq_s / bat_s,
+            "batched_precision": args.precision, "batched_rates_ms": rates["ms"], "batched_solve_ms": solve["ms"],
+            "union_tuples": rates["n_tuples"], "converged": solve["converged"],
+            "max_coeff_rel_err_vs_sequential_fp64": worst}
 
 
 def reference_arm(args):
@@ -431,6 +485,8 @@ def main():
                               "rates_ms": rv.rates["ms"], "stage_b_ms": rv.rates["ms_stage_b"],
                               "coeff_rel_err": err}
 
+    batched = batched_block(B, ctx, wl, args, flush, torch, np) if args.instances > 0 else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nt, dt, row = oracle_sample(wl)
@@ -457,7 +513,7 @@ def main():
                           "self_sweep_kernel": r0.solve["ms_self_kernel"], "n_runs": r0.solve["n_runs"],
                           "drag_terms": r0.solve["ms_drag"], "ph_sweeps": r0.solve["ms_ph_sweep"],
                           "n_sweeps": r0.solve["n_sweeps"], "outer_iters": r0.solve["outer_iters"]},
-            "variants": variants,
+            "variants": variants, "batched": batched,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(out))

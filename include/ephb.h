@@ -157,11 +157,12 @@ typedef struct { double sigma_eV, cutoff_sigmas; } ephb_delta;
 /* Precision of the R_ph contraction of the vertex (the largest part of the work):
  *   EPHB_FP64         FP64 on the CUDA cores.
  *   EPHB_FP64_SLICED  tensor cores (tcgen05, BF16 in, FP32 accumulate) on exact fixed-point
- *                     slices: operands split into 7 slices of 8 bits, the 28 slice products
- *                     of the leading diagonals, the two largest diagonals each kept in an
- *                     accumulator where the FP32 sums are exact; FP64-grade results.
- *   EPHB_SPLIT_BF16   the same with 3 slices and one FP32 accumulator (mixed precision,
- *                     ~1e-7 relative).
+ *                     slices: operands rounded to 2^-55 of their scale and split into 7 slices
+ *                     of 8 bits, the 28 slice products of the leading diagonals, the four
+ *                     largest diagonals each kept in an accumulator where the FP32 sums are
+ *                     exact; FP64-grade results.  Needs 2 nRgp <= 256 (EPHB_EINVAL otherwise).
+ *   EPHB_SPLIT_BF16   3 slices, the leading diagonal exact, the rest in one FP32 accumulator
+ *                     (mixed precision, ~1e-7 relative).  Needs 2 nRgp <= 1024.
  *   EPHB_SPLIT_TF32   not available (EPHB_EINVAL).
  * The stage-A contraction, the rotations, |g|^2, occupations and delta stay FP64 in every
  * mode. */

@@ -621,6 +621,11 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     return fail(ctx, EPHB_EINVAL, "precision must be EPHB_FP64, EPHB_FP64_SLICED or EPHB_SPLIT_BF16");
   if (!(delta->sigma_eV > 0) || !(delta->cutoff_sigmas > 0))
     return fail(ctx, EPHB_EINVAL, "sigma and cutoff must be positive");
+  // exact FP32 sums of the accumulated slice diagonals bound the contraction length
+  if (precision == EPHB_FP64_SLICED && tc_kp(ctx->M) > 256)
+    return fail(ctx, EPHB_EINVAL, "EPHB_FP64_SLICED needs 2 nRgp <= 256");
+  if (precision == EPHB_SPLIT_BF16 && tc_kp(ctx->M) > 1024)
+    return fail(ctx, EPHB_EINVAL, "EPHB_SPLIT_BF16 needs 2 nRgp <= 1024");
   bool windowed = false;
   for (int i = 0; i < ninst; ++i) {
     if (!(inst[i].T_K > 0)) return fail(ctx, EPHB_EINVAL, "T must be positive");

@@ -10,15 +10,15 @@
 //   x = sum_i s_i,  s_i = n_i 2^(-7-8(i-1)),  |n_i| <= 128,
 // so each slice is an exact BF16 number.  A product of two slices is an integer multiple of
 // 2^(-14-8(i+l-2)) below 2^(-8(i+l-2)) in size, and a K = 256 sum of such products (or the
-// two products of the second diagonal) fits the 24-bit FP32 significand: the tensor core
-// computes those diagonals exactly.  FP64-grade mode: 7 slices (inputs to 2^-55 of the
-// column scale, which the Fourier sums need because they cancel: a result 1e-3 of its
-// column scale keeps ~1e-14 relative accuracy), the 28 products with i + l <= 8,
-// accumulators (i+l = 2), (i+l = 3), (i+l = 4) -- each summed exactly -- and (i+l >= 5),
-// which rounds at 2^-24 of a sum that is itself below 2^-22 of the column scale.  (With the
-// third diagonal merged into the tail, its rounding, ~2^-40 of the column scale, showed up as
-// 1e-8 relative errors on the smallest rates.)  Mixed mode: 3 slices, the 6 products with
-// i + l <= 4, accumulators (i+l = 2) (exact) and (i+l >= 3).
+// two products of the second diagonal, or the four of the fourth as long as K <= 256) fits
+// the 24-bit FP32 significand: the tensor core computes those diagonals exactly.  FP64-grade
+// mode: 7 slices (inputs to 2^-55 of the column scale, which the Fourier sums need because
+// they cancel: a result 1e-3 of its column scale keeps ~1e-13 relative accuracy), the 28
+// products with i + l <= 8, accumulators (i+l = 2), (3), (4), (5) -- each summed exactly --
+// and (i+l >= 6), which rounds at 2^-24 of a sum below 2^-30 of the column scale.  (With
+// the fourth diagonal in the tail, its rounding, ~2^-42 of the column scale, reached 1.2e-10
+// relative on the smallest rates; with the third there too, 1e-8.)  Mixed mode: 3 slices, the
+// 6 products with i + l <= 4, accumulators (i+l = 2) (exact) and (i+l >= 3).
 //
 // The GEMM runs on 5th-generation tensor cores: operands in shared memory in the
 // no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix), accumulators in
@@ -378,7 +378,7 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
   if (e != cudaSuccess || nitems == 0) return e;
   TcParams P;
   P.ns = ns;
-  P.nacc = ns == 7 ? 4 : 2;
+  P.nacc = ns == 7 ? 5 : 2;
   P.Kp = Kp;
   P.Nmax = Nmax;
   P.nc_max = ncm;
@@ -391,9 +391,9 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
     if (e != cudaSuccess) return e;
   }
   if (ns == 7) {
-    e = cudaFuncSetAttribute(k_vertex_gemm<7, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    e = cudaFuncSetAttribute(k_vertex_gemm<7, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    EPHB_LAUNCH((k_vertex_gemm<7, 4>), unsigned(nitems), kTcThreads, smem, st, M, D, P, item_ptr, phis, bs, bscale,
+    EPHB_LAUNCH((k_vertex_gemm<7, 5>), unsigned(nitems), kTcThreads, smem, st, M, D, P, item_ptr, phis, bs, bscale,
                 Cbuf, err);
   } else {
     e = cudaFuncSetAttribute(k_vertex_gemm<3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));

@@ -275,6 +275,17 @@ def workload_cscl4(n: int = 24, T_K: float = 300.0) -> Workload:
                     window=(mu - 0.3, mu + 0.3), tol=1e-10)
 
 
+def instance_grid(n: int, mu0_eV: float = 0.0, half_window_eV: float = 0.25, seed: int = SEED_BASE + 4):
+    """n (T_K, mu_eV, window_lo_eV, window_hi_eV) instances: T on a linspace of [100, 500] K and
+    mu on a linspace of mu0 +- 0.2 eV, the two paired by a seeded shuffle; each instance's
+    window is mu +- half_window, so the active k sets differ from instance to instance."""
+    rng = np.random.default_rng(seed)
+    T = np.linspace(100.0, 500.0, n)
+    mu = mu0_eV + np.linspace(-0.2, 0.2, n)
+    rng.shuffle(mu)
+    return [(float(t), float(m), float(m - half_window_eV), float(m + half_window_eV)) for t, m in zip(T, mu)]
+
+
 def model_nbytes(m: WannierModel) -> int:
     return int(sum(x.nbytes for x in (m.lattice, m.mass_amu, m.tau_cart, m.Re, m.H_R, m.Rd, m.D_R,
                                        m.Rge, m.Rgp, m.g_R, m.sym_rot, m.sym_cart)))
