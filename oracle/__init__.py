@@ -12,3 +12,4 @@ plain double precision.  Library primitives used as steps: numpy.linalg.eigh
 (Hermitian eigen-decomposition) and matrix products.
 """
 from .ephb_oracle import *  # noqa: F401,F403
+from . import mlp_oracle  # noqa: F401

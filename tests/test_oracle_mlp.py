@@ -1,0 +1,79 @@
+"""Pins of the FP64 warm-start network reference (CPU): its gradient against central finite
+differences of its loss, invariants of a network with zero hidden weights, gradient descent on
+a network without hidden layers reaching the least-squares solution of numpy.linalg.lstsq,
+and the targets / features on cases with known values."""
+import numpy as np
+
+from oracle import mlp_oracle as MO
+from oracle import KB_EVK
+
+
+def _case(seed=3, n=20, width=8, depth=3):
+    rng = np.random.default_rng(seed)
+    params = MO.init_params(MO.NFEAT, width, depth, MO.NOUT, seed)
+    params = [(W, rng.normal(0, 0.3, size=b.shape)) for W, b in params]   # nonzero biases too
+    x = rng.normal(size=(n, MO.NFEAT))
+    t = rng.normal(size=(n, MO.NOUT))
+    return params, x, t
+
+
+def test_gradient_matches_central_differences():
+    params, x, t = _case()
+    g = MO.flatten([(dW, db) for dW, db in MO.gradients(params, x, t)])
+    v = MO.flatten(params)
+    h = 1e-6
+    fd = np.empty_like(v)
+    for i in range(len(v)):
+        vp, vm = v.copy(), v.copy()
+        vp[i] += h
+        vm[i] -= h
+        fd[i] = (MO.loss(MO.unflatten(vp, params), x, t) - MO.loss(MO.unflatten(vm, params), x, t)) / (2 * h)
+    assert np.max(np.abs(g - fd)) <= 1e-7 * max(1.0, np.max(np.abs(fd)))
+
+
+def test_zero_hidden_weights():
+    """With every hidden weight zero the hidden states are constant, so the first layers get
+    no weight gradient and the output bias gradient is the mean residual."""
+    params, x, t = _case()
+    params = [(np.zeros_like(W) if l < len(params) - 1 else W, b) for l, (W, b) in enumerate(params)]
+    grads = MO.gradients(params, x, t)
+    y, _ = MO.forward(params, x)
+    for l in range(len(params) - 2):
+        assert np.all(grads[l][0] == 0.0)
+    np.testing.assert_allclose(grads[-1][1], (y - t).mean(axis=0), rtol=1e-12, atol=1e-14)
+
+
+def test_linear_network_descends_to_least_squares():
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=(64, MO.NFEAT))
+    t = rng.normal(size=(64, MO.NOUT))
+    params = MO.init_params(MO.NFEAT, 1, 0, MO.NOUT, 7)     # no hidden layer: y = W x + b
+    for _ in range(4000):
+        (dW, db), = MO.gradients(params, x, t)
+        (W, b), = params
+        params = [(W - 0.5 * dW, b - 0.5 * db)]
+    A = np.hstack([x, np.ones((len(x), 1))])
+    sol = np.linalg.lstsq(A, t, rcond=None)[0]
+    (W, b), = params
+    np.testing.assert_allclose(W, sol[:-1].T, atol=1e-8)
+    np.testing.assert_allclose(b, sol[-1], atol=1e-8)
+
+
+def test_targets_and_features():
+    rng = np.random.default_rng(2)
+    I0 = rng.normal(size=(10, 3))
+    J0 = rng.normal(size=(10, 3))
+    I0[3] = 0.0
+    np.testing.assert_array_equal(MO.scale_targets(I0, J0, I0, J0), 0.0)
+    a = MO.scale_targets(2.0 * I0, 0.5 * J0, I0, J0)
+    assert a[3, 0] == 0.0
+    np.testing.assert_allclose(np.delete(a[:, 0], 3), 1.0, rtol=1e-15)
+    np.testing.assert_allclose(a[:, 1], -0.5, rtol=1e-15)
+    Iw, Jw = MO.warm_start(I0, J0, a)
+    np.testing.assert_allclose(np.delete(Iw, 3, axis=0), 2.0 * np.delete(I0, 3, axis=0), rtol=1e-15)
+    f = MO.state_features(np.array([0.1, -0.2]), np.array([[3.0, 4.0, 0.0], [0.0, 0.0, 1.0]]),
+                          np.array([1e13, 0.0]), 300.0, 0.05)
+    np.testing.assert_allclose(f[:, 0], np.array([0.05, -0.25]) / (KB_EVK * 300.0), rtol=1e-15)
+    np.testing.assert_allclose(f[:, 1], [0.0, 0.0], atol=1e-15)
+    np.testing.assert_allclose(f[:, 2], [1.0, 0.2], rtol=1e-15)
+    np.testing.assert_allclose(f[:, 3:], [[1.0, 0.5, 1.0 / 3.0], [1.0, 0.5, -2.0 / 3.0]], rtol=1e-15)
