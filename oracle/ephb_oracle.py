@@ -369,7 +369,9 @@ class BTEResult:
     residuals: list
     lambdas: list
     converged: bool
-    rta_coeffs: dict
+    rta_coeffs: dict            # coefficients of the starting responses (the RTA unless init)
+    I0: np.ndarray = None
+    J0: np.ndarray = None
 
 
 class _System:
@@ -468,11 +470,14 @@ def coefficients_from_responses(sys_: _System, I, J, F, G) -> dict:
 
 
 def solve_coupled_bte(P: Prepared, R: Rates, level: str = "dragged", ko: bool = True, tol: float = None,
-                      max_outer: int = 500, max_inner: int = 5000, inner_tol: float = None) -> BTEResult:
+                      max_outer: int = 500, max_inner: int = 5000, inner_tol: float = None,
+                      init=None) -> BTEResult:
     """RTA (iteration 0), then the unified single-iterator scheme: each phonon iteration
     updates F, G from the current electron responses (drag terms), brings the electron
     equations for both fields to self-consistency against those phonons, and applies
-    the Kelvin-Onsager correction.  level: 'rta' | 'dragless' | 'partial' | 'dragged'."""
+    the Kelvin-Onsager correction.  level: 'rta' | 'dragless' | 'partial' | 'dragged'.
+    init: optional starting electron responses (I, J) in place of the RTA ones (I0, J0); the
+    phonons start from the RTA either way."""
     wl = P.wl
     tol = wl.tol if tol is None else tol
     inner_tol = 0.1 * tol if inner_tol is None else inner_tol
@@ -527,6 +532,8 @@ def solve_coupled_bte(P: Prepared, R: Rates, level: str = "dragged", ko: bool = 
         return ds * sy.fold(Bv) * inv_nnW[..., None]
 
     I, J, F, G = I0.copy(), J0.copy(), F0.copy(), G0.copy()
+    if init is not None:
+        I, J = np.array(init[0], dtype=np.float64), np.array(init[1], dtype=np.float64)
     rta = coefficients_from_responses(sy, I, J, F, G)
     res_hist, lam_hist, inner_hist = [], [], []
     ekeys = ("sigma", "sigmaS", "alpha_el", "kappa0_el")
@@ -580,4 +587,4 @@ def solve_coupled_bte(P: Prepared, R: Rates, level: str = "dragged", ko: bool = 
     coeffs = coefficients_from_responses(sy, I, J, F, G)
     return BTEResult(coeffs=coeffs, I=I, J=J, F=F, G=G, W_e=W_e, W_ph=W_ph, states=sy.states,
                      outer_iters=outer, inner_iters=inner_hist, residuals=res_hist, lambdas=lam_hist,
-                     converged=converged, rta_coeffs=rta)
+                     converged=converged, rta_coeffs=rta, I0=I0, J0=J0)

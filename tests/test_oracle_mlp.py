@@ -77,3 +77,20 @@ def test_targets_and_features():
     np.testing.assert_allclose(f[:, 1], [0.0, 0.0], atol=1e-15)
     np.testing.assert_allclose(f[:, 2], [1.0, 0.2], rtol=1e-15)
     np.testing.assert_allclose(f[:, 3:], [[1.0, 0.5, 1.0 / 3.0], [1.0, 0.5, -2.0 / 3.0]], rtol=1e-15)
+
+
+def test_starting_responses_leave_the_answer_unchanged():
+    """The coupled iteration is a contraction: any start reaches the same coefficients, and a
+    start at the converged responses stops after its first outer check."""
+    from oracle import prepare, transition_rates, solve_coupled_bte, TENSORS
+    from paper_2109_08547_gb300 import synthetic as SY
+    wl = SY.workload_sc1(n=6)
+    P = prepare(wl)
+    R = transition_rates(P)
+    ref = solve_coupled_bte(P, R, level="dragged")
+    odd = solve_coupled_bte(P, R, level="dragged", init=(1.3 * ref.I0, 0.8 * ref.J0))
+    for key in TENSORS:
+        a, b = odd.coeffs[key], ref.coeffs[key]
+        assert np.linalg.norm(a - b) <= 1e-8 * np.linalg.norm(b), key
+    again = solve_coupled_bte(P, R, level="dragged", init=(ref.I, ref.J))
+    assert again.converged and again.outer_iters <= 2 < ref.outer_iters
