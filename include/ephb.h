@@ -207,6 +207,7 @@ typedef struct {
   double inner_tol;            /* electron loop tolerance (<= 0: 0.1*tol)                  */
   int max_outer, max_inner;
   int ko_correction;           /* 1: apply the Kelvin-Onsager step (dragged levels)        */
+  int warm_start;              /* 1: start from ephb_set_warm_start's responses where set   */
 } ephb_solve_opts;
 
 typedef struct {
@@ -233,6 +234,50 @@ typedef struct {
 ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *opts, ephb_solve_info *out);
 /* The last solve of one instance. */
 ephb_status ephb_instance_solve_info(ephb_ctx *ctx, int inst, ephb_solve_info *out);
+
+/* ----------------------------------------------------------------------------------
+ * Learned warm start (an extension: the paper starts the iteration from the RTA).
+ * A network proposes, per electron state, scale factors a = (a_I, a_J) of the RTA responses;
+ * the next solve of the instance (opts.warm_start = 1) then starts from I = I0 (1 + a_I),
+ * J = J0 (1 + a_J) instead of I0, J0, with the phonons from the RTA as before.  The iteration
+ * and its convergence test are unchanged, so the answer is the same to the tolerance; if the
+ * warm-started solve does not converge, the instance is solved again from the RTA start.
+ * States: the n_states = ephb_num_states() electron states (irreducible-window k x band) of
+ * the meshes; inactive states get zero inputs and are ignored.
+ *   features: EPHB_NFEAT floats per state: (eps-mu)/kT clipped to +-40, log10(W_RTA) - 13,
+ *             |v|/max|v|, T/300 K, mu/0.1 eV, eps/0.3 eV (device, FP32, [n_states][6]).
+ *   targets:  after a solve, (I.I0/I0.I0 - 1, J.J0/J0.J0 - 1) per state (0 where I0 = 0).
+ * All pointers are device pointers owned by the caller.
+ * --------------------------------------------------------------------------------*/
+#define EPHB_NFEAT 6
+int64_t ephb_num_states(const ephb_ctx *ctx);
+ephb_status ephb_state_features(ephb_ctx *ctx, int inst, float *feat_dev, int64_t n_states);
+ephb_status ephb_state_targets(ephb_ctx *ctx, int inst, float *targ_dev, int64_t n_states);
+/* scale_dev = NULL clears the instance's warm start. */
+ephb_status ephb_set_warm_start(ephb_ctx *ctx, int inst, const float *scale_dev, int64_t n_states);
+
+/* The network: n_in inputs, depth hidden tanh layers of the given width, n_out linear outputs;
+ * FP32 master parameters (layer by layer: W [fan_out][fan_in] row-major, then b), Glorot
+ * uniform weights from a counter-based generator (splitmix64 of seed and index), zero biases.
+ * Products take BF16-rounded operands with FP32 accumulation (ephb_mlp_set_bf16(net, 0): FP32
+ * operands).  Loss 1/(2n) sum |y - t|^2.  Training: full-batch Adam (0.9, 0.999, 1e-8). */
+typedef struct ephb_mlp ephb_mlp;
+ephb_status ephb_mlp_create(ephb_mlp **out, int device, void *cuda_stream, int n_in, int width, int depth, int n_out,
+                            uint64_t seed);
+void ephb_mlp_destroy(ephb_mlp *net);
+const char *ephb_mlp_last_error(const ephb_mlp *net);
+int64_t ephb_mlp_num_params(const ephb_mlp *net);
+ephb_status ephb_mlp_set_bf16(ephb_mlp *net, int on);
+ephb_status ephb_mlp_get_params(ephb_mlp *net, float *host, int64_t n);
+ephb_status ephb_mlp_set_params(ephb_mlp *net, const float *host, int64_t n);   /* also resets Adam */
+/* y_dev [n][n_out] = net(x_dev [n][n_in]) */
+ephb_status ephb_mlp_forward(ephb_mlp *net, const float *x_dev, int64_t n, float *y_dev);
+/* loss (host, optional) and its gradient (device [num_params], optional) on (x, t) */
+ephb_status ephb_mlp_loss_grad(ephb_mlp *net, const float *x_dev, const float *t_dev, int64_t n, float *loss_host,
+                               float *grad_dev);
+/* one Adam step of learning rate lr on the full batch (x, t); loss before the step */
+ephb_status ephb_mlp_train_step(ephb_mlp *net, const float *x_dev, const float *t_dev, int64_t n, float lr,
+                                float *loss_host);
 
 /* ----------------------------------------------------------------------------------
  * Transport coefficients of the current responses (Eqs. sigma/sigmaS,

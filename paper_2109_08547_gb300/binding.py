@@ -33,7 +33,11 @@ EXPORTED = ["ephb_create", "ephb_destroy", "ephb_last_error", "ephb_set_wannier_
             "ephb_compute_transition_rates", "ephb_solve_coupled_bte", "ephb_transport_coefficients",
             "ephb_get_device_array", "ephb_copy_array_to_host", "ephb_kernel_launches",
             "ephb_transport_coefficients_noalloc", "ephb_select_instance", "ephb_num_instances",
-            "ephb_instance_solve_info"]
+            "ephb_instance_solve_info", "ephb_num_states", "ephb_state_features", "ephb_state_targets",
+            "ephb_set_warm_start", "ephb_mlp_create", "ephb_mlp_destroy", "ephb_mlp_last_error",
+            "ephb_mlp_num_params", "ephb_mlp_set_bf16", "ephb_mlp_get_params", "ephb_mlp_set_params",
+            "ephb_mlp_forward", "ephb_mlp_loss_grad", "ephb_mlp_train_step"]
+NFEAT = 6
 
 _pd = C.POINTER(C.c_double)
 _pi = C.POINTER(C.c_int32)
@@ -76,7 +80,7 @@ class RatesInfoC(C.Structure):
 
 class SolveOptsC(C.Structure):
     _fields_ = [("level", C.c_int), ("tol", C.c_double), ("inner_tol", C.c_double), ("max_outer", C.c_int),
-                ("max_inner", C.c_int), ("ko_correction", C.c_int)]
+                ("max_inner", C.c_int), ("ko_correction", C.c_int), ("warm_start", C.c_int)]
 
 
 class SolveInfoC(C.Structure):
@@ -133,10 +137,32 @@ def load(path: str = None):
     lib.ephb_select_instance.argtypes = [C.c_void_p, C.c_int]
     lib.ephb_num_instances.argtypes = [C.c_void_p]
     lib.ephb_instance_solve_info.argtypes = [C.c_void_p, C.c_int, C.POINTER(SolveInfoC)]
+    lib.ephb_num_states.argtypes = [C.c_void_p]
+    lib.ephb_state_features.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]
+    lib.ephb_state_targets.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]
+    lib.ephb_set_warm_start.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]
+    lib.ephb_mlp_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                                    C.c_uint64]
+    lib.ephb_mlp_destroy.argtypes = [C.c_void_p]
+    lib.ephb_mlp_last_error.argtypes = [C.c_void_p]
+    lib.ephb_mlp_num_params.argtypes = [C.c_void_p]
+    lib.ephb_mlp_set_bf16.argtypes = [C.c_void_p, C.c_int]
+    lib.ephb_mlp_get_params.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+    lib.ephb_mlp_set_params.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+    lib.ephb_mlp_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]
+    lib.ephb_mlp_loss_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_float),
+                                       C.c_void_p]
+    lib.ephb_mlp_train_step.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float,
+                                        C.POINTER(C.c_float)]
     for name in EXPORTED:
-        if name not in ("ephb_destroy", "ephb_last_error", "ephb_kernel_launches"):
+        if name not in ("ephb_destroy", "ephb_last_error", "ephb_kernel_launches", "ephb_num_states",
+                        "ephb_mlp_destroy", "ephb_mlp_last_error", "ephb_mlp_num_params"):
             getattr(lib, name).restype = C.c_int
     lib.ephb_kernel_launches.restype = C.c_int64
+    lib.ephb_num_states.restype = C.c_int64
+    lib.ephb_mlp_destroy.restype = None
+    lib.ephb_mlp_last_error.restype = C.c_char_p
+    lib.ephb_mlp_num_params.restype = C.c_int64
     _lib = lib
     return lib
 
@@ -277,9 +303,9 @@ def instance_solve_info(ctx: Context, inst: int) -> dict:
 
 
 def solve_coupled_bte(ctx: Context, level="dragged", tol=1e-10, inner_tol=0.0, max_outer=500, max_inner=5000,
-                      ko_correction=True, allow_noconv=False) -> dict:
+                      ko_correction=True, allow_noconv=False, warm_start=False) -> dict:
     o = SolveOptsC(LEVELS[level] if isinstance(level, str) else int(level), float(tol), float(inner_tol),
-                   int(max_outer), int(max_inner), 1 if ko_correction else 0)
+                   int(max_outer), int(max_inner), 1 if ko_correction else 0, 1 if warm_start else 0)
     info = SolveInfoC()
     st = _check(ctx, _lib.ephb_solve_coupled_bte(ctx.handle, C.byref(o), C.byref(info)),
                 allow=(ENOCONV,) if allow_noconv else ())
@@ -355,3 +381,87 @@ def run_path(ctx: Context, wl, level="dragged", ko_correction=True, tol=None, ma
     solve = solve_coupled_bte(ctx, level, wl.tol if tol is None else tol, 0.0, max_outer, max_inner, ko_correction,
                               allow_noconv)
     return PathResult(mesh, rates, solve, transport_coefficients(ctx))
+
+
+# ----------------------------------------------------------------------------------------
+# learned warm start
+# ----------------------------------------------------------------------------------------
+
+def num_states(ctx: Context) -> int:
+    return int(_lib.ephb_num_states(ctx.handle))
+
+
+def state_features(ctx: Context, inst: int, out_ptr: int) -> None:
+    """Network inputs of instance inst into device memory out_ptr ([num_states][NFEAT] FP32)."""
+    _check(ctx, _lib.ephb_state_features(ctx.handle, int(inst), C.c_void_p(out_ptr), num_states(ctx)))
+
+
+def state_targets(ctx: Context, inst: int, out_ptr: int) -> None:
+    """Training targets of a solved instance into device memory out_ptr ([num_states][2] FP32)."""
+    _check(ctx, _lib.ephb_state_targets(ctx.handle, int(inst), C.c_void_p(out_ptr), num_states(ctx)))
+
+
+def set_warm_start(ctx: Context, inst: int, scale_ptr) -> None:
+    """Scale factors [num_states][2] (device FP32) for the next solve of instance inst; None clears."""
+    _check(ctx, _lib.ephb_set_warm_start(ctx.handle, int(inst), C.c_void_p(scale_ptr) if scale_ptr else None,
+                                         num_states(ctx)))
+
+
+class MLP:
+    """The warm-start network (device parameters; see include/ephb.h)."""
+
+    def __init__(self, n_in=NFEAT, width=128, depth=3, n_out=2, seed=0, device=0, stream=None):
+        load()
+        h = C.c_void_p()
+        st = _lib.ephb_mlp_create(C.byref(h), int(device), C.c_void_p(stream) if stream else None, int(n_in),
+                                  int(width), int(depth), int(n_out), C.c_uint64(seed))
+        if st != OK:
+            raise EphbError(st, "ephb_mlp_create failed")
+        self.handle = h
+        self.n_in, self.width, self.depth, self.n_out = n_in, width, depth, n_out
+
+    def _check(self, st):
+        if st != OK:
+            raise EphbError(st, _lib.ephb_mlp_last_error(self.handle).decode())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.ephb_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_params(self) -> int:
+        return int(_lib.ephb_mlp_num_params(self.handle))
+
+    def set_bf16(self, on: bool) -> None:
+        self._check(_lib.ephb_mlp_set_bf16(self.handle, 1 if on else 0))
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.num_params, dtype=np.float32)
+        self._check(_lib.ephb_mlp_get_params(self.handle, out.ctypes.data_as(C.c_void_p), out.size))
+        return out
+
+    def set_params(self, v) -> None:
+        v = np.ascontiguousarray(v, dtype=np.float32)
+        self._check(_lib.ephb_mlp_set_params(self.handle, v.ctypes.data_as(C.c_void_p), v.size))
+
+    def forward(self, x_ptr: int, n: int, y_ptr: int) -> None:
+        self._check(_lib.ephb_mlp_forward(self.handle, C.c_void_p(x_ptr), int(n), C.c_void_p(y_ptr)))
+
+    def loss_grad(self, x_ptr: int, t_ptr: int, n: int, grad_ptr: int = 0) -> float:
+        lo = C.c_float()
+        self._check(_lib.ephb_mlp_loss_grad(self.handle, C.c_void_p(x_ptr), C.c_void_p(t_ptr), int(n), C.byref(lo),
+                                            C.c_void_p(grad_ptr) if grad_ptr else None))
+        return float(lo.value)
+
+    def train_step(self, x_ptr: int, t_ptr: int, n: int, lr: float) -> float:
+        lo = C.c_float()
+        self._check(_lib.ephb_mlp_train_step(self.handle, C.c_void_p(x_ptr), C.c_void_p(t_ptr), int(n), float(lr),
+                                             C.byref(lo)))
+        return float(lo.value)

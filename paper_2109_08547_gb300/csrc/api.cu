@@ -101,7 +101,9 @@ struct InstState {
   DBuf<int2> kinfo;
   DBuf<int> sctl;               // device-driven sweep loop: stop flag, sweeps done, converged
   DBuf<unsigned long long> nzero;
-  bool bte_ready = false;
+  DBuf<float> warm;             // warm-start scale factors [nst][2]
+  DBuf<unsigned> vmaxb;
+  bool bte_ready = false, has_warm = false, solved = false;
   ephb_solve_info last{};       // the instance's last solve
 
   void release_all() {
@@ -113,8 +115,9 @@ struct InstState {
       b->release();
     nseg_row.release(); eseg_row.release(); rseg_row.release(); run_flag.release(); eseg_ptr.release();
     eseg_begin.release(); rseg_ptr.release(); rseg_begin.release(); run_ptr.release(); run_idx.release();
-    run_col.release(); kcrd.release(); kinfo.release(); sctl.release(); nzero.release();
-    bte_ready = false;
+    run_col.release(); kcrd.release(); kinfo.release(); sctl.release(); nzero.release(); warm.release();
+    vmaxb.release();
+    bte_ready = has_warm = solved = false;
   }
 };
 
@@ -543,8 +546,8 @@ void set_instances(ephb_ctx *ctx, int n) {
   }
   ctx->slots.resize(n);
   ctx->ninst = n;
-  ctx->bte_ready = false;
-  for (int i = 1; i < n; ++i) ctx->slots[i].bte_ready = false;
+  ctx->bte_ready = ctx->has_warm = ctx->solved = false;
+  for (int i = 1; i < n; ++i) ctx->slots[i].bte_ready = ctx->slots[i].has_warm = ctx->slots[i].solved = false;
 }
 
 // The lists just computed (vertex-only) become the union lists; each instance then takes the
@@ -921,13 +924,20 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
   CK(cudaEventCreate(&ev0));
   CK(cudaEventCreate(&ev1));
   CK(cudaEventRecord(ev0, st));
-  ephb_status s = bte_setup(ctx);
-  if (s != EPHB_OK) return s;
+  ephb_status s = EPHB_OK;
+  if (!ctx->bte_ready) {   // RTA terms, runs and segments depend on the rate lists only
+    s = bte_setup(ctx);
+    if (s != EPHB_OK) return s;
+  }
   const ModelDev &M = ctx->M;
   const int64_t nst = ctx->n_ibzw * M.nb, nph = ctx->qm.size() * M.nbr;
   const double tol = o->tol, inner_tol = o->inner_tol > 0 ? o->inner_tol : 0.1 * o->tol;
-  CK(cudaMemcpyAsync(ctx->I.p, ctx->I0.p, nst * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(ctx->J.p, ctx->J0.p, nst * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (o->warm_start && ctx->has_warm) {   // learned start I = I0 (1 + a_I), J = J0 (1 + a_J)
+    CK(launch_apply_warm(nst, ctx->I0.p, ctx->J0.p, ctx->warm.p, ctx->I.p, ctx->J.p, st));
+  } else {
+    CK(cudaMemcpyAsync(ctx->I.p, ctx->I0.p, nst * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ctx->J.p, ctx->J0.p, nst * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
   CK(cudaMemcpyAsync(ctx->F.p, ctx->F0.p, nph * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemsetAsync(ctx->G.p, 0, nph * 3 * sizeof(double), st));
   CK(cudaMemsetAsync(ctx->prev_out.p, 0, kResLen * sizeof(double), st));
@@ -1061,6 +1071,7 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
     out->ms_drag = td.ms;
     out->n_runs = ctx->nruns;
   }
+  ctx->solved = true;
   if (!converged) return fail(ctx, EPHB_ENOCONV, "iteration limit reached before the tolerance");
   return EPHB_OK;
 }
@@ -1082,7 +1093,18 @@ ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb
   for (int i = 0; i < ctx->ninst; ++i) {
     select_instance(ctx, i);
     ephb_solve_info one{};
-    const ephb_status r = solve_one(ctx, o, &one);
+    ephb_status r = solve_one(ctx, o, &one);
+    if (r == EPHB_ENOCONV && o->warm_start && ctx->has_warm) {
+      // the learned start did not converge: the plain RTA start decides
+      ephb_solve_opts plain = *o;
+      plain.warm_start = 0;
+      ephb_solve_info again{};
+      r = solve_one(ctx, &plain, &again);
+      again.n_sweeps += one.n_sweeps;
+      again.inner_iters_total += one.inner_iters_total;
+      again.ms += one.ms;
+      one = again;
+    }
     if (r != EPHB_OK && r != EPHB_ENOCONV) return r;
     noconv = noconv || r == EPHB_ENOCONV;
     ctx->last = one;
@@ -1131,6 +1153,56 @@ ephb_status ephb_transport_coefficients(ephb_ctx *ctx, int inst, ephb_coeffs *ou
 }
 
 // ---------------------------------------------------------------------------------------
+int64_t ephb_num_states(const ephb_ctx *ctx) { return ctx ? ctx->n_ibzw * ctx->M.nb : 0; }
+
+ephb_status ephb_state_features(ephb_ctx *ctx, int inst, float *feat_dev, int64_t n_states) {
+  if (!ctx || !feat_dev) return EPHB_EINVAL;
+  if (ctx->stage < 3) return fail(ctx, EPHB_ESTATE, "compute_transition_rates must come first");
+  if (inst < 0 || inst >= ctx->ninst) return fail(ctx, EPHB_EINVAL, "inst out of range");
+  if (n_states != ctx->n_ibzw * ctx->M.nb) return fail(ctx, EPHB_EINVAL, "n_states must be ephb_num_states()");
+  CK(cudaSetDevice(ctx->device));
+  select_instance(ctx, inst);
+  if (!ctx->bte_ready) {
+    ephb_status s = bte_setup(ctx);
+    if (s != EPHB_OK) return s;
+  }
+  CK(ctx->vmaxb.ensure(1));
+  CK(launch_state_features(bte_view(ctx), ctx->W_e.p, ctx->vmaxb.p, feat_dev, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return EPHB_OK;
+}
+
+ephb_status ephb_state_targets(ephb_ctx *ctx, int inst, float *targ_dev, int64_t n_states) {
+  if (!ctx || !targ_dev) return EPHB_EINVAL;
+  if (inst < 0 || inst >= ctx->ninst) return fail(ctx, EPHB_EINVAL, "inst out of range");
+  select_instance(ctx, inst);
+  if (ctx->stage < 4 || !ctx->solved) return fail(ctx, EPHB_ESTATE, "the instance has no solution yet");
+  if (n_states != ctx->n_ibzw * ctx->M.nb) return fail(ctx, EPHB_EINVAL, "n_states must be ephb_num_states()");
+  CK(cudaSetDevice(ctx->device));
+  CK(launch_state_targets(n_states, ctx->I.p, ctx->J.p, ctx->I0.p, ctx->J0.p, targ_dev, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return EPHB_OK;
+}
+
+ephb_status ephb_set_warm_start(ephb_ctx *ctx, int inst, const float *scale_dev, int64_t n_states) {
+  if (!ctx) return EPHB_EINVAL;
+  if (ctx->stage < 3) return fail(ctx, EPHB_ESTATE, "compute_transition_rates must come first");
+  if (inst < 0 || inst >= ctx->ninst) return fail(ctx, EPHB_EINVAL, "inst out of range");
+  if (n_states != ctx->n_ibzw * ctx->M.nb) return fail(ctx, EPHB_EINVAL, "n_states must be ephb_num_states()");
+  CK(cudaSetDevice(ctx->device));
+  select_instance(ctx, inst);
+  if (!scale_dev) {
+    ctx->has_warm = false;
+    return EPHB_OK;
+  }
+  CK(ctx->warm.ensure(size_t(n_states) * 2));
+  CK(cudaMemcpyAsync(ctx->warm.p, scale_dev, size_t(n_states) * 2 * sizeof(float), cudaMemcpyDeviceToDevice,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->has_warm = true;
+  return EPHB_OK;
+}
+
 ephb_status ephb_instance_solve_info(ephb_ctx *ctx, int inst, ephb_solve_info *out) {
   if (!ctx || !out) return EPHB_EINVAL;
   if (inst < 0 || inst >= ctx->ninst) return fail(ctx, EPHB_EINVAL, "inst out of range");

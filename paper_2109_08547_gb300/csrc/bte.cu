@@ -782,6 +782,87 @@ cudaError_t launch_coeff_final(const ModelDev &M, const BteDev &B, const double 
   return cudaGetLastError();
 }
 
+namespace {
+
+// largest electron speed over the active states (non-negative floats order as their bits)
+__global__ void k_speed_max(BteDev B, unsigned *vmax_bits) {
+  const int64_t st = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (st >= B.nst || !(B.st_wt[st] > 0.0)) return;
+  const double *v = B.st_vel + st * 3;
+  const float sp = float(sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+  atomicMax(vmax_bits, __float_as_uint(sp));
+}
+
+// inputs of the warm-start network per state: (eps-mu)/kT (clipped to +-40), log10(W)-13,
+// |v|/max|v|, T/300 K, mu/0.1 eV, eps/0.3 eV; zeros for inactive states
+__global__ void k_state_features(BteDev B, const double *__restrict__ W_e, const unsigned *vmax_bits, float *feat) {
+  const int64_t st = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (st >= B.nst) return;
+  float *f = feat + st * kNFeat;
+  if (!(B.st_wt[st] > 0.0)) {
+    for (int c = 0; c < kNFeat; ++c) f[c] = 0.f;
+    return;
+  }
+  const double e = B.st_eps[st], kT = kKbEVK * B.T, W = W_e[st];
+  const double *v = B.st_vel + st * 3;
+  const float vmax = __uint_as_float(*vmax_bits);
+  const double sp = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  f[0] = float(fmin(fmax((e - B.mu) / kT, -40.0), 40.0));
+  f[1] = W > 0.0 ? float(log10(W) - 13.0) : 0.f;
+  f[2] = vmax > 0.f ? float(sp / double(vmax)) : 0.f;
+  f[3] = float(B.T / 300.0);
+  f[4] = float(B.mu / 0.1);
+  f[5] = float(e / 0.3);
+}
+
+// training targets: converged responses as multiples of the RTA ones along the RTA direction
+__global__ void k_state_targets(int64_t nst, const double *I, const double *J, const double *I0, const double *J0,
+                                float *t) {
+  const int64_t st = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (st >= nst) return;
+  for (int f = 0; f < 2; ++f) {
+    const double *X = (f == 0 ? I : J) + st * 3, *X0 = (f == 0 ? I0 : J0) + st * 3;
+    const double d = X0[0] * X0[0] + X0[1] * X0[1] + X0[2] * X0[2];
+    const double p = X[0] * X0[0] + X[1] * X0[1] + X[2] * X0[2];
+    t[st * 2 + f] = d > 0.0 ? float(p / d - 1.0) : 0.f;
+  }
+}
+
+// starting responses I = I0 (1 + a_I), J = J0 (1 + a_J)
+__global__ void k_apply_warm(int64_t nst, const double *I0, const double *J0, const float *a, double *I, double *J) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= nst * 3) return;
+  const int64_t st = t / 3;
+  I[t] = I0[t] * (1.0 + double(a[st * 2]));
+  J[t] = J0[t] * (1.0 + double(a[st * 2 + 1]));
+}
+
+}  // namespace
+
+cudaError_t launch_state_features(const BteDev &B, const double *W_e, unsigned *vmax_bits, float *feat,
+                                  cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(vmax_bits, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess || B.nst == 0) return e;
+  const unsigned g = unsigned((B.nst + 255) / 256);
+  EPHB_LAUNCH(k_speed_max, g, 256, 0, st, B, vmax_bits);
+  EPHB_LAUNCH(k_state_features, g, 256, 0, st, B, W_e, vmax_bits, feat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_state_targets(int64_t nst, const double *I, const double *J, const double *I0, const double *J0,
+                                 float *t, cudaStream_t st) {
+  if (nst == 0) return cudaSuccess;
+  EPHB_LAUNCH(k_state_targets, unsigned((nst + 255) / 256), 256, 0, st, nst, I, J, I0, J0, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_warm(int64_t nst, const double *I0, const double *J0, const float *a, double *I, double *J,
+                              cudaStream_t st) {
+  if (nst == 0) return cudaSuccess;
+  EPHB_LAUNCH(k_apply_warm, unsigned((nst * 3 + 255) / 256), 256, 0, st, nst, I0, J0, a, I, J);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ko(const ModelDev &M, const MeshDev &D, const BteDev &B, double *I, const double *J,
                       double *kpart, double *res, cudaStream_t st) {
   (void)D;

@@ -202,6 +202,15 @@ int coeff_partials();
 cudaError_t launch_e_partial(const BteDev &B, const double *I, const double *J, double *epart, cudaStream_t st);
 cudaError_t launch_ph_partial(const MeshDev &D, const BteDev &B, const double *F, const double *G, double *ppart,
                               cudaStream_t st);
+// Warm start: network inputs per state (kNFeat floats), training targets (2 floats: the
+// converged I, J as multiples of I0, J0 along them), and starting responses from scale factors.
+constexpr int kNFeat = 6;
+cudaError_t launch_state_features(const BteDev &B, const double *W_e, unsigned *vmax_bits, float *feat,
+                                  cudaStream_t st);
+cudaError_t launch_state_targets(int64_t nst, const double *I, const double *J, const double *I0, const double *J0,
+                                 float *t, cudaStream_t st);
+cudaError_t launch_apply_warm(int64_t nst, const double *I0, const double *J0, const float *a, double *I, double *J,
+                              cudaStream_t st);
 cudaError_t launch_coeff_final(const ModelDev &M, const BteDev &B, const double *epart, const double *ppart,
                                double *res, double *prev, cudaStream_t st, int *ctl = nullptr, int max_sweeps = 0,
                                double tol = 0.0);

@@ -1,0 +1,167 @@
+"""The learned warm start on the GPU: the network's forward pass and gradients against the FP64
+oracle (FP32 operands tightly, BF16 operands loosely), deterministic training, the per-state
+inputs and targets against the oracle, the warm-started iteration against the oracle started
+from the same responses, and the gain of a trained network on held-out (T, mu) instances."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import mlp_oracle as MO
+from paper_2109_08547_gb300 import binding as B
+from paper_2109_08547_gb300 import synthetic as SY
+from _parity import COEFF_RTOL, rel_fro
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TENSORS = ("sigma", "sigmaS", "alpha_el", "kappa0_el", "alpha_ph", "kappa_ph")
+
+
+def _net_case(width=32, depth=3, n=300, seed=11):
+    rng = np.random.default_rng(seed)
+    params = MO.init_params(MO.NFEAT, width, depth, MO.NOUT, seed)
+    params = [(W, rng.normal(0, 0.2, size=b.shape)) for W, b in params]
+    # parameters and data exactly representable in FP32, so both sides see the same numbers
+    params = MO.unflatten(MO.flatten(params).astype(np.float32).astype(np.float64), params)
+    x = rng.normal(size=(n, MO.NFEAT)).astype(np.float32).astype(np.float64)
+    t = rng.normal(size=(n, MO.NOUT)).astype(np.float32).astype(np.float64)
+    return params, x, t
+
+
+def _gpu_net(params, width, depth, bf16):
+    net = B.MLP(MO.NFEAT, width, depth, MO.NOUT, seed=1)
+    net.set_params(MO.flatten(params).astype(np.float32))
+    net.set_bf16(bf16)
+    return net
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+
+
+def test_forward_matches_oracle():
+    params, x, _ = _net_case()
+    net = _gpu_net(params, 32, 3, bf16=False)
+    X = _dev(x)
+    Y = torch.empty((len(x), MO.NOUT), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    net.forward(X.data_ptr(), len(x), Y.data_ptr())
+    y_ref, _ = MO.forward(params, x)
+    np.testing.assert_allclose(Y.cpu().numpy(), y_ref, rtol=1e-5, atol=1e-5 * np.abs(y_ref).max())
+
+
+@pytest.mark.parametrize("bf16,rtol", [(False, 2e-5), (True, 5e-2)])
+def test_gradients_match_oracle(bf16, rtol):
+    params, x, t = _net_case()
+    net = _gpu_net(params, 32, 3, bf16)
+    X, T = _dev(x), _dev(t)
+    G = torch.empty(net.num_params, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    loss = net.loss_grad(X.data_ptr(), T.data_ptr(), len(x), G.data_ptr())
+    ref = MO.gradients(params, x, t)
+    got = MO.unflatten(G.cpu().numpy().astype(np.float64), params)
+    assert abs(loss - MO.loss(params, x, t)) <= rtol * MO.loss(params, x, t)
+    for l, ((gW, gb), (rW, rb)) in enumerate(zip(got, ref)):
+        assert rel_fro(gW, rW) <= rtol, f"layer {l} W: {rel_fro(gW, rW):.3e}"
+        assert rel_fro(gb, rb) <= rtol, f"layer {l} b: {rel_fro(gb, rb):.3e}"
+
+
+def test_training_learns_and_is_deterministic():
+    rng = np.random.default_rng(4)
+    x = rng.normal(size=(2048, MO.NFEAT))
+    t = np.stack([0.5 * np.sin(x[:, 0]) + 0.2 * x[:, 1], 0.3 * np.tanh(x[:, 2] * x[:, 3])], axis=1)
+    X, T = _dev(x), _dev(t)
+    runs = []
+    for _ in range(2):
+        net = B.MLP(MO.NFEAT, 128, 3, MO.NOUT, seed=5)
+        torch.cuda.synchronize()
+        runs.append([net.train_step(X.data_ptr(), T.data_ptr(), len(x), 3e-3) for _ in range(300)])
+    assert runs[0] == runs[1]
+    assert runs[0][-1] < 0.1 * runs[0][0]
+
+
+@pytest.fixture(scope="module")
+def solved_cscl4():
+    wl = SY.workload_cscl4(n=6)
+    ctx = B.Context(0)
+    B.set_wannier_model(ctx, wl.model)
+    B.run_path(ctx, wl, level="dragged")
+    P = O.prepare(wl)
+    R = O.transition_rates(P)
+    ref = O.solve_coupled_bte(P, R, level="dragged")
+    yield wl, ctx, P, R, ref
+    ctx.close()
+
+
+def test_features_and_targets_match_oracle(solved_cscl4):
+    wl, ctx, P, R, ref = solved_cscl4
+    n = B.num_states(ctx)
+    F = torch.empty((n, B.NFEAT), dtype=torch.float32, device="cuda")
+    Tg = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    B.state_features(ctx, 0, F.data_ptr())
+    B.state_targets(ctx, 0, Tg.data_ptr())
+    f, tg = F.cpu().numpy(), Tg.cpu().numpy()
+    ibzw = B.get_array(ctx, "ibzw_list")
+    nb = wl.model.nb
+    row = {(int(ibzw[i // nb]), i % nb): i for i in range(n)}
+    idx = np.array([row[(int(k), int(b))] for k, b in ref.states])
+    ks, bs = ref.states[:, 0], ref.states[:, 1]
+    f_ref = MO.state_features(P.eps[ks, bs], P.vel[ks, bs], ref.W_e, wl.T_K, wl.mu_eV)
+    np.testing.assert_allclose(f[idx], f_ref, rtol=2e-6, atol=2e-6)
+    t_ref = MO.scale_targets(ref.I, ref.J, ref.I0, ref.J0)
+    np.testing.assert_allclose(tg[idx], t_ref, rtol=1e-5, atol=1e-6)
+    others = np.setdiff1d(np.arange(n), idx)
+    assert np.all(f[others] == 0.0) and np.all(tg[others] == 0.0)
+
+
+def test_warm_started_iteration_matches_oracle(solved_cscl4):
+    """Start from I = 1.3 I0, J = 0.8 J0 on both sides: same converged coefficients as the
+    oracle started there, and as the RTA start."""
+    wl, ctx, P, R, ref = solved_cscl4
+    n = B.num_states(ctx)
+    a = torch.tensor(np.tile([0.3, -0.2], (n, 1)), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    B.set_warm_start(ctx, 0, a.data_ptr())
+    info = B.solve_coupled_bte(ctx, "dragged", wl.tol, warm_start=True)
+    got = B.transport_coefficients(ctx)
+    wref = O.solve_coupled_bte(P, R, level="dragged", init=(1.3 * ref.I0, 0.8 * ref.J0))
+    assert info["converged"] == 1 and wref.converged
+    for key in TENSORS:
+        assert rel_fro(got[key], wref.coeffs[key]) <= COEFF_RTOL, key
+        assert rel_fro(got[key], ref.coeffs[key]) <= COEFF_RTOL, key
+    B.set_warm_start(ctx, 0, None)
+
+
+def test_trained_network_reduces_sweeps_on_held_out_instances():
+    """Train on 24 (T, mu) instances of the 8^3 CsCl-type model, then solve 6 held-out ones from
+    the RTA start and from the network's start: fewer sweeps, the same coefficients."""
+    from paper_2109_08547_gb300 import warmstart as WS
+    wl = SY.workload_cscl4(n=8)
+    grid = SY.instance_grid(30, wl.mu_eV, seed=SY.SEED_BASE + 5)
+    train, held = grid[:24], grid[24:]
+    union = (min(i[2] for i in grid), max(i[3] for i in grid))
+    dev = torch.device("cuda", 0)
+    with B.Context(0) as ctx:
+        B.set_wannier_model(ctx, wl.model)
+        B.build_meshes_ibz(ctx, wl.kmesh, wl.qmesh, union, wl.degen_tol_eV, wl.omega_min_eV)
+        B.compute_transition_rates(ctx, 0.0, 0.0, wl.sigma_eV, wl.cutoff_sigmas, instances=train)
+        B.solve_coupled_bte(ctx, "dragged", wl.tol)
+        X, T = WS.instance_data(ctx, range(len(train)), dev)
+        net = B.MLP(seed=9)
+        losses = WS.train(net, X, T, steps=400, lr=2e-3)
+        assert losses[-1] < 0.5 * losses[0]
+        B.compute_transition_rates(ctx, 0.0, 0.0, wl.sigma_eV, wl.cutoff_sigmas, instances=held)
+        plain = B.solve_coupled_bte(ctx, "dragged", wl.tol)
+        base = [B.transport_coefficients(ctx, i) for i in range(len(held))]
+        for i in range(len(held)):
+            WS.apply(ctx, net, i, dev)
+        warm = B.solve_coupled_bte(ctx, "dragged", wl.tol, warm_start=True)
+        assert plain["converged"] == 1 and warm["converged"] == 1
+        assert warm["n_sweeps"] < plain["n_sweeps"], (warm["n_sweeps"], plain["n_sweeps"])
+        for i in range(len(held)):
+            c = B.transport_coefficients(ctx, i)
+            for key in TENSORS:
+                assert rel_fro(c[key], base[i][key]) <= 1e-6, (i, key)
