@@ -237,16 +237,18 @@ ephb_status ephb_instance_solve_info(ephb_ctx *ctx, int inst, ephb_solve_info *o
 
 /* ----------------------------------------------------------------------------------
  * Learned warm start (an extension: the paper starts the iteration from the RTA).
- * A network proposes, per electron state, scale factors a = (a_I, a_J) of the RTA responses;
- * the next solve of the instance (opts.warm_start = 1) then starts from I = I0 (1 + a_I),
- * J = J0 (1 + a_J) instead of I0, J0, with the phonons from the RTA as before.  The iteration
+ * A network proposes, per electron state, coordinates a = (a_I, a_J) of the responses along
+ * the RTA direction J0 = v/W; the next solve of the instance (opts.warm_start = 1) then starts
+ * from I = I0 + a_I k_B J0, J = J0 (1 + a_J) instead of I0, J0 (a = 0 is the RTA start), with
+ * the phonons from the RTA as before.  The iteration
  * and its convergence test are unchanged, so the answer is the same to the tolerance; if the
  * warm-started solve does not converge, the instance is solved again from the RTA start.
  * States: the n_states = ephb_num_states() electron states (irreducible-window k x band) of
  * the meshes; inactive states get zero inputs and are ignored.
  *   features: EPHB_NFEAT floats per state: (eps-mu)/kT clipped to +-40, log10(W_RTA) - 13,
  *             |v|/max|v|, T/300 K, mu/0.1 eV, eps/0.3 eV (device, FP32, [n_states][6]).
- *   targets:  after a solve, (I.I0/I0.I0 - 1, J.J0/J0.J0 - 1) per state (0 where I0 = 0).
+ *   targets:  after a solve, a_I = (I.J0)/(J0.J0)/k_B - (eps-mu)/(k_B T) and
+ *             a_J = (J.J0)/(J0.J0) - 1 per state (0 where J0 = 0 or |v| < 1e-6 max|v|).
  * All pointers are device pointers owned by the caller.
  * --------------------------------------------------------------------------------*/
 #define EPHB_NFEAT 6

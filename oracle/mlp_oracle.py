@@ -100,18 +100,23 @@ def state_features(eps, vel, W_e, T, mu):
                      np.full_like(eps, mu / 0.1), eps / 0.3], axis=1)
 
 
-def scale_targets(I, J, I0, J0):
-    """t = ((I.I0)/(I0.I0) - 1, (J.J0)/(J0.J0) - 1) per state (0 where the RTA vector is 0):
-    the converged responses as multiples of the RTA ones along the RTA direction."""
-    def one(X, X0):
-        d = np.sum(X0 * X0, axis=1)
-        return np.where(d > 0, np.sum(X * X0, axis=1) / np.where(d > 0, d, 1.0) - 1.0, 0.0)
-    return np.stack([one(I, I0), one(J, J0)], axis=1)
+def scale_targets(I, J, J0, x, speed, speed_cut=1e-6):
+    """Per state, along the RTA direction J0 = v/W:
+         a_I = (I.J0)/(J0.J0)/k_B - x,   a_J = (J.J0)/(J0.J0) - 1,
+    with x = (eps-mu)/(k_B T), so the RTA solution (I0 = (eps-mu)/T J0) has a = 0.  Zero where
+    J0 = 0 or the speed is below speed_cut of the largest (velocities that vanish by symmetry
+    carry no direction)."""
+    d = np.sum(J0 * J0, axis=1)
+    ok = (d > 0) & (speed > speed_cut * (speed.max() if speed.size else 0.0))
+    dd = np.where(ok, d, 1.0)
+    aI = np.where(ok, np.sum(I * J0, axis=1) / dd / KB_EVK - x, 0.0)
+    aJ = np.where(ok, np.sum(J * J0, axis=1) / dd - 1.0, 0.0)
+    return np.stack([aI, aJ], axis=1)
 
 
 def warm_start(I0, J0, a):
-    """Starting responses I = I0 (1 + a_I), J = J0 (1 + a_J)."""
-    return I0 * (1.0 + a[:, 0:1]), J0 * (1.0 + a[:, 1:2])
+    """Starting responses I = I0 + a_I k_B J0, J = J0 (1 + a_J)."""
+    return I0 + (a[:, 0:1] * KB_EVK) * J0, J0 * (1.0 + a[:, 1:2])
 
 
 __all__ = ["NFEAT", "NOUT", "init_params", "forward", "loss", "gradients", "flatten", "unflatten",

@@ -932,7 +932,7 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
   const ModelDev &M = ctx->M;
   const int64_t nst = ctx->n_ibzw * M.nb, nph = ctx->qm.size() * M.nbr;
   const double tol = o->tol, inner_tol = o->inner_tol > 0 ? o->inner_tol : 0.1 * o->tol;
-  if (o->warm_start && ctx->has_warm) {   // learned start I = I0 (1 + a_I), J = J0 (1 + a_J)
+  if (o->warm_start && ctx->has_warm) {   // learned start I = I0 + a_I k_B J0, J = J0 (1 + a_J)
     CK(launch_apply_warm(nst, ctx->I0.p, ctx->J0.p, ctx->warm.p, ctx->I.p, ctx->J.p, st));
   } else {
     CK(cudaMemcpyAsync(ctx->I.p, ctx->I0.p, nst * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1179,7 +1179,8 @@ ephb_status ephb_state_targets(ephb_ctx *ctx, int inst, float *targ_dev, int64_t
   if (ctx->stage < 4 || !ctx->solved) return fail(ctx, EPHB_ESTATE, "the instance has no solution yet");
   if (n_states != ctx->n_ibzw * ctx->M.nb) return fail(ctx, EPHB_EINVAL, "n_states must be ephb_num_states()");
   CK(cudaSetDevice(ctx->device));
-  CK(launch_state_targets(n_states, ctx->I.p, ctx->J.p, ctx->I0.p, ctx->J0.p, targ_dev, ctx->stream));
+  CK(ctx->vmaxb.ensure(1));
+  CK(launch_state_targets(bte_view(ctx), ctx->I.p, ctx->J.p, ctx->J0.p, ctx->vmaxb.p, targ_dev, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return EPHB_OK;
 }

@@ -815,25 +815,34 @@ __global__ void k_state_features(BteDev B, const double *__restrict__ W_e, const
   f[5] = float(e / 0.3);
 }
 
-// training targets: converged responses as multiples of the RTA ones along the RTA direction
-__global__ void k_state_targets(int64_t nst, const double *I, const double *J, const double *I0, const double *J0,
-                                float *t) {
+// training targets along the RTA direction J0 = v/W: a_I = (I.J0)/(J0.J0)/k_B - (eps-mu)/(k_B T),
+// a_J = (J.J0)/(J0.J0) - 1; zero for inactive states, J0 = 0, or speeds below 1e-6 of the largest
+__global__ void k_state_targets(BteDev B, const double *I, const double *J, const double *J0,
+                                const unsigned *vmax_bits, float *t) {
   const int64_t st = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (st >= nst) return;
-  for (int f = 0; f < 2; ++f) {
-    const double *X = (f == 0 ? I : J) + st * 3, *X0 = (f == 0 ? I0 : J0) + st * 3;
-    const double d = X0[0] * X0[0] + X0[1] * X0[1] + X0[2] * X0[2];
-    const double p = X[0] * X0[0] + X[1] * X0[1] + X[2] * X0[2];
-    t[st * 2 + f] = d > 0.0 ? float(p / d - 1.0) : 0.f;
+  if (st >= B.nst) return;
+  const double *v = B.st_vel + st * 3, *b = J0 + st * 3;
+  const double sp = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  const double d = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+  const bool ok = B.st_wt[st] > 0.0 && d > 0.0 && sp > 1e-6 * double(__uint_as_float(*vmax_bits));
+  if (!ok) {
+    t[st * 2] = 0.f;
+    t[st * 2 + 1] = 0.f;
+    return;
   }
+  const double *x = I + st * 3, *y = J + st * 3;
+  const double pi = x[0] * b[0] + x[1] * b[1] + x[2] * b[2];
+  const double pj = y[0] * b[0] + y[1] * b[1] + y[2] * b[2];
+  t[st * 2] = float(pi / d / kKbEVK - (B.st_eps[st] - B.mu) / (kKbEVK * B.T));
+  t[st * 2 + 1] = float(pj / d - 1.0);
 }
 
-// starting responses I = I0 (1 + a_I), J = J0 (1 + a_J)
+// starting responses I = I0 + a_I k_B J0, J = J0 (1 + a_J)
 __global__ void k_apply_warm(int64_t nst, const double *I0, const double *J0, const float *a, double *I, double *J) {
   const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (t >= nst * 3) return;
   const int64_t st = t / 3;
-  I[t] = I0[t] * (1.0 + double(a[st * 2]));
+  I[t] = I0[t] + double(a[st * 2]) * kKbEVK * J0[t];
   J[t] = J0[t] * (1.0 + double(a[st * 2 + 1]));
 }
 
@@ -849,10 +858,13 @@ cudaError_t launch_state_features(const BteDev &B, const double *W_e, unsigned *
   return cudaGetLastError();
 }
 
-cudaError_t launch_state_targets(int64_t nst, const double *I, const double *J, const double *I0, const double *J0,
-                                 float *t, cudaStream_t st) {
-  if (nst == 0) return cudaSuccess;
-  EPHB_LAUNCH(k_state_targets, unsigned((nst + 255) / 256), 256, 0, st, nst, I, J, I0, J0, t);
+cudaError_t launch_state_targets(const BteDev &B, const double *I, const double *J, const double *J0,
+                                 unsigned *vmax_bits, float *t, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(vmax_bits, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess || B.nst == 0) return e;
+  const unsigned g = unsigned((B.nst + 255) / 256);
+  EPHB_LAUNCH(k_speed_max, g, 256, 0, st, B, vmax_bits);
+  EPHB_LAUNCH(k_state_targets, g, 256, 0, st, B, I, J, J0, vmax_bits, t);
   return cudaGetLastError();
 }
 

@@ -203,12 +203,12 @@ cudaError_t launch_e_partial(const BteDev &B, const double *I, const double *J, 
 cudaError_t launch_ph_partial(const MeshDev &D, const BteDev &B, const double *F, const double *G, double *ppart,
                               cudaStream_t st);
 // Warm start: network inputs per state (kNFeat floats), training targets (2 floats: the
-// converged I, J as multiples of I0, J0 along them), and starting responses from scale factors.
+// converged I, J along the RTA direction J0 = v/W), and starting responses from them.
 constexpr int kNFeat = 6;
 cudaError_t launch_state_features(const BteDev &B, const double *W_e, unsigned *vmax_bits, float *feat,
                                   cudaStream_t st);
-cudaError_t launch_state_targets(int64_t nst, const double *I, const double *J, const double *I0, const double *J0,
-                                 float *t, cudaStream_t st);
+cudaError_t launch_state_targets(const BteDev &B, const double *I, const double *J, const double *J0,
+                                 unsigned *vmax_bits, float *t, cudaStream_t st);
 cudaError_t launch_apply_warm(int64_t nst, const double *I0, const double *J0, const float *a, double *I, double *J,
                               cudaStream_t st);
 cudaError_t launch_coeff_final(const ModelDev &M, const BteDev &B, const double *epart, const double *ppart,

@@ -111,15 +111,16 @@ def test_features_and_targets_match_oracle(solved_cscl4):
     ks, bs = ref.states[:, 0], ref.states[:, 1]
     f_ref = MO.state_features(P.eps[ks, bs], P.vel[ks, bs], ref.W_e, wl.T_K, wl.mu_eV)
     np.testing.assert_allclose(f[idx], f_ref, rtol=2e-6, atol=2e-6)
-    t_ref = MO.scale_targets(ref.I, ref.J, ref.I0, ref.J0)
-    np.testing.assert_allclose(tg[idx], t_ref, rtol=1e-5, atol=1e-6)
+    x = (P.eps[ks, bs] - wl.mu_eV) / (O.KB_EVK * wl.T_K)
+    t_ref = MO.scale_targets(ref.I, ref.J, ref.J0, x, np.linalg.norm(P.vel[ks, bs], axis=1))
+    np.testing.assert_allclose(tg[idx], t_ref, rtol=1e-5, atol=1e-5)
     others = np.setdiff1d(np.arange(n), idx)
     assert np.all(f[others] == 0.0) and np.all(tg[others] == 0.0)
 
 
 def test_warm_started_iteration_matches_oracle(solved_cscl4):
-    """Start from I = 1.3 I0, J = 0.8 J0 on both sides: same converged coefficients as the
-    oracle started there, and as the RTA start."""
+    """Start from I = I0 + 0.3 k_B J0, J = 0.8 J0 on both sides: same converged coefficients as
+    the oracle started there, and as the RTA start."""
     wl, ctx, P, R, ref = solved_cscl4
     n = B.num_states(ctx)
     a = torch.tensor(np.tile([0.3, -0.2], (n, 1)), dtype=torch.float32, device="cuda")
@@ -127,7 +128,8 @@ def test_warm_started_iteration_matches_oracle(solved_cscl4):
     B.set_warm_start(ctx, 0, a.data_ptr())
     info = B.solve_coupled_bte(ctx, "dragged", wl.tol, warm_start=True)
     got = B.transport_coefficients(ctx)
-    wref = O.solve_coupled_bte(P, R, level="dragged", init=(1.3 * ref.I0, 0.8 * ref.J0))
+    wref = O.solve_coupled_bte(P, R, level="dragged", init=MO.warm_start(ref.I0, ref.J0, np.tile([0.3, -0.2],
+                                                                                               (len(ref.I0), 1))))
     assert info["converged"] == 1 and wref.converged
     for key in TENSORS:
         assert rel_fro(got[key], wref.coeffs[key]) <= COEFF_RTOL, key

@@ -61,16 +61,23 @@ def test_linear_network_descends_to_least_squares():
 
 def test_targets_and_features():
     rng = np.random.default_rng(2)
-    I0 = rng.normal(size=(10, 3))
-    J0 = rng.normal(size=(10, 3))
-    I0[3] = 0.0
-    np.testing.assert_array_equal(MO.scale_targets(I0, J0, I0, J0), 0.0)
-    a = MO.scale_targets(2.0 * I0, 0.5 * J0, I0, J0)
-    assert a[3, 0] == 0.0
-    np.testing.assert_allclose(np.delete(a[:, 0], 3), 1.0, rtol=1e-15)
-    np.testing.assert_allclose(a[:, 1], -0.5, rtol=1e-15)
+    T, mu = 300.0, 0.05
+    eps = rng.uniform(-0.2, 0.2, size=10)
+    x = (eps - mu) / (KB_EVK * T)
+    v = rng.normal(size=(10, 3))
+    v[3] = 0.0
+    W = rng.uniform(1e12, 1e13, size=10)
+    J0 = v / W[:, None]
+    I0 = ((eps - mu) / T)[:, None] * J0
+    speed = np.linalg.norm(v, axis=1)
+    np.testing.assert_allclose(MO.scale_targets(I0, J0, J0, x, speed), 0.0, atol=1e-9)
+    a = MO.scale_targets(I0 + 0.5 * KB_EVK * J0, 2.0 * J0, J0, x, speed)
+    assert np.all(a[3] == 0.0)
+    np.testing.assert_allclose(np.delete(a[:, 0], 3), 0.5, rtol=1e-9)
+    np.testing.assert_allclose(np.delete(a[:, 1], 3), 1.0, rtol=1e-12)
     Iw, Jw = MO.warm_start(I0, J0, a)
-    np.testing.assert_allclose(np.delete(Iw, 3, axis=0), 2.0 * np.delete(I0, 3, axis=0), rtol=1e-15)
+    np.testing.assert_allclose(Iw, I0 + 0.5 * KB_EVK * J0, rtol=1e-9, atol=1e-30)
+    np.testing.assert_allclose(Jw, 2.0 * J0, rtol=1e-12)
     f = MO.state_features(np.array([0.1, -0.2]), np.array([[3.0, 4.0, 0.0], [0.0, 0.0, 1.0]]),
                           np.array([1e13, 0.0]), 300.0, 0.05)
     np.testing.assert_allclose(f[:, 0], np.array([0.05, -0.25]) / (KB_EVK * 300.0), rtol=1e-15)
