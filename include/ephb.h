@@ -182,6 +182,8 @@ typedef struct {
   double tensor_flops;         /* tensor-core modes: flops issued as tcgen05.mma           */
   double rot_flops;            /* algorithmic flops of the band and branch rotations       */
   double ms_gemm;              /* tensor-core modes: device time of the tcgen05 GEMM kernel  */
+  int tc_cols;                 /* tensor-core modes: column-chunk width used               */
+  int autotuned;               /* 1 if this call chose tc_cols by timing the candidates    */
 } ephb_rates_info;
 
 ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst, int ninst,
@@ -326,6 +328,14 @@ typedef enum {
   EPHB_ARR_STATE_WEIGHT = 21,  /* [n_ibz_window*nb] f64 1/|stabiliser| (0 when inactive)   */
   EPHB_ARR_COUNT = 22
 } ephb_array;
+
+/* Tuning.  EPHB_TUNE_TC_COLS: column-chunk width of the tensor-core contraction (the tile is
+ * 128 (k,q) pairs x width columns).  0 (default): the first tensor-core rates call of a context
+ * times the candidate widths (48/64/96 FP64-grade, 64/128/256 mixed) on its first chunk and
+ * keeps the fastest for the context; setting 0 again re-tunes.  Otherwise the given width
+ * (a multiple of 16, at most 96 / 256) is used.  The results do not depend on the width. */
+#define EPHB_TUNE_TC_COLS 0
+ephb_status ephb_set_tuning(ephb_ctx *ctx, int key, int value);
 
 /* Make instance inst the one whose arrays the views and copies below return (and the one
  * whose solution a later solve leaves in place).  EPHB_EINVAL if inst is out of range. */

@@ -36,7 +36,7 @@ EXPORTED = ["ephb_create", "ephb_destroy", "ephb_last_error", "ephb_set_wannier_
             "ephb_instance_solve_info", "ephb_num_states", "ephb_state_features", "ephb_state_targets",
             "ephb_set_warm_start", "ephb_mlp_create", "ephb_mlp_destroy", "ephb_mlp_last_error",
             "ephb_mlp_num_params", "ephb_mlp_set_bf16", "ephb_mlp_get_params", "ephb_mlp_set_params",
-            "ephb_mlp_forward", "ephb_mlp_loss_grad", "ephb_mlp_train_step"]
+            "ephb_mlp_forward", "ephb_mlp_loss_grad", "ephb_mlp_train_step", "ephb_set_tuning"]
 NFEAT = 6
 
 _pd = C.POINTER(C.c_double)
@@ -75,7 +75,8 @@ class RatesInfoC(C.Structure):
     _fields_ = [("n_tuples", C.c_int64), ("n_entries", C.c_int64), ("n_ph_entries", C.c_int64),
                 ("n_pairs", C.c_int64), ("ms", C.c_double), ("ms_stage_a", C.c_double), ("ms_stage_b", C.c_double),
                 ("stage_a_flops", C.c_double), ("stage_b_flops", C.c_double), ("ms_epilogue", C.c_double),
-                ("tensor_flops", C.c_double), ("rot_flops", C.c_double), ("ms_gemm", C.c_double)]
+                ("tensor_flops", C.c_double), ("rot_flops", C.c_double), ("ms_gemm", C.c_double),
+                ("tc_cols", C.c_int), ("autotuned", C.c_int)]
 
 
 class SolveOptsC(C.Structure):
@@ -137,6 +138,7 @@ def load(path: str = None):
     lib.ephb_select_instance.argtypes = [C.c_void_p, C.c_int]
     lib.ephb_num_instances.argtypes = [C.c_void_p]
     lib.ephb_instance_solve_info.argtypes = [C.c_void_p, C.c_int, C.POINTER(SolveInfoC)]
+    lib.ephb_set_tuning.argtypes = [C.c_void_p, C.c_int, C.c_int]
     lib.ephb_num_states.argtypes = [C.c_void_p]
     lib.ephb_state_features.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]
     lib.ephb_state_targets.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]
@@ -284,6 +286,13 @@ def compute_transition_rates(ctx: Context, T_K, mu_eV, sigma_eV=0.01, cutoff_sig
     _check(ctx, _lib.ephb_compute_transition_rates(ctx.handle, arr, len(instances), C.byref(de), int(precision),
                                                    C.byref(info)))
     return {f: getattr(info, f) for f, _ in RatesInfoC._fields_}
+
+
+TUNE_TC_COLS = 0
+
+
+def set_tuning(ctx: Context, key: int, value: int) -> None:
+    _check(ctx, _lib.ephb_set_tuning(ctx.handle, int(key), int(value)))
 
 
 def select_instance(ctx: Context, inst: int) -> None:

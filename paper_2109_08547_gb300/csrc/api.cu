@@ -172,6 +172,10 @@ struct ephb_ctx : InstState {
   // instances: the one in use lives in the InstState base, the others in slots
   int ninst = 1, cur = 0;
   std::vector<InstState> slots = std::vector<InstState>(1);
+  // tuning: column-chunk width of the tensor-core contraction (FP64-grade, mixed); 0 = not
+  // tuned yet.  force_cols != 0 overrides the tuner.
+  int tune_cols[2] = {0, 0};
+  int force_cols = 0;
   double *host_res = nullptr;   // pinned: kResLen doubles, then the sweep-loop control (4 ints)
 };
 
@@ -420,6 +424,7 @@ ephb_status ephb_set_wannier_model(ephb_ctx *ctx, const ephb_model *m) {
   M.sym_cart = ctx->sym_cart.p;
   M.sym_inv = ctx->sym_inv.p;
   ctx->stage = 1;
+  ctx->tune_cols[0] = ctx->tune_cols[1] = 0;   // a new model shape is tuned again
   ctx->bte_ready = false;
   return EPHB_OK;
 }
@@ -707,6 +712,8 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
   CK(tg.init());
   const bool tensor = precision != EPHB_FP64;
   const int ns = precision == EPHB_FP64_SLICED ? 7 : 3;
+  const int ncm = tensor && ctx->force_cols ? std::min(ctx->force_cols, tc_nc_max(ns)) : 0;   // 0: tuned width
+  int autotuned = 0;
   std::vector<int64_t> hpp;
   int Nmax = 0;
   const int64_t kMaxChunkPairs = 1 << 20;   // bound of the contraction scratch (pairs x Nmax doubles)
@@ -751,10 +758,33 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
                               ctx->e_X.p, ctx->ph_st.p, ctx->ph_kpn.p, ctx->ph_Y.p, st));
       CK(tb.stop(st));
     } else {
-      CK(launch_vertex_tc(M, D, ns, i0, nkc, hpp[i0], ctx->Abuf.p, ctx->phis.p, ctx->bslices.p, ctx->bscale.p,
-                          ctx->nitem.p, ctx->item_ptr.p, ctx->scratch.p, ctx->scratch.n, ctx->scal.p + 6,
-                          ctx->Cbuf.p, ctx->tc_err.p, st, tg.a, tg.b));
-      tg.pending = true;
+      auto contract = [&](cudaEvent_t e0, cudaEvent_t e1, int width) {
+        return launch_vertex_tc(M, D, ns, i0, nkc, hpp[i0], ctx->Abuf.p, ctx->phis.p, ctx->bslices.p,
+                                ctx->bscale.p, ctx->nitem.p, ctx->item_ptr.p, ctx->scratch.p, ctx->scratch.n,
+                                ctx->scal.p + 6, ctx->Cbuf.p, ctx->tc_err.p, st, e0, e1, width);
+      };
+      int &tuned = ctx->tune_cols[ns == 7 ? 0 : 1];
+      if (ncm == 0 && tuned == 0) {
+        // autotune on this chunk: time the GEMM at every candidate column-chunk width and keep
+        // the fastest (the contraction is the same for every width, so the last run stands)
+        float best = 3.4e38f;
+        for (int width : tc_nc_candidates(ns)) {
+          EventTimer tt;
+          CK(tt.init());
+          CK(contract(tt.a, tt.b, width));
+          tt.pending = true;
+          CK(cudaStreamSynchronize(st));
+          CK(tt.collect());
+          if (tt.ms < best) {
+            best = float(tt.ms);
+            tuned = width;
+          }
+        }
+        autotuned = 1;
+      } else {
+        CK(contract(tg.a, tg.b, ncm ? ncm : tuned));
+        tg.pending = true;
+      }
       CK(tb.stop(st));
       CK(tc.start(st));
       CK(launch_vertex_epilogue(M, D, rp, hpp[i0], hpp[i0 + nkc], hpp[i0], ctx->Cbuf.p, Nmax, ctx->fk.p,
@@ -806,6 +836,8 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     out->tensor_flops = tensor_flops;
     out->rot_flops = double(cnt[4]);
     out->ms_gemm = tg.ms;
+    out->tc_cols = tensor ? (ncm ? ncm : ctx->tune_cols[ns == 7 ? 0 : 1]) : 0;
+    out->autotuned = autotuned;
   }
   ctx->stage = 3;
   return EPHB_OK;
@@ -1208,6 +1240,16 @@ ephb_status ephb_instance_solve_info(ephb_ctx *ctx, int inst, ephb_solve_info *o
   if (!ctx || !out) return EPHB_EINVAL;
   if (inst < 0 || inst >= ctx->ninst) return fail(ctx, EPHB_EINVAL, "inst out of range");
   *out = inst == ctx->cur ? ctx->last : ctx->slots[inst].last;
+  return EPHB_OK;
+}
+
+ephb_status ephb_set_tuning(ephb_ctx *ctx, int key, int value) {
+  if (!ctx) return EPHB_EINVAL;
+  if (key != EPHB_TUNE_TC_COLS) return fail(ctx, EPHB_EINVAL, "unknown tuning key");
+  if (value != 0 && (value < 16 || value % 16 != 0 || value > 256))
+    return fail(ctx, EPHB_EINVAL, "column-chunk width must be 0 or a multiple of 16 in [16, 256]");
+  ctx->force_cols = value;
+  if (value == 0) ctx->tune_cols[0] = ctx->tune_cols[1] = 0;   // tune again on the next call
   return EPHB_OK;
 }
 

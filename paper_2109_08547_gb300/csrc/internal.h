@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of the CUDA library.
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -112,8 +113,13 @@ cudaError_t launch_phase_slices(const ModelDev &M, const MeshDev &D, int ns, __n
 cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_t i0, int64_t nkc, int64_t pair_base,
                              const double2 *A, const __nv_bfloat16 *phis, __nv_bfloat16 *bs, double *bscale,
                              int *nitem, int64_t *item_ptr, int64_t *scratch, int64_t scratch_elems,
-                             int64_t *total_dev, double *Cbuf, int *err, cudaStream_t st,
-                             cudaEvent_t gemm0 = nullptr, cudaEvent_t gemm1 = nullptr);
+                             int64_t *total_dev, double *Cbuf, int *err, cudaStream_t st, cudaEvent_t gemm0,
+                             cudaEvent_t gemm1, int ncm);
+// Column-chunk width of the contraction (its result does not depend on it: every column is
+// summed in the same order whatever the chunking).
+int tc_nc_max(int ns);
+bool tc_nc_valid(int ns, int ncm);
+std::vector<int> tc_nc_candidates(int ns);
 
 // ---- bte.cu
 struct BteDev {

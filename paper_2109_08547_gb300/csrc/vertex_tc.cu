@@ -28,6 +28,8 @@
 // returns.
 #include <cuda_bf16.h>
 
+#include <vector>
+
 #include "internal.h"
 
 namespace ephb {
@@ -348,8 +350,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vertex_gemm(ModelDev M, MeshD
 
 int tc_kp(const ModelDev &M) { return round_up(2 * M.nRgp, kTcKc); }
 int tc_nmax(const ModelDev &M) { return round_up(2 * M.nb * M.nb * M.nbr, 16); }
+// Column-chunk widths a launch may use: every accumulator of a chunk must fit the 512 TMEM
+// columns (NACC x width) and two operand stages the shared memory.
 int tc_nc_max(int ns) { return ns == 7 ? 96 : 256; }
-size_t tc_smem_bytes(int ns) { return 2 * (size_t(ns) * kTcM * kTcKc * 2 + size_t(ns) * tc_nc_max(ns) * kTcKc * 2); }
+bool tc_nc_valid(int ns, int ncm) { return ncm >= 16 && ncm % 16 == 0 && ncm <= tc_nc_max(ns); }
+std::vector<int> tc_nc_candidates(int ns) {
+  return ns == 7 ? std::vector<int>{48, 64, 96} : std::vector<int>{64, 128, 256};
+}
+size_t tc_smem_bytes(int ns, int ncm) { return 2 * (size_t(ns) * kTcM * kTcKc * 2 + size_t(ns) * ncm * kTcKc * 2); }
 
 cudaError_t launch_phase_slices(const ModelDev &M, const MeshDev &D, int ns, __nv_bfloat16 *phis, cudaStream_t st) {
   const int Kp = tc_kp(M);
@@ -362,9 +370,10 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
                              const double2 *A, const __nv_bfloat16 *phis, __nv_bfloat16 *bs, double *bscale,
                              int *nitem, int64_t *item_ptr, int64_t *scratch, int64_t scratch_elems,
                              int64_t *total_dev, double *Cbuf, int *err, cudaStream_t st, cudaEvent_t gemm0,
-                             cudaEvent_t gemm1) {
+                             cudaEvent_t gemm1, int ncm) {
   if (nkc <= 0) return cudaSuccess;
-  const int Kp = tc_kp(M), Nmax = tc_nmax(M), ncm = tc_nc_max(ns);
+  if (!tc_nc_valid(ns, ncm)) return cudaErrorInvalidValue;
+  const int Kp = tc_kp(M), Nmax = tc_nmax(M);
   const int64_t nw = nkc * Nmax;
   EPHB_LAUNCH(k_b_slices, unsigned((nw * 32 + 255) / 256), 256, 0, st, M, D, i0, nkc, A, ns, Kp, Nmax, bs, bscale);
   const int nprod = ns * (ns + 1) / 2;
@@ -385,7 +394,7 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
   P.i0 = i0;
   P.nkc = nkc;
   P.pair_base = pair_base;
-  const size_t smem = tc_smem_bytes(ns);
+  const size_t smem = tc_smem_bytes(ns, ncm);
   if (gemm0) {
     e = cudaEventRecord(gemm0, st);
     if (e != cudaSuccess) return e;

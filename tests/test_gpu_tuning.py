@@ -1,0 +1,40 @@
+"""The tile autotuner of the tensor-core contraction: the first call of a context times the
+candidate column-chunk widths and keeps one; the rates do not depend on the width chosen
+(every column is summed in the same order), so they are bit-identical for every width."""
+import numpy as np
+import pytest
+
+from paper_2109_08547_gb300 import binding as B
+from paper_2109_08547_gb300 import synthetic as SY
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision,widths", [("fp64-sliced", (48, 64, 96)), ("split-bf16", (64, 128, 256))])
+def test_tile_width_is_tuned_and_result_invariant(precision, widths):
+    wl = SY.workload_cscl4(n=6)
+    outs = []
+    for width in (0,) + widths:
+        with B.Context(0) as ctx:
+            B.set_wannier_model(ctx, wl.model)
+            B.set_tuning(ctx, B.TUNE_TC_COLS, width)
+            B.build_meshes_ibz(ctx, wl.kmesh, wl.qmesh, wl.window, wl.degen_tol_eV, wl.omega_min_eV)
+            r = B.compute_transition_rates(ctx, wl.T_K, wl.mu_eV, wl.sigma_eV, wl.cutoff_sigmas,
+                                           B.PRECISIONS[precision])
+            if width == 0:
+                assert r["autotuned"] == 1 and r["tc_cols"] in widths
+                r2 = B.compute_transition_rates(ctx, wl.T_K, wl.mu_eV, wl.sigma_eV, wl.cutoff_sigmas,
+                                                B.PRECISIONS[precision])
+                assert r2["autotuned"] == 0 and r2["tc_cols"] == r["tc_cols"]
+            else:
+                assert r["autotuned"] == 0 and r["tc_cols"] == width
+            outs.append(B.get_array(ctx, "entry_x"))
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+
+
+def test_bad_width_is_rejected():
+    with B.Context(0) as ctx:
+        for bad in (8, 100, 512):
+            with pytest.raises(B.EphbError):
+                B.set_tuning(ctx, B.TUNE_TC_COLS, bad)
