@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--no-variants", action="store_true", help="skip the one-step timings of the other precisions")
     p.add_argument("--instances", type=int, default=8,
                    help="(T, mu, window) instances of the batched-vs-sequential comparison (0: skip it)")
+    p.add_argument("--warm", type=int, default=12,
+                   help="mesh size of the learned-warm-start report (40 training + 10 held-out instances; 0: skip)")
     p.add_argument("--fp64-peak", action="store_true",
                    help="measure FP64 and FP32 FMA throughput with a small probe kernel and exit")
     return p.parse_args()
@@ -276,6 +278,75 @@ def batched_block(B, ctx, wl, args, flush, torch, np):
             "max_coeff_rel_err_vs_sequential_fp64": worst}
 
 
+def warm_block(B, args, torch, np):
+    """The learned warm start: train the network on converged solutions of 40 (T, mu, window)
+    instances of the 4-band model on args.warm^3 meshes, then solve 10 held-out instances from
+    the RTA start and from the network's start (tolerance 1e-8): sweeps, outer iterations,
+    solve time and the worst coefficient difference between the two."""
+    from paper_2109_08547_gb300 import synthetic as S
+    from paper_2109_08547_gb300 import warmstart as WS
+    wl = S.workload_cscl4(args.warm)
+    grid = S.instance_grid(50, wl.mu_eV, seed=S.SEED_BASE + 6)
+    train, held = grid[:40], grid[40:]
+    union = (min(i[2] for i in grid), max(i[3] for i in grid))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tol = 1e-8
+    with B.Context(dev.index) as ctx:
+        B.set_wannier_model(ctx, wl.model)
+        B.build_meshes_ibz(ctx, wl.kmesh, wl.qmesh, union, wl.degen_tol_eV, wl.omega_min_eV)
+        B.compute_transition_rates(ctx, 0.0, 0.0, wl.sigma_eV, wl.cutoff_sigmas, instances=train)
+        B.solve_coupled_bte(ctx, "dragged", tol)
+        X, T = WS.instance_data(ctx, range(len(train)), dev)
+        net = B.MLP(seed=11)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        losses = WS.train(net, X, T, steps=600, lr=2e-3)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        B.compute_transition_rates(ctx, 0.0, 0.0, wl.sigma_eV, wl.cutoff_sigmas, instances=held)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plain = B.solve_coupled_bte(ctx, "dragged", tol)
+        torch.cuda.synchronize()
+        plain_s = time.perf_counter() - t0
+        base = [B.transport_coefficients(ctx, i) for i in range(len(held))]
+        # the best this parametrisation can do: each instance's own converged coordinates
+        nst = B.num_states(ctx)
+        ideal_a = []
+        for i in range(len(held)):
+            a = torch.empty((nst, 2), dtype=torch.float32, device=dev)
+            torch.cuda.synchronize()
+            B.state_targets(ctx, i, a.data_ptr())
+            ideal_a.append(a)
+        for i in range(len(held)):
+            B.set_warm_start(ctx, i, ideal_a[i].data_ptr())
+        ideal = B.solve_coupled_bte(ctx, "dragged", tol, warm_start=True)
+        B.compute_transition_rates(ctx, 0.0, 0.0, wl.sigma_eV, wl.cutoff_sigmas, instances=held)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(len(held)):
+            WS.apply(ctx, net, i, dev)
+        warm = B.solve_coupled_bte(ctx, "dragged", tol, warm_start=True)
+        torch.cuda.synchronize()
+        warm_s = time.perf_counter() - t0
+        worst = 0.0
+        for i in range(len(held)):
+            c = B.transport_coefficients(ctx, i)
+            for key, v in base[i].items():
+                nrm = float(np.linalg.norm(v))
+                if nrm > 0:
+                    worst = max(worst, float(np.linalg.norm(c[key] - v) / nrm))
+        net.close()
+    return {"mesh": args.warm, "train_instances": len(train), "held_out": len(held), "samples": int(X.shape[0]),
+            "train_steps": len(losses), "train_s": train_s, "loss_first": losses[0], "loss_last": losses[-1],
+            "tol": tol, "rta_start": {"sweeps": plain["n_sweeps"], "outer": plain["outer_iters"], "s": plain_s},
+            "warm_start": {"sweeps": warm["n_sweeps"], "outer": warm["outer_iters"], "s": warm_s,
+                           "includes": "network inference for every held-out instance"},
+            "ideal_projection_start": {"sweeps": ideal["n_sweeps"], "outer": ideal["outer_iters"],
+                                       "note": "each instance started from its own converged coordinates"},
+            "max_coeff_rel_diff": worst}
+
+
 def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -486,6 +557,7 @@ def main():
                               "coeff_rel_err": err}
 
     batched = batched_block(B, ctx, wl, args, flush, torch, np) if args.instances > 0 else None
+    warm = warm_block(B, args, torch, np) if args.warm > 0 else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -513,7 +585,7 @@ def main():
                           "self_sweep_kernel": r0.solve["ms_self_kernel"], "n_runs": r0.solve["n_runs"],
                           "drag_terms": r0.solve["ms_drag"], "ph_sweeps": r0.solve["ms_ph_sweep"],
                           "n_sweeps": r0.solve["n_sweeps"], "outer_iters": r0.solve["outer_iters"]},
-            "variants": variants, "batched": batched,
+            "variants": variants, "batched": batched, "warm_start": warm,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(out))

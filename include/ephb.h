@@ -247,7 +247,8 @@ ephb_status ephb_instance_solve_info(ephb_ctx *ctx, int inst, ephb_solve_info *o
  * warm-started solve does not converge, the instance is solved again from the RTA start.
  * States: the n_states = ephb_num_states() electron states (irreducible-window k x band) of
  * the meshes; inactive states get zero inputs and are ignored.
- *   features: EPHB_NFEAT floats per state: (eps-mu)/kT clipped to +-40, log10(W_RTA) - 13,
+ *   features: EPHB_NFEAT floats per state: (eps-mu)/kT clipped to +-40 and divided by 10,
+ *             log10(W_RTA) - 13,
  *             |v|/max|v|, T/300 K, mu/0.1 eV, eps/0.3 eV (device, FP32, [n_states][6]).
  *   targets:  after a solve, a_I = (I.J0)/(J0.J0)/k_B - (eps-mu)/(k_B T) and
  *             a_J = (J.J0)/(J0.J0) - 1 per state (0 where J0 = 0 or |v| < 1e-6 max|v|).

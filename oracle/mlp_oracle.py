@@ -89,14 +89,14 @@ def unflatten(vec, like):
 # ----------------------------------------------------------------------------------------
 
 def state_features(eps, vel, W_e, T, mu):
-    """Per state: (eps-mu)/kT, log10(W_e) - 13, |v| / max|v|, T/300 K, mu/0.1 eV, eps/0.3 eV.
-    States without a rate (W_e = 0) get log10 term 0."""
+    """Per state: (eps-mu)/kT clipped to +-40 and divided by 10, log10(W_e) - 13, |v| / max|v|,
+    T/300 K, mu/0.1 eV, eps/0.3 eV.  States without a rate (W_e = 0) get log10 term 0."""
     eps = np.asarray(eps, dtype=np.float64)
     kT = KB_EVK * T
     speed = np.linalg.norm(vel, axis=1)
     vmax = speed.max() if speed.size and speed.max() > 0 else 1.0
     lw = np.where(W_e > 0, np.log10(np.where(W_e > 0, W_e, 1.0)) - 13.0, 0.0)
-    return np.stack([np.clip((eps - mu) / kT, -40.0, 40.0), lw, speed / vmax, np.full_like(eps, T / 300.0),
+    return np.stack([np.clip((eps - mu) / kT, -40.0, 40.0) / 10.0, lw, speed / vmax, np.full_like(eps, T / 300.0),
                      np.full_like(eps, mu / 0.1), eps / 0.3], axis=1)
 
 

@@ -154,6 +154,11 @@ struct ephb_ctx : InstState {
   DBuf<double2> Tbuf, Abuf;
   // tensor-core contraction: phase slices, B' slices and scales, work items, output scratch
   DBuf<__nv_bfloat16> phis, bslices;
+  // stage A on tensor cores: k phase slices of a chunk, the model's g slices (made once per
+  // model and slice count) and their column scales
+  DBuf<__nv_bfloat16> phik, gslices;
+  DBuf<double> gscale;
+  int gslices_ns = 0;
   DBuf<double> bscale, Cbuf;
   DBuf<int> nitem, tc_err;
   DBuf<int64_t> item_ptr;
@@ -327,6 +332,7 @@ void ephb_destroy(ephb_ctx *ctx) {
   ctx->pair_ptr.release(); ctx->qpair_ptr.release(); ctx->scratch.release(); ctx->scal.release();
   ctx->cntE.release(); ctx->cntPh.release(); ctx->escan.release(); ctx->phscan.release();
   ctx->Tbuf.release(); ctx->Abuf.release();
+  ctx->phik.release(); ctx->gslices.release(); ctx->gscale.release();
   ctx->phis.release(); ctx->bslices.release(); ctx->bscale.release(); ctx->Cbuf.release(); ctx->nitem.release();
   ctx->tc_err.release(); ctx->item_ptr.release(); ctx->fk.release(); ctx->nbq.release(); ctx->wr.release();
   ctx->ut.release(); ctx->ucount.release();
@@ -425,6 +431,7 @@ ephb_status ephb_set_wannier_model(ephb_ctx *ctx, const ephb_model *m) {
   M.sym_inv = ctx->sym_inv.p;
   ctx->stage = 1;
   ctx->tune_cols[0] = ctx->tune_cols[1] = 0;   // a new model shape is tuned again
+  ctx->gslices_ns = 0;                          // and its g slices are made again
   ctx->bte_ready = false;
   return EPHB_OK;
 }
@@ -714,6 +721,9 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
   const int ns = precision == EPHB_FP64_SLICED ? 7 : 3;
   const int ncm = tensor && ctx->force_cols ? std::min(ctx->force_cols, tc_nc_max(ns)) : 0;   // 0: tuned width
   int autotuned = 0;
+  // stage A on the tensor cores too while its contraction length keeps the sums exact
+  const bool tensor_a = tensor && tc_kp_a(M) <= (ns == 7 ? 256 : 1024);
+  double tensor_flops_a = 0.0;
   std::vector<int64_t> hpp;
   int Nmax = 0;
   const int64_t kMaxChunkPairs = 1 << 20;   // bound of the contraction scratch (pairs x Nmax doubles)
@@ -732,6 +742,16 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     CK(ctx->item_ptr.ensure(chunk));
     CK(ctx->Cbuf.ensure(size_t(std::min<int64_t>(np, kMaxChunkPairs)) * Nmax));
     CK(ctx->tc_err.ensure(1));
+    if (tensor_a) {   // g slices once per model and slice count; k phase slices per chunk
+      const size_t gsz = size_t(ns) * tc_ncols_a(M) * tc_kp_a(M);
+      if (ctx->gslices_ns != ns || ctx->gslices.n < gsz) {
+        CK(ctx->gslices.ensure(gsz));
+        CK(ctx->gscale.ensure(tc_ncols_a(M)));
+        CK(launch_g_slices(M, ns, ctx->gslices.p, ctx->gscale.p, st));
+        ctx->gslices_ns = ns;
+      }
+      CK(ctx->phik.ensure(size_t(chunk) * ns * tc_kp_a(M)));
+    }
     CK(cudaMemsetAsync(ctx->tc_err.p, 0, sizeof(int), st));
     CK(cudaMemsetAsync(ctx->scal.p + 7, 0, sizeof(int64_t), st));
     CK(ctx->scratch.ensure(scan_scratch_elems(chunk > big ? chunk : big)));
@@ -750,7 +770,15 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
         return fail(ctx, EPHB_EINVAL, "one irreducible k has more pairs than the contraction scratch holds");
     }
     CK(ta.start(st));
-    CK(launch_stage_a(M, D, i0, nkc, ctx->Tbuf.p, ctx->Abuf.p, st));
+    if (tensor_a) {
+      CK(launch_stage_a_tc(M, D, ns, i0, nkc, ctx->phik.p, ctx->gslices.p, ctx->gscale.p, ctx->Tbuf.p,
+                           ctx->tc_err.p, ncm ? ncm : (ctx->tune_cols[ns == 7 ? 0 : 1] ? ctx->tune_cols[ns == 7 ? 0 : 1]
+                                                                                         : tc_nc_max(ns)),
+                           st, &tensor_flops_a));
+      CK(launch_stage_a2(M, D, i0, nkc, ctx->Tbuf.p, ctx->Abuf.p, st));
+    } else {
+      CK(launch_stage_a(M, D, i0, nkc, ctx->Tbuf.p, ctx->Abuf.p, st));
+    }
     CK(ta.stop(st));
     CK(tb.start(st));
     if (!tensor) {
@@ -807,7 +835,7 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     CK(cudaMemcpyAsync(&tfl, ctx->scal.p + 7, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (herr) return fail(ctx, EPHB_ETIMEOUT, "a tensor-core wait gave up (vertex contraction)");
-    tensor_flops = double(tfl);
+    tensor_flops = double(tfl) + tensor_flops_a;
   }
   unsigned long long cnt[5];
   CK(cudaMemcpyAsync(cnt, ctx->ucount.p, sizeof(cnt), cudaMemcpyDeviceToHost, st));

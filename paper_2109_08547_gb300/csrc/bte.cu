@@ -793,7 +793,7 @@ __global__ void k_speed_max(BteDev B, unsigned *vmax_bits) {
   atomicMax(vmax_bits, __float_as_uint(sp));
 }
 
-// inputs of the warm-start network per state: (eps-mu)/kT (clipped to +-40), log10(W)-13,
+// inputs of the warm-start network per state: (eps-mu)/kT (clipped to +-40) / 10, log10(W)-13,
 // |v|/max|v|, T/300 K, mu/0.1 eV, eps/0.3 eV; zeros for inactive states
 __global__ void k_state_features(BteDev B, const double *__restrict__ W_e, const unsigned *vmax_bits, float *feat) {
   const int64_t st = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
@@ -807,7 +807,7 @@ __global__ void k_state_features(BteDev B, const double *__restrict__ W_e, const
   const double *v = B.st_vel + st * 3;
   const float vmax = __uint_as_float(*vmax_bits);
   const double sp = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-  f[0] = float(fmin(fmax((e - B.mu) / kT, -40.0), 40.0));
+  f[0] = float(fmin(fmax((e - B.mu) / kT, -40.0), 40.0) / 10.0);
   f[1] = W > 0.0 ? float(log10(W) - 13.0) : 0.f;
   f[2] = vmax > 0.f ? float(sp / double(vmax)) : 0.f;
   f[3] = float(B.T / 300.0);

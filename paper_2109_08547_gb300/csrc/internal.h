@@ -115,6 +115,18 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
                              int *nitem, int64_t *item_ptr, int64_t *scratch, int64_t scratch_elems,
                              int64_t *total_dev, double *Cbuf, int *err, cudaStream_t st, cudaEvent_t gemm0,
                              cudaEvent_t gemm1, int ncm);
+// Stage A on tensor cores: T[kc][col] = sum_Re e^{ik.Re} g[Re][col] for the k of a chunk, as
+// the same exact-slice GEMM with the k phase slices as rows and the model's g slices (made
+// once by launch_g_slices, [ns][tc_ncols_a][tc_kp_a] BF16 + column scales) as B.
+int tc_kp_a(const ModelDev &M);
+int tc_ncols_a(const ModelDev &M);
+cudaError_t launch_g_slices(const ModelDev &M, int ns, __nv_bfloat16 *gs, double *gscale, cudaStream_t st);
+cudaError_t launch_stage_a_tc(const ModelDev &M, const MeshDev &D, int ns, int64_t i0, int64_t nkc,
+                              __nv_bfloat16 *phik, const __nv_bfloat16 *gs, const double *gscale, double2 *T, int *err,
+                              int ncm, cudaStream_t st, double *flops_acc);
+// The band rotation of stage A: A[kc][rp][(m,n',a)] = sum_m' c_{m'm}(k) T[kc][rp][m'][n'][a].
+cudaError_t launch_stage_a2(const ModelDev &M, const MeshDev &D, int64_t i0, int64_t nkc, const double2 *T, double2 *A,
+                            cudaStream_t st);
 // Column-chunk width of the contraction (its result does not depend on it: every column is
 // summed in the same order whatever the chunking).
 int tc_nc_max(int ns);

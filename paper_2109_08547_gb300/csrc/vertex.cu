@@ -633,6 +633,14 @@ cudaError_t launch_stage_a(const ModelDev &M, const MeshDev &D, int64_t i0, int6
   return cudaGetLastError();
 }
 
+cudaError_t launch_stage_a2(const ModelDev &M, const MeshDev &D, int64_t i0, int64_t nkc, const double2 *T, double2 *A,
+                            cudaStream_t st) {
+  const int64_t n2 = nkc * int64_t(M.nRgp) * M.nb * M.nb * M.nbr;
+  if (n2 == 0) return cudaSuccess;
+  EPHB_LAUNCH(k_stage_a2, unsigned((n2 + 255) / 256), 256, 0, st, M, D, i0, nkc, T, A);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_stage_b_rates(const ModelDev &M, const MeshDev &D, RateParams rp, int64_t i0, int64_t nkc,
                                  const double2 *A, const int64_t *escan, const int64_t *phscan, uint32_t *e_kpns,
                                  double2 *e_X, int *ph_st, uint32_t *ph_kpn, double *ph_Y, cudaStream_t st) {

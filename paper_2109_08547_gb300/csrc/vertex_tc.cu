@@ -122,6 +122,60 @@ __global__ void k_b_slices(ModelDev M, MeshDev D, int64_t i0, int64_t nkc, const
   }
 }
 
+// Phase slices of the k points of a chunk (stage A rows): PhiK[kc][slice][Kp] with the
+// (cos, sin) of 2 pi k.Re for r < nRe and nRe <= r < 2 nRe.
+__global__ void k_phase_slices_k(ModelDev M, MeshDev D, int64_t i0, int64_t nkc, int ns, int Kp,
+                                 __nv_bfloat16 *phik) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int R = M.nRge;
+  if (t >= nkc * int64_t(Kp)) return;
+  const int64_t kc = t / Kp;
+  const int r = int(t % Kp);
+  double x = 0.0;
+  if (r < 2 * R) {
+    const int rr = r < R ? r : r - R;
+    int a0, a1, a2;
+    D.km.unflat(D.ibzw_list[i0 + kc], a0, a1, a2);
+    const int *Rv = M.Rge + 3 * rr;
+    const double2 ph = mesh_phase(D.ktab, D.km, a0, a1, a2, Rv[0], Rv[1], Rv[2]);
+    x = r < R ? ph.x : ph.y;
+  }
+  fixed_slices(x, ns, phik + (size_t(kc) * ns) * Kp + r, size_t(Kp));
+}
+
+// Slices of the model's g as the B operand of stage A: column j' = 2 col + part of
+// T[k][col] = sum_Re e^{ik.Re} g[Re][col], col = (rp, m', n', alpha):
+//   part 0 (real): rows r < nRe: Re g[r][col];  r >= nRe: -Im g[r-nRe][col]
+//   part 1 (imag): rows r < nRe: Im g[r][col];  r >= nRe:  Re g[r-nRe][col]
+// GS[slice][Ncols][Kp] (BF16) and power-of-two column scales; one warp per column.
+__global__ void k_g_slices(ModelDev M, int ns, int Kp, int Ncols, __nv_bfloat16 *gs, double *gscale) {
+  const int64_t w = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= Ncols) return;
+  const int jp = int(w);
+  const int64_t ncol = int64_t(M.nRgp) * M.nb * M.nb * M.nbr;
+  const int R = M.nRge;
+  const int64_t col = jp / 2;
+  const int part = jp & 1;
+  const bool live = col < ncol;
+  auto value = [&](int r) -> double {
+    const double2 g = M.g_R[size_t(r < R ? r : r - R) * ncol + col];
+    return r < R ? (part == 0 ? g.x : g.y) : (part == 0 ? -g.y : g.x);
+  };
+  double mx = 0.0;
+  for (int r = lane; r < 2 * R; r += 32)
+    if (live) mx = fmax(mx, fabs(value(r)));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  int ex = 0;
+  if (mx > 0.0) frexp(mx, &ex);
+  const double inv_sigma = mx > 0.0 ? ldexp(1.0, -ex) : 1.0;
+  if (lane == 0) gscale[jp] = mx > 0.0 ? ldexp(1.0, ex) : 1.0;
+  for (int r = lane; r < Kp; r += 32) {
+    const double v = live && r < 2 * R ? value(r) : 0.0;
+    fixed_slices(v * inv_sigma, ns, gs + size_t(jp) * Kp + r, size_t(Ncols) * Kp);
+  }
+}
+
 // work items of a chunk: (k, 128-pair tile, column chunk); per k: ceil(npl/128) * nchunk(k)
 // (also accumulates the issued tensor-core flops: 2 * 128 * columns * Kp per slice product)
 __global__ void k_tc_items(ModelDev M, MeshDev D, int64_t i0, int64_t nkc, int nc_max, int Kp, int nprod,
@@ -178,12 +232,18 @@ __device__ __forceinline__ uint32_t core_off(int row, int kgroup) {
   return uint32_t(((row >> 3) * (kTcKc / 8) + kgroup) * 128 + (row & 7) * 16);
 }
 
+// Rows of a contraction: (k,q) pairs of each k (stage B: A rows are the phase slices of the
+// pair's q, B and the column scales belong to the pair's k) or k points of a chunk (stage A:
+// A rows are the k phase slices, B = the model's g slices shared by every k).
+enum { kRowsPairs = 0, kRowsK = 1 };
+
 struct TcParams {
-  int ns, nacc, Kp, Nmax, nc_max;
-  int64_t i0, nkc, pair_base;   // first pair of the chunk
+  int ns, nacc, Kp, Nmax, nc_max;   // Nmax: B rows per slice (columns of the real GEMM)
+  int64_t i0, nkc, pair_base;       // stage B: first pair of the chunk
+  int ncols, out_stride;            // stage A: live columns and the output row stride (doubles)
 };
 
-template <int NS, int NACC>
+template <int NS, int NACC, int ROWS>
 __global__ void __launch_bounds__(kTcThreads, 1) k_vertex_gemm(ModelDev M, MeshDev D, TcParams P,
                                                                const int64_t *__restrict__ item_ptr,
                                                                const __nv_bfloat16 *__restrict__ phis,
@@ -196,28 +256,50 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vertex_gemm(ModelDev M, MeshD
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // once a CTA has recorded a timeout the remaining ones return without waiting in turn
   if (*reinterpret_cast<volatile int *>(err)) return;
-  // which (k, tile, column chunk)
   const int64_t item = blockIdx.x;
-  int64_t lo = 0, hi = P.nkc;
-  while (hi - lo > 1) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (item_ptr[mid] <= item) lo = mid; else hi = mid;
+  int nc, n0, ncw, npt, a_row;   // a_row: this thread's A row (-1: zero-filled)
+  const __nv_bfloat16 *bsk;      // B slices of this item
+  const double *sc;              // column scales from n0
+  double *crow;                  // this thread's output row from n0
+  if (ROWS == kRowsPairs) {
+    // which (k, 128-pair tile, column chunk)
+    int64_t lo = 0, hi = P.nkc;
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (item_ptr[mid] <= item) lo = mid; else hi = mid;
+    }
+    const int64_t kc = lo;
+    const int64_t i = P.i0 + kc;
+    const int k = D.ibzw_list[i];
+    const int nk = round_up(2 * __popc(D.amask[k]) * M.nb * M.nbr, 16);
+    const int nch = (nk + P.nc_max - 1) / P.nc_max;
+    nc = round_up((nk + nch - 1) / nch, 16);                   // balanced chunk width
+    const int64_t local = item - item_ptr[kc];
+    const int tile = int(local / nch), chunk = int(local % nch);
+    n0 = chunk * nc;
+    ncw = nk - n0 < nc ? nk - n0 : nc;                        // columns of this chunk (multiple of 16)
+    const int64_t p0 = D.pair_ptr[i];
+    const int64_t npl = D.pair_ptr[i + 1] - p0;
+    const int64_t t0 = int64_t(tile) * kTcM;
+    npt = int(npl - t0 < kTcM ? npl - t0 : kTcM);
+    a_row = tid < npt ? D.pair_q[p0 + t0 + tid] : -1;
+    bsk = bs + size_t(kc) * NS * P.Nmax * P.Kp;
+    sc = bscale + kc * P.Nmax + n0;
+    crow = Cbuf + (p0 + t0 + tid - P.pair_base) * P.Nmax + n0;
+  } else {
+    // which (128-k tile, column chunk)
+    const int nch = (P.Nmax + P.nc_max - 1) / P.nc_max;
+    nc = round_up((P.Nmax + nch - 1) / nch, 16);
+    const int tile = int(item / nch), chunk = int(item % nch);
+    n0 = chunk * nc;
+    ncw = P.Nmax - n0 < nc ? P.Nmax - n0 : nc;
+    const int64_t t0 = int64_t(tile) * kTcM;
+    npt = int(P.nkc - t0 < kTcM ? P.nkc - t0 : kTcM);
+    a_row = tid < npt ? int(t0 + tid) : -1;
+    bsk = bs;
+    sc = bscale + n0;
+    crow = Cbuf + (t0 + tid) * P.out_stride + n0;
   }
-  const int64_t kc = lo;
-  const int64_t i = P.i0 + kc;
-  const int k = D.ibzw_list[i];
-  const int nb = M.nb, nbr = M.nbr;
-  const int nk = round_up(2 * __popc(D.amask[k]) * nb * nbr, 16);
-  const int nch = (nk + P.nc_max - 1) / P.nc_max;
-  const int nc = round_up((nk + nch - 1) / nch, 16);        // balanced chunk width
-  const int64_t local = item - item_ptr[kc];
-  const int tile = int(local / nch), chunk = int(local % nch);
-  const int n0 = chunk * nc;
-  const int ncw = nk - n0 < nc ? nk - n0 : nc;              // columns of this chunk (multiple of 16)
-  const int64_t p0 = D.pair_ptr[i];
-  const int64_t npl = D.pair_ptr[i + 1] - p0;
-  const int64_t t0 = int64_t(tile) * kTcM;
-  const int npt = int(npl - t0 < kTcM ? npl - t0 : kTcM);
 
   // two shared-memory stages, each NS x [128 x Kc] (A) followed by NS x [nc_max x Kc] (B)
   const size_t a_slice = size_t(kTcM) * kTcKc * 2, b_slice = size_t(P.nc_max) * kTcKc * 2;
@@ -240,10 +322,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vertex_gemm(ModelDev M, MeshD
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t taddr = tslot;
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(ncw >> 3) << 17) | (uint32_t(kTcM >> 4) << 24);
-  const int q_row = tid < npt ? D.pair_q[p0 + t0 + tid] : -1;
-  const __nv_bfloat16 *bsk = bs + size_t(kc) * NS * P.Nmax * P.Kp;
-  const __nv_bfloat16 *arow = phis + size_t(q_row < 0 ? 0 : q_row) * NS * P.Kp;
-  const uint32_t abytes = q_row >= 0 ? 16u : 0u;   // rows past the tile are zero-filled
+  const __nv_bfloat16 *arow = phis + size_t(a_row < 0 ? 0 : a_row) * NS * P.Kp;
+  const uint32_t abytes = a_row >= 0 ? 16u : 0u;   // rows past the tile are zero-filled
 
   // asynchronous copies of the operands of K block kb into stage buf (one commit group)
   auto stage_load = [&](int buf, int kb) {
@@ -319,13 +399,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vertex_gemm(ModelDev M, MeshD
   if (!ok) {
     if (tid == 0) atomicExch(err, 1);
   } else {
-    // accumulators -> FP64 combination -> C'[pair][n0 + j]
+    // accumulators -> FP64 combination -> C'[row][n0 + j]
     const int row = warp * 32 + lane;
-    const double *sc = bscale + kc * P.Nmax + n0;
-    double *crow = Cbuf + (p0 + t0 + row - P.pair_base) * P.Nmax + n0;
+    const int nlive = ROWS == kRowsPairs ? ncw : (P.ncols - n0 < ncw ? P.ncols - n0 : ncw);
+    // Exact accumulators (diagonals d = 0..NACC-2) hold integer multiples of 2^(-14-8d) below
+    // 2^24 of that unit; the tail is rounded to 2^-48.  All of them go into one 64-bit integer
+    // in units of 2^-48 (at most 2^57), converted to FP64 once.
     for (int c0 = 0; c0 < ncw; c0 += 16) {
-      double sum[16];
-      for (int j = 0; j < 16; ++j) sum[j] = 0.0;
+      long long sum[16];
+      for (int j = 0; j < 16; ++j) sum[j] = 0;
       for (int a = 0; a < NACC; ++a) {
         uint32_t v[16];
         const uint32_t ta = taddr + (uint32_t(warp * 32) << 16) + uint32_t(a * nc + c0);
@@ -335,10 +417,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vertex_gemm(ModelDev M, MeshD
               "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
             : "r"(ta));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        for (int j = 0; j < 16; ++j) sum[j] += double(__uint_as_float(v[j]));
+        if (a < NACC - 1) {
+          const float up = __int_as_float((127 + 14 + 8 * a) << 23);   // 2^(14+8a)
+          for (int j = 0; j < 16; ++j)
+            sum[j] += (long long)__float2int_rn(__uint_as_float(v[j]) * up) << (34 - 8 * a);
+        } else {
+          for (int j = 0; j < 16; ++j) sum[j] += __float2ll_rn(ldexpf(__uint_as_float(v[j]), 48));
+        }
       }
       if (row < npt)
-        for (int j = 0; j < 16; ++j) crow[c0 + j] = sc[c0 + j] * sum[j];
+        for (int j = 0; j < 16; ++j)
+          if (c0 + j < nlive) crow[c0 + j] = (sc[c0 + j] * 0x1p-48) * double(sum[j]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -358,6 +447,59 @@ std::vector<int> tc_nc_candidates(int ns) {
   return ns == 7 ? std::vector<int>{48, 64, 96} : std::vector<int>{64, 128, 256};
 }
 size_t tc_smem_bytes(int ns, int ncm) { return 2 * (size_t(ns) * kTcM * kTcKc * 2 + size_t(ns) * ncm * kTcKc * 2); }
+
+int tc_kp_a(const ModelDev &M) { return round_up(2 * M.nRge, kTcKc); }
+int tc_ncols_a(const ModelDev &M) { return round_up(2 * M.nRgp * M.nb * M.nb * M.nbr, 16); }
+
+cudaError_t launch_g_slices(const ModelDev &M, int ns, __nv_bfloat16 *gs, double *gscale, cudaStream_t st) {
+  const int Ncols = tc_ncols_a(M);
+  EPHB_LAUNCH(k_g_slices, unsigned((int64_t(Ncols) * 32 + 255) / 256), 256, 0, st, M, ns, tc_kp_a(M), Ncols, gs,
+              gscale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stage_a_tc(const ModelDev &M, const MeshDev &D, int ns, int64_t i0, int64_t nkc,
+                              __nv_bfloat16 *phik, const __nv_bfloat16 *gs, const double *gscale, double2 *T, int *err,
+                              int ncm, cudaStream_t st, double *flops_acc) {
+  if (nkc <= 0) return cudaSuccess;
+  if (!tc_nc_valid(ns, ncm)) return cudaErrorInvalidValue;
+  const int Kp = tc_kp_a(M), Ncols = tc_ncols_a(M);
+  const int64_t n = nkc * int64_t(Kp);
+  EPHB_LAUNCH(k_phase_slices_k, unsigned((n + 255) / 256), 256, 0, st, M, D, i0, nkc, ns, Kp, phik);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  TcParams P;
+  P.ns = ns;
+  P.nacc = ns == 7 ? 5 : 2;
+  P.Kp = Kp;
+  P.Nmax = Ncols;
+  P.nc_max = ncm;
+  P.i0 = i0;
+  P.nkc = nkc;
+  P.pair_base = 0;
+  P.ncols = 2 * M.nRgp * M.nb * M.nb * M.nbr;
+  P.out_stride = P.ncols;
+  const int nch = (Ncols + ncm - 1) / ncm;
+  const int64_t ntile = (nkc + kTcM - 1) / kTcM;
+  const int64_t nitems = ntile * nch;
+  const size_t smem = tc_smem_bytes(ns, ncm);
+  double *out = reinterpret_cast<double *>(T);
+  if (ns == 7) {
+    e = cudaFuncSetAttribute(k_vertex_gemm<7, 5, kRowsK>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    EPHB_LAUNCH((k_vertex_gemm<7, 5, kRowsK>), unsigned(nitems), kTcThreads, smem, st, M, D, P, nullptr, phik, gs,
+                gscale, out, err);
+  } else {
+    e = cudaFuncSetAttribute(k_vertex_gemm<3, 2, kRowsK>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    EPHB_LAUNCH((k_vertex_gemm<3, 2, kRowsK>), unsigned(nitems), kTcThreads, smem, st, M, D, P, nullptr, phik, gs,
+                gscale, out, err);
+  }
+  e = cudaGetLastError();
+  // issued MMA work: every item runs 128 rows x its chunk width x Kp for each slice product
+  if (flops_acc) *flops_acc += 2.0 * kTcM * double(Ncols) * Kp * (ns * (ns + 1) / 2) * double(ntile);
+  return e;
+}
 
 cudaError_t launch_phase_slices(const ModelDev &M, const MeshDev &D, int ns, __nv_bfloat16 *phis, cudaStream_t st) {
   const int Kp = tc_kp(M);
@@ -394,20 +536,22 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
   P.i0 = i0;
   P.nkc = nkc;
   P.pair_base = pair_base;
+  P.ncols = Nmax;
+  P.out_stride = Nmax;
   const size_t smem = tc_smem_bytes(ns, ncm);
   if (gemm0) {
     e = cudaEventRecord(gemm0, st);
     if (e != cudaSuccess) return e;
   }
   if (ns == 7) {
-    e = cudaFuncSetAttribute(k_vertex_gemm<7, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    e = cudaFuncSetAttribute(k_vertex_gemm<7, 5, kRowsPairs>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    EPHB_LAUNCH((k_vertex_gemm<7, 5>), unsigned(nitems), kTcThreads, smem, st, M, D, P, item_ptr, phis, bs, bscale,
+    EPHB_LAUNCH((k_vertex_gemm<7, 5, kRowsPairs>), unsigned(nitems), kTcThreads, smem, st, M, D, P, item_ptr, phis, bs, bscale,
                 Cbuf, err);
   } else {
-    e = cudaFuncSetAttribute(k_vertex_gemm<3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    e = cudaFuncSetAttribute(k_vertex_gemm<3, 2, kRowsPairs>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    EPHB_LAUNCH((k_vertex_gemm<3, 2>), unsigned(nitems), kTcThreads, smem, st, M, D, P, item_ptr, phis, bs, bscale,
+    EPHB_LAUNCH((k_vertex_gemm<3, 2, kRowsPairs>), unsigned(nitems), kTcThreads, smem, st, M, D, P, item_ptr, phis, bs, bscale,
                 Cbuf, err);
   }
   e = cudaGetLastError();

@@ -80,7 +80,7 @@ def test_targets_and_features():
     np.testing.assert_allclose(Jw, 2.0 * J0, rtol=1e-12)
     f = MO.state_features(np.array([0.1, -0.2]), np.array([[3.0, 4.0, 0.0], [0.0, 0.0, 1.0]]),
                           np.array([1e13, 0.0]), 300.0, 0.05)
-    np.testing.assert_allclose(f[:, 0], np.array([0.05, -0.25]) / (KB_EVK * 300.0), rtol=1e-15)
+    np.testing.assert_allclose(f[:, 0], np.array([0.05, -0.25]) / (KB_EVK * 300.0) / 10.0, rtol=1e-15)
     np.testing.assert_allclose(f[:, 1], [0.0, 0.0], atol=1e-15)
     np.testing.assert_allclose(f[:, 2], [1.0, 0.2], rtol=1e-15)
     np.testing.assert_allclose(f[:, 3:], [[1.0, 0.5, 1.0 / 3.0], [1.0, 0.5, -2.0 / 3.0]], rtol=1e-15)
