@@ -250,32 +250,38 @@ def batched_block(B, ctx, wl, args, flush, torch, np):
         seq_s += time.perf_counter() - t0
         seq_coeffs.append(r.coeffs)
 
-    def batched_run():
+    def batched_run(prec, solve_prec):
         B.build_meshes_ibz(ctx, wl.kmesh, wl.qmesh, union, wl.degen_tol_eV, wl.omega_min_eV)
-        rates = B.compute_transition_rates(ctx, 0.0, 0.0, wl.sigma_eV, wl.cutoff_sigmas,
-                                           B.PRECISIONS[args.precision], instances=insts)
-        solve = B.solve_coupled_bte(ctx, "dragged", wl.tol)
+        rates = B.compute_transition_rates(ctx, 0.0, 0.0, wl.sigma_eV, wl.cutoff_sigmas, B.PRECISIONS[prec],
+                                           instances=insts)
+        solve = B.solve_coupled_bte(ctx, "dragged", wl.tol, solve_precision=solve_prec)
         return rates, solve, [B.transport_coefficients(ctx, i) for i in range(len(insts))]
 
-    flush.zero_()
-    batched_run()                     # warm-up (allocations)
-    flush.zero_()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    rates, solve, coeffs = batched_run()
-    torch.cuda.synchronize()
-    bat_s = time.perf_counter() - t0
-    worst = {}
-    for c, ref in zip(coeffs, seq_coeffs):
-        for key, v in ref.items():
-            nrm = float(np.linalg.norm(v))
-            e = float(np.linalg.norm(c[key] - v) / nrm) if nrm > 0 else 0.0
-            worst[key] = max(worst.get(key, 0.0), e)
-    return {"instances": len(insts), "union_window_eV": list(union), "T_K_range": [100.0, 500.0],
-            "s_sequential_fp64": seq_s, "s_batched": bat_s, "speedup": seq_s / bat_s,
-            "batched_precision": args.precision, "batched_rates_ms": rates["ms"], "batched_solve_ms": solve["ms"],
-            "union_tuples": rates["n_tuples"], "converged": solve["converged"],
-            "max_coeff_rel_err_vs_sequential_fp64": worst}
+    out = {"instances": len(insts), "union_window_eV": list(union), "T_K_range": [100.0, 500.0],
+           "s_sequential_fp64": seq_s}
+    # FP64-grade batch (exact-slice vertex, FP64 iteration) and mixed batch (split-BF16 vertex,
+    # mixed-precision iteration)
+    for tag, prec, sp in (("fp64_grade", args.precision, "fp64"), ("mixed", "split-bf16", "mixed")):
+        flush.zero_()
+        batched_run(prec, sp)             # warm-up (allocations, tile tuning)
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rates, solve, coeffs = batched_run(prec, sp)
+        torch.cuda.synchronize()
+        bat_s = time.perf_counter() - t0
+        worst = {}
+        for c, ref in zip(coeffs, seq_coeffs):
+            for key, v in ref.items():
+                nrm = float(np.linalg.norm(v))
+                e = float(np.linalg.norm(c[key] - v) / nrm) if nrm > 0 else 0.0
+                worst[key] = max(worst.get(key, 0.0), e)
+        out[tag] = {"vertex_precision": prec, "solve_precision": sp, "s_batched": bat_s,
+                    "speedup_vs_sequential_fp64": seq_s / bat_s, "rates_ms": rates["ms"], "solve_ms": solve["ms"],
+                    "fp64_sweeps": solve["n_sweeps"], "fp32_sweeps": solve["n_sweeps32"],
+                    "union_tuples": rates["n_tuples"], "converged": solve["converged"],
+                    "max_coeff_rel_err_vs_sequential_fp64": worst}
+    return out
 
 
 def warm_block(B, args, torch, np):
@@ -403,8 +409,8 @@ def main():
 
     prec = B.PRECISIONS[args.precision]
 
-    def step(p=prec):
-        return B.run_path(ctx, wl, level="dragged", ko_correction=True, precision=p)
+    def step(p=prec, sp="fp64"):
+        return B.run_path(ctx, wl, level="dragged", ko_correction=True, precision=p, solve_precision=sp)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -537,15 +543,15 @@ def main():
     # result (which itself matches the FP64 oracle to 1e-8 in the parity tests)
     variants = {}
     if not args.no_variants:
-        for name, p in B.PRECISIONS.items():
-            if name == args.precision:
-                continue
+        cases = [(name, p, "fp64") for name, p in B.PRECISIONS.items() if name != args.precision]
+        cases += [(f"{args.precision}+mixed-solve", prec, "mixed"), ("split-bf16+mixed-solve", B.SPLIT_BF16, "mixed")]
+        for name, p, sp in cases:
             flush.zero_()
-            step(p)                       # warm-up of this mode
+            step(p, sp)                   # warm-up of this mode
             flush.zero_()
             torch.cuda.synchronize()
             tv = time.perf_counter()
-            rv = step(p)
+            rv = step(p, sp)
             torch.cuda.synchronize()
             sv = time.perf_counter() - tv
             err = {}
@@ -554,6 +560,8 @@ def main():
                 err[key] = float(np.linalg.norm(rv.coeffs[key] - ref) / nrm) if nrm > 0 else 0.0
             variants[name] = {"s_to_converged": sv, "value": rv.rates["n_tuples"] / sv,
                               "rates_ms": rv.rates["ms"], "stage_b_ms": rv.rates["ms_stage_b"],
+                              "solve_ms": rv.solve["ms"], "fp64_sweeps": rv.solve["n_sweeps"],
+                              "fp32_sweeps": rv.solve["n_sweeps32"],
                               "coeff_rel_err": err}
 
     batched = batched_block(B, ctx, wl, args, flush, torch, np) if args.instances > 0 else None

@@ -202,6 +202,14 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
  * terms are therefore absent.
  * --------------------------------------------------------------------------------*/
 typedef enum { EPHB_RTA = 0, EPHB_PARTIAL = 1, EPHB_DRAGLESS = 2, EPHB_DRAGGED = 3 } ephb_level;
+/* Arithmetic of the electron loop.
+ *   EPHB_SOLVE_FP64   plain FP64 Jacobi sweeps (the paper's iteration).
+ *   EPHB_SOLVE_MIXED  iterative refinement: every FP64 sweep x' = b + A x supplies the
+ *                     residual r = x' - x and the same convergence test as the plain loop; then
+ *                     12 FP32 sweeps of d <- r + A d (FP32 run weights) and x <- x + d before the
+ *                     next FP64 sweep.  Same fixed point; fewer FP64 sweeps.  The phonon sweeps,
+ *                     drag terms, KO step and coefficients stay FP64. */
+typedef enum { EPHB_SOLVE_FP64 = 0, EPHB_SOLVE_MIXED = 1 } ephb_solve_precision;
 
 typedef struct {
   int level;                   /* ephb_level                                               */
@@ -210,6 +218,7 @@ typedef struct {
   int max_outer, max_inner;
   int ko_correction;           /* 1: apply the Kelvin-Onsager step (dragged levels)        */
   int warm_start;              /* 1: start from ephb_set_warm_start's responses where set   */
+  int precision;               /* ephb_solve_precision                                     */
 } ephb_solve_opts;
 
 typedef struct {
@@ -228,6 +237,8 @@ typedef struct {
   int64_t n_runs;              /* partner runs: entries of a row merged over branches      */
   double ms_self_kernel;       /* summed device time of the self-term gather kernel alone  */
   double e_sweep_flops;        /* algorithmic FP64 flops of one self-term sweep            */
+  int64_t n_sweeps32;          /* FP32 correction sweeps (EPHB_SOLVE_MIXED)                */
+  double ms_corr;              /* device time of the FP32 corrections                      */
 } ephb_solve_info;
 
 /* Solves every instance.  `out` (optional) sums the counts and device times over the

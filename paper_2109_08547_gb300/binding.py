@@ -20,6 +20,7 @@ OK, EINVAL, ENOMEM, ECUDA, ESTATE, ENOCONV, ETIMEOUT, EINTERNAL = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ESTATE", "ENOCONV", "ETIMEOUT", "EINTERNAL"]
 FP64, SPLIT_TF32, SPLIT_BF16, FP64_SLICED = 0, 1, 2, 3
 PRECISIONS = {"fp64": FP64, "fp64-sliced": FP64_SLICED, "split-bf16": SPLIT_BF16}
+SOLVE_PRECISIONS = {"fp64": 0, "mixed": 1}
 RTA, PARTIAL, DRAGLESS, DRAGGED = 0, 1, 2, 3
 LEVELS = {"rta": RTA, "partial": PARTIAL, "dragless": DRAGLESS, "dragged": DRAGGED}
 
@@ -81,7 +82,8 @@ class RatesInfoC(C.Structure):
 
 class SolveOptsC(C.Structure):
     _fields_ = [("level", C.c_int), ("tol", C.c_double), ("inner_tol", C.c_double), ("max_outer", C.c_int),
-                ("max_inner", C.c_int), ("ko_correction", C.c_int), ("warm_start", C.c_int)]
+                ("max_inner", C.c_int), ("ko_correction", C.c_int), ("warm_start", C.c_int),
+                ("precision", C.c_int)]
 
 
 class SolveInfoC(C.Structure):
@@ -89,7 +91,8 @@ class SolveInfoC(C.Structure):
                 ("n_zero_rate_states", C.c_int), ("residual", C.c_double), ("lambda_", C.c_double),
                 ("n_sweeps", C.c_int64), ("ms", C.c_double), ("ms_e_sweep", C.c_double),
                 ("ms_ph_sweep", C.c_double), ("e_sweep_bytes", C.c_double), ("ms_drag", C.c_double),
-                ("n_runs", C.c_int64), ("ms_self_kernel", C.c_double), ("e_sweep_flops", C.c_double)]
+                ("n_runs", C.c_int64), ("ms_self_kernel", C.c_double), ("e_sweep_flops", C.c_double),
+                ("n_sweeps32", C.c_int64), ("ms_corr", C.c_double)]
 
 
 class CoeffsC(C.Structure):
@@ -312,9 +315,10 @@ def instance_solve_info(ctx: Context, inst: int) -> dict:
 
 
 def solve_coupled_bte(ctx: Context, level="dragged", tol=1e-10, inner_tol=0.0, max_outer=500, max_inner=5000,
-                      ko_correction=True, allow_noconv=False, warm_start=False) -> dict:
+                      ko_correction=True, allow_noconv=False, warm_start=False, solve_precision="fp64") -> dict:
     o = SolveOptsC(LEVELS[level] if isinstance(level, str) else int(level), float(tol), float(inner_tol),
-                   int(max_outer), int(max_inner), 1 if ko_correction else 0, 1 if warm_start else 0)
+                   int(max_outer), int(max_inner), 1 if ko_correction else 0, 1 if warm_start else 0,
+                   SOLVE_PRECISIONS[solve_precision])
     info = SolveInfoC()
     st = _check(ctx, _lib.ephb_solve_coupled_bte(ctx.handle, C.byref(o), C.byref(info)),
                 allow=(ENOCONV,) if allow_noconv else ())
@@ -383,12 +387,12 @@ class PathResult:
 
 
 def run_path(ctx: Context, wl, level="dragged", ko_correction=True, tol=None, max_outer=500, max_inner=5000,
-             precision=FP64, allow_noconv=False) -> PathResult:
+             precision=FP64, allow_noconv=False, solve_precision="fp64") -> PathResult:
     """The whole hot path for one workload on an existing context whose model is set."""
     mesh = build_meshes_ibz(ctx, wl.kmesh, wl.qmesh, wl.window, wl.degen_tol_eV, wl.omega_min_eV)
     rates = compute_transition_rates(ctx, wl.T_K, wl.mu_eV, wl.sigma_eV, wl.cutoff_sigmas, precision)
     solve = solve_coupled_bte(ctx, level, wl.tol if tol is None else tol, 0.0, max_outer, max_inner, ko_correction,
-                              allow_noconv)
+                              allow_noconv, solve_precision=solve_precision)
     return PathResult(mesh, rates, solve, transport_coefficients(ctx))
 
 

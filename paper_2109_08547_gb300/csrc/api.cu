@@ -102,6 +102,9 @@ struct InstState {
   DBuf<int> sctl;               // device-driven sweep loop: stop flag, sweeps done, converged
   DBuf<unsigned long long> nzero;
   DBuf<float> warm;             // warm-start scale factors [nst][2]
+  // mixed-precision electron loop: FP32 run weights, residual and correction vectors, partials
+  DBuf<float> run_w32, rI, rJ, dI, dJ, dI2, dJ2, part32;
+  bool have_f32 = false;
   DBuf<unsigned> vmaxb;
   bool bte_ready = false, has_warm = false, solved = false;
   ephb_solve_info last{};       // the instance's last solve
@@ -117,7 +120,8 @@ struct InstState {
     eseg_begin.release(); rseg_ptr.release(); rseg_begin.release(); run_ptr.release(); run_idx.release();
     run_col.release(); kcrd.release(); kinfo.release(); sctl.release(); nzero.release(); warm.release();
     vmaxb.release();
-    bte_ready = has_warm = solved = false;
+    for (auto *b : {&run_w32, &rI, &rJ, &dI, &dJ, &dI2, &dJ2, &part32}) b->release();
+    bte_ready = has_warm = solved = have_f32 = false;
   }
 };
 
@@ -936,6 +940,7 @@ ephb_status bte_setup(ephb_ctx *ctx) {
   CK(ctx->Dterm.ensure(nst * 6));
   CK(cudaMemsetAsync(ctx->Dterm.p, 0, nst * 6 * sizeof(double), st));
   ctx->bte_ready = true;
+  ctx->have_f32 = false;
   return EPHB_OK;
 }
 
@@ -974,6 +979,7 @@ ephb_status coefficients_to_host(ephb_ctx *ctx, double *prev, bool electron = tr
 }  // namespace
 
 constexpr int kSweepBatch = 8;   // electron sweeps queued per host round trip
+constexpr int kCorrSweeps = 12;  // FP32 correction sweeps per FP64 sweep (mixed precision)
 
 namespace {
 
@@ -1011,12 +1017,88 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
   double residual = 0.0, lambda = 1.0;
   EventTimer te, tp, td;
   EventTimer tsw[kSweepBatch];   // the self-term kernel of each queued sweep
+  EventTimer tc32;               // FP32 correction sweeps (mixed precision)
+  int64_t sweeps32 = 0;
+  CK(tc32.init());
   CK(te.init());
   CK(tp.init());
   CK(td.init());
   for (auto &t : tsw) CK(t.init());
 
+  // Mixed precision: each FP64 sweep x' = b + A x gives the residual (and the convergence test,
+  // the same as the plain loop's); then kCorrSweeps FP32 sweeps of d <- r + A d, r = x' - x,
+  // and x <- x + d, before the next FP64 sweep.
+  auto inner_loop_mixed = [&](int drag, bool &ok) -> ephb_status {
+    ok = false;
+    const int64_t n3 = nst * 3;
+    if (!ctx->have_f32) {
+      CK(ctx->run_w32.ensure(ctx->nruns));
+      for (auto *b : {&ctx->rI, &ctx->rJ, &ctx->dI, &ctx->dJ, &ctx->dI2, &ctx->dJ2}) CK(b->ensure(n3));
+      CK(ctx->part32.ensure(size_t(ctx->nrseg) * 6));
+      CK(launch_to_f32(ctx->nruns, ctx->run_w.p, ctx->run_w32.p, st));
+      ctx->have_f32 = true;
+    }
+    CK(cudaMemsetAsync(ctx->prev_in.p, 0, kResLen * sizeof(double), st));
+    ephb_status r = coefficients_to_host(ctx, ctx->prev_in.p, true, true);
+    if (r != EPHB_OK) return r;
+    if (drag) {
+      CK(td.start(st));
+      CK(launch_drag_term(D, B, entry_segs(ctx), ctx->F.p, ctx->G.p, ctx->seg_part.p, ctx->Dterm.p, st));
+      CK(td.stop(st));
+    }
+    const SweepSegs S = run_segs(ctx);
+    for (int it = 1; it <= o->max_inner; ++it) {
+      CK(te.start(st));
+      CK(launch_self_sweep(M, B, S, ctx->run_col.p, ctx->run_w.p, ctx->I0.p, ctx->J0.p, ctx->inv_ffW.p, ctx->I.p,
+                           ctx->J.p, ctx->I2.p, ctx->J2.p, drag ? ctx->Dterm.p : nullptr, ctx->seg_part.p,
+                           ctx->epart.p, nullptr, st, tsw[0].a, tsw[0].b));
+      tsw[0].pending = true;
+      CK(launch_coeff_final(ctx->M, B, ctx->epart.p, ctx->ppart.p, ctx->res.p, ctx->prev_in.p, st));
+      CK(te.stop(st));
+      CK(cudaMemcpyAsync(ctx->host_res, ctx->res.p, kResLen * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      CK(te.collect());
+      CK(td.collect());
+      CK(tsw[0].collect());
+      ++sweeps;
+      ++inner_total;
+      if (ctx->host_res[72] < inner_tol) {   // x' is the answer
+        std::swap(ctx->I.p, ctx->I2.p);
+        std::swap(ctx->J.p, ctx->J2.p);
+        B = bte_view(ctx);
+        ok = true;
+        return EPHB_OK;
+      }
+      if (it == o->max_inner) {
+        std::swap(ctx->I.p, ctx->I2.p);
+        std::swap(ctx->J.p, ctx->J2.p);
+        B = bte_view(ctx);
+        return EPHB_OK;
+      }
+      CK(tc32.start(st));
+      CK(launch_corr_init(nst, ctx->I2.p, ctx->I.p, ctx->J2.p, ctx->J.p, ctx->rI.p, ctx->rJ.p, ctx->dI.p, ctx->dJ.p,
+                          st));
+      float *dA = ctx->dI.p, *dAJ = ctx->dJ.p, *dB = ctx->dI2.p, *dBJ = ctx->dJ2.p;
+      for (int j = 0; j < kCorrSweeps; ++j) {
+        CK(launch_corr_sweep(M, nst, S, ctx->run_col.p, ctx->run_w32.p, ctx->inv_ffW.p, ctx->rI.p, ctx->rJ.p, dA,
+                             dAJ, ctx->part32.p, dB, dBJ, st));
+        std::swap(dA, dB);
+        std::swap(dAJ, dBJ);
+      }
+      sweeps32 += kCorrSweeps;
+      CK(launch_corr_apply(nst, dA, dAJ, ctx->I.p, ctx->J.p, st));
+      CK(tc32.stop(st));
+      // coefficients of the corrected x become the reference of the next FP64 sweep's test
+      CK(launch_e_partial(B, ctx->I.p, ctx->J.p, ctx->epart.p, st));
+      CK(launch_coeff_final(ctx->M, B, ctx->epart.p, ctx->ppart.p, ctx->res.p, ctx->prev_in.p, st));
+      CK(cudaStreamSynchronize(st));
+      CK(tc32.collect());
+    }
+    return EPHB_OK;
+  };
+
   auto inner_loop = [&](int drag, bool &ok) -> ephb_status {
+    if (o->precision == EPHB_SOLVE_MIXED) return inner_loop_mixed(drag, ok);
     ok = false;
     CK(cudaMemsetAsync(ctx->prev_in.p, 0, kResLen * sizeof(double), st));
     ephb_status r = coefficients_to_host(ctx, ctx->prev_in.p, true, true);
@@ -1121,6 +1203,8 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
     double ms_self = 0.0;
     for (auto &t : tsw) ms_self += t.ms;
     out->ms_self_kernel = ms_self;
+    out->n_sweeps32 = sweeps32;
+    out->ms_corr = tc32.ms;
     // FP64 work of one self-term sweep: 6 multiply-adds per run (+ two 3x3 rotations with symmetry)
     out->e_sweep_flops = double(ctx->nruns) * (ctx->M.nsym > 1 ? 12.0 + 36.0 : 12.0);
     out->ms_ph_sweep = tp.ms;
@@ -1144,6 +1228,8 @@ ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb
   if (!o) return fail(ctx, EPHB_EINVAL, "opts is NULL");
   if (o->level < EPHB_RTA || o->level > EPHB_DRAGGED) return fail(ctx, EPHB_EINVAL, "bad level");
   if (!(o->tol > 0) || o->max_outer < 1 || o->max_inner < 1) return fail(ctx, EPHB_EINVAL, "bad tolerances");
+  if (o->precision != EPHB_SOLVE_FP64 && o->precision != EPHB_SOLVE_MIXED)
+    return fail(ctx, EPHB_EINVAL, "bad solve precision");
   CK(cudaSetDevice(ctx->device));
   // every instance in turn; the summary adds up counts and times and keeps the worst residual
   ephb_solve_info sum{};
@@ -1182,6 +1268,8 @@ ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb
     sum.ms_drag += one.ms_drag;
     sum.n_runs += one.n_runs;
     sum.ms_self_kernel += one.ms_self_kernel;
+    sum.n_sweeps32 += one.n_sweeps32;
+    sum.ms_corr += one.ms_corr;
     sum.e_sweep_flops += one.e_sweep_flops;
   }
   select_instance(ctx, 0);

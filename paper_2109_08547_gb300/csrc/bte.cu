@@ -745,6 +745,131 @@ cudaError_t launch_self_sweep(const ModelDev &M, const BteDev &B, const SweepSeg
   return cudaGetLastError();
 }
 
+namespace {
+
+// ---- mixed-precision electron loop: FP32 correction sweeps between FP64 residual sweeps
+// d <- r + (1/(f(1-f)W)) sum_runs w d[partner] in FP32 over the same runs and segments.
+
+__global__ void __launch_bounds__(256) k_corr_sweep_seg(ModelDev M, SweepSegs S, const uint32_t *__restrict__ run_col,
+                                                        const float *__restrict__ run_w32,
+                                                        const float *__restrict__ dI, const float *__restrict__ dJ,
+                                                        float *__restrict__ part) {
+  __shared__ float C[kMaxSym * 9];
+  const bool sym = M.nsym > 1;
+  if (sym) {
+    for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) C[t] = float(M.sym_cart[t]);
+    __syncthreads();
+  }
+  const int64_t g = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= S.nseg) return;
+  const int row = S.seg_row[g];
+  const int64_t b = S.seg_begin[g];
+  const int64_t rend = S.row_ptr[row + 1];
+  const int64_t e_end = b + kSeg < rend ? b + kSeg : rend;
+  float a[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t e = b + lane; e < e_end; e += 32) {
+    const uint32_t pc = run_col[e];
+    const uint32_t col = pc & kRunColMask;
+    if (col == kRunNone) continue;
+    const float w = run_w32[e];
+    float vi[3] = {dI[int64_t(col) * 3], dI[int64_t(col) * 3 + 1], dI[int64_t(col) * 3 + 2]};
+    float vj[3] = {dJ[int64_t(col) * 3], dJ[int64_t(col) * 3 + 1], dJ[int64_t(col) * 3 + 2]};
+    if (sym) {
+      const float *Cs = C + 9 * (pc >> 26);
+      float r[3];
+      for (int x = 0; x < 3; ++x) r[x] = Cs[3 * x] * vi[0] + Cs[3 * x + 1] * vi[1] + Cs[3 * x + 2] * vi[2];
+      for (int x = 0; x < 3; ++x) vi[x] = r[x];
+      for (int x = 0; x < 3; ++x) r[x] = Cs[3 * x] * vj[0] + Cs[3 * x + 1] * vj[1] + Cs[3 * x + 2] * vj[2];
+      for (int x = 0; x < 3; ++x) vj[x] = r[x];
+    }
+    for (int c = 0; c < 3; ++c) {
+      a[c] = fmaf(w, vi[c], a[c]);
+      a[3 + c] = fmaf(w, vj[c], a[3 + c]);
+    }
+  }
+  for (int c = 0; c < 6; ++c)
+    for (int o = 16; o > 0; o >>= 1) a[c] += __shfl_down_sync(0xffffffffu, a[c], o);
+  if (lane == 0)
+    for (int c = 0; c < 6; ++c) part[g * 6 + c] = a[c];
+}
+
+__global__ void k_corr_finalize(int64_t nst, SweepSegs S, const float *__restrict__ part,
+                                const float *__restrict__ rI, const float *__restrict__ rJ,
+                                const double *__restrict__ inv_ffW, float *dI, float *dJ) {
+  const int64_t st = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (st >= nst) return;
+  float sum[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t g = S.seg_ptr[st]; g < S.seg_ptr[st + 1]; ++g)
+    for (int c = 0; c < 6; ++c) sum[c] += part[g * 6 + c];
+  const float c0 = float(inv_ffW[st]);
+  for (int c = 0; c < 3; ++c) {
+    dI[st * 3 + c] = rI[st * 3 + c] + c0 * sum[c];
+    dJ[st * 3 + c] = rJ[st * 3 + c] + c0 * sum[3 + c];
+  }
+}
+
+// r = x' - x (FP32), d = r
+__global__ void k_corr_init(int64_t n3, const double *I1, const double *I0x, const double *J1, const double *J0x,
+                            float *rI, float *rJ, float *dI, float *dJ) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= n3) return;
+  const float a = float(I1[t] - I0x[t]), b = float(J1[t] - J0x[t]);
+  rI[t] = a;
+  dI[t] = a;
+  rJ[t] = b;
+  dJ[t] = b;
+}
+
+// x <- x + d (FP64)
+__global__ void k_corr_apply(int64_t n3, const float *dI, const float *dJ, double *I, double *J) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= n3) return;
+  I[t] += double(dI[t]);
+  J[t] += double(dJ[t]);
+}
+
+__global__ void k_to_f32(int64_t n, const double *a, float *b) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t < n) b[t] = float(a[t]);
+}
+
+}  // namespace
+
+cudaError_t launch_to_f32(int64_t n, const double *a, float *b, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  EPHB_LAUNCH(k_to_f32, unsigned((n + 255) / 256), 256, 0, st, n, a, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_corr_init(int64_t nst, const double *I1, const double *I0x, const double *J1, const double *J0x,
+                             float *rI, float *rJ, float *dI, float *dJ, cudaStream_t st) {
+  const int64_t n3 = nst * 3;
+  if (n3 == 0) return cudaSuccess;
+  EPHB_LAUNCH(k_corr_init, unsigned((n3 + 255) / 256), 256, 0, st, n3, I1, I0x, J1, J0x, rI, rJ, dI, dJ);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_corr_sweep(const ModelDev &M, int64_t nst, const SweepSegs &S, const uint32_t *run_col,
+                              const float *run_w32, const double *inv_ffW, const float *rI, const float *rJ,
+                              const float *dI, const float *dJ, float *part, float *dI_out, float *dJ_out,
+                              cudaStream_t st) {
+  if (S.nseg > 0)
+    EPHB_LAUNCH(k_corr_sweep_seg, unsigned((S.nseg * 32 + 255) / 256), 256, 0, st, M, S, run_col, run_w32, dI, dJ,
+                part);
+  if (nst > 0)
+    EPHB_LAUNCH(k_corr_finalize, unsigned((nst + 255) / 256), 256, 0, st, nst, S, part, rI, rJ, inv_ffW, dI_out,
+                dJ_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_corr_apply(int64_t nst, const float *dI, const float *dJ, double *I, double *J, cudaStream_t st) {
+  const int64_t n3 = nst * 3;
+  if (n3 == 0) return cudaSuccess;
+  EPHB_LAUNCH(k_corr_apply, unsigned((n3 + 255) / 256), 256, 0, st, n3, dI, dJ, I, J);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_drag_term(const MeshDev &D, const BteDev &B, const SweepSegs &S, const double *F, const double *G,
                              double *part, double *Dterm, cudaStream_t st) {
   if (B.nst == 0) return cudaSuccess;

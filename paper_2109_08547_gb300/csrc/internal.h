@@ -220,6 +220,16 @@ int coeff_partials();
 cudaError_t launch_e_partial(const BteDev &B, const double *I, const double *J, double *epart, cudaStream_t st);
 cudaError_t launch_ph_partial(const MeshDev &D, const BteDev &B, const double *F, const double *G, double *ppart,
                               cudaStream_t st);
+// Mixed-precision electron loop: FP32 copies, the correction start r = x' - x (d = r), one FP32
+// correction sweep d_out = r + (1/(f(1-f)W)) sum_runs w d[partner], and x += d.
+cudaError_t launch_to_f32(int64_t n, const double *a, float *b, cudaStream_t st);
+cudaError_t launch_corr_init(int64_t nst, const double *I1, const double *I0x, const double *J1, const double *J0x,
+                             float *rI, float *rJ, float *dI, float *dJ, cudaStream_t st);
+cudaError_t launch_corr_sweep(const ModelDev &M, int64_t nst, const SweepSegs &S, const uint32_t *run_col,
+                              const float *run_w32, const double *inv_ffW, const float *rI, const float *rJ,
+                              const float *dI, const float *dJ, float *part, float *dI_out, float *dJ_out,
+                              cudaStream_t st);
+cudaError_t launch_corr_apply(int64_t nst, const float *dI, const float *dJ, double *I, double *J, cudaStream_t st);
 // Warm start: network inputs per state (kNFeat floats), training targets (2 floats: the
 // converged I, J along the RTA direction J0 = v/W), and starting responses from them.
 constexpr int kNFeat = 6;
