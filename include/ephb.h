@@ -164,8 +164,9 @@ typedef struct { double sigma_eV, cutoff_sigmas; } ephb_delta;
  *   EPHB_SPLIT_BF16   3 slices, the leading diagonal exact, the rest in one FP32 accumulator
  *                     (mixed precision, ~1e-7 relative).  Needs 2 nRgp <= 1024.
  *   EPHB_SPLIT_TF32   not available (EPHB_EINVAL).
- * The stage-A contraction, the rotations, |g|^2, occupations and delta stay FP64 in every
- * mode. */
+ * In both tensor-core modes the stage-A contraction (R_e sum) runs on the tensor cores in the
+ * FP64-grade 7-slice form when 2 nRe <= 256 (else in FP64).  The rotations, |g|^2,
+ * occupations and delta stay FP64 in every mode. */
 typedef enum { EPHB_FP64 = 0, EPHB_SPLIT_TF32 = 1, EPHB_SPLIT_BF16 = 2, EPHB_FP64_SLICED = 3 } ephb_precision;
 
 typedef struct {

@@ -725,8 +725,10 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
   const int ns = precision == EPHB_FP64_SLICED ? 7 : 3;
   const int ncm = tensor && ctx->force_cols ? std::min(ctx->force_cols, tc_nc_max(ns)) : 0;   // 0: tuned width
   int autotuned = 0;
-  // stage A on the tensor cores too while its contraction length keeps the sums exact
-  const bool tensor_a = tensor && tc_kp_a(M) <= (ns == 7 ? 256 : 1024);
+  // stage A on the tensor cores too, always in the FP64-grade form (its error would add to the
+  // mixed mode's), while its contraction length keeps the diagonal sums exact
+  const int ns_a = 7;
+  const bool tensor_a = tensor && tc_kp_a(M) <= 256;
   double tensor_flops_a = 0.0;
   std::vector<int64_t> hpp;
   int Nmax = 0;
@@ -746,15 +748,15 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     CK(ctx->item_ptr.ensure(chunk));
     CK(ctx->Cbuf.ensure(size_t(std::min<int64_t>(np, kMaxChunkPairs)) * Nmax));
     CK(ctx->tc_err.ensure(1));
-    if (tensor_a) {   // g slices once per model and slice count; k phase slices per chunk
-      const size_t gsz = size_t(ns) * tc_ncols_a(M) * tc_kp_a(M);
-      if (ctx->gslices_ns != ns || ctx->gslices.n < gsz) {
+    if (tensor_a) {   // g slices once per model; k phase slices per chunk
+      const size_t gsz = size_t(ns_a) * tc_ncols_a(M) * tc_kp_a(M);
+      if (ctx->gslices_ns != ns_a || ctx->gslices.n < gsz) {
         CK(ctx->gslices.ensure(gsz));
         CK(ctx->gscale.ensure(tc_ncols_a(M)));
-        CK(launch_g_slices(M, ns, ctx->gslices.p, ctx->gscale.p, st));
-        ctx->gslices_ns = ns;
+        CK(launch_g_slices(M, ns_a, ctx->gslices.p, ctx->gscale.p, st));
+        ctx->gslices_ns = ns_a;
       }
-      CK(ctx->phik.ensure(size_t(chunk) * ns * tc_kp_a(M)));
+      CK(ctx->phik.ensure(size_t(chunk) * ns_a * tc_kp_a(M)));
     }
     CK(cudaMemsetAsync(ctx->tc_err.p, 0, sizeof(int), st));
     CK(cudaMemsetAsync(ctx->scal.p + 7, 0, sizeof(int64_t), st));
@@ -775,10 +777,10 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     }
     CK(ta.start(st));
     if (tensor_a) {
-      CK(launch_stage_a_tc(M, D, ns, i0, nkc, ctx->phik.p, ctx->gslices.p, ctx->gscale.p, ctx->Tbuf.p,
-                           ctx->tc_err.p, ncm ? ncm : (ctx->tune_cols[ns == 7 ? 0 : 1] ? ctx->tune_cols[ns == 7 ? 0 : 1]
-                                                                                         : tc_nc_max(ns)),
-                           st, &tensor_flops_a));
+      const int width_a = ctx->force_cols ? std::min(ctx->force_cols, tc_nc_max(ns_a))
+                                          : (ctx->tune_cols[0] ? ctx->tune_cols[0] : tc_nc_max(ns_a));
+      CK(launch_stage_a_tc(M, D, ns_a, i0, nkc, ctx->phik.p, ctx->gslices.p, ctx->gscale.p, ctx->Tbuf.p,
+                           ctx->tc_err.p, width_a, st, &tensor_flops_a));
       CK(launch_stage_a2(M, D, i0, nkc, ctx->Tbuf.p, ctx->Abuf.p, st));
     } else {
       CK(launch_stage_a(M, D, i0, nkc, ctx->Tbuf.p, ctx->Abuf.p, st));
