@@ -104,6 +104,8 @@ struct InstState {
   DBuf<float> warm;             // warm-start scale factors [nst][2]
   // mixed-precision electron loop: FP32 run weights, residual and correction vectors, partials
   DBuf<float> run_w32, rI, rJ, dI, dJ, dI2, dJ2, part32;
+  DBuf<double2> IJ, IJ2;        // packed responses for the FP64 gathers
+  DBuf<unsigned> fuse_ctr;      // blocks done in the fused finalisation
   bool have_f32 = false;
   DBuf<unsigned> vmaxb;
   bool bte_ready = false, has_warm = false, solved = false;
@@ -121,6 +123,9 @@ struct InstState {
     run_col.release(); kcrd.release(); kinfo.release(); sctl.release(); nzero.release(); warm.release();
     vmaxb.release();
     for (auto *b : {&run_w32, &rI, &rJ, &dI, &dJ, &dI2, &dJ2, &part32}) b->release();
+    IJ.release();
+    IJ2.release();
+    fuse_ctr.release();
     bte_ready = has_warm = solved = have_f32 = false;
   }
 };
@@ -1116,6 +1121,21 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
     const SweepSegs S = run_segs(ctx);
     int *hctl = reinterpret_cast<int *>(ctx->host_res + kResLen);
     CK(cudaMemsetAsync(ctx->sctl.p, 0, 4 * sizeof(int), st));
+    CK(ctx->IJ.ensure(nst * 3));
+    CK(ctx->IJ2.ensure(nst * 3));
+    CK(launch_pack_ij(nst, ctx->I.p, ctx->J.p, ctx->IJ.p, st));
+    // the sweep writes the electron partial sums and, in its last block, the coefficients
+    // (the phonon partials are unchanged in the electron loop)
+    CK(ctx->fuse_ctr.ensure(1));
+    CK(cudaMemsetAsync(ctx->fuse_ctr.p, 0, sizeof(unsigned), st));
+    CoeffFuse fuse;
+    fuse.ppart = ctx->ppart.p;
+    fuse.res = ctx->res.p;
+    fuse.prev = ctx->prev_in.p;
+    fuse.ctl = ctx->sctl.p;
+    fuse.max_sweeps = o->max_inner;
+    fuse.tol = inner_tol;
+    fuse.counter = ctx->fuse_ctr.p;
     int queued = 0;
     for (;;) {
       const int nb = std::min(kSweepBatch, o->max_inner - queued);
@@ -1123,11 +1143,8 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
       for (int j = 0; j < nb; ++j) {
         CK(launch_self_sweep(M, B, S, ctx->run_col.p, ctx->run_w.p, ctx->I0.p, ctx->J0.p, ctx->inv_ffW.p, ctx->I.p,
                              ctx->J.p, ctx->I2.p, ctx->J2.p, drag ? ctx->Dterm.p : nullptr, ctx->seg_part.p,
-                             ctx->epart.p, ctx->sctl.p, st, tsw[j].a, tsw[j].b));
+                             ctx->epart.p, ctx->sctl.p, st, tsw[j].a, tsw[j].b, ctx->IJ.p, ctx->IJ2.p, &fuse));
         tsw[j].pending = true;
-        // the sweep already wrote the electron partial sums; the phonon ones are unchanged
-        CK(launch_coeff_final(ctx->M, B, ctx->epart.p, ctx->ppart.p, ctx->res.p, ctx->prev_in.p, st, ctx->sctl.p,
-                              o->max_inner, inner_tol));
       }
       CK(te.stop(st));
       queued += nb;
@@ -1145,6 +1162,7 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
     if (done & 1) {   // the last sweep wrote the second buffer pair
       std::swap(ctx->I.p, ctx->I2.p);
       std::swap(ctx->J.p, ctx->J2.p);
+      std::swap(ctx->IJ.p, ctx->IJ2.p);
     }
     B = bte_view(ctx);
     ok = hctl[2] != 0;

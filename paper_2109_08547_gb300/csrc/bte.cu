@@ -206,6 +206,8 @@ __global__ void __launch_bounds__(256) k_self_sweep_seg(ModelDev M, SweepSegs S,
                                                         const double *__restrict__ run_w,
                                                         const double *__restrict__ I, const double *__restrict__ J,
                                                         const double *__restrict__ I2, const double *__restrict__ J2,
+                                                        const double2 *__restrict__ IJ,
+                                                        const double2 *__restrict__ IJ2,
                                                         const int *__restrict__ ctl, double *__restrict__ part) {
   // device-driven loop: skip once stopped; odd sweeps read the second buffer pair
   if (ctl) {
@@ -213,6 +215,7 @@ __global__ void __launch_bounds__(256) k_self_sweep_seg(ModelDev M, SweepSegs S,
     if (ctl[1] & 1) {
       I = I2;
       J = J2;
+      IJ = IJ2;
     }
   }
   __shared__ double C[kMaxSym * 9];
@@ -241,8 +244,16 @@ __global__ void __launch_bounds__(256) k_self_sweep_seg(ModelDev M, SweepSegs S,
     for (int u = 0; u < kUnroll; ++u) {
       const uint32_t col = pc[u] & kRunColMask;
       if (col == kRunNone) continue;
-      double vi[3] = {I[int64_t(col) * 3], I[int64_t(col) * 3 + 1], I[int64_t(col) * 3 + 2]};
-      double vj[3] = {J[int64_t(col) * 3], J[int64_t(col) * 3 + 1], J[int64_t(col) * 3 + 2]};
+      double vi[3], vj[3];
+      if (IJ) {   // packed (I, J) of the partner: three 16-byte loads
+        const double2 *p = IJ + int64_t(col) * 3;
+        const double2 a = p[0], b = p[1], c = p[2];
+        vi[0] = a.x; vi[1] = a.y; vi[2] = b.x;
+        vj[0] = b.y; vj[1] = c.x; vj[2] = c.y;
+      } else {
+        vi[0] = I[int64_t(col) * 3]; vi[1] = I[int64_t(col) * 3 + 1]; vi[2] = I[int64_t(col) * 3 + 2];
+        vj[0] = J[int64_t(col) * 3]; vj[1] = J[int64_t(col) * 3 + 1]; vj[2] = J[int64_t(col) * 3 + 2];
+      }
       if (SYM) {
         double r[3];
         const double *Cs = C + 9 * (pc[u] >> 26);
@@ -415,78 +426,11 @@ __device__ inline void e_tensor_acc(const BteDev &B, int64_t st, const double *I
     }
 }
 
-// I = I0 + (self partials + drag term) / (f(1-f) W), same for J; plus the electron
-// coefficient partial sums of the new responses.
-__global__ void __launch_bounds__(kCT) k_e_finalize(BteDev B, SweepSegs S, const double *__restrict__ part,
-                                                    const double *__restrict__ Dterm, const double *__restrict__ I0,
-                                                    const double *__restrict__ J0, const double *__restrict__ inv_ffW,
-                                                    double *I_out, double *J_out, double *I_alt, double *J_alt,
-                                                    const int *__restrict__ ctl, double *epart) {
-  if (ctl) {
-    if (ctl[0]) return;
-    if (ctl[1] & 1) {
-      I_out = I_alt;
-      J_out = J_alt;
-    }
-  }
-  double acc[kNE];
-  for (int j = 0; j < kNE; ++j) acc[j] = 0.0;
-  const int64_t stride = int64_t(gridDim.x) * kCT;
-  for (int64_t st = blockIdx.x * int64_t(kCT) + threadIdx.x; st < B.nst; st += stride) {
-    double s[6] = {0, 0, 0, 0, 0, 0};
-    for (int64_t g = S.seg_ptr[st]; g < S.seg_ptr[st + 1]; ++g)
-      for (int c = 0; c < 6; ++c) s[c] += part[g * 6 + c];
-    if (Dterm)
-      for (int c = 0; c < 6; ++c) s[c] += Dterm[st * 6 + c];
-    const double c0 = inv_ffW[st];
-    double In[3], Jn[3];
-    for (int c = 0; c < 3; ++c) {
-      In[c] = I0[st * 3 + c] + s[c] * c0;
-      Jn[c] = J0[st * 3 + c] + s[3 + c] * c0;
-      I_out[st * 3 + c] = In[c];
-      J_out[st * 3 + c] = Jn[c];
-    }
-    e_tensor_acc(B, st, In, Jn, acc);
-  }
-  block_reduce_store(acc, kNE, epart + size_t(blockIdx.x) * kNE);
-}
-
-__global__ void __launch_bounds__(kCT) k_e_partial(BteDev B, const double *I, const double *J, double *epart) {
-  double acc[kNE];
-  for (int j = 0; j < kNE; ++j) acc[j] = 0.0;
-  const int64_t stride = int64_t(gridDim.x) * kCT;
-  for (int64_t st = blockIdx.x * int64_t(kCT) + threadIdx.x; st < B.nst; st += stride)
-    e_tensor_acc(B, st, I + st * 3, J + st * 3, acc);
-  block_reduce_store(acc, kNE, epart + size_t(blockIdx.x) * kNE);
-}
-
-__global__ void __launch_bounds__(kCT) k_ph_partial(MeshDev D, BteDev B, const double *F, const double *G,
-                                                    double *ppart) {
-  double acc[kNP];
-  for (int j = 0; j < kNP; ++j) acc[j] = 0.0;
-  const int64_t stride = int64_t(gridDim.x) * kCT;
-  const double kT = kKbEVK * B.T;
-  for (int64_t t = blockIdx.x * int64_t(kCT) + threadIdx.x; t < B.nq * B.nbr; t += stride) {
-    double w = D.w[t];
-    if (!(w > D.omega_min)) continue;
-    double n = bose_b(w, kT);
-    double wt = w * n * (1.0 + n);
-    const double *v = D.vph + t * 3;
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) {
-        acc[a * 3 + b] += -wt * v[a] * G[t * 3 + b];
-        acc[9 + a * 3 + b] += wt * v[a] * F[t * 3 + b];
-      }
-  }
-  block_reduce_store(acc, kNP, ppart + size_t(blockIdx.x) * kNP);
-}
-
 // Final assembly, spread over threads (single-thread FP64 chains are slow on this GPU).
 // res: [0] sigma [9] sigmaS [18] alpha_el [27] kappa0_el [36] alpha_ph [45] kappa_ph [54] S [63] kappa_el
 //      [72] residual_e [73] residual_all
-__global__ void __launch_bounds__(512) k_coeff_final(ModelDev M, BteDev B, const double *epart,
-                                                     const double *ppart, int npart, double *res, double *prev,
-                                                     int *ctl, int max_sweeps, double tol) {
+__device__ void coeff_final_body(const ModelDev &M, const BteDev &B, const double *epart, const double *ppart,
+                                 int npart, double *res, double *prev, int *ctl, int max_sweeps, double tol) {
   // device-driven loop (ctl != nullptr): ctl[0] stop flag, ctl[1] sweeps done, ctl[2] converged
   if (ctl && ctl[0]) return;
   __shared__ double Ms[kNE + kNP];
@@ -497,7 +441,7 @@ __global__ void __launch_bounds__(512) k_coeff_final(ModelDev M, BteDev B, const
   for (int j = wid; j < kNE + kNP; j += nw) {
     double s = 0.0;
     for (int b = lane; b < npart; b += 32)
-      s += j < kNE ? epart[size_t(b) * kNE + j] : ppart[size_t(b) * kNP + (j - kNE)];
+      s += j < kNE ? __ldcg(epart + size_t(b) * kNE + j) : __ldcg(ppart + size_t(b) * kNP + (j - kNE));
     s = warp_sum(s);
     if (lane == 0) Ms[j] = s;
   }
@@ -569,6 +513,99 @@ __global__ void __launch_bounds__(512) k_coeff_final(ModelDev M, BteDev B, const
       if (conv || n >= max_sweeps) ctl[0] = 1;
     }
   }
+}
+
+// I = I0 + (self partials + drag term) / (f(1-f) W), same for J; plus the electron
+// coefficient partial sums of the new responses.
+__global__ void __launch_bounds__(kCT) k_e_finalize(BteDev B, SweepSegs S, const double *__restrict__ part,
+                                                    const double *__restrict__ Dterm, const double *__restrict__ I0,
+                                                    const double *__restrict__ J0, const double *__restrict__ inv_ffW,
+                                                    double *I_out, double *J_out, double *I_alt, double *J_alt,
+                                                    double2 *IJ_out, double2 *IJ_alt,
+                                                    const int *__restrict__ ctl, double *epart, ModelDev M,
+                                                    CoeffFuse F) {
+  if (ctl) {
+    if (ctl[0]) return;
+    if (ctl[1] & 1) {
+      I_out = I_alt;
+      J_out = J_alt;
+      IJ_out = IJ_alt;
+    }
+  }
+  double acc[kNE];
+  for (int j = 0; j < kNE; ++j) acc[j] = 0.0;
+  const int64_t stride = int64_t(gridDim.x) * kCT;
+  for (int64_t st = blockIdx.x * int64_t(kCT) + threadIdx.x; st < B.nst; st += stride) {
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t g = S.seg_ptr[st]; g < S.seg_ptr[st + 1]; ++g)
+      for (int c = 0; c < 6; ++c) s[c] += part[g * 6 + c];
+    if (Dterm)
+      for (int c = 0; c < 6; ++c) s[c] += Dterm[st * 6 + c];
+    const double c0 = inv_ffW[st];
+    double In[3], Jn[3];
+    for (int c = 0; c < 3; ++c) {
+      In[c] = I0[st * 3 + c] + s[c] * c0;
+      Jn[c] = J0[st * 3 + c] + s[3 + c] * c0;
+      I_out[st * 3 + c] = In[c];
+      J_out[st * 3 + c] = Jn[c];
+    }
+    if (IJ_out) {
+      double2 *p = IJ_out + st * 3;
+      p[0] = make_double2(In[0], In[1]);
+      p[1] = make_double2(In[2], Jn[0]);
+      p[2] = make_double2(Jn[1], Jn[2]);
+    }
+    e_tensor_acc(B, st, In, Jn, acc);
+  }
+  block_reduce_store(acc, kNE, epart + size_t(blockIdx.x) * kNE);
+  if (!F.counter) return;
+  // the last block to finish assembles the coefficients (and advances the sweep loop), so a
+  // sweep costs two launches instead of three
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(F.counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  coeff_final_body(M, B, epart, F.ppart, gridDim.x, F.res, F.prev, F.ctl, F.max_sweeps, F.tol);
+  if (threadIdx.x == 0) *F.counter = 0u;
+}
+
+__global__ void __launch_bounds__(kCT) k_e_partial(BteDev B, const double *I, const double *J, double *epart) {
+  double acc[kNE];
+  for (int j = 0; j < kNE; ++j) acc[j] = 0.0;
+  const int64_t stride = int64_t(gridDim.x) * kCT;
+  for (int64_t st = blockIdx.x * int64_t(kCT) + threadIdx.x; st < B.nst; st += stride)
+    e_tensor_acc(B, st, I + st * 3, J + st * 3, acc);
+  block_reduce_store(acc, kNE, epart + size_t(blockIdx.x) * kNE);
+}
+
+__global__ void __launch_bounds__(kCT) k_ph_partial(MeshDev D, BteDev B, const double *F, const double *G,
+                                                    double *ppart) {
+  double acc[kNP];
+  for (int j = 0; j < kNP; ++j) acc[j] = 0.0;
+  const int64_t stride = int64_t(gridDim.x) * kCT;
+  const double kT = kKbEVK * B.T;
+  for (int64_t t = blockIdx.x * int64_t(kCT) + threadIdx.x; t < B.nq * B.nbr; t += stride) {
+    double w = D.w[t];
+    if (!(w > D.omega_min)) continue;
+    double n = bose_b(w, kT);
+    double wt = w * n * (1.0 + n);
+    const double *v = D.vph + t * 3;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        acc[a * 3 + b] += -wt * v[a] * G[t * 3 + b];
+        acc[9 + a * 3 + b] += wt * v[a] * F[t * 3 + b];
+      }
+  }
+  block_reduce_store(acc, kNP, ppart + size_t(blockIdx.x) * kNP);
+}
+
+__global__ void __launch_bounds__(512) k_coeff_final(ModelDev M, BteDev B, const double *epart,
+                                                     const double *ppart, int npart, double *res, double *prev,
+                                                     int *ctl, int max_sweeps, double tol) {
+  coeff_final_body(M, B, epart, ppart, npart, res, prev, ctl, max_sweeps, tol);
 }
 
 // Kelvin-Onsager step: B = sigmaS[I_drag], A = alpha_ph / T, lambda = <A,B>/<B,B>
@@ -723,7 +760,8 @@ cudaError_t launch_fill_runs(const BteDev &B, int64_t n_entries, int64_t nruns, 
 cudaError_t launch_self_sweep(const ModelDev &M, const BteDev &B, const SweepSegs &S, const uint32_t *run_col,
                               const double *run_w, const double *I0, const double *J0, const double *inv_ffW,
                               double *Ia, double *Ja, double *Ib, double *Jb, const double *Dterm, double *part,
-                              double *epart, const int *ctl, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
+                              double *epart, const int *ctl, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1,
+                              double2 *IJa, double2 *IJb, const CoeffFuse *fuse) {
   if (ev0) {
     cudaError_t e = cudaEventRecord(ev0, st);
     if (e != cudaSuccess) return e;
@@ -731,9 +769,11 @@ cudaError_t launch_self_sweep(const ModelDev &M, const BteDev &B, const SweepSeg
   if (S.nseg > 0) {
     const unsigned grid = unsigned((S.nseg * 32 + 255) / 256);
     if (M.nsym > 1)
-      EPHB_LAUNCH(k_self_sweep_seg<true>, grid, 256, 0, st, M, S, run_col, run_w, Ia, Ja, Ib, Jb, ctl, part);
+      EPHB_LAUNCH(k_self_sweep_seg<true>, grid, 256, 0, st, M, S, run_col, run_w, Ia, Ja, Ib, Jb, IJa, IJb, ctl,
+                  part);
     else
-      EPHB_LAUNCH(k_self_sweep_seg<false>, grid, 256, 0, st, M, S, run_col, run_w, Ia, Ja, Ib, Jb, ctl, part);
+      EPHB_LAUNCH(k_self_sweep_seg<false>, grid, 256, 0, st, M, S, run_col, run_w, Ia, Ja, Ib, Jb, IJa, IJb, ctl,
+                  part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -741,7 +781,8 @@ cudaError_t launch_self_sweep(const ModelDev &M, const BteDev &B, const SweepSeg
     cudaError_t e = cudaEventRecord(ev1, st);
     if (e != cudaSuccess) return e;
   }
-  EPHB_LAUNCH(k_e_finalize, kNPart, kCT, 0, st, B, S, part, Dterm, I0, J0, inv_ffW, Ib, Jb, Ia, Ja, ctl, epart);
+  EPHB_LAUNCH(k_e_finalize, kNPart, kCT, 0, st, B, S, part, Dterm, I0, J0, inv_ffW, Ib, Jb, Ia, Ja, IJb, IJa, ctl,
+              epart, M, fuse ? *fuse : CoeffFuse{});
   return cudaGetLastError();
 }
 
@@ -835,6 +876,23 @@ __global__ void k_to_f32(int64_t n, const double *a, float *b) {
 }
 
 }  // namespace
+
+namespace {
+__global__ void k_pack_ij(int64_t nst, const double *I, const double *J, double2 *IJ) {
+  const int64_t st = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (st >= nst) return;
+  double2 *p = IJ + st * 3;
+  p[0] = make_double2(I[st * 3], I[st * 3 + 1]);
+  p[1] = make_double2(I[st * 3 + 2], J[st * 3]);
+  p[2] = make_double2(J[st * 3 + 1], J[st * 3 + 2]);
+}
+}  // namespace
+
+cudaError_t launch_pack_ij(int64_t nst, const double *I, const double *J, double2 *IJ, cudaStream_t st) {
+  if (nst == 0) return cudaSuccess;
+  EPHB_LAUNCH(k_pack_ij, unsigned((nst + 255) / 256), 256, 0, st, nst, I, J, IJ);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_to_f32(int64_t n, const double *a, float *b, cudaStream_t st) {
   if (n == 0) return cudaSuccess;

@@ -194,6 +194,16 @@ cudaError_t launch_build_runs(const BteDev &B, int64_t n_entries, const int2 *ki
 cudaError_t launch_fill_runs(const BteDev &B, int64_t n_entries, int64_t nruns, const int2 *kinfo, const int *flag,
                              const int64_t *runidx, int64_t *run_ptr, uint32_t *run_col, double *run_w,
                              cudaStream_t st);
+// Coefficient assembly fused into the finalisation (its last block does what
+// launch_coeff_final does, with the same arguments); counter: a zeroed device word.
+struct CoeffFuse {
+  const double *ppart = nullptr;
+  double *res = nullptr, *prev = nullptr;
+  int *ctl = nullptr;
+  int max_sweeps = 0;
+  double tol = 0.0;
+  unsigned *counter = nullptr;
+};
 // One electron sweep (self term over the runs) and the per-row finalisation
 // I = I0 + (self + Dterm)/(f(1-f)W), which also writes the electron coefficient partials.
 // ctl == nullptr: reads (Ia, Ja), writes (Ib, Jb).  Otherwise the loop is driven on the device:
@@ -203,7 +213,12 @@ cudaError_t launch_self_sweep(const ModelDev &M, const BteDev &B, const SweepSeg
                               const double *run_w, const double *I0, const double *J0, const double *inv_ffW,
                               double *Ia, double *Ja, double *Ib, double *Jb, const double *Dterm, double *part,
                               double *epart, const int *ctl, cudaStream_t st, cudaEvent_t ev0 = nullptr,
-                              cudaEvent_t ev1 = nullptr);   // events around the self-term kernel
+                              cudaEvent_t ev1 = nullptr,    // events around the self-term kernel
+                              double2 *IJa = nullptr, double2 *IJb = nullptr, const CoeffFuse *fuse = nullptr);
+// Packed copy of the responses for the gathers: IJ[st] = (I0 I1 | I2 J0 | J1 J2) as 3 double2.
+// With IJa/IJb given the sweep gathers from them (by the same parity as Ia/Ib) and the
+// finalisation writes both layouts.
+cudaError_t launch_pack_ij(int64_t nst, const double *I, const double *J, double2 *IJ, cudaStream_t st);
 // Drag term of every row for the current F, G: Dterm[st][6].
 cudaError_t launch_drag_term(const MeshDev &D, const BteDev &B, const SweepSegs &S, const double *F, const double *G,
                              double *part, double *Dterm, cudaStream_t st);
