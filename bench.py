@@ -174,9 +174,11 @@ def measured_peaks():
 
 def profile_traffic(kernel_tag, source_file):
     """dram bytes per unit from a committed ncu summary, if it was taken on the current source."""
-    path = os.path.join(ROOT, "profiles", f"ncu_{kernel_tag}.txt")
-    if not os.path.exists(path):
+    import glob
+    paths = sorted(glob.glob(os.path.join(ROOT, "profiles", f"ncu_{kernel_tag}*.txt")))
+    if not paths:
         return None
+    path = paths[0]
     kv = {}
     for ln in open(path):
         if ":" in ln:

@@ -184,7 +184,9 @@ typedef struct {
   double rot_flops;            /* algorithmic flops of the band and branch rotations       */
   double ms_gemm;              /* tensor-core modes: device time of the tcgen05 GEMM kernel  */
   int tc_cols;                 /* tensor-core modes: column-chunk width used               */
-  int autotuned;               /* 1 if this call chose tc_cols by timing the candidates    */
+  int autotuned;               /* 1 if this call chose the tile shape by timing candidates */
+  int tc_kblock;               /* tensor-core modes: K per shared-memory stage (16: 2 CTAs/SM) */
+  int reserved;
 } ephb_rates_info;
 
 ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst, int ninst,
@@ -342,11 +344,13 @@ typedef enum {
   EPHB_ARR_COUNT = 22
 } ephb_array;
 
-/* Tuning.  EPHB_TUNE_TC_COLS: column-chunk width of the tensor-core contraction (the tile is
- * 128 (k,q) pairs x width columns).  0 (default): the first tensor-core rates call of a context
- * times the candidate widths (48/64/96 FP64-grade, 64/128/256 mixed) on its first chunk and
- * keeps the fastest for the context; setting 0 again re-tunes.  Otherwise the given width
- * (a multiple of 16, at most 96 / 256) is used.  The results do not depend on the width. */
+/* Tuning.  EPHB_TUNE_TC_COLS: tile shape of the tensor-core R_ph contraction (the tile is
+ * 128 (k,q) pairs x width columns, K streamed in stages of kblock).  0 (default): the first
+ * tensor-core rates call of a context times the candidate shapes on its first chunk (FP64-grade:
+ * widths 48/64/96 with K stages of 32 and one CTA per SM, width 48 with stages of 16 and two
+ * CTAs per SM; mixed: 64/128/256, and 128 with two CTAs per SM) and keeps the fastest for the
+ * context; setting 0 again re-tunes.  Otherwise the given width (a multiple of 16, at most
+ * 96 / 256) is used with stages of 32.  The results do not depend on the shape. */
 #define EPHB_TUNE_TC_COLS 0
 ephb_status ephb_set_tuning(ephb_ctx *ctx, int key, int value);
 

@@ -189,6 +189,7 @@ struct ephb_ctx : InstState {
   // tuning: column-chunk width of the tensor-core contraction (FP64-grade, mixed); 0 = not
   // tuned yet.  force_cols != 0 overrides the tuner.
   int tune_cols[2] = {0, 0};
+  int tune_kc[2] = {32, 32};
   int force_cols = 0;
   double *host_res = nullptr;   // pinned: kResLen doubles, then the sweep-loop control (4 ints)
 };
@@ -782,8 +783,7 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     }
     CK(ta.start(st));
     if (tensor_a) {
-      const int width_a = ctx->force_cols ? std::min(ctx->force_cols, tc_nc_max(ns_a))
-                                          : (ctx->tune_cols[0] ? ctx->tune_cols[0] : tc_nc_max(ns_a));
+      const int width_a = ctx->force_cols ? std::min(ctx->force_cols, tc_nc_max(ns_a)) : tc_nc_max(ns_a);
       CK(launch_stage_a_tc(M, D, ns_a, i0, nkc, ctx->phik.p, ctx->gslices.p, ctx->gscale.p, ctx->Tbuf.p,
                            ctx->tc_err.p, width_a, st, &tensor_flops_a));
       CK(launch_stage_a2(M, D, i0, nkc, ctx->Tbuf.p, ctx->Abuf.p, st));
@@ -797,31 +797,33 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
                               ctx->e_X.p, ctx->ph_st.p, ctx->ph_kpn.p, ctx->ph_Y.p, st));
       CK(tb.stop(st));
     } else {
-      auto contract = [&](cudaEvent_t e0, cudaEvent_t e1, int width) {
+      auto contract = [&](cudaEvent_t e0, cudaEvent_t e1, int width, int kc) {
         return launch_vertex_tc(M, D, ns, i0, nkc, hpp[i0], ctx->Abuf.p, ctx->phis.p, ctx->bslices.p,
                                 ctx->bscale.p, ctx->nitem.p, ctx->item_ptr.p, ctx->scratch.p, ctx->scratch.n,
-                                ctx->scal.p + 6, ctx->Cbuf.p, ctx->tc_err.p, st, e0, e1, width);
+                                ctx->scal.p + 6, ctx->Cbuf.p, ctx->tc_err.p, st, e0, e1, width, kc);
       };
       int &tuned = ctx->tune_cols[ns == 7 ? 0 : 1];
+      int &tuned_kc = ctx->tune_kc[ns == 7 ? 0 : 1];
       if (ncm == 0 && tuned == 0) {
-        // autotune on this chunk: time the GEMM at every candidate column-chunk width and keep
-        // the fastest (the contraction is the same for every width, so the last run stands)
+        // autotune on this chunk: time the GEMM at every candidate tile shape and keep the
+        // fastest (the contraction is the same for every shape, so the last run stands)
         float best = 3.4e38f;
-        for (int width : tc_nc_candidates(ns)) {
+        for (const TcShape &sh : tc_shape_candidates(ns)) {
           EventTimer tt;
           CK(tt.init());
-          CK(contract(tt.a, tt.b, width));
+          CK(contract(tt.a, tt.b, sh.width, sh.kc));
           tt.pending = true;
           CK(cudaStreamSynchronize(st));
           CK(tt.collect());
           if (tt.ms < best) {
             best = float(tt.ms);
-            tuned = width;
+            tuned = sh.width;
+            tuned_kc = sh.kc;
           }
         }
         autotuned = 1;
       } else {
-        CK(contract(tg.a, tg.b, ncm ? ncm : tuned));
+        CK(contract(tg.a, tg.b, ncm ? ncm : tuned, ncm ? 32 : tuned_kc));
         tg.pending = true;
       }
       CK(tb.stop(st));
@@ -876,6 +878,7 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     out->rot_flops = double(cnt[4]);
     out->ms_gemm = tg.ms;
     out->tc_cols = tensor ? (ncm ? ncm : ctx->tune_cols[ns == 7 ? 0 : 1]) : 0;
+    out->tc_kblock = tensor ? (ncm ? 32 : ctx->tune_kc[ns == 7 ? 0 : 1]) : 0;
     out->autotuned = autotuned;
   }
   ctx->stage = 3;

@@ -114,7 +114,7 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
                              const double2 *A, const __nv_bfloat16 *phis, __nv_bfloat16 *bs, double *bscale,
                              int *nitem, int64_t *item_ptr, int64_t *scratch, int64_t scratch_elems,
                              int64_t *total_dev, double *Cbuf, int *err, cudaStream_t st, cudaEvent_t gemm0,
-                             cudaEvent_t gemm1, int ncm);
+                             cudaEvent_t gemm1, int ncm, int kc);
 // Stage A on tensor cores: T[kc][col] = sum_Re e^{ik.Re} g[Re][col] for the k of a chunk, as
 // the same exact-slice GEMM with the k phase slices as rows and the model's g slices (made
 // once by launch_g_slices, [ns][tc_ncols_a][tc_kp_a] BF16 + column scales) as B.
@@ -127,11 +127,14 @@ cudaError_t launch_stage_a_tc(const ModelDev &M, const MeshDev &D, int ns, int64
 // The band rotation of stage A: A[kc][rp][(m,n',a)] = sum_m' c_{m'm}(k) T[kc][rp][m'][n'][a].
 cudaError_t launch_stage_a2(const ModelDev &M, const MeshDev &D, int64_t i0, int64_t nkc, const double2 *T, double2 *A,
                             cudaStream_t st);
-// Column-chunk width of the contraction (its result does not depend on it: every column is
-// summed in the same order whatever the chunking).
+// Tile shape of the contraction: column-chunk width and K per shared-memory stage (16: two CTAs
+// per SM).  The result does not depend on it: every column is summed in the same order.
+struct TcShape {
+  int width, kc;
+};
 int tc_nc_max(int ns);
-bool tc_nc_valid(int ns, int ncm);
-std::vector<int> tc_nc_candidates(int ns);
+bool tc_nc_valid(int ns, int ncm, int kc);
+std::vector<TcShape> tc_shape_candidates(int ns);
 
 // ---- bte.cu
 struct BteDev {

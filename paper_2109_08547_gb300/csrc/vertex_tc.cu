@@ -227,9 +227,10 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
 
-// core-matrix offset (bytes) of element (row, k) in a [rows x kTcKc] K-major tile
+// core-matrix offset (bytes) of element (row, k) in a [rows x KC] K-major tile
+template <int KC>
 __device__ __forceinline__ uint32_t core_off(int row, int kgroup) {
-  return uint32_t(((row >> 3) * (kTcKc / 8) + kgroup) * 128 + (row & 7) * 16);
+  return uint32_t(((row >> 3) * (KC / 8) + kgroup) * 128 + (row & 7) * 16);
 }
 
 // Rows of a contraction: (k,q) pairs of each k (stage B: A rows are the phase slices of the
@@ -243,8 +244,10 @@ struct TcParams {
   int ncols, out_stride;            // stage A: live columns and the output row stride (doubles)
 };
 
-template <int NS, int NACC, int ROWS>
-__global__ void __launch_bounds__(kTcThreads, 1) k_vertex_gemm(ModelDev M, MeshDev D, TcParams P,
+// KC: K per shared-memory stage (32: one CTA per SM; 16: two CTAs per SM share the SM's
+// shared memory and tensor memory, one's epilogue overlapping the other's products).
+template <int NS, int NACC, int ROWS, int KC>
+__global__ void __launch_bounds__(kTcThreads, KC == 16 ? 2 : 1) k_vertex_gemm(ModelDev M, MeshDev D, TcParams P,
                                                                const int64_t *__restrict__ item_ptr,
                                                                const __nv_bfloat16 *__restrict__ phis,
                                                                const __nv_bfloat16 *__restrict__ bs,
@@ -302,7 +305,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vertex_gemm(ModelDev M, MeshD
   }
 
   // two shared-memory stages, each NS x [128 x Kc] (A) followed by NS x [nc_max x Kc] (B)
-  const size_t a_slice = size_t(kTcM) * kTcKc * 2, b_slice = size_t(P.nc_max) * kTcKc * 2;
+  const size_t a_slice = size_t(kTcM) * KC * 2, b_slice = size_t(P.nc_max) * KC * 2;
   const size_t stage_bytes = size_t(NS) * (a_slice + b_slice);
 
   if (tid == 0) {
@@ -330,13 +333,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vertex_gemm(ModelDev M, MeshD
     unsigned char *sA = smem + buf * stage_bytes;
     unsigned char *sB = sA + NS * a_slice;
     for (int s = 0; s < NS; ++s)
-      for (int g = 0; g < kTcKc / 8; ++g)
-        cp_async16(smem_u32(sA + s * a_slice + core_off(tid, g)), arow + size_t(s) * P.Kp + kb + g * 8, abytes);
-    for (int t = tid; t < NS * ncw * (kTcKc / 8); t += kTcThreads) {
-      const int s = t / (ncw * (kTcKc / 8));
-      const int rem = t % (ncw * (kTcKc / 8));
-      const int row = rem / (kTcKc / 8), g = rem % (kTcKc / 8);
-      cp_async16(smem_u32(sB + s * b_slice + core_off(row, g)),
+      for (int g = 0; g < KC / 8; ++g)
+        cp_async16(smem_u32(sA + s * a_slice + core_off<KC>(tid, g)), arow + size_t(s) * P.Kp + kb + g * 8, abytes);
+    for (int t = tid; t < NS * ncw * (KC / 8); t += kTcThreads) {
+      const int s = t / (ncw * (KC / 8));
+      const int rem = t % (ncw * (KC / 8));
+      const int row = rem / (KC / 8), g = rem % (KC / 8);
+      cp_async16(smem_u32(sB + s * b_slice + core_off<KC>(row, g)),
                  bsk + (size_t(s) * P.Nmax + n0 + row) * P.Kp + kb + g * 8, 16u);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -345,7 +348,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vertex_gemm(ModelDev M, MeshD
   // Pipeline: the MMAs of block b are issued as soon as its operands have landed; the copies
   // of block b + 1 go into the other stage once the MMAs of block b - 1 (its last readers)
   // have completed, so they overlap the MMAs of block b.
-  const int nkb = P.Kp / kTcKc;
+  const int nkb = P.Kp / KC;
   bool ok = true;
   int issued = -1;    // last K block whose MMAs were committed
   stage_load(0, 0);
@@ -363,9 +366,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vertex_gemm(ModelDev M, MeshD
           const int d = is + ls;
           const int acc = NACC == 1 ? 0 : (d < NACC - 1 ? d : NACC - 1);
           const uint32_t dtm = taddr + uint32_t(acc * nc);
-          for (int ks = 0; ks < kTcKc / 16; ++ks) {
-            const uint64_t ad = smem_desc(smem_u32(sA + is * a_slice) + ks * 256, 128u, (kTcKc / 8) * 128u);
-            const uint64_t bd = smem_desc(smem_u32(sB + ls * b_slice) + ks * 256, 128u, (kTcKc / 8) * 128u);
+          for (int ks = 0; ks < KC / 16; ++ks) {
+            const uint64_t ad = smem_desc(smem_u32(sA + is * a_slice) + ks * 256, 128u, (KC / 8) * 128u);
+            const uint64_t bd = smem_desc(smem_u32(sB + ls * b_slice) + ks * 256, 128u, (KC / 8) * 128u);
             // the first product into each accumulator (first K block, first K step) overwrites it
             const bool first = b == 0 && ks == 0 &&
                                (NACC == 1 ? (is == 0 && ls == 0) :
@@ -387,7 +390,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vertex_gemm(ModelDev M, MeshD
         const bool waited = mbar_wait(smem_u32(&mbar[buf ^ 1]), uint32_t(((b - 1) >> 1) & 1));
         ok = __syncthreads_and(waited ? 1 : 0) != 0;
       }
-      if (ok) stage_load(buf ^ 1, (b + 1) * kTcKc);
+      if (ok) stage_load(buf ^ 1, (b + 1) * KC);
     }
   }
   // the last commit tracks every MMA issued before it (after a timeout: the bounded second wait)
@@ -439,14 +442,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vertex_gemm(ModelDev M, MeshD
 
 int tc_kp(const ModelDev &M) { return round_up(2 * M.nRgp, kTcKc); }
 int tc_nmax(const ModelDev &M) { return round_up(2 * M.nb * M.nb * M.nbr, 16); }
-// Column-chunk widths a launch may use: every accumulator of a chunk must fit the 512 TMEM
-// columns (NACC x width) and two operand stages the shared memory.
+// Tile shapes a launch may use.  Every accumulator of a chunk must fit the CTA's tensor memory
+// (NACC x width columns: all 512 with one CTA per SM, 256 with two) and two operand stages its
+// shared memory.
 int tc_nc_max(int ns) { return ns == 7 ? 96 : 256; }
-bool tc_nc_valid(int ns, int ncm) { return ncm >= 16 && ncm % 16 == 0 && ncm <= tc_nc_max(ns); }
-std::vector<int> tc_nc_candidates(int ns) {
-  return ns == 7 ? std::vector<int>{48, 64, 96} : std::vector<int>{64, 128, 256};
+static int nacc_of(int ns) { return ns == 7 ? 5 : 2; }
+bool tc_nc_valid(int ns, int ncm, int kc) {
+  if (ncm < 16 || ncm % 16 != 0 || ncm > tc_nc_max(ns) || (kc != 16 && kc != 32)) return false;
+  return kc == 32 || nacc_of(ns) * ncm <= 256;
 }
-size_t tc_smem_bytes(int ns, int ncm) { return 2 * (size_t(ns) * kTcM * kTcKc * 2 + size_t(ns) * ncm * kTcKc * 2); }
+std::vector<TcShape> tc_shape_candidates(int ns) {
+  if (ns == 7) return {{48, 32}, {64, 32}, {96, 32}, {48, 16}};
+  return {{64, 32}, {128, 32}, {256, 32}, {128, 16}};
+}
+size_t tc_smem_bytes(int ns, int ncm, int kc) {
+  const size_t need = 2 * (size_t(ns) * kTcM * kc * 2 + size_t(ns) * ncm * kc * 2);
+  // two-CTA shapes ask for at least 96 KB so that no third CTA (whose tensor memory would not
+  // fit) is placed on the SM
+  return kc == 16 && need < 96 * 1024 ? 96 * 1024 : need;
+}
 
 int tc_kp_a(const ModelDev &M) { return round_up(2 * M.nRge, kTcKc); }
 int tc_ncols_a(const ModelDev &M) { return round_up(2 * M.nRgp * M.nb * M.nb * M.nbr, 16); }
@@ -462,7 +476,7 @@ cudaError_t launch_stage_a_tc(const ModelDev &M, const MeshDev &D, int ns, int64
                               __nv_bfloat16 *phik, const __nv_bfloat16 *gs, const double *gscale, double2 *T, int *err,
                               int ncm, cudaStream_t st, double *flops_acc) {
   if (nkc <= 0) return cudaSuccess;
-  if (!tc_nc_valid(ns, ncm)) return cudaErrorInvalidValue;
+  if (!tc_nc_valid(ns, ncm, 32)) return cudaErrorInvalidValue;
   const int Kp = tc_kp_a(M), Ncols = tc_ncols_a(M);
   const int64_t n = nkc * int64_t(Kp);
   EPHB_LAUNCH(k_phase_slices_k, unsigned((n + 255) / 256), 256, 0, st, M, D, i0, nkc, ns, Kp, phik);
@@ -482,17 +496,17 @@ cudaError_t launch_stage_a_tc(const ModelDev &M, const MeshDev &D, int ns, int64
   const int nch = (Ncols + ncm - 1) / ncm;
   const int64_t ntile = (nkc + kTcM - 1) / kTcM;
   const int64_t nitems = ntile * nch;
-  const size_t smem = tc_smem_bytes(ns, ncm);
+  const size_t smem = tc_smem_bytes(ns, ncm, 32);
   double *out = reinterpret_cast<double *>(T);
   if (ns == 7) {
-    e = cudaFuncSetAttribute(k_vertex_gemm<7, 5, kRowsK>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    e = cudaFuncSetAttribute(k_vertex_gemm<7, 5, kRowsK, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    EPHB_LAUNCH((k_vertex_gemm<7, 5, kRowsK>), unsigned(nitems), kTcThreads, smem, st, M, D, P, nullptr, phik, gs,
+    EPHB_LAUNCH((k_vertex_gemm<7, 5, kRowsK, 32>), unsigned(nitems), kTcThreads, smem, st, M, D, P, nullptr, phik, gs,
                 gscale, out, err);
   } else {
-    e = cudaFuncSetAttribute(k_vertex_gemm<3, 2, kRowsK>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    e = cudaFuncSetAttribute(k_vertex_gemm<3, 2, kRowsK, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    EPHB_LAUNCH((k_vertex_gemm<3, 2, kRowsK>), unsigned(nitems), kTcThreads, smem, st, M, D, P, nullptr, phik, gs,
+    EPHB_LAUNCH((k_vertex_gemm<3, 2, kRowsK, 32>), unsigned(nitems), kTcThreads, smem, st, M, D, P, nullptr, phik, gs,
                 gscale, out, err);
   }
   e = cudaGetLastError();
@@ -512,9 +526,9 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
                              const double2 *A, const __nv_bfloat16 *phis, __nv_bfloat16 *bs, double *bscale,
                              int *nitem, int64_t *item_ptr, int64_t *scratch, int64_t scratch_elems,
                              int64_t *total_dev, double *Cbuf, int *err, cudaStream_t st, cudaEvent_t gemm0,
-                             cudaEvent_t gemm1, int ncm) {
+                             cudaEvent_t gemm1, int ncm, int kc) {
   if (nkc <= 0) return cudaSuccess;
-  if (!tc_nc_valid(ns, ncm)) return cudaErrorInvalidValue;
+  if (!tc_nc_valid(ns, ncm, kc)) return cudaErrorInvalidValue;
   const int Kp = tc_kp(M), Nmax = tc_nmax(M);
   const int64_t nw = nkc * Nmax;
   EPHB_LAUNCH(k_b_slices, unsigned((nw * 32 + 255) / 256), 256, 0, st, M, D, i0, nkc, A, ns, Kp, Nmax, bs, bscale);
@@ -538,22 +552,22 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
   P.pair_base = pair_base;
   P.ncols = Nmax;
   P.out_stride = Nmax;
-  const size_t smem = tc_smem_bytes(ns, ncm);
+  const size_t smem = tc_smem_bytes(ns, ncm, kc);
   if (gemm0) {
     e = cudaEventRecord(gemm0, st);
     if (e != cudaSuccess) return e;
   }
-  if (ns == 7) {
-    e = cudaFuncSetAttribute(k_vertex_gemm<7, 5, kRowsPairs>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    EPHB_LAUNCH((k_vertex_gemm<7, 5, kRowsPairs>), unsigned(nitems), kTcThreads, smem, st, M, D, P, item_ptr, phis, bs, bscale,
-                Cbuf, err);
-  } else {
-    e = cudaFuncSetAttribute(k_vertex_gemm<3, 2, kRowsPairs>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    EPHB_LAUNCH((k_vertex_gemm<3, 2, kRowsPairs>), unsigned(nitems), kTcThreads, smem, st, M, D, P, item_ptr, phis, bs, bscale,
-                Cbuf, err);
-  }
+  auto go = [&](auto kern) -> cudaError_t {
+    cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (r != cudaSuccess) return r;
+    EPHB_LAUNCH(kern, unsigned(nitems), kTcThreads, smem, st, M, D, P, item_ptr, phis, bs, bscale, Cbuf, err);
+    return cudaGetLastError();
+  };
+  if (ns == 7)
+    e = kc == 16 ? go(k_vertex_gemm<7, 5, kRowsPairs, 16>) : go(k_vertex_gemm<7, 5, kRowsPairs, 32>);
+  else
+    e = kc == 16 ? go(k_vertex_gemm<3, 2, kRowsPairs, 16>) : go(k_vertex_gemm<3, 2, kRowsPairs, 32>);
+  if (e != cudaSuccess) return e;
   e = cudaGetLastError();
   if (e == cudaSuccess && gemm1) e = cudaEventRecord(gemm1, st);
   return e;
