@@ -105,6 +105,19 @@ def fp64_peak():
     print(json.dumps({k: float(v) for k, v in vals.items()}))
 
 
+def whole_job(seconds, units, world, device):
+    """Whole-job throughput of independent replicas: the units all ranks processed over the
+    slowest rank's time (max over ranks).  Returns (units_total, seconds_max, value)."""
+    import torch
+    import torch.distributed as dist
+    el_t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    un_t = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(el_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(un_t, op=dist.ReduceOp.SUM)
+    return float(un_t.item()), float(el_t.item()), float(un_t.item()) / float(el_t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -438,13 +451,7 @@ def main():
     el = time.perf_counter() - t0
     launches = B.kernel_launches() - l0
     clocks = sampler.stop()
-    el_t = torch.tensor([el], dtype=torch.float64, device=dev)
-    tup_t = torch.tensor([float(sum(r.rates["n_tuples"] for r in results))], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(el_t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tup_t, op=dist.ReduceOp.SUM)
-    el_max = float(el_t.item())
-    value = float(tup_t.item()) / el_max
+    _, el_max, value = whole_job(el, sum(r.rates["n_tuples"] for r in results), world, dev)
     r0 = results[-1]
 
     # dominant kernel and its roofline (device time measured with CUDA events in this run)
@@ -531,13 +538,9 @@ def main():
         torch.cuda.synchronize()
         barrier()
         el2 = time.perf_counter() - t1
-        e2_t = torch.tensor([el2], dtype=torch.float64, device=dev)
-        tu_t = torch.tensor([float(tup)], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(e2_t, op=dist.ReduceOp.MAX)
-            dist.all_reduce(tu_t, op=dist.ReduceOp.SUM)
-        e2e = {"value": float(tu_t.item()) / float(e2_t.item()), "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": 8 * 9 * 8, "s_per_step": float(e2_t.item()) / args.steps}
+        _, e2_max, e2_val = whole_job(el2, tup, world, dev)
+        e2e = {"value": e2_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 8 * 9 * 8, "s_per_step": e2_max / args.steps}
         ctx2.close()
 
     # one step of each other precision of the vertex contraction: time to converged
