@@ -35,6 +35,8 @@ FP64_PEAK_TFLOPS = 1.188  # lower of two measurements (1.188, 1.255)
 # arithmetic of the vertex contraction per precision mode (everything else is FP64)
 DTYPES = {"fp64": "f64", "fp64-sliced": "f64 (tcgen05 bf16 x7 exact fixed-point slices, f32 accumulate)",
           "split-bf16": "bf16 x3 slices, f32 accumulate (mixed)"}
+SOLVE_DTYPES = {"fp64": "; iteration f64",
+                "mixed": "; iteration f64 residual sweeps + f32 correction sweeps (same fixed point)"}
 
 
 def parse():
@@ -48,6 +50,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--precision", default="fp64-sliced", choices=["fp64", "fp64-sliced", "split-bf16"],
                    help="vertex contraction: FP64 CUDA cores, FP64-grade tensor-core slices, or mixed precision")
+    p.add_argument("--solve", default="mixed", choices=["fp64", "mixed"],
+                   help="electron loop: plain FP64 sweeps, or FP64 residual sweeps with FP32 corrections "
+                        "(same fixed point)")
     p.add_argument("--no-variants", action="store_true", help="skip the one-step timings of the other precisions")
     p.add_argument("--instances", type=int, default=8,
                    help="(T, mu, window) instances of the batched-vs-sequential comparison (0: skip it)")
@@ -424,7 +429,7 @@ def main():
 
     prec = B.PRECISIONS[args.precision]
 
-    def step(p=prec, sp="fp64"):
+    def step(p=prec, sp=args.solve):
         return B.run_path(ctx, wl, level="dragged", ko_correction=True, precision=p, solve_precision=sp)
 
     for _ in range(args.warmup):
@@ -533,7 +538,8 @@ def main():
         for _ in range(args.steps):
             flush.zero_()
             B.set_wannier_model(ctx2, mp)
-            rr = B.run_path(ctx2, wl, level="dragged", ko_correction=True, precision=prec)
+            rr = B.run_path(ctx2, wl, level="dragged", ko_correction=True, precision=prec,
+                            solve_precision=args.solve)
             tup += rr.rates["n_tuples"]
         torch.cuda.synchronize()
         barrier()
@@ -548,8 +554,8 @@ def main():
     # result (which itself matches the FP64 oracle to 1e-8 in the parity tests)
     variants = {}
     if not args.no_variants:
-        cases = [(name, p, "fp64") for name, p in B.PRECISIONS.items() if name != args.precision]
-        cases += [(f"{args.precision}+mixed-solve", prec, "mixed"), ("split-bf16+mixed-solve", B.SPLIT_BF16, "mixed")]
+        cases = [(f"{name}+{sp}-solve", p, sp) for name, p in B.PRECISIONS.items() for sp in ("fp64", "mixed")
+                 if (name, sp) != (args.precision, args.solve)]
         for name, p, sp in cases:
             flush.zero_()
             step(p, sp)                   # warm-up of this mode
@@ -583,11 +589,11 @@ def main():
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision] + SOLVE_DTYPES[args.solve], "data": "synthetic",
             "config": {"workload": wl.name, "model": "4-band/6-branch CsCl-type cubic, 5^3 x 5^3 R grids (g 24 MB)",
                        "kmesh": list(wl.kmesh), "qmesh": list(wl.qmesh), "T_K": wl.T_K, "mu_eV": wl.mu_eV,
                        "window_eV": list(wl.window), "sigma_eV": wl.sigma_eV, "level": "dragged+KO",
-                       "tol": wl.tol, "precision": args.precision, "l2": "256 MB buffer written before every step",
+                       "tol": wl.tol, "precision": args.precision, "solve": args.solve, "l2": "256 MB buffer written before every step",
                        "parallelism": f"replicas x{world}", "tuples_per_step": r0.rates["n_tuples"],
                        "entries": r0.rates["n_entries"], "pairs": r0.rates["n_pairs"]},
             "s_to_converged": 1e-3 * el_max / args.steps,
