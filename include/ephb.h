@@ -185,8 +185,8 @@ typedef struct {
   double ms_gemm;              /* tensor-core modes: device time of the tcgen05 GEMM kernel  */
   int tc_cols;                 /* tensor-core modes: column-chunk width used               */
   int autotuned;               /* 1 if this call chose the tile shape by timing candidates */
-  int tc_kblock;               /* tensor-core modes: K per shared-memory stage (16: 2 CTAs/SM) */
-  int reserved;
+  int tc_kblock;               /* tensor-core modes: K per shared-memory stage             */
+  int tc_stages;               /* tensor-core modes: shared-memory stages (K16 x 2: 2 CTAs/SM) */
 } ephb_rates_info;
 
 ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst, int ninst,
@@ -347,8 +347,9 @@ typedef enum {
 /* Tuning.  EPHB_TUNE_TC_COLS: tile shape of the tensor-core R_ph contraction (the tile is
  * 128 (k,q) pairs x width columns, K streamed in stages of kblock).  0 (default): the first
  * tensor-core rates call of a context times the candidate shapes on its first chunk (FP64-grade:
- * widths 48/64/96 with K stages of 32 and one CTA per SM, width 48 with stages of 16 and two
- * CTAs per SM; mixed: 64/128/256, and 128 with two CTAs per SM) and keeps the fastest for the
+ * widths 48/64/96 with two K stages of 32 and one CTA per SM, width 48 with two stages of 16
+ * and two CTAs per SM, width 96 with four stages of 16; mixed: 64/128/256, 128 with two CTAs
+ * per SM, 256 with four stages) and keeps the fastest for the
  * context; setting 0 again re-tunes.  Otherwise the given width (a multiple of 16, at most
  * 96 / 256) is used with stages of 32.  The results do not depend on the shape. */
 #define EPHB_TUNE_TC_COLS 0

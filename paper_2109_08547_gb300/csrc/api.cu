@@ -190,6 +190,7 @@ struct ephb_ctx : InstState {
   // tuned yet.  force_cols != 0 overrides the tuner.
   int tune_cols[2] = {0, 0};
   int tune_kc[2] = {32, 32};
+  int tune_st[2] = {2, 2};
   int force_cols = 0;
   double *host_res = nullptr;   // pinned: kResLen doubles, then the sweep-loop control (4 ints)
 };
@@ -797,13 +798,14 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
                               ctx->e_X.p, ctx->ph_st.p, ctx->ph_kpn.p, ctx->ph_Y.p, st));
       CK(tb.stop(st));
     } else {
-      auto contract = [&](cudaEvent_t e0, cudaEvent_t e1, int width, int kc) {
+      auto contract = [&](cudaEvent_t e0, cudaEvent_t e1, int width, int kc, int stages) {
         return launch_vertex_tc(M, D, ns, i0, nkc, hpp[i0], ctx->Abuf.p, ctx->phis.p, ctx->bslices.p,
                                 ctx->bscale.p, ctx->nitem.p, ctx->item_ptr.p, ctx->scratch.p, ctx->scratch.n,
-                                ctx->scal.p + 6, ctx->Cbuf.p, ctx->tc_err.p, st, e0, e1, width, kc);
+                                ctx->scal.p + 6, ctx->Cbuf.p, ctx->tc_err.p, st, e0, e1, width, kc, stages);
       };
       int &tuned = ctx->tune_cols[ns == 7 ? 0 : 1];
       int &tuned_kc = ctx->tune_kc[ns == 7 ? 0 : 1];
+      int &tuned_st = ctx->tune_st[ns == 7 ? 0 : 1];
       if (ncm == 0 && tuned == 0) {
         // autotune on this chunk: time the GEMM at every candidate tile shape and keep the
         // fastest (the contraction is the same for every shape, so the last run stands)
@@ -811,7 +813,7 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
         for (const TcShape &sh : tc_shape_candidates(ns)) {
           EventTimer tt;
           CK(tt.init());
-          CK(contract(tt.a, tt.b, sh.width, sh.kc));
+          CK(contract(tt.a, tt.b, sh.width, sh.kc, sh.stages));
           tt.pending = true;
           CK(cudaStreamSynchronize(st));
           CK(tt.collect());
@@ -819,11 +821,12 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
             best = float(tt.ms);
             tuned = sh.width;
             tuned_kc = sh.kc;
+            tuned_st = sh.stages;
           }
         }
         autotuned = 1;
       } else {
-        CK(contract(tg.a, tg.b, ncm ? ncm : tuned, ncm ? 32 : tuned_kc));
+        CK(contract(tg.a, tg.b, ncm ? ncm : tuned, ncm ? 32 : tuned_kc, ncm ? 2 : tuned_st));
         tg.pending = true;
       }
       CK(tb.stop(st));
@@ -879,6 +882,7 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     out->ms_gemm = tg.ms;
     out->tc_cols = tensor ? (ncm ? ncm : ctx->tune_cols[ns == 7 ? 0 : 1]) : 0;
     out->tc_kblock = tensor ? (ncm ? 32 : ctx->tune_kc[ns == 7 ? 0 : 1]) : 0;
+    out->tc_stages = tensor ? (ncm ? 2 : ctx->tune_st[ns == 7 ? 0 : 1]) : 0;
     out->autotuned = autotuned;
   }
   ctx->stage = 3;

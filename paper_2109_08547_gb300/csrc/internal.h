@@ -114,7 +114,7 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
                              const double2 *A, const __nv_bfloat16 *phis, __nv_bfloat16 *bs, double *bscale,
                              int *nitem, int64_t *item_ptr, int64_t *scratch, int64_t scratch_elems,
                              int64_t *total_dev, double *Cbuf, int *err, cudaStream_t st, cudaEvent_t gemm0,
-                             cudaEvent_t gemm1, int ncm, int kc);
+                             cudaEvent_t gemm1, int ncm, int kc, int stages);
 // Stage A on tensor cores: T[kc][col] = sum_Re e^{ik.Re} g[Re][col] for the k of a chunk, as
 // the same exact-slice GEMM with the k phase slices as rows and the model's g slices (made
 // once by launch_g_slices, [ns][tc_ncols_a][tc_kp_a] BF16 + column scales) as B.
@@ -130,10 +130,10 @@ cudaError_t launch_stage_a2(const ModelDev &M, const MeshDev &D, int64_t i0, int
 // Tile shape of the contraction: column-chunk width and K per shared-memory stage (16: two CTAs
 // per SM).  The result does not depend on it: every column is summed in the same order.
 struct TcShape {
-  int width, kc;
+  int width, kc, stages;
 };
 int tc_nc_max(int ns);
-bool tc_nc_valid(int ns, int ncm, int kc);
+bool tc_nc_valid(int ns, int ncm, int kc, int stages);
 std::vector<TcShape> tc_shape_candidates(int ns);
 
 // ---- bte.cu

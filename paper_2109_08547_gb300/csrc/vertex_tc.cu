@@ -246,15 +246,16 @@ struct TcParams {
 
 // KC: K per shared-memory stage (32: one CTA per SM; 16: two CTAs per SM share the SM's
 // shared memory and tensor memory, one's epilogue overlapping the other's products).
-template <int NS, int NACC, int ROWS, int KC>
-__global__ void __launch_bounds__(kTcThreads, KC == 16 ? 2 : 1) k_vertex_gemm(ModelDev M, MeshDev D, TcParams P,
+// ST: shared-memory stages (copies run up to ST - 1 K blocks ahead of the MMAs).
+template <int NS, int NACC, int ROWS, int KC, int ST>
+__global__ void __launch_bounds__(kTcThreads, (KC == 16 && ST == 2) ? 2 : 1) k_vertex_gemm(ModelDev M, MeshDev D, TcParams P,
                                                                const int64_t *__restrict__ item_ptr,
                                                                const __nv_bfloat16 *__restrict__ phis,
                                                                const __nv_bfloat16 *__restrict__ bs,
                                                                const double *__restrict__ bscale, double *Cbuf,
                                                                int *err) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t mbar[ST];
   __shared__ uint32_t tslot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // once a CTA has recorded a timeout the remaining ones return without waiting in turn
@@ -304,13 +305,12 @@ __global__ void __launch_bounds__(kTcThreads, KC == 16 ? 2 : 1) k_vertex_gemm(Mo
     crow = Cbuf + (t0 + tid) * P.out_stride + n0;
   }
 
-  // two shared-memory stages, each NS x [128 x Kc] (A) followed by NS x [nc_max x Kc] (B)
+  // ST shared-memory stages, each NS x [128 x KC] (A) followed by NS x [nc_max x KC] (B)
   const size_t a_slice = size_t(kTcM) * KC * 2, b_slice = size_t(P.nc_max) * KC * 2;
   const size_t stage_bytes = size_t(NS) * (a_slice + b_slice);
 
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[1])));
+    for (int i = 0; i < ST; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[i])));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   const uint32_t ncols_alloc = NACC * nc <= 32 ? 32u : (NACC * nc <= 64 ? 64u : (NACC * nc <= 128 ? 128u :
@@ -346,15 +346,19 @@ __global__ void __launch_bounds__(kTcThreads, KC == 16 ? 2 : 1) k_vertex_gemm(Mo
   };
 
   // Pipeline: the MMAs of block b are issued as soon as its operands have landed; the copies
-  // of block b + 1 go into the other stage once the MMAs of block b - 1 (its last readers)
-  // have completed, so they overlap the MMAs of block b.
+  // of block b + ST - 1 go into the stage of block b - 1 once the MMAs of block b - 1 (its last
+  // readers) have completed, so up to ST - 1 blocks of copies overlap the MMAs.
   const int nkb = P.Kp / KC;
   bool ok = true;
   int issued = -1;    // last K block whose MMAs were committed
-  stage_load(0, 0);
+  for (int p = 0; p < ST - 1 && p < nkb; ++p) stage_load(p, p * KC);
   for (int b = 0; b < nkb && ok; ++b) {
-    const int buf = b & 1;
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    const int buf = b % ST;
+    // block b's copies have landed once at most min(ST - 2, nkb - 1 - b) later groups are pending
+    const int later = (nkb - 1 - b) < (ST - 2) ? (nkb - 1 - b) : (ST - 2);
+    if (later >= 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
+    else if (later == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
@@ -383,19 +387,20 @@ __global__ void __launch_bounds__(kTcThreads, KC == 16 ? 2 : 1) k_vertex_gemm(Mo
                    :: "r"(smem_u32(&mbar[buf])) : "memory");
     }
     issued = b;
-    if (b + 1 < nkb) {
+    const int nb = b + ST - 1;   // next block to copy, into the stage of block b - 1
+    if (nb < nkb) {
       if (b >= 1) {
-        // stage buf ^ 1 was read by the MMAs of block b - 1 (use (b - 1) / 2 of its barrier);
-        // the block agrees on the outcome, so a timeout leaves the loop on every thread together
-        const bool waited = mbar_wait(smem_u32(&mbar[buf ^ 1]), uint32_t(((b - 1) >> 1) & 1));
+        // use (b - 1) / ST of that stage's barrier; the block agrees on the outcome, so a
+        // timeout leaves the loop on every thread together
+        const bool waited = mbar_wait(smem_u32(&mbar[(b - 1) % ST]), uint32_t(((b - 1) / ST) & 1));
         ok = __syncthreads_and(waited ? 1 : 0) != 0;
       }
-      if (ok) stage_load(buf ^ 1, (b + 1) * KC);
+      if (ok) stage_load(nb % ST, nb * KC);
     }
   }
   // the last commit tracks every MMA issued before it (after a timeout: the bounded second wait)
   {
-    const bool waited = mbar_wait(smem_u32(&mbar[issued & 1]), uint32_t((issued >> 1) & 1));
+    const bool waited = mbar_wait(smem_u32(&mbar[issued % ST]), uint32_t((issued / ST) & 1));
     if (!__syncthreads_and(waited ? 1 : 0)) ok = false;
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -443,23 +448,26 @@ __global__ void __launch_bounds__(kTcThreads, KC == 16 ? 2 : 1) k_vertex_gemm(Mo
 int tc_kp(const ModelDev &M) { return round_up(2 * M.nRgp, kTcKc); }
 int tc_nmax(const ModelDev &M) { return round_up(2 * M.nb * M.nb * M.nbr, 16); }
 // Tile shapes a launch may use.  Every accumulator of a chunk must fit the CTA's tensor memory
-// (NACC x width columns: all 512 with one CTA per SM, 256 with two) and two operand stages its
-// shared memory.
+// (NACC x width columns: all 512 with one CTA per SM, 256 with two) and the operand stages its
+// shared memory.  Two CTAs per SM: K blocks of 16 in two stages.
 int tc_nc_max(int ns) { return ns == 7 ? 96 : 256; }
 static int nacc_of(int ns) { return ns == 7 ? 5 : 2; }
-bool tc_nc_valid(int ns, int ncm, int kc) {
-  if (ncm < 16 || ncm % 16 != 0 || ncm > tc_nc_max(ns) || (kc != 16 && kc != 32)) return false;
-  return kc == 32 || nacc_of(ns) * ncm <= 256;
-}
-std::vector<TcShape> tc_shape_candidates(int ns) {
-  if (ns == 7) return {{48, 32}, {64, 32}, {96, 32}, {48, 16}};
-  return {{64, 32}, {128, 32}, {256, 32}, {128, 16}};
-}
-size_t tc_smem_bytes(int ns, int ncm, int kc) {
-  const size_t need = 2 * (size_t(ns) * kTcM * kc * 2 + size_t(ns) * ncm * kc * 2);
+static bool two_ctas(int kc, int st) { return kc == 16 && st == 2; }
+size_t tc_smem_bytes(int ns, int ncm, int kc, int st) {
+  const size_t need = size_t(st) * (size_t(ns) * kTcM * kc * 2 + size_t(ns) * ncm * kc * 2);
   // two-CTA shapes ask for at least 96 KB so that no third CTA (whose tensor memory would not
   // fit) is placed on the SM
-  return kc == 16 && need < 96 * 1024 ? 96 * 1024 : need;
+  return two_ctas(kc, st) && need < 96 * 1024 ? 96 * 1024 : need;
+}
+bool tc_nc_valid(int ns, int ncm, int kc, int st) {
+  if (ncm < 16 || ncm % 16 != 0 || ncm > tc_nc_max(ns)) return false;
+  if (!((kc == 32 && st == 2) || (kc == 16 && (st == 2 || st == 4)))) return false;
+  if (tc_smem_bytes(ns, ncm, kc, st) > 200 * 1024 + 1024) return false;
+  return !two_ctas(kc, st) || nacc_of(ns) * ncm <= 256;
+}
+std::vector<TcShape> tc_shape_candidates(int ns) {
+  if (ns == 7) return {{48, 32, 2}, {64, 32, 2}, {96, 32, 2}, {48, 16, 2}, {96, 16, 4}};
+  return {{64, 32, 2}, {128, 32, 2}, {256, 32, 2}, {128, 16, 2}, {256, 16, 4}};
 }
 
 int tc_kp_a(const ModelDev &M) { return round_up(2 * M.nRge, kTcKc); }
@@ -476,7 +484,7 @@ cudaError_t launch_stage_a_tc(const ModelDev &M, const MeshDev &D, int ns, int64
                               __nv_bfloat16 *phik, const __nv_bfloat16 *gs, const double *gscale, double2 *T, int *err,
                               int ncm, cudaStream_t st, double *flops_acc) {
   if (nkc <= 0) return cudaSuccess;
-  if (!tc_nc_valid(ns, ncm, 32)) return cudaErrorInvalidValue;
+  if (!tc_nc_valid(ns, ncm, 32, 2)) return cudaErrorInvalidValue;
   const int Kp = tc_kp_a(M), Ncols = tc_ncols_a(M);
   const int64_t n = nkc * int64_t(Kp);
   EPHB_LAUNCH(k_phase_slices_k, unsigned((n + 255) / 256), 256, 0, st, M, D, i0, nkc, ns, Kp, phik);
@@ -496,17 +504,17 @@ cudaError_t launch_stage_a_tc(const ModelDev &M, const MeshDev &D, int ns, int64
   const int nch = (Ncols + ncm - 1) / ncm;
   const int64_t ntile = (nkc + kTcM - 1) / kTcM;
   const int64_t nitems = ntile * nch;
-  const size_t smem = tc_smem_bytes(ns, ncm, 32);
+  const size_t smem = tc_smem_bytes(ns, ncm, 32, 2);
   double *out = reinterpret_cast<double *>(T);
   if (ns == 7) {
-    e = cudaFuncSetAttribute(k_vertex_gemm<7, 5, kRowsK, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    e = cudaFuncSetAttribute(k_vertex_gemm<7, 5, kRowsK, 32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    EPHB_LAUNCH((k_vertex_gemm<7, 5, kRowsK, 32>), unsigned(nitems), kTcThreads, smem, st, M, D, P, nullptr, phik, gs,
+    EPHB_LAUNCH((k_vertex_gemm<7, 5, kRowsK, 32, 2>), unsigned(nitems), kTcThreads, smem, st, M, D, P, nullptr, phik, gs,
                 gscale, out, err);
   } else {
-    e = cudaFuncSetAttribute(k_vertex_gemm<3, 2, kRowsK, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    e = cudaFuncSetAttribute(k_vertex_gemm<3, 2, kRowsK, 32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    EPHB_LAUNCH((k_vertex_gemm<3, 2, kRowsK, 32>), unsigned(nitems), kTcThreads, smem, st, M, D, P, nullptr, phik, gs,
+    EPHB_LAUNCH((k_vertex_gemm<3, 2, kRowsK, 32, 2>), unsigned(nitems), kTcThreads, smem, st, M, D, P, nullptr, phik, gs,
                 gscale, out, err);
   }
   e = cudaGetLastError();
@@ -526,9 +534,9 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
                              const double2 *A, const __nv_bfloat16 *phis, __nv_bfloat16 *bs, double *bscale,
                              int *nitem, int64_t *item_ptr, int64_t *scratch, int64_t scratch_elems,
                              int64_t *total_dev, double *Cbuf, int *err, cudaStream_t st, cudaEvent_t gemm0,
-                             cudaEvent_t gemm1, int ncm, int kc) {
+                             cudaEvent_t gemm1, int ncm, int kc, int stages) {
   if (nkc <= 0) return cudaSuccess;
-  if (!tc_nc_valid(ns, ncm, kc)) return cudaErrorInvalidValue;
+  if (!tc_nc_valid(ns, ncm, kc, stages)) return cudaErrorInvalidValue;
   const int Kp = tc_kp(M), Nmax = tc_nmax(M);
   const int64_t nw = nkc * Nmax;
   EPHB_LAUNCH(k_b_slices, unsigned((nw * 32 + 255) / 256), 256, 0, st, M, D, i0, nkc, A, ns, Kp, Nmax, bs, bscale);
@@ -552,7 +560,7 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
   P.pair_base = pair_base;
   P.ncols = Nmax;
   P.out_stride = Nmax;
-  const size_t smem = tc_smem_bytes(ns, ncm, kc);
+  const size_t smem = tc_smem_bytes(ns, ncm, kc, stages);
   if (gemm0) {
     e = cudaEventRecord(gemm0, st);
     if (e != cudaSuccess) return e;
@@ -564,9 +572,11 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
     return cudaGetLastError();
   };
   if (ns == 7)
-    e = kc == 16 ? go(k_vertex_gemm<7, 5, kRowsPairs, 16>) : go(k_vertex_gemm<7, 5, kRowsPairs, 32>);
+    e = kc == 32 ? go(k_vertex_gemm<7, 5, kRowsPairs, 32, 2>)
+                 : (stages == 4 ? go(k_vertex_gemm<7, 5, kRowsPairs, 16, 4>) : go(k_vertex_gemm<7, 5, kRowsPairs, 16, 2>));
   else
-    e = kc == 16 ? go(k_vertex_gemm<3, 2, kRowsPairs, 16>) : go(k_vertex_gemm<3, 2, kRowsPairs, 32>);
+    e = kc == 32 ? go(k_vertex_gemm<3, 2, kRowsPairs, 32, 2>)
+                 : (stages == 4 ? go(k_vertex_gemm<3, 2, kRowsPairs, 16, 4>) : go(k_vertex_gemm<3, 2, kRowsPairs, 16, 2>));
   if (e != cudaSuccess) return e;
   e = cudaGetLastError();
   if (e == cudaSuccess && gemm1) e = cudaEventRecord(gemm1, st);
