@@ -809,24 +809,36 @@ __global__ void __launch_bounds__(256) k_corr_sweep_seg(ModelDev M, SweepSegs S,
   const int64_t rend = S.row_ptr[row + 1];
   const int64_t e_end = b + kSeg < rend ? b + kSeg : rend;
   float a[6] = {0, 0, 0, 0, 0, 0};
-  for (int64_t e = b + lane; e < e_end; e += 32) {
-    const uint32_t pc = run_col[e];
-    const uint32_t col = pc & kRunColMask;
-    if (col == kRunNone) continue;
-    const float w = run_w32[e];
-    float vi[3] = {dI[int64_t(col) * 3], dI[int64_t(col) * 3 + 1], dI[int64_t(col) * 3 + 2]};
-    float vj[3] = {dJ[int64_t(col) * 3], dJ[int64_t(col) * 3 + 1], dJ[int64_t(col) * 3 + 2]};
-    if (sym) {
-      const float *Cs = C + 9 * (pc >> 26);
-      float r[3];
-      for (int x = 0; x < 3; ++x) r[x] = Cs[3 * x] * vi[0] + Cs[3 * x + 1] * vi[1] + Cs[3 * x + 2] * vi[2];
-      for (int x = 0; x < 3; ++x) vi[x] = r[x];
-      for (int x = 0; x < 3; ++x) r[x] = Cs[3 * x] * vj[0] + Cs[3 * x + 1] * vj[1] + Cs[3 * x + 2] * vj[2];
-      for (int x = 0; x < 3; ++x) vj[x] = r[x];
+  for (int64_t e0 = b + lane; e0 < e_end; e0 += 32 * kUnroll) {
+    // the run words and weights of kUnroll runs first, then their gathers (more loads in flight)
+    uint32_t pcs[kUnroll];
+    float ws[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t e = e0 + 32 * u;
+      pcs[u] = e < e_end ? __ldcs(run_col + e) : kRunNone;
+      ws[u] = e < e_end ? __ldcs(run_w32 + e) : 0.f;
     }
-    for (int c = 0; c < 3; ++c) {
-      a[c] = fmaf(w, vi[c], a[c]);
-      a[3 + c] = fmaf(w, vj[c], a[3 + c]);
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t pc = pcs[u];
+      const uint32_t col = pc & kRunColMask;
+      if (col == kRunNone) continue;
+      const float w = ws[u];
+      float vi[3] = {dI[int64_t(col) * 3], dI[int64_t(col) * 3 + 1], dI[int64_t(col) * 3 + 2]};
+      float vj[3] = {dJ[int64_t(col) * 3], dJ[int64_t(col) * 3 + 1], dJ[int64_t(col) * 3 + 2]};
+      if (sym) {
+        const float *Cs = C + 9 * (pc >> 26);
+        float r[3];
+        for (int x = 0; x < 3; ++x) r[x] = Cs[3 * x] * vi[0] + Cs[3 * x + 1] * vi[1] + Cs[3 * x + 2] * vi[2];
+        for (int x = 0; x < 3; ++x) vi[x] = r[x];
+        for (int x = 0; x < 3; ++x) r[x] = Cs[3 * x] * vj[0] + Cs[3 * x + 1] * vj[1] + Cs[3 * x + 2] * vj[2];
+        for (int x = 0; x < 3; ++x) vj[x] = r[x];
+      }
+      for (int c = 0; c < 3; ++c) {
+        a[c] = fmaf(w, vi[c], a[c]);
+        a[3 + c] = fmaf(w, vj[c], a[3 + c]);
+      }
     }
   }
   for (int c = 0; c < 6; ++c)
