@@ -161,12 +161,13 @@ typedef struct { double sigma_eV, cutoff_sigmas; } ephb_delta;
  *                     of 8 bits, the 28 slice products of the leading diagonals, the four
  *                     largest diagonals each kept in an accumulator where the FP32 sums are
  *                     exact; FP64-grade results.  Needs 2 nRgp <= 256 (EPHB_EINVAL otherwise).
- *   EPHB_SPLIT_BF16   3 slices, the leading diagonal exact, the rest in one FP32 accumulator
- *                     (mixed precision, ~1e-7 relative).  Needs 2 nRgp <= 1024.
+ *   EPHB_SPLIT_BF16   3 slices, the leading diagonal exact, the rest in one FP32 accumulator,
+ *                     and the band/branch rotations of the epilogue in FP32 (mixed precision,
+ *                     ~1e-7 relative).  Needs 2 nRgp <= 1024.
  *   EPHB_SPLIT_TF32   not available (EPHB_EINVAL).
  * In both tensor-core modes the stage-A contraction (R_e sum) runs on the tensor cores in the
- * FP64-grade 7-slice form when 2 nRe <= 256 (else in FP64).  The rotations, |g|^2,
- * occupations and delta stay FP64 in every mode. */
+ * FP64-grade 7-slice form when 2 nRe <= 256 (else in FP64).  |g|^2 averages, occupations and
+ * delta stay FP64 in every mode, and so do the rotations except in EPHB_SPLIT_BF16. */
 typedef enum { EPHB_FP64 = 0, EPHB_SPLIT_TF32 = 1, EPHB_SPLIT_BF16 = 2, EPHB_FP64_SLICED = 3 } ephb_precision;
 
 typedef struct {

@@ -684,6 +684,7 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
   rp.inv_Nq_pref = 2.0 * kPi / (kHbarEVs * double(nq));
   rp.y_scale = double(nq) / double(ctx->km.size());
   rp.vertex_only = multi ? 1 : 0;
+  rp.rot_fp32 = precision == EPHB_SPLIT_BF16 ? 1 : 0;   // mixed mode: FP32 rotations in the epilogue
   const int64_t np = ctx->n_pairs;
   CK(ctx->cntE.ensure(np * nb));
   CK(ctx->cntPh.ensure(np * nbr));

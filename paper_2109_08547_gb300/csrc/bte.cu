@@ -287,17 +287,25 @@ __global__ void __launch_bounds__(256) k_drag_sweep_seg(MeshDev D, BteDev B, Swe
   const int nbr = B.nbr;
   const uint32_t kc = B.kcrd[D.ibzw_list[st / B.nb]];
   const int k0 = kc & 1023u, k1 = (kc >> 10) & 1023u, k2 = kc >> 20;
+  const bool unit_ratio = D.ratio[0] == 1 && D.ratio[1] == 1 && D.ratio[2] == 1;
   double a[6] = {0, 0, 0, 0, 0, 0};
   for (int64_t e = b + lane; e < e_end; e += 32) {
     const uint32_t pk = __ldcs(B.e_kpns + e);
     const double2 X = __ldcs(B.e_X + e);
     const int kp = unpack_kp(pk), s = unpack_s(pk);
     const uint32_t pc = B.kcrd[kp];
-    const int d0 = pmod(int(pc & 1023u) - k0, D.km.n[0]) / D.ratio[0];
-    const int d1 = pmod(int((pc >> 10) & 1023u) - k1, D.km.n[1]) / D.ratio[1];
-    const int d2 = pmod(int(pc >> 20) - k2, D.km.n[2]) / D.ratio[2];
+    // q = (k' - k) / ratio per dimension (k' - k is a multiple of the ratio); -q on the q mesh
+    int d0 = int(pc & 1023u) - k0, d1 = int((pc >> 10) & 1023u) - k1, d2 = int(pc >> 20) - k2;
+    d0 += d0 < 0 ? D.km.n[0] : 0;
+    d1 += d1 < 0 ? D.km.n[1] : 0;
+    d2 += d2 < 0 ? D.km.n[2] : 0;
+    if (!unit_ratio) {
+      d0 /= D.ratio[0];
+      d1 /= D.ratio[1];
+      d2 /= D.ratio[2];
+    }
     const int64_t q = D.qm.flat(d0, d1, d2);
-    const int64_t mq = D.qm.flat(pmod(-d0, D.qm.n[0]), pmod(-d1, D.qm.n[1]), pmod(-d2, D.qm.n[2]));
+    const int64_t mq = D.qm.flat(d0 ? D.qm.n[0] - d0 : 0, d1 ? D.qm.n[1] - d1 : 0, d2 ? D.qm.n[2] - d2 : 0);
     const double *Fq = F + (q * nbr + s) * 3, *Fm = F + (mq * nbr + s) * 3;
     const double *Gq = G + (q * nbr + s) * 3, *Gm = G + (mq * nbr + s) * 3;
     for (int c = 0; c < 3; ++c) {
@@ -321,12 +329,15 @@ __global__ void k_drag_finalize(int64_t nst, SweepSegs S, const double *part, do
 }
 
 // One warp per phonon row (q,s): Btv = sum Y/|stab| (S_k' I_<k'>n - I_km), fields I and J.
+template <bool SYM>
 __global__ void __launch_bounds__(256) k_ph_sweep(ModelDev M, MeshDev D, BteDev B, const int2 *__restrict__ kinfo,
                                                   const double *__restrict__ I, const double *__restrict__ J,
                                                   double *Btv) {
   __shared__ double C[kMaxSym * 9];
-  for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) C[t] = M.sym_cart[t];
-  __syncthreads();
+  if (SYM) {
+    for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) C[t] = M.sym_cart[t];
+    __syncthreads();
+  }
   int64_t row = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (row >= B.nq * B.nbr) return;
@@ -338,11 +349,21 @@ __global__ void __launch_bounds__(256) k_ph_sweep(ModelDev M, MeshDev D, BteDev 
     int kp = unpack_kp(pk), n = unpack_n(pk);
     int2 inf = kinfo[kp];
     double r[3] = {0.0, 0.0, 0.0};
-    const double *Cs = C + 9 * (inf.y > 0 ? inf.y : 0);
     const int64_t st2 = inf.x + n;
-    if (inf.x >= 0) rot3(Cs, I + st2 * 3, r);   // inf.x < 0: see the electron sweep
+    // inf.x < 0: see the electron sweep.  Without symmetry every k is its own representative.
+    if (SYM) {
+      const double *Cs = C + 9 * (inf.y > 0 ? inf.y : 0);
+      if (inf.x >= 0) rot3(Cs, I + st2 * 3, r);
+    } else if (inf.x >= 0) {
+      for (int a = 0; a < 3; ++a) r[a] = I[st2 * 3 + a];
+    }
     for (int a = 0; a < 3; ++a) aI[a] += y * (r[a] - I[int64_t(st) * 3 + a]);
-    if (inf.x >= 0) rot3(Cs, J + st2 * 3, r);
+    if (SYM) {
+      const double *Cs = C + 9 * (inf.y > 0 ? inf.y : 0);
+      if (inf.x >= 0) rot3(Cs, J + st2 * 3, r);
+    } else if (inf.x >= 0) {
+      for (int a = 0; a < 3; ++a) r[a] = J[st2 * 3 + a];
+    }
     for (int a = 0; a < 3; ++a) aJ[a] += y * (r[a] - J[int64_t(st) * 3 + a]);
   }
   for (int a = 0; a < 3; ++a) {
@@ -950,7 +971,11 @@ cudaError_t launch_drag_term(const MeshDev &D, const BteDev &B, const SweepSegs 
 
 cudaError_t launch_ph_sweep(const ModelDev &M, const MeshDev &D, const BteDev &B, const int2 *kinfo, const double *I,
                             const double *J, double *Btv, cudaStream_t st) {
-  EPHB_LAUNCH(k_ph_sweep, unsigned((B.nq * B.nbr * 32 + 255) / 256), 256, 0, st, M, D, B, kinfo, I, J, Btv);
+  const unsigned g = unsigned((B.nq * B.nbr * 32 + 255) / 256);
+  if (M.nsym > 1)
+    EPHB_LAUNCH(k_ph_sweep<true>, g, 256, 0, st, M, D, B, kinfo, I, J, Btv);
+  else
+    EPHB_LAUNCH(k_ph_sweep<false>, g, 256, 0, st, M, D, B, kinfo, I, J, Btv);
   return cudaGetLastError();
 }
 

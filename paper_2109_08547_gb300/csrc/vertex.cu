@@ -453,7 +453,9 @@ __global__ void k_epi_tables(ModelDev M, MeshDev D, double T, double mu, double 
 // before the branch index, W[m n a] = sum_n' conj(c_{n'n}(k')) B[m n' a], then
 // g[m n s] = sqrt(w_ref/w_s) sum_a W[m n a] u_{a s}(q)/sqrt(m_a/m_bar): the same product as
 // the fused kernel, with nact' instead of nb final-band rows in the branch rotation.
-template <int NBM, int NBRM>
+// ROT32: the band and branch rotations in FP32 (mixed mode, whose contraction is ~1e-7 accurate
+// anyway); |g|^2 is then carried on in FP64 like the rest of the epilogue.
+template <int NBM, int NBRM, bool ROT32>
 __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, RateParams rp, int64_t pbeg,
                                                        int64_t pend, int64_t pair_base, const double *__restrict__ Cbuf,
                                                        int Nmax, const double *__restrict__ fk,
@@ -477,6 +479,34 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
   const double2 *uq = ut + size_t(q) * nbr * nbr;
   const double *wrq = wr + size_t(q) * nbr;
   double g2[NBM * NBM * NBRM];
+  if (ROT32) {
+    for (int ml = 0; ml < nact; ++ml)
+      for (int nl = 0; nl < nactp; ++nl) {
+        const int n = nth_bit(an, nl);
+        float Wr[NBRM], Wi[NBRM];
+        for (int a = 0; a < nbr; ++a) Wr[a] = Wi[a] = 0.f;
+        for (int np_ = 0; np_ < nb; ++np_) {
+          const double2 c = ckp[np_ * nb + n];
+          const float cr = float(c.x), ci = float(c.y);
+          const double *re = crow + ml * 2 * nbnbr + np_ * nbr;
+          for (int a = 0; a < nbr; ++a) {   // W += conj(c) B
+            const float br = float(re[a]), bi = float(re[nbnbr + a]);
+            Wr[a] = fmaf(cr, br, fmaf(ci, bi, Wr[a]));
+            Wi[a] = fmaf(cr, bi, fmaf(-ci, br, Wi[a]));
+          }
+        }
+        for (int s = 0; s < nbr; ++s) {
+          float gr = 0.f, gi = 0.f;
+          for (int a = 0; a < nbr; ++a) {   // g += W u
+            const double2 u = uq[a * nbr + s];
+            const float ur = float(u.x), ui = float(u.y);
+            gr = fmaf(Wr[a], ur, fmaf(-Wi[a], ui, gr));
+            gi = fmaf(Wr[a], ui, fmaf(Wi[a], ur, gi));
+          }
+          g2[(ml * nactp + nl) * nbr + s] = double(gr * gr + gi * gi) * wrq[s];
+        }
+      }
+  } else
   for (int ml = 0; ml < nact; ++ml)
     for (int nl = 0; nl < nactp; ++nl) {
       const int n = nth_bit(an, nl);
@@ -585,15 +615,17 @@ cudaError_t launch_vertex_epilogue(const ModelDev &M, const MeshDev &D, RatePara
                                    uint32_t *ph_kpn, double *ph_Y, cudaStream_t st) {
   if (pend <= pbeg) return cudaSuccess;
   const unsigned grid = unsigned((pend - pbeg + 127) / 128);
+  auto go = [&](auto kern) {
+    EPHB_LAUNCH(kern, grid, 128, 0, st, M, D, rp, pbeg, pend, pair_base, Cbuf, Nmax, fk, nbq, wr, ut, escan, phscan,
+                e_kpns, e_X, ph_st, ph_kpn, ph_Y);
+  };
   if (M.nb <= 1 && M.nbr <= 3)
-    EPHB_LAUNCH((k_rate_epilogue<1, 3>), grid, 128, 0, st, M, D, rp, pbeg, pend, pair_base, Cbuf, Nmax, fk, nbq, wr,
-                ut, escan, phscan, e_kpns, e_X, ph_st, ph_kpn, ph_Y);
+    rp.rot_fp32 ? go(k_rate_epilogue<1, 3, true>) : go(k_rate_epilogue<1, 3, false>);
   else if (M.nb <= 4 && M.nbr <= 6)
-    EPHB_LAUNCH((k_rate_epilogue<4, 6>), grid, 128, 0, st, M, D, rp, pbeg, pend, pair_base, Cbuf, Nmax, fk, nbq, wr,
-                ut, escan, phscan, e_kpns, e_X, ph_st, ph_kpn, ph_Y);
+    rp.rot_fp32 ? go(k_rate_epilogue<4, 6, true>) : go(k_rate_epilogue<4, 6, false>);
   else
-    EPHB_LAUNCH((k_rate_epilogue<kMaxBands, kMaxBranches>), grid, 128, 0, st, M, D, rp, pbeg, pend, pair_base, Cbuf,
-                Nmax, fk, nbq, wr, ut, escan, phscan, e_kpns, e_X, ph_st, ph_kpn, ph_Y);
+    rp.rot_fp32 ? go(k_rate_epilogue<kMaxBands, kMaxBranches, true>)
+                : go(k_rate_epilogue<kMaxBands, kMaxBranches, false>);
   return cudaGetLastError();
 }
 
