@@ -365,12 +365,15 @@ __global__ void __launch_bounds__(kTcThreads, (KC == 16 && ST == 2) ? 2 : 1) k_v
       asm volatile("tcgen05.fence::after_thread_sync;");
       const unsigned char *sA = smem + buf * stage_bytes;
       const unsigned char *sB = sA + NS * a_slice;
-      for (int is = 0; is < NS; ++is)
-        for (int ls = 0; ls < NS - is; ++ls) {   // diagonal d = is + ls <= NS - 1 (i + l <= NS + 1)
-          const int d = is + ls;
-          const int acc = NACC == 1 ? 0 : (d < NACC - 1 ? d : NACC - 1);
-          const uint32_t dtm = taddr + uint32_t(acc * nc);
-          for (int ks = 0; ks < KC / 16; ++ks) {
+      // K-step-major order: every accumulator receives its products in the same sequence
+      // whatever KC is, so the rounded tail accumulator (and the result) does not depend on
+      // the tile shape
+      for (int ks = 0; ks < KC / 16; ++ks)
+        for (int is = 0; is < NS; ++is)
+          for (int ls = 0; ls < NS - is; ++ls) {   // diagonal d = is + ls <= NS - 1 (i + l <= NS + 1)
+            const int d = is + ls;
+            const int acc = NACC == 1 ? 0 : (d < NACC - 1 ? d : NACC - 1);
+            const uint32_t dtm = taddr + uint32_t(acc * nc);
             const uint64_t ad = smem_desc(smem_u32(sA + is * a_slice) + ks * 256, 128u, (KC / 8) * 128u);
             const uint64_t bd = smem_desc(smem_u32(sB + ls * b_slice) + ks * 256, 128u, (KC / 8) * 128u);
             // the first product into each accumulator (first K block, first K step) overwrites it
@@ -382,7 +385,6 @@ __global__ void __launch_bounds__(kTcThreads, (KC == 16 && ST == 2) ? 2 : 1) k_v
                          "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
                          :: "r"(dtm), "l"(ad), "l"(bd), "r"(idesc), "r"(en));
           }
-        }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                    :: "r"(smem_u32(&mbar[buf])) : "memory");
     }
