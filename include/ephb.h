@@ -354,6 +354,12 @@ typedef enum {
  * context; setting 0 again re-tunes.  Otherwise the given width (a multiple of 16, at most
  * 96 / 256) is used with stages of 32.  The results do not depend on the shape. */
 #define EPHB_TUNE_TC_COLS 0
+/* EPHB_TUNE_WITHHOLD_MMA (value 1): the stage-B contraction issues no tensor-core MMA, so the
+ * barriers its CTAs wait on never complete; every wait gives up after its 2 s bound, the CTAs
+ * record the timeout, free their tensor memory and return, and the rates call returns
+ * EPHB_ETIMEOUT with the context still usable.  It exists to check that failure path; value 0
+ * restores normal operation. */
+#define EPHB_TUNE_WITHHOLD_MMA 1
 ephb_status ephb_set_tuning(ephb_ctx *ctx, int key, int value);
 
 /* Make instance inst the one whose arrays the views and copies below return (and the one

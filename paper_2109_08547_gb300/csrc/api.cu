@@ -192,6 +192,7 @@ struct ephb_ctx : InstState {
   int tune_kc[2] = {32, 32};
   int tune_st[2] = {2, 2};
   int force_cols = 0;
+  int withhold_mma = 0;   // failure-path check (EPHB_TUNE_WITHHOLD_MMA)
   double *host_res = nullptr;   // pinned: kResLen doubles, then the sweep-loop control (4 ints)
 };
 
@@ -802,7 +803,8 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
       auto contract = [&](cudaEvent_t e0, cudaEvent_t e1, int width, int kc, int stages) {
         return launch_vertex_tc(M, D, ns, i0, nkc, hpp[i0], ctx->Abuf.p, ctx->phis.p, ctx->bslices.p,
                                 ctx->bscale.p, ctx->nitem.p, ctx->item_ptr.p, ctx->scratch.p, ctx->scratch.n,
-                                ctx->scal.p + 6, ctx->Cbuf.p, ctx->tc_err.p, st, e0, e1, width, kc, stages);
+                                ctx->scal.p + 6, ctx->Cbuf.p, ctx->tc_err.p, st, e0, e1, width, kc, stages,
+                                ctx->withhold_mma);
       };
       int &tuned = ctx->tune_cols[ns == 7 ? 0 : 1];
       int &tuned_kc = ctx->tune_kc[ns == 7 ? 0 : 1];
@@ -1389,6 +1391,10 @@ ephb_status ephb_instance_solve_info(ephb_ctx *ctx, int inst, ephb_solve_info *o
 
 ephb_status ephb_set_tuning(ephb_ctx *ctx, int key, int value) {
   if (!ctx) return EPHB_EINVAL;
+  if (key == EPHB_TUNE_WITHHOLD_MMA) {
+    ctx->withhold_mma = value ? 1 : 0;
+    return EPHB_OK;
+  }
   if (key != EPHB_TUNE_TC_COLS) return fail(ctx, EPHB_EINVAL, "unknown tuning key");
   if (value != 0 && (value < 16 || value % 16 != 0 || value > 256))
     return fail(ctx, EPHB_EINVAL, "column-chunk width must be 0 or a multiple of 16 in [16, 256]");

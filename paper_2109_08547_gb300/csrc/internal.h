@@ -115,7 +115,7 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
                              const double2 *A, const __nv_bfloat16 *phis, __nv_bfloat16 *bs, double *bscale,
                              int *nitem, int64_t *item_ptr, int64_t *scratch, int64_t scratch_elems,
                              int64_t *total_dev, double *Cbuf, int *err, cudaStream_t st, cudaEvent_t gemm0,
-                             cudaEvent_t gemm1, int ncm, int kc, int stages);
+                             cudaEvent_t gemm1, int ncm, int kc, int stages, int withhold = 0);
 // Stage A on tensor cores: T[kc][col] = sum_Re e^{ik.Re} g[Re][col] for the k of a chunk, as
 // the same exact-slice GEMM with the k phase slices as rows and the model's g slices (made
 // once by launch_g_slices, [ns][tc_ncols_a][tc_kp_a] BF16 + column scales) as B.

@@ -242,6 +242,7 @@ struct TcParams {
   int ns, nacc, Kp, Nmax, nc_max;   // Nmax: B rows per slice (columns of the real GEMM)
   int64_t i0, nkc, pair_base;       // stage B: first pair of the chunk
   int ncols, out_stride;            // stage A: live columns and the output row stride (doubles)
+  int withhold;                     // failure-path check: issue no MMA (so no barrier completes)
 };
 
 // KC: K per shared-memory stage (32: one CTA per SM; 16: two CTAs per SM share the SM's
@@ -361,7 +362,7 @@ __global__ void __launch_bounds__(kTcThreads, (KC == 16 && ST == 2) ? 2 : 1) k_v
     else asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && !P.withhold) {
       asm volatile("tcgen05.fence::after_thread_sync;");
       const unsigned char *sA = smem + buf * stage_bytes;
       const unsigned char *sB = sA + NS * a_slice;
@@ -400,6 +401,8 @@ __global__ void __launch_bounds__(kTcThreads, (KC == 16 && ST == 2) ? 2 : 1) k_v
       if (ok) stage_load(nb % ST, nb * KC);
     }
   }
+  // no copy may still be in flight when the CTA leaves (after a timeout some can be)
+  asm volatile("cp.async.wait_all;" ::: "memory");
   // the last commit tracks every MMA issued before it (after a timeout: the bounded second wait)
   {
     const bool waited = mbar_wait(smem_u32(&mbar[issued % ST]), uint32_t((issued / ST) & 1));
@@ -503,6 +506,7 @@ cudaError_t launch_stage_a_tc(const ModelDev &M, const MeshDev &D, int ns, int64
   P.pair_base = 0;
   P.ncols = 2 * M.nRgp * M.nb * M.nb * M.nbr;
   P.out_stride = P.ncols;
+  P.withhold = 0;
   const int nch = (Ncols + ncm - 1) / ncm;
   const int64_t ntile = (nkc + kTcM - 1) / kTcM;
   const int64_t nitems = ntile * nch;
@@ -536,7 +540,7 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
                              const double2 *A, const __nv_bfloat16 *phis, __nv_bfloat16 *bs, double *bscale,
                              int *nitem, int64_t *item_ptr, int64_t *scratch, int64_t scratch_elems,
                              int64_t *total_dev, double *Cbuf, int *err, cudaStream_t st, cudaEvent_t gemm0,
-                             cudaEvent_t gemm1, int ncm, int kc, int stages) {
+                             cudaEvent_t gemm1, int ncm, int kc, int stages, int withhold) {
   if (nkc <= 0) return cudaSuccess;
   if (!tc_nc_valid(ns, ncm, kc, stages)) return cudaErrorInvalidValue;
   const int Kp = tc_kp(M), Nmax = tc_nmax(M);
@@ -562,6 +566,7 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
   P.pair_base = pair_base;
   P.ncols = Nmax;
   P.out_stride = Nmax;
+  P.withhold = withhold;
   const size_t smem = tc_smem_bytes(ns, ncm, kc, stages);
   if (gemm0) {
     e = cudaEventRecord(gemm0, st);

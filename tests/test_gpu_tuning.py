@@ -38,3 +38,23 @@ def test_bad_width_is_rejected():
         for bad in (8, 100, 512):
             with pytest.raises(B.EphbError):
                 B.set_tuning(ctx, B.TUNE_TC_COLS, bad)
+
+
+def test_wait_timeout_is_reported_and_the_context_recovers():
+    """With the tensor-core MMAs withheld the barriers never complete: every bounded wait gives
+    up (2 s), the call returns EPHB_ETIMEOUT, and the same context then computes the same rates
+    as a fresh one."""
+    wl = SY.workload_cscl4(n=6)
+    with B.Context(0) as ctx, B.Context(0) as ref:
+        for c in (ctx, ref):
+            B.set_wannier_model(c, wl.model)
+            B.set_tuning(c, B.TUNE_TC_COLS, 96)
+            B.build_meshes_ibz(c, wl.kmesh, wl.qmesh, wl.window, wl.degen_tol_eV, wl.omega_min_eV)
+        B.set_tuning(ctx, B.TUNE_WITHHOLD_MMA, 1)
+        with pytest.raises(B.EphbError) as err:
+            B.compute_transition_rates(ctx, wl.T_K, wl.mu_eV, wl.sigma_eV, wl.cutoff_sigmas, B.FP64_SLICED)
+        assert err.value.status == B.ETIMEOUT
+        B.set_tuning(ctx, B.TUNE_WITHHOLD_MMA, 0)
+        B.compute_transition_rates(ctx, wl.T_K, wl.mu_eV, wl.sigma_eV, wl.cutoff_sigmas, B.FP64_SLICED)
+        B.compute_transition_rates(ref, wl.T_K, wl.mu_eV, wl.sigma_eV, wl.cutoff_sigmas, B.FP64_SLICED)
+        assert np.array_equal(B.get_array(ctx, "entry_x"), B.get_array(ref, "entry_x"))
