@@ -939,6 +939,23 @@ __global__ void k_runs32(int64_t n, const uint32_t *col, const double *w, uint2 
 
 }  // namespace
 
+namespace {
+__global__ void k_pack_ij(int64_t nst, const double *I, const double *J, double2 *IJ) {
+  const int64_t st = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (st >= nst) return;
+  double2 *p = IJ + st * 3;
+  p[0] = make_double2(I[st * 3], I[st * 3 + 1]);
+  p[1] = make_double2(I[st * 3 + 2], J[st * 3]);
+  p[2] = make_double2(J[st * 3 + 1], J[st * 3 + 2]);
+}
+}  // namespace
+
+cudaError_t launch_pack_ij(int64_t nst, const double *I, const double *J, double2 *IJ, cudaStream_t st) {
+  if (nst == 0) return cudaSuccess;
+  EPHB_LAUNCH(k_pack_ij, unsigned((nst + 255) / 256), 256, 0, st, nst, I, J, IJ);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_runs32(int64_t n, const uint32_t *col, const double *w, uint2 *out, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   EPHB_LAUNCH(k_runs32, unsigned((n + 255) / 256), 256, 0, st, n, col, w, out);
