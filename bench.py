@@ -469,7 +469,8 @@ def main():
     peaks = measured_peaks()
     step_ms = 1e3 * el_max / args.steps
     fp64_src = "measured FP64 FMA rate (bench.py --fp64-peak, profiles/fp64_peak_gb300.txt)"
-    cands = [("stage_a", ms_a), ("epilogue", ms_ep), ("self_sweep", ms_self)]
+    ms_corr = mean(lambda r: r.solve["ms_corr"])
+    cands = [("stage_a", ms_a), ("epilogue", ms_ep), ("self_sweep", ms_self), ("corr", ms_corr)]
     cands.append(("stage_b", ms_b) if args.precision == "fp64" else ("gemm", ms_g))
     dominant = max(cands, key=lambda x: x[1])[0]
     if dominant == "stage_b":
@@ -496,6 +497,18 @@ def main():
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": fp64_src, "traffic": None,
                 "ms_per_step": ms_a, "share_of_step": ms_a / step_ms}
+    elif dominant == "corr":
+        # FP32 correction sweeps of the mixed iteration: the run words (8 B per run) are the
+        # algorithmic stream; the partner vectors are L2/L1-resident gathers and not counted
+        n32 = r0.solve["n_sweeps32"]
+        pk = peaks.get("hbm_gbs", 6800.0)
+        achieved = 8.0 * r0.solve["n_runs"] * n32 / (ms_corr * 1e-3) / 1e9
+        tr = profile_traffic("corr_sweep", "bte.cu")
+        roof = {"kernel": "k_corr_sweep_seg + k_corr_finalize (FP32 correction sweeps of the mixed iteration)",
+                "bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s", "frac": achieved / pk,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback",
+                "traffic": (tr[0] * r0.solve["n_runs"]) if tr else None,
+                "ms_per_step": ms_corr, "share_of_step": ms_corr / step_ms}
     elif dominant == "epilogue":
         achieved = r0.rates["rot_flops"] / (ms_ep * 1e-3) / 1e12
         tr = profile_traffic("rate_epilogue", "vertex.cu")

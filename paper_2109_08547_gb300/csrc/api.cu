@@ -103,12 +103,9 @@ struct InstState {
   DBuf<unsigned long long> nzero;
   DBuf<float> warm;             // warm-start scale factors [nst][2]
   // mixed-precision electron loop: FP32 run weights, residual and correction vectors, partials
-  DBuf<uint2> runs32;           // FP32 run words (partner | op, weight)
-  DBuf<float4> r32, d32, d32b;  // packed FP32 residual and corrections [nst][2]
-  DBuf<float> part32;
+  DBuf<float> run_w32, rI, rJ, dI, dJ, dI2, dJ2, part32;
   DBuf<double2> IJ, IJ2;        // packed responses for the FP64 gathers
   DBuf<unsigned> fuse_ctr;      // blocks done in the fused finalisation
-  DBuf<double2> FG;             // packed (F, G) per mode for the drag gathers
   bool have_f32 = false;
   DBuf<unsigned> vmaxb;
   bool bte_ready = false, has_warm = false, solved = false;
@@ -125,15 +122,10 @@ struct InstState {
     eseg_begin.release(); rseg_ptr.release(); rseg_begin.release(); run_ptr.release(); run_idx.release();
     run_col.release(); kcrd.release(); kinfo.release(); sctl.release(); nzero.release(); warm.release();
     vmaxb.release();
-    runs32.release();
-    r32.release();
-    d32.release();
-    d32b.release();
-    part32.release();
+    for (auto *b : {&run_w32, &rI, &rJ, &dI, &dJ, &dI2, &dJ2, &part32}) b->release();
     IJ.release();
     IJ2.release();
     fuse_ctr.release();
-    FG.release();
     bte_ready = has_warm = solved = have_f32 = false;
   }
 };
@@ -920,7 +912,6 @@ ephb_status bte_setup(ephb_ctx *ctx) {
   CK(ctx->W_ph.ensure(nph));
   CK(ctx->inv_nnW.ensure(nph));
   for (auto *b : {&ctx->F0, &ctx->F, &ctx->G}) CK(b->ensure(nph * 3));
-  CK(ctx->FG.ensure(nph * 3));
   CK(ctx->Btv.ensure(nph * 6));
   CK(ctx->epart.ensure(size_t(coeff_partials()) * 36));
   CK(ctx->ppart.ensure(size_t(coeff_partials()) * 18));
@@ -1056,11 +1047,12 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
   // and x <- x + d, before the next FP64 sweep.
   auto inner_loop_mixed = [&](int drag, bool &ok) -> ephb_status {
     ok = false;
+    const int64_t n3 = nst * 3;
     if (!ctx->have_f32) {
-      CK(ctx->runs32.ensure(ctx->nruns));
-      for (auto *b : {&ctx->r32, &ctx->d32, &ctx->d32b}) CK(b->ensure(size_t(nst) * 2));
+      CK(ctx->run_w32.ensure(ctx->nruns));
+      for (auto *b : {&ctx->rI, &ctx->rJ, &ctx->dI, &ctx->dJ, &ctx->dI2, &ctx->dJ2}) CK(b->ensure(n3));
       CK(ctx->part32.ensure(size_t(ctx->nrseg) * 6));
-      CK(launch_runs32(ctx->nruns, ctx->run_col.p, ctx->run_w.p, ctx->runs32.p, st));
+      CK(launch_to_f32(ctx->nruns, ctx->run_w.p, ctx->run_w32.p, st));
       ctx->have_f32 = true;
     }
     CK(cudaMemsetAsync(ctx->prev_in.p, 0, kResLen * sizeof(double), st));
@@ -1068,8 +1060,7 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
     if (r != EPHB_OK) return r;
     if (drag) {
       CK(td.start(st));
-      CK(launch_drag_term(D, B, entry_segs(ctx), ctx->F.p, ctx->G.p, ctx->seg_part.p, ctx->Dterm.p, st,
-                          ctx->FG.p));
+      CK(launch_drag_term(D, B, entry_segs(ctx), ctx->F.p, ctx->G.p, ctx->seg_part.p, ctx->Dterm.p, st));
       CK(td.stop(st));
     }
     const SweepSegs S = run_segs(ctx);
@@ -1102,14 +1093,17 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
         return EPHB_OK;
       }
       CK(tc32.start(st));
-      CK(launch_corr_init(nst, ctx->I2.p, ctx->I.p, ctx->J2.p, ctx->J.p, ctx->r32.p, ctx->d32.p, st));
-      float4 *dA = ctx->d32.p, *dB = ctx->d32b.p;
+      CK(launch_corr_init(nst, ctx->I2.p, ctx->I.p, ctx->J2.p, ctx->J.p, ctx->rI.p, ctx->rJ.p, ctx->dI.p, ctx->dJ.p,
+                          st));
+      float *dA = ctx->dI.p, *dAJ = ctx->dJ.p, *dB = ctx->dI2.p, *dBJ = ctx->dJ2.p;
       for (int j = 0; j < kCorrSweeps; ++j) {
-        CK(launch_corr_sweep(M, nst, S, ctx->runs32.p, ctx->inv_ffW.p, ctx->r32.p, dA, ctx->part32.p, dB, st));
+        CK(launch_corr_sweep(M, nst, S, ctx->run_col.p, ctx->run_w32.p, ctx->inv_ffW.p, ctx->rI.p, ctx->rJ.p, dA,
+                             dAJ, ctx->part32.p, dB, dBJ, st));
         std::swap(dA, dB);
+        std::swap(dAJ, dBJ);
       }
       sweeps32 += kCorrSweeps;
-      CK(launch_corr_apply(nst, dA, ctx->I.p, ctx->J.p, st));
+      CK(launch_corr_apply(nst, dA, dAJ, ctx->I.p, ctx->J.p, st));
       CK(tc32.stop(st));
       // coefficients of the corrected x become the reference of the next FP64 sweep's test
       CK(launch_e_partial(B, ctx->I.p, ctx->J.p, ctx->epart.p, st));
@@ -1128,8 +1122,7 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
     if (r != EPHB_OK) return r;
     if (drag) {   // F, G are fixed for this electron loop: its drag term is computed once
       CK(td.start(st));
-      CK(launch_drag_term(D, B, entry_segs(ctx), ctx->F.p, ctx->G.p, ctx->seg_part.p, ctx->Dterm.p, st,
-                          ctx->FG.p));
+      CK(launch_drag_term(D, B, entry_segs(ctx), ctx->F.p, ctx->G.p, ctx->seg_part.p, ctx->Dterm.p, st));
       CK(td.stop(st));
     }
     // Sweeps are queued in batches without a host round trip each: the coefficient kernel
@@ -1198,7 +1191,7 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
       CK(tp.start(st));
       CK(launch_ph_sweep(M, D, B, ctx->kinfo.p, ctx->I.p, ctx->J.p, ctx->Btv.p, st));
       CK(tp.stop(st));
-      CK(launch_ph_update(M, D, B, ctx->Btv.p, ctx->F0.p, ctx->inv_nnW.p, ctx->F.p, ctx->G.p, st, ctx->FG.p));
+      CK(launch_ph_update(M, D, B, ctx->Btv.p, ctx->F0.p, ctx->inv_nnW.p, ctx->F.p, ctx->G.p, st));
       bool ok;
       s = inner_loop(1, ok);
       if (s != EPHB_OK) return s;

@@ -276,7 +276,6 @@ __global__ void __launch_bounds__(256) k_self_sweep_seg(ModelDev M, SweepSegs S,
 // drag term over the rate entries of one segment
 __global__ void __launch_bounds__(256) k_drag_sweep_seg(MeshDev D, BteDev B, SweepSegs S,
                                                         const double *__restrict__ F, const double *__restrict__ G,
-                                                        const double2 *__restrict__ FG,
                                                         double *__restrict__ part) {
   const int64_t g = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -307,20 +306,8 @@ __global__ void __launch_bounds__(256) k_drag_sweep_seg(MeshDev D, BteDev B, Swe
     }
     const int64_t q = D.qm.flat(d0, d1, d2);
     const int64_t mq = D.qm.flat(d0 ? D.qm.n[0] - d0 : 0, d1 ? D.qm.n[1] - d1 : 0, d2 ? D.qm.n[2] - d2 : 0);
-    double Fq[3], Fm[3], Gq[3], Gm[3];
-    if (FG) {   // packed gathers: three 16-byte loads per mode
-      const double2 *pq = FG + (q * nbr + s) * 3, *pm = FG + (mq * nbr + s) * 3;
-      const double2 a0 = pq[0], a1 = pq[1], a2 = pq[2], b0 = pm[0], b1 = pm[1], b2 = pm[2];
-      Fq[0] = a0.x; Fq[1] = a0.y; Fq[2] = a1.x; Gq[0] = a1.y; Gq[1] = a2.x; Gq[2] = a2.y;
-      Fm[0] = b0.x; Fm[1] = b0.y; Fm[2] = b1.x; Gm[0] = b1.y; Gm[1] = b2.x; Gm[2] = b2.y;
-    } else {
-      for (int c = 0; c < 3; ++c) {
-        Fq[c] = F[(q * nbr + s) * 3 + c];
-        Fm[c] = F[(mq * nbr + s) * 3 + c];
-        Gq[c] = G[(q * nbr + s) * 3 + c];
-        Gm[c] = G[(mq * nbr + s) * 3 + c];
-      }
-    }
+    const double *Fq = F + (q * nbr + s) * 3, *Fm = F + (mq * nbr + s) * 3;
+    const double *Gq = G + (q * nbr + s) * 3, *Gm = G + (mq * nbr + s) * 3;
     for (int c = 0; c < 3; ++c) {
       a[c] += -Fq[c] * X.x + Fm[c] * X.y;
       a[3 + c] += -Gq[c] * X.x + Gm[c] * X.y;
@@ -392,7 +379,7 @@ __global__ void __launch_bounds__(256) k_ph_sweep(ModelDev M, MeshDev D, BteDev 
 
 // F = F0 + d_s/(n(1+n)W) sum_S C_S Btv_I(S^-1 q); G = d_s/(n(1+n)W) sum_S C_S Btv_J(S^-1 q)   (Eq. dF^D)
 __global__ void k_ph_update(ModelDev M, MeshDev D, BteDev B, const double *Btv, const double *F0,
-                            const double *inv_nnW, double *F, double *G, double2 *FG) {
+                            const double *inv_nnW, double *F, double *G) {
   __shared__ int rot[kMaxSym * 9];
   __shared__ int inv[kMaxSym];
   __shared__ double C[kMaxSym * 9];
@@ -416,17 +403,9 @@ __global__ void k_ph_update(ModelDev M, MeshDev D, BteDev B, const double *Btv, 
     for (int a = 0; a < 3; ++a) aJ[a] += r[a];
   }
   double c = M.spin_deg * inv_nnW[t];
-  double f[3], g[3];
   for (int a = 0; a < 3; ++a) {
-    f[a] = F0[t * 3 + a] + c * aI[a];
-    g[a] = c * aJ[a];
-    F[t * 3 + a] = f[a];
-    G[t * 3 + a] = g[a];
-  }
-  if (FG) {   // packed (F, G) of the mode for the drag gathers: (F0 F1 | F2 G0 | G1 G2)
-    FG[t * 3] = make_double2(f[0], f[1]);
-    FG[t * 3 + 1] = make_double2(f[2], g[0]);
-    FG[t * 3 + 2] = make_double2(g[1], g[2]);
+    F[t * 3 + a] = F0[t * 3 + a] + c * aI[a];
+    G[t * 3 + a] = c * aJ[a];
   }
 }
 
@@ -832,11 +811,11 @@ namespace {
 
 // ---- mixed-precision electron loop: FP32 correction sweeps between FP64 residual sweeps
 // d <- r + (1/(f(1-f)W)) sum_runs w d[partner] in FP32 over the same runs and segments.
-// Layouts: a run is one 8-byte word (partner | op, FP32 weight); a state's (dI, dJ) is two
-// float4 (dI0 dI1 dI2 dJ0 | dJ1 dJ2 0 0), so a partner costs one 8-byte and two 16-byte loads.
 
-__global__ void __launch_bounds__(256) k_corr_sweep_seg(ModelDev M, SweepSegs S, const uint2 *__restrict__ runs,
-                                                        const float4 *__restrict__ d, float *__restrict__ part) {
+__global__ void __launch_bounds__(256) k_corr_sweep_seg(ModelDev M, SweepSegs S, const uint32_t *__restrict__ run_col,
+                                                        const float *__restrict__ run_w32,
+                                                        const float *__restrict__ dI, const float *__restrict__ dJ,
+                                                        float *__restrict__ part) {
   __shared__ float C[kMaxSym * 9];
   const bool sym = M.nsym > 1;
   if (sym) {
@@ -852,22 +831,23 @@ __global__ void __launch_bounds__(256) k_corr_sweep_seg(ModelDev M, SweepSegs S,
   const int64_t e_end = b + kSeg < rend ? b + kSeg : rend;
   float a[6] = {0, 0, 0, 0, 0, 0};
   for (int64_t e0 = b + lane; e0 < e_end; e0 += 32 * kUnroll) {
-    // the run words of kUnroll runs first, then their gathers (more loads in flight)
-    uint2 rw[kUnroll];
+    // the run words and weights of kUnroll runs first, then their gathers (more loads in flight)
+    uint32_t pcs[kUnroll];
+    float ws[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const int64_t e = e0 + 32 * u;
-      rw[u] = e < e_end ? __ldcs(runs + e) : make_uint2(kRunNone, 0u);
+      pcs[u] = e < e_end ? __ldcs(run_col + e) : kRunNone;
+      ws[u] = e < e_end ? __ldcs(run_w32 + e) : 0.f;
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      const uint32_t pc = rw[u].x;
+      const uint32_t pc = pcs[u];
       const uint32_t col = pc & kRunColMask;
       if (col == kRunNone) continue;
-      const float w = __uint_as_float(rw[u].y);
-      const float4 p = d[int64_t(col) * 2], q = d[int64_t(col) * 2 + 1];
-      float vi[3] = {p.x, p.y, p.z};
-      float vj[3] = {p.w, q.x, q.y};
+      const float w = ws[u];
+      float vi[3] = {dI[int64_t(col) * 3], dI[int64_t(col) * 3 + 1], dI[int64_t(col) * 3 + 2]};
+      float vj[3] = {dJ[int64_t(col) * 3], dJ[int64_t(col) * 3 + 1], dJ[int64_t(col) * 3 + 2]};
       if (sym) {
         const float *Cs = C + 9 * (pc >> 26);
         float r[3];
@@ -889,52 +869,43 @@ __global__ void __launch_bounds__(256) k_corr_sweep_seg(ModelDev M, SweepSegs S,
 }
 
 __global__ void k_corr_finalize(int64_t nst, SweepSegs S, const float *__restrict__ part,
-                                const float4 *__restrict__ r, const double *__restrict__ inv_ffW, float4 *d) {
+                                const float *__restrict__ rI, const float *__restrict__ rJ,
+                                const double *__restrict__ inv_ffW, float *dI, float *dJ) {
   const int64_t st = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (st >= nst) return;
   float sum[6] = {0, 0, 0, 0, 0, 0};
   for (int64_t g = S.seg_ptr[st]; g < S.seg_ptr[st + 1]; ++g)
     for (int c = 0; c < 6; ++c) sum[c] += part[g * 6 + c];
   const float c0 = float(inv_ffW[st]);
-  const float4 p = r[st * 2], q = r[st * 2 + 1];
-  d[st * 2] = make_float4(p.x + c0 * sum[0], p.y + c0 * sum[1], p.z + c0 * sum[2], p.w + c0 * sum[3]);
-  d[st * 2 + 1] = make_float4(q.x + c0 * sum[4], q.y + c0 * sum[5], 0.f, 0.f);
+  for (int c = 0; c < 3; ++c) {
+    dI[st * 3 + c] = rI[st * 3 + c] + c0 * sum[c];
+    dJ[st * 3 + c] = rJ[st * 3 + c] + c0 * sum[3 + c];
+  }
 }
 
-// r = x' - x (FP32, packed), d = r
-__global__ void k_corr_init(int64_t nst, const double *I1, const double *I0x, const double *J1, const double *J0x,
-                            float4 *r, float4 *d) {
-  const int64_t st = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (st >= nst) return;
-  float v[6];
-  for (int c = 0; c < 3; ++c) {
-    v[c] = float(I1[st * 3 + c] - I0x[st * 3 + c]);
-    v[3 + c] = float(J1[st * 3 + c] - J0x[st * 3 + c]);
-  }
-  const float4 p = make_float4(v[0], v[1], v[2], v[3]), q = make_float4(v[4], v[5], 0.f, 0.f);
-  r[st * 2] = p;
-  r[st * 2 + 1] = q;
-  d[st * 2] = p;
-  d[st * 2 + 1] = q;
+// r = x' - x (FP32), d = r
+__global__ void k_corr_init(int64_t n3, const double *I1, const double *I0x, const double *J1, const double *J0x,
+                            float *rI, float *rJ, float *dI, float *dJ) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= n3) return;
+  const float a = float(I1[t] - I0x[t]), b = float(J1[t] - J0x[t]);
+  rI[t] = a;
+  dI[t] = a;
+  rJ[t] = b;
+  dJ[t] = b;
 }
 
 // x <- x + d (FP64)
-__global__ void k_corr_apply(int64_t nst, const float4 *d, double *I, double *J) {
-  const int64_t st = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (st >= nst) return;
-  const float4 p = d[st * 2], q = d[st * 2 + 1];
-  I[st * 3] += double(p.x);
-  I[st * 3 + 1] += double(p.y);
-  I[st * 3 + 2] += double(p.z);
-  J[st * 3] += double(p.w);
-  J[st * 3 + 1] += double(q.x);
-  J[st * 3 + 2] += double(q.y);
+__global__ void k_corr_apply(int64_t n3, const float *dI, const float *dJ, double *I, double *J) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= n3) return;
+  I[t] += double(dI[t]);
+  J[t] += double(dJ[t]);
 }
 
-// FP32 run words (partner | op, weight)
-__global__ void k_runs32(int64_t n, const uint32_t *col, const double *w, uint2 *out) {
+__global__ void k_to_f32(int64_t n, const double *a, float *b) {
   const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (t < n) out[t] = make_uint2(col[t], __float_as_uint(float(w[t])));
+  if (t < n) b[t] = float(a[t]);
 }
 
 }  // namespace
@@ -956,40 +927,44 @@ cudaError_t launch_pack_ij(int64_t nst, const double *I, const double *J, double
   return cudaGetLastError();
 }
 
-cudaError_t launch_runs32(int64_t n, const uint32_t *col, const double *w, uint2 *out, cudaStream_t st) {
+cudaError_t launch_to_f32(int64_t n, const double *a, float *b, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  EPHB_LAUNCH(k_runs32, unsigned((n + 255) / 256), 256, 0, st, n, col, w, out);
+  EPHB_LAUNCH(k_to_f32, unsigned((n + 255) / 256), 256, 0, st, n, a, b);
   return cudaGetLastError();
 }
 
 cudaError_t launch_corr_init(int64_t nst, const double *I1, const double *I0x, const double *J1, const double *J0x,
-                             float4 *r, float4 *d, cudaStream_t st) {
-  if (nst == 0) return cudaSuccess;
-  EPHB_LAUNCH(k_corr_init, unsigned((nst + 255) / 256), 256, 0, st, nst, I1, I0x, J1, J0x, r, d);
+                             float *rI, float *rJ, float *dI, float *dJ, cudaStream_t st) {
+  const int64_t n3 = nst * 3;
+  if (n3 == 0) return cudaSuccess;
+  EPHB_LAUNCH(k_corr_init, unsigned((n3 + 255) / 256), 256, 0, st, n3, I1, I0x, J1, J0x, rI, rJ, dI, dJ);
   return cudaGetLastError();
 }
 
-cudaError_t launch_corr_sweep(const ModelDev &M, int64_t nst, const SweepSegs &S, const uint2 *runs,
-                              const double *inv_ffW, const float4 *r, const float4 *d, float *part, float4 *d_out,
+cudaError_t launch_corr_sweep(const ModelDev &M, int64_t nst, const SweepSegs &S, const uint32_t *run_col,
+                              const float *run_w32, const double *inv_ffW, const float *rI, const float *rJ,
+                              const float *dI, const float *dJ, float *part, float *dI_out, float *dJ_out,
                               cudaStream_t st) {
   if (S.nseg > 0)
-    EPHB_LAUNCH(k_corr_sweep_seg, unsigned((S.nseg * 32 + 255) / 256), 256, 0, st, M, S, runs, d, part);
+    EPHB_LAUNCH(k_corr_sweep_seg, unsigned((S.nseg * 32 + 255) / 256), 256, 0, st, M, S, run_col, run_w32, dI, dJ,
+                part);
   if (nst > 0)
-    EPHB_LAUNCH(k_corr_finalize, unsigned((nst + 255) / 256), 256, 0, st, nst, S, part, r, inv_ffW, d_out);
+    EPHB_LAUNCH(k_corr_finalize, unsigned((nst + 255) / 256), 256, 0, st, nst, S, part, rI, rJ, inv_ffW, dI_out,
+                dJ_out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_corr_apply(int64_t nst, const float4 *d, double *I, double *J, cudaStream_t st) {
-  if (nst == 0) return cudaSuccess;
-  EPHB_LAUNCH(k_corr_apply, unsigned((nst + 255) / 256), 256, 0, st, nst, d, I, J);
+cudaError_t launch_corr_apply(int64_t nst, const float *dI, const float *dJ, double *I, double *J, cudaStream_t st) {
+  const int64_t n3 = nst * 3;
+  if (n3 == 0) return cudaSuccess;
+  EPHB_LAUNCH(k_corr_apply, unsigned((n3 + 255) / 256), 256, 0, st, n3, dI, dJ, I, J);
   return cudaGetLastError();
 }
 
 cudaError_t launch_drag_term(const MeshDev &D, const BteDev &B, const SweepSegs &S, const double *F, const double *G,
-                             double *part, double *Dterm, cudaStream_t st, const double2 *FG) {
+                             double *part, double *Dterm, cudaStream_t st) {
   if (B.nst == 0) return cudaSuccess;
-  if (S.nseg > 0)
-    EPHB_LAUNCH(k_drag_sweep_seg, unsigned((S.nseg * 32 + 255) / 256), 256, 0, st, D, B, S, F, G, FG, part);
+  if (S.nseg > 0) EPHB_LAUNCH(k_drag_sweep_seg, unsigned((S.nseg * 32 + 255) / 256), 256, 0, st, D, B, S, F, G, part);
   EPHB_LAUNCH(k_drag_finalize, unsigned((B.nst + 255) / 256), 256, 0, st, B.nst, S, part, Dterm);
   return cudaGetLastError();
 }
@@ -1005,9 +980,8 @@ cudaError_t launch_ph_sweep(const ModelDev &M, const MeshDev &D, const BteDev &B
 }
 
 cudaError_t launch_ph_update(const ModelDev &M, const MeshDev &D, const BteDev &B, const double *Btv,
-                             const double *F0, const double *inv_nnW, double *F, double *G, cudaStream_t st,
-                             double2 *FG) {
-  EPHB_LAUNCH(k_ph_update, unsigned((D.nq * M.nbr + 255) / 256), 256, 0, st, M, D, B, Btv, F0, inv_nnW, F, G, FG);
+                             const double *F0, const double *inv_nnW, double *F, double *G, cudaStream_t st) {
+  EPHB_LAUNCH(k_ph_update, unsigned((D.nq * M.nbr + 255) / 256), 256, 0, st, M, D, B, Btv, F0, inv_nnW, F, G);
   return cudaGetLastError();
 }
 

@@ -224,14 +224,12 @@ cudaError_t launch_self_sweep(const ModelDev &M, const BteDev &B, const SweepSeg
 // finalisation writes both layouts.
 cudaError_t launch_pack_ij(int64_t nst, const double *I, const double *J, double2 *IJ, cudaStream_t st);
 // Drag term of every row for the current F, G: Dterm[st][6].
-// (FG: optional packed copy of F, G written by launch_ph_update, gathered instead of F, G.)
 cudaError_t launch_drag_term(const MeshDev &D, const BteDev &B, const SweepSegs &S, const double *F, const double *G,
-                             double *part, double *Dterm, cudaStream_t st, const double2 *FG = nullptr);
+                             double *part, double *Dterm, cudaStream_t st);
 cudaError_t launch_ph_sweep(const ModelDev &M, const MeshDev &D, const BteDev &B, const int2 *kinfo, const double *I,
                             const double *J, double *Btv, cudaStream_t st);
 cudaError_t launch_ph_update(const ModelDev &M, const MeshDev &D, const BteDev &B, const double *Btv,
-                             const double *F0, const double *inv_nnW, double *F, double *G, cudaStream_t st,
-                            double2 *FG = nullptr);
+                             const double *F0, const double *inv_nnW, double *F, double *G, cudaStream_t st);
 // Coefficient tensors: fixed-count partial sums (electron: 36 per block, phonon: 18 per
 // block) and a single-block finalisation into `res`.
 //   res layout: [0] sigma [9] sigmaS [18] alpha_el [27] kappa0_el [36] alpha_ph [45] kappa_ph
@@ -241,16 +239,16 @@ int coeff_partials();
 cudaError_t launch_e_partial(const BteDev &B, const double *I, const double *J, double *epart, cudaStream_t st);
 cudaError_t launch_ph_partial(const MeshDev &D, const BteDev &B, const double *F, const double *G, double *ppart,
                               cudaStream_t st);
-// Mixed-precision electron loop: FP32 run words (partner | op, weight), the correction start
-// r = x' - x (d = r), one FP32 correction sweep d_out = r + (1/(f(1-f)W)) sum_runs w d[partner],
-// and x += d.  r and d are packed per state as two float4 (dI0 dI1 dI2 dJ0 | dJ1 dJ2 0 0).
-cudaError_t launch_runs32(int64_t n, const uint32_t *col, const double *w, uint2 *out, cudaStream_t st);
+// Mixed-precision electron loop: FP32 copies, the correction start r = x' - x (d = r), one FP32
+// correction sweep d_out = r + (1/(f(1-f)W)) sum_runs w d[partner], and x += d.
+cudaError_t launch_to_f32(int64_t n, const double *a, float *b, cudaStream_t st);
 cudaError_t launch_corr_init(int64_t nst, const double *I1, const double *I0x, const double *J1, const double *J0x,
-                             float4 *r, float4 *d, cudaStream_t st);
-cudaError_t launch_corr_sweep(const ModelDev &M, int64_t nst, const SweepSegs &S, const uint2 *runs,
-                              const double *inv_ffW, const float4 *r, const float4 *d, float *part, float4 *d_out,
+                             float *rI, float *rJ, float *dI, float *dJ, cudaStream_t st);
+cudaError_t launch_corr_sweep(const ModelDev &M, int64_t nst, const SweepSegs &S, const uint32_t *run_col,
+                              const float *run_w32, const double *inv_ffW, const float *rI, const float *rJ,
+                              const float *dI, const float *dJ, float *part, float *dI_out, float *dJ_out,
                               cudaStream_t st);
-cudaError_t launch_corr_apply(int64_t nst, const float4 *d, double *I, double *J, cudaStream_t st);
+cudaError_t launch_corr_apply(int64_t nst, const float *dI, const float *dJ, double *I, double *J, cudaStream_t st);
 // Warm start: network inputs per state (kNFeat floats), training targets (2 floats: the
 // converged I, J along the RTA direction J0 = v/W), and starting responses from them.
 constexpr int kNFeat = 6;
