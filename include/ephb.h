@@ -209,10 +209,14 @@ typedef enum { EPHB_RTA = 0, EPHB_PARTIAL = 1, EPHB_DRAGLESS = 2, EPHB_DRAGGED =
 /* Arithmetic of the electron loop.
  *   EPHB_SOLVE_FP64   plain FP64 Jacobi sweeps (the paper's iteration).
  *   EPHB_SOLVE_MIXED  iterative refinement: every FP64 sweep x' = b + A x supplies the
- *                     residual r = x' - x and the same convergence test as the plain loop; then
+ *                     residual r = x' - x and the convergence test of the electron loop; then
  *                     12 FP32 sweeps of d <- r + A d (FP32 run weights) and x <- x + d before the
- *                     next FP64 sweep.  Same fixed point; fewer FP64 sweeps.  The phonon sweeps,
- *                     drag terms, KO step and coefficients stay FP64. */
+ *                     next FP64 sweep.  At the dragged level the electron loop of an outer
+ *                     iteration stops at 1e-2 of the previous outer residual (1e-2 in the
+ *                     first), never before inner_tol, and the solve ends only after an outer
+ *                     iteration whose electron loop reached inner_tol.  Same fixed point and
+ *                     outer test; fewer sweeps.  The phonon sweeps, drag terms, KO step and
+ *                     coefficients stay FP64. */
 typedef enum { EPHB_SOLVE_FP64 = 0, EPHB_SOLVE_MIXED = 1 } ephb_solve_precision;
 
 typedef struct {

@@ -1032,6 +1032,8 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
   int64_t sweeps = 0;
   bool converged = o->level == EPHB_RTA;
   double residual = 0.0, lambda = 1.0;
+  bool outer_seen = false;   // an outer residual exists (mixed precision's inexact inner solves)
+  double last_tol_k = 0.0;   // tolerance of the last electron loop (mixed precision)
   EventTimer te, tp, td;
   EventTimer tsw[kSweepBatch];   // the self-term kernel of each queued sweep
   EventTimer tc32;               // FP32 correction sweeps (mixed precision)
@@ -1047,6 +1049,12 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
   // and x <- x + d, before the next FP64 sweep.
   auto inner_loop_mixed = [&](int drag, bool &ok) -> ephb_status {
     ok = false;
+    // inexact inner solves while the outer iteration is far from converged: the electron loop
+    // stops at 1e-2 of the last outer residual, but never before inner_tol, so the final outer
+    // iterations (residual near tol) still bring the electrons to inner_tol
+    const double tol_k = o->level != EPHB_DRAGGED ? inner_tol
+                                                  : std::max(inner_tol, outer_seen ? 1e-2 * residual : 1e-2);
+    last_tol_k = tol_k;
     const int64_t n3 = nst * 3;
     if (!ctx->have_f32) {
       CK(ctx->run_w32.ensure(ctx->nruns));
@@ -1079,7 +1087,7 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
       CK(tsw[0].collect());
       ++sweeps;
       ++inner_total;
-      if (ctx->host_res[72] < inner_tol) {   // x' is the answer
+      if (ctx->host_res[72] < tol_k) {   // x' is the answer
         std::swap(ctx->I.p, ctx->I2.p);
         std::swap(ctx->J.p, ctx->J2.p);
         B = bte_view(ctx);
@@ -1205,7 +1213,9 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
       s = coefficients_to_host(ctx, ctx->prev_out.p);
       if (s != EPHB_OK) return s;
       residual = ctx->host_res[73];
-      if (o->level == EPHB_PARTIAL || residual < tol) {
+      outer_seen = true;
+      // an outer iteration whose electron loop stopped early does not end the iteration
+      if (o->level == EPHB_PARTIAL || (residual < tol && last_tol_k <= inner_tol)) {
         converged = true;
         break;
       }
