@@ -178,6 +178,58 @@ def model_sc1(seed: int = SEED_BASE + 1, a: float = 3.0, t_eV: float = 1.0,
 
 
 # --------------------------------------------------------------------------------------
+# Model 3: 8 s-like bands on a simple cubic lattice with the full O_h symmetry
+# --------------------------------------------------------------------------------------
+
+def model_sc8(seed: int = SEED_BASE + 3, a: float = 3.0, omega_max_eV: float = 0.060,
+              g0_eV: float = 0.01) -> WannierModel:
+    """Eight s-like orbitals on one simple-cubic site: four "valence" orbitals with on-site
+    energies near -1.2 eV and four "conduction" orbitals near +0.4 eV, hoppings on the
+    nearest, edge and corner shells (one real symmetric 8x8 matrix per shell, amplitude
+    0.25 eV exp(-|R|/a), the same for every R of a shell, so H(SR) = H(R) for all 48
+    operations); the one-atom nearest-neighbour springs of model 1 (w_max 60 meV); real
+    couplings g0 exp(-(|Re|+|Rp|)/a) on 3^3 x 3^3 grids, made O_h covariant by the group
+    average g^a(Re,Rp) <- (1/48) sum_S sum_b S_ba g^b(S Re, S Rp) and Hermitian-pair
+    symmetric.  Real hoppings and couplings keep time-reversal symmetry."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nb = 8
+    lattice = a * np.eye(3)
+    grid = cube_grid(1)
+    shell = np.abs(grid).sum(axis=1)          # 0 on-site, 1 faces, 2 edges, 3 corners
+    onsite = np.concatenate([-1.2 + 0.15 * rng.uniform(-1, 1, 4), 0.4 + 0.15 * rng.uniform(-1, 1, 4)])
+    t = np.zeros((4, nb, nb))
+    c0 = rng.normal(0.0, 0.05, (nb, nb))
+    t[0] = np.diag(onsite) + 0.5 * (c0 + c0.T) - np.diag(np.diag(0.5 * (c0 + c0.T)))
+    for sh in (1, 2, 3):
+        m = rng.normal(0.0, 1.0, (nb, nb))
+        t[sh] = 0.25 * np.exp(-np.sqrt(sh)) * 0.5 * (m + m.T)
+    H_R = np.array([t[sh] for sh in shell], dtype=np.complex128)
+    # phonons: model 1's nearest-neighbour springs
+    nn = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], dtype=np.int32)
+    W2 = omega_max_eV ** 2
+    D_R = np.zeros((7, 3, 3), dtype=np.complex128)
+    D_R[0] = 0.5 * W2 * np.eye(3)
+    for i, r in enumerate(nn[1:], start=1):
+        ax = int(np.nonzero(r)[0][0])
+        D_R[i, ax, ax] = -0.25 * W2
+    # couplings: random, decaying, then the O_h group average (covariant in the displacement)
+    ops = oh_group()
+    idx = _index_of(grid)
+    dec = np.exp(-(np.linalg.norm(grid, axis=1)[:, None] + np.linalg.norm(grid, axis=1)[None, :]))
+    g = rng.normal(0.0, 1.0, (27, 27, nb, nb, 3)) * (g0_eV * dec)[:, :, None, None, None]
+    gs = np.zeros_like(g)
+    for S in ops:
+        perm = np.array([idx[tuple(S @ r)] for r in grid])   # index of S R
+        gs += np.einsum("ba,xymnb->xymna", S.astype(np.float64), g[perm][:, perm])
+    gs /= len(ops)
+    gs = hermitian_pair_symmetrise(gs.astype(np.complex128), grid, grid)
+    return WannierModel(lattice=lattice, mass_amu=np.array([28.0855]), tau_cart=np.zeros((1, 3)), nb=nb,
+                        Re=grid.copy(), H_R=H_R, Rd=nn.copy(), D_R=D_R, Rge=grid.copy(), Rgp=grid.copy(), g_R=gs,
+                        omega_ref_eV=omega_max_eV, sym_rot=ops, sym_cart=ops.astype(np.float64),
+                        bg_omega_ref_eV=omega_max_eV)
+
+
+# --------------------------------------------------------------------------------------
 # Model 2: 4-band seeded random Hamiltonian, 2-atom CsCl-type cubic basis, 6 branches
 # --------------------------------------------------------------------------------------
 
@@ -264,6 +316,18 @@ def workload_sc1(n: int = 8, nsym_full: bool = True, T_K: float = 300.0) -> Work
     mu = 0.3
     return Workload(name=f"sc1-{n}^3", model=m, kmesh=(n, n, n), qmesh=(n, n, n), T_K=T_K, mu_eV=mu,
                     window=(mu - 0.4, mu + 0.4), tol=1e-10)
+
+
+def workload_sc8(n: int = 6, nsym_full: bool = True, T_K: float = 300.0, ratio: int = 1) -> Workload:
+    """Eight-band O_h case: n^3 k mesh, (n/ratio)^3 q mesh, mu = 0.2 eV, window mu +- 0.35 eV
+    (the lower edge of the conduction group), T = 300 K."""
+    m = model_sc8()
+    if not nsym_full:
+        m = dataclasses.replace(m, sym_rot=identity_group(), sym_cart=identity_group().astype(np.float64))
+    mu = 0.2
+    q = n // ratio
+    return Workload(name=f"sc8-{n}^3", model=m, kmesh=(n, n, n), qmesh=(q, q, q), T_K=T_K, mu_eV=mu,
+                    window=(mu - 0.35, mu + 0.35), tol=1e-10)
 
 
 def workload_cscl4(n: int = 24, T_K: float = 300.0) -> Workload:

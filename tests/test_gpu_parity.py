@@ -28,6 +28,9 @@ def _cases():
         "cscl4-6": cs,
         "cscl4-ragged": dataclasses.replace(cs, name="cscl4-6x4x5", kmesh=(6, 4, 5), qmesh=(6, 4, 5)),
         "cscl4-ratio2": dataclasses.replace(cs, name="cscl4-k8-q4", kmesh=(8, 8, 8), qmesh=(4, 4, 4)),
+        # eight bands under O_h, on equal meshes and with the k mesh twice the q mesh
+        "sc8-oh": S.workload_sc8(6),
+        "sc8-k8-q4": S.workload_sc8(8, ratio=2),
     }
 
 
