@@ -616,7 +616,8 @@ def main():
                           "solve": r0.solve["ms"], "e_sweeps": r0.solve["ms_e_sweep"],
                           "self_sweep_kernel": r0.solve["ms_self_kernel"], "n_runs": r0.solve["n_runs"],
                           "drag_terms": r0.solve["ms_drag"], "ph_sweeps": r0.solve["ms_ph_sweep"],
-                          "n_sweeps": r0.solve["n_sweeps"], "outer_iters": r0.solve["outer_iters"]},
+                          "n_sweeps": r0.solve["n_sweeps"], "outer_iters": r0.solve["outer_iters"],
+                          "outer_iters32": r0.solve["outer_iters32"]},
             "variants": variants, "batched": batched, "warm_start": warm,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         }

@@ -247,6 +247,9 @@ typedef struct {
   double e_sweep_flops;        /* algorithmic FP64 flops of one self-term sweep            */
   int64_t n_sweeps32;          /* FP32 correction sweeps (EPHB_SOLVE_MIXED)                */
   double ms_corr;              /* device time of the FP32 corrections                      */
+  int outer_iters32;           /* outer iterations whose phonon scatter and drag term ran in
+                                  FP32 (EPHB_SOLVE_MIXED, dragged level: those begun with the
+                                  outer residual at or above 1e-5; never the last one)      */
 } ephb_solve_info;
 
 /* Solves every instance.  `out` (optional) sums the counts and device times over the

@@ -92,7 +92,7 @@ class SolveInfoC(C.Structure):
                 ("n_sweeps", C.c_int64), ("ms", C.c_double), ("ms_e_sweep", C.c_double),
                 ("ms_ph_sweep", C.c_double), ("e_sweep_bytes", C.c_double), ("ms_drag", C.c_double),
                 ("n_runs", C.c_int64), ("ms_self_kernel", C.c_double), ("e_sweep_flops", C.c_double),
-                ("n_sweeps32", C.c_int64), ("ms_corr", C.c_double)]
+                ("n_sweeps32", C.c_int64), ("ms_corr", C.c_double), ("outer_iters32", C.c_int)]
 
 
 class CoeffsC(C.Structure):

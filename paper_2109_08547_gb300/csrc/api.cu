@@ -182,6 +182,10 @@ struct ephb_ctx : InstState {
   DBuf<double2> u_X;
   DBuf<int> u_ph_st;
   DBuf<double> u_ph_V;
+  // mixed iteration, early outer iterations: FP32 copies of the instance's rates (X, Y) and of
+  // the responses ([state][I | J]) and phonon deviations ([mode][F | G]); rebuilt per solve
+  DBuf<float2> X32;
+  DBuf<float> Y32, IJ32, FG32;
 
   // instances: the one in use lives in the InstState base, the others in slots
   int ninst = 1, cur = 0;
@@ -997,6 +1001,7 @@ ephb_status coefficients_to_host(ephb_ctx *ctx, double *prev, bool electron = tr
 
 constexpr int kSweepBatch = 8;   // electron sweeps queued per host round trip
 constexpr int kCorrSweeps = 12;  // FP32 correction sweeps per FP64 sweep (mixed precision)
+constexpr double kPh32Until = 1e-5;  // outer residual below which the phonon-side terms are FP64
 
 namespace {
 
@@ -1047,6 +1052,22 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
   // Mixed precision: each FP64 sweep x' = b + A x gives the residual (and the convergence test,
   // the same as the plain loop's); then kCorrSweeps FP32 sweeps of d <- r + A d, r = x' - x,
   // and x <- x + d, before the next FP64 sweep.
+  // Mixed precision, dragged level: while the outer residual is above kPh32Until the phonon
+  // scatter and the drag term run in FP32 (their error is far below the residual of those
+  // iterations); the solve ends only after an outer iteration with both in FP64.
+  const bool ph32_allowed = o->precision == EPHB_SOLVE_MIXED && o->level == EPHB_DRAGGED;
+  bool ph32 = false;
+  int outer32 = 0;
+  if (ph32_allowed) {
+    CK(ctx->X32.ensure(ctx->n_entries));
+    CK(ctx->Y32.ensure(ctx->n_ph_entries));
+    CK(ctx->IJ32.ensure(nst * 6));
+    CK(ctx->FG32.ensure(nph * 6));
+    CK(launch_copy_f32(2 * ctx->n_entries, reinterpret_cast<const double *>(ctx->e_X.p),
+                       reinterpret_cast<float *>(ctx->X32.p), st));
+    CK(launch_copy_f32(ctx->n_ph_entries, ctx->ph_Y.p, ctx->Y32.p, st));
+  }
+
   auto inner_loop_mixed = [&](int drag, bool &ok) -> ephb_status {
     ok = false;
     // inexact inner solves while the outer iteration is far from converged: the electron loop
@@ -1068,7 +1089,10 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
     if (r != EPHB_OK) return r;
     if (drag) {
       CK(td.start(st));
-      CK(launch_drag_term(D, B, entry_segs(ctx), ctx->F.p, ctx->G.p, ctx->seg_part.p, ctx->Dterm.p, st));
+      if (ph32)
+        CK(launch_drag_term32(D, B, entry_segs(ctx), ctx->X32.p, ctx->FG32.p, ctx->seg_part.p, ctx->Dterm.p, st));
+      else
+        CK(launch_drag_term(D, B, entry_segs(ctx), ctx->F.p, ctx->G.p, ctx->seg_part.p, ctx->Dterm.p, st));
       CK(td.stop(st));
     }
     const SweepSegs S = run_segs(ctx);
@@ -1196,10 +1220,18 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
     residual = ctx->host_res[72];
   } else if (o->level == EPHB_DRAGGED || o->level == EPHB_PARTIAL) {
     for (outer = 1; outer <= o->max_outer; ++outer) {
+      ph32 = ph32_allowed && (!outer_seen || residual >= kPh32Until);
+      outer32 += ph32 ? 1 : 0;
       CK(tp.start(st));
-      CK(launch_ph_sweep(M, D, B, ctx->kinfo.p, ctx->I.p, ctx->J.p, ctx->Btv.p, st));
+      if (ph32) {
+        CK(launch_pack6_f32(nst, ctx->I.p, ctx->J.p, ctx->IJ32.p, st));
+        CK(launch_ph_sweep32(M, B, ctx->kinfo.p, ctx->Y32.p, ctx->IJ32.p, ctx->Btv.p, st));
+      } else {
+        CK(launch_ph_sweep(M, D, B, ctx->kinfo.p, ctx->I.p, ctx->J.p, ctx->Btv.p, st));
+      }
       CK(tp.stop(st));
       CK(launch_ph_update(M, D, B, ctx->Btv.p, ctx->F0.p, ctx->inv_nnW.p, ctx->F.p, ctx->G.p, st));
+      if (ph32) CK(launch_pack6_f32(nph, ctx->F.p, ctx->G.p, ctx->FG32.p, st));
       bool ok;
       s = inner_loop(1, ok);
       if (s != EPHB_OK) return s;
@@ -1215,7 +1247,7 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
       residual = ctx->host_res[73];
       outer_seen = true;
       // an outer iteration whose electron loop stopped early does not end the iteration
-      if (o->level == EPHB_PARTIAL || (residual < tol && last_tol_k <= inner_tol)) {
+      if (o->level == EPHB_PARTIAL || (residual < tol && last_tol_k <= inner_tol && !ph32)) {
         converged = true;
         break;
       }
@@ -1245,6 +1277,7 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
     out->ms_self_kernel = ms_self;
     out->n_sweeps32 = sweeps32;
     out->ms_corr = tc32.ms;
+    out->outer_iters32 = outer32;
     // FP64 work of one self-term sweep: 6 multiply-adds per run (+ two 3x3 rotations with symmetry)
     out->e_sweep_flops = double(ctx->nruns) * (ctx->M.nsym > 1 ? 12.0 + 36.0 : 12.0);
     out->ms_ph_sweep = tp.ms;
@@ -1310,6 +1343,7 @@ ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb
     sum.ms_self_kernel += one.ms_self_kernel;
     sum.n_sweeps32 += one.n_sweeps32;
     sum.ms_corr += one.ms_corr;
+    sum.outer_iters32 = std::max(sum.outer_iters32, one.outer_iters32);
     sum.e_sweep_flops += one.e_sweep_flops;
   }
   select_instance(ctx, 0);

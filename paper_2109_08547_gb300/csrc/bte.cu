@@ -318,6 +318,48 @@ __global__ void __launch_bounds__(256) k_drag_sweep_seg(MeshDev D, BteDev B, Swe
     for (int c = 0; c < 6; ++c) part[g * 6 + c] = a[c];
 }
 
+// FP32 form of the drag term (mixed iteration while the outer residual is large): the same
+// sums from FP32 copies of the rates (X32) and of F, G (FG32: [mode][F0 F1 F2 G0 G1 G2]).
+__global__ void __launch_bounds__(256) k_drag_sweep_seg32(MeshDev D, BteDev B, SweepSegs S,
+                                                          const float2 *__restrict__ X32,
+                                                          const float *__restrict__ FG32, double *__restrict__ part) {
+  const int64_t g = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= S.nseg) return;
+  const int st = S.seg_row[g];
+  const int64_t b = S.seg_begin[g];
+  const int64_t rend = S.row_ptr[st + 1];
+  const int64_t e_end = b + kSeg < rend ? b + kSeg : rend;
+  const int nbr = B.nbr;
+  const uint32_t kc = B.kcrd[D.ibzw_list[st / B.nb]];
+  const int k0 = kc & 1023u, k1 = (kc >> 10) & 1023u, k2 = kc >> 20;
+  const bool unit_ratio = D.ratio[0] == 1 && D.ratio[1] == 1 && D.ratio[2] == 1;
+  float a[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t e = b + lane; e < e_end; e += 32) {
+    const uint32_t pk = __ldcs(B.e_kpns + e);
+    const float2 X = __ldcs(X32 + e);
+    const int kp = unpack_kp(pk), s = unpack_s(pk);
+    const uint32_t pc = B.kcrd[kp];
+    int d0 = int(pc & 1023u) - k0, d1 = int((pc >> 10) & 1023u) - k1, d2 = int(pc >> 20) - k2;
+    d0 += d0 < 0 ? D.km.n[0] : 0;
+    d1 += d1 < 0 ? D.km.n[1] : 0;
+    d2 += d2 < 0 ? D.km.n[2] : 0;
+    if (!unit_ratio) {
+      d0 /= D.ratio[0];
+      d1 /= D.ratio[1];
+      d2 /= D.ratio[2];
+    }
+    const int64_t q = D.qm.flat(d0, d1, d2);
+    const int64_t mq = D.qm.flat(d0 ? D.qm.n[0] - d0 : 0, d1 ? D.qm.n[1] - d1 : 0, d2 ? D.qm.n[2] - d2 : 0);
+    const float *pq = FG32 + (q * nbr + s) * 6, *pm = FG32 + (mq * nbr + s) * 6;
+    for (int c = 0; c < 6; ++c) a[c] = fmaf(pm[c], X.y, fmaf(-pq[c], X.x, a[c]));
+  }
+  for (int c = 0; c < 6; ++c)
+    for (int o = 16; o > 0; o >>= 1) a[c] += __shfl_down_sync(0xffffffffu, a[c], o);
+  if (lane == 0)
+    for (int c = 0; c < 6; ++c) part[g * 6 + c] = double(a[c]);
+}
+
 // Dterm[st] = sum of the row's drag segment partials (in segment order)
 __global__ void k_drag_finalize(int64_t nst, SweepSegs S, const double *part, double *Dterm) {
   int64_t st = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
@@ -329,6 +371,62 @@ __global__ void k_drag_finalize(int64_t nst, SweepSegs S, const double *part, do
 }
 
 // One warp per phonon row (q,s): Btv = sum Y/|stab| (S_k' I_<k'>n - I_km), fields I and J.
+// FP32 form of the phonon drag scatter (mixed iteration while the outer residual is large),
+// from FP32 copies of Y and of the responses (IJ32: [state][I0 I1 I2 J0 J1 J2]).
+template <bool SYM>
+__global__ void __launch_bounds__(256) k_ph_sweep32(ModelDev M, BteDev B, const int2 *__restrict__ kinfo,
+                                                    const float *__restrict__ Y32, const float *__restrict__ IJ32,
+                                                    double *Btv) {
+  __shared__ float C[kMaxSym * 9];
+  if (SYM) {
+    for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) C[t] = float(M.sym_cart[t]);
+    __syncthreads();
+  }
+  const int64_t row = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= B.nq * B.nbr) return;
+  float a[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t e = B.ph_row_ptr[row] + lane; e < B.ph_row_ptr[row + 1]; e += 32) {
+    const int st = B.ph_st[e];
+    const uint32_t pk = B.ph_kpn[e];
+    const float y = Y32[e];
+    const int2 inf = kinfo[unpack_kp(pk)];
+    const float *own = IJ32 + int64_t(st) * 6;
+    float r[6] = {0, 0, 0, 0, 0, 0};
+    if (inf.x >= 0) {   // inf.x < 0: see the electron sweep
+      const float *src = IJ32 + (int64_t(inf.x) + unpack_n(pk)) * 6;
+      if (SYM) {
+        const float *Cs = C + 9 * (inf.y > 0 ? inf.y : 0);
+        for (int f = 0; f < 2; ++f)
+          for (int x = 0; x < 3; ++x)
+            r[3 * f + x] = Cs[3 * x] * src[3 * f] + Cs[3 * x + 1] * src[3 * f + 1] + Cs[3 * x + 2] * src[3 * f + 2];
+      } else {
+        for (int c = 0; c < 6; ++c) r[c] = src[c];
+      }
+    }
+    for (int c = 0; c < 6; ++c) a[c] = fmaf(y, r[c] - own[c], a[c]);
+  }
+  for (int c = 0; c < 6; ++c)
+    for (int o = 16; o > 0; o >>= 1) a[c] += __shfl_down_sync(0xffffffffu, a[c], o);
+  if (lane == 0)
+    for (int c = 0; c < 6; ++c) Btv[row * 6 + c] = double(a[c]);
+}
+
+// FP32 copies: out[i][0..2] = A[i][0..2], out[i][3..5] = B[i][0..2]; and plain element copies
+__global__ void k_pack6_f32(int64_t n, const double *A, const double *Bv, float *out) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  for (int c = 0; c < 3; ++c) {
+    out[i * 6 + c] = float(A[i * 3 + c]);
+    out[i * 6 + 3 + c] = float(Bv[i * 3 + c]);
+  }
+}
+
+__global__ void k_copy_f32(int64_t n, const double *a, float *b) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i < n) b[i] = float(a[i]);
+}
+
 template <bool SYM>
 __global__ void __launch_bounds__(256) k_ph_sweep(ModelDev M, MeshDev D, BteDev B, const int2 *__restrict__ kinfo,
                                                   const double *__restrict__ I, const double *__restrict__ J,
@@ -958,6 +1056,37 @@ cudaError_t launch_corr_apply(int64_t nst, const float *dI, const float *dJ, dou
   const int64_t n3 = nst * 3;
   if (n3 == 0) return cudaSuccess;
   EPHB_LAUNCH(k_corr_apply, unsigned((n3 + 255) / 256), 256, 0, st, n3, dI, dJ, I, J);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_drag_term32(const MeshDev &D, const BteDev &B, const SweepSegs &S, const float2 *X32,
+                               const float *FG32, double *part, double *Dterm, cudaStream_t st) {
+  if (B.nst == 0) return cudaSuccess;
+  if (S.nseg > 0)
+    EPHB_LAUNCH(k_drag_sweep_seg32, unsigned((S.nseg * 32 + 255) / 256), 256, 0, st, D, B, S, X32, FG32, part);
+  EPHB_LAUNCH(k_drag_finalize, unsigned((B.nst + 255) / 256), 256, 0, st, B.nst, S, part, Dterm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ph_sweep32(const ModelDev &M, const BteDev &B, const int2 *kinfo, const float *Y32,
+                              const float *IJ32, double *Btv, cudaStream_t st) {
+  const unsigned g = unsigned((B.nq * B.nbr * 32 + 255) / 256);
+  if (M.nsym > 1)
+    EPHB_LAUNCH(k_ph_sweep32<true>, g, 256, 0, st, M, B, kinfo, Y32, IJ32, Btv);
+  else
+    EPHB_LAUNCH(k_ph_sweep32<false>, g, 256, 0, st, M, B, kinfo, Y32, IJ32, Btv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack6_f32(int64_t n, const double *A, const double *Bv, float *out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  EPHB_LAUNCH(k_pack6_f32, unsigned((n + 255) / 256), 256, 0, st, n, A, Bv, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_f32(int64_t n, const double *a, float *b, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  EPHB_LAUNCH(k_copy_f32, unsigned((n + 255) / 256), 256, 0, st, n, a, b);
   return cudaGetLastError();
 }
 

@@ -249,6 +249,15 @@ cudaError_t launch_corr_sweep(const ModelDev &M, int64_t nst, const SweepSegs &S
                               const float *dI, const float *dJ, float *part, float *dI_out, float *dJ_out,
                               cudaStream_t st);
 cudaError_t launch_corr_apply(int64_t nst, const float *dI, const float *dJ, double *I, double *J, cudaStream_t st);
+// FP32 forms of the phonon-side terms for the mixed iteration's early outer iterations:
+// drag term from X32 (float2 per entry) and FG32 ([mode][F | G] floats), phonon scatter from
+// Y32 (float per phonon entry) and IJ32 ([state][I | J] floats); pack6: out[i] = (A[i], B[i]).
+cudaError_t launch_drag_term32(const MeshDev &D, const BteDev &B, const SweepSegs &S, const float2 *X32,
+                               const float *FG32, double *part, double *Dterm, cudaStream_t st);
+cudaError_t launch_ph_sweep32(const ModelDev &M, const BteDev &B, const int2 *kinfo, const float *Y32,
+                              const float *IJ32, double *Btv, cudaStream_t st);
+cudaError_t launch_pack6_f32(int64_t n, const double *A, const double *Bv, float *out, cudaStream_t st);
+cudaError_t launch_copy_f32(int64_t n, const double *a, float *b, cudaStream_t st);
 // Warm start: network inputs per state (kNFeat floats), training targets (2 floats: the
 // converged I, J along the RTA direction J0 = v/W), and starting responses from them.
 constexpr int kNFeat = 6;

@@ -25,9 +25,29 @@ def test_mixed_solve_matches_oracle(name, level):
         mixed = B.run_path(ctx, wl, level=level, solve_precision="mixed")
     assert mixed.solve["converged"] == 1 and ref.converged
     assert mixed.solve["n_sweeps32"] > 0
+    # dragged: the early outer iterations take FP32 phonon-side terms, the last one FP64
+    if level == "dragged":
+        assert 0 < mixed.solve["outer_iters32"] < mixed.solve["outer_iters"]
+    else:
+        assert mixed.solve["outer_iters32"] == 0
     assert mixed.solve["n_sweeps"] < plain.solve["n_sweeps"], (mixed.solve["n_sweeps"], plain.solve["n_sweeps"])
     for key in TENSORS:
         assert rel_fro(mixed.coeffs[key], ref.coeffs[key]) <= COEFF_RTOL, key
+
+
+def test_loose_tolerance_ends_on_fp64_outer_iteration():
+    """A tolerance above the FP32 phonon-side switch point: the solve still ends only after an
+    outer iteration whose phonon scatter and drag term ran in FP64."""
+    import dataclasses
+    wl = dataclasses.replace(SY.workload_cscl4(n=6), tol=1e-4)
+    with B.Context(0) as ctx:
+        B.set_wannier_model(ctx, wl.model)
+        plain = B.run_path(ctx, wl, level="dragged")
+        mixed = B.run_path(ctx, wl, level="dragged", solve_precision="mixed")
+    assert mixed.solve["converged"] == 1 and plain.solve["converged"] == 1
+    assert mixed.solve["outer_iters32"] < mixed.solve["outer_iters"]
+    for key in TENSORS:
+        assert rel_fro(mixed.coeffs[key], plain.coeffs[key]) <= 1e-3, key
 
 
 def test_bad_solve_precision():
