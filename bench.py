@@ -54,6 +54,8 @@ def parse():
                    help="electron loop: plain FP64 sweeps, or FP64 residual sweeps with FP32 corrections "
                         "(same fixed point)")
     p.add_argument("--no-variants", action="store_true", help="skip the one-step timings of the other precisions")
+    p.add_argument("--accel", type=int, default=3,
+                   help="Anderson history depth of the outer iteration (0: the plain iteration)")
     p.add_argument("--instances", type=int, default=8,
                    help="(T, mu, window) instances of the batched-vs-sequential comparison (0: skip it)")
     p.add_argument("--warm", type=int, default=12,
@@ -274,7 +276,7 @@ def batched_block(B, ctx, wl, args, flush, torch, np):
         B.build_meshes_ibz(ctx, wl.kmesh, wl.qmesh, union, wl.degen_tol_eV, wl.omega_min_eV)
         rates = B.compute_transition_rates(ctx, 0.0, 0.0, wl.sigma_eV, wl.cutoff_sigmas, B.PRECISIONS[prec],
                                            instances=insts)
-        solve = B.solve_coupled_bte(ctx, "dragged", wl.tol, solve_precision=solve_prec)
+        solve = B.solve_coupled_bte(ctx, "dragged", wl.tol, solve_precision=solve_prec, accel=args.accel)
         return rates, solve, [B.transport_coefficients(ctx, i) for i in range(len(insts))]
 
     out = {"instances": len(insts), "union_window_eV": list(union), "T_K_range": [100.0, 500.0],
@@ -429,8 +431,8 @@ def main():
 
     prec = B.PRECISIONS[args.precision]
 
-    def step(p=prec, sp=args.solve):
-        return B.run_path(ctx, wl, level="dragged", ko_correction=True, precision=p, solve_precision=sp)
+    def step(p=prec, sp=args.solve, acc=args.accel):
+        return B.run_path(ctx, wl, level="dragged", ko_correction=True, precision=p, solve_precision=sp, accel=acc)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -552,7 +554,7 @@ def main():
             flush.zero_()
             B.set_wannier_model(ctx2, mp)
             rr = B.run_path(ctx2, wl, level="dragged", ko_correction=True, precision=prec,
-                            solve_precision=args.solve)
+                            solve_precision=args.solve, accel=args.accel)
             tup += rr.rates["n_tuples"]
         torch.cuda.synchronize()
         barrier()
@@ -567,15 +569,17 @@ def main():
     # result (which itself matches the FP64 oracle to 1e-8 in the parity tests)
     variants = {}
     if not args.no_variants:
-        cases = [(f"{name}+{sp}-solve", p, sp) for name, p in B.PRECISIONS.items() for sp in ("fp64", "mixed")
-                 if (name, sp) != (args.precision, args.solve)]
-        for name, p, sp in cases:
+        cases = [(f"{name}+{sp}-solve", p, sp, args.accel) for name, p in B.PRECISIONS.items()
+                 for sp in ("fp64", "mixed") if (name, sp) != (args.precision, args.solve)]
+        if args.accel > 0:   # this run's mode with the plain outer iteration
+            cases.append((f"{args.precision}+{args.solve}-solve+plain-outer", prec, args.solve, 0))
+        for name, p, sp, acc in cases:
             flush.zero_()
-            step(p, sp)                   # warm-up of this mode
+            step(p, sp, acc)              # warm-up of this mode
             flush.zero_()
             torch.cuda.synchronize()
             tv = time.perf_counter()
-            rv = step(p, sp)
+            rv = step(p, sp, acc)
             torch.cuda.synchronize()
             sv = time.perf_counter() - tv
             err = {}
@@ -585,7 +589,8 @@ def main():
             variants[name] = {"s_to_converged": sv, "value": rv.rates["n_tuples"] / sv,
                               "rates_ms": rv.rates["ms"], "stage_b_ms": rv.rates["ms_stage_b"],
                               "solve_ms": rv.solve["ms"], "fp64_sweeps": rv.solve["n_sweeps"],
-                              "fp32_sweeps": rv.solve["n_sweeps32"],
+                              "fp32_sweeps": rv.solve["n_sweeps32"], "outer_iters": rv.solve["outer_iters"],
+                              "outer_accel": acc,
                               "coeff_rel_err": err}
 
     batched = batched_block(B, ctx, wl, args, flush, torch, np) if args.instances > 0 else None
@@ -606,7 +611,8 @@ def main():
             "config": {"workload": wl.name, "model": "4-band/6-branch CsCl-type cubic, 5^3 x 5^3 R grids (g 24 MB)",
                        "kmesh": list(wl.kmesh), "qmesh": list(wl.qmesh), "T_K": wl.T_K, "mu_eV": wl.mu_eV,
                        "window_eV": list(wl.window), "sigma_eV": wl.sigma_eV, "level": "dragged+KO",
-                       "tol": wl.tol, "precision": args.precision, "solve": args.solve, "l2": "256 MB buffer written before every step",
+                       "tol": wl.tol, "precision": args.precision, "solve": args.solve, "outer_accel": args.accel,
+                       "l2": "256 MB buffer written before every step",
                        "parallelism": f"replicas x{world}", "tuples_per_step": r0.rates["n_tuples"],
                        "entries": r0.rates["n_entries"], "pairs": r0.rates["n_pairs"]},
             "s_to_converged": 1e-3 * el_max / args.steps,

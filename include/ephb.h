@@ -215,8 +215,12 @@ typedef enum { EPHB_RTA = 0, EPHB_PARTIAL = 1, EPHB_DRAGLESS = 2, EPHB_DRAGGED =
  *                     iteration stops at 1e-2 of the previous outer residual (1e-2 in the
  *                     first), never before inner_tol, and the solve ends only after an outer
  *                     iteration whose electron loop reached inner_tol.  Same fixed point and
- *                     outer test; fewer sweeps.  The phonon sweeps, drag terms, KO step and
- *                     coefficients stay FP64. */
+ *                     outer test; fewer sweeps.  At the dragged level the phonon scatter and
+ *                     the drag term of an outer iteration begun with the outer residual at or
+ *                     above 1e-5 run in FP32 (FP32 copies of X, Y, I, J, F, G; FP64 partial
+ *                     sums across segments), and the solve ends only after an outer iteration
+ *                     with both in FP64.  The phonon update, KO step and coefficients stay
+ *                     FP64. */
 typedef enum { EPHB_SOLVE_FP64 = 0, EPHB_SOLVE_MIXED = 1 } ephb_solve_precision;
 
 typedef struct {
@@ -227,7 +231,19 @@ typedef struct {
   int ko_correction;           /* 1: apply the Kelvin-Onsager step (dragged levels)        */
   int warm_start;              /* 1: start from ephb_set_warm_start's responses where set   */
   int precision;               /* ephb_solve_precision                                     */
+  int accel_depth;             /* 0: the plain outer iteration (the paper's).  1..EPHB_MAX_ACCEL_DEPTH:
+                                  Anderson acceleration of the outer iteration (dragged level
+                                  only) with that history depth m over the iterate x = (F, G):
+                                  the last m+1 phonon updates g_j and residuals f_j = g_j - x_j
+                                  are kept, and from the third outer iteration on the electrons
+                                  are solved against sum_j alpha_j g_j with alpha minimising
+                                  |sum_j alpha_j f_j| (F and G parts weighted by the first
+                                  residual's) subject to sum_j alpha_j = 1; a singular or
+                                  ill-bounded system falls back to the newest g alone.  Same
+                                  fixed point and convergence test as the plain iteration.
+                                  Outside 0..EPHB_MAX_ACCEL_DEPTH: EPHB_EINVAL.              */
 } ephb_solve_opts;
+#define EPHB_MAX_ACCEL_DEPTH 8
 
 typedef struct {
   int outer_iters;

@@ -39,6 +39,7 @@ EXPORTED = ["ephb_create", "ephb_destroy", "ephb_last_error", "ephb_set_wannier_
             "ephb_mlp_num_params", "ephb_mlp_set_bf16", "ephb_mlp_get_params", "ephb_mlp_set_params",
             "ephb_mlp_forward", "ephb_mlp_loss_grad", "ephb_mlp_train_step", "ephb_set_tuning"]
 NFEAT = 6
+MAX_ACCEL_DEPTH = 8   # EPHB_MAX_ACCEL_DEPTH
 
 _pd = C.POINTER(C.c_double)
 _pi = C.POINTER(C.c_int32)
@@ -83,7 +84,7 @@ class RatesInfoC(C.Structure):
 class SolveOptsC(C.Structure):
     _fields_ = [("level", C.c_int), ("tol", C.c_double), ("inner_tol", C.c_double), ("max_outer", C.c_int),
                 ("max_inner", C.c_int), ("ko_correction", C.c_int), ("warm_start", C.c_int),
-                ("precision", C.c_int)]
+                ("precision", C.c_int), ("accel_depth", C.c_int)]
 
 
 class SolveInfoC(C.Structure):
@@ -316,10 +317,12 @@ def instance_solve_info(ctx: Context, inst: int) -> dict:
 
 
 def solve_coupled_bte(ctx: Context, level="dragged", tol=1e-10, inner_tol=0.0, max_outer=500, max_inner=5000,
-                      ko_correction=True, allow_noconv=False, warm_start=False, solve_precision="fp64") -> dict:
+                      ko_correction=True, allow_noconv=False, warm_start=False, solve_precision="fp64",
+                      accel=0) -> dict:
+    """accel: Anderson history depth of the outer iteration (0: the plain iteration)."""
     o = SolveOptsC(LEVELS[level] if isinstance(level, str) else int(level), float(tol), float(inner_tol),
                    int(max_outer), int(max_inner), 1 if ko_correction else 0, 1 if warm_start else 0,
-                   SOLVE_PRECISIONS[solve_precision])
+                   SOLVE_PRECISIONS[solve_precision], int(accel))
     info = SolveInfoC()
     st = _check(ctx, _lib.ephb_solve_coupled_bte(ctx.handle, C.byref(o), C.byref(info)),
                 allow=(ENOCONV,) if allow_noconv else ())
@@ -388,12 +391,12 @@ class PathResult:
 
 
 def run_path(ctx: Context, wl, level="dragged", ko_correction=True, tol=None, max_outer=500, max_inner=5000,
-             precision=FP64, allow_noconv=False, solve_precision="fp64") -> PathResult:
+             precision=FP64, allow_noconv=False, solve_precision="fp64", accel=0) -> PathResult:
     """The whole hot path for one workload on an existing context whose model is set."""
     mesh = build_meshes_ibz(ctx, wl.kmesh, wl.qmesh, wl.window, wl.degen_tol_eV, wl.omega_min_eV)
     rates = compute_transition_rates(ctx, wl.T_K, wl.mu_eV, wl.sigma_eV, wl.cutoff_sigmas, precision)
     solve = solve_coupled_bte(ctx, level, wl.tol if tol is None else tol, 0.0, max_outer, max_inner, ko_correction,
-                              allow_noconv, solve_precision=solve_precision)
+                              allow_noconv, solve_precision=solve_precision, accel=accel)
     return PathResult(mesh, rates, solve, transport_coefficients(ctx))
 
 

@@ -186,6 +186,8 @@ struct ephb_ctx : InstState {
   // the responses ([state][I | J]) and phonon deviations ([mode][F | G]); rebuilt per solve
   DBuf<float2> X32;
   DBuf<float> Y32, IJ32, FG32;
+  // Anderson acceleration of the outer iteration: ring of phonon updates g and residuals f
+  DBuf<double> and_g, and_f, and_part, and_dots;
 
   // instances: the one in use lives in the InstState base, the others in slots
   int ninst = 1, cur = 0;
@@ -1001,9 +1003,63 @@ ephb_status coefficients_to_host(ephb_ctx *ctx, double *prev, bool electron = tr
 
 constexpr int kSweepBatch = 8;   // electron sweeps queued per host round trip
 constexpr int kCorrSweeps = 12;  // FP32 correction sweeps per FP64 sweep (mixed precision)
+static_assert(kAndMaxSlots == EPHB_MAX_ACCEL_DEPTH + 1, "Anderson ring size");
 constexpr double kPh32Until = 1e-5;  // outer residual below which the phonon-side terms are FP64
 
 namespace {
+
+// Anderson weights over the n ring slots (newest: slot `head`) from their weighted Gram
+// matrix H: alpha_head = 1 - sum gamma, alpha_j = gamma_j, gamma the least-squares solution of
+// min |f_head - sum_j gamma_j (f_head - f_j)| (normal equations, partial pivoting, a 1e-12
+// relative ridge).  False when the system is singular or the weights are out of bounds.
+bool anderson_weights(const double (&H)[kAndMaxSlots][kAndMaxSlots], int n, int head, double *alpha) {
+  int idx[kAndMaxSlots];
+  int m = 0;
+  for (int j = 0; j < n; ++j)
+    if (j != head) idx[m++] = j;
+  for (int j = 0; j < kAndMaxSlots; ++j) alpha[j] = 0.0;
+  alpha[head] = 1.0;
+  if (m == 0) return true;
+  double A[kAndMaxSlots][kAndMaxSlots + 1];
+  const double hh = H[head][head];
+  double tr = 0.0;
+  for (int a = 0; a < m; ++a) {
+    for (int c = 0; c < m; ++c)
+      A[a][c] = hh - H[head][idx[a]] - H[head][idx[c]] + H[idx[a]][idx[c]];
+    A[a][m] = hh - H[head][idx[a]];
+    tr += A[a][a];
+  }
+  if (!(tr > 0) || !std::isfinite(tr)) return false;
+  for (int a = 0; a < m; ++a) A[a][a] += 1e-12 * tr / m;
+  for (int c = 0; c < m; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < m; ++r)
+      if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+    if (!(fabs(A[piv][c]) > 1e-14 * tr)) return false;
+    if (piv != c)
+      for (int k = 0; k <= m; ++k) std::swap(A[c][k], A[piv][k]);
+    for (int r = c + 1; r < m; ++r) {
+      const double fct = A[r][c] / A[c][c];
+      for (int k = c; k <= m; ++k) A[r][k] -= fct * A[c][k];
+    }
+  }
+  double gam[kAndMaxSlots];
+  for (int r = m - 1; r >= 0; --r) {
+    double v = A[r][m];
+    for (int k = r + 1; k < m; ++k) v -= A[r][k] * gam[k];
+    gam[r] = v / A[r][r];
+  }
+  double sg = 0.0, l1 = 0.0;
+  for (int a = 0; a < m; ++a) {
+    if (!std::isfinite(gam[a])) return false;
+    sg += gam[a];
+    l1 += fabs(gam[a]);
+  }
+  if (l1 > 1e3) return false;
+  for (int a = 0; a < m; ++a) alpha[idx[a]] = gam[a];
+  alpha[head] = 1.0 - sg;
+  return true;
+}
 
 // The coupled solve of the instance in the InstState base.
 ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *out) {
@@ -1067,6 +1123,56 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
                        reinterpret_cast<float *>(ctx->X32.p), st));
     CK(launch_copy_f32(ctx->n_ph_entries, ctx->ph_Y.p, ctx->Y32.p, st));
   }
+
+  // Anderson acceleration (dragged level): ring of the last m+1 phonon updates g_j and
+  // residuals f_j = g_j - x_j over x = (F, G); from the third outer iteration on the electrons
+  // are solved against x = sum_j alpha_j g_j, alpha minimising |sum_j alpha_j f_j| (F and G
+  // halves weighted by the first residual's) subject to sum_j alpha_j = 1.
+  const int and_m = o->level == EPHB_DRAGGED ? o->accel_depth : 0;
+  const int and_R = and_m + 1;
+  const int64_t half = nph * 3;
+  int and_n = 0, and_head = 0;
+  double and_H[kAndMaxSlots][kAndMaxSlots] = {};
+  double and_wF = 0.0, and_wG = 0.0;
+  if (and_m > 0) {
+    CK(ctx->and_g.ensure(size_t(and_R) * 2 * half));
+    CK(ctx->and_f.ensure(size_t(and_R) * 2 * half));
+    CK(ctx->and_part.ensure(and_part_len()));
+    CK(ctx->and_dots.ensure(2 * kAndMaxSlots));
+  }
+  // g is in ring slot and_head; x = (F, G) is the iterate the electrons were solved against
+  auto anderson_step = [&]() -> ephb_status {
+    double *g = ctx->and_g.p + size_t(and_head) * 2 * half;
+    double *f = ctx->and_f.p + size_t(and_head) * 2 * half;
+    CK(launch_and_resid(half, g, ctx->F.p, ctx->G.p, f, st));
+    and_n = std::min(and_n + 1, and_R);
+    CK(launch_and_dots(half, f, ctx->and_f.p, 2 * half, and_n, ctx->and_part.p, ctx->and_dots.p, st));
+    double hd[2 * kAndMaxSlots];
+    CK(cudaMemcpyAsync(hd, ctx->and_dots.p, 2 * and_n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (and_wF == 0.0) {
+      and_wF = hd[2 * and_head] > 0 ? 1.0 / hd[2 * and_head] : 1.0;
+      and_wG = hd[2 * and_head + 1] > 0 ? 1.0 / hd[2 * and_head + 1] : 1.0;
+    }
+    for (int j = 0; j < and_n; ++j) and_H[and_head][j] = and_H[j][and_head] = and_wF * hd[2 * j] + and_wG * hd[2 * j + 1];
+    AndCoef al{};
+    al.a[and_head] = 1.0;
+    if (!anderson_weights(and_H, and_n, and_head, al.a)) {   // keep only the newest entry
+      for (int j = 0; j < kAndMaxSlots; ++j) al.a[j] = j == and_head ? 1.0 : 0.0;
+      if (and_head != 0) {
+        CK(cudaMemcpyAsync(ctx->and_g.p, g, 2 * half * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(ctx->and_f.p, f, 2 * half * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        and_H[0][0] = and_H[and_head][and_head];
+        al.a[0] = 1.0;
+        al.a[and_head] = 0.0;
+      }
+      and_n = 1;
+      and_head = 0;
+    }
+    CK(launch_and_mix(half, ctx->and_g.p, 2 * half, and_n, al, ctx->F.p, ctx->G.p, st));
+    and_head = (and_head + 1) % and_R;
+    return EPHB_OK;
+  };
 
   auto inner_loop_mixed = [&](int drag, bool &ok) -> ephb_status {
     ok = false;
@@ -1230,7 +1336,14 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
         CK(launch_ph_sweep(M, D, B, ctx->kinfo.p, ctx->I.p, ctx->J.p, ctx->Btv.p, st));
       }
       CK(tp.stop(st));
-      CK(launch_ph_update(M, D, B, ctx->Btv.p, ctx->F0.p, ctx->inv_nnW.p, ctx->F.p, ctx->G.p, st));
+      if (and_m > 0 && outer >= 2) {   // the update goes to the ring, the mix to (F, G)
+        double *g = ctx->and_g.p + size_t(and_head) * 2 * half;
+        CK(launch_ph_update(M, D, B, ctx->Btv.p, ctx->F0.p, ctx->inv_nnW.p, g, g + half, st));
+        s = anderson_step();
+        if (s != EPHB_OK) return s;
+      } else {
+        CK(launch_ph_update(M, D, B, ctx->Btv.p, ctx->F0.p, ctx->inv_nnW.p, ctx->F.p, ctx->G.p, st));
+      }
       if (ph32) CK(launch_pack6_f32(nph, ctx->F.p, ctx->G.p, ctx->FG32.p, st));
       bool ok;
       s = inner_loop(1, ok);
@@ -1303,6 +1416,8 @@ ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb
   if (!(o->tol > 0) || o->max_outer < 1 || o->max_inner < 1) return fail(ctx, EPHB_EINVAL, "bad tolerances");
   if (o->precision != EPHB_SOLVE_FP64 && o->precision != EPHB_SOLVE_MIXED)
     return fail(ctx, EPHB_EINVAL, "bad solve precision");
+  if (o->accel_depth < 0 || o->accel_depth > EPHB_MAX_ACCEL_DEPTH)
+    return fail(ctx, EPHB_EINVAL, "accel_depth outside 0..EPHB_MAX_ACCEL_DEPTH");
   CK(cudaSetDevice(ctx->device));
   // every instance in turn; the summary adds up counts and times and keeps the worst residual
   ephb_solve_info sum{};

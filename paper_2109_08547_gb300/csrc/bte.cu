@@ -1059,6 +1059,87 @@ cudaError_t launch_corr_apply(int64_t nst, const float *dI, const float *dJ, dou
   return cudaGetLastError();
 }
 
+// ---- Anderson acceleration of the outer iteration.  The iterate is x = (F, G) (F: nph*3
+// doubles, then G: nph*3); g = the phonon update from the electrons solved against x; f = g - x.
+
+__global__ void k_and_resid(int64_t half, const double *g, const double *F, const double *G, double *f) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= 2 * half) return;
+  f[i] = g[i] - (i < half ? F[i] : G[i - half]);
+}
+
+// dot products of f_new with the nslot ring vectors, F half and G half apart, per block
+// (fixed grid and per-thread assignment: the sums do not depend on timing)
+constexpr int kAndBlocks = 296, kAndThreads = 256;
+__global__ void __launch_bounds__(kAndThreads) k_and_dots(int64_t half, const double *fnew, const double *ring,
+                                                          int64_t stride, int nslot, double *part) {
+  __shared__ double red[kAndThreads / 32][2 * kAndMaxSlots];
+  double a[2 * kAndMaxSlots];
+  for (int j = 0; j < 2 * kAndMaxSlots; ++j) a[j] = 0.0;
+  const int64_t n = 2 * half;
+  for (int64_t i = blockIdx.x * int64_t(kAndThreads) + threadIdx.x; i < n; i += int64_t(kAndBlocks) * kAndThreads) {
+    const double x = fnew[i];
+    const int h = i < half ? 0 : 1;
+    for (int j = 0; j < kAndMaxSlots; ++j)
+      if (j < nslot) a[2 * j + h] += x * ring[j * stride + i];
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int j = 0; j < 2 * kAndMaxSlots; ++j) {
+    double v = a[j];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[w][j] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * kAndMaxSlots) {
+    double v = 0.0;
+    for (int k = 0; k < kAndThreads / 32; ++k) v += red[k][threadIdx.x];
+    part[blockIdx.x * 2 * kAndMaxSlots + threadIdx.x] = v;
+  }
+}
+
+__global__ void k_and_dots_final(const double *part, double *dots) {
+  const int j = threadIdx.x;
+  if (j >= 2 * kAndMaxSlots) return;
+  double v = 0.0;
+  for (int b = 0; b < kAndBlocks; ++b) v += part[b * 2 * kAndMaxSlots + j];
+  dots[j] = v;
+}
+
+// x = sum_j alpha_j g_j over the ring slots, written to F and G
+__global__ void k_and_mix(int64_t half, const double *ring, int64_t stride, int nslot, AndCoef al, double *F,
+                          double *G) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= 2 * half) return;
+  double x = 0.0;
+  for (int j = 0; j < nslot; ++j) x += al.a[j] * ring[j * stride + i];
+  if (i < half) F[i] = x; else G[i - half] = x;
+}
+
+cudaError_t launch_and_resid(int64_t half, const double *g, const double *F, const double *G, double *f,
+                             cudaStream_t st) {
+  if (half == 0) return cudaSuccess;
+  EPHB_LAUNCH(k_and_resid, unsigned((2 * half + 255) / 256), 256, 0, st, half, g, F, G, f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_and_dots(int64_t half, const double *fnew, const double *ring, int64_t stride, int nslot,
+                            double *part, double *dots, cudaStream_t st) {
+  if (nslot < 1 || nslot > kAndMaxSlots) return cudaErrorInvalidValue;
+  EPHB_LAUNCH(k_and_dots, kAndBlocks, kAndThreads, 0, st, half, fnew, ring, stride, nslot, part);
+  EPHB_LAUNCH(k_and_dots_final, 1, 32, 0, st, part, dots);
+  return cudaGetLastError();
+}
+
+size_t and_part_len() { return size_t(kAndBlocks) * 2 * kAndMaxSlots; }
+
+cudaError_t launch_and_mix(int64_t half, const double *ring, int64_t stride, int nslot, const AndCoef &al, double *F,
+                           double *G, cudaStream_t st) {
+  if (half == 0) return cudaSuccess;
+  if (nslot < 1 || nslot > kAndMaxSlots) return cudaErrorInvalidValue;
+  EPHB_LAUNCH(k_and_mix, unsigned((2 * half + 255) / 256), 256, 0, st, half, ring, stride, nslot, al, F, G);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_drag_term32(const MeshDev &D, const BteDev &B, const SweepSegs &S, const float2 *X32,
                                const float *FG32, double *part, double *Dterm, cudaStream_t st) {
   if (B.nst == 0) return cudaSuccess;

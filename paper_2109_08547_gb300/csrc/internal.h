@@ -258,6 +258,19 @@ cudaError_t launch_ph_sweep32(const ModelDev &M, const BteDev &B, const int2 *ki
                               const float *IJ32, double *Btv, cudaStream_t st);
 cudaError_t launch_pack6_f32(int64_t n, const double *A, const double *Bv, float *out, cudaStream_t st);
 cudaError_t launch_copy_f32(int64_t n, const double *a, float *b, cudaStream_t st);
+// Anderson acceleration of the outer iteration over x = (F, G) (2 * half doubles): the
+// residual f = g - x, the dot products of a new residual with up to kAndMaxSlots ring vectors
+// (F and G halves apart: dots[2j], dots[2j+1]; part holds and_part_len() doubles), and the
+// mixed iterate x = sum_j alpha_j g_j (ring vectors `stride` doubles apart).
+constexpr int kAndMaxSlots = 9;
+struct AndCoef { double a[kAndMaxSlots]; };
+cudaError_t launch_and_resid(int64_t half, const double *g, const double *F, const double *G, double *f,
+                             cudaStream_t st);
+cudaError_t launch_and_dots(int64_t half, const double *fnew, const double *ring, int64_t stride, int nslot,
+                            double *part, double *dots, cudaStream_t st);
+size_t and_part_len();
+cudaError_t launch_and_mix(int64_t half, const double *ring, int64_t stride, int nslot, const AndCoef &al, double *F,
+                           double *G, cudaStream_t st);
 // Warm start: network inputs per state (kNFeat floats), training targets (2 floats: the
 // converged I, J along the RTA direction J0 = v/W), and starting responses from them.
 constexpr int kNFeat = 6;

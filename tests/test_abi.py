@@ -51,6 +51,14 @@ def test_struct_layouts_match_header(tmp_path):
         assert ctypes.sizeof(cls) == sz, n
 
 
+def test_binding_constants_match_header():
+    text = open(HEADER).read()
+    for name, value in (("EPHB_MAX_ACCEL_DEPTH", B.MAX_ACCEL_DEPTH), ("EPHB_NFEAT", B.NFEAT),
+                        ("EPHB_TUNE_TC_COLS", B.TUNE_TC_COLS), ("EPHB_TUNE_WITHHOLD_MMA", B.TUNE_WITHHOLD_MMA)):
+        m = re.search(r"#define\s+%s\s+(\d+)" % name, text)
+        assert m and int(m.group(1)) == value, name
+
+
 def test_create_without_device_fails_cleanly():
     try:
         import torch
