@@ -2,7 +2,9 @@
 """Benchmark of the e-ph scattering + coupled-BTE hot path on GB300.
 
 One step = build_meshes_ibz + compute_transition_rates + solve_coupled_bte (dragged,
-tol 1e-10, Kelvin-Onsager on) + transport_coefficients for the 4-band / 6-branch model on
+tol 1e-10, Kelvin-Onsager on; by default the FP64-grade tensor-core vertex, the
+mixed-precision iteration and Anderson depth 3 on the outer iteration, all with the FP64
+path's fixed point) + transport_coefficients for the 4-band / 6-branch model on
 24^3 k and q meshes, with the Wannier model already resident on the device.  L2 is
 flushed (256 MB write) before every step.  The metric is transition rates per second:
 (k m, q, n, s) tuples interpolated and delta-weighted per step / step time.
