@@ -258,6 +258,7 @@ __global__ void __launch_bounds__(kTcThreads, (KC == 16 && ST == 2) ? 2 : 1) k_v
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar[ST];
   __shared__ uint32_t tslot;
+  __shared__ const __nv_bfloat16 *arow_s[kTcM];   // A row sources (nullptr: zero-filled row)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // once a CTA has recorded a timeout the remaining ones return without waiting in turn
   if (*reinterpret_cast<volatile int *>(err)) return;
@@ -310,6 +311,7 @@ __global__ void __launch_bounds__(kTcThreads, (KC == 16 && ST == 2) ? 2 : 1) k_v
   const size_t a_slice = size_t(kTcM) * KC * 2, b_slice = size_t(P.nc_max) * KC * 2;
   const size_t stage_bytes = size_t(NS) * (a_slice + b_slice);
 
+  arow_s[tid] = a_row >= 0 ? phis + size_t(a_row) * NS * P.Kp : nullptr;   // read after the barrier below
   if (tid == 0) {
     for (int i = 0; i < ST; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[i])));
     asm volatile("fence.mbarrier_init.release.cluster;");
@@ -326,16 +328,20 @@ __global__ void __launch_bounds__(kTcThreads, (KC == 16 && ST == 2) ? 2 : 1) k_v
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t taddr = tslot;
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(ncw >> 3) << 17) | (uint32_t(kTcM >> 4) << 24);
-  const __nv_bfloat16 *arow = phis + size_t(a_row < 0 ? 0 : a_row) * NS * P.Kp;
-  const uint32_t abytes = a_row >= 0 ? 16u : 0u;   // rows past the tile are zero-filled
 
-  // asynchronous copies of the operands of K block kb into stage buf (one commit group)
+  // asynchronous copies of the operands of K block kb into stage buf (one commit group).  A:
+  // consecutive threads take consecutive 16-byte pieces of one row's slice, so a warp's
+  // copies cover whole 32-byte sectors of 16 rows instead of half-sectors of 32.
   auto stage_load = [&](int buf, int kb) {
     unsigned char *sA = smem + buf * stage_bytes;
     unsigned char *sB = sA + NS * a_slice;
-    for (int s = 0; s < NS; ++s)
-      for (int g = 0; g < KC / 8; ++g)
-        cp_async16(smem_u32(sA + s * a_slice + core_off<KC>(tid, g)), arow + size_t(s) * P.Kp + kb + g * 8, abytes);
+    constexpr int G = KC / 8;
+    for (int c = tid; c < NS * kTcM * G; c += kTcThreads) {
+      const int g = c % G, rs = c / G, row = rs % kTcM, s = rs / kTcM;
+      const __nv_bfloat16 *src = arow_s[row];
+      cp_async16(smem_u32(sA + s * a_slice + core_off<KC>(row, g)), (src ? src : phis) + size_t(s) * P.Kp + kb + g * 8,
+                 src ? 16u : 0u);
+    }
     for (int t = tid; t < NS * ncw * (KC / 8); t += kTcThreads) {
       const int s = t / (ncw * (KC / 8));
       const int rem = t % (ncw * (KC / 8));
