@@ -173,6 +173,7 @@ struct ephb_ctx : InstState {
   DBuf<int64_t> item_ptr;
   DBuf<double> fk, nbq, wr;
   DBuf<double2> ut;
+  DBuf<float4> cff, uff;   // float-float c(k) and u(q) of the tensor-core epilogue
   DBuf<unsigned long long> ucount;
 
   // T-independent vertex lists over the union of the instance windows (several instances)
@@ -353,7 +354,7 @@ void ephb_destroy(ephb_ctx *ctx) {
   ctx->phik.release(); ctx->gslices.release(); ctx->gscale.release();
   ctx->phis.release(); ctx->bslices.release(); ctx->bscale.release(); ctx->Cbuf.release(); ctx->nitem.release();
   ctx->tc_err.release(); ctx->item_ptr.release(); ctx->fk.release(); ctx->nbq.release(); ctx->wr.release();
-  ctx->ut.release(); ctx->ucount.release();
+  ctx->ut.release(); ctx->ucount.release(); ctx->cff.release(); ctx->uff.release();
   ctx->u_row_ptr.release(); ctx->u_ph_row_ptr.release(); ctx->u_kpns.release(); ctx->u_ph_kpn.release();
   ctx->u_X.release(); ctx->u_ph_st.release(); ctx->u_ph_V.release();
   ctx->release_all();
@@ -688,6 +689,8 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
   rp.mu = inst->mu_eV;
   rp.sigma = delta->sigma_eV;
   rp.cut = delta->cutoff_sigmas * delta->sigma_eV;
+  rp.inv_sigma = 1.0 / delta->sigma_eV;
+  rp.gnorm = 1.0 / (delta->sigma_eV * std::sqrt(2.0 * kPi));
   rp.inv_Nq_pref = 2.0 * kPi / (kHbarEVs * double(nq));
   rp.y_scale = double(nq) / double(ctx->km.size());
   rp.vertex_only = multi ? 1 : 0;
@@ -782,6 +785,11 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     CK(ctx->wr.ensure(size_t(nq) * nbr));
     CK(ctx->ut.ensure(size_t(nq) * nbr * nbr));
     CK(launch_epi_tables(M, D, rp.T, rp.mu, ctx->fk.p, ctx->nbq.p, ctx->wr.p, ctx->ut.p, st));
+    if (tensor) {
+      CK(ctx->cff.ensure(size_t(ctx->km.size()) * M.nb * M.nb));
+      CK(ctx->uff.ensure(size_t(ctx->qm.size()) * M.nbr * M.nbr));
+      CK(launch_ff_tables(M, D, ctx->ut.p, ctx->cff.p, ctx->uff.p, st));
+    }
   }
   for (int64_t i0 = 0; i0 < ctx->n_ibzw;) {
     int64_t nkc = ctx->n_ibzw - i0 < chunk ? ctx->n_ibzw - i0 : chunk;
@@ -841,8 +849,9 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
       CK(tb.stop(st));
       CK(tc.start(st));
       CK(launch_vertex_epilogue(M, D, rp, hpp[i0], hpp[i0 + nkc], hpp[i0], ctx->Cbuf.p, Nmax, ctx->fk.p,
-                                ctx->nbq.p, ctx->wr.p, ctx->ut.p, ctx->escan.p, ctx->phscan.p, ctx->e_kpns.p,
-                                ctx->e_X.p, ctx->ph_st.p, ctx->ph_kpn.p, ctx->ph_Y.p, st));
+                                ctx->nbq.p, ctx->wr.p, ctx->ut.p, ctx->cff.p, ctx->uff.p, ctx->escan.p,
+                                ctx->phscan.p, ctx->e_kpns.p, ctx->e_X.p, ctx->ph_st.p, ctx->ph_kpn.p, ctx->ph_Y.p,
+                                st));
       CK(tc.stop(st));
     }
     CK(cudaStreamSynchronize(st));

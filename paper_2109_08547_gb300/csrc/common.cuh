@@ -63,6 +63,45 @@ __host__ __device__ inline void cfma_conj(double2 &acc, double2 a, double2 b) {
 }
 __host__ __device__ inline double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 
+// Float-float arithmetic: a value carried as hi + lo in two FP32 numbers (~48 significant
+// bits).  TwoSum (Knuth) gives the exact rounding error of a sum in 6 operations; the FMA
+// gives the exact error of a product.  The compensated accumulator below adds products the
+// way the compensated dot product of Ogita, Rump and Oishi does: the leading parts through
+// TwoSum, every error term into a second FP32 sum.  Used where the FP64 rate (1/64 of FP32
+// on this part) would bound a kernel and 2^-47 relative accuracy suffices.  The explicit
+// _rn intrinsics keep the compiler from contracting the sums into FMAs.
+__device__ __forceinline__ void ff_two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+struct FFAcc {
+  float s = 0.f, e = 0.f;
+};
+// a += x * y for float-float x = (x.x + x.y), y = (y.x + y.y); the lo * lo term (2^-48 of the
+// product) is left out
+__device__ __forceinline__ void ff_acc_mul(FFAcc &a, float2 x, float2 y) {
+  const float p = __fmul_rn(x.x, y.x);
+  float err = __fmaf_rn(x.x, y.x, -p);
+  err = __fmaf_rn(x.x, y.y, err);
+  err = __fmaf_rn(x.y, y.x, err);
+  float s, t;
+  ff_two_sum(a.s, p, s, t);
+  a.s = s;
+  a.e = __fadd_rn(a.e, __fadd_rn(t, err));
+}
+__device__ __forceinline__ float2 ff_norm(const FFAcc &a) {
+  float h, l;
+  ff_two_sum(a.s, a.e, h, l);
+  return make_float2(h, l);
+}
+__device__ __forceinline__ float2 ff_neg(float2 x) { return make_float2(-x.x, -x.y); }
+// float-float of a double (hi = nearest float, lo = nearest float of the remainder)
+__device__ __forceinline__ float2 ff_from_double(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - double(h)));
+}
+
 // mesh helpers -----------------------------------------------------------------------------
 struct Mesh {
   int n[3];

@@ -79,6 +79,7 @@ cudaError_t launch_count_reps(const int *rep, int64_t n, int64_t *out, cudaStrea
 // ---- vertex.cu
 struct RateParams {
   double T, mu, sigma, cut, inv_Nq_pref;   // inv_Nq_pref = 2 pi / (hbar N_q)
+  double inv_sigma, gnorm;                 // 1 / sigma, 1 / (sigma sqrt(2 pi))
   double y_scale;                          // N_q / N_k
   int vertex_only;                         // 1: store V+- = 2pi/(hbar N_q)|g|^2 delta (no occupations)
   int rot_fp32;                            // 1: band/branch rotations in FP32 (mixed mode)
@@ -99,11 +100,15 @@ size_t stage_a_A_elems(const ModelDev &M);
 // ut [nq][nbr][nbr] mass-scaled phonon eigenvectors.
 cudaError_t launch_epi_tables(const ModelDev &M, const MeshDev &D, double T, double mu, double *fk, double *nbq,
                               double *wr, double2 *ut, cudaStream_t st);
+// float-float copies of c(k) and of the mass-scaled u(q) for the FP64-grade epilogue
+cudaError_t launch_ff_tables(const ModelDev &M, const MeshDev &D, const double2 *ut, float4 *cff, float4 *uff,
+                             cudaStream_t st);
 // Rates of pairs [pbeg, pend) from a contraction already in Cbuf[pair - pair_base][Nmax]
-// (tensor-core path), one thread per pair.
+// (tensor-core path: float-float pairs), one thread per pair.
 cudaError_t launch_vertex_epilogue(const ModelDev &M, const MeshDev &D, RateParams rp, int64_t pbeg, int64_t pend,
                                    int64_t pair_base, const double *Cbuf, int Nmax, const double *fk,
-                                   const double *nbq, const double *wr, const double2 *ut, const int64_t *escan,
+                                   const double *nbq, const double *wr, const double2 *ut, const float4 *cff,
+                                   const float4 *uff, const int64_t *escan,
                                    const int64_t *phscan, uint32_t *e_kpns, double2 *e_X, int *ph_st,
                                    uint32_t *ph_kpn, double *ph_Y, cudaStream_t st);
 

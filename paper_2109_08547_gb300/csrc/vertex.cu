@@ -32,10 +32,12 @@ __device__ inline int nth_bit(uint32_t m, int n) {
 
 __device__ inline double fermi_d(double e, double mu, double kT) { return 1.0 / (exp((e - mu) / kT) + 1.0); }
 __device__ inline double bose_d(double w, double kT) { return w > 0.0 ? 1.0 / expm1(w / kT) : 0.0; }
-__device__ inline double gauss_d(double x, double sigma, double cut) {
-  if (fabs(x) > cut) return 0.0;
-  double r = x / sigma;
-  return exp(-0.5 * r * r) / (sigma * 2.5066282746310002);   // sqrt(2 pi)
+// (1/(sigma sqrt(2 pi))) exp(-x^2 / (2 sigma^2)) inside the cutoff, from the reciprocals
+// held in the parameters (no FP64 division on the per-tuple path)
+__device__ inline double gauss_d(double x, const RateParams &rp) {
+  if (fabs(x) > rp.cut) return 0.0;
+  const double r = x * rp.inv_sigma;
+  return exp(-0.5 * r * r) * rp.gnorm;
 }
 
 // ------------------------------------------------------------------------ count pass
@@ -268,18 +270,18 @@ __device__ void pair_epilogue(const ModelDev &M, const MeshDev &D, const RatePar
           }
         }
       }
-      double g2 = sum / double(cnt);
+      double g2 = cnt == 1 ? sum : sum / double(cnt);
       double dxp = ekp[n] - ek[m] - wq[s];
       double dxm = ekp[n] - ek[m] + wq[s];
       if (rp.vertex_only) {   // T-independent vertex weights V+-: occupation factors left out
         const double v = rp.inv_Nq_pref * g2;
-        xp = v * gauss_d(dxp, rp.sigma, rp.cut);
-        xm = v * gauss_d(dxm, rp.sigma, rp.cut);
+        xp = v * gauss_d(dxp, rp);
+        xm = v * gauss_d(dxm, rp);
       } else {
         double fm = fermi_d(ek[m], rp.mu, kT), fn = fermi_d(ekp[n], rp.mu, kT), nq = bose_d(wq[s], kT);
         double occ = rp.inv_Nq_pref * g2 * fm * (1.0 - fn);
-        xp = occ * nq * gauss_d(dxp, rp.sigma, rp.cut);
-        xm = occ * (1.0 + nq) * gauss_d(dxm, rp.sigma, rp.cut);
+        xp = occ * nq * gauss_d(dxp, rp);
+        xm = occ * (1.0 + nq) * gauss_d(dxm, rp);
       }
       Xps[t] = xp;
       Xms[t] = xm;
@@ -447,6 +449,21 @@ __global__ void k_epi_tables(ModelDev M, MeshDev D, double T, double mu, double 
   }
 }
 
+// Float-float copies of the final-band eigenvectors c(k) ([k][n'][n]) and of the mass-scaled
+// phonon eigenvectors ([q][a][s]) for the FP64-grade epilogue: (re hi, re lo, im hi, im lo)
+__global__ void k_ff_tables(int64_t nc, const double2 *cvec, int64_t nu, const double2 *ut, float4 *cff,
+                            float4 *uff) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t < nc) {
+    const float2 r = ff_from_double(cvec[t].x), i = ff_from_double(cvec[t].y);
+    cff[t] = make_float4(r.x, r.y, i.x, i.y);
+  }
+  if (t < nu) {
+    const float2 r = ff_from_double(ut[t].x), i = ff_from_double(ut[t].y);
+    uff[t] = make_float4(r.x, r.y, i.x, i.y);
+  }
+}
+
 // Rates from a contraction held in Cbuf: C'[pair][j'] with j' = ml*(2 nb nbr) + part*(nb nbr)
 // + n'*nbr + a (part 0: real, 1: imaginary).  One thread per (k, q) pair, so every lane works
 // even when a pair has only a handful of (m, n, s) tuples.  The final-band index is contracted
@@ -461,6 +478,7 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
                                                        int Nmax, const double *__restrict__ fk,
                                                        const double *__restrict__ nbq, const double *__restrict__ wr,
                                                        const double2 *__restrict__ ut,
+                                                       const float4 *__restrict__ cff, const float4 *__restrict__ uff,
                                                        const int64_t *__restrict__ escan,
                                                        const int64_t *__restrict__ phscan, uint32_t *e_kpns,
                                                        double2 *e_X, int *ph_st, uint32_t *ph_kpn, double *ph_Y) {
@@ -474,7 +492,7 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
   const int nact = __popc(am), nactp = __popc(an);
   const int64_t p0 = D.pair_ptr[i];
   const int64_t npl = D.pair_ptr[i + 1] - p0;
-  const double *crow = Cbuf + (pg - pair_base) * Nmax;
+  const float2 *crow = reinterpret_cast<const float2 *>(Cbuf) + (pg - pair_base) * Nmax;
   const double2 *ckp = D.cvec + size_t(kp) * nb * nb;
   const double2 *uq = ut + size_t(q) * nbr * nbr;
   const double *wrq = wr + size_t(q) * nbr;
@@ -488,9 +506,9 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
         for (int np_ = 0; np_ < nb; ++np_) {
           const double2 c = ckp[np_ * nb + n];
           const float cr = float(c.x), ci = float(c.y);
-          const double *re = crow + ml * 2 * nbnbr + np_ * nbr;
+          const float2 *re = crow + ml * 2 * nbnbr + np_ * nbr;
           for (int a = 0; a < nbr; ++a) {   // W += conj(c) B
-            const float br = float(re[a]), bi = float(re[nbnbr + a]);
+            const float br = re[a].x + re[a].y, bi = re[nbnbr + a].x + re[nbnbr + a].y;
             Wr[a] = fmaf(cr, br, fmaf(ci, bi, Wr[a]));
             Wi[a] = fmaf(cr, bi, fmaf(-ci, br, Wi[a]));
           }
@@ -506,23 +524,52 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
           g2[(ml * nactp + nl) * nbr + s] = double(gr * gr + gi * gi) * wrq[s];
         }
       }
-  } else
-  for (int ml = 0; ml < nact; ++ml)
-    for (int nl = 0; nl < nactp; ++nl) {
-      const int n = nth_bit(an, nl);
-      double2 W[NBRM];
-      for (int a = 0; a < nbr; ++a) W[a] = cmk(0, 0);
-      for (int np_ = 0; np_ < nb; ++np_) {
-        const double2 cc = ckp[np_ * nb + n];
-        const double *re = crow + ml * 2 * nbnbr + np_ * nbr;
-        for (int a = 0; a < nbr; ++a) cfma_conj(W[a], cc, cmk(re[a], re[nbnbr + a]));
+  } else {
+    // FP64-grade rotations in float-float arithmetic (~2^-47 of the summed magnitudes) on the
+    // FP32 pipe: C' arrives as float-float pairs, c(k') and u(q) from float-float tables;
+    // |g|^2 goes to FP64 once per (m, n, s)
+    const float4 *cf = cff + size_t(kp) * nb * nb;
+    const float4 *uf = uff + size_t(q) * nbr * nbr;
+    for (int ml = 0; ml < nact; ++ml)
+      for (int nl = 0; nl < nactp; ++nl) {
+        const int n = nth_bit(an, nl);
+        FFAcc Wr[NBRM], Wi[NBRM];
+        for (int np_ = 0; np_ < nb; ++np_) {
+          const float4 c4 = cf[np_ * nb + n];
+          const float2 cr = make_float2(c4.x, c4.y), ci = make_float2(c4.z, c4.w);
+          const float2 *re = crow + ml * 2 * nbnbr + np_ * nbr;
+          for (int a = 0; a < nbr; ++a) {   // W += conj(c) B
+            const float2 br = re[a], bi = re[nbnbr + a];
+            ff_acc_mul(Wr[a], cr, br);
+            ff_acc_mul(Wr[a], ci, bi);
+            ff_acc_mul(Wi[a], cr, bi);
+            ff_acc_mul(Wi[a], ff_neg(ci), br);
+          }
+        }
+        float2 wr2[NBRM], wi2[NBRM];
+        for (int a = 0; a < nbr; ++a) {
+          wr2[a] = ff_norm(Wr[a]);
+          wi2[a] = ff_norm(Wi[a]);
+        }
+        for (int s = 0; s < nbr; ++s) {
+          FFAcc gr, gi;
+          for (int a = 0; a < nbr; ++a) {   // g += W u
+            const float4 u4 = uf[a * nbr + s];
+            const float2 ur = make_float2(u4.x, u4.y), ui = make_float2(u4.z, u4.w);
+            ff_acc_mul(gr, wr2[a], ur);
+            ff_acc_mul(gr, ff_neg(wi2[a]), ui);
+            ff_acc_mul(gi, wr2[a], ui);
+            ff_acc_mul(gi, wi2[a], ur);
+          }
+          const float2 Gr = ff_norm(gr), Gi = ff_norm(gi);
+          FFAcc m2;
+          ff_acc_mul(m2, Gr, Gr);
+          ff_acc_mul(m2, Gi, Gi);
+          const float2 m = ff_norm(m2);
+          g2[(ml * nactp + nl) * nbr + s] = (double(m.x) + double(m.y)) * wrq[s];
+        }
       }
-      for (int s = 0; s < nbr; ++s) {
-        double2 g = cmk(0, 0);
-        for (int a = 0; a < nbr; ++a) cfma(g, W[a], uq[a * nbr + s]);
-        g2[(ml * nactp + nl) * nbr + s] = cabs2(g) * wrq[s];
-      }
-    }
+  }
   // degenerate averages, occupations (tables), delta
   const double *ek = D.eps + size_t(k) * nb, *ekp = D.eps + size_t(kp) * nb, *wq = D.w + size_t(q) * nbr;
   const uint8_t *gk = D.egrp + size_t(k) * nb * 2, *gkp = D.egrp + size_t(kp) * nb * 2;
@@ -554,15 +601,15 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
     const double dxp = ekp[n] - ek[m] - wq[s];
     const double dxm = ekp[n] - ek[m] + wq[s];
     if (rp.vertex_only) {   // T-independent vertex weights V+-: occupation factors left out
-      const double v = rp.inv_Nq_pref * (sum / double(cnt));
-      Xp[t] = v * gauss_d(dxp, rp.sigma, rp.cut);
-      Xm[t] = v * gauss_d(dxm, rp.sigma, rp.cut);
+      const double v = rp.inv_Nq_pref * (cnt == 1 ? sum : sum / double(cnt));
+      Xp[t] = v * gauss_d(dxp, rp);
+      Xm[t] = v * gauss_d(dxm, rp);
     } else {
       const double nqs = nbq[size_t(q) * nbr + s];
       const double occ =
-          rp.inv_Nq_pref * (sum / double(cnt)) * fk[size_t(k) * nb + m] * (1.0 - fk[size_t(kp) * nb + n]);
-      Xp[t] = occ * nqs * gauss_d(dxp, rp.sigma, rp.cut);
-      Xm[t] = occ * (1.0 + nqs) * gauss_d(dxm, rp.sigma, rp.cut);
+          rp.inv_Nq_pref * (cnt == 1 ? sum : sum / double(cnt)) * fk[size_t(k) * nb + m] * (1.0 - fk[size_t(kp) * nb + n]);
+      Xp[t] = occ * nqs * gauss_d(dxp, rp);
+      Xm[t] = occ * (1.0 + nqs) * gauss_d(dxm, rp);
     }
     flg[t] = uint8_t((fabs(dxp) <= rp.cut ? 1 : 0) | (fabs(dxm) <= rp.cut ? 2 : 0));
   }
@@ -608,16 +655,26 @@ cudaError_t launch_epi_tables(const ModelDev &M, const MeshDev &D, double T, dou
   return cudaGetLastError();
 }
 
+cudaError_t launch_ff_tables(const ModelDev &M, const MeshDev &D, const double2 *ut, float4 *cff, float4 *uff,
+                             cudaStream_t st) {
+  const int64_t nc = D.nk * M.nb * M.nb, nu = D.nq * M.nbr * M.nbr;
+  const int64_t n = nc > nu ? nc : nu;
+  if (n == 0) return cudaSuccess;
+  EPHB_LAUNCH(k_ff_tables, unsigned((n + 255) / 256), 256, 0, st, nc, D.cvec, nu, ut, cff, uff);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_vertex_epilogue(const ModelDev &M, const MeshDev &D, RateParams rp, int64_t pbeg, int64_t pend,
                                    int64_t pair_base, const double *Cbuf, int Nmax, const double *fk,
-                                   const double *nbq, const double *wr, const double2 *ut, const int64_t *escan,
+                                   const double *nbq, const double *wr, const double2 *ut, const float4 *cff,
+                                   const float4 *uff, const int64_t *escan,
                                    const int64_t *phscan, uint32_t *e_kpns, double2 *e_X, int *ph_st,
                                    uint32_t *ph_kpn, double *ph_Y, cudaStream_t st) {
   if (pend <= pbeg) return cudaSuccess;
   const unsigned grid = unsigned((pend - pbeg + 127) / 128);
   auto go = [&](auto kern) {
-    EPHB_LAUNCH(kern, grid, 128, 0, st, M, D, rp, pbeg, pend, pair_base, Cbuf, Nmax, fk, nbq, wr, ut, escan, phscan,
-                e_kpns, e_X, ph_st, ph_kpn, ph_Y);
+    EPHB_LAUNCH(kern, grid, 128, 0, st, M, D, rp, pbeg, pend, pair_base, Cbuf, Nmax, fk, nbq, wr, ut, cff, uff, escan,
+                phscan, e_kpns, e_X, ph_st, ph_kpn, ph_Y);
   };
   if (M.nb <= 1 && M.nbr <= 3)
     rp.rot_fp32 ? go(k_rate_epilogue<1, 3, true>) : go(k_rate_epilogue<1, 3, false>);

@@ -233,6 +233,56 @@ __device__ __forceinline__ uint32_t core_off(int row, int kgroup) {
   return uint32_t(((row >> 3) * (KC / 8) + kgroup) * 128 + (row & 7) * 16);
 }
 
+// 2^k as an FP32 number from the FP64 power of two 2^k (0 for 0 and below the FP32 normal
+// range), by exponent arithmetic: no FP64 operation
+__device__ __forceinline__ float pow2_float(double sigma) {
+  const long long b = __double_as_longlong(sigma);
+  const int k = int((b >> 52) & 0x7ff) - 1023;
+  if (b == 0 || k < -126) return 0.f;
+  return __int_as_float(k > 127 ? 0x7f800000 : (k + 127) << 23);
+}
+
+// Stage-B accumulator combination of 16 columns: the rounded tail plus the exact diagonals
+// (each an exact FP32 multiple of its unit), summed by TwoSum into a float-float pair; the
+// only rounding is that of the error sum, ~2^-48 of the result.  No FP64 operation: the FP64
+// pipe is shared with the tensor pipe, and this runs beside the next products.
+template <int NACC>
+__device__ __forceinline__ void tmem_ff16(uint32_t ta, int nc, float *s, float *e) {
+  for (int a = NACC - 1; a >= 0; --a) {
+    uint32_t v[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(ta + uint32_t(a * nc)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (a == NACC - 1) {
+      for (int j = 0; j < 16; ++j) {
+        s[j] = __uint_as_float(v[j]);
+        e[j] = 0.f;
+      }
+    } else {
+      for (int j = 0; j < 16; ++j) {
+        float t, u;
+        ff_two_sum(s[j], __uint_as_float(v[j]), t, u);
+        s[j] = t;
+        e[j] = __fadd_rn(e[j], u);
+      }
+    }
+  }
+}
+
+// the float-float sums s + e of 16 columns times their column scales, into C'[row][c0 + j]
+__device__ __forceinline__ void store_ff16(const float *s, const float *e, const double *sc, float2 *dst, int nvalid) {
+  for (int j = 0; j < 16; ++j)
+    if (j < nvalid) {
+      float h, l;
+      ff_two_sum(s[j], e[j], h, l);
+      const float f = pow2_float(sc[j]);
+      dst[j] = make_float2(__fmul_rn(h, f), __fmul_rn(l, f));
+    }
+}
+
 // Rows of a contraction: (k,q) pairs of each k (stage B: A rows are the phase slices of the
 // pair's q, B and the column scales belong to the pair's k) or k points of a chunk (stage A:
 // A rows are the k phase slices, B = the model's g slices shared by every k).
@@ -424,6 +474,14 @@ __global__ void __launch_bounds__(kTcThreads, (KC == 16 && ST == 2) ? 2 : 1) k_v
     // Exact accumulators (diagonals d = 0..NACC-2) hold integer multiples of 2^(-14-8d) below
     // 2^24 of that unit; the tail is rounded to 2^-48.  All of them go into one 64-bit integer
     // in units of 2^-48 (at most 2^57), converted to FP64 once.
+    if (ROWS == kRowsPairs) {   // C' as float-float pairs
+      float2 *frow = reinterpret_cast<float2 *>(Cbuf) + (crow - Cbuf);
+      for (int c0 = 0; c0 < ncw; c0 += 16) {
+        float sm[16], er[16];
+        tmem_ff16<NACC>(taddr + (uint32_t(warp * 32) << 16) + uint32_t(c0), nc, sm, er);
+        if (row < npt) store_ff16(sm, er, sc + c0, frow + c0, nlive - c0);
+      }
+    } else
     for (int c0 = 0; c0 < ncw; c0 += 16) {
       long long sum[16];
       for (int j = 0; j < 16; ++j) sum[j] = 0;
@@ -454,6 +512,259 @@ __global__ void __launch_bounds__(kTcThreads, (KC == 16 && ST == 2) ? 2 : 1) k_v
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(ncols_alloc));
 }
 
+// ---- warp-specialised persistent form (stage B rows: (k,q) pairs) ------------------------
+// One CTA per SM walks the work items blockIdx.x, blockIdx.x + gridDim.x, ...  Roles:
+//   warps 0-3  epilogue: tensor-memory lane quadrant w, int64 combination, FP64 stores;
+//   warp 4     tensor-memory allocation; lane 0 issues every tcgen05.mma and commit;
+//   warps 5-8  copies: cp.async of the A and B slices of K blocks of 16 into ST stages.
+// Barriers: full[s] (128 copy threads arrive once their copies of stage s have landed),
+// empty[s] (the MMA commit after the products that read stage s), accf[b] (the commit after
+// an item's last products into accumulator buffer b), acce[b] (128 epilogue threads arrive
+// once buffer b is read).  Two accumulator buffers of NACC x nc_max columns let the epilogue
+// of one item run under the products of the next; ST - 2 stages of copies run ahead of the
+// products.  Every wait is bounded; a timeout sets a CTA-wide abort flag and the error flag,
+// each role leaves its loop, the copies and MMAs in flight are waited for (bounded) and the
+// tensor memory is freed.
+constexpr int kWsThreads = 288;
+constexpr int kWsCopyThreads = 128;
+
+struct WsItem {
+  int nc, n0, ncw, npt;
+  int64_t p0t0;   // first pair of the tile
+  int kc;         // chunk-local k index
+};
+
+__device__ __forceinline__ WsItem ws_item(const ModelDev &M, const MeshDev &D, const TcParams &P,
+                                          const int64_t *item_ptr, int64_t item) {
+  int64_t lo = 0, hi = P.nkc;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (item_ptr[mid] <= item) lo = mid; else hi = mid;
+  }
+  WsItem w;
+  w.kc = int(lo);
+  const int64_t i = P.i0 + lo;
+  const int k = D.ibzw_list[i];
+  const int nk = round_up(2 * __popc(D.amask[k]) * M.nb * M.nbr, 16);
+  const int nch = (nk + P.nc_max - 1) / P.nc_max;
+  w.nc = round_up((nk + nch - 1) / nch, 16);
+  const int64_t local = item - item_ptr[lo];
+  const int tile = int(local / nch), chunk = int(local % nch);
+  w.n0 = chunk * w.nc;
+  w.ncw = nk - w.n0 < w.nc ? nk - w.n0 : w.nc;
+  const int64_t p0 = D.pair_ptr[i];
+  const int64_t npl = D.pair_ptr[i + 1] - p0;
+  const int64_t t0 = int64_t(tile) * kTcM;
+  w.npt = int(npl - t0 < kTcM ? npl - t0 : kTcM);
+  w.p0t0 = p0 + t0;
+  return w;
+}
+
+// AND of v over the 128 epilogue threads (warps 0-3), named barrier 1
+__device__ __forceinline__ bool epi_sync_and(bool v) {
+  uint32_t r;
+  asm volatile("{\n.reg .pred p, q;\nsetp.ne.u32 q, %1, 0;\nbar.red.and.pred p, 1, 128, q;\nselp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(r) : "r"(v ? 1u : 0u) : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" :: "r"(mbar) : "memory");
+}
+
+template <int NS, int NACC, int ST>
+__global__ void __launch_bounds__(kWsThreads, 1) k_vertex_gemm_ws(ModelDev M, MeshDev D, TcParams P, int64_t nitems,
+                                                                  const int64_t *__restrict__ item_ptr,
+                                                                  const __nv_bfloat16 *__restrict__ phis,
+                                                                  const __nv_bfloat16 *__restrict__ bs,
+                                                                  const double *__restrict__ bscale, double *Cbuf,
+                                                                  int *err) {
+  constexpr int KC = 16;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[ST], empty[ST], accf[2], acce[2];
+  __shared__ uint32_t tslot;
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (*reinterpret_cast<volatile int *>(err)) return;   // the whole CTA returns, before any barrier
+  const size_t a_slice = size_t(kTcM) * KC * 2, b_slice = size_t(P.nc_max) * KC * 2;
+  const size_t stage_bytes = size_t(NS) * (a_slice + b_slice);
+  const int nkb = P.Kp / KC;
+  if (tid == 0) {
+    for (int i = 0; i < ST; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&full[i])), "r"(kWsCopyThreads));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&empty[i])));
+    }
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&accf[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&acce[b])), "r"(kTcM));
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 4) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" :: "r"(smem_u32(&tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t taddr = tslot;
+  auto give_up = [&]() {
+    abort_flag = 1;
+    atomicExch(err, 1);
+  };
+
+  if (warp >= 5) {
+    // ---------------- copies
+    const int ct = tid - 5 * 32;               // 0..127
+    const int g = ct & 1, r0 = ct >> 1;        // this thread's 16-byte piece and A rows r0, r0 + 64
+    uint32_t it = 0;                           // K blocks issued so far (all items)
+    bool ok = true;
+    auto complete = [&](uint32_t j) {          // stage of block j has landed: publish it
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(smem_u32(&full[j % ST]));
+    };
+    for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+      const WsItem w = ws_item(M, D, P, item_ptr, item);
+      const __nv_bfloat16 *src0 = r0 < w.npt ? phis + size_t(D.pair_q[w.p0t0 + r0]) * NS * P.Kp : nullptr;
+      const __nv_bfloat16 *src1 = r0 + 64 < w.npt ? phis + size_t(D.pair_q[w.p0t0 + r0 + 64]) * NS * P.Kp : nullptr;
+      const __nv_bfloat16 *bsk = bs + (size_t(w.kc) * NS * P.Nmax + w.n0) * P.Kp;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const uint32_t slot = it % ST;
+        if (it >= ST && !mbar_wait(smem_u32(&empty[slot]), ((it / ST) - 1) & 1)) {
+          give_up();
+          ok = false;
+          break;
+        }
+        if (abort_flag) {
+          ok = false;
+          break;
+        }
+        unsigned char *sA = smem + slot * stage_bytes;
+        unsigned char *sB = sA + NS * a_slice;
+        const int k0 = kb * KC + g * 8;
+        for (int sl = 0; sl < NS; ++sl) {
+          cp_async16(smem_u32(sA + sl * a_slice + core_off<KC>(r0, g)), (src0 ? src0 : phis) + size_t(sl) * P.Kp + k0,
+                     src0 ? 16u : 0u);
+          cp_async16(smem_u32(sA + sl * a_slice + core_off<KC>(r0 + 64, g)),
+                     (src1 ? src1 : phis) + size_t(sl) * P.Kp + k0, src1 ? 16u : 0u);
+        }
+        for (int rem = r0; rem < NS * w.ncw; rem += 64) {
+          const int sl = rem / w.ncw, row = rem - sl * w.ncw;
+          cp_async16(smem_u32(sB + sl * b_slice + core_off<KC>(row, g)),
+                     bsk + (size_t(sl) * P.Nmax + row) * P.Kp + k0, 16u);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        if (it >= ST - 2) {                    // block it - (ST - 2) has landed once ST - 2 later groups remain
+          asm volatile("cp.async.wait_group %0;" :: "n"(ST - 2) : "memory");
+          complete(it - (ST - 2));
+        }
+        ++it;
+      }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (ok)
+      for (uint32_t j = it >= ST - 2 ? it - (ST - 2) : 0; j < it; ++j) complete(j);
+  } else if (warp == 4) {
+    // ---------------- tensor-core products (one thread)
+    if (lane == 0) {
+      uint32_t it = 0, tcount = 0;
+      uint64_t last_bar = 0;                   // barrier address + parity of the last commit
+      uint32_t last_par = 0;
+      bool any = false;
+      for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        if (abort_flag) break;
+        const WsItem w = ws_item(M, D, P, item_ptr, item);
+        const uint32_t buf = tcount & 1;
+        if (tcount >= 2 && !mbar_wait(smem_u32(&acce[buf]), ((tcount >> 1) - 1) & 1)) {
+          give_up();
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(w.ncw >> 3) << 17) |
+                               (uint32_t(kTcM >> 4) << 24);
+        const uint32_t tbase = taddr + buf * uint32_t(NACC * P.nc_max);
+        bool ok = true;
+        for (int kb = 0; kb < nkb; ++kb) {
+          const uint32_t slot = it % ST;
+          if (!mbar_wait(smem_u32(&full[slot]), (it / ST) & 1) || abort_flag) {
+            if (!abort_flag) give_up();
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          if (!P.withhold) {
+            const unsigned char *sA = smem + slot * stage_bytes;
+            const unsigned char *sB = sA + NS * a_slice;
+            for (int is = 0; is < NS; ++is)
+              for (int ls = 0; ls < NS - is; ++ls) {
+                const int d = is + ls;
+                const int acc = NACC == 1 ? 0 : (d < NACC - 1 ? d : NACC - 1);
+                const uint32_t dtm = tbase + uint32_t(acc * w.nc);
+                const uint64_t ad = smem_desc(smem_u32(sA + is * a_slice), 128u, (KC / 8) * 128u);
+                const uint64_t bd = smem_desc(smem_u32(sB + ls * b_slice), 128u, (KC / 8) * 128u);
+                const bool first = kb == 0 && (NACC == 1 ? (is == 0 && ls == 0) :
+                                               (acc < NACC - 1 ? (is == 0) : (is == 0 && ls == NACC - 1)));
+                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                             :: "r"(dtm), "l"(ad), "l"(bd), "r"(idesc), "r"(first ? 0u : 1u));
+              }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(&empty[slot])) : "memory");
+            any = true;
+            last_bar = smem_u32(&empty[slot]);
+            last_par = (it / ST) & 1;
+          }
+          ++it;
+        }
+        if (!ok) break;
+        if (!P.withhold) {
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                       :: "r"(smem_u32(&accf[buf])) : "memory");
+          last_bar = smem_u32(&accf[buf]);
+          last_par = (tcount >> 1) & 1;
+        }
+        ++tcount;
+      }
+      // every MMA issued is complete before the tensor memory is freed
+      if (any && !mbar_wait(uint32_t(last_bar), last_par)) give_up();
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue (warps 0-3: tensor-memory lanes 32w .. 32w + 31)
+    const int row = warp * 32 + lane;
+    uint32_t tcount = 0;
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+      const WsItem w = ws_item(M, D, P, item_ptr, item);
+      const uint32_t buf = tcount & 1;
+      const bool waited = mbar_wait(smem_u32(&accf[buf]), (tcount >> 1) & 1);
+      // the four warps agree before leaving, so no warp reads a buffer another abandoned
+      const bool ok = epi_sync_and(waited && !abort_flag);
+      if (!ok) {
+        if (!waited && !abort_flag) give_up();
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const double *sc = bscale + w.kc * P.Nmax + w.n0;
+      float2 *frow = reinterpret_cast<float2 *>(Cbuf) + (w.p0t0 + row - P.pair_base) * P.Nmax + w.n0;
+      const uint32_t tbase = taddr + (uint32_t(warp * 32) << 16) + buf * uint32_t(NACC * P.nc_max);
+      for (int c0 = 0; c0 < w.ncw; c0 += 16) {
+        float sm[16], er[16];
+        tmem_ff16<NACC>(tbase + uint32_t(c0), w.nc, sm, er);
+        if (c0 + 16 >= w.ncw) {   // the last reads of this buffer are done: hand it back
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          mbar_arrive(smem_u32(&acce[buf]));
+        }
+        if (row < w.npt) store_ff16(sm, er, sc + c0, frow + c0, w.ncw - c0);
+      }
+      ++tcount;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 4) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(taddr));
+}
+
 }  // namespace
 
 int tc_kp(const ModelDev &M) { return round_up(2 * M.nRgp, kTcKc); }
@@ -464,21 +775,25 @@ int tc_nmax(const ModelDev &M) { return round_up(2 * M.nb * M.nb * M.nbr, 16); }
 int tc_nc_max(int ns) { return ns == 7 ? 96 : 256; }
 static int nacc_of(int ns) { return ns == 7 ? 5 : 2; }
 static bool two_ctas(int kc, int st) { return kc == 16 && st == 2; }
+static bool warp_specialised(int kc, int st) { return kc == 16 && st == 5; }
 size_t tc_smem_bytes(int ns, int ncm, int kc, int st) {
   const size_t need = size_t(st) * (size_t(ns) * kTcM * kc * 2 + size_t(ns) * ncm * kc * 2);
+  if (warp_specialised(kc, st)) return need;
   // two-CTA shapes ask for at least 96 KB so that no third CTA (whose tensor memory would not
   // fit) is placed on the SM
   return two_ctas(kc, st) && need < 96 * 1024 ? 96 * 1024 : need;
 }
 bool tc_nc_valid(int ns, int ncm, int kc, int st) {
   if (ncm < 16 || ncm % 16 != 0 || ncm > tc_nc_max(ns)) return false;
-  if (!((kc == 32 && st == 2) || (kc == 16 && (st == 2 || st == 4)))) return false;
+  if (!((kc == 32 && st == 2) || (kc == 16 && (st == 2 || st == 4 || st == 5)))) return false;
   if (tc_smem_bytes(ns, ncm, kc, st) > 200 * 1024 + 1024) return false;
+  // the warp-specialised form double-buffers its accumulators in the 512 columns
+  if (warp_specialised(kc, st)) return 2 * nacc_of(ns) * ncm <= 512;
   return !two_ctas(kc, st) || nacc_of(ns) * ncm <= 256;
 }
 std::vector<TcShape> tc_shape_candidates(int ns) {
-  if (ns == 7) return {{48, 32, 2}, {64, 32, 2}, {96, 32, 2}, {48, 16, 2}, {96, 16, 4}};
-  return {{64, 32, 2}, {128, 32, 2}, {256, 32, 2}, {128, 16, 2}, {256, 16, 4}};
+  if (ns == 7) return {{48, 32, 2}, {64, 32, 2}, {96, 32, 2}, {48, 16, 2}, {96, 16, 4}, {48, 16, 5}};
+  return {{64, 32, 2}, {128, 32, 2}, {256, 32, 2}, {128, 16, 2}, {256, 16, 4}, {64, 16, 5}, {128, 16, 5}};
 }
 
 int tc_kp_a(const ModelDev &M) { return round_up(2 * M.nRge, kTcKc); }
@@ -584,7 +899,21 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
     EPHB_LAUNCH(kern, unsigned(nitems), kTcThreads, smem, st, M, D, P, item_ptr, phis, bs, bscale, Cbuf, err);
     return cudaGetLastError();
   };
-  if (ns == 7)
+  // persistent form: one CTA per SM
+  auto go_ws = [&](auto kern) -> cudaError_t {
+    cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (r != cudaSuccess) return r;
+    int dev = 0, nsm = 0;
+    r = cudaGetDevice(&dev);
+    if (r == cudaSuccess) r = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (r != cudaSuccess) return r;
+    const unsigned grid = unsigned(nitems < nsm ? nitems : nsm);
+    EPHB_LAUNCH(kern, grid, kWsThreads, smem, st, M, D, P, nitems, item_ptr, phis, bs, bscale, Cbuf, err);
+    return cudaGetLastError();
+  };
+  if (warp_specialised(kc, stages))
+    e = ns == 7 ? go_ws(k_vertex_gemm_ws<7, 5, 5>) : go_ws(k_vertex_gemm_ws<3, 2, 5>);
+  else if (ns == 7)
     e = kc == 32 ? go(k_vertex_gemm<7, 5, kRowsPairs, 32, 2>)
                  : (stages == 4 ? go(k_vertex_gemm<7, 5, kRowsPairs, 16, 4>) : go(k_vertex_gemm<7, 5, kRowsPairs, 16, 2>));
   else
