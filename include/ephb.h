@@ -218,9 +218,10 @@ typedef enum { EPHB_RTA = 0, EPHB_PARTIAL = 1, EPHB_DRAGLESS = 2, EPHB_DRAGGED =
  *                     outer test; fewer sweeps.  At the dragged level the phonon scatter and
  *                     the drag term of an outer iteration begun with the outer residual at or
  *                     above 1e-5 run in FP32 (FP32 copies of X, Y, I, J, F, G; FP64 partial
- *                     sums across segments), and the solve ends only after an outer iteration
- *                     with both in FP64.  The phonon update, KO step and coefficients stay
- *                     FP64. */
+ *                     sums across segments); later ones in float-float arithmetic (pairs of
+ *                     FP32 numbers, ~2^-47 relative, on the FP32 pipe), and the solve ends
+ *                     only after an outer iteration with both in float-float.  The phonon
+ *                     update, KO step and coefficients stay FP64. */
 typedef enum { EPHB_SOLVE_FP64 = 0, EPHB_SOLVE_MIXED = 1 } ephb_solve_precision;
 
 typedef struct {

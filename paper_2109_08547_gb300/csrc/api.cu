@@ -171,6 +171,8 @@ struct ephb_ctx : InstState {
   DBuf<double> bscale, Cbuf;
   DBuf<int> nitem, tc_err;
   DBuf<int64_t> item_ptr;
+  DBuf<int64_t> ws_desc;   // work-item descriptors of the persistent contraction (4 int64 each)
+  int64_t ws_cap = 0;
   DBuf<double> fk, nbq, wr;
   DBuf<double2> ut;
   DBuf<float4> cff, uff;   // float-float c(k) and u(q) of the tensor-core epilogue
@@ -187,6 +189,9 @@ struct ephb_ctx : InstState {
   // the responses ([state][I | J]) and phonon deviations ([mode][F | G]); rebuilt per solve
   DBuf<float2> X32;
   DBuf<float> Y32, IJ32, FG32;
+  // later outer iterations: float-float copies of the same (FP64-grade on the FP32 pipe)
+  DBuf<float4> Xff;
+  DBuf<float2> Yff, IJff, FGff;
   // Anderson acceleration of the outer iteration: ring of phonon updates g and residuals f
   DBuf<double> and_g, and_f, and_part, and_dots;
 
@@ -353,7 +358,7 @@ void ephb_destroy(ephb_ctx *ctx) {
   ctx->Tbuf.release(); ctx->Abuf.release();
   ctx->phik.release(); ctx->gslices.release(); ctx->gscale.release();
   ctx->phis.release(); ctx->bslices.release(); ctx->bscale.release(); ctx->Cbuf.release(); ctx->nitem.release();
-  ctx->tc_err.release(); ctx->item_ptr.release(); ctx->fk.release(); ctx->nbq.release(); ctx->wr.release();
+  ctx->tc_err.release(); ctx->item_ptr.release(); ctx->ws_desc.release(); ctx->fk.release(); ctx->nbq.release(); ctx->wr.release();
   ctx->ut.release(); ctx->ucount.release(); ctx->cff.release(); ctx->uff.release();
   ctx->u_row_ptr.release(); ctx->u_ph_row_ptr.release(); ctx->u_kpns.release(); ctx->u_ph_kpn.release();
   ctx->u_X.release(); ctx->u_ph_st.release(); ctx->u_ph_V.release();
@@ -765,6 +770,10 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     CK(ctx->nitem.ensure(chunk));
     CK(ctx->item_ptr.ensure(chunk));
     CK(ctx->Cbuf.ensure(size_t(std::min<int64_t>(np, kMaxChunkPairs)) * Nmax));
+    // work items of a chunk: at most (pairs / 128 + k points) tiles, each in at most Nmax / 16
+    // column chunks
+    ctx->ws_cap = (std::min<int64_t>(np, kMaxChunkPairs) / 128 + chunk) * ((Nmax + 15) / 16);
+    CK(ctx->ws_desc.ensure(size_t(ctx->ws_cap) * 4));
     CK(ctx->tc_err.ensure(1));
     if (tensor_a) {   // g slices once per model; k phase slices per chunk
       const size_t gsz = size_t(ns_a) * tc_ncols_a(M) * tc_kp_a(M);
@@ -818,7 +827,7 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
         return launch_vertex_tc(M, D, ns, i0, nkc, hpp[i0], ctx->Abuf.p, ctx->phis.p, ctx->bslices.p,
                                 ctx->bscale.p, ctx->nitem.p, ctx->item_ptr.p, ctx->scratch.p, ctx->scratch.n,
                                 ctx->scal.p + 6, ctx->Cbuf.p, ctx->tc_err.p, st, e0, e1, width, kc, stages,
-                                ctx->withhold_mma);
+                                ctx->withhold_mma, ctx->ws_desc.p, ctx->ws_cap);
       };
       int &tuned = ctx->tune_cols[ns == 7 ? 0 : 1];
       int &tuned_kc = ctx->tune_kc[ns == 7 ? 0 : 1];
@@ -1131,6 +1140,13 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
     CK(launch_copy_f32(2 * ctx->n_entries, reinterpret_cast<const double *>(ctx->e_X.p),
                        reinterpret_cast<float *>(ctx->X32.p), st));
     CK(launch_copy_f32(ctx->n_ph_entries, ctx->ph_Y.p, ctx->Y32.p, st));
+    CK(ctx->Xff.ensure(ctx->n_entries));
+    CK(ctx->Yff.ensure(ctx->n_ph_entries));
+    CK(ctx->IJff.ensure(nst * 6));
+    CK(ctx->FGff.ensure(nph * 6));
+    CK(launch_copy_ff(2 * ctx->n_entries, reinterpret_cast<const double *>(ctx->e_X.p),
+                      reinterpret_cast<float2 *>(ctx->Xff.p), st));
+    CK(launch_copy_ff(ctx->n_ph_entries, ctx->ph_Y.p, ctx->Yff.p, st));
   }
 
   // Anderson acceleration (dragged level): ring of the last m+1 phonon updates g_j and
@@ -1206,6 +1222,8 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
       CK(td.start(st));
       if (ph32)
         CK(launch_drag_term32(D, B, entry_segs(ctx), ctx->X32.p, ctx->FG32.p, ctx->seg_part.p, ctx->Dterm.p, st));
+      else if (ph32_allowed)
+        CK(launch_drag_termff(D, B, entry_segs(ctx), ctx->Xff.p, ctx->FGff.p, ctx->seg_part.p, ctx->Dterm.p, st));
       else
         CK(launch_drag_term(D, B, entry_segs(ctx), ctx->F.p, ctx->G.p, ctx->seg_part.p, ctx->Dterm.p, st));
       CK(td.stop(st));
@@ -1341,6 +1359,9 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
       if (ph32) {
         CK(launch_pack6_f32(nst, ctx->I.p, ctx->J.p, ctx->IJ32.p, st));
         CK(launch_ph_sweep32(M, B, ctx->kinfo.p, ctx->Y32.p, ctx->IJ32.p, ctx->Btv.p, st));
+      } else if (ph32_allowed) {
+        CK(launch_pack6_ff(nst, ctx->I.p, ctx->J.p, ctx->IJff.p, st));
+        CK(launch_ph_sweepff(M, B, ctx->kinfo.p, ctx->Yff.p, ctx->IJff.p, ctx->Btv.p, st));
       } else {
         CK(launch_ph_sweep(M, D, B, ctx->kinfo.p, ctx->I.p, ctx->J.p, ctx->Btv.p, st));
       }
@@ -1354,6 +1375,7 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
         CK(launch_ph_update(M, D, B, ctx->Btv.p, ctx->F0.p, ctx->inv_nnW.p, ctx->F.p, ctx->G.p, st));
       }
       if (ph32) CK(launch_pack6_f32(nph, ctx->F.p, ctx->G.p, ctx->FG32.p, st));
+      else if (ph32_allowed) CK(launch_pack6_ff(nph, ctx->F.p, ctx->G.p, ctx->FGff.p, st));
       bool ok;
       s = inner_loop(1, ok);
       if (s != EPHB_OK) return s;

@@ -318,6 +318,53 @@ __global__ void __launch_bounds__(256) k_drag_sweep_seg(MeshDev D, BteDev B, Swe
     for (int c = 0; c < 6; ++c) part[g * 6 + c] = a[c];
 }
 
+// Float-float form of the drag term (mixed iteration once the outer residual is small): the
+// same sums from float-float copies of the rates (Xff: X+ hi, lo, X- hi, lo) and of F, G
+// (FGff: [mode][F0 F1 F2 G0 G1 G2] pairs), ~2^-47 of the summed magnitudes, on the FP32 pipe.
+__global__ void __launch_bounds__(256) k_drag_sweep_segff(MeshDev D, BteDev B, SweepSegs S,
+                                                          const float4 *__restrict__ Xff,
+                                                          const float2 *__restrict__ FGff, double *__restrict__ part) {
+  const int64_t g = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= S.nseg) return;
+  const int st = S.seg_row[g];
+  const int64_t b = S.seg_begin[g];
+  const int64_t rend = S.row_ptr[st + 1];
+  const int64_t e_end = b + kSeg < rend ? b + kSeg : rend;
+  const int nbr = B.nbr;
+  const uint32_t kc = B.kcrd[D.ibzw_list[st / B.nb]];
+  const int k0 = kc & 1023u, k1 = (kc >> 10) & 1023u, k2 = kc >> 20;
+  const bool unit_ratio = D.ratio[0] == 1 && D.ratio[1] == 1 && D.ratio[2] == 1;
+  FFAcc a[6];
+  for (int64_t e = b + lane; e < e_end; e += 32) {
+    const uint32_t pk = __ldcs(B.e_kpns + e);
+    const float4 X = __ldcs(Xff + e);
+    const int kp = unpack_kp(pk), s = unpack_s(pk);
+    const uint32_t pc = B.kcrd[kp];
+    int d0 = int(pc & 1023u) - k0, d1 = int((pc >> 10) & 1023u) - k1, d2 = int(pc >> 20) - k2;
+    d0 += d0 < 0 ? D.km.n[0] : 0;
+    d1 += d1 < 0 ? D.km.n[1] : 0;
+    d2 += d2 < 0 ? D.km.n[2] : 0;
+    if (!unit_ratio) {
+      d0 /= D.ratio[0];
+      d1 /= D.ratio[1];
+      d2 /= D.ratio[2];
+    }
+    const int64_t q = D.qm.flat(d0, d1, d2);
+    const int64_t mq = D.qm.flat(d0 ? D.qm.n[0] - d0 : 0, d1 ? D.qm.n[1] - d1 : 0, d2 ? D.qm.n[2] - d2 : 0);
+    const float2 *pq = FGff + (q * nbr + s) * 6, *pm = FGff + (mq * nbr + s) * 6;
+    const float2 xp = make_float2(X.x, X.y), xm = make_float2(X.z, X.w);
+    for (int c = 0; c < 6; ++c) {
+      ff_acc_mul(a[c], ff_neg(pq[c]), xp);
+      ff_acc_mul(a[c], pm[c], xm);
+    }
+  }
+  for (int c = 0; c < 6; ++c) {
+    const double v = warp_sum(ff_to_double(a[c]));
+    if (lane == 0) part[g * 6 + c] = v;
+  }
+}
+
 // FP32 form of the drag term (mixed iteration while the outer residual is large): the same
 // sums from FP32 copies of the rates (X32) and of F, G (FG32: [mode][F0 F1 F2 G0 G1 G2]).
 __global__ void __launch_bounds__(256) k_drag_sweep_seg32(MeshDev D, BteDev B, SweepSegs S,
@@ -371,6 +418,67 @@ __global__ void k_drag_finalize(int64_t nst, SweepSegs S, const double *part, do
 }
 
 // One warp per phonon row (q,s): Btv = sum Y/|stab| (S_k' I_<k'>n - I_km), fields I and J.
+// Float-float form of the phonon drag scatter (mixed iteration once the outer residual is
+// small), from float-float copies of Y and of the responses (IJff: [state][I0 I1 I2 J0 J1 J2]).
+template <bool SYM>
+__global__ void __launch_bounds__(256) k_ph_sweepff(ModelDev M, BteDev B, const int2 *__restrict__ kinfo,
+                                                    const float2 *__restrict__ Yff,
+                                                    const float2 *__restrict__ IJff, double *Btv) {
+  __shared__ float2 C[kMaxSym * 9];
+  if (SYM) {
+    for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) C[t] = ff_from_double(M.sym_cart[t]);
+    __syncthreads();
+  }
+  const int64_t row = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= B.nq * B.nbr) return;
+  FFAcc a[6];
+  for (int64_t e = B.ph_row_ptr[row] + lane; e < B.ph_row_ptr[row + 1]; e += 32) {
+    const int st = B.ph_st[e];
+    const uint32_t pk = B.ph_kpn[e];
+    const float2 y = Yff[e];
+    const int2 inf = kinfo[unpack_kp(pk)];
+    const float2 *own = IJff + int64_t(st) * 6;
+    float2 r[6];
+    for (int c = 0; c < 6; ++c) r[c] = make_float2(0.f, 0.f);
+    if (inf.x >= 0) {   // inf.x < 0: see the electron sweep
+      const float2 *src = IJff + (int64_t(inf.x) + unpack_n(pk)) * 6;
+      if (SYM) {
+        const float2 *Cs = C + 9 * (inf.y > 0 ? inf.y : 0);
+        for (int f = 0; f < 2; ++f)
+          for (int x = 0; x < 3; ++x) {
+            FFAcc t;
+            for (int z = 0; z < 3; ++z) ff_acc_mul(t, Cs[3 * x + z], src[3 * f + z]);
+            r[3 * f + x] = ff_norm(t);
+          }
+      } else {
+        for (int c = 0; c < 6; ++c) r[c] = src[c];
+      }
+    }
+    for (int c = 0; c < 6; ++c) ff_acc_mul(a[c], y, ff_sub(r[c], own[c]));
+  }
+  for (int c = 0; c < 6; ++c) {
+    const double v = warp_sum(ff_to_double(a[c]));
+    if (lane == 0) Btv[row * 6 + c] = v;
+  }
+}
+
+// float-float copies: out[i] = ff(a[i]) (n values); pack: out[i][0..2] = ff(A[i][..]),
+// out[i][3..5] = ff(B[i][..])
+__global__ void k_copy_ff(int64_t n, const double *a, float2 *out) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i < n) out[i] = ff_from_double(a[i]);
+}
+
+__global__ void k_pack6_ff(int64_t n, const double *A, const double *Bv, float2 *out) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  for (int c = 0; c < 3; ++c) {
+    out[i * 6 + c] = ff_from_double(A[i * 3 + c]);
+    out[i * 6 + 3 + c] = ff_from_double(Bv[i * 3 + c]);
+  }
+}
+
 // FP32 form of the phonon drag scatter (mixed iteration while the outer residual is large),
 // from FP32 copies of Y and of the responses (IJ32: [state][I0 I1 I2 J0 J1 J2]).
 template <bool SYM>
@@ -1137,6 +1245,37 @@ cudaError_t launch_and_mix(int64_t half, const double *ring, int64_t stride, int
   if (half == 0) return cudaSuccess;
   if (nslot < 1 || nslot > kAndMaxSlots) return cudaErrorInvalidValue;
   EPHB_LAUNCH(k_and_mix, unsigned((2 * half + 255) / 256), 256, 0, st, half, ring, stride, nslot, al, F, G);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_drag_termff(const MeshDev &D, const BteDev &B, const SweepSegs &S, const float4 *Xff,
+                               const float2 *FGff, double *part, double *Dterm, cudaStream_t st) {
+  if (B.nst == 0) return cudaSuccess;
+  if (S.nseg > 0)
+    EPHB_LAUNCH(k_drag_sweep_segff, unsigned((S.nseg * 32 + 255) / 256), 256, 0, st, D, B, S, Xff, FGff, part);
+  EPHB_LAUNCH(k_drag_finalize, unsigned((B.nst + 255) / 256), 256, 0, st, B.nst, S, part, Dterm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ph_sweepff(const ModelDev &M, const BteDev &B, const int2 *kinfo, const float2 *Yff,
+                              const float2 *IJff, double *Btv, cudaStream_t st) {
+  const unsigned g = unsigned((B.nq * B.nbr * 32 + 255) / 256);
+  if (M.nsym > 1)
+    EPHB_LAUNCH(k_ph_sweepff<true>, g, 256, 0, st, M, B, kinfo, Yff, IJff, Btv);
+  else
+    EPHB_LAUNCH(k_ph_sweepff<false>, g, 256, 0, st, M, B, kinfo, Yff, IJff, Btv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_ff(int64_t n, const double *a, float2 *out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  EPHB_LAUNCH(k_copy_ff, unsigned((n + 255) / 256), 256, 0, st, n, a, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack6_ff(int64_t n, const double *A, const double *Bv, float2 *out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  EPHB_LAUNCH(k_pack6_ff, unsigned((n + 255) / 256), 256, 0, st, n, A, Bv, out);
   return cudaGetLastError();
 }
 

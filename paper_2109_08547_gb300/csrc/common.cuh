@@ -96,6 +96,19 @@ __device__ __forceinline__ float2 ff_norm(const FFAcc &a) {
   return make_float2(h, l);
 }
 __device__ __forceinline__ float2 ff_neg(float2 x) { return make_float2(-x.x, -x.y); }
+// a - b in float-float
+__device__ __forceinline__ float2 ff_sub(float2 a, float2 b) {
+  float s, t;
+  ff_two_sum(a.x, -b.x, s, t);
+  t = __fadd_rn(t, __fsub_rn(a.y, b.y));
+  float h, l;
+  ff_two_sum(s, t, h, l);
+  return make_float2(h, l);
+}
+__device__ __forceinline__ double ff_to_double(const FFAcc &a) {
+  const float2 n = ff_norm(a);
+  return double(n.x) + double(n.y);
+}
 // float-float of a double (hi = nearest float, lo = nearest float of the remainder)
 __device__ __forceinline__ float2 ff_from_double(double x) {
   const float h = __double2float_rn(x);

@@ -120,7 +120,9 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
                              const double2 *A, const __nv_bfloat16 *phis, __nv_bfloat16 *bs, double *bscale,
                              int *nitem, int64_t *item_ptr, int64_t *scratch, int64_t scratch_elems,
                              int64_t *total_dev, double *Cbuf, int *err, cudaStream_t st, cudaEvent_t gemm0,
-                             cudaEvent_t gemm1, int ncm, int kc, int stages, int withhold = 0);
+                             cudaEvent_t gemm1, int ncm, int kc, int stages, int withhold, int64_t *ws_desc,
+                             int64_t ws_cap);
+// ws_desc: scratch of 4 int64 per work item (descriptors of the persistent form), ws_cap items
 // Stage A on tensor cores: T[kc][col] = sum_Re e^{ik.Re} g[Re][col] for the k of a chunk, as
 // the same exact-slice GEMM with the k phase slices as rows and the model's g slices (made
 // once by launch_g_slices, [ns][tc_ncols_a][tc_kp_a] BF16 + column scales) as B.
@@ -262,6 +264,15 @@ cudaError_t launch_drag_term32(const MeshDev &D, const BteDev &B, const SweepSeg
 cudaError_t launch_ph_sweep32(const ModelDev &M, const BteDev &B, const int2 *kinfo, const float *Y32,
                               const float *IJ32, double *Btv, cudaStream_t st);
 cudaError_t launch_pack6_f32(int64_t n, const double *A, const double *Bv, float *out, cudaStream_t st);
+// Float-float forms of the same two terms for the later outer iterations of the mixed
+// iteration: Xff (X+ hi, lo, X- hi, lo per entry), Yff, IJff ([state][6] pairs), FGff
+// ([mode][6] pairs); partial sums converted to FP64 per lane and reduced in FP64.
+cudaError_t launch_drag_termff(const MeshDev &D, const BteDev &B, const SweepSegs &S, const float4 *Xff,
+                               const float2 *FGff, double *part, double *Dterm, cudaStream_t st);
+cudaError_t launch_ph_sweepff(const ModelDev &M, const BteDev &B, const int2 *kinfo, const float2 *Yff,
+                              const float2 *IJff, double *Btv, cudaStream_t st);
+cudaError_t launch_copy_ff(int64_t n, const double *a, float2 *out, cudaStream_t st);
+cudaError_t launch_pack6_ff(int64_t n, const double *A, const double *Bv, float2 *out, cudaStream_t st);
 cudaError_t launch_copy_f32(int64_t n, const double *a, float *b, cudaStream_t st);
 // Anderson acceleration of the outer iteration over x = (F, G) (2 * half doubles): the
 // residual f = g - x, the dot products of a new residual with up to kAndMaxSlots ring vectors

@@ -532,33 +532,10 @@ struct WsItem {
   int nc, n0, ncw, npt;
   int64_t p0t0;   // first pair of the tile
   int kc;         // chunk-local k index
+  int pad;
 };
+static_assert(sizeof(WsItem) == 4 * sizeof(int64_t), "work-item descriptor size");
 
-__device__ __forceinline__ WsItem ws_item(const ModelDev &M, const MeshDev &D, const TcParams &P,
-                                          const int64_t *item_ptr, int64_t item) {
-  int64_t lo = 0, hi = P.nkc;
-  while (hi - lo > 1) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (item_ptr[mid] <= item) lo = mid; else hi = mid;
-  }
-  WsItem w;
-  w.kc = int(lo);
-  const int64_t i = P.i0 + lo;
-  const int k = D.ibzw_list[i];
-  const int nk = round_up(2 * __popc(D.amask[k]) * M.nb * M.nbr, 16);
-  const int nch = (nk + P.nc_max - 1) / P.nc_max;
-  w.nc = round_up((nk + nch - 1) / nch, 16);
-  const int64_t local = item - item_ptr[lo];
-  const int tile = int(local / nch), chunk = int(local % nch);
-  w.n0 = chunk * w.nc;
-  w.ncw = nk - w.n0 < w.nc ? nk - w.n0 : w.nc;
-  const int64_t p0 = D.pair_ptr[i];
-  const int64_t npl = D.pair_ptr[i + 1] - p0;
-  const int64_t t0 = int64_t(tile) * kTcM;
-  w.npt = int(npl - t0 < kTcM ? npl - t0 : kTcM);
-  w.p0t0 = p0 + t0;
-  return w;
-}
 
 // AND of v over the 128 epilogue threads (warps 0-3), named barrier 1
 __device__ __forceinline__ bool epi_sync_and(bool v) {
@@ -568,13 +545,42 @@ __device__ __forceinline__ bool epi_sync_and(bool v) {
   return r != 0;
 }
 
+// descriptors of every work item of a chunk (one thread per k), so that the roles of the
+// persistent kernel read one 32-byte record per item instead of searching item_ptr
+__global__ void k_ws_items(ModelDev M, MeshDev D, TcParams P, const int64_t *item_ptr, WsItem *desc) {
+  const int64_t kc = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (kc >= P.nkc) return;
+  const int64_t i = P.i0 + kc;
+  const int k = D.ibzw_list[i];
+  const int nk = round_up(2 * __popc(D.amask[k]) * M.nb * M.nbr, 16);
+  const int nch = (nk + P.nc_max - 1) / P.nc_max;
+  const int nc = round_up((nk + nch - 1) / nch, 16);
+  const int64_t p0 = D.pair_ptr[i];
+  const int64_t npl = D.pair_ptr[i + 1] - p0;
+  const int64_t base = item_ptr[kc];
+  const int64_t n = int64_t((npl + kTcM - 1) / kTcM) * nch;   // as counted by k_tc_items
+  for (int64_t l = 0; l < n; ++l) {
+    const int tile = int(l / nch), chunk = int(l % nch);
+    WsItem w;
+    w.kc = int(kc);
+    w.nc = nc;
+    w.n0 = chunk * nc;
+    w.ncw = nk - w.n0 < nc ? nk - w.n0 : nc;
+    const int64_t t0 = int64_t(tile) * kTcM;
+    w.npt = int(npl - t0 < kTcM ? npl - t0 : kTcM);
+    w.p0t0 = p0 + t0;
+    w.pad = 0;
+    desc[base + l] = w;
+  }
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
   asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" :: "r"(mbar) : "memory");
 }
 
 template <int NS, int NACC, int ST>
 __global__ void __launch_bounds__(kWsThreads, 1) k_vertex_gemm_ws(ModelDev M, MeshDev D, TcParams P, int64_t nitems,
-                                                                  const int64_t *__restrict__ item_ptr,
+                                                                  const WsItem *__restrict__ desc,
                                                                   const __nv_bfloat16 *__restrict__ phis,
                                                                   const __nv_bfloat16 *__restrict__ bs,
                                                                   const double *__restrict__ bscale, double *Cbuf,
@@ -624,12 +630,21 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_vertex_gemm_ws(ModelDev M, Me
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(smem_u32(&full[j % ST]));
     };
+    // the next item's descriptor and A rows are fetched while the current item's copies go out
+    WsItem w = blockIdx.x < nitems ? desc[blockIdx.x] : WsItem{};
+    int q0 = r0 < w.npt ? D.pair_q[w.p0t0 + r0] : -1, q1 = r0 + 64 < w.npt ? D.pair_q[w.p0t0 + r0 + 64] : -1;
     for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-      const WsItem w = ws_item(M, D, P, item_ptr, item);
-      const __nv_bfloat16 *src0 = r0 < w.npt ? phis + size_t(D.pair_q[w.p0t0 + r0]) * NS * P.Kp : nullptr;
-      const __nv_bfloat16 *src1 = r0 + 64 < w.npt ? phis + size_t(D.pair_q[w.p0t0 + r0 + 64]) * NS * P.Kp : nullptr;
+      const WsItem wn = item + gridDim.x < nitems ? desc[item + gridDim.x] : w;
+      int q0n = -1, q1n = -1;
+      const __nv_bfloat16 *src0 = q0 >= 0 ? phis + size_t(q0) * NS * P.Kp : nullptr;
+      const __nv_bfloat16 *src1 = q1 >= 0 ? phis + size_t(q1) * NS * P.Kp : nullptr;
       const __nv_bfloat16 *bsk = bs + (size_t(w.kc) * NS * P.Nmax + w.n0) * P.Kp;
+      const int kpre = nkb > 4 ? 4 : nkb - 1;
       for (int kb = 0; kb < nkb; ++kb) {
+        if (kb == kpre && item + gridDim.x < nitems) {
+          q0n = r0 < wn.npt ? D.pair_q[wn.p0t0 + r0] : -1;
+          q1n = r0 + 64 < wn.npt ? D.pair_q[wn.p0t0 + r0 + 64] : -1;
+        }
         const uint32_t slot = it % ST;
         if (it >= ST && !mbar_wait(smem_u32(&empty[slot]), ((it / ST) - 1) & 1)) {
           give_up();
@@ -661,6 +676,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_vertex_gemm_ws(ModelDev M, Me
         }
         ++it;
       }
+      w = wn;
+      q0 = q0n;
+      q1 = q1n;
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     if (ok)
@@ -672,9 +690,11 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_vertex_gemm_ws(ModelDev M, Me
       uint64_t last_bar = 0;                   // barrier address + parity of the last commit
       uint32_t last_par = 0;
       bool any = false;
+      WsItem wn = blockIdx.x < nitems ? desc[blockIdx.x] : WsItem{};
       for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
         if (abort_flag) break;
-        const WsItem w = ws_item(M, D, P, item_ptr, item);
+        const WsItem w = wn;
+        if (item + gridDim.x < nitems) wn = desc[item + gridDim.x];
         const uint32_t buf = tcount & 1;
         if (tcount >= 2 && !mbar_wait(smem_u32(&acce[buf]), ((tcount >> 1) - 1) & 1)) {
           give_up();
@@ -734,8 +754,10 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_vertex_gemm_ws(ModelDev M, Me
     // ---------------- epilogue (warps 0-3: tensor-memory lanes 32w .. 32w + 31)
     const int row = warp * 32 + lane;
     uint32_t tcount = 0;
+    WsItem wn = blockIdx.x < nitems ? desc[blockIdx.x] : WsItem{};
     for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
-      const WsItem w = ws_item(M, D, P, item_ptr, item);
+      const WsItem w = wn;
+      if (item + gridDim.x < nitems) wn = desc[item + gridDim.x];
       const uint32_t buf = tcount & 1;
       const bool waited = mbar_wait(smem_u32(&accf[buf]), (tcount >> 1) & 1);
       // the four warps agree before leaving, so no warp reads a buffer another abandoned
@@ -861,7 +883,8 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
                              const double2 *A, const __nv_bfloat16 *phis, __nv_bfloat16 *bs, double *bscale,
                              int *nitem, int64_t *item_ptr, int64_t *scratch, int64_t scratch_elems,
                              int64_t *total_dev, double *Cbuf, int *err, cudaStream_t st, cudaEvent_t gemm0,
-                             cudaEvent_t gemm1, int ncm, int kc, int stages, int withhold) {
+                             cudaEvent_t gemm1, int ncm, int kc, int stages, int withhold, int64_t *ws_desc,
+                             int64_t ws_cap) {
   if (nkc <= 0) return cudaSuccess;
   if (!tc_nc_valid(ns, ncm, kc, stages)) return cudaErrorInvalidValue;
   const int Kp = tc_kp(M), Nmax = tc_nmax(M);
@@ -901,6 +924,9 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
   };
   // persistent form: one CTA per SM
   auto go_ws = [&](auto kern) -> cudaError_t {
+    if (nitems > ws_cap) return cudaErrorInvalidValue;
+    WsItem *desc = reinterpret_cast<WsItem *>(ws_desc);
+    EPHB_LAUNCH(k_ws_items, unsigned((nkc + 255) / 256), 256, 0, st, M, D, P, item_ptr, desc);
     cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (r != cudaSuccess) return r;
     int dev = 0, nsm = 0;
@@ -908,7 +934,7 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
     if (r == cudaSuccess) r = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (r != cudaSuccess) return r;
     const unsigned grid = unsigned(nitems < nsm ? nitems : nsm);
-    EPHB_LAUNCH(kern, grid, kWsThreads, smem, st, M, D, P, nitems, item_ptr, phis, bs, bscale, Cbuf, err);
+    EPHB_LAUNCH(kern, grid, kWsThreads, smem, st, M, D, P, nitems, desc, phis, bs, bscale, Cbuf, err);
     return cudaGetLastError();
   };
   if (warp_specialised(kc, stages))
