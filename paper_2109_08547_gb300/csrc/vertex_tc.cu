@@ -58,6 +58,38 @@ __device__ inline void fixed_slices(double x, int ns, __nv_bfloat16 *out, size_t
   out[0] = __float2bfloat16_rn(ldexpf(float(N), -7));
 }
 
+// rint(x 2^p) (ties to even) from the bits of x, by integer operations only; the same value
+// as the FP64 scaling and conversion for every |x 2^p| < 2^62 (p <= 9 above the exponent of
+// x's leading bit keeps the shift in range).  Zero and subnormal x give 0.
+__device__ inline long long fixed_round(double x, int p) {
+  const unsigned long long b = __double_as_longlong(x);
+  const int e = int((b >> 52) & 0x7ff);
+  if (e == 0) return 0;
+  const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
+  const int sh = e - 1075 + p;   // x 2^p = m 2^sh
+  unsigned long long n;
+  if (sh >= 0) {
+    n = m << sh;
+  } else if (sh < -53) {
+    n = 0;                       // below 1/2
+  } else {
+    const int r = -sh;
+    const unsigned long long q = m >> r, rem = m & ((1ull << r) - 1), half = 1ull << (r - 1);
+    n = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+  }
+  return (b >> 63) ? -(long long)n : (long long)n;
+}
+
+// the ns slices of the integer N (as fixed_slices does after its rounding)
+__device__ inline void int_slices(long long N, int ns, __nv_bfloat16 *out, size_t stride) {
+  for (int i = ns - 1; i >= 1; --i) {
+    const long long d = ((N + 128) & 255) - 128;
+    N = (N - d) >> 8;
+    out[i * stride] = __float2bfloat16_rn(ldexpf(float(d), -7 - 8 * i));
+  }
+  out[0] = __float2bfloat16_rn(ldexpf(float(N), -7));
+}
+
 // Phase slices of every q of the phonon mesh: PhiS[q][slice][Kp] (BF16)
 __global__ void k_phase_slices(ModelDev M, MeshDev D, int ns, int Kp, __nv_bfloat16 *phis) {
   const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
@@ -77,50 +109,70 @@ __global__ void k_phase_slices(ModelDev M, MeshDev D, int ns, int Kp, __nv_bfloa
 }
 
 // B' slices of the k points of a chunk: BS[kc][slice][Nmax][Kp] (BF16) and column scales.
-// One warp per column j' = ml*(2 nb nbr) + part*(nb nbr) + n'*nbr + a.
-__global__ void k_b_slices(ModelDev M, MeshDev D, int64_t i0, int64_t nkc, const double2 *A, int ns, int Kp,
-                           int Nmax, __nv_bfloat16 *bs, double *bscale) {
-  const int64_t w = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= nkc * Nmax) return;
-  const int64_t kc = w / Nmax;
-  const int jp = int(w % Nmax);
+// Column j' = ml*(2 nb nbr) + part*(nb nbr) + n'*nbr + a.  One block per (k, ml): the stage-A
+// rows of that initial band (R x nb nbr complex values) are read once, coalesced, into shared
+// memory; each of its 2 nb nbr columns gets the power of two sigma >= its largest magnitude;
+// the slices are written with consecutive threads on consecutive r.  Integer arithmetic only
+// (the scale, the rounding to 2^-55 of sigma and the digits): no FP64 operation.  Block
+// y = nb writes the zero padding columns past 2 nb nb nbr.
+__global__ void __launch_bounds__(256) k_b_slices(ModelDev M, MeshDev D, int64_t i0, const double2 *A, int ns,
+                                                  int Kp, int Nmax, __nv_bfloat16 *bs, double *bscale) {
+  extern __shared__ double2 tileA[];            // [R][nb nbr]
+  __shared__ int sh_ex[2 * kMaxBands * kMaxBranches];   // exponent of sigma per column (-2000: zero column)
+  const int64_t kc = blockIdx.x;
+  const int ml = blockIdx.y;
   const int nb = M.nb, nbr = M.nbr, R = M.nRgp;
-  const int nbnbr = nb * nbr;
-  const int jmax = nb * nb * nbr;
+  const int nbnbr = nb * nbr, jmax = nb * nb * nbr;
   const int k = D.ibzw_list[i0 + kc];
-  const int nact = __popc(D.amask[k]);
-  const int ml = jp / (2 * nbnbr), part = (jp / nbnbr) & 1, rest = jp % nbnbr;
-  const bool live = ml < nact;
-  const int j = ml * nbnbr + rest;    // column of the stage-A tile
-  const double2 *Ak = A + size_t(kc) * R * jmax;
-  // largest magnitude of the column
-  double mx = 0.0;
-  for (int r = lane; r < 2 * R; r += 32) {
-    if (!live) break;
-    const double2 a = Ak[size_t(r < R ? r : r - R) * jmax + j];
-    const double v = r < R ? (part == 0 ? a.x : a.y) : (part == 0 ? -a.y : a.x);
-    mx = fmax(mx, fabs(v));
-  }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  int ex = 0;
-  if (mx > 0.0) {
-    frexp(mx, &ex);          // mx = f 2^ex, f in [0.5, 1): 2^ex >= mx
-  }
-  const double sigma = mx > 0.0 ? ldexp(1.0, ex) : 1.0;
-  const double inv_sigma = mx > 0.0 ? ldexp(1.0, -ex) : 1.0;
-  if (lane == 0) bscale[kc * Nmax + jp] = sigma;
-  __nv_bfloat16 *dst = bs + (size_t(kc) * ns * Nmax + jp) * Kp;
+  const bool live = ml < nb && ml < __popc(D.amask[k]);
+  const int c0 = ml < nb ? ml * 2 * nbnbr : 2 * nb * nbnbr;    // first column of the block
+  const int ncol = ml < nb ? 2 * nbnbr : Nmax - 2 * nb * nbnbr;
   const size_t sstride = size_t(Nmax) * Kp;
-  for (int r = lane; r < Kp; r += 32) {
-    double v = 0.0;
-    if (live && r < 2 * R) {
-      const double2 a = Ak[size_t(r < R ? r : r - R) * jmax + j];
-      v = r < R ? (part == 0 ? a.x : a.y) : (part == 0 ? -a.y : a.x);
+  __nv_bfloat16 *dst = bs + (size_t(kc) * ns * Nmax + c0) * Kp;
+  if (!live) {   // zero slices, scale 1
+    for (int t = threadIdx.x; t < ncol * Kp; t += blockDim.x) {
+      const int c = t / Kp, r = t - c * Kp;
+      for (int sl = 0; sl < ns; ++sl) dst[sl * sstride + size_t(c) * Kp + r] = __float2bfloat16_rn(0.f);
     }
-    fixed_slices(v * inv_sigma, ns, dst + r, sstride);   // sigma is a power of two: exact
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) bscale[kc * Nmax + c0 + c] = 1.0;
+    return;
+  }
+  const double2 *Ak = A + size_t(kc) * R * jmax + size_t(ml) * nbnbr;
+  for (int t = threadIdx.x; t < R * nbnbr; t += blockDim.x) {
+    const int r = t / nbnbr, j = t - r * nbnbr;
+    tileA[t] = Ak[size_t(r) * jmax + j];
+  }
+  __syncthreads();
+  // column c = part * nbnbr + rest; row r < R: (Re, Im)[part] of A[r]; r >= R: (-Im, Re)[part]
+  auto value_bits = [&](int c, int r) -> unsigned long long {
+    const int part = c >= nbnbr, rest = c - part * nbnbr;
+    const double2 a = tileA[(r < R ? r : r - R) * nbnbr + rest];
+    const double v = r < R ? (part == 0 ? a.x : a.y) : (part == 0 ? -a.y : a.x);
+    return (unsigned long long)__double_as_longlong(v);
+  };
+  for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+    unsigned long long mx = 0;   // largest |v| as bits (the order of non-negative doubles)
+    for (int r = 0; r < 2 * R; ++r) {
+      const unsigned long long ab = value_bits(c, r) & 0x7fffffffffffffffull;
+      mx = ab > mx ? ab : mx;
+    }
+    const int e = int(mx >> 52);
+    // sigma = 2^ex with ex = e - 1022 (2^ex >= mx, as frexp gives); a zero (or subnormal) column: 1
+    const int ex = e == 0 ? 0 : e - 1022;
+    sh_ex[c] = e == 0 ? -2000 : ex;
+    bscale[kc * Nmax + c0 + c] = __longlong_as_double((long long)(ex + 1023) << 52);
+  }
+  __syncthreads();
+  const int top = 7 + 8 * (ns - 1);
+  for (int t = threadIdx.x; t < ncol * Kp; t += blockDim.x) {
+    const int c = t / Kp, r = t - c * Kp;
+    long long N = 0;
+    if (r < 2 * R && sh_ex[c] != -2000) N = fixed_round(__longlong_as_double(value_bits(c, r)), top - sh_ex[c]);
+    int_slices(N, ns, dst + size_t(c) * Kp + r, sstride);
   }
 }
+
+size_t b_slices_smem(const ModelDev &M) { return size_t(M.nRgp) * M.nb * M.nbr * sizeof(double2); }
 
 // Phase slices of the k points of a chunk (stage A rows): PhiK[kc][slice][Kp] with the
 // (cos, sin) of 2 pi k.Re for r < nRe and nRe <= r < 2 nRe.
@@ -888,8 +940,13 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
   if (nkc <= 0) return cudaSuccess;
   if (!tc_nc_valid(ns, ncm, kc, stages)) return cudaErrorInvalidValue;
   const int Kp = tc_kp(M), Nmax = tc_nmax(M);
-  const int64_t nw = nkc * Nmax;
-  EPHB_LAUNCH(k_b_slices, unsigned((nw * 32 + 255) / 256), 256, 0, st, M, D, i0, nkc, A, ns, Kp, Nmax, bs, bscale);
+  {
+    const size_t smem = b_slices_smem(M);
+    cudaError_t r = cudaFuncSetAttribute(k_b_slices, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (r != cudaSuccess) return r;
+    EPHB_LAUNCH(k_b_slices, dim3(unsigned(nkc), unsigned(M.nb + 1)), 256, smem, st, M, D, i0, A, ns, Kp, Nmax, bs,
+                bscale);
+  }
   const int nprod = ns * (ns + 1) / 2;
   EPHB_LAUNCH(k_tc_items, unsigned((nkc + 255) / 256), 256, 0, st, M, D, i0, nkc, ncm, Kp, nprod, nitem,
               reinterpret_cast<unsigned long long *>(total_dev + 1));
