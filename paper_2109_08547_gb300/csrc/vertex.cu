@@ -39,6 +39,11 @@ __device__ inline double gauss_d(double x, const RateParams &rp) {
   const double r = x * rp.inv_sigma;
   return exp(-0.5 * r * r) * rp.gnorm;
 }
+// the same for x already known to lie inside the cutoff
+__device__ inline double gauss_in(double x, const RateParams &rp) {
+  const double r = x * rp.inv_sigma;
+  return exp(-0.5 * r * r) * rp.gnorm;
+}
 
 // ------------------------------------------------------------------------ count pass
 __global__ void k_rate_count(ModelDev M, MeshDev D, RateParams rp, int *cntE, int *cntPh,
@@ -496,7 +501,9 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
   const double2 *ckp = D.cvec + size_t(kp) * nb * nb;
   const double2 *uq = ut + size_t(q) * nbr * nbr;
   const double *wrq = wr + size_t(q) * nbr;
-  double g2[NBM * NBM * NBRM];
+  // |g|^2 per (m, n, s) as a float-float pair; the FP64 conversion and the w_ref/w factor are
+  // applied only where a tuple inside the delta cutoff needs the value
+  float2 g2[NBM * NBM * NBRM];
   if (ROT32) {
     for (int ml = 0; ml < nact; ++ml)
       for (int nl = 0; nl < nactp; ++nl) {
@@ -521,7 +528,7 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
             gr = fmaf(Wr[a], ur, fmaf(-Wi[a], ui, gr));
             gi = fmaf(Wr[a], ui, fmaf(Wi[a], ur, gi));
           }
-          g2[(ml * nactp + nl) * nbr + s] = double(gr * gr + gi * gi) * wrq[s];
+          g2[(ml * nactp + nl) * nbr + s] = make_float2(gr * gr + gi * gi, 0.f);
         }
       }
   } else {
@@ -565,8 +572,7 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
           FFAcc m2;
           ff_acc_mul(m2, Gr, Gr);
           ff_acc_mul(m2, Gi, Gi);
-          const float2 m = ff_norm(m2);
-          g2[(ml * nactp + nl) * nbr + s] = (double(m.x) + double(m.y)) * wrq[s];
+          g2[(ml * nactp + nl) * nbr + s] = ff_norm(m2);
         }
       }
   }
@@ -584,6 +590,12 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
     Xm[t] = 0.0;
     flg[t] = 0;
     if (!(wq[s] > D.omega_min)) continue;
+    // the cutoff test first: tuples with neither delta inside it need no average or occupation
+    const double dxp = ekp[n] - ek[m] - wq[s];
+    const double dxm = ekp[n] - ek[m] + wq[s];
+    const bool inp = fabs(dxp) <= rp.cut, inm = fabs(dxm) <= rp.cut;
+    if (!inp && !inm) continue;
+    flg[t] = uint8_t((inp ? 1 : 0) | (inm ? 2 : 0));
     double sum = 0.0;
     int cnt = 0;
     for (int a = gk[2 * m]; a < gk[2 * m + 1]; ++a) {
@@ -593,25 +605,24 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
         if (!((an >> b) & 1u)) continue;
         const int bl = __popc(an & ((1u << b) - 1u));
         for (int c = gq[2 * s]; c < gq[2 * s + 1]; ++c) {
-          sum += g2[(al * nactp + bl) * nbr + c];
+          const float2 v = g2[(al * nactp + bl) * nbr + c];
+          sum += (double(v.x) + double(v.y)) * wrq[c];
           ++cnt;
         }
       }
     }
-    const double dxp = ekp[n] - ek[m] - wq[s];
-    const double dxm = ekp[n] - ek[m] + wq[s];
+    const double gp = inp ? gauss_in(dxp, rp) : 0.0, gm = inm ? gauss_in(dxm, rp) : 0.0;
     if (rp.vertex_only) {   // T-independent vertex weights V+-: occupation factors left out
       const double v = rp.inv_Nq_pref * (cnt == 1 ? sum : sum / double(cnt));
-      Xp[t] = v * gauss_d(dxp, rp);
-      Xm[t] = v * gauss_d(dxm, rp);
+      Xp[t] = v * gp;
+      Xm[t] = v * gm;
     } else {
       const double nqs = nbq[size_t(q) * nbr + s];
       const double occ =
           rp.inv_Nq_pref * (cnt == 1 ? sum : sum / double(cnt)) * fk[size_t(k) * nb + m] * (1.0 - fk[size_t(kp) * nb + n]);
-      Xp[t] = occ * nqs * gauss_d(dxp, rp);
-      Xm[t] = occ * (1.0 + nqs) * gauss_d(dxm, rp);
+      Xp[t] = occ * nqs * gp;
+      Xm[t] = occ * (1.0 + nqs) * gm;
     }
-    flg[t] = uint8_t((fabs(dxp) <= rp.cut ? 1 : 0) | (fabs(dxm) <= rp.cut ? 2 : 0));
   }
   // electron rows (k, m): entries ordered (n, s)
   const int64_t pl = pg - p0;
