@@ -476,63 +476,71 @@ def main():
     ms_corr = mean(lambda r: r.solve["ms_corr"])
     cands = [("stage_a", ms_a), ("epilogue", ms_ep), ("self_sweep", ms_self), ("corr", ms_corr)]
     cands.append(("stage_b", ms_b) if args.precision == "fp64" else ("gemm", ms_g))
+    def roof_of(dominant):
+        if dominant == "stage_b":
+            achieved = r0.rates["stage_b_flops"] / (ms_b * 1e-3) / 1e12
+            tr = profile_traffic("stage_b_rates", "vertex.cu")
+            roof = {"kernel": "k_stage_b_rates (R_ph contraction + rotations + rates, FP64)", "bound": "alu",
+                    "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": fp64_src,
+                    "traffic": (tr[0] * r0.rates["n_pairs"]) if tr else None,
+                    "ms_per_step": ms_b, "share_of_step": ms_b / step_ms}
+        elif dominant == "gemm":
+            # tensor-core contraction: the MMA work the slicing issues, against the measured BF16 peak
+            pk = peaks.get("bf16_tflops", 1900.0)
+            achieved = r0.rates["tensor_flops"] / (ms_g * 1e-3) / 1e12
+            tr = profile_traffic("vertex_gemm", "vertex_tc.cu")
+            roof = {"kernel": f"k_vertex_gemm (tcgen05 R_ph contraction, {args.precision})", "bound": "tensor",
+                    "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured burst)" if "bf16_tflops" in peaks
+                    else "fallback", "traffic": (tr[0] * r0.rates["n_pairs"]) if tr else None,
+                    "ms_per_step": ms_g, "share_of_step": ms_g / step_ms}
+        elif dominant == "stage_a":
+            achieved = r0.rates["stage_a_flops"] / (ms_a * 1e-3) / 1e12
+            roof = {"kernel": "k_stage_a1/a2 (R_e contraction and band rotation, FP64)", "bound": "alu",
+                    "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": fp64_src, "traffic": None,
+                    "ms_per_step": ms_a, "share_of_step": ms_a / step_ms}
+        elif dominant == "corr":
+            # FP32 correction sweeps of the mixed iteration: the run words (8 B per run) are the
+            # algorithmic stream; the partner vectors are L2/L1-resident gathers and not counted
+            n32 = r0.solve["n_sweeps32"]
+            pk = peaks.get("hbm_gbs", 6800.0)
+            achieved = 8.0 * r0.solve["n_runs"] * n32 / (ms_corr * 1e-3) / 1e9
+            tr = profile_traffic("corr_sweep", "bte.cu")
+            roof = {"kernel": "k_corr_sweep_seg + k_corr_finalize (FP32 correction sweeps of the mixed iteration)",
+                    "bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s", "frac": achieved / pk,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback",
+                    "traffic": (tr[0] * r0.solve["n_runs"]) if tr else None,
+                    "ms_per_step": ms_corr, "share_of_step": ms_corr / step_ms}
+        elif dominant == "epilogue":
+            achieved = r0.rates["rot_flops"] / (ms_ep * 1e-3) / 1e12
+            tr = profile_traffic("rate_epilogue", "vertex.cu")
+            roof = {"kernel": "k_rate_epilogue (rotations, |g|^2, occupations, delta, writes; FP64)", "bound": "alu",
+                    "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": fp64_src,
+                    "traffic": (tr[0] * r0.rates["n_pairs"]) if tr else None,
+                    "ms_per_step": ms_ep, "share_of_step": ms_ep / step_ms}
+        else:
+            # the self-term gather sweep: 6 FP64 multiply-adds per partner run; the run stream
+            # (12 B per run) sits in L2 between sweeps, so the FP64 pipe is the bound
+            nsw = r0.solve["n_sweeps"]
+            achieved = r0.solve["e_sweep_flops"] * nsw / (ms_self * 1e-3) / 1e12
+            tr = profile_traffic("self_sweep", "bte.cu")
+            roof = {"kernel": "k_self_sweep_seg (electron self-term gather sweep, FP64)", "bound": "alu",
+                    "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": fp64_src,
+                    "traffic": (tr[0] * r0.solve["n_runs"]) if tr else None,
+                    "hbm_gbs_algorithmic": r0.solve["e_sweep_bytes"] * nsw / (ms_self * 1e-3) / 1e9,
+                    "ms_per_step": ms_self, "share_of_step": ms_self / step_ms}
+
+
+        return roof
+
     dominant = max(cands, key=lambda x: x[1])[0]
-    if dominant == "stage_b":
-        achieved = r0.rates["stage_b_flops"] / (ms_b * 1e-3) / 1e12
-        tr = profile_traffic("stage_b_rates", "vertex.cu")
-        roof = {"kernel": "k_stage_b_rates (R_ph contraction + rotations + rates, FP64)", "bound": "alu",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": fp64_src,
-                "traffic": (tr[0] * r0.rates["n_pairs"]) if tr else None,
-                "ms_per_step": ms_b, "share_of_step": ms_b / step_ms}
-    elif dominant == "gemm":
-        # tensor-core contraction: the MMA work the slicing issues, against the measured BF16 peak
-        pk = peaks.get("bf16_tflops", 1900.0)
-        achieved = r0.rates["tensor_flops"] / (ms_g * 1e-3) / 1e12
-        tr = profile_traffic("vertex_gemm", "vertex_tc.cu")
-        roof = {"kernel": f"k_vertex_gemm (tcgen05 R_ph contraction, {args.precision})", "bound": "tensor",
-                "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured burst)" if "bf16_tflops" in peaks
-                else "fallback", "traffic": (tr[0] * r0.rates["n_pairs"]) if tr else None,
-                "ms_per_step": ms_g, "share_of_step": ms_g / step_ms}
-    elif dominant == "stage_a":
-        achieved = r0.rates["stage_a_flops"] / (ms_a * 1e-3) / 1e12
-        roof = {"kernel": "k_stage_a1/a2 (R_e contraction and band rotation, FP64)", "bound": "alu",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": fp64_src, "traffic": None,
-                "ms_per_step": ms_a, "share_of_step": ms_a / step_ms}
-    elif dominant == "corr":
-        # FP32 correction sweeps of the mixed iteration: the run words (8 B per run) are the
-        # algorithmic stream; the partner vectors are L2/L1-resident gathers and not counted
-        n32 = r0.solve["n_sweeps32"]
-        pk = peaks.get("hbm_gbs", 6800.0)
-        achieved = 8.0 * r0.solve["n_runs"] * n32 / (ms_corr * 1e-3) / 1e9
-        tr = profile_traffic("corr_sweep", "bte.cu")
-        roof = {"kernel": "k_corr_sweep_seg + k_corr_finalize (FP32 correction sweeps of the mixed iteration)",
-                "bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s", "frac": achieved / pk,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback",
-                "traffic": (tr[0] * r0.solve["n_runs"]) if tr else None,
-                "ms_per_step": ms_corr, "share_of_step": ms_corr / step_ms}
-    elif dominant == "epilogue":
-        achieved = r0.rates["rot_flops"] / (ms_ep * 1e-3) / 1e12
-        tr = profile_traffic("rate_epilogue", "vertex.cu")
-        roof = {"kernel": "k_rate_epilogue (rotations, |g|^2, occupations, delta, writes; FP64)", "bound": "alu",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": fp64_src,
-                "traffic": (tr[0] * r0.rates["n_pairs"]) if tr else None,
-                "ms_per_step": ms_ep, "share_of_step": ms_ep / step_ms}
-    else:
-        # the self-term gather sweep: 6 FP64 multiply-adds per partner run; the run stream
-        # (12 B per run) sits in L2 between sweeps, so the FP64 pipe is the bound
-        nsw = r0.solve["n_sweeps"]
-        achieved = r0.solve["e_sweep_flops"] * nsw / (ms_self * 1e-3) / 1e12
-        tr = profile_traffic("self_sweep", "bte.cu")
-        roof = {"kernel": "k_self_sweep_seg (electron self-term gather sweep, FP64)", "bound": "alu",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": fp64_src,
-                "traffic": (tr[0] * r0.solve["n_runs"]) if tr else None,
-                "hbm_gbs_algorithmic": r0.solve["e_sweep_bytes"] * nsw / (ms_self * 1e-3) / 1e9,
-                "ms_per_step": ms_self, "share_of_step": ms_self / step_ms}
+    roof = roof_of(dominant)
+    # every candidate kernel against its own bound, largest share first
+    rooflines = [dict(roof_of(n), name=n) for n, _ in sorted(cands, key=lambda x: -x[1])]
 
     # end-to-end through the C ABI with host buffers: model H2D (pinned) + path + coefficients D2H
     e2e = None
@@ -614,6 +622,8 @@ def main():
                        "kmesh": list(wl.kmesh), "qmesh": list(wl.qmesh), "T_K": wl.T_K, "mu_eV": wl.mu_eV,
                        "window_eV": list(wl.window), "sigma_eV": wl.sigma_eV, "level": "dragged+KO",
                        "tol": wl.tol, "precision": args.precision, "solve": args.solve, "outer_accel": args.accel,
+                       "tc_tile": {"cols": r0.rates["tc_cols"], "kblock": r0.rates["tc_kblock"],
+                                   "stages": r0.rates["tc_stages"]},
                        "l2": "256 MB buffer written before every step",
                        "parallelism": f"replicas x{world}", "tuples_per_step": r0.rates["n_tuples"],
                        "entries": r0.rates["n_entries"], "pairs": r0.rates["n_pairs"]},
@@ -625,9 +635,10 @@ def main():
                           "self_sweep_kernel": r0.solve["ms_self_kernel"], "n_runs": r0.solve["n_runs"],
                           "drag_terms": r0.solve["ms_drag"], "ph_sweeps": r0.solve["ms_ph_sweep"],
                           "n_sweeps": r0.solve["n_sweeps"], "outer_iters": r0.solve["outer_iters"],
-                          "outer_iters32": r0.solve["outer_iters32"]},
+                          "outer_iters32": r0.solve["outer_iters32"], "fp32_corrections": ms_corr,
+                          "n_sweeps32": r0.solve["n_sweeps32"]},
             "variants": variants, "batched": batched, "warm_start": warm,
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "roofline": roof, "rooflines": rooflines, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(out))
     ctx.close()

@@ -181,13 +181,16 @@ typedef struct {
   double stage_a_flops;        /* algorithmic flops of the R_e contraction                 */
   double stage_b_flops;        /* algorithmic flops of the R_ph contraction + rotations    */
   double ms_epilogue;          /* tensor-core modes: device time of the rotation/rate kernel */
-  double tensor_flops;         /* tensor-core modes: flops issued as tcgen05.mma           */
+  double tensor_flops;         /* tensor-core modes: flops issued as tcgen05.mma by the
+                                  stage-B contraction (the work ms_gemm times)              */
   double rot_flops;            /* algorithmic flops of the band and branch rotations       */
   double ms_gemm;              /* tensor-core modes: device time of the tcgen05 GEMM kernel  */
   int tc_cols;                 /* tensor-core modes: column-chunk width used               */
   int autotuned;               /* 1 if this call chose the tile shape by timing candidates */
   int tc_kblock;               /* tensor-core modes: K per shared-memory stage             */
-  int tc_stages;               /* tensor-core modes: shared-memory stages (K16 x 2: 2 CTAs/SM) */
+  int tc_stages;               /* tensor-core modes: shared-memory stages (K16 x 2: 2 CTAs/SM;
+                                  K16 x 5: the persistent warp-specialised form)          */
+  double tensor_flops_a;       /* flops issued as tcgen05.mma by stage A (tensor cores)    */
 } ephb_rates_info;
 
 ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst, int ninst,

@@ -78,7 +78,8 @@ class RatesInfoC(C.Structure):
                 ("n_pairs", C.c_int64), ("ms", C.c_double), ("ms_stage_a", C.c_double), ("ms_stage_b", C.c_double),
                 ("stage_a_flops", C.c_double), ("stage_b_flops", C.c_double), ("ms_epilogue", C.c_double),
                 ("tensor_flops", C.c_double), ("rot_flops", C.c_double), ("ms_gemm", C.c_double),
-                ("tc_cols", C.c_int), ("autotuned", C.c_int), ("tc_kblock", C.c_int), ("tc_stages", C.c_int)]
+                ("tc_cols", C.c_int), ("autotuned", C.c_int), ("tc_kblock", C.c_int), ("tc_stages", C.c_int),
+                ("tensor_flops_a", C.c_double)]
 
 
 class SolveOptsC(C.Structure):

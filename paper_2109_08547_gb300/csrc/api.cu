@@ -878,7 +878,7 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     CK(cudaMemcpyAsync(&tfl, ctx->scal.p + 7, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (herr) return fail(ctx, EPHB_ETIMEOUT, "a tensor-core wait gave up (vertex contraction)");
-    tensor_flops = double(tfl) + tensor_flops_a;
+    tensor_flops = double(tfl);
   }
   unsigned long long cnt[5];
   CK(cudaMemcpyAsync(cnt, ctx->ucount.p, sizeof(cnt), cudaMemcpyDeviceToHost, st));
@@ -905,6 +905,7 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     out->stage_b_flops = double(cnt[2]);
     out->ms_epilogue = tc.ms;
     out->tensor_flops = tensor_flops;
+    out->tensor_flops_a = tensor_flops_a;
     out->rot_flops = double(cnt[4]);
     out->ms_gemm = tg.ms;
     out->tc_cols = tensor ? (ncm ? ncm : ctx->tune_cols[ns == 7 ? 0 : 1]) : 0;
