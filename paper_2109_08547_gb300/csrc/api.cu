@@ -696,6 +696,12 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
   rp.cut = delta->cutoff_sigmas * delta->sigma_eV;
   rp.inv_sigma = 1.0 / delta->sigma_eV;
   rp.gnorm = 1.0 / (delta->sigma_eV * std::sqrt(2.0 * kPi));
+  auto ff_split = [](double v) {
+    const float h = float(v);
+    return make_float2(h, float(v - double(h)));
+  };
+  rp.inv_sigma_ff = ff_split(rp.inv_sigma);
+  rp.gnorm_ff = ff_split(rp.gnorm);
   rp.inv_Nq_pref = 2.0 * kPi / (kHbarEVs * double(nq));
   rp.y_scale = double(nq) / double(ctx->km.size());
   rp.vertex_only = multi ? 1 : 0;

@@ -96,6 +96,24 @@ __device__ __forceinline__ float2 ff_norm(const FFAcc &a) {
   return make_float2(h, l);
 }
 __device__ __forceinline__ float2 ff_neg(float2 x) { return make_float2(-x.x, -x.y); }
+// float-float product: the leading product exactly (FMA), the cross terms in FP32
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  float h, l;
+  ff_two_sum(p, e, h, l);
+  return make_float2(h, l);
+}
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  float s, t;
+  ff_two_sum(a.x, b.x, s, t);
+  t = __fadd_rn(t, __fadd_rn(a.y, b.y));
+  float h, l;
+  ff_two_sum(s, t, h, l);
+  return make_float2(h, l);
+}
 // a - b in float-float
 __device__ __forceinline__ float2 ff_sub(float2 a, float2 b) {
   float s, t;

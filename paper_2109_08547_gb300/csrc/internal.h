@@ -80,6 +80,7 @@ cudaError_t launch_count_reps(const int *rep, int64_t n, int64_t *out, cudaStrea
 struct RateParams {
   double T, mu, sigma, cut, inv_Nq_pref;   // inv_Nq_pref = 2 pi / (hbar N_q)
   double inv_sigma, gnorm;                 // 1 / sigma, 1 / (sigma sqrt(2 pi))
+  float2 inv_sigma_ff, gnorm_ff;           // the same as float-float pairs
   double y_scale;                          // N_q / N_k
   int vertex_only;                         // 1: store V+- = 2pi/(hbar N_q)|g|^2 delta (no occupations)
   int rot_fp32;                            // 1: band/branch rotations in FP32 (mixed mode)

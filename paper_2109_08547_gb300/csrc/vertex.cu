@@ -45,6 +45,40 @@ __device__ inline double gauss_in(double x, const RateParams &rp) {
   return exp(-0.5 * r * r) * rp.gnorm;
 }
 
+// 1/n! for n = 0..13 and ln 2 as float-float pairs (hi = nearest FP32, lo = nearest FP32 of
+// the remainder; computed from the exact rationals and a 60-digit ln 2)
+__constant__ float2 kInvFact[14] = {
+    {0x1p+0f, 0.f}, {0x1p+0f, 0.f}, {0x1p-1f, 0.f}, {0x1.555556p-3f, -0x1.555556p-28f},
+    {0x1.555556p-5f, -0x1.555556p-30f}, {0x1.111112p-7f, -0x1.ddddde0p-32f}, {0x1.6c16c2p-10f, -0x1.27d27ep-35f},
+    {0x1.a01a02p-13f, -0x1.7f97fap-39f}, {0x1.a01a02p-16f, -0x1.7f97fap-42f}, {0x1.71de3ap-19f, 0x1.55b1ccp-45f},
+    {0x1.27e4fcp-22f, -0x1.10ec14p-47f}, {0x1.ae6456p-26f, 0x1.fd5138p-52f}, {0x1.1eed8ep-29f, 0x1.ff1b12p-54f},
+    {0x1.612462p-33f, -0x1.8af25ep-58f}};
+
+// e^y in float-float for -60 <= y <= 0: y = k ln2 + r with |r| <= ln2/2 (plus rounding),
+// e^r from its Taylor series to r^13/13! (the remainder is below 1e-17 of the sum) by
+// float-float Horner steps, then the exact scaling by 2^k.  ~2^-46 relative, FP32 pipe only.
+__device__ inline float2 exp_ff(float2 y) {
+  const float2 ln2 = make_float2(0x1.62e43p-1f, -0x1.05c61p-29f);
+  const int k = __float2int_rn(__fmul_rn(y.x, 0x1.715476p+0f));   // y / ln2, nearest integer
+  const float2 r = ff_add(y, ff_neg(ff_mul(make_float2(float(k), 0.f), ln2)));
+  float2 p = kInvFact[13];
+  for (int n = 12; n >= 0; --n) p = ff_add(ff_mul(p, r), kInvFact[n]);
+  const float s = __int_as_float((k + 127) << 23);   // 2^k, k >= -87 here
+  return make_float2(__fmul_rn(p.x, s), __fmul_rn(p.y, s));
+}
+
+// gauss_in with the exponential in float-float: the FP64 pipe sees only the conversions of x
+// in and of the result out; arguments past 60 in the exponent (values below e^-60 of the
+// peak) take the FP64 form
+__device__ inline double gauss_ff(double x, const RateParams &rp) {
+  const float2 r = ff_mul(ff_from_double(x), rp.inv_sigma_ff);
+  const float2 r2 = ff_mul(r, r);
+  const float2 y = make_float2(-0.5f * r2.x, -0.5f * r2.y);
+  if (!(y.x >= -60.f)) return gauss_in(x, rp);
+  const float2 g = ff_mul(exp_ff(y), rp.gnorm_ff);
+  return double(g.x) + double(g.y);
+}
+
 // ------------------------------------------------------------------------ count pass
 __global__ void k_rate_count(ModelDev M, MeshDev D, RateParams rp, int *cntE, int *cntPh,
                              unsigned long long *n_tuples) {
@@ -611,7 +645,7 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
         }
       }
     }
-    const double gp = inp ? gauss_in(dxp, rp) : 0.0, gm = inm ? gauss_in(dxm, rp) : 0.0;
+    const double gp = inp ? gauss_ff(dxp, rp) : 0.0, gm = inm ? gauss_ff(dxm, rp) : 0.0;
     if (rp.vertex_only) {   // T-independent vertex weights V+-: occupation factors left out
       const double v = rp.inv_Nq_pref * (cnt == 1 ? sum : sum / double(cnt));
       Xp[t] = v * gp;
