@@ -176,6 +176,7 @@ struct ephb_ctx : InstState {
   DBuf<double> fk, nbq, wr;
   DBuf<double2> ut;
   DBuf<float4> cff, uff;   // float-float c(k) and u(q) of the tensor-core epilogue
+  DBuf<float> eps32, w32;  // FP32 copies of the energies (delta-cutoff estimate)
   DBuf<unsigned long long> ucount;
 
   // T-independent vertex lists over the union of the instance windows (several instances)
@@ -359,7 +360,8 @@ void ephb_destroy(ephb_ctx *ctx) {
   ctx->phik.release(); ctx->gslices.release(); ctx->gscale.release();
   ctx->phis.release(); ctx->bslices.release(); ctx->bscale.release(); ctx->Cbuf.release(); ctx->nitem.release();
   ctx->tc_err.release(); ctx->item_ptr.release(); ctx->ws_desc.release(); ctx->fk.release(); ctx->nbq.release(); ctx->wr.release();
-  ctx->ut.release(); ctx->ucount.release(); ctx->cff.release(); ctx->uff.release();
+  ctx->ut.release(); ctx->ucount.release(); ctx->cff.release(); ctx->uff.release(); ctx->eps32.release();
+  ctx->w32.release();
   ctx->u_row_ptr.release(); ctx->u_ph_row_ptr.release(); ctx->u_kpns.release(); ctx->u_ph_kpn.release();
   ctx->u_X.release(); ctx->u_ph_st.release(); ctx->u_ph_V.release();
   ctx->release_all();
@@ -713,6 +715,13 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
   CK(ctx->phscan.ensure(np * nbr));
   CK(ctx->ucount.ensure(8));
   MeshDev D = mesh_view(ctx);
+  // FP32 copies of the energies for the FP32 estimate of the delta-cutoff decisions
+  CK(ctx->eps32.ensure(size_t(ctx->km.size()) * nb));
+  CK(ctx->w32.ensure(size_t(nq) * nbr));
+  CK(launch_to_f32(int64_t(ctx->km.size()) * nb, ctx->eps.p, ctx->eps32.p, st));
+  CK(launch_to_f32(int64_t(nq) * nbr, ctx->w.p, ctx->w32.p, st));
+  rp.eps32 = ctx->eps32.p;
+  rp.w32 = ctx->w32.p;
   CK(launch_rate_count(M, D, rp, ctx->cntE.p, ctx->cntPh.p, ctx->ucount.p, st));
   int64_t big = np * (nb > nbr ? nb : nbr);
   CK(ctx->scratch.ensure(scan_scratch_elems(big)));

@@ -79,6 +79,25 @@ __device__ inline double gauss_ff(double x, const RateParams &rp) {
   return double(g.x) + double(g.y);
 }
 
+// Delta-cutoff flags of a tuple (bit 0: |e' - e - w| <= cut, bit 1: |e' - e + w| <= cut), the
+// decisions of the FP64 expressions below.  An FP32 estimate from FP32 copies of the three
+// energies settles every case farther from the cutoff than its error bound: the FP32 inputs
+// and two FP32 operations are within 2^-22 of S = |e'| + |e| + |w| of the FP64 values, the FP64
+// expressions within 2^-52 S, and cut's FP32 copy within 2^-24 cut; the margin 2^-20 (S + cut)
+// covers them with room.  The rest take the FP64 expressions.  The count pass and the rate
+// epilogue use this one function, so their decisions agree.
+__device__ inline int cut_flags(double ekpn, double ekm, double wqs, float fkpn, float fkm, float fwqs, double cut) {
+  const float cutf = float(cut);
+  const float de = __fsub_rn(fkpn, fkm);
+  const float ap = fabsf(__fsub_rn(de, fwqs)), am = fabsf(__fadd_rn(de, fwqs));
+  const float tol = __fmul_rn(__fadd_rn(__fadd_rn(__fadd_rn(fabsf(fkpn), fabsf(fkm)), fabsf(fwqs)), cutf), 0x1p-20f);
+  const float lo = __fsub_rn(cutf, tol), hi = __fadd_rn(cutf, tol);
+  if ((ap < lo || ap > hi) && (am < lo || am > hi)) return (ap < lo ? 1 : 0) | (am < lo ? 2 : 0);
+  const double dxp = ekpn - ekm - wqs;
+  const double dxm = ekpn - ekm + wqs;
+  return (fabs(dxp) <= cut ? 1 : 0) | (fabs(dxm) <= cut ? 2 : 0);
+}
+
 // ------------------------------------------------------------------------ count pass
 __global__ void k_rate_count(ModelDev M, MeshDev D, RateParams rp, int *cntE, int *cntPh,
                              unsigned long long *n_tuples) {
@@ -98,6 +117,11 @@ __global__ void k_rate_count(ModelDev M, MeshDev D, RateParams rp, int *cntE, in
     if (pl == 0) ns = na;
     rf = 8ull * (na * nb * nbr * nbr + na * nap * nb * nbr);   // rotations only
     const double *ek = D.eps + size_t(k) * nb, *ekp = D.eps + size_t(kp) * nb, *wq = D.w + size_t(q) * nbr;
+    const float *fk = rp.eps32 + size_t(k) * nb, *fkp = rp.eps32 + size_t(kp) * nb, *fw = rp.w32 + size_t(q) * nbr;
+    int64_t qb = D.qpair_ptr[q];
+    int64_t npq = D.qpair_ptr[q + 1] - qb;
+    int cph[kMaxBranches];
+    for (int s = 0; s < nbr; ++s) cph[s] = 0;
     for (int m = 0; m < nb; ++m) {
       int c = 0;
       if ((am >> m) & 1u)
@@ -106,28 +130,14 @@ __global__ void k_rate_count(ModelDev M, MeshDev D, RateParams rp, int *cntE, in
           for (int s = 0; s < nbr; ++s) {
             if (!(wq[s] > D.omega_min)) continue;
             ++nt;
-            double xp = ekp[n] - ek[m] - wq[s];
-            double xm = ekp[n] - ek[m] + wq[s];
-            c += (fabs(xp) <= rp.cut || fabs(xm) <= rp.cut);
+            const int f = cut_flags(ekp[n], ek[m], wq[s], fkp[n], fk[m], fw[s], rp.cut);
+            c += f != 0;
+            cph[s] += f & 1;
           }
         }
       cntE[p0 * nb + m * npl + pl] = c;
     }
-    int64_t qb = D.qpair_ptr[q];
-    int64_t npq = D.qpair_ptr[q + 1] - qb;
-    for (int s = 0; s < nbr; ++s) {
-      int c = 0;
-      if (wq[s] > D.omega_min)
-        for (int m = 0; m < nb; ++m) {
-          if (!((am >> m) & 1u)) continue;
-          for (int n = 0; n < nb; ++n) {
-            if (!((an >> n) & 1u)) continue;
-            double xp = ekp[n] - ek[m] - wq[s];
-            c += fabs(xp) <= rp.cut;
-          }
-        }
-      cntPh[qb * nbr + s * npq + D.pq_rank[p]] = c;
-    }
+    for (int s = 0; s < nbr; ++s) cntPh[qb * nbr + s * npq + D.pq_rank[p]] = cph[s];
   }
   for (int o = 16; o > 0; o >>= 1) {
     nt += __shfl_down_sync(0xffffffffu, nt, o);
@@ -617,6 +627,7 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
   double Xp[NBM * NBM * NBRM], Xm[NBM * NBM * NBRM];
   uint8_t flg[NBM * NBM * NBRM];
   const int ntup = nact * nactp * nbr;
+  const float *fk32 = rp.eps32 + size_t(k) * nb, *fkp32 = rp.eps32 + size_t(kp) * nb, *fw32 = rp.w32 + size_t(q) * nbr;
   for (int t = 0; t < ntup; ++t) {
     const int ml = t / (nactp * nbr), nl = (t / nbr) % nactp, s = t % nbr;
     const int m = nth_bit(am, ml), n = nth_bit(an, nl);
@@ -625,11 +636,12 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
     flg[t] = 0;
     if (!(wq[s] > D.omega_min)) continue;
     // the cutoff test first: tuples with neither delta inside it need no average or occupation
+    const int f = cut_flags(ekp[n], ek[m], wq[s], fkp32[n], fk32[m], fw32[s], rp.cut);
+    if (!f) continue;
+    const bool inp = f & 1, inm = f & 2;
+    flg[t] = uint8_t(f);
     const double dxp = ekp[n] - ek[m] - wq[s];
     const double dxm = ekp[n] - ek[m] + wq[s];
-    const bool inp = fabs(dxp) <= rp.cut, inm = fabs(dxm) <= rp.cut;
-    if (!inp && !inm) continue;
-    flg[t] = uint8_t((inp ? 1 : 0) | (inm ? 2 : 0));
     double sum = 0.0;
     int cnt = 0;
     for (int a = gk[2 * m]; a < gk[2 * m + 1]; ++a) {
