@@ -1258,6 +1258,7 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
       CK(te.collect());
       CK(td.collect());
       CK(tsw[0].collect());
+      CK(tc32.collect());
       ++sweeps;
       ++inner_total;
       if (ctx->host_res[72] < tol_k) {   // x' is the answer
@@ -1287,10 +1288,9 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
       CK(launch_corr_apply(nst, dA, dAJ, ctx->I.p, ctx->J.p, st));
       CK(tc32.stop(st));
       // coefficients of the corrected x become the reference of the next FP64 sweep's test
+      // (on the device: the next sweep's read-back is the next host round trip)
       CK(launch_e_partial(B, ctx->I.p, ctx->J.p, ctx->epart.p, st));
       CK(launch_coeff_final(ctx->M, B, ctx->epart.p, ctx->ppart.p, ctx->res.p, ctx->prev_in.p, st));
-      CK(cudaStreamSynchronize(st));
-      CK(tc32.collect());
     }
     return EPHB_OK;
   };
@@ -1396,14 +1396,12 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
       s = inner_loop(1, ok);
       if (s != EPHB_OK) return s;
       CK(tp.collect());
-      if (o->ko_correction) {
-        CK(launch_ko(M, D, B, ctx->I.p, ctx->J.p, ctx->kpart.p, ctx->res.p, st));
-        CK(cudaMemcpyAsync(ctx->host_res + 74, ctx->res.p + 74, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (ctx->host_res[75] != 0.0) lambda = ctx->host_res[74];
-      }
+      // the KO step keeps lambda in res[74] (res[75]: applied); the coefficient read-back
+      // below brings both to the host with the residual, so the step needs no round trip
+      if (o->ko_correction) CK(launch_ko(M, D, B, ctx->I.p, ctx->J.p, ctx->kpart.p, ctx->res.p, st));
       s = coefficients_to_host(ctx, ctx->prev_out.p);
       if (s != EPHB_OK) return s;
+      if (o->ko_correction && ctx->host_res[75] != 0.0) lambda = ctx->host_res[74];
       residual = ctx->host_res[73];
       outer_seen = true;
       // an outer iteration whose electron loop stopped early does not end the iteration
