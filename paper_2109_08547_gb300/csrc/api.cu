@@ -815,31 +815,41 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
       CK(launch_ff_tables(M, D, ctx->ut.p, ctx->cff.p, ctx->uff.p, st));
     }
   }
+  // Stage A runs on groups of up to `chunk` k points (all of them when the buffers allow), so
+  // its contraction sees many k tiles per launch; stage B then walks the group in sub-chunks
+  // whose pairs fit the contraction scratch, reading the group's stage-A output at its offset.
+  int64_t a0 = 0, a_end = 0;
   for (int64_t i0 = 0; i0 < ctx->n_ibzw;) {
-    int64_t nkc = ctx->n_ibzw - i0 < chunk ? ctx->n_ibzw - i0 : chunk;
+    if (i0 >= a_end) {
+      a0 = i0;
+      a_end = ctx->n_ibzw - i0 < chunk ? ctx->n_ibzw : i0 + chunk;
+      const int64_t na = a_end - a0;
+      CK(ta.start(st));
+      if (tensor_a) {
+        const int width_a = ctx->force_cols ? std::min(ctx->force_cols, tc_nc_max(ns_a)) : tc_nc_max(ns_a);
+        CK(launch_stage_a_tc(M, D, ns_a, a0, na, ctx->phik.p, ctx->gslices.p, ctx->gscale.p, ctx->Tbuf.p,
+                             ctx->tc_err.p, width_a, st, &tensor_flops_a));
+        CK(launch_stage_a2(M, D, a0, na, ctx->Tbuf.p, ctx->Abuf.p, st));
+      } else {
+        CK(launch_stage_a(M, D, a0, na, ctx->Tbuf.p, ctx->Abuf.p, st));
+      }
+      CK(ta.stop(st));
+    }
+    int64_t nkc = a_end - i0;
     if (tensor) {   // also keep the chunk's pairs within the contraction scratch
       while (nkc > 1 && hpp[i0 + nkc] - hpp[i0] > kMaxChunkPairs) nkc = (nkc + 1) / 2;
       if (hpp[i0 + nkc] - hpp[i0] > kMaxChunkPairs)
         return fail(ctx, EPHB_EINVAL, "one irreducible k has more pairs than the contraction scratch holds");
     }
-    CK(ta.start(st));
-    if (tensor_a) {
-      const int width_a = ctx->force_cols ? std::min(ctx->force_cols, tc_nc_max(ns_a)) : tc_nc_max(ns_a);
-      CK(launch_stage_a_tc(M, D, ns_a, i0, nkc, ctx->phik.p, ctx->gslices.p, ctx->gscale.p, ctx->Tbuf.p,
-                           ctx->tc_err.p, width_a, st, &tensor_flops_a));
-      CK(launch_stage_a2(M, D, i0, nkc, ctx->Tbuf.p, ctx->Abuf.p, st));
-    } else {
-      CK(launch_stage_a(M, D, i0, nkc, ctx->Tbuf.p, ctx->Abuf.p, st));
-    }
-    CK(ta.stop(st));
+    const double2 *Achunk = ctx->Abuf.p + size_t(i0 - a0) * stage_a_A_elems(M);
     CK(tb.start(st));
     if (!tensor) {
-      CK(launch_stage_b_rates(M, D, rp, i0, nkc, ctx->Abuf.p, ctx->escan.p, ctx->phscan.p, ctx->e_kpns.p,
+      CK(launch_stage_b_rates(M, D, rp, i0, nkc, Achunk, ctx->escan.p, ctx->phscan.p, ctx->e_kpns.p,
                               ctx->e_X.p, ctx->ph_st.p, ctx->ph_kpn.p, ctx->ph_Y.p, st));
       CK(tb.stop(st));
     } else {
       auto contract = [&](cudaEvent_t e0, cudaEvent_t e1, int width, int kc, int stages) {
-        return launch_vertex_tc(M, D, ns, i0, nkc, hpp[i0], ctx->Abuf.p, ctx->phis.p, ctx->bslices.p,
+        return launch_vertex_tc(M, D, ns, i0, nkc, hpp[i0], Achunk, ctx->phis.p, ctx->bslices.p,
                                 ctx->bscale.p, ctx->nitem.p, ctx->item_ptr.p, ctx->scratch.p, ctx->scratch.n,
                                 ctx->scal.p + 6, ctx->Cbuf.p, ctx->tc_err.p, st, e0, e1, width, kc, stages,
                                 ctx->withhold_mma, ctx->ws_desc.p, ctx->ws_cap);
