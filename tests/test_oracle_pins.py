@@ -391,3 +391,216 @@ def test_eight_band_model_symmetry_ibz_equals_full_bz():
     for key in ("sigma", "sigmaS", "alpha_el", "kappa0_el", "alpha_ph", "kappa_ph"):
         a, b = res[0].coeffs[key], res[1].coeffs[key]
         assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(b), key
+
+
+# ------------------------------------------------------------------ absolute rate scale and mesh ratio
+
+def _sc1_r0_workload(n_k, n_q, sym=True, **kw):
+    """The one-band cubic model with only the R = 0 coupling kept: every |g_s|^2 is then
+    (w_ref / w_s) |g(0,0)|^2, so the rates follow from closed-form bands and phonons."""
+    wl = S.workload_sc1(n_k, nsym_full=sym)
+    m0, g00 = _r0_only(wl.model)
+    return dataclasses.replace(wl, model=m0, qmesh=(n_q,) * 3, **kw), abs(g00[0, 0, 0]) ** 2
+
+
+def _sc1_closed(wl):
+    """Closed-form eps(k) (nearest-neighbour band, t = 1 eV) and the three Cartesian phonon
+    branches w_a(q) = w_max |sin(pi q_a / n_q)| of the one-band model."""
+    nk, nq = np.array(wl.kmesh), np.array(wl.qmesh)
+    eps = lambda ki: -2.0 * np.cos(2 * np.pi * ki / nk).sum(axis=-1)
+    wq = lambda qi: 0.030 * np.abs(np.sin(np.pi * qi / nq))
+    return eps, wq
+
+
+@pytest.mark.parametrize("n_k,n_q", [(8, 8), (8, 4)])
+def test_rate_sums_equal_golden_rule_brute_force(n_k, n_q):
+    """Absolute scale of Eq. X^e-ph on equal and ratio-2 meshes.  With a constant |g|^2 the
+    summed absorption / emission rates of an initial state are golden-rule sums over the
+    final states k' = k + q, q running over the N_q points of the phonon mesh:
+      sum X^{+/-}(k) = (2 pi / hbar) (1/N_q) sum_{q, a} |g_a|^2 f_k (1 - f_k') {n, 1+n} delta(x),
+    with delta the unit-normalised Gaussian of standard deviation sigma (zero beyond the cut).
+    The loop below uses the closed-form band and phonon energies, visits every q of the
+    phonon mesh directly (no irreducible wedge, no pair tables) and checks every irreducible
+    state to 1e-12.  A wrong 2 pi, hbar, 1/N normalisation or Gaussian normalisation fails."""
+    wl, g2 = _sc1_r0_workload(n_k, n_q)
+    P = O.prepare(wl)
+    R = O.transition_rates(P)
+    eps, wq = _sc1_closed(wl)
+    T, mu, sig, cut = wl.T_K, wl.mu_eV, wl.sigma_eV, wl.cutoff_sigmas * wl.sigma_eV
+    kT = O.KB_EVK * T
+    lo, hi = wl.window
+    qall = O.mesh_indices(wl.qmesh)
+    r = n_k // n_q
+    gauss = lambda x: np.where(np.abs(x) <= cut, np.exp(-x * x / (2 * sig * sig)) / (sig * np.sqrt(2 * np.pi)), 0.0)
+    checked = 0
+    for k in R.ibz_win:
+        ki = P.kidx[k]
+        e = eps(ki)
+        kpi = ki[None, :] + r * qall
+        ep = eps(kpi)
+        act = (ep >= lo) & (ep <= hi)
+        f, fp = 1 / (np.exp((e - mu) / kT) + 1), 1 / (np.exp((ep - mu) / kT) + 1)
+        sp = sm = 0.0
+        for a in range(3):
+            w = wq(qall)[:, a]
+            ok = act & (w > wl.omega_min_eV)
+            n = 1.0 / np.expm1(w[ok] / kT)
+            base = (2 * np.pi / HB) / qall.shape[0] * g2 * (wl.model.omega_ref_eV / w[ok]) * f * (1 - fp[ok])
+            sp += np.sum(base * n * gauss(ep[ok] - e - w[ok]))
+            sm += np.sum(base * (1 + n) * gauss(ep[ok] - e + w[ok]))
+        sel = R.ik == k
+        np.testing.assert_allclose(R.Xp[sel].sum(), sp, rtol=1e-12)
+        np.testing.assert_allclose(R.Xm[sel].sum(), sm, rtol=1e-12)
+        checked += 1
+    assert checked == len(R.ibz_win) > 0
+
+
+@pytest.mark.parametrize("n_k,n_q", [(8, 8), (8, 4)])
+def test_phonon_rta_rate_equals_brute_force_over_all_k(n_k, n_q):
+    """Eq. W^RTA of the phonons on equal and ratio-2 meshes: the electron part of a mode's
+    rate is d_s sum_{k in FBZ} Y / (n(1+n)) with Y = (2 pi / hbar)(1/N_k) |g|^2 f_k (1 - f_k+q) n
+    delta: a golden-rule sum over every k of the electron mesh, each weighted 1/N_k.  The loop
+    below visits all N_k points (the oracle builds the same sum from irreducible rows and the
+    symmetry fold) with closed-form energies, and adds the background rate."""
+    wl, g2 = _sc1_r0_workload(n_k, n_q)
+    P = O.prepare(wl)
+    R = O.transition_rates(P)
+    res = O.solve_coupled_bte(P, R, level="rta")
+    eps, wq = _sc1_closed(wl)
+    T, mu, sig, cut = wl.T_K, wl.mu_eV, wl.sigma_eV, wl.cutoff_sigmas * wl.sigma_eV
+    kT = O.KB_EVK * T
+    lo, hi = wl.window
+    m = wl.model
+    kall = P.kidx
+    e = eps(kall)
+    f = 1 / (np.exp((e - mu) / kT) + 1)
+    act = (e >= lo) & (e <= hi)
+    r = n_k // n_q
+    for q in range(P.Nq):
+        qi = P.qidx[q]
+        w_all = wq(qi)
+        order = np.argsort(w_all, kind="stable")
+        ep = eps(kall + r * qi[None, :])
+        fp = 1 / (np.exp((ep - mu) / kT) + 1)
+        both = act & (ep >= lo) & (ep <= hi)
+        for s, a in enumerate(order):
+            w = w_all[a]
+            if w <= wl.omega_min_eV:
+                continue
+            n = 1.0 / np.expm1(w / kT)
+            x = ep[both] - e[both] - w
+            d = np.where(np.abs(x) <= cut, np.exp(-x * x / (2 * sig * sig)) / (sig * np.sqrt(2 * np.pi)), 0.0)
+            Y = (2 * np.pi / HB) / P.Nk * g2 * (m.omega_ref_eV / w) * f[both] * (1 - fp[both]) * n * d
+            expect = m.spin_deg * Y.sum() / (n * (1 + n)) + m.bg_rate_coeff * (w / m.bg_omega_ref_eV) ** 2 * (T / m.bg_T_ref)
+            np.testing.assert_allclose(res.W_ph[q, s], expect, rtol=1e-12)
+
+
+def test_rta_rates_do_not_depend_on_the_mesh_ratio():
+    """[A3] from the physics side: the RTA rates are Brillouin-zone integrals, so an 8^3 k mesh
+    with a 4^3 or an 8^3 phonon mesh must give the same rates up to discretisation error.
+    Normalising X by 1/N_k instead of 1/N_q, or Y by 1/N_q instead of 1/N_k, would change one
+    of them by a factor 8.  Mean electron rate over the active states and the n(1+n)-weighted
+    zone average of the phonon rates' electron part, wide Gaussian (50 meV) so the mesh sums
+    are smooth."""
+    out = []
+    for n_q in (8, 4):
+        wl, _ = _sc1_r0_workload(8, n_q, sigma_eV=0.05)
+        P = O.prepare(wl)
+        res = O.solve_coupled_bte(P, O.transition_rates(P), level="rta")
+        m = wl.model
+        bg = m.bg_rate_coeff * (P.w / m.bg_omega_ref_eV) ** 2 * (wl.T_K / m.bg_T_ref)
+        nb = O.bose(P.w, wl.T_K)
+        ok = P.w > wl.omega_min_eV
+        out.append((res.W_e.mean(), np.sum(((res.W_ph - bg) * nb * (1 + nb))[ok]) / P.Nq))
+    (we8, wp8), (we4, wp4) = out
+    assert 0.8 < we4 / we8 < 1.25
+    assert 0.6 < wp4 / wp8 < 1.6
+
+
+def test_gaussian_delta_is_unit_normalised_with_sigma_as_standard_deviation():
+    """[A10] delta(x) integrates to 1 inside the 8-sigma cut (up to the erfc(8/sqrt 2) ~ 1e-15
+    tail), its second moment is sigma^2, its peak 1/(sigma sqrt(2 pi)), and it is exactly zero
+    beyond the cut."""
+    sig, cut = 0.010, 8.0
+    x = np.linspace(-cut * sig, cut * sig, 400001)
+    d = O.gaussian_delta(x, sig, cut)
+    h = x[1] - x[0]
+    trap = lambda y: h * (y.sum() - 0.5 * (y[0] + y[-1]))
+    np.testing.assert_allclose(trap(d), 1.0, rtol=1e-10)
+    np.testing.assert_allclose(trap(d * x * x), sig * sig, rtol=1e-9)
+    np.testing.assert_allclose(O.gaussian_delta(np.array([0.0]), sig, cut)[0], 1.0 / (sig * np.sqrt(2 * np.pi)), rtol=1e-15)
+    assert O.gaussian_delta(np.array([cut * sig * (1 + 1e-12)]), sig, cut)[0] == 0.0
+
+
+def test_kelvin_onsager_identity_on_ratio_two_mesh():
+    """The Kelvin-Onsager identities after the correction on an 8^3 k / 4^3 q mesh (O_h
+    wedge).  The plain iteration barely contracts on this small ratio-2 mesh, so a fixed
+    number of iterations is run: the identity holds after every correction step."""
+    wl = dataclasses.replace(S.workload_sc1(8), qmesh=(4, 4, 4))
+    P = O.prepare(wl)
+    R = O.transition_rates(P)
+    r = O.solve_coupled_bte(P, R, level="dragged", ko=True, max_outer=3, max_inner=40)
+    c = r.coeffs
+    T = wl.T_K
+    np.testing.assert_allclose(c["sigmaS"], (c["alpha_el"] + c["alpha_ph"]) / T, rtol=1e-11,
+                               atol=1e-11 * np.abs(c["sigmaS"]).max())
+    sp = O.StateSpace(P, R)
+    I_diff = ((sp.eps - wl.mu_eV) / T)[:, None] * r.J
+    np.testing.assert_allclose(sp.electron_tensors(I_diff, r.J)["sigmaS"], c["alpha_el"] / T, rtol=1e-13,
+                               atol=1e-13 * np.abs(c["alpha_el"]).max() / T)
+
+
+def _dense_coupled_operator(P, R, W_e, W_ph):
+    """The linear map of one sweep of the coupled BTEs (KO step off), assembled entry by entry
+    from the rate list: electron rows (self and drag terms of Eqs. dI^S, dI^D) and phonon rows
+    (Eq. dF^D, each X^+ entry seen from the phonon with Y = X^+ N_q / N_k)."""
+    sp = O.StateSpace(P, R)
+    ne, nbr = len(sp.states), sp.nbr
+    nph = P.Nq * nbr
+    ds = P.wl.model.spin_deg
+    M = np.zeros((ne + nph, ne + nph))
+    for e in range(len(R.Xp)):
+        i, j = sp.row[e], sp.col[e]
+        qs = R.iq[e] * nbr + R.s[e]
+        mqs = sp.mq[e] * nbr + R.s[e]
+        c = 1.0 / (sp.ff[i] * W_e[i])
+        M[i, j] += c * (R.Xp[e] + R.Xm[e])
+        M[i, ne + qs] -= c * R.Xp[e]
+        M[i, ne + mqs] += c * R.Xm[e]
+        y = R.Xp[e] * P.Nq / P.Nk
+        cp = ds / (sp.nn1.ravel()[qs] * W_ph.ravel()[qs])
+        M[ne + qs, j] += cp * y
+        M[ne + qs, i] -= cp * y
+    return sp, M, ne, nph
+
+
+def test_partial_level_is_one_drag_update_then_exact_electrons(sc1_full_prepared, sc1_full_rates):
+    """The partially decoupled iterate ("Coupled and decoupled BTEs", iterate 1): the phonons
+    take one drag update from the RTA electrons, F = F0 + dF^D[I0], G = dG^D[J0], and the
+    electron equations are then solved exactly against those fixed phonons (KO step off).
+    Reference: the dense operator applied once to the RTA, then a direct least-squares solve
+    of the electron block."""
+    P, R = sc1_full_prepared, sc1_full_rates
+    it = O.solve_coupled_bte(P, R, level="partial", ko=False, tol=1e-12)
+    assert it.converged and it.outer_iters == 1
+    sp, M, ne, nph = _dense_coupled_operator(P, R, it.W_e, it.W_ph)
+    ok = P.w.ravel() > P.wl.omega_min_eV
+    T, mu = P.wl.T_K, P.wl.mu_eV
+    I0 = ((sp.eps - mu) / T)[:, None] * sp.v / it.W_e[:, None]
+    J0 = sp.v / it.W_e[:, None]
+    F0 = ((P.w / T)[..., None] * P.vph / np.where(it.W_ph > 0, it.W_ph, 1.0)[..., None]).reshape(nph, 3)
+    F0[~ok] = 0.0
+    F1 = F0 + M[ne:, :ne] @ I0
+    G1 = M[ne:, :ne] @ J0
+    F1[~ok] = 0.0
+    G1[~ok] = 0.0
+    A = np.eye(ne) - M[:ne, :ne]
+    I = np.linalg.lstsq(A, I0 + M[:ne, ne:] @ F1, rcond=None)[0]
+    J = np.linalg.lstsq(A, J0 + M[:ne, ne:] @ G1, rcond=None)[0]
+    c = O.coefficients_from_responses(sp, I, J, F1.reshape(P.Nq, sp.nbr, 3), G1.reshape(P.Nq, sp.nbr, 3))
+    for key in ("sigma", "sigmaS", "alpha_el", "kappa0_el", "alpha_ph", "kappa_ph"):
+        np.testing.assert_allclose(it.coeffs[key], c[key], rtol=1e-7, atol=1e-7 * np.abs(c[key]).max())
+    # and the partial iterate differs from both the RTA and the converged dragged answer
+    d = O.solve_coupled_bte(P, R, level="dragged", ko=False, tol=1e-12)
+    assert np.linalg.norm(it.coeffs["sigma"] - it.rta_coeffs["sigma"]) > 1e-6 * np.linalg.norm(it.coeffs["sigma"])
+    assert np.linalg.norm(it.coeffs["kappa_ph"] - d.coeffs["kappa_ph"]) > 1e-9 * np.linalg.norm(d.coeffs["kappa_ph"])
