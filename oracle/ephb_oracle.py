@@ -36,7 +36,7 @@ __all__ = [
     "electron_bands", "phonon_modes", "irreducible_wedge", "bloch_vertex_sq",
     "transition_rates", "Rates", "BTEResult", "solve_coupled_bte", "coefficients_from_responses",
     "prepare", "Prepared", "gaussian_delta", "fermi", "bose", "StateSpace", "ibz_window_points",
-    "kplusq", "minus_q", "TENSORS", "inverse_ops", "ANGSTROM",
+    "kplusq", "minus_q", "TENSORS", "inverse_ops", "ANGSTROM", "ibz_window_rows", "prepare_rows",
 ]
 
 
@@ -212,6 +212,51 @@ def prepare(wl) -> Prepared:
     qimages = np.stack([flat_index(np.mod(qidx @ S.T.astype(np.int64), qq), wl.qmesh) for S in m.sym_rot])
     return Prepared(wl=wl, kidx=kidx, qidx=qidx, eps=eps, c=c, vel=vel, w=w, u=u, vph=vph, active=active,
                     rep=rep, op=op, stab=stab, ratio=ratio, inv_op=inverse_ops(m.sym_rot), qimages=qimages)
+
+
+def ibz_window_rows(wl) -> np.ndarray:
+    """The irreducible representatives (smallest flat index of each star) holding an active
+    band, from bands computed on the representatives only (large meshes)."""
+    kidx = mesh_indices(wl.kmesh)
+    nn = np.array(wl.kmesh)
+    images = np.stack([flat_index(np.mod(kidx @ S.T.astype(np.int64), nn), wl.kmesh) for S in wl.model.sym_rot])
+    reps = np.unique(images.min(axis=0))
+    lo, hi = wl.window
+    act = np.zeros(len(reps), bool)
+    for c0 in range(0, len(reps), 65536):
+        e, _, _ = electron_bands(wl.model, kidx[reps[c0:c0 + 65536]] / nn, wl.degen_tol_eV)
+        act[c0:c0 + 65536] = ((e >= lo) & (e <= hi)).any(axis=1)
+    return reps[act]
+
+
+def prepare_rows(wl, rows) -> Prepared:
+    """A Prepared state for transition_rates(P, ks=rows) on a large mesh: bands, eigenvectors
+    and velocities only at the given k rows and their partners k + q (zero elsewhere, never
+    read by the rates of those rows); phonons on the whole q mesh.  The symmetry tables are
+    not filled (the rates of given rows do not use them)."""
+    kidx = mesh_indices(wl.kmesh)
+    qidx = mesh_indices(wl.qmesh)
+    nk, nq = np.array(wl.kmesh), np.array(wl.qmesh)
+    ratio = nk // nq
+    need = [np.asarray(rows, dtype=np.int64)]
+    for k in rows:
+        need.append(flat_index(np.mod(kidx[k][None, :] + ratio[None, :] * qidx, nk), wl.kmesh))
+    need = np.unique(np.concatenate(need))
+    nb = wl.model.nb
+    eps = np.zeros((kidx.shape[0], nb))
+    c = np.zeros((kidx.shape[0], nb, nb), dtype=np.complex128)
+    vel = np.zeros((kidx.shape[0], nb, 3))
+    for c0 in range(0, len(need), 65536):
+        sel = need[c0:c0 + 65536]
+        eps[sel], c[sel], vel[sel] = electron_bands(wl.model, kidx[sel] / nk, wl.degen_tol_eV)
+    w, u, vph = phonon_modes(wl.model, qidx / nq, wl.degen_tol_eV, wl.omega_min_eV)
+    lo, hi = wl.window
+    active = np.zeros(eps.shape, dtype=bool)
+    active[need] = (eps[need] >= lo) & (eps[need] <= hi)
+    none = np.full(kidx.shape[0], -1, dtype=np.int64)
+    return Prepared(wl=wl, kidx=kidx, qidx=qidx, eps=eps, c=c, vel=vel, w=w, u=u, vph=vph, active=active,
+                    rep=none, op=none, stab=none, ratio=ratio, inv_op=inverse_ops(wl.model.sym_rot),
+                    qimages=None)
 
 
 def kplusq(P: Prepared, k: int, q: np.ndarray) -> np.ndarray:

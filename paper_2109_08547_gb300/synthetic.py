@@ -353,3 +353,183 @@ def instance_grid(n: int, mu0_eV: float = 0.0, half_window_eV: float = 0.25, see
 def model_nbytes(m: WannierModel) -> int:
     return int(sum(x.nbytes for x in (m.lattice, m.mass_amu, m.tau_cart, m.Re, m.H_R, m.Rd, m.D_R,
                                        m.Rge, m.Rgp, m.g_R, m.sym_rot, m.sym_cart)))
+
+
+# --------------------------------------------------------------------------------------
+# Model 4: 8-band O_h semiconductor with a 1.0 eV gap, CsCl-type 2-atom basis, 6 branches
+# (the fine-mesh drag case: 7^3 x 7^3 coupling grids, 80^3 k / 40^3 q)
+# --------------------------------------------------------------------------------------
+
+def _shell_of(R: np.ndarray) -> np.ndarray:
+    """Shell of a vector of the 3^3 grid: 0 on-site, 1 faces, 2 edges, 3 corners."""
+    return np.abs(R).sum(axis=-1)
+
+
+# Dispersion parameters (e, t1, t2, t3) of the two band edges.  With only the face (t1), edge
+# (t2) and corner (t3) shells, eps(k) = e + 2 t1 sum_a c_a + 4 t2 sum_{a<b} c_a c_b
+# + 8 t3 c_x c_y c_z with c_a = cos(2 pi k_a) is multilinear in (c_x, c_y, c_z), so its extrema
+# over the zone sit at the eight corners of the c cube (Gamma, 3 X, 3 M, R).
+#   top valence band: t1, t2, t3 > 0, maximum at Gamma: VBM = e + 6 t1 + 12 t2 + 8 t3;
+#   lowest conduction band: t1 = -0.8, t2 = 0.3, t3 = 0.05 gives Gamma e-0.8, X e-3.2,
+#   M e+0.8, R e+8.0: minimum at the three X points (longitudinal / transverse curvature
+#   4 t2 - t1 + 4 t3 ... = 0.4 / 0.8 eV per rad^2, so three anisotropic valleys).
+CSCL8_VBM_EV = -0.5
+CSCL8_GAP_EV = 1.0
+_V0 = (0.35, 0.10, 0.02)
+_C0 = (-0.8, 0.3, 0.05)
+_C1 = (-0.5, -0.05, -0.01)     # second conduction band: all shells negative, minimum at Gamma
+_C1_ABOVE_CBM = 0.12
+
+
+def cscl8_band_edges():
+    """(VBM, CBM) of model_cscl8 in eV, in closed form: the top valence band's maximum at
+    Gamma and the lowest conduction band's minimum at X (every even k mesh contains both)."""
+    return CSCL8_VBM_EV, CSCL8_VBM_EV + CSCL8_GAP_EV
+
+
+def _edge_dispersions(rng):
+    """On-site energies and shell hoppings (e, t1, t2, t3) of the eight orbitals, valence
+    0-3 then conduction 4-7.  Orbitals v0 and c0 carry the band edges (closed form above);
+    the others are seeded and placed so that even their extreme values (e +- the summed shell
+    magnitudes 6|t1| + 12|t2| + 8|t3|) stay 0.05-0.3 eV below the VBM (valence) or 0.35 eV or
+    more above the CBM (c2, c3; c1 is the Gamma valley 0.12 eV above the CBM)."""
+    vbm, cbm = cscl8_band_edges()
+    par = np.zeros((8, 4))
+    span = lambda t: 6 * abs(t[0]) + 12 * abs(t[1]) + 8 * abs(t[2])
+    par[0, 1:] = _V0
+    par[0, 0] = vbm - (6 * _V0[0] + 12 * _V0[1] + 8 * _V0[2])
+    for i in (1, 2, 3):
+        t = rng.uniform(-1.0, 1.0, 3) * np.array([0.3, 0.08, 0.02])
+        par[i, 1:] = t
+        par[i, 0] = vbm - rng.uniform(0.05, 0.3) - span(t)
+    par[4, 1:] = _C0
+    par[4, 0] = cbm - (2 * _C0[0] * 1 + 4 * _C0[1] * (-1) + 8 * _C0[2] * (-1))
+    par[5, 1:] = _C1
+    par[5, 0] = cbm + _C1_ABOVE_CBM - (6 * _C1[0] + 12 * _C1[1] + 8 * _C1[2])
+    for i in (6, 7):
+        t = rng.uniform(-1.0, 1.0, 3) * np.array([0.3, 0.08, 0.02])
+        par[i, 1:] = t
+        par[i, 0] = cbm + rng.uniform(0.35, 0.8) + span(t)
+    return par
+
+
+def _oh_covariant_couplings(g: np.ndarray, half: int) -> np.ndarray:
+    """Group average of couplings g[re][rp][m'][n'][atom][cart] (re, rp flat indices of
+    cube_grid(half)) over the 48 operations S of O_h, for the CsCl-type basis (A at the
+    origin, B at tau = (1/2,1/2,1/2)):
+      g^{kappa a}(Re, Rp) <- (1/48) sum_S sum_b S_ba g^{kappa b}(S Re, S(Rp + tau_kappa) - tau_kappa).
+    The B atom's couplings live on the cells whose atom positions Rp + tau lie inside the
+    grid's symmetric cube (Rp_i in [-half, half-1]); they are zero elsewhere, and a source cell
+    outside that set contributes zero."""
+    grid = cube_grid(half)
+    idx = _index_of(grid)
+    nR = grid.shape[0]
+    tau = np.array([0.5, 0.5, 0.5])
+    inB = np.all(grid <= half - 1, axis=1)
+    out = np.zeros_like(g)
+    parts = [np.ascontiguousarray(g[..., kappa, :]) for kappa in (0, 1)]
+    for S in oh_group():
+        perm = [int(np.nonzero(S[i])[0][0]) for i in range(3)]     # S[i, perm[i]] = sign[i]
+        sign = [float(S[i, perm[i]]) for i in range(3)]
+        pe = np.array([idx[tuple(S @ r)] for r in grid])
+        pB = np.full(nR, -1)
+        for i, r in enumerate(grid):
+            if inB[i]:
+                pB[i] = idx[tuple(np.rint(S.astype(np.float64) @ (r + tau) - tau).astype(np.int32))]
+        for kappa, prow in ((0, pe), (1, pB)):
+            src = parts[kappa][np.ix_(pe, np.maximum(prow, 0))]
+            src[:, prow < 0] = 0.0
+            # sum_b S_ba src_b: S_ba is nonzero only for a = perm[b]
+            for b in range(3):
+                out[..., kappa, perm[b]] += sign[b] * src[..., b]
+    return out / 48.0
+
+
+def _hermitian_pair_cscl(g: np.ndarray, half: int) -> np.ndarray:
+    """g_{m'n'}^{kappa a}(Re, Rp) <- (g_{m'n'}(Re, Rp) + conj g_{n'm'}(-Re, Rp - Re)) / 2 for both
+    atoms (the same cell shift for A and B); zero where Rp - Re leaves the atom's cells."""
+    grid = cube_grid(half)
+    idx = _index_of(grid)
+    nR = grid.shape[0]
+    inB = np.all(grid <= half - 1, axis=1)
+    out = np.zeros_like(g)
+    for a, re in enumerate(grid):
+        pe = idx[tuple(-re)]
+        d = grid - re[None, :]
+        ok = np.all(np.abs(d) <= half, axis=1)
+        pp = np.full(nR, 0)
+        pp[ok] = [idx[tuple(v)] for v in d[ok]]
+        partner = np.conj(np.swapaxes(g[pe][pp], 1, 2))       # [rp][m'][n'][atom][cart]
+        okB = ok & inB & inB[pp]
+        out[a, ok, :, :, 0] = 0.5 * (g[a, ok, :, :, 0] + partner[ok, :, :, 0])
+        out[a, okB, :, :, 1] = 0.5 * (g[a, okB, :, :, 1] + partner[okB, :, :, 1])
+    return out
+
+
+def model_cscl8(seed: int = SEED_BASE + 5, a: float = 3.0, omega_max_eV: float = 0.060, g0_eV: float = 0.01,
+                r_half: int = 3) -> WannierModel:
+    """Eight-band O_h semiconductor on a CsCl-type cubic basis (the fine-mesh drag case).
+
+    Electrons: eight s-like orbitals on the A site, four valence and four conduction, with no
+    valence-conduction hopping.  Each block is Q diag(h_i(R)) Q^T with a seeded orthogonal Q
+    and one hopping per shell (faces, edges, corners) and orbital, so H(SR) = H(R) for the 48
+    operations, the eigenvalues are the orbital dispersions and the band edges are closed
+    forms (cscl8_band_edges): top valence at Gamma, lowest conduction at the three X points,
+    gap exactly 1.0 eV on every even mesh; a second conduction band has its minimum at Gamma
+    0.12 eV above the CBM.  Real hoppings (time-reversal symmetric).
+    Phonons: model 2's CsCl-type central springs (seeded shell constants, masses 28.0855 /
+    15.999 amu, zone-centre optical phonon omega_max), six branches, O_h symmetric.
+    Couplings: real normal g0 exp(-(|Re| + |Rp + tau_kappa|)/a) on (2 r_half + 1)^3 x
+    (2 r_half + 1)^3 grids (7^3 x 7^3 at full size: 45 M complex values, 723 MB), made O_h
+    covariant by the group average and Hermitian-pair symmetric (model_sc8's two steps, with
+    the B atom's cell shift under S)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nb = 8
+    lattice = a * np.eye(3)
+    Rh = cube_grid(1)
+    par = _edge_dispersions(rng)
+    Q = []
+    for _ in range(2):
+        q_, r_ = np.linalg.qr(rng.standard_normal((4, 4)))
+        Q.append(q_ * np.sign(np.diag(r_))[None, :])
+    sh = _shell_of(Rh)
+    H_R = np.zeros((Rh.shape[0], nb, nb), dtype=np.complex128)
+    for r in range(Rh.shape[0]):
+        h = par[:, 0] if sh[r] == 0 else par[:, sh[r]]
+        H_R[r, :4, :4] = Q[0] @ np.diag(h[:4]) @ Q[0].T
+        H_R[r, 4:, 4:] = Q[1] @ np.diag(h[4:]) @ Q[1].T
+    mA, mB = 28.0855, 15.999
+    K = rng.uniform(0.5, 1.5, size=3)
+    Rd, D = _cscl_force_constants(K[0], K[1], K[2], mA, mB)
+    w2_opt = (8.0 * K[0] / 3.0) * (1.0 / mA + 1.0 / mB)
+    D_R = (D * (omega_max_eV ** 2 / w2_opt)).astype(np.complex128)
+    # couplings g[re][rp][m'][n'][atom][cart], decaying with |Re| and the displaced atom's |Rp + tau|
+    grid = cube_grid(r_half)
+    rre = np.linalg.norm(grid, axis=1)
+    rpB = np.linalg.norm(grid + 0.5, axis=1)
+    g = rng.standard_normal((grid.shape[0], grid.shape[0], nb, nb, 2, 3))
+    g[..., 0, :] *= g0_eV * np.exp(-(rre[:, None] + rre[None, :]))[:, :, None, None, None]
+    g[..., 1, :] *= g0_eV * np.exp(-(rre[:, None] + rpB[None, :]))[:, :, None, None, None]
+    g = _oh_covariant_couplings(g, r_half)
+    g = _hermitian_pair_cscl(g.astype(np.complex128), r_half)
+    g_R = np.ascontiguousarray(g.reshape(grid.shape[0], grid.shape[0], nb, nb, 6))
+    ops = oh_group()
+    return WannierModel(lattice=lattice, mass_amu=np.array([mA, mB]),
+                        tau_cart=np.array([[0.0, 0.0, 0.0], [0.5 * a, 0.5 * a, 0.5 * a]]), nb=nb,
+                        Re=Rh, H_R=H_R, Rd=Rd, D_R=D_R, Rge=grid, Rgp=grid.copy(), g_R=g_R,
+                        omega_ref_eV=omega_max_eV, sym_rot=ops, sym_cart=ops.astype(np.float64),
+                        bg_omega_ref_eV=omega_max_eV)
+
+
+def workload_cscl8(n_k: int = 80, n_q: int = 40, r_half: int = 3, nsym_full: bool = True, T_K: float = 300.0,
+                   model: WannierModel = None, above_cbm_eV: float = 0.25) -> Workload:
+    """Fine-mesh drag case: n_k^3 k mesh (irreducible wedge under O_h), n_q^3 q mesh,
+    mu = E_CBM - 0.1 eV, T = 300 K; the transport window holds the conduction states up to
+    0.25 eV (above_cbm_eV) above the CBM: (E_CBM - gap/2, E_CBM + 0.25 eV), the lower edge at
+    mid-gap so no state lies near it."""
+    m = model_cscl8(r_half=r_half) if model is None else model
+    if not nsym_full:
+        m = dataclasses.replace(m, sym_rot=identity_group(), sym_cart=identity_group().astype(np.float64))
+    _, cbm = cscl8_band_edges()
+    return Workload(name=f"cscl8-{n_k}^3/{n_q}^3", model=m, kmesh=(n_k,) * 3, qmesh=(n_q,) * 3, T_K=T_K,
+                    mu_eV=cbm - 0.1, window=(cbm - 0.5 * CSCL8_GAP_EV, cbm + above_cbm_eV), tol=1e-10)

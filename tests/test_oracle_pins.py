@@ -604,3 +604,83 @@ def test_partial_level_is_one_drag_update_then_exact_electrons(sc1_full_prepared
     d = O.solve_coupled_bte(P, R, level="dragged", ko=False, tol=1e-12)
     assert np.linalg.norm(it.coeffs["sigma"] - it.rta_coeffs["sigma"]) > 1e-6 * np.linalg.norm(it.coeffs["sigma"])
     assert np.linalg.norm(it.coeffs["kappa_ph"] - d.coeffs["kappa_ph"]) > 1e-9 * np.linalg.norm(d.coeffs["kappa_ph"])
+
+
+# ------------------------------------------------------------------ the 8-band fine-mesh drag model
+
+def test_cscl8_band_edges_on_the_80_mesh():
+    """The 8-band semiconductor's gap is 1.0 eV on the 80^3 mesh: the oracle's bands on every
+    irreducible point give the closed-form VBM (top valence band at Gamma) and CBM (lowest
+    conduction band at X) to 1e-12 eV, the conduction minimum sits at the X points, and no
+    state lies within 1e-9 eV of a window edge."""
+    wl = S.workload_cscl8(80, 40, r_half=1)
+    vbm, cbm = S.cscl8_band_edges()
+    kidx = O.mesh_indices(wl.kmesh)
+    nn = np.array(wl.kmesh)
+    images = np.stack([O.flat_index(np.mod(kidx @ Sop.T.astype(np.int64), nn), wl.kmesh) for Sop in wl.model.sym_rot])
+    reps = np.unique(images.min(axis=0))
+    assert len(reps) == 12341       # C(43, 3): the O_h wedge of an 80^3 mesh
+    e, _, _ = O.electron_bands(wl.model, kidx[reps] / nn, wl.degen_tol_eV)
+    np.testing.assert_allclose(e[:, :4].max(), vbm, atol=1e-12)
+    np.testing.assert_allclose(e[:, 4:].min(), cbm, atol=1e-12)
+    np.testing.assert_allclose(e[:, 4:].min() - e[:, :4].max(), 1.0, atol=1e-12)
+    kmin = kidx[reps[np.argmin(e[:, 4])]]
+    assert sorted(kmin.tolist()) == [0, 0, 40]          # X = (1/2, 0, 0)
+    assert np.min(np.abs(e[..., None] - np.array(wl.window))) > 1e-9
+    # the window holds conduction states only
+    act = (e >= wl.window[0]) & (e <= wl.window[1])
+    assert act[:, :4].sum() == 0 and act.sum() > 100
+
+
+def test_cscl8_couplings_are_oh_covariant_and_hermitian_pair_symmetric():
+    """The coupling generator's two symmetry steps, checked entry by entry on a 5^3 grid:
+    g^{kappa a}(Re, Rp) = sum_b S_ba g^{kappa b}(S Re, S(Rp + tau_kappa) - tau_kappa) for all 48
+    operations (the B atom shifts cell under S), and g_{m'n'}(Re, Rp) = conj g_{n'm'}(-Re, Rp - Re)."""
+    m = S.model_cscl8(r_half=2)
+    grid = m.Rge
+    idx = {tuple(v): i for i, v in enumerate(grid)}
+    g = m.g_R.reshape(len(grid), len(grid), 8, 8, 2, 3)
+    rng = np.random.default_rng(3)
+    tau = np.array([0.5, 0.5, 0.5])
+    n_checked = 0
+    for Sop in m.sym_rot:
+        for _ in range(40):
+            a, b, kap = rng.integers(0, len(grid)), rng.integers(0, len(grid)), rng.integers(0, 2)
+            re, rp = grid[a], grid[b]
+            if kap == 1 and np.any(rp == 2):
+                assert np.all(g[a, b, :, :, 1] == 0)
+                continue
+            rp2 = np.rint(Sop @ (rp + kap * tau) - kap * tau).astype(int)
+            rhs = np.einsum("ba,mnb->mna", Sop.astype(float), g[idx[tuple(Sop @ re)], idx[tuple(rp2)], :, :, kap])
+            np.testing.assert_allclose(g[a, b, :, :, kap], rhs, atol=1e-17)
+            n_checked += 1
+    assert n_checked > 1000
+    for _ in range(500):
+        a, b = rng.integers(0, len(grid)), rng.integers(0, len(grid))
+        p = tuple(grid[b] - grid[a])
+        if p in idx:
+            partner = np.conj(np.swapaxes(g[idx[tuple(-grid[a])], idx[p]], 0, 1))
+            for kap in (0, 1):
+                if kap == 1 and (np.any(grid[b] == 2) or np.any(np.array(p) == 2)):
+                    continue
+                np.testing.assert_allclose(g[a, b, :, :, kap], partner[:, :, kap], atol=1e-17)
+
+
+def test_cscl8_irreducible_wedge_equals_full_zone():
+    """The 8-band 2-atom O_h model (small coupling grid): irreducible-wedge rates, RTA,
+    dragless and dragged iterates (a fixed number of iterations) equal the full-zone ones
+    without symmetry, which needs H(SR) = H(R), the O_h phonons and the covariance of g with
+    the B atom's cell shift."""
+    m1 = S.model_cscl8(r_half=1)
+    res = []
+    for full in (True, False):
+        wl = S.workload_cscl8(12, 12, model=m1, nsym_full=full)
+        P = O.prepare(wl)
+        R = O.transition_rates(P)
+        res.append([O.solve_coupled_bte(P, R, level=lv, max_outer=4, max_inner=30) for lv in ("rta", "dragless",
+                                                                                               "dragged")])
+    for a, b in zip(*res):
+        for key in ("sigma", "sigmaS", "alpha_el", "kappa0_el", "alpha_ph", "kappa_ph"):
+            nb_ = np.linalg.norm(b.coeffs[key])
+            if nb_ > 0:
+                assert np.linalg.norm(a.coeffs[key] - b.coeffs[key]) <= 1e-11 * nb_, key
