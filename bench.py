@@ -1,13 +1,18 @@
 #!/usr/bin/env python
 """Benchmark of the e-ph scattering + coupled-BTE hot path on GB300.
 
-One step = build_meshes_ibz + compute_transition_rates + solve_coupled_bte (dragged,
-tol 1e-10, Kelvin-Onsager on; by default the FP64-grade tensor-core vertex, the
-mixed-precision iteration and Anderson depth 3 on the outer iteration, all with the FP64
-path's fixed point) + transport_coefficients for the 4-band / 6-branch model on
-24^3 k and q meshes, with the Wannier model already resident on the device.  L2 is
-flushed (256 MB write) before every step.  The metric is transition rates per second:
-(k m, q, n, s) tuples interpolated and delta-weighted per step / step time.
+One step = build_meshes_ibz + compute_transition_rates + solve_coupled_bte (dragged, Kelvin-
+Onsager on) + transport_coefficients, with the Wannier model already resident on the device.
+The default workload is the fine-mesh drag case: the 8-band / 2-atom / 6-branch O_h
+semiconductor with 7^3 x 7^3 coupling grids (723 MB) on an 80^3 k mesh (irreducible wedge)
+and a 40^3 q mesh, window 0.25 eV above the conduction-band minimum, mu = E_CBM - 0.1 eV,
+300 K.  Default mode: FP64-grade tensor-core vertex, mixed-precision iteration, the plain outer
+iteration, stopping tolerance 1e-8 (the metric asks for coefficients within 1e-6 of the converged FP64
+answer; the run measures the achieved error against the FP64 path at 1e-10).  L2 is flushed
+(256 MB write) before every step.  The metric is transition rates per second: (k m, q, n, s)
+tuples interpolated and delta-weighted per step / step time; the time to converged
+coefficients is reported beside it, for the default mode and for the plain FP64 GPU path
+(FP64 vertex, plain FP64 iteration, no acceleration).
 
 Under torchrun (N > 1) every rank runs an independent replica on its own GPU (the path
 needs no exchange on one device; the value is all ranks' tuples / the slowest rank).
@@ -31,23 +36,45 @@ sys.path.insert(0, ROOT)
 
 METRIC = "transition rates/s and s to converged σ,S,κ at 1e-6 rel: mixed+batched vs FP64"
 UNIT = "transition rates/s"
-# FP64 FMA throughput of the GB300s, measured with `bench.py --fp64-peak`
+# FP64 FMA throughput of the GB300s, measured with a standalone FMA probe kernel
 # (profiles/fp64_peak_gb300.txt); the nominal figure is 1.25 TFLOP/s.
 FP64_PEAK_TFLOPS = 1.188  # lower of two measurements (1.188, 1.255)
+FP64_PEAK_SRC = "measured FP64 FMA rate (profiles/fp64_peak_gb300.txt)"
 # arithmetic of the vertex contraction per precision mode (everything else is FP64)
-DTYPES = {"fp64": "f64", "fp64-sliced": "f64 (tcgen05 bf16 x7 exact fixed-point slices, f32 accumulate)",
-          "split-bf16": "bf16 x3 slices, f32 accumulate (mixed)"}
+DTYPES = {"fp64": "f64", "fp64-sliced": "f64 (tcgen05 bf16 exact fixed-point slices, f32 accumulate)",
+          "split-bf16": "bf16 x3 slices (x4 for contractions longer than 256), f32 accumulate (mixed)"}
 SOLVE_DTYPES = {"fp64": "; iteration f64",
                 "mixed": "; iteration f64 residual sweeps + f32 correction sweeps (same fixed point)"}
+COEFFS = ("sigma", "sigmaS", "S", "alpha_el", "kappa0_el", "kappa_el", "alpha_ph", "kappa_ph")
+METRIC_RTOL = 1e-6
+REF_TOL = 1e-10
+
+
+def workload(args):
+    from paper_2109_08547_gb300 import synthetic as S
+    if args.workload == "cscl8":
+        return S.workload_cscl8(args.nk, args.nq)
+    return S.workload_cscl4(args.n)
+
+
+def model_label(wl):
+    m = wl.model
+    ng = int(round(m.Rge.shape[0] ** (1 / 3)))
+    return (f"{m.nb}-band/{m.nbranch}-branch cubic ({'O_h' if len(m.sym_rot) == 48 else 'no point symmetry'}), "
+            f"{ng}^3 x {ng}^3 coupling grids (g {m.g_R.nbytes / 1e6:.0f} MB)")
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--n", type=int, default=24, help="k and q mesh size per dimension")
+    p.add_argument("--workload", default="cscl8", choices=["cscl8", "cscl4"],
+                   help="cscl8: fine-mesh drag case (80^3 k / 40^3 q); cscl4: 4-band precision case (--n^3)")
+    p.add_argument("--nk", type=int, default=80, help="k mesh of the cscl8 workload")
+    p.add_argument("--nq", type=int, default=40, help="q mesh of the cscl8 workload")
+    p.add_argument("--n", type=int, default=24, help="k and q mesh of the cscl4 workload")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--precision", default="fp64-sliced", choices=["fp64", "fp64-sliced", "split-bf16"],
@@ -55,63 +82,21 @@ def parse():
     p.add_argument("--solve", default="mixed", choices=["fp64", "mixed"],
                    help="electron loop: plain FP64 sweeps, or FP64 residual sweeps with FP32 corrections "
                         "(same fixed point)")
-    p.add_argument("--no-variants", action="store_true", help="skip the one-step timings of the other precisions")
-    p.add_argument("--accel", type=int, default=3,
+    p.add_argument("--tol", type=float, default=1e-8,
+                   help="stopping tolerance of the timed modes (the FP64 reference always runs at 1e-10)")
+    p.add_argument("--no-variants", action="store_true", help="skip the one-step timings of the other modes")
+    p.add_argument("--accel", type=int, default=0,
                    help="Anderson history depth of the outer iteration (0: the plain iteration)")
     p.add_argument("--instances", type=int, default=8,
                    help="(T, mu, window) instances of the batched-vs-sequential comparison (0: skip it)")
     p.add_argument("--warm", type=int, default=12,
                    help="mesh size of the learned-warm-start report (40 training + 10 held-out instances; 0: skip)")
-    p.add_argument("--fp64-peak", action="store_true",
-                   help="measure FP64 and FP32 FMA throughput with a small probe kernel and exit")
     return p.parse_args()
 
 
-FMA_PROBE = r"""
-#include <cstdio>
-#include <cuda_runtime.h>
-template <typename T> __global__ void probe(T *out, int iters, T a, T b) {
-  T x[8];
-  for (int j = 0; j < 8; ++j) x[j] = T(threadIdx.x) * T(1e-3) + T(j);
-  for (int i = 0; i < iters; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) x[j] = x[j] * a + b;
-  T s = 0; for (int j = 0; j < 8; ++j) s += x[j];
-  if (s == T(12345.678)) out[0] = s;
-}
-template <typename T> double run(int iters) {
-  T *d; cudaMalloc(&d, sizeof(T));
-  int sms; cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-  int grid = sms * 8, block = 256;
-  cudaEvent_t a, b; cudaEventCreate(&a); cudaEventCreate(&b);
-  probe<T><<<grid, block>>>(d, iters, T(0.999999), T(1e-7));
-  float best = 1e30f;
-  for (int r = 0; r < 5; ++r) {
-    cudaEventRecord(a); probe<T><<<grid, block>>>(d, iters, T(0.999999), T(1e-7)); cudaEventRecord(b);
-    cudaEventSynchronize(b); float ms; cudaEventElapsedTime(&ms, a, b); best = ms < best ? ms : best;
-  }
-  cudaFree(d);
-  return 2.0 * 8 * iters * double(grid) * block / (best * 1e-3) / 1e12;
-}
-int main() {
-  printf("fp64_fma_tflops %.4f\nfp32_fma_tflops %.4f\n", run<double>(4096), run<float>(16384));
-  return cudaGetLastError() == cudaSuccess ? 0 : 1;
-}
-"""
-
-
-def fp64_peak():
-    """Compile and run the FMA probe (nvcc, sm_103a); prints TFLOP/s for FP64 and FP32."""
-    import tempfile
-    with tempfile.TemporaryDirectory() as d:
-        src = os.path.join(d, "probe.cu")
-        exe = os.path.join(d, "probe")
-        with open(src, "w") as f:
-            f.write(FMA_PROBE)
-        subprocess.run(["nvcc", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-o", exe, src], check=True)
-        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
-    vals = dict(line.split() for line in out.strip().splitlines())
-    print(json.dumps({k: float(v) for k, v in vals.items()}))
+def step_seconds(el_max, steps):
+    """(ms per step, seconds per step) of a timed region of `steps` steps lasting el_max s."""
+    return 1e3 * el_max / steps, el_max / steps
 
 
 def whole_job(seconds, units, world, device):
@@ -216,38 +201,31 @@ def profile_traffic(kernel_tag, source_file):
         return None
 
 
-def oracle_sample(wl, n_q=None, row_index=None):
-    """Time the oracle's transition rates for (part of) one irreducible row."""
-    import numpy as np
+def oracle_row(wl, row_pos=0.5):
+    """The oracle's state for one irreducible row of the workload (bands at the row and its
+    partners only): (Prepared, row)."""
     import oracle as O
-    P = O.prepare(wl)
-    ibzw = O.ibz_window_points(P)
-    row = int(ibzw[len(ibzw) // 2 if row_index is None else row_index])
-    t0 = time.perf_counter()
-    if n_q is None:
-        R = O.transition_rates(P, ks=[row])
-    else:
-        # restrict the row to its first n_q partner q points
-        allq = np.arange(P.Nq)
-        kps = O.kplusq(P, row, allq)
-        qs = allq[P.active[kps].any(axis=1)][:n_q]
-        mask = np.zeros(P.Nq, bool)
-        mask[qs] = True
-        P2 = P
-        R = _rates_subset(O, P2, row, mask)
-    dt = time.perf_counter() - t0
-    return R.n_tuples, dt, row
+    ibzw = O.ibz_window_rows(wl)
+    row = int(ibzw[int(len(ibzw) * row_pos)])
+    return O.prepare_rows(wl, [row]), row
 
 
-def _rates_subset(O, P, row, qmask):
+def oracle_sample(P, row, n_pairs=None):
+    """Time the oracle's transition rates of one irreducible row (or of its first n_pairs
+    partner q points): (tuples, seconds)."""
     import dataclasses
     import numpy as np
-    act = P.active.copy()
-    kps = O.kplusq(P, row, np.arange(P.Nq))
-    keep = np.zeros_like(act)
-    keep[kps[qmask]] = act[kps[qmask]]
-    keep[row] = act[row]
-    return O.transition_rates(dataclasses.replace(P, active=keep), ks=[row])
+    import oracle as O
+    if n_pairs is not None:
+        kps = O.kplusq(P, row, np.arange(P.Nq))
+        qs = np.nonzero(P.active[kps].any(axis=1))[0][:n_pairs]
+        keep = np.zeros_like(P.active)
+        keep[kps[qs]] = P.active[kps[qs]]
+        keep[row] = P.active[row]
+        P = dataclasses.replace(P, active=keep)
+    t0 = time.perf_counter()
+    R = O.transition_rates(P, ks=[row])
+    return R.n_tuples, time.perf_counter() - t0
 
 
 def batched_block(B, ctx, wl, args, flush, torch, np):
@@ -262,6 +240,7 @@ def batched_block(B, ctx, wl, args, flush, torch, np):
     import dataclasses
     from paper_2109_08547_gb300 import synthetic as S
     insts = S.instance_grid(args.instances, wl.mu_eV)
+    B.set_wannier_model(ctx, wl.model)
     union = (min(i[2] for i in insts), max(i[3] for i in insts))
     seq_coeffs, seq_s = [], 0.0
     for T, mu, lo, hi in insts:
@@ -281,7 +260,7 @@ def batched_block(B, ctx, wl, args, flush, torch, np):
         solve = B.solve_coupled_bte(ctx, "dragged", wl.tol, solve_precision=solve_prec, accel=args.accel)
         return rates, solve, [B.transport_coefficients(ctx, i) for i in range(len(insts))]
 
-    out = {"instances": len(insts), "union_window_eV": list(union), "T_K_range": [100.0, 500.0],
+    out = {"workload": wl.name, "instances": len(insts), "union_window_eV": list(union), "T_K_range": [100.0, 500.0],
            "s_sequential_fp64": seq_s}
     # FP64-grade batch (exact-slice vertex, FP64 iteration) and mixed batch (split-BF16 vertex,
     # mixed-precision iteration)
@@ -381,11 +360,11 @@ def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    from paper_2109_08547_gb300 import synthetic as S
-    wl = S.workload_cscl4(args.n)
+    wl = workload(args)
+    P, row = oracle_row(wl)
     steps = []
     for i in range(args.warmup + args.steps):
-        nt, dt, row = oracle_sample(wl, n_q=256)
+        nt, dt = oracle_sample(P, row, n_pairs=64)
         if i >= args.warmup:
             steps.append((nt, dt))
     tot = sum(s[0] for s in steps)
@@ -396,20 +375,28 @@ def reference_arm(args):
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.name, "model": "4-band/6-branch CsCl-type, 5^3 R grids", "kmesh": list(wl.kmesh),
+        "config": {"workload": wl.name, "model": model_label(wl), "kmesh": list(wl.kmesh),
                    "qmesh": list(wl.qmesh), "T_K": wl.T_K, "mu_eV": wl.mu_eV, "window_eV": list(wl.window)},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": "FP64 oracle transition rates of 256 (k,q) pairs of one irreducible row per step"},
+                         "sample": f"FP64 oracle transition rates of the first 64 (k,q) pairs of irreducible row "
+                                   f"{row} per step"},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
 
 
+def coeff_errors(got, ref):
+    """Relative Frobenius difference of every coefficient tensor from the reference."""
+    import numpy as np
+    out = {}
+    for key in COEFFS:
+        nrm = float(np.linalg.norm(ref[key]))
+        out[key] = float(np.linalg.norm(got[key] - ref[key]) / nrm) if nrm > 0 else 0.0
+    return out
+
+
 def main():
     args = parse()
-    if args.fp64_peak:
-        fp64_peak()
-        return
     if args.impl == "reference":
         reference_arm(args)
         return
@@ -418,7 +405,6 @@ def main():
     import torch.distributed as dist
 
     from paper_2109_08547_gb300 import binding as B
-    from paper_2109_08547_gb300 import synthetic as S
 
     rank, world, local = dist_env()
     if world > 1:
@@ -426,15 +412,16 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    wl = S.workload_cscl4(args.n)
+    wl = workload(args)
     ctx = B.Context(local, stream=stream.cuda_stream)
     B.set_wannier_model(ctx, wl.model)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
 
     prec = B.PRECISIONS[args.precision]
 
-    def step(p=prec, sp=args.solve, acc=args.accel):
-        return B.run_path(ctx, wl, level="dragged", ko_correction=True, precision=p, solve_precision=sp, accel=acc)
+    def step(p=prec, sp=args.solve, acc=args.accel, tol=args.tol):
+        return B.run_path(ctx, wl, level="dragged", ko_correction=True, precision=p, solve_precision=sp, accel=acc,
+                          tol=tol)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -461,104 +448,131 @@ def main():
     launches = B.kernel_launches() - l0
     clocks = sampler.stop()
     _, el_max, value = whole_job(el, sum(r.rates["n_tuples"] for r in results), world, dev)
+    ms_step, s_step = step_seconds(el_max, args.steps)
     r0 = results[-1]
 
-    # dominant kernel and its roofline (device time measured with CUDA events in this run)
+    # the metric's accuracy reference: FP64 vertex, plain FP64 iteration, tol 1e-10; and the plain
+    # FP64 GPU path at this run's tolerance, timed the same way (its time to converged
+    # coefficients is the metric's comparator)
+    flush.zero_()
+    ref = step(B.FP64, "fp64", 0, REF_TOL)
+    fp64_times = []
+    for i in range(3):
+        flush.zero_()
+        torch.cuda.synchronize()
+        tv = time.perf_counter()
+        rf = step(B.FP64, "fp64", 0, args.tol)
+        torch.cuda.synchronize()
+        if i > 0:
+            fp64_times.append(time.perf_counter() - tv)
+    err = coeff_errors(r0.coeffs, ref.coeffs)
+    fp64_err = coeff_errors(rf.coeffs, ref.coeffs)
+    s_fp64 = statistics.mean(fp64_times)
+    accuracy = {"reference": f"FP64 vertex + plain FP64 iteration, tol {REF_TOL:g}",
+                "max_coeff_rel_err": max(err.values()), "coeff_rel_err": err,
+                "within_1e-6": max(err.values()) <= METRIC_RTOL}
+    fp64_block = {"mode": "FP64 vertex (CUDA cores) + plain FP64 iteration + no outer acceleration",
+                  "tol": args.tol, "s_to_converged": s_fp64, "value": rf.rates["n_tuples"] / s_fp64,
+                  "rates_ms": rf.rates["ms"], "solve_ms": rf.solve["ms"], "outer_iters": rf.solve["outer_iters"],
+                  "fp64_sweeps": rf.solve["n_sweeps"], "max_coeff_rel_err": max(fp64_err.values()),
+                  "speedup_of_default": s_fp64 / s_step}
+
+    # dominant kernels and their rooflines (device time from CUDA events in this run)
     mean = lambda f: statistics.mean(f(r) for r in results)
+    ms_a = mean(lambda r: r.rates["ms_stage_a"])
     ms_b = mean(lambda r: r.rates["ms_stage_b"])
     ms_g = mean(lambda r: r.rates["ms_gemm"])
-    ms_a = mean(lambda r: r.rates["ms_stage_a"])
     ms_ep = mean(lambda r: r.rates["ms_epilogue"])
     ms_self = mean(lambda r: r.solve["ms_self_kernel"])
-    peaks = measured_peaks()
-    step_ms = 1e3 * el_max / args.steps
-    fp64_src = "measured FP64 FMA rate (bench.py --fp64-peak, profiles/fp64_peak_gb300.txt)"
     ms_corr = mean(lambda r: r.solve["ms_corr"])
-    cands = [("stage_a", ms_a), ("epilogue", ms_ep), ("self_sweep", ms_self), ("corr", ms_corr)]
-    cands.append(("stage_b", ms_b) if args.precision == "fp64" else ("gemm", ms_g))
-    def roof_of(dominant):
-        if dominant == "stage_b":
-            achieved = r0.rates["stage_b_flops"] / (ms_b * 1e-3) / 1e12
-            tr = profile_traffic("stage_b_rates", "vertex.cu")
-            roof = {"kernel": "k_stage_b_rates (R_ph contraction + rotations + rates, FP64)", "bound": "alu",
-                    "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": fp64_src,
-                    "traffic": (tr[0] * r0.rates["n_pairs"]) if tr else None,
-                    "ms_per_step": ms_b, "share_of_step": ms_b / step_ms}
-        elif dominant == "gemm":
-            # tensor-core contraction: the MMA work the slicing issues, against the measured BF16 peak
-            pk = peaks.get("bf16_tflops", 1900.0)
-            achieved = r0.rates["tensor_flops"] / (ms_g * 1e-3) / 1e12
+    peaks = measured_peaks()
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    bf16_src = "MEASURED_PEAKS.json bf16_tflops (measured burst)" if "bf16_tflops" in peaks else "fallback"
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"
+    tensor = args.precision != "fp64"
+    cands = [("stage_a", ms_a), ("self_sweep", ms_self)]
+    if tensor:
+        cands += [("gemm", ms_g), ("epilogue", ms_ep)]
+    else:
+        cands += [("stage_b", ms_b)]
+    if args.solve == "mixed":
+        cands.append(("corr", ms_corr))
+
+    def roof_of(name):
+        ra, so = r0.rates, r0.solve
+        base = {"ms_per_step": None, "share_of_step": None}
+        if name == "stage_a":
+            alg = ra["stage_a_flops"]     # 8 N_Re ncol per irreducible-window k, plus the band rotation
+            if ra["tensor_flops_a"] > 0:
+                ach = alg / (ms_a * 1e-3) / 1e12
+                roof = {"kernel": "stage A (k phase slices + tcgen05 R_e contraction + band rotation)",
+                        "bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
+                        "peak_source": bf16_src, "traffic": None, "algorithmic_flops": alg,
+                        "issued_mma_tflops": ra["tensor_flops_a"] / (ms_a * 1e-3) / 1e12,
+                        "issued_frac": ra["tensor_flops_a"] / (ms_a * 1e-3) / 1e12 / bf16}
+            else:
+                ach = alg / (ms_a * 1e-3) / 1e12
+                roof = {"kernel": "k_stage_a1/a2 (R_e contraction and band rotation, FP64)", "bound": "alu",
+                        "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                        "peak_source": FP64_PEAK_SRC, "traffic": None, "algorithmic_flops": alg}
+            t = ms_a
+        elif name == "gemm":
+            alg = ra["stage_b_flops"] - ra["rot_flops"]   # 8 N_Rp nwin N_b 3N_at per (k,q) pair
+            ach = alg / (ms_g * 1e-3) / 1e12
             tr = profile_traffic("vertex_gemm", "vertex_tc.cu")
-            roof = {"kernel": f"k_vertex_gemm (tcgen05 R_ph contraction, {args.precision})", "bound": "tensor",
-                    "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
-                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured burst)" if "bf16_tflops" in peaks
-                    else "fallback", "traffic": (tr[0] * r0.rates["n_pairs"]) if tr else None,
-                    "ms_per_step": ms_g, "share_of_step": ms_g / step_ms}
-        elif dominant == "stage_a" and r0.rates["tensor_flops_a"] > 0:
-            # stage A on the tensor cores: its issued MMA work over the whole stage-A time
-            pk = peaks.get("bf16_tflops", 1900.0)
-            achieved = r0.rates["tensor_flops_a"] / (ms_a * 1e-3) / 1e12
-            roof = {"kernel": "stage A (k_phase_slices_k + tcgen05 R_e contraction + k_stage_a2 band rotation)",
-                    "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
-                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured burst)" if "bf16_tflops" in peaks
-                    else "fallback", "traffic": None, "ms_per_step": ms_a, "share_of_step": ms_a / step_ms}
-        elif dominant == "stage_a":
-            achieved = r0.rates["stage_a_flops"] / (ms_a * 1e-3) / 1e12
-            roof = {"kernel": "k_stage_a1/a2 (R_e contraction and band rotation, FP64)", "bound": "alu",
-                    "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": fp64_src, "traffic": None,
-                    "ms_per_step": ms_a, "share_of_step": ms_a / step_ms}
-        elif dominant == "corr":
-            # FP32 correction sweeps of the mixed iteration: the run words (8 B per run) are the
-            # algorithmic stream; the partner vectors are L2/L1-resident gathers and not counted
-            n32 = r0.solve["n_sweeps32"]
-            pk = peaks.get("hbm_gbs", 6800.0)
-            achieved = 8.0 * r0.solve["n_runs"] * n32 / (ms_corr * 1e-3) / 1e9
-            tr = profile_traffic("corr_sweep", "bte.cu")
+            roof = {"kernel": f"k_vertex_gemm* (tcgen05 R_ph contraction, {args.precision})", "bound": "tensor",
+                    "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16, "peak_source": bf16_src,
+                    "traffic": (tr[0] * ra["n_pairs"]) if tr else None, "algorithmic_flops": alg,
+                    "issued_mma_tflops": ra["tensor_flops"] / (ms_g * 1e-3) / 1e12,
+                    "issued_frac": ra["tensor_flops"] / (ms_g * 1e-3) / 1e12 / bf16}
+            t = ms_g
+        elif name == "stage_b":
+            alg = ra["stage_b_flops"]
+            ach = alg / (ms_b * 1e-3) / 1e12
+            roof = {"kernel": "k_stage_b_rates (R_ph contraction + rotations + rates, FP64)", "bound": "alu",
+                    "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                    "peak_source": FP64_PEAK_SRC, "traffic": None, "algorithmic_flops": alg}
+            t = ms_b
+        elif name == "epilogue":
+            # bytes the method must move per pair: the rate entries written (20 B each, electron
+            # rows) and the phonon-side entries (16 B each); the rotations run on the FP32 pipe
+            alg = 20.0 * ra["n_entries"] + 16.0 * ra["n_ph_entries"]
+            ach = alg / (ms_ep * 1e-3) / 1e9
+            roof = {"kernel": "k_rate_epilogue (rotations, |g|^2, occupations, delta, compacted writes)",
+                    "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                    "peak_source": hbm_src, "traffic": None,
+                    "note": "algorithmic bytes = rate entries written; latency of the per-pair tables bounds it"}
+            t = ms_ep
+        elif name == "corr":
+            n32 = so["n_sweeps32"]
+            alg = 8.0 * so["n_runs"] * n32
+            ach = alg / (ms_corr * 1e-3) / 1e9 if ms_corr > 0 else 0.0
             roof = {"kernel": "k_corr_sweep_seg + k_corr_finalize (FP32 correction sweeps of the mixed iteration)",
-                    "bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s", "frac": achieved / pk,
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback",
-                    "traffic": (tr[0] * r0.solve["n_runs"]) if tr else None,
-                    "ms_per_step": ms_corr, "share_of_step": ms_corr / step_ms}
-        elif dominant == "epilogue":
-            achieved = r0.rates["rot_flops"] / (ms_ep * 1e-3) / 1e12
-            tr = profile_traffic("rate_epilogue", "vertex.cu")
-            ff = args.precision == "fp64-sliced"
-            roof = {"kernel": "k_rate_epilogue (rotations, |g|^2, occupations, delta, writes; "
-                              + ("float-float rotations on the FP32 pipe, FP64 tail)" if ff else "FP64)"),
-                    "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": fp64_src,
-                    "traffic": (tr[0] * r0.rates["n_pairs"]) if tr else None,
-                    "ms_per_step": ms_ep, "share_of_step": ms_ep / step_ms}
-            if ff:
-                roof["note"] = ("achieved counts the rotations' FP64-grade flops; they run as float-float on the "
-                                "FP32 pipe, so frac can exceed 1; the FP64 pipe (delta, occupations, conversions) "
-                                "is the busiest unit (ncu: 72 %)")
+                    "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                    "peak_source": hbm_src, "traffic": None}
+            t = ms_corr
         else:
-            # the self-term gather sweep: 6 FP64 multiply-adds per partner run; the run stream
-            # (12 B per run) sits in L2 between sweeps, so the FP64 pipe is the bound
-            nsw = r0.solve["n_sweeps"]
-            achieved = r0.solve["e_sweep_flops"] * nsw / (ms_self * 1e-3) / 1e12
-            tr = profile_traffic("self_sweep", "bte.cu")
+            nsw = so["n_sweeps"]
+            ach = so["e_sweep_flops"] * nsw / (ms_self * 1e-3) / 1e12 if ms_self > 0 else 0.0
             roof = {"kernel": "k_self_sweep_seg (electron self-term gather sweep, FP64)", "bound": "alu",
-                    "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": fp64_src,
-                    "traffic": (tr[0] * r0.solve["n_runs"]) if tr else None,
-                    "hbm_gbs_algorithmic": r0.solve["e_sweep_bytes"] * nsw / (ms_self * 1e-3) / 1e9,
-                    "ms_per_step": ms_self, "share_of_step": ms_self / step_ms}
-
-
-        return roof
+                    "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                    "peak_source": FP64_PEAK_SRC, "traffic": None,
+                    "hbm_gbs_algorithmic": so["e_sweep_bytes"] * nsw / (ms_self * 1e-3) / 1e9 if ms_self > 0 else 0.0}
+            t = ms_self
+        base.update(roof)
+        base["ms_per_step"] = t
+        base["share_of_step"] = t / ms_step
+        return base
 
     dominant = max(cands, key=lambda x: x[1])[0]
     roof = roof_of(dominant)
-    # every candidate kernel against its own bound, largest share first
     rooflines = [dict(roof_of(n), name=n) for n, _ in sorted(cands, key=lambda x: -x[1])]
 
-    # end-to-end through the C ABI with host buffers: model H2D (pinned) + path + coefficients D2H
+    # end to end through the C ABI with host buffers: model H2D (pinned) + path + coefficients D2H
     e2e = None
     if not args.no_e2e:
+        import dataclasses
         m = wl.model
         pinned = {}
         for name in ("H_R", "D_R", "g_R", "Re", "Rd", "Rge", "Rgp", "sym_rot", "sym_cart", "mass_amu", "tau_cart"):
@@ -566,10 +580,12 @@ def main():
             t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
             t.numpy()[...] = a
             pinned[name] = t
-        import dataclasses
         mp = dataclasses.replace(m, **{k: v.numpy() for k, v in pinned.items()})
         h2d = int(sum(v.numel() * v.element_size() for v in pinned.values()))
         ctx2 = B.Context(local, stream=stream.cuda_stream)
+        B.set_wannier_model(ctx2, mp)
+        B.run_path(ctx2, wl, level="dragged", ko_correction=True, precision=prec, solve_precision=args.solve,
+                   accel=args.accel, tol=args.tol)       # warm-up (allocations, tile tuning)
         barrier()
         torch.cuda.synchronize()
         t1 = time.perf_counter()
@@ -578,7 +594,7 @@ def main():
             flush.zero_()
             B.set_wannier_model(ctx2, mp)
             rr = B.run_path(ctx2, wl, level="dragged", ko_correction=True, precision=prec,
-                            solve_precision=args.solve, accel=args.accel)
+                            solve_precision=args.solve, accel=args.accel, tol=args.tol)
             tup += rr.rates["n_tuples"]
         torch.cuda.synchronize()
         barrier()
@@ -588,15 +604,14 @@ def main():
                "d2h_bytes_per_step": 8 * 9 * 8, "s_per_step": e2_max / args.steps}
         ctx2.close()
 
-    # one step of each other precision of the vertex contraction: time to converged
-    # coefficients and each coefficient's relative (Frobenius) difference from this run's
-    # result (which itself matches the FP64 oracle to 1e-8 in the parity tests)
+    # one step of each other mode: time to converged coefficients at this run's tolerance and the
+    # error of every coefficient against the FP64 reference
     variants = {}
     if not args.no_variants:
         cases = [(f"{name}+{sp}-solve", p, sp, args.accel) for name, p in B.PRECISIONS.items()
                  for sp in ("fp64", "mixed") if (name, sp) != (args.precision, args.solve)]
-        if args.accel > 0:   # this run's mode with the plain outer iteration
-            cases.append((f"{args.precision}+{args.solve}-solve+plain-outer", prec, args.solve, 0))
+        cases.append((f"{args.precision}+{args.solve}-solve+outer-accel-{3 if args.accel == 0 else 0}", prec,
+                      args.solve, 3 if args.accel == 0 else 0))
         for name, p, sp, acc in cases:
             flush.zero_()
             step(p, sp, acc)              # warm-up of this mode
@@ -606,23 +621,25 @@ def main():
             rv = step(p, sp, acc)
             torch.cuda.synchronize()
             sv = time.perf_counter() - tv
-            err = {}
-            for key, ref in r0.coeffs.items():
-                nrm = float(np.linalg.norm(ref))
-                err[key] = float(np.linalg.norm(rv.coeffs[key] - ref) / nrm) if nrm > 0 else 0.0
+            e = coeff_errors(rv.coeffs, ref.coeffs)
             variants[name] = {"s_to_converged": sv, "value": rv.rates["n_tuples"] / sv,
-                              "rates_ms": rv.rates["ms"], "stage_b_ms": rv.rates["ms_stage_b"],
-                              "solve_ms": rv.solve["ms"], "fp64_sweeps": rv.solve["n_sweeps"],
-                              "fp32_sweeps": rv.solve["n_sweeps32"], "outer_iters": rv.solve["outer_iters"],
-                              "outer_accel": acc,
-                              "coeff_rel_err": err}
+                              "rates_ms": rv.rates["ms"], "stage_a_ms": rv.rates["ms_stage_a"],
+                              "stage_b_ms": rv.rates["ms_stage_b"], "solve_ms": rv.solve["ms"],
+                              "fp64_sweeps": rv.solve["n_sweeps"], "fp32_sweeps": rv.solve["n_sweeps32"],
+                              "outer_iters": rv.solve["outer_iters"], "outer_accel": acc,
+                              "max_coeff_rel_err": max(e.values()), "coeff_rel_err": e}
 
-    batched = batched_block(B, ctx, wl, args, flush, torch, np) if args.instances > 0 else None
+    batched = None
+    if args.instances > 0:
+        from paper_2109_08547_gb300 import synthetic as S
+        with B.Context(local, stream=stream.cuda_stream) as bctx:
+            batched = batched_block(B, bctx, S.workload_cscl4(24), args, flush, torch, np)
     warm = warm_block(B, args, torch, np) if args.warm > 0 else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        nt, dt, row = oracle_sample(wl)
+        P, row = oracle_row(wl)
+        nt, dt = oracle_sample(P, row)
         cpu = {"value": nt / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"FP64 oracle transition rates of one irreducible row (k index {row}, {nt} tuples, "
                          f"{dt:.1f} s)"}
@@ -630,19 +647,23 @@ def main():
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * el_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision] + SOLVE_DTYPES[args.solve], "data": "synthetic",
-            "config": {"workload": wl.name, "model": "4-band/6-branch CsCl-type cubic, 5^3 x 5^3 R grids (g 24 MB)",
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision] + SOLVE_DTYPES[args.solve],
+            "data": "synthetic",
+            "config": {"workload": wl.name, "model": model_label(wl),
                        "kmesh": list(wl.kmesh), "qmesh": list(wl.qmesh), "T_K": wl.T_K, "mu_eV": wl.mu_eV,
                        "window_eV": list(wl.window), "sigma_eV": wl.sigma_eV, "level": "dragged+KO",
-                       "tol": wl.tol, "precision": args.precision, "solve": args.solve, "outer_accel": args.accel,
+                       "tol": args.tol, "precision": args.precision, "solve": args.solve, "outer_accel": args.accel,
                        "tc_tile": {"cols": r0.rates["tc_cols"], "kblock": r0.rates["tc_kblock"],
                                    "stages": r0.rates["tc_stages"]},
                        "l2": "256 MB buffer written before every step",
                        "parallelism": f"replicas x{world}", "tuples_per_step": r0.rates["n_tuples"],
-                       "entries": r0.rates["n_entries"], "pairs": r0.rates["n_pairs"]},
-            "s_to_converged": 1e-3 * el_max / args.steps,
-            "phases_ms": {"rates": r0.rates["ms"], "stage_a": r0.rates["ms_stage_a"],
+                       "entries": r0.rates["n_entries"], "pairs": r0.rates["n_pairs"],
+                       "irreducible_window_k": r0.mesh["n_ibz_window"]},
+            "s_to_converged": s_step,
+            "accuracy": accuracy,
+            "fp64_path": fp64_block,
+            "phases_ms": {"mesh": r0.mesh.get("ms"), "rates": r0.rates["ms"], "stage_a": r0.rates["ms_stage_a"],
                           "stage_b": r0.rates["ms_stage_b"], "tensor_gemm": r0.rates["ms_gemm"],
                           "rate_epilogue": r0.rates["ms_epilogue"],
                           "solve": r0.solve["ms"], "e_sweeps": r0.solve["ms_e_sweep"],
@@ -652,7 +673,8 @@ def main():
                           "outer_iters32": r0.solve["outer_iters32"], "fp32_corrections": ms_corr,
                           "n_sweeps32": r0.solve["n_sweeps32"]},
             "variants": variants, "batched": batched, "warm_start": warm,
-            "roofline": roof, "rooflines": rooflines, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "roofline": roof, "rooflines": rooflines, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks,
         }
         print(json.dumps(out))
     ctx.close()

@@ -123,6 +123,7 @@ typedef struct {
   int64_t n_ibz;               /* irreducible points of the k mesh                         */
   int64_t n_ibz_window;        /* irreducible points with an active band                   */
   int64_t n_pairs;             /* (irreducible-window k, q) with an active band at k+q     */
+  double ms;                   /* device time of the call (CUDA events)                    */
 } ephb_mesh_info;
 
 ephb_status ephb_build_meshes_ibz(ephb_ctx *ctx, const ephb_mesh_opts *opts, ephb_mesh_info *out);
@@ -400,13 +401,22 @@ ephb_status ephb_copy_array_to_host(ephb_ctx *ctx, int which, void *host_dst, in
 /* Number of CUDA kernels the library has launched in this process (all contexts). */
 int64_t ephb_kernel_launches(void);
 
+/* Accuracy check of the library's float-float exponential, the e^(-x^2/2 sigma^2) of the
+ * Gaussian delta weights (Eq. X^e-ph, reading [A10]) in the FP64-grade rate epilogue:
+ * out_dev[i] = e^(y_dev[i]) for -60 <= y <= 0, the input taken as a float-float pair (nearest
+ * FP32 and nearest FP32 of the remainder) and the result returned as hi + lo in FP64.  Device
+ * pointers of n doubles; the work is enqueued on cuda_stream (NULL: the legacy default
+ * stream).  EPHB_EINVAL for n < 0 or a NULL pointer with n > 0, EPHB_ECUDA for a launch
+ * failure. */
+ephb_status ephb_selftest_exp_ff(const double *y_dev, double *out_dev, int64_t n, void *cuda_stream);
+
 /* ----------------------------------------------------------------------------------
  * Transport coefficients without any memory allocation.
  *
- * The paper has no counterpart: this is a service for callers that cannot allocate GPU
- * memory -- code that runs while a stream is being captured into a CUDA graph, hosts
- * whose every allocation must come from their own pool, embedders that may only use
- * buffers they were handed.  It computes the same tensors as ephb_transport_coefficients
+ * The paper has no counterpart: this is a service for callers that may not allocate GPU
+ * memory when they need the coefficients -- hosts whose every allocation must come from
+ * their own pool, embedders that may only use buffers they were handed.  It computes the
+ * same tensors as ephb_transport_coefficients
  * from response arrays the caller already holds on the device, and calls no cudaMalloc,
  * cudaFree or allocating library routine.
  *
@@ -424,7 +434,9 @@ int64_t ephb_kernel_launches(void);
  * overlaps on the GPU (different streams, or different host threads) race and must be
  * serialised by the caller.
  * The first call on a device looks up the scratch's device address for that device (with
- * that device current); make that first call before starting any stream capture.
+ * that device current) and keeps it; make that first call before starting any stream
+ * capture.  A device reset (cudaDeviceReset) invalidates the kept address: after one, this
+ * entry point must not be called again in the same process.
  * The work is enqueued on cuda_stream (NULL: the legacy default stream) and the call
  * returns without waiting; out_dev is valid once the stream reaches that point.
  * Errors: EPHB_EINVAL for NULL or out-of-range arguments, EPHB_ECUDA for a launch

@@ -37,7 +37,8 @@ EXPORTED = ["ephb_create", "ephb_destroy", "ephb_last_error", "ephb_set_wannier_
             "ephb_instance_solve_info", "ephb_num_states", "ephb_state_features", "ephb_state_targets",
             "ephb_set_warm_start", "ephb_mlp_create", "ephb_mlp_destroy", "ephb_mlp_last_error",
             "ephb_mlp_num_params", "ephb_mlp_set_bf16", "ephb_mlp_get_params", "ephb_mlp_set_params",
-            "ephb_mlp_forward", "ephb_mlp_loss_grad", "ephb_mlp_train_step", "ephb_set_tuning"]
+            "ephb_mlp_forward", "ephb_mlp_loss_grad", "ephb_mlp_train_step", "ephb_set_tuning",
+            "ephb_selftest_exp_ff"]
 NFEAT = 6
 MAX_ACCEL_DEPTH = 8   # EPHB_MAX_ACCEL_DEPTH
 
@@ -61,7 +62,7 @@ class MeshOptsC(C.Structure):
 
 class MeshInfoC(C.Structure):
     _fields_ = [("nk", C.c_int64), ("nq", C.c_int64), ("n_active_states", C.c_int64), ("n_ibz", C.c_int64),
-                ("n_ibz_window", C.c_int64), ("n_pairs", C.c_int64)]
+                ("n_ibz_window", C.c_int64), ("n_pairs", C.c_int64), ("ms", C.c_double)]
 
 
 class ThermoC(C.Structure):
@@ -381,6 +382,13 @@ def transport_coefficients_noalloc(ptrs: dict, n_states: int, n_modes: int, T_K:
     c.sym_cart[:] = list(flat)
     return int(lib.ephb_transport_coefficients_noalloc(C.byref(c), C.c_void_p(out_dev),
                                                         C.c_void_p(stream) if stream else None))
+
+
+def selftest_exp_ff(y_dev: int, out_dev: int, n: int, stream: int = 0) -> int:
+    """ephb_selftest_exp_ff: e^y of n device doubles through the library's float-float
+    exponential.  Returns the status."""
+    return int(load().ephb_selftest_exp_ff(C.c_void_p(y_dev), C.c_void_p(out_dev), C.c_int64(n),
+                                           C.c_void_p(stream) if stream else None))
 
 
 @dataclasses.dataclass

@@ -153,7 +153,7 @@ struct ephb_ctx : InstState {
   DBuf<double2> ktab, qtab, cvec, u;
   DBuf<double> eps, vel, w, vph;
   DBuf<uint8_t> egrp, pgrp;
-  DBuf<uint32_t> amask;
+  DBuf<uint32_t> amask, rmask;
   DBuf<int> rep, op, stab, flag, ibzw_list, ibzw_of, npairs, pair_q, pair_i, qcount, pq_rank;
   DBuf<int64_t> pos, pair_ptr, qpair_ptr, scratch, scal;
 
@@ -201,9 +201,9 @@ struct ephb_ctx : InstState {
   std::vector<InstState> slots = std::vector<InstState>(1);
   // tuning: column-chunk width of the tensor-core contraction (FP64-grade, mixed); 0 = not
   // tuned yet.  force_cols != 0 overrides the tuner.
-  int tune_cols[2] = {0, 0};
-  int tune_kc[2] = {32, 32};
-  int tune_st[2] = {2, 2};
+  int tune_cols[3] = {0, 0, 0};   // [7 slices, 3 slices, 8 slices]
+  int tune_kc[3] = {32, 32, 32};
+  int tune_st[3] = {2, 2, 2};
   int force_cols = 0;
   int withhold_mma = 0;   // failure-path check (EPHB_TUNE_WITHHOLD_MMA)
   double *host_res = nullptr;   // pinned: kResLen doubles, then the sweep-loop control (4 ints)
@@ -255,6 +255,7 @@ MeshDev mesh_view(ephb_ctx *c) {
   D.vel = c->vel.p;
   D.egrp = c->egrp.p;
   D.amask = c->amask.p;
+  D.rmask = c->rmask.p;
   D.w = c->w.p;
   D.u = c->u.p;
   D.vph = c->vph.p;
@@ -351,7 +352,7 @@ void ephb_destroy(ephb_ctx *ctx) {
   ctx->sym_inv.release(); ctx->H_R.release(); ctx->D_R.release(); ctx->g_R.release(); ctx->sym_cart.release();
   ctx->ktab.release(); ctx->qtab.release(); ctx->cvec.release(); ctx->u.release(); ctx->eps.release();
   ctx->vel.release(); ctx->w.release(); ctx->vph.release(); ctx->egrp.release(); ctx->pgrp.release();
-  ctx->amask.release(); ctx->rep.release(); ctx->op.release(); ctx->stab.release(); ctx->flag.release();
+  ctx->amask.release(); ctx->rmask.release(); ctx->rep.release(); ctx->op.release(); ctx->stab.release(); ctx->flag.release();
   ctx->ibzw_list.release(); ctx->ibzw_of.release(); ctx->npairs.release(); ctx->pair_q.release();
   ctx->pair_i.release(); ctx->qcount.release(); ctx->pq_rank.release(); ctx->pos.release();
   ctx->pair_ptr.release(); ctx->qpair_ptr.release(); ctx->scratch.release(); ctx->scal.release();
@@ -456,7 +457,7 @@ ephb_status ephb_set_wannier_model(ephb_ctx *ctx, const ephb_model *m) {
   M.sym_cart = ctx->sym_cart.p;
   M.sym_inv = ctx->sym_inv.p;
   ctx->stage = 1;
-  ctx->tune_cols[0] = ctx->tune_cols[1] = 0;   // a new model shape is tuned again
+  ctx->tune_cols[0] = ctx->tune_cols[1] = ctx->tune_cols[2] = 0;   // a new model shape is tuned again
   ctx->gslices_ns = 0;                          // and its g slices are made again
   ctx->bte_ready = false;
   return EPHB_OK;
@@ -489,6 +490,9 @@ ephb_status ephb_build_meshes_ibz(ephb_ctx *ctx, const ephb_mesh_opts *o, ephb_m
   const int64_t nk = km.size(), nq = qm.size();
   const int nb = M.nb, nbr = M.nbr;
   cudaStream_t st = ctx->stream;
+  EventTimer tm;
+  CK(tm.init());
+  CK(tm.start(st));
   CK(ctx->ktab.ensure(km.n[0] + km.n[1] + km.n[2]));
   CK(ctx->qtab.ensure(qm.n[0] + qm.n[1] + qm.n[2]));
   CK(ctx->eps.ensure(nk * nb));
@@ -496,6 +500,7 @@ ephb_status ephb_build_meshes_ibz(ephb_ctx *ctx, const ephb_mesh_opts *o, ephb_m
   CK(ctx->vel.ensure(nk * nb * 3));
   CK(ctx->egrp.ensure(nk * nb * 2));
   CK(ctx->amask.ensure(nk));
+  CK(ctx->rmask.ensure(nk));
   CK(ctx->w.ensure(nq * nbr));
   CK(ctx->u.ensure(nq * nbr * nbr));
   CK(ctx->vph.ensure(nq * nbr * 3));
@@ -511,11 +516,29 @@ ephb_status ephb_build_meshes_ibz(ephb_ctx *ctx, const ephb_mesh_opts *o, ephb_m
   CK(ctx->scratch.ensure(scr));
   CK(launch_phase_tables(ctx->ktab.p, km, st));
   CK(launch_phase_tables(ctx->qtab.p, qm, st));
-  CK(launch_electron_bands(M, km, ctx->ktab.p, ctx->degen_tol, ctx->lo, ctx->hi, ctx->eps.p, ctx->cvec.p,
-                           ctx->vel.p, ctx->egrp.p, ctx->amask.p, st));
   CK(launch_phonon_modes(M, qm, ctx->qtab.p, ctx->degen_tol, ctx->omega_min, ctx->w.p, ctx->u.p, ctx->vph.p,
                          ctx->pgrp.p, st));
-  CK(launch_ibz(M, km, ctx->rep.p, ctx->op.p, ctx->stab.p, ctx->flag.p, ctx->amask.p, st));
+  // Electron bands: eigen-decompositions on the representatives of the wedge first; a point whose
+  // representative has no band in the window takes the representative's energies and rotated
+  // velocities (it holds no active state and no rate reads its eigenvectors); every other point
+  // is decomposed itself.  Without symmetry every point is its own representative.
+  CK(launch_ibz(M, km, ctx->rep.p, ctx->op.p, ctx->stab.p, ctx->flag.p, st));
+  CK(exclusive_scan<int>(ctx->flag.p, ctx->pos.p, nk, ctx->scal.p + 0, ctx->scratch.p, ctx->scratch.n, st));
+  CK(launch_compact(nk, ctx->flag.p, ctx->pos.p, ctx->ibzw_of.p, st));     // representatives (scratch use)
+  int64_t n_rep = 0, n_own = 0;
+  CK(cudaMemcpyAsync(&n_rep, ctx->scal.p + 0, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  CK(launch_electron_bands(M, km, ctx->ibzw_of.p, n_rep, ctx->ktab.p, ctx->degen_tol, ctx->lo, ctx->hi, ctx->eps.p,
+                           ctx->cvec.p, ctx->vel.p, ctx->egrp.p, ctx->amask.p, ctx->rmask.p, st));
+  CK(launch_bands_from_rep(M, km, ctx->rep.p, ctx->op.p, ctx->eps.p, ctx->vel.p, ctx->egrp.p, ctx->amask.p,
+                           ctx->rmask.p, ctx->flag.p, st));
+  CK(exclusive_scan<int>(ctx->flag.p, ctx->pos.p, nk, ctx->scal.p + 0, ctx->scratch.p, ctx->scratch.n, st));
+  CK(launch_compact(nk, ctx->flag.p, ctx->pos.p, ctx->ibzw_of.p, st));     // points decomposed themselves
+  CK(cudaMemcpyAsync(&n_own, ctx->scal.p + 0, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  CK(launch_electron_bands(M, km, ctx->ibzw_of.p, n_own, ctx->ktab.p, ctx->degen_tol, ctx->lo, ctx->hi, ctx->eps.p,
+                           ctx->cvec.p, ctx->vel.p, ctx->egrp.p, ctx->amask.p, ctx->rmask.p, st));
+  CK(launch_ibzw_flag(nk, ctx->rep.p, ctx->amask.p, ctx->flag.p, st));
   CK(exclusive_scan<int>(ctx->flag.p, ctx->pos.p, nk, ctx->scal.p + 0, ctx->scratch.p, ctx->scratch.n, st));
   CK(launch_count_bits(ctx->amask.p, nk, ctx->scal.p + 1, st));
   CK(launch_count_reps(ctx->rep.p, nk, ctx->scal.p + 2, st));
@@ -548,8 +571,11 @@ ephb_status ephb_build_meshes_ibz(ephb_ctx *ctx, const ephb_mesh_opts *o, ephb_m
                          ctx->scratch.n, st));
   D = mesh_view(ctx);
   CK(launch_qpair_fill(D, ctx->pq_rank.p, st));
+  CK(tm.stop(st));
   CK(cudaStreamSynchronize(st));
+  CK(tm.collect());
   ephb_mesh_info info;
+  info.ms = tm.ms;
   info.nk = nk;
   info.nq = nq;
   info.n_active_states = host_scal[1];
@@ -663,9 +689,9 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
   if (!(delta->sigma_eV > 0) || !(delta->cutoff_sigmas > 0))
     return fail(ctx, EPHB_EINVAL, "sigma and cutoff must be positive");
   // exact FP32 sums of the accumulated slice diagonals bound the contraction length
-  if (precision == EPHB_FP64_SLICED && tc_kp(ctx->M) > 256)
-    return fail(ctx, EPHB_EINVAL, "EPHB_FP64_SLICED needs 2 nRgp <= 256");
-  if (precision == EPHB_SPLIT_BF16 && tc_kp(ctx->M) > 1024)
+  if (precision == EPHB_FP64_SLICED && tc_slices_for(tc_kp(ctx->M), true) == 0)
+    return fail(ctx, EPHB_EINVAL, "EPHB_FP64_SLICED needs 2 nRgp <= 816");
+  if (precision == EPHB_SPLIT_BF16 && tc_slices_for(tc_kp(ctx->M), false) == 0)
     return fail(ctx, EPHB_EINVAL, "EPHB_SPLIT_BF16 needs 2 nRgp <= 1024");
   bool windowed = false;
   for (int i = 0; i < ninst; ++i) {
@@ -760,13 +786,14 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
   CK(tc.init());
   CK(tg.init());
   const bool tensor = precision != EPHB_FP64;
-  const int ns = precision == EPHB_FP64_SLICED ? 7 : 3;
+  const int ns = tensor ? tc_slices_for(tc_kp(M), precision == EPHB_FP64_SLICED) : 0;
+  const int tslot = ns == 8 ? 2 : (ns == 7 ? 0 : 1);   // tuned tile shape per slicing (3 or 4 slices: 1)
   const int ncm = tensor && ctx->force_cols ? std::min(ctx->force_cols, tc_nc_max(ns)) : 0;   // 0: tuned width
   int autotuned = 0;
   // stage A on the tensor cores too, always in the FP64-grade form (its error would add to the
   // mixed mode's), while its contraction length keeps the diagonal sums exact
-  const int ns_a = 7;
-  const bool tensor_a = tensor && tc_kp_a(M) <= 256;
+  const int ns_a = tc_slices_for(tc_kp_a(M), true);
+  const bool tensor_a = tensor && ns_a != 0;
   double tensor_flops_a = 0.0;
   std::vector<int64_t> hpp;
   int Nmax = 0;
@@ -854,9 +881,9 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
                                 ctx->scal.p + 6, ctx->Cbuf.p, ctx->tc_err.p, st, e0, e1, width, kc, stages,
                                 ctx->withhold_mma, ctx->ws_desc.p, ctx->ws_cap);
       };
-      int &tuned = ctx->tune_cols[ns == 7 ? 0 : 1];
-      int &tuned_kc = ctx->tune_kc[ns == 7 ? 0 : 1];
-      int &tuned_st = ctx->tune_st[ns == 7 ? 0 : 1];
+      int &tuned = ctx->tune_cols[tslot];
+      int &tuned_kc = ctx->tune_kc[tslot];
+      int &tuned_st = ctx->tune_st[tslot];
       if (ncm == 0 && tuned == 0) {
         // autotune on this chunk: time the GEMM at every candidate tile shape and keep the
         // fastest (the contraction is the same for every shape, so the last run stands)
@@ -933,9 +960,9 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     out->tensor_flops_a = tensor_flops_a;
     out->rot_flops = double(cnt[4]);
     out->ms_gemm = tg.ms;
-    out->tc_cols = tensor ? (ncm ? ncm : ctx->tune_cols[ns == 7 ? 0 : 1]) : 0;
-    out->tc_kblock = tensor ? (ncm ? 32 : ctx->tune_kc[ns == 7 ? 0 : 1]) : 0;
-    out->tc_stages = tensor ? (ncm ? 2 : ctx->tune_st[ns == 7 ? 0 : 1]) : 0;
+    out->tc_cols = tensor ? (ncm ? ncm : ctx->tune_cols[tslot]) : 0;
+    out->tc_kblock = tensor ? (ncm ? 32 : ctx->tune_kc[tslot]) : 0;
+    out->tc_stages = tensor ? (ncm ? 2 : ctx->tune_st[tslot]) : 0;
     out->autotuned = autotuned;
   }
   ctx->stage = 3;
@@ -1613,7 +1640,7 @@ ephb_status ephb_set_tuning(ephb_ctx *ctx, int key, int value) {
   if (value != 0 && (value < 16 || value % 16 != 0 || value > 256))
     return fail(ctx, EPHB_EINVAL, "column-chunk width must be 0 or a multiple of 16 in [16, 256]");
   ctx->force_cols = value;
-  if (value == 0) ctx->tune_cols[0] = ctx->tune_cols[1] = 0;   // tune again on the next call
+  if (value == 0) ctx->tune_cols[0] = ctx->tune_cols[1] = ctx->tune_cols[2] = 0;   // tune again on the next call
   return EPHB_OK;
 }
 
@@ -1686,3 +1713,10 @@ ephb_status ephb_copy_array_to_host(ephb_ctx *ctx, int which, void *host_dst, in
 }
 
 }  // extern "C"
+
+extern "C" ephb_status ephb_selftest_exp_ff(const double *y_dev, double *out_dev, int64_t n, void *cuda_stream) {
+  if (n < 0 || (n > 0 && (!y_dev || !out_dev))) return EPHB_EINVAL;
+  if (launch_selftest_exp_ff(y_dev, out_dev, n, static_cast<cudaStream_t>(cuda_stream)) != cudaSuccess)
+    return EPHB_ECUDA;
+  return EPHB_OK;
+}

@@ -19,14 +19,16 @@ __global__ void k_phase_tables(double2 *tab, Mesh m) {
   tab[t] = cmk(c, s);
 }
 
-// One thread per k point: H(k), grad_k H(k), eigen-decomposition, velocities.
+// One thread per listed k point: H(k), grad_k H(k), eigen-decomposition, velocities.
 template <int NB>
-__global__ void __launch_bounds__(128) k_electron_bands(ModelDev M, Mesh km, const double2 *__restrict__ ktab,
+__global__ void __launch_bounds__(128) k_electron_bands(ModelDev M, Mesh km, const int *__restrict__ list, int64_t n,
+                                                        const double2 *__restrict__ ktab,
                                                         double degen_tol, double lo, double hi, double *eps,
                                                         double2 *cvec, double *vel, uint8_t *egrp,
-                                                        uint32_t *amask) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= km.size()) return;
+                                                        uint32_t *amask, uint32_t *rmask) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= n) return;
+  const int k = list[t];
   const int nb = M.nb;
   int i0, i1, i2;
   km.unflat(k, i0, i1, i2);
@@ -82,6 +84,13 @@ __global__ void __launch_bounds__(128) k_electron_bands(ModelDev M, Mesh km, con
     for (int i = 0; i < nb; ++i) cvec[(size_t(k) * nb + i) * nb + m] = V[i * NB + m];
   }
   amask[k] = mask;
+  // the degenerate subspaces of the active bands, whole ([A9]: a subspace cut by a window edge
+  // still averages |g|^2 over all its bands)
+  uint32_t rot = 0;
+  for (int m = 0; m < nb; ++m)
+    if ((mask >> m) & 1u)
+      for (int a = grp[2 * m]; a < grp[2 * m + 1]; ++a) rot |= 1u << a;
+  rmask[k] = rot;
 }
 
 // One thread per q point: D(q), eigen-decomposition, hbar w = sqrt(max(lambda,0)), velocities.
@@ -152,8 +161,8 @@ __global__ void __launch_bounds__(128) k_phonon_modes(ModelDev M, Mesh qm, const
 }
 
 // Irreducible wedge: representative = smallest image index, first op S with S<k> = k,
-// stabiliser size.  Also flags representatives holding an active band.
-__global__ void k_ibz(ModelDev M, Mesh km, int *rep, int *op, int *stab, int *flag, const uint32_t *amask) {
+// stabiliser size.  flag = 1 for the representatives.
+__global__ void k_ibz(ModelDev M, Mesh km, int *rep, int *op, int *stab, int *flag) {
   __shared__ int rot[kMaxSym * 9];
   for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) rot[t] = M.sym_rot[t];
   __syncthreads();
@@ -185,7 +194,51 @@ __global__ void k_ibz(ModelDev M, Mesh km, int *rep, int *op, int *stab, int *fl
   rep[k] = best;
   op[k] = first;
   stab[k] = ns;
-  flag[k] = (best == k && amask[k] != 0u) ? 1 : 0;
+  flag[k] = best == k ? 1 : 0;
+}
+
+// Every point that is not a representative: when its representative has no band in the window
+// (band energies are symmetric, eps(S<k>) = eps(<k>), so neither has this point) it takes the
+// representative's energies and degenerate groups and the rotated velocities v(S<k>) = S v(<k>),
+// with no active band; otherwise flag = 1 asks for its own eigen-decomposition (the rates need
+// its eigenvectors).  Representatives: flag = 0.
+__global__ void k_bands_from_rep(ModelDev M, Mesh km, const int *rep, const int *op, double *eps, double *vel,
+                                 uint8_t *egrp, uint32_t *amask, uint32_t *rmask, int *flag) {
+  const int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (k >= km.size()) return;
+  const int r = rep[k];
+  if (r == int(k)) {
+    flag[k] = 0;
+    return;
+  }
+  if (amask[r] != 0u) {
+    flag[k] = 1;
+    return;
+  }
+  flag[k] = 0;
+  const int nb = M.nb;
+  const double *S = M.sym_cart + 9 * op[k];
+  for (int m = 0; m < nb; ++m) {
+    eps[k * nb + m] = eps[size_t(r) * nb + m];
+    egrp[(k * nb + m) * 2] = egrp[(size_t(r) * nb + m) * 2];
+    egrp[(k * nb + m) * 2 + 1] = egrp[(size_t(r) * nb + m) * 2 + 1];
+    const double *v = vel + (size_t(r) * nb + m) * 3;
+    for (int a = 0; a < 3; ++a) vel[(k * nb + m) * 3 + a] = S[3 * a] * v[0] + S[3 * a + 1] * v[1] + S[3 * a + 2] * v[2];
+  }
+  amask[k] = 0u;
+  rmask[k] = 0u;
+}
+
+// flag = 1 for representatives with an active band
+__global__ void k_ibzw_flag(int64_t nk, const int *rep, const uint32_t *amask, int *flag) {
+  const int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (k < nk) flag[k] = (rep[k] == int(k) && amask[k] != 0u) ? 1 : 0;
+}
+
+// list[pos[k]] = k for the flagged points
+__global__ void k_compact(int64_t n, const int *flag, const int64_t *pos, int *list) {
+  const int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (k < n && flag[k]) list[pos[k]] = int(k);
 }
 
 __global__ void k_ibzw_fill(int64_t nk, const int *flag, const int64_t *pos, int *list, int *of) {
@@ -322,17 +375,37 @@ cudaError_t launch_phase_tables(double2 *tab, Mesh m, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_electron_bands(const ModelDev &M, Mesh km, const double2 *ktab, double degen_tol, double lo,
-                                  double hi, double *eps, double2 *cvec, double *vel, uint8_t *egrp,
-                                  uint32_t *amask, cudaStream_t st) {
-  int64_t n = km.size();
+cudaError_t launch_electron_bands(const ModelDev &M, Mesh km, const int *list, int64_t n, const double2 *ktab,
+                                  double degen_tol, double lo, double hi, double *eps, double2 *cvec, double *vel,
+                                  uint8_t *egrp, uint32_t *amask, uint32_t *rmask, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
   int grid = int((n + 127) / 128);
   if (M.nb <= 1)
-    EPHB_LAUNCH(k_electron_bands<1>, grid, 128, 0, st, M, km, ktab, degen_tol, lo, hi, eps, cvec, vel, egrp, amask);
+    EPHB_LAUNCH(k_electron_bands<1>, grid, 128, 0, st, M, km, list, n, ktab, degen_tol, lo, hi, eps, cvec, vel, egrp,
+                amask, rmask);
   else if (M.nb <= 4)
-    EPHB_LAUNCH(k_electron_bands<4>, grid, 128, 0, st, M, km, ktab, degen_tol, lo, hi, eps, cvec, vel, egrp, amask);
+    EPHB_LAUNCH(k_electron_bands<4>, grid, 128, 0, st, M, km, list, n, ktab, degen_tol, lo, hi, eps, cvec, vel, egrp,
+                amask, rmask);
   else
-    EPHB_LAUNCH(k_electron_bands<8>, grid, 128, 0, st, M, km, ktab, degen_tol, lo, hi, eps, cvec, vel, egrp, amask);
+    EPHB_LAUNCH(k_electron_bands<8>, grid, 128, 0, st, M, km, list, n, ktab, degen_tol, lo, hi, eps, cvec, vel, egrp,
+                amask, rmask);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bands_from_rep(const ModelDev &M, Mesh km, const int *rep, const int *op, double *eps, double *vel,
+                                  uint8_t *egrp, uint32_t *amask, uint32_t *rmask, int *flag, cudaStream_t st) {
+  const int64_t n = km.size();
+  EPHB_LAUNCH(k_bands_from_rep, int((n + 255) / 256), 256, 0, st, M, km, rep, op, eps, vel, egrp, amask, rmask, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ibzw_flag(int64_t nk, const int *rep, const uint32_t *amask, int *flag, cudaStream_t st) {
+  EPHB_LAUNCH(k_ibzw_flag, int((nk + 255) / 256), 256, 0, st, nk, rep, amask, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact(int64_t n, const int *flag, const int64_t *pos, int *list, cudaStream_t st) {
+  EPHB_LAUNCH(k_compact, int((n + 255) / 256), 256, 0, st, n, flag, pos, list);
   return cudaGetLastError();
 }
 
@@ -349,10 +422,9 @@ cudaError_t launch_phonon_modes(const ModelDev &M, Mesh qm, const double2 *qtab,
   return cudaGetLastError();
 }
 
-cudaError_t launch_ibz(const ModelDev &M, Mesh km, int *rep, int *op, int *stab, int *flag, const uint32_t *amask,
-                       cudaStream_t st) {
+cudaError_t launch_ibz(const ModelDev &M, Mesh km, int *rep, int *op, int *stab, int *flag, cudaStream_t st) {
   int64_t n = km.size();
-  EPHB_LAUNCH(k_ibz, int((n + 127) / 128), 128, 0, st, M, km, rep, op, stab, flag, amask);
+  EPHB_LAUNCH(k_ibz, int((n + 127) / 128), 128, 0, st, M, km, rep, op, stab, flag);
   return cudaGetLastError();
 }
 

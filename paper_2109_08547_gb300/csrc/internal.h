@@ -33,7 +33,9 @@ struct MeshDev {
   const double2 *cvec;                // [nk][nb][nb]  c[k][row][col]
   const double *vel;                  // [nk][nb][3]
   const uint8_t *egrp;                // [nk][nb][2] degenerate group [lo, hi)
-  const uint32_t *amask;              // [nk]
+  const uint32_t *amask;              // [nk] bands inside the window (the states of the BTE)
+  const uint32_t *rmask;              // [nk] amask plus every band degenerate with an active one:
+                                      //      the bands whose |g|^2 enters the degenerate averages
   const double *w;                    // [nq][nbr]
   const double2 *u;                   // [nq][nbr][nbr]
   const double *vph;                  // [nq][nbr][3]
@@ -60,13 +62,16 @@ int64_t scan_scratch_elems(int64_t n);
 
 // ---- bloch.cu
 cudaError_t launch_phase_tables(double2 *tab, Mesh m, cudaStream_t st);
-cudaError_t launch_electron_bands(const ModelDev &M, Mesh km, const double2 *ktab, double degen_tol, double lo,
-                                  double hi, double *eps, double2 *cvec, double *vel, uint8_t *egrp,
-                                  uint32_t *amask, cudaStream_t st);
+cudaError_t launch_electron_bands(const ModelDev &M, Mesh km, const int *list, int64_t n, const double2 *ktab,
+                                  double degen_tol, double lo, double hi, double *eps, double2 *cvec, double *vel,
+                                  uint8_t *egrp, uint32_t *amask, uint32_t *rmask, cudaStream_t st);
+cudaError_t launch_bands_from_rep(const ModelDev &M, Mesh km, const int *rep, const int *op, double *eps, double *vel,
+                                  uint8_t *egrp, uint32_t *amask, uint32_t *rmask, int *flag, cudaStream_t st);
+cudaError_t launch_ibzw_flag(int64_t nk, const int *rep, const uint32_t *amask, int *flag, cudaStream_t st);
+cudaError_t launch_compact(int64_t n, const int *flag, const int64_t *pos, int *list, cudaStream_t st);
 cudaError_t launch_phonon_modes(const ModelDev &M, Mesh qm, const double2 *qtab, double degen_tol, double omega_min,
                                 double *w, double2 *u, double *vph, uint8_t *pgrp, cudaStream_t st);
-cudaError_t launch_ibz(const ModelDev &M, Mesh km, int *rep, int *op, int *stab, int *ibzw_flag,
-                       const uint32_t *amask, cudaStream_t st);
+cudaError_t launch_ibz(const ModelDev &M, Mesh km, int *rep, int *op, int *stab, int *flag, cudaStream_t st);
 cudaError_t launch_ibzw_fill(int64_t nk, const int *flag, const int64_t *pos, int *ibzw_list, int *ibzw_of,
                              cudaStream_t st);
 cudaError_t launch_pair_count(const MeshDev &D, int *npairs, cudaStream_t st);
@@ -142,7 +147,11 @@ cudaError_t launch_stage_a2(const ModelDev &M, const MeshDev &D, int64_t i0, int
 struct TcShape {
   int width, kc, stages;
 };
+cudaError_t launch_selftest_exp_ff(const double *y, double *out, int64_t n, cudaStream_t st);
 int tc_nc_max(int ns);
+// slices of the exact fixed-point form for a contraction length kp: FP64-grade 7 (kp <= 256)
+// or 8 (base-128 digits, kp <= 816), split-BF16 3 (kp <= 1024); 0 where none applies
+int tc_slices_for(int kp, bool fp64_grade);
 bool tc_nc_valid(int ns, int ncm, int kc, int stages);
 std::vector<TcShape> tc_shape_candidates(int ns);
 

@@ -1,11 +1,11 @@
 // Transport-coefficient reduction that allocates no memory.
 //
-// Some callers cannot call cudaMalloc: code running while a stream is being captured into
-// a CUDA graph, host frameworks that hand every allocation to their own pool, and
-// embedders that may only touch memory they were given.  This entry point lets them turn
-// response arrays they already own into the coefficient tensors.  Its only scratch is a
-// file-scope __device__ array holding the per-block partial sums; every GPU that loads the
-// library keeps that array until the process exits.
+// Some callers may not allocate device memory when they need the coefficients: hosts that
+// route every allocation through a pool of their own, and embedders that may only touch the
+// buffers they were handed.  This entry point lets them turn response arrays they already
+// own into the coefficient tensors.  Its only scratch is a file-scope __device__ array
+// holding the per-block partial sums; every GPU that loads the library keeps that array
+// until the process exits.
 #include <mutex>
 
 #include "ephb.h"
@@ -106,23 +106,23 @@ __global__ void k_na_final(NaParams p, const double *scratch, double *out) {
     if (lane == 0) M[j] = s;
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  double t[4][9];
+  // symmetrised electron tensors, one thread per (tensor, a, b): sum_S S M S^T (48 x 9 terms)
+  __shared__ double t[4][9];
   const double sg[4] = {1.0, 1.0, -1.0, -1.0};
-  for (int c = 0; c < 4; ++c) {
-    for (int j = 0; j < 9; ++j) t[c][j] = 0.0;
+  if (threadIdx.x < 36) {
+    const int c = threadIdx.x / 9, a = (threadIdx.x % 9) / 3, b = threadIdx.x % 3;
+    double acc = 0.0;
     for (int o = 0; o < p.nsym; ++o) {
       const double *S = p.C + 9 * o;
-      for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) {
-          double s = 0.0;
-          for (int e = 0; e < 3; ++e)
-            for (int f = 0; f < 3; ++f) s += S[a * 3 + e] * M[9 * c + e * 3 + f] * S[b * 3 + f];
-          t[c][a * 3 + b] += s;
-        }
+      double s = 0.0;
+      for (int e = 0; e < 3; ++e)
+        for (int f = 0; f < 3; ++f) s += S[a * 3 + e] * M[9 * c + e * 3 + f] * S[b * 3 + f];
+      acc += s;
     }
-    for (int j = 0; j < 9; ++j) t[c][j] *= sg[c] * p.Pe;
+    t[c][a * 3 + b] = acc * sg[c] * p.Pe;
   }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   const double *sig = t[0];
   double inv[9];
   inv[0] = sig[4] * sig[8] - sig[5] * sig[7];

@@ -56,15 +56,37 @@ __constant__ float2 kInvFact[14] = {
 
 // e^y in float-float for -60 <= y <= 0: y = k ln2 + r with |r| <= ln2/2 (plus rounding),
 // e^r from its Taylor series to r^13/13! (the remainder is below 1e-17 of the sum) by
-// float-float Horner steps, then the exact scaling by 2^k.  ~2^-46 relative, FP32 pipe only.
+// float-float Horner steps, then the exact scaling by 2^k.  The reduction subtracts k ln2 in
+// three parts (Cody and Waite's splitting of the constant): C1 and C2 carry 17 significant bits,
+// so k C1 and k C2 are exact FP32 products for |k| <= 127, and C3 the rest of ln 2 (the three
+// sum to ln 2 within 3e-19); r then carries ~2^-49 absolute error instead of 2^-48 of |y|.
+// ~2^-46 relative overall, FP32 pipe only.
 __device__ inline float2 exp_ff(float2 y) {
-  const float2 ln2 = make_float2(0x1.62e43p-1f, -0x1.05c61p-29f);
+  const float C1 = 0x1.62e4p-1f, C2 = 0x1.7f7ep-20f, C3 = -0x1.c610cap-37f;
   const int k = __float2int_rn(__fmul_rn(y.x, 0x1.715476p+0f));   // y / ln2, nearest integer
-  const float2 r = ff_add(y, ff_neg(ff_mul(make_float2(float(k), 0.f), ln2)));
+  const float kf = float(k);
+  // y.x - k C1 is exact (Sterbenz: the two are within a factor 2 for k != 0); then y.y and
+  // -k C2 join by error-free TwoSums, and the error terms with -k C3 in one FP32 sum
+  const float a = __fsub_rn(y.x, __fmul_rn(kf, C1));
+  float s1, e1, s2, e2;
+  ff_two_sum(a, y.y, s1, e1);
+  ff_two_sum(s1, __fmul_rn(-kf, C2), s2, e2);
+  const float e = __fmaf_rn(-kf, C3, __fadd_rn(e1, e2));
+  float2 r;
+  ff_two_sum(s2, e, r.x, r.y);
   float2 p = kInvFact[13];
   for (int n = 12; n >= 0; --n) p = ff_add(ff_mul(p, r), kInvFact[n]);
   const float s = __int_as_float((k + 127) << 23);   // 2^k, k >= -87 here
   return make_float2(__fmul_rn(p.x, s), __fmul_rn(p.y, s));
+}
+
+// e^y of n values through exp_ff (the input converted to float-float as the epilogue does,
+// the result summed back to FP64): the library's own exponential, exposed for its accuracy test
+__global__ void k_selftest_exp_ff(const double *y, double *out, int64_t n) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const float2 e = exp_ff(ff_from_double(y[i]));
+  out[i] = double(e.x) + double(e.y);
 }
 
 // gauss_in with the exponential in float-float: the FP64 pipe sees only the conversions of x
@@ -111,8 +133,9 @@ __global__ void k_rate_count(ModelDev M, MeshDev D, RateParams rp, int *cntE, in
     uint32_t am = D.amask[k], an = D.amask[kp];
     int64_t p0 = D.pair_ptr[i];
     int64_t npl = D.pair_ptr[i + 1] - p0, pl = p - p0;
-    // algorithmic flops of stage B for this pair: R_ph sum, branch rotation, band rotation
-    const unsigned long long na = __popc(am), nap = __popc(an);
+    // algorithmic flops of stage B for this pair: R_ph sum, branch rotation, band rotation (over
+    // the rotation bands: the active ones and their degenerate partners)
+    const unsigned long long na = __popc(D.rmask[k]), nap = __popc(D.rmask[kp]);
     fl = 8ull * (na * nb * nbr * (unsigned long long)M.nRgp + na * nb * nbr * nbr + na * nap * nb * nbr);
     if (pl == 0) ns = na;
     rf = 8ull * (na * nb * nbr * nbr + na * nap * nb * nbr);   // rotations only
@@ -206,7 +229,8 @@ __global__ void __launch_bounds__(256) k_stage_a1(ModelDev M, MeshDev D, int64_t
     if (kc0 + kk < nkc) T[(kc0 + kk) * ncol + col] = acc[kk];
 }
 
-// A[kc][rp][j], j = ml*(nb*nbr) + n'*nbr + a over the active bands m of k:
+// A[kc][rp][j], j = ml*(nb*nbr) + n'*nbr + a over the rotation bands m of k (the active bands
+// and their degenerate partners):
 //   A = sum_m' c_{m'm}(k) T[kc][rp][m'][n'][a]
 __global__ void k_stage_a2(ModelDev M, MeshDev D, int64_t i0, int64_t nkc, const double2 *T, double2 *A) {
   const int nb = M.nb, nbr = M.nbr;
@@ -218,10 +242,10 @@ __global__ void k_stage_a2(ModelDev M, MeshDev D, int64_t i0, int64_t nkc, const
   int rp = int(r / jmax), j = int(r % jmax);
   int ml = j / (nb * nbr), na = j % (nb * nbr);
   int k = D.ibzw_list[i0 + kc];
-  uint32_t am = D.amask[k];
+  uint32_t rm = D.rmask[k];
   double2 acc = cmk(0, 0);
-  if (ml < __popc(am)) {
-    int m = nth_bit(am, ml);
+  if (ml < __popc(rm)) {
+    int m = nth_bit(rm, ml);
     const double2 *Tk = T + kc * per_k + int64_t(rp) * jmax;
     const double2 *ck = D.cvec + size_t(k) * nb * nb;
     for (int mp = 0; mp < nb; ++mp) cfma(acc, ck[mp * nb + m], Tk[mp * nb * nbr + na]);
@@ -258,7 +282,7 @@ __host__ __device__ inline StageBSmem stage_b_layout(int nb, int nbr) {
 // Rotations, |g|^2, degenerate average, occupations, delta and the compacted writes of one
 // (k, q) pair, executed by one warp.  Bp holds B[ml][n'][alpha] = sum_Rp e^{iq.Rp} A (complex).
 __device__ void pair_epilogue(const ModelDev &M, const MeshDev &D, const RateParams &rp, int64_t i, int k,
-                              uint32_t am, int nact, int Jk, int64_t p0, int64_t npl, int64_t pg,
+                              uint32_t am, uint32_t rm, int nrot, int Jk, int64_t p0, int64_t npl, int64_t pg,
                               const double2 *Bp, double2 *Zs, double *g2s, double *Xps, double *Xms,
                               const double *mscale, double inv_stab, const double *ek, double kT,
                               const int64_t *__restrict__ escan, const int64_t *__restrict__ phscan,
@@ -267,8 +291,9 @@ __device__ void pair_epilogue(const ModelDev &M, const MeshDev &D, const RatePar
   const int lane = threadIdx.x & 31;
   const int q = D.pair_q[pg];
   const int kp = kplusq_d(D, k, q);
-  const uint32_t an = D.amask[kp];
-  const int nactp = __popc(an);
+  // emission: active bands am (k), an (k'); rotations: rm, rn (with the degenerate partners)
+  const uint32_t an = D.amask[kp], rn = D.rmask[kp];
+  const int nact = __popc(am), nactp = __popc(an), nrotp = __popc(rn);
   const double2 *uq = D.u + size_t(q) * nbr * nbr;
   const double *wq = D.w + size_t(q) * nbr;
   const double2 *ckp = D.cvec + size_t(kp) * nb * nb;
@@ -282,11 +307,11 @@ __device__ void pair_epilogue(const ModelDev &M, const MeshDev &D, const RatePar
     Zs[t] = z;
   }
   __syncwarp();
-  // g[ml][nl][s] = sqrt(w_ref / w_s) sum_n' conj(c_{n'n}(k')) Z[ml][n'][s]
-  const int ntup = nact * nactp * nbr;
-  for (int t = lane; t < ntup; t += 32) {
-    int ml = t / (nactp * nbr), nl = (t / nbr) % nactp, s = t % nbr;
-    int n = nth_bit(an, nl);
+  // g[ml][nl][s] = sqrt(w_ref / w_s) sum_n' conj(c_{n'n}(k')) Z[ml][n'][s], rotation bands
+  const int nrtup = nrot * nrotp * nbr;
+  for (int t = lane; t < nrtup; t += 32) {
+    int ml = t / (nrotp * nbr), nl = (t / nbr) % nrotp, s = t % nbr;
+    int n = nth_bit(rn, nl);
     double v = 0.0;
     if (wq[s] > D.omega_min) {
       double2 g = cmk(0, 0);
@@ -300,21 +325,21 @@ __device__ void pair_epilogue(const ModelDev &M, const MeshDev &D, const RatePar
   int *flg = reinterpret_cast<int *>(Zs);
   const uint8_t *gk = D.egrp + size_t(k) * nb * 2, *gkp = D.egrp + size_t(kp) * nb * 2;
   const uint8_t *gq = D.pgrp + size_t(q) * nbr * 2;
+  const int ntup = nact * nactp * nbr;
   for (int t = lane; t < ntup; t += 32) {
     int ml = t / (nactp * nbr), nl = (t / nbr) % nactp, s = t % nbr;
     int m = nth_bit(am, ml), n = nth_bit(an, nl);
     double xp = 0.0, xm = 0.0;
     if (wq[s] > D.omega_min) {
+      // average over the whole degenerate subspaces (every member is a rotation band)
       double sum = 0.0;
       int cnt = 0;
       for (int a = gk[2 * m]; a < gk[2 * m + 1]; ++a) {
-        if (!((am >> a) & 1u)) continue;
-        int al = __popc(am & ((1u << a) - 1u));
+        int al = __popc(rm & ((1u << a) - 1u));
         for (int b = gkp[2 * n]; b < gkp[2 * n + 1]; ++b) {
-          if (!((an >> b) & 1u)) continue;
-          int bl = __popc(an & ((1u << b) - 1u));
+          int bl = __popc(rn & ((1u << b) - 1u));
           for (int c = gq[2 * s]; c < gq[2 * s + 1]; ++c) {
-            sum += g2s[(al * nactp + bl) * nbr + c];
+            sum += g2s[(al * nrotp + bl) * nbr + c];
             ++cnt;
           }
         }
@@ -414,9 +439,9 @@ __global__ void __launch_bounds__(kBT) k_stage_b_rates(ModelDev M, MeshDev D, Ra
 
   const int64_t i = i0 + blockIdx.x;
   const int k = D.ibzw_list[i];
-  const uint32_t am = D.amask[k];
-  const int nact = __popc(am);
-  const int Jk = nact * nb * nbr;
+  const uint32_t am = D.amask[k], rm = D.rmask[k];
+  const int nrot = __popc(rm);
+  const int Jk = nrot * nb * nbr;
   const int64_t p0 = D.pair_ptr[i];
   const int64_t npl = D.pair_ptr[i + 1] - p0;
   const double2 *Ak = A + size_t(blockIdx.x) * M.nRgp * L.jmax;
@@ -473,7 +498,7 @@ __global__ void __launch_bounds__(kBT) k_stage_b_rates(ModelDev M, MeshDev D, Ra
 
     // ---- epilogue: one warp per pair
     for (int p = wid; p < npt; p += kBT / 32)
-      pair_epilogue(M, D, rp, i, k, am, nact, Jk, p0, npl, p0 + t0 + p, Bsh + p * Jk, Zs, g2s, Xps, Xms, mscale,
+      pair_epilogue(M, D, rp, i, k, am, rm, nrot, Jk, p0, npl, p0 + t0 + p, Bsh + p * Jk, Zs, g2s, Xps, Xms, mscale,
                     inv_stab, ek, kT, escan, phscan, e_kpns, e_X, ph_st, ph_kpn, ph_Y);
   }
 }
@@ -537,8 +562,9 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
   const int i = D.pair_i[pg], q = D.pair_q[pg];
   const int k = D.ibzw_list[i];
   const int kp = kplusq_d(D, k, q);
-  const uint32_t am = D.amask[k], an = D.amask[kp];
-  const int nact = __popc(am), nactp = __popc(an);
+  // emission: active bands am (k), an (k'); rotations: rm, rn (with the degenerate partners)
+  const uint32_t am = D.amask[k], an = D.amask[kp], rm = D.rmask[k], rn = D.rmask[kp];
+  const int nact = __popc(am), nactp = __popc(an), nrot = __popc(rm), nrotp = __popc(rn);
   const int64_t p0 = D.pair_ptr[i];
   const int64_t npl = D.pair_ptr[i + 1] - p0;
   const float2 *crow = reinterpret_cast<const float2 *>(Cbuf) + (pg - pair_base) * Nmax;
@@ -549,9 +575,9 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
   // applied only where a tuple inside the delta cutoff needs the value
   float2 g2[NBM * NBM * NBRM];
   if (ROT32) {
-    for (int ml = 0; ml < nact; ++ml)
-      for (int nl = 0; nl < nactp; ++nl) {
-        const int n = nth_bit(an, nl);
+    for (int ml = 0; ml < nrot; ++ml)
+      for (int nl = 0; nl < nrotp; ++nl) {
+        const int n = nth_bit(rn, nl);
         float Wr[NBRM], Wi[NBRM];
         for (int a = 0; a < nbr; ++a) Wr[a] = Wi[a] = 0.f;
         for (int np_ = 0; np_ < nb; ++np_) {
@@ -572,7 +598,7 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
             gr = fmaf(Wr[a], ur, fmaf(-Wi[a], ui, gr));
             gi = fmaf(Wr[a], ui, fmaf(Wi[a], ur, gi));
           }
-          g2[(ml * nactp + nl) * nbr + s] = make_float2(gr * gr + gi * gi, 0.f);
+          g2[(ml * nrotp + nl) * nbr + s] = make_float2(gr * gr + gi * gi, 0.f);
         }
       }
   } else {
@@ -581,9 +607,9 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
     // |g|^2 goes to FP64 once per (m, n, s)
     const float4 *cf = cff + size_t(kp) * nb * nb;
     const float4 *uf = uff + size_t(q) * nbr * nbr;
-    for (int ml = 0; ml < nact; ++ml)
-      for (int nl = 0; nl < nactp; ++nl) {
-        const int n = nth_bit(an, nl);
+    for (int ml = 0; ml < nrot; ++ml)
+      for (int nl = 0; nl < nrotp; ++nl) {
+        const int n = nth_bit(rn, nl);
         FFAcc Wr[NBRM], Wi[NBRM];
         for (int np_ = 0; np_ < nb; ++np_) {
           const float4 c4 = cf[np_ * nb + n];
@@ -616,7 +642,7 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
           FFAcc m2;
           ff_acc_mul(m2, Gr, Gr);
           ff_acc_mul(m2, Gi, Gi);
-          g2[(ml * nactp + nl) * nbr + s] = ff_norm(m2);
+          g2[(ml * nrotp + nl) * nbr + s] = ff_norm(m2);
         }
       }
   }
@@ -642,16 +668,15 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
     flg[t] = uint8_t(f);
     const double dxp = ekp[n] - ek[m] - wq[s];
     const double dxm = ekp[n] - ek[m] + wq[s];
+    // average over the whole degenerate subspaces (every member is a rotation band)
     double sum = 0.0;
     int cnt = 0;
     for (int a = gk[2 * m]; a < gk[2 * m + 1]; ++a) {
-      if (!((am >> a) & 1u)) continue;
-      const int al = __popc(am & ((1u << a) - 1u));
+      const int al = __popc(rm & ((1u << a) - 1u));
       for (int b = gkp[2 * n]; b < gkp[2 * n + 1]; ++b) {
-        if (!((an >> b) & 1u)) continue;
-        const int bl = __popc(an & ((1u << b) - 1u));
+        const int bl = __popc(rn & ((1u << b) - 1u));
         for (int c = gq[2 * s]; c < gq[2 * s + 1]; ++c) {
-          const float2 v = g2[(al * nactp + bl) * nbr + c];
+          const float2 v = g2[(al * nrotp + bl) * nbr + c];
           sum += (double(v.x) + double(v.y)) * wrq[c];
           ++cnt;
         }
@@ -737,9 +762,17 @@ cudaError_t launch_vertex_epilogue(const ModelDev &M, const MeshDev &D, RatePara
     rp.rot_fp32 ? go(k_rate_epilogue<1, 3, true>) : go(k_rate_epilogue<1, 3, false>);
   else if (M.nb <= 4 && M.nbr <= 6)
     rp.rot_fp32 ? go(k_rate_epilogue<4, 6, true>) : go(k_rate_epilogue<4, 6, false>);
+  else if (M.nbr <= 6)
+    rp.rot_fp32 ? go(k_rate_epilogue<kMaxBands, 6, true>) : go(k_rate_epilogue<kMaxBands, 6, false>);
   else
     rp.rot_fp32 ? go(k_rate_epilogue<kMaxBands, kMaxBranches, true>)
                 : go(k_rate_epilogue<kMaxBands, kMaxBranches, false>);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_selftest_exp_ff(const double *y, double *out, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  EPHB_LAUNCH(k_selftest_exp_ff, unsigned((n + 255) / 256), 256, 0, st, y, out, n);
   return cudaGetLastError();
 }
 

@@ -18,7 +18,13 @@
 // and (i+l >= 6), which rounds at 2^-24 of a sum below 2^-30 of the column scale.  (With
 // the fourth diagonal in the tail, its rounding, ~2^-42 of the column scale, reached 1.2e-10
 // relative on the smallest rates; with the third there too, 1e-8.)  Mixed mode: 3 slices, the
-// 6 products with i + l <= 4, accumulators (i+l = 2) (exact) and (i+l >= 3).
+// 6 products with i + l <= 4, accumulators (i+l = 2) (exact) and (i+l >= 3); for contraction
+// lengths above 256, 4 slices and the 10 products with i + l <= 5 in the same two accumulators.
+// Wide-K FP64-grade mode (contraction lengths 256 < K <= 816, e.g. 7^3 R grids): 8 slices of
+// balanced base-128 digits (|n_i| <= 64, s_i = n_i 2^(-6-7(i-1)), the same 2^-55 input
+// resolution), the 36 products with i + l <= 9, accumulators (i+l = 2) .. (6) -- a diagonal of
+// d - 1 products of magnitude <= 2^12 units stays below 2^24 units for (d - 1) K <= 4096,
+// i.e. K <= 819 for the fifth -- and (i+l >= 7).
 //
 // The GEMM runs on 5th-generation tensor cores: operands in shared memory in the
 // no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix), accumulators in
@@ -43,19 +49,29 @@ constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s bound on any wait
 
 __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-// Split x in [-1,1] into ns exact BF16 fixed-point slices.  x is rounded once to the 64-bit
-// integer N = rint(x 2^(7+8(ns-1))); N is cut into balanced base-256 digits from the bottom
-// (each in [-128, 127], the top one within [-128, 128]) and digit i becomes the BF16 number
-// n_i 2^(-7-8(i-1)), which is exact.  Two FP64 operations per element; the rest is integer.
-__device__ inline void fixed_slices(double x, int ns, __nv_bfloat16 *out, size_t stride) {
-  const int top = 7 + 8 * (ns - 1);
-  long long N = __double2ll_rn(ldexp(x, top));
+// Digit width of the slicing: 8 bits (base 256) for 3 and 7 slices, 7 bits (base 128) for the
+// 8-slice wide-K form.  Slice i (0-based) of a value is n_i 2^-(B-1+B i), |n_i| <= 2^(B-1).
+__host__ __device__ constexpr int digit_bits(int ns) { return ns == 8 ? 7 : 8; }
+__host__ __device__ constexpr int slice_top(int ns) { return (digit_bits(ns) - 1) + digit_bits(ns) * (ns - 1); }
+
+// the ns slices of the integer N = rint(x 2^slice_top): balanced base-2^B digits cut from the
+// bottom (each in [-2^(B-1), 2^(B-1) - 1], the top one within [-2^(B-1), 2^(B-1)]); digit i
+// becomes the BF16 number n_i 2^(-(B-1)-B i), which is exact
+__device__ inline void int_slices(long long N, int ns, __nv_bfloat16 *out, size_t stride) {
+  const int B = digit_bits(ns);
+  const long long half = 1ll << (B - 1), mask = (1ll << B) - 1;
   for (int i = ns - 1; i >= 1; --i) {
-    const long long d = ((N + 128) & 255) - 128;   // balanced digit, N - d divisible by 256
-    N = (N - d) >> 8;
-    out[i * stride] = __float2bfloat16_rn(ldexpf(float(d), -7 - 8 * i));
+    const long long d = ((N + half) & mask) - half;   // balanced digit, N - d divisible by 2^B
+    N = (N - d) >> B;
+    out[i * stride] = __float2bfloat16_rn(ldexpf(float(d), -(B - 1) - B * i));
   }
-  out[0] = __float2bfloat16_rn(ldexpf(float(N), -7));
+  out[0] = __float2bfloat16_rn(ldexpf(float(N), -(B - 1)));
+}
+
+// Split x in [-1,1] into ns exact BF16 fixed-point slices: x is rounded once to the 64-bit
+// integer N = rint(x 2^slice_top(ns)) (2^55 in every FP64-grade form); the rest is integer.
+__device__ inline void fixed_slices(double x, int ns, __nv_bfloat16 *out, size_t stride) {
+  int_slices(__double2ll_rn(ldexp(x, slice_top(ns))), ns, out, stride);
 }
 
 // rint(x 2^p) (ties to even) from the bits of x, by integer operations only; the same value
@@ -80,16 +96,6 @@ __device__ inline long long fixed_round(double x, int p) {
   return (b >> 63) ? -(long long)n : (long long)n;
 }
 
-// the ns slices of the integer N (as fixed_slices does after its rounding)
-__device__ inline void int_slices(long long N, int ns, __nv_bfloat16 *out, size_t stride) {
-  for (int i = ns - 1; i >= 1; --i) {
-    const long long d = ((N + 128) & 255) - 128;
-    N = (N - d) >> 8;
-    out[i * stride] = __float2bfloat16_rn(ldexpf(float(d), -7 - 8 * i));
-  }
-  out[0] = __float2bfloat16_rn(ldexpf(float(N), -7));
-}
-
 // Phase slices of every q of the phonon mesh: PhiS[q][slice][Kp] (BF16)
 __global__ void k_phase_slices(ModelDev M, MeshDev D, int ns, int Kp, __nv_bfloat16 *phis) {
   const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
@@ -109,70 +115,100 @@ __global__ void k_phase_slices(ModelDev M, MeshDev D, int ns, int Kp, __nv_bfloa
 }
 
 // B' slices of the k points of a chunk: BS[kc][slice][Nmax][Kp] (BF16) and column scales.
-// Column j' = ml*(2 nb nbr) + part*(nb nbr) + n'*nbr + a.  One block per (k, ml): the stage-A
-// rows of that initial band (R x nb nbr complex values) are read once, coalesced, into shared
-// memory; each of its 2 nb nbr columns gets the power of two sigma >= its largest magnitude;
-// the slices are written with consecutive threads on consecutive r.  Integer arithmetic only
-// (the scale, the rounding to 2^-55 of sigma and the digits): no FP64 operation.  Block
-// y = nb writes the zero padding columns past 2 nb nb nbr.
+// Column j' = ml*(2 nb nbr) + part*(nb nbr) + n'*nbr + a.  One block per (k, ml, column group):
+// the stage-A rows of that initial band for the group's (n', a) range (R x h complex values,
+// both parts) are read once, coalesced, into shared memory; each column gets the power of two
+// sigma >= its largest magnitude; the slices are written with consecutive threads on
+// consecutive r.  Integer arithmetic only (the scale, the rounding to 2^-55 of sigma and the
+// digits): no FP64 operation.  Blocks y = nb (group 0) write the zero padding columns past
+// 2 nb nb nbr.
 __global__ void __launch_bounds__(256) k_b_slices(ModelDev M, MeshDev D, int64_t i0, const double2 *A, int ns,
-                                                  int Kp, int Nmax, __nv_bfloat16 *bs, double *bscale) {
-  extern __shared__ double2 tileA[];            // [R][nb nbr]
-  __shared__ int sh_ex[2 * kMaxBands * kMaxBranches];   // exponent of sigma per column (-2000: zero column)
+                                                  int Kp, int Nmax, int ngrp, __nv_bfloat16 *bs, double *bscale) {
+  extern __shared__ double2 tileA[];            // [R][h]
+  __shared__ int sh_ex[2 * kMaxBands * kMaxBranches];   // exponent of sigma per local column (-2000: zero column)
   const int64_t kc = blockIdx.x;
-  const int ml = blockIdx.y;
+  const int ml = blockIdx.y, grp = blockIdx.z;
   const int nb = M.nb, nbr = M.nbr, R = M.nRgp;
   const int nbnbr = nb * nbr, jmax = nb * nb * nbr;
-  const int k = D.ibzw_list[i0 + kc];
-  const bool live = ml < nb && ml < __popc(D.amask[k]);
-  const int c0 = ml < nb ? ml * 2 * nbnbr : 2 * nb * nbnbr;    // first column of the block
-  const int ncol = ml < nb ? 2 * nbnbr : Nmax - 2 * nb * nbnbr;
+  const int h = (nbnbr + ngrp - 1) / ngrp;                     // (n', a) values per group
+  const int r0 = grp * h;
+  const int hg = nbnbr - r0 < h ? nbnbr - r0 : h;              // this group's share
   const size_t sstride = size_t(Nmax) * Kp;
-  __nv_bfloat16 *dst = bs + (size_t(kc) * ns * Nmax + c0) * Kp;
-  if (!live) {   // zero slices, scale 1
+  __nv_bfloat16 *dstk = bs + size_t(kc) * ns * Nmax * Kp;
+  if (ml >= nb) {   // zero padding columns, scale 1 (group 0 only)
+    if (grp != 0) return;
+    const int c0 = 2 * nb * nbnbr, ncol = Nmax - c0;
     for (int t = threadIdx.x; t < ncol * Kp; t += blockDim.x) {
       const int c = t / Kp, r = t - c * Kp;
-      for (int sl = 0; sl < ns; ++sl) dst[sl * sstride + size_t(c) * Kp + r] = __float2bfloat16_rn(0.f);
+      for (int sl = 0; sl < ns; ++sl) dstk[sl * sstride + size_t(c0 + c) * Kp + r] = __float2bfloat16_rn(0.f);
     }
     for (int c = threadIdx.x; c < ncol; c += blockDim.x) bscale[kc * Nmax + c0 + c] = 1.0;
     return;
   }
-  const double2 *Ak = A + size_t(kc) * R * jmax + size_t(ml) * nbnbr;
-  for (int t = threadIdx.x; t < R * nbnbr; t += blockDim.x) {
-    const int r = t / nbnbr, j = t - r * nbnbr;
+  if (hg <= 0) return;
+  const int k = D.ibzw_list[i0 + kc];
+  const bool live = ml < __popc(D.rmask[k]);
+  const int ncol = 2 * hg;
+  // local column lc: part = lc / hg, (n', a) index rest = r0 + lc % hg; global column c0 + gcol(lc)
+  const int c0 = ml * 2 * nbnbr;
+  auto gcol = [&](int lc) { return lc < hg ? r0 + lc : nbnbr + r0 + (lc - hg); };
+  if (!live) {   // zero slices, scale 1
+    for (int t = threadIdx.x; t < ncol * Kp; t += blockDim.x) {
+      const int lc = t / Kp, r = t - lc * Kp;
+      for (int sl = 0; sl < ns; ++sl)
+        dstk[sl * sstride + size_t(c0 + gcol(lc)) * Kp + r] = __float2bfloat16_rn(0.f);
+    }
+    for (int lc = threadIdx.x; lc < ncol; lc += blockDim.x) bscale[kc * Nmax + c0 + gcol(lc)] = 1.0;
+    return;
+  }
+  const double2 *Ak = A + size_t(kc) * R * jmax + size_t(ml) * nbnbr + r0;
+  for (int t = threadIdx.x; t < R * hg; t += blockDim.x) {
+    const int r = t / hg, j = t - r * hg;
     tileA[t] = Ak[size_t(r) * jmax + j];
   }
   __syncthreads();
-  // column c = part * nbnbr + rest; row r < R: (Re, Im)[part] of A[r]; r >= R: (-Im, Re)[part]
-  auto value_bits = [&](int c, int r) -> unsigned long long {
-    const int part = c >= nbnbr, rest = c - part * nbnbr;
-    const double2 a = tileA[(r < R ? r : r - R) * nbnbr + rest];
+  // local column lc; row r < R: (Re, Im)[part] of A[r]; r >= R: (-Im, Re)[part]
+  auto value_bits = [&](int lc, int r) -> unsigned long long {
+    const int part = lc >= hg, rest = lc - part * hg;
+    const double2 a = tileA[(r < R ? r : r - R) * hg + rest];
     const double v = r < R ? (part == 0 ? a.x : a.y) : (part == 0 ? -a.y : a.x);
     return (unsigned long long)__double_as_longlong(v);
   };
-  for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+  for (int lc = threadIdx.x; lc < ncol; lc += blockDim.x) {
     unsigned long long mx = 0;   // largest |v| as bits (the order of non-negative doubles)
     for (int r = 0; r < 2 * R; ++r) {
-      const unsigned long long ab = value_bits(c, r) & 0x7fffffffffffffffull;
+      const unsigned long long ab = value_bits(lc, r) & 0x7fffffffffffffffull;
       mx = ab > mx ? ab : mx;
     }
     const int e = int(mx >> 52);
     // sigma = 2^ex with ex = e - 1022 (2^ex >= mx, as frexp gives); a zero (or subnormal) column: 1
     const int ex = e == 0 ? 0 : e - 1022;
-    sh_ex[c] = e == 0 ? -2000 : ex;
-    bscale[kc * Nmax + c0 + c] = __longlong_as_double((long long)(ex + 1023) << 52);
+    sh_ex[lc] = e == 0 ? -2000 : ex;
+    bscale[kc * Nmax + c0 + gcol(lc)] = __longlong_as_double((long long)(ex + 1023) << 52);
   }
   __syncthreads();
-  const int top = 7 + 8 * (ns - 1);
+  const int top = slice_top(ns);
   for (int t = threadIdx.x; t < ncol * Kp; t += blockDim.x) {
-    const int c = t / Kp, r = t - c * Kp;
+    const int lc = t / Kp, r = t - lc * Kp;
     long long N = 0;
-    if (r < 2 * R && sh_ex[c] != -2000) N = fixed_round(__longlong_as_double(value_bits(c, r)), top - sh_ex[c]);
-    int_slices(N, ns, dst + size_t(c) * Kp + r, sstride);
+    if (r < 2 * R && sh_ex[lc] != -2000) N = fixed_round(__longlong_as_double(value_bits(lc, r)), top - sh_ex[lc]);
+    int_slices(N, ns, dstk + size_t(c0 + gcol(lc)) * Kp + r, sstride);
   }
 }
 
-size_t b_slices_smem(const ModelDev &M) { return size_t(M.nRgp) * M.nb * M.nbr * sizeof(double2); }
+// column groups of k_b_slices: the fewest whose shared-memory tile stays within 96 KB
+static int b_slices_groups(const ModelDev &M) {
+  const int nbnbr = M.nb * M.nbr;
+  for (int g = 1; g < nbnbr; ++g) {
+    const int h = (nbnbr + g - 1) / g;
+    if (size_t(M.nRgp) * h * sizeof(double2) <= 96 * 1024) return g;
+  }
+  return nbnbr;
+}
+static size_t b_slices_smem(const ModelDev &M) {
+  const int g = b_slices_groups(M), nbnbr = M.nb * M.nbr;
+  return size_t(M.nRgp) * ((nbnbr + g - 1) / g) * sizeof(double2);
+}
 
 // Phase slices of the k points of a chunk (stage A rows): PhiK[kc][slice][Kp] with the
 // (cos, sin) of 2 pi k.Re for r < nRe and nRe <= r < 2 nRe.
@@ -236,7 +272,7 @@ __global__ void k_tc_items(ModelDev M, MeshDev D, int64_t i0, int64_t nkc, int n
   if (kc >= nkc) return;
   const int64_t i = i0 + kc;
   const int64_t npl = D.pair_ptr[i + 1] - D.pair_ptr[i];
-  const int nk = round_up(2 * __popc(D.amask[D.ibzw_list[i]]) * M.nb * M.nbr, 16);
+  const int nk = round_up(2 * __popc(D.rmask[D.ibzw_list[i]]) * M.nb * M.nbr, 16);
   const int nch = (nk + nc_max - 1) / nc_max;
   const int ntile = int((npl + kTcM - 1) / kTcM);
   nitem[kc] = ntile * nch;
@@ -379,7 +415,7 @@ __global__ void __launch_bounds__(kTcThreads, (KC == 16 && ST == 2) ? 2 : 1) k_v
     const int64_t kc = lo;
     const int64_t i = P.i0 + kc;
     const int k = D.ibzw_list[i];
-    const int nk = round_up(2 * __popc(D.amask[k]) * M.nb * M.nbr, 16);
+    const int nk = round_up(2 * __popc(D.rmask[k]) * M.nb * M.nbr, 16);
     const int nch = (nk + P.nc_max - 1) / P.nc_max;
     nc = round_up((nk + nch - 1) / nch, 16);                   // balanced chunk width
     const int64_t local = item - item_ptr[kc];
@@ -523,9 +559,9 @@ __global__ void __launch_bounds__(kTcThreads, (KC == 16 && ST == 2) ? 2 : 1) k_v
     // accumulators -> FP64 combination -> C'[row][n0 + j]
     const int row = warp * 32 + lane;
     const int nlive = ROWS == kRowsPairs ? ncw : (P.ncols - n0 < ncw ? P.ncols - n0 : ncw);
-    // Exact accumulators (diagonals d = 0..NACC-2) hold integer multiples of 2^(-14-8d) below
-    // 2^24 of that unit; the tail is rounded to 2^-48.  All of them go into one 64-bit integer
-    // in units of 2^-48 (at most 2^57), converted to FP64 once.
+    // Exact accumulators (diagonals d = 0..NACC-2) hold integer multiples of 2^-(2(B-1)+Bd)
+    // below 2^24 of that unit; the tail is rounded to 2^-48.  All of them go into one 64-bit
+    // integer in units of 2^-48 (at most 2^60), converted to FP64 once.
     if (ROWS == kRowsPairs) {   // C' as float-float pairs
       float2 *frow = reinterpret_cast<float2 *>(Cbuf) + (crow - Cbuf);
       for (int c0 = 0; c0 < ncw; c0 += 16) {
@@ -547,9 +583,11 @@ __global__ void __launch_bounds__(kTcThreads, (KC == 16 && ST == 2) ? 2 : 1) k_v
             : "r"(ta));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (a < NACC - 1) {
-          const float up = __int_as_float((127 + 14 + 8 * a) << 23);   // 2^(14+8a)
+          // diagonal a: integer multiples of 2^-(2(B-1) + B a), B the digit width
+          constexpr int B = digit_bits(NS);
+          const float up = __int_as_float((127 + 2 * (B - 1) + B * a) << 23);
           for (int j = 0; j < 16; ++j)
-            sum[j] += (long long)__float2int_rn(__uint_as_float(v[j]) * up) << (34 - 8 * a);
+            sum[j] += (long long)__float2int_rn(__uint_as_float(v[j]) * up) << (48 - 2 * (B - 1) - B * a);
         } else {
           for (int j = 0; j < 16; ++j) sum[j] += __float2ll_rn(ldexpf(__uint_as_float(v[j]), 48));
         }
@@ -604,7 +642,7 @@ __global__ void k_ws_items(ModelDev M, MeshDev D, TcParams P, const int64_t *ite
   if (kc >= P.nkc) return;
   const int64_t i = P.i0 + kc;
   const int k = D.ibzw_list[i];
-  const int nk = round_up(2 * __popc(D.amask[k]) * M.nb * M.nbr, 16);
+  const int nk = round_up(2 * __popc(D.rmask[k]) * M.nb * M.nbr, 16);
   const int nch = (nk + P.nc_max - 1) / P.nc_max;
   const int nc = round_up((nk + nch - 1) / nch, 16);
   const int64_t p0 = D.pair_ptr[i];
@@ -846,8 +884,14 @@ int tc_nmax(const ModelDev &M) { return round_up(2 * M.nb * M.nb * M.nbr, 16); }
 // Tile shapes a launch may use.  Every accumulator of a chunk must fit the CTA's tensor memory
 // (NACC x width columns: all 512 with one CTA per SM, 256 with two) and the operand stages its
 // shared memory.  Two CTAs per SM: K blocks of 16 in two stages.
-int tc_nc_max(int ns) { return ns == 7 ? 96 : 256; }
-static int nacc_of(int ns) { return ns == 7 ? 5 : 2; }
+int tc_nc_max(int ns) { return ns == 8 ? 64 : (ns == 7 ? 96 : 256); }
+static int nacc_of(int ns) { return ns == 8 ? 6 : (ns == 7 ? 5 : 2); }
+// Mixed mode: 3 slices (24-bit inputs) up to K = 256; longer contractions sum more rounded
+// terms and take a fourth slice (32-bit inputs, 10 products, the same two accumulators).
+int tc_slices_for(int kp, bool fp64_grade) {
+  if (!fp64_grade) return kp <= 256 ? 3 : (kp <= 1024 ? 4 : 0);
+  return kp <= 256 ? 7 : (kp <= 816 ? 8 : 0);
+}
 static bool two_ctas(int kc, int st) { return kc == 16 && st == 2; }
 static bool warp_specialised(int kc, int st) { return kc == 16 && st == 5; }
 size_t tc_smem_bytes(int ns, int ncm, int kc, int st) {
@@ -866,6 +910,7 @@ bool tc_nc_valid(int ns, int ncm, int kc, int st) {
   return !two_ctas(kc, st) || nacc_of(ns) * ncm <= 256;
 }
 std::vector<TcShape> tc_shape_candidates(int ns) {
+  if (ns == 8) return {{48, 32, 2}, {64, 32, 2}, {32, 16, 2}, {64, 16, 4}, {32, 16, 5}};
   if (ns == 7) return {{48, 32, 2}, {64, 32, 2}, {96, 32, 2}, {48, 16, 2}, {96, 16, 4}, {48, 16, 5}};
   return {{64, 32, 2}, {128, 32, 2}, {256, 32, 2}, {128, 16, 2}, {256, 16, 4}, {64, 16, 5}, {128, 16, 5}};
 }
@@ -892,7 +937,7 @@ cudaError_t launch_stage_a_tc(const ModelDev &M, const MeshDev &D, int ns, int64
   if (e != cudaSuccess) return e;
   TcParams P;
   P.ns = ns;
-  P.nacc = ns == 7 ? 5 : 2;
+  P.nacc = nacc_of(ns);
   P.Kp = Kp;
   P.Nmax = Ncols;
   P.nc_max = ncm;
@@ -907,7 +952,12 @@ cudaError_t launch_stage_a_tc(const ModelDev &M, const MeshDev &D, int ns, int64
   const int64_t nitems = ntile * nch;
   const size_t smem = tc_smem_bytes(ns, ncm, 32, 2);
   double *out = reinterpret_cast<double *>(T);
-  if (ns == 7) {
+  if (ns == 8) {
+    e = cudaFuncSetAttribute(k_vertex_gemm<8, 6, kRowsK, 32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    EPHB_LAUNCH((k_vertex_gemm<8, 6, kRowsK, 32, 2>), unsigned(nitems), kTcThreads, smem, st, M, D, P, nullptr, phik, gs,
+                gscale, out, err);
+  } else if (ns == 7) {
     e = cudaFuncSetAttribute(k_vertex_gemm<7, 5, kRowsK, 32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     EPHB_LAUNCH((k_vertex_gemm<7, 5, kRowsK, 32, 2>), unsigned(nitems), kTcThreads, smem, st, M, D, P, nullptr, phik, gs,
@@ -944,8 +994,9 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
     const size_t smem = b_slices_smem(M);
     cudaError_t r = cudaFuncSetAttribute(k_b_slices, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (r != cudaSuccess) return r;
-    EPHB_LAUNCH(k_b_slices, dim3(unsigned(nkc), unsigned(M.nb + 1)), 256, smem, st, M, D, i0, A, ns, Kp, Nmax, bs,
-                bscale);
+    const int ngrp = b_slices_groups(M);
+    EPHB_LAUNCH(k_b_slices, dim3(unsigned(nkc), unsigned(M.nb + 1), unsigned(ngrp)), 256, smem, st, M, D, i0, A, ns,
+                Kp, Nmax, ngrp, bs, bscale);
   }
   const int nprod = ns * (ns + 1) / 2;
   EPHB_LAUNCH(k_tc_items, unsigned((nkc + 255) / 256), 256, 0, st, M, D, i0, nkc, ncm, Kp, nprod, nitem,
@@ -958,7 +1009,7 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
   if (e != cudaSuccess || nitems == 0) return e;
   TcParams P;
   P.ns = ns;
-  P.nacc = ns == 7 ? 5 : 2;
+  P.nacc = nacc_of(ns);
   P.Kp = Kp;
   P.Nmax = Nmax;
   P.nc_max = ncm;
@@ -995,7 +1046,15 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
     return cudaGetLastError();
   };
   if (warp_specialised(kc, stages))
-    e = ns == 7 ? go_ws(k_vertex_gemm_ws<7, 5, 5>) : go_ws(k_vertex_gemm_ws<3, 2, 5>);
+    e = ns == 8 ? go_ws(k_vertex_gemm_ws<8, 6, 5>)
+                : (ns == 7 ? go_ws(k_vertex_gemm_ws<7, 5, 5>)
+                           : (ns == 4 ? go_ws(k_vertex_gemm_ws<4, 2, 5>) : go_ws(k_vertex_gemm_ws<3, 2, 5>)));
+  else if (ns == 4)
+    e = kc == 32 ? go(k_vertex_gemm<4, 2, kRowsPairs, 32, 2>)
+                 : (stages == 4 ? go(k_vertex_gemm<4, 2, kRowsPairs, 16, 4>) : go(k_vertex_gemm<4, 2, kRowsPairs, 16, 2>));
+  else if (ns == 8)
+    e = kc == 32 ? go(k_vertex_gemm<8, 6, kRowsPairs, 32, 2>)
+                 : (stages == 4 ? go(k_vertex_gemm<8, 6, kRowsPairs, 16, 4>) : go(k_vertex_gemm<8, 6, kRowsPairs, 16, 2>));
   else if (ns == 7)
     e = kc == 32 ? go(k_vertex_gemm<7, 5, kRowsPairs, 32, 2>)
                  : (stages == 4 ? go(k_vertex_gemm<7, 5, kRowsPairs, 16, 4>) : go(k_vertex_gemm<7, 5, kRowsPairs, 16, 2>));

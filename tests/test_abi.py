@@ -37,7 +37,8 @@ def test_library_exports_every_declared_symbol():
 def test_struct_layouts_match_header(tmp_path):
     structs = {"ephb_model": B.ModelC, "ephb_mesh_opts": B.MeshOptsC, "ephb_mesh_info": B.MeshInfoC,
                "ephb_thermo": B.ThermoC, "ephb_delta": B.DeltaC, "ephb_rates_info": B.RatesInfoC,
-               "ephb_solve_opts": B.SolveOptsC, "ephb_solve_info": B.SolveInfoC, "ephb_coeffs": B.CoeffsC}
+               "ephb_solve_opts": B.SolveOptsC, "ephb_solve_info": B.SolveInfoC, "ephb_coeffs": B.CoeffsC,
+               "ephb_coeff_inputs": B.CoeffInputsC}
     src = tmp_path / "sz.c"
     lines = ['#include <stdio.h>', '#include "ephb.h"', "int main(void){"]
     for n in structs:
@@ -54,7 +55,8 @@ def test_struct_layouts_match_header(tmp_path):
 def test_binding_constants_match_header():
     text = open(HEADER).read()
     for name, value in (("EPHB_MAX_ACCEL_DEPTH", B.MAX_ACCEL_DEPTH), ("EPHB_NFEAT", B.NFEAT),
-                        ("EPHB_TUNE_TC_COLS", B.TUNE_TC_COLS), ("EPHB_TUNE_WITHHOLD_MMA", B.TUNE_WITHHOLD_MMA)):
+                        ("EPHB_TUNE_TC_COLS", B.TUNE_TC_COLS), ("EPHB_TUNE_WITHHOLD_MMA", B.TUNE_WITHHOLD_MMA),
+                        ("EPHB_NOALLOC_MAX_ITEMS", B.NOALLOC_MAX_ITEMS)):
         m = re.search(r"#define\s+%s\s+(\d+)" % name, text)
         assert m and int(m.group(1)) == value, name
 

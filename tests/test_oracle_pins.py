@@ -684,3 +684,29 @@ def test_cscl8_irreducible_wedge_equals_full_zone():
             nb_ = np.linalg.norm(b.coeffs[key])
             if nb_ > 0:
                 assert np.linalg.norm(a.coeffs[key] - b.coeffs[key]) <= 1e-11 * nb_, key
+
+
+def test_cscl8_detailed_balance():
+    """Detailed balance of the 8-band 2-atom model (full zone, small coupling grid, window widened
+    to 0.9 eV above the CBM): X+(mk -> nk' | q) / X-(nk' -> mk | -q) = exp(beta (eps' - eps - hbar w))
+    for every pair of entries above 1e-6 of the largest rate (below that, couplings that the
+    symmetry makes vanish leave rounding-level rates whose ratio means nothing)."""
+    wl = S.workload_cscl8(8, 8, r_half=1, nsym_full=False, above_cbm_eV=0.9)
+    P = O.prepare(wl)
+    R = O.transition_rates(P)
+    key = {(a, b, c, d, e): i for i, (a, b, c, d, e) in enumerate(zip(R.ik, R.m, R.iq, R.n, R.s))}
+    beta = 1.0 / (O.KB_EVK * wl.T_K)
+    mq = O.minus_q(P, R.iq)
+    floor = 1e-6 * max(R.Xp.max(), R.Xm.max())
+    n = 0
+    for i in range(len(R.Xp)):
+        if R.Xp[i] <= floor:
+            continue
+        j = key.get((R.ikp[i], R.n[i], mq[i], R.m[i], R.s[i]))
+        assert j is not None
+        if R.Xm[j] <= floor:
+            continue
+        x = P.eps[R.ikp[i], R.n[i]] - P.eps[R.ik[i], R.m[i]] - P.w[R.iq[i], R.s[i]]
+        np.testing.assert_allclose(R.Xp[i] / R.Xm[j], np.exp(beta * x), rtol=1e-9)
+        n += 1
+    assert n > 500
