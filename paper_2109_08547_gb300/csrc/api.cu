@@ -3,6 +3,7 @@
 // enqueued as CUDA kernels on the context stream; the host only validates arguments,
 // sizes buffers and reads back scalars (counts, residuals) that steer the next launch.
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
@@ -154,6 +155,12 @@ struct ephb_ctx : InstState {
   DBuf<double> eps, vel, w, vph;
   DBuf<uint8_t> egrp, pgrp;
   DBuf<uint32_t> amask, rmask;
+  DBuf<int> qrep, qop, qstab, qflag, qlist, qrep_of;
+  DBuf<int64_t> qpos;
+  int64_t n_qrep = 0;
+  DBuf<double> Afold;                 // phonon fold at the q representatives [n_qrep][nbr][6]
+  DBuf<__nv_bfloat16> angle_tab;      // slices of cos, sin of the 2 pi j / n angles of a cubic q mesh
+  DBuf<int> atom_perm, atom_shift;
   DBuf<int> rep, op, stab, flag, ibzw_list, ibzw_of, npairs, pair_q, pair_i, qcount, pq_rank;
   DBuf<int64_t> pos, pair_ptr, qpair_ptr, scratch, scal;
 
@@ -256,6 +263,11 @@ MeshDev mesh_view(ephb_ctx *c) {
   D.egrp = c->egrp.p;
   D.amask = c->amask.p;
   D.rmask = c->rmask.p;
+  D.qrep = c->qrep.p;
+  D.qop = c->qop.p;
+  D.qrep_of = c->qrep_of.p;
+  D.qlist = c->qlist.p;
+  D.n_qrep = c->n_qrep;
   D.w = c->w.p;
   D.u = c->u.p;
   D.vph = c->vph.p;
@@ -352,6 +364,9 @@ void ephb_destroy(ephb_ctx *ctx) {
   ctx->sym_inv.release(); ctx->H_R.release(); ctx->D_R.release(); ctx->g_R.release(); ctx->sym_cart.release();
   ctx->ktab.release(); ctx->qtab.release(); ctx->cvec.release(); ctx->u.release(); ctx->eps.release();
   ctx->vel.release(); ctx->w.release(); ctx->vph.release(); ctx->egrp.release(); ctx->pgrp.release();
+  ctx->qrep.release(); ctx->qop.release(); ctx->qstab.release(); ctx->qflag.release(); ctx->qlist.release();
+  ctx->qrep_of.release(); ctx->qpos.release(); ctx->Afold.release(); ctx->atom_perm.release();
+  ctx->atom_shift.release(); ctx->angle_tab.release();
   ctx->amask.release(); ctx->rmask.release(); ctx->rep.release(); ctx->op.release(); ctx->stab.release(); ctx->flag.release();
   ctx->ibzw_list.release(); ctx->ibzw_of.release(); ctx->npairs.release(); ctx->pair_q.release();
   ctx->pair_i.release(); ctx->qcount.release(); ctx->pq_rank.release(); ctx->pos.release();
@@ -411,6 +426,49 @@ ephb_status ephb_set_wannier_model(ephb_ctx *ctx, const ephb_model *m) {
     }
     if (inv[s] < 0) return fail(ctx, EPHB_EINVAL, "symmetry operations are not closed under inversion");
   }
+  // atom map of every operation: S tau_a = tau_{p(a)} + L_a with L_a a lattice vector (crystal
+  // coordinates); the phonon eigenvectors at S q follow from those at q with it
+  std::vector<int> aperm(size_t(m->nsym) * m->nat), ashift(size_t(m->nsym) * m->nat * 3);
+  {
+    double A[3][3], Ai[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) A[i][j] = m->lattice[i][j];
+    const double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+                       A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                       A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    if (!(std::fabs(det) > 0)) return fail(ctx, EPHB_EINVAL, "singular lattice");
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        const int i1 = (j + 1) % 3, i2 = (j + 2) % 3, j1 = (i + 1) % 3, j2 = (i + 2) % 3;
+        Ai[i][j] = (A[i1][j1] * A[i2][j2] - A[i1][j2] * A[i2][j1]) / det;   // inverse: (A^-1)_ij
+      }
+    static const double zero[3] = {0, 0, 0};
+    for (int s = 0; s < m->nsym; ++s) {
+      const double *C = m->sym_cart + 9 * s;
+      for (int a = 0; a < m->nat; ++a) {
+        const double *ta = m->tau_cart ? m->tau_cart + 3 * a : zero;
+        double p[3];
+        for (int x = 0; x < 3; ++x) p[x] = C[3 * x] * ta[0] + C[3 * x + 1] * ta[1] + C[3 * x + 2] * ta[2];
+        int found = -1;
+        for (int b = 0; b < m->nat && found < 0; ++b) {
+          const double *tb = m->tau_cart ? m->tau_cart + 3 * b : zero;
+          double d[3] = {p[0] - tb[0], p[1] - tb[1], p[2] - tb[2]};
+          double c[3];
+          bool lattice_vec = true;
+          for (int j = 0; j < 3; ++j) {
+            c[j] = d[0] * Ai[0][j] + d[1] * Ai[1][j] + d[2] * Ai[2][j];
+            if (std::fabs(c[j] - std::round(c[j])) > 1e-6) lattice_vec = false;
+          }
+          if (lattice_vec) {
+            found = b;
+            for (int j = 0; j < 3; ++j) ashift[(size_t(s) * m->nat + a) * 3 + j] = int(std::lround(c[j]));
+          }
+        }
+        if (found < 0) return fail(ctx, EPHB_EINVAL, "a symmetry operation does not map the atoms onto each other");
+        aperm[size_t(s) * m->nat + a] = found;
+      }
+    }
+  }
   ModelDev &M = ctx->M;
   M = ModelDev();
   M.nat = m->nat;
@@ -446,6 +504,8 @@ ephb_status ephb_set_wannier_model(ephb_ctx *ctx, const ephb_model *m) {
   CK(upload(ctx->sym_rot, m->sym_rot, size_t(m->nsym) * 9, st));
   CK(upload(ctx->sym_cart, m->sym_cart, size_t(m->nsym) * 9, st));
   CK(upload(ctx->sym_inv, inv.data(), inv.size(), st));
+  CK(upload(ctx->atom_perm, aperm.data(), aperm.size(), st));
+  CK(upload(ctx->atom_shift, ashift.data(), ashift.size(), st));
   M.Re = ctx->Re.p;
   M.Rd = ctx->Rd.p;
   M.Rge = ctx->Rge.p;
@@ -456,6 +516,8 @@ ephb_status ephb_set_wannier_model(ephb_ctx *ctx, const ephb_model *m) {
   M.sym_rot = ctx->sym_rot.p;
   M.sym_cart = ctx->sym_cart.p;
   M.sym_inv = ctx->sym_inv.p;
+  M.atom_perm = ctx->atom_perm.p;
+  M.atom_shift = ctx->atom_shift.p;
   ctx->stage = 1;
   ctx->tune_cols[0] = ctx->tune_cols[1] = ctx->tune_cols[2] = 0;   // a new model shape is tuned again
   ctx->gslices_ns = 0;                          // and its g slices are made again
@@ -516,8 +578,24 @@ ephb_status ephb_build_meshes_ibz(ephb_ctx *ctx, const ephb_mesh_opts *o, ephb_m
   CK(ctx->scratch.ensure(scr));
   CK(launch_phase_tables(ctx->ktab.p, km, st));
   CK(launch_phase_tables(ctx->qtab.p, qm, st));
-  CK(launch_phonon_modes(M, qm, ctx->qtab.p, ctx->degen_tol, ctx->omega_min, ctx->w.p, ctx->u.p, ctx->vph.p,
-                         ctx->pgrp.p, st));
+  // Phonons: eigen-decompositions on the representatives of the q wedge, the rest by rotation
+  CK(ctx->qrep.ensure(nq));
+  CK(ctx->qop.ensure(nq));
+  CK(ctx->qstab.ensure(nq));
+  CK(ctx->qflag.ensure(nq));
+  CK(ctx->qpos.ensure(nq));
+  CK(ctx->qlist.ensure(nq));
+  CK(ctx->qrep_of.ensure(nq));
+  CK(launch_ibz(M, qm, ctx->qrep.p, ctx->qop.p, ctx->qstab.p, ctx->qflag.p, st));
+  CK(exclusive_scan<int>(ctx->qflag.p, ctx->qpos.p, nq, ctx->scal.p + 0, ctx->scratch.p, ctx->scratch.n, st));
+  CK(launch_compact(nq, ctx->qflag.p, ctx->qpos.p, ctx->qlist.p, st));
+  CK(cudaMemcpyAsync(&ctx->n_qrep, ctx->scal.p + 0, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  CK(launch_rep_index(nq, ctx->qlist.p, ctx->n_qrep, ctx->qrep_of.p, st));
+  CK(launch_phonon_modes(M, qm, ctx->qlist.p, ctx->n_qrep, ctx->qtab.p, ctx->degen_tol, ctx->omega_min, ctx->w.p,
+                         ctx->u.p, ctx->vph.p, ctx->pgrp.p, st));
+  CK(launch_phonons_from_rep(M, qm, ctx->qtab.p, ctx->qrep.p, ctx->qop.p, ctx->w.p, ctx->u.p, ctx->vph.p,
+                             ctx->pgrp.p, st));
   // Electron bands: eigen-decompositions on the representatives of the wedge first; a point whose
   // representative has no band in the window takes the representative's energies and rotated
   // velocities (it holds no active state and no rate reads its eigenvectors); every other point
@@ -803,7 +881,8 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     Nmax = tc_nmax(M);
     const int Kp = tc_kp(M);
     CK(ctx->phis.ensure(size_t(nq) * ns * Kp));
-    CK(launch_phase_slices(M, D, ns, ctx->phis.p, st));
+    CK(ctx->angle_tab.ensure(size_t(2) * 1024 * 8));
+    CK(launch_phase_slices(M, D, ns, ctx->phis.p, ctx->angle_tab.p, st));
     hpp.resize(ctx->n_ibzw + 1);
     CK(cudaMemcpyAsync(hpp.data(), ctx->pair_ptr.p, hpp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -990,6 +1069,7 @@ ephb_status bte_setup(ephb_ctx *ctx) {
   CK(ctx->inv_nnW.ensure(nph));
   for (auto *b : {&ctx->F0, &ctx->F, &ctx->G}) CK(b->ensure(nph * 3));
   CK(ctx->Btv.ensure(nph * 6));
+  CK(ctx->Afold.ensure(size_t(ctx->n_qrep > 0 ? ctx->n_qrep : 1) * M.nbr * 6));
   CK(ctx->epart.ensure(size_t(coeff_partials()) * 36));
   CK(ctx->ppart.ensure(size_t(coeff_partials()) * 18));
   CK(ctx->kpart.ensure(size_t(coeff_partials()) * 9));
@@ -1411,21 +1491,21 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
       CK(tp.start(st));
       if (ph32) {
         CK(launch_pack6_f32(nst, ctx->I.p, ctx->J.p, ctx->IJ32.p, st));
-        CK(launch_ph_sweep32(M, B, ctx->kinfo.p, ctx->Y32.p, ctx->IJ32.p, ctx->Btv.p, st));
+        CK(launch_ph_sweep32(M, B, ctx->kinfo.p, ctx->Y32.p, ctx->IJ32.p, ctx->Btv.p, ctx->n_ph_entries, st));
       } else if (ph32_allowed) {
         CK(launch_pack6_ff(nst, ctx->I.p, ctx->J.p, ctx->IJff.p, st));
-        CK(launch_ph_sweepff(M, B, ctx->kinfo.p, ctx->Yff.p, ctx->IJff.p, ctx->Btv.p, st));
+        CK(launch_ph_sweepff(M, B, ctx->kinfo.p, ctx->Yff.p, ctx->IJff.p, ctx->Btv.p, ctx->n_ph_entries, st));
       } else {
-        CK(launch_ph_sweep(M, D, B, ctx->kinfo.p, ctx->I.p, ctx->J.p, ctx->Btv.p, st));
+        CK(launch_ph_sweep(M, D, B, ctx->kinfo.p, ctx->I.p, ctx->J.p, ctx->Btv.p, ctx->n_ph_entries, st));
       }
       CK(tp.stop(st));
       if (and_m > 0 && outer >= 2) {   // the update goes to the ring, the mix to (F, G)
         double *g = ctx->and_g.p + size_t(and_head) * 2 * half;
-        CK(launch_ph_update(M, D, B, ctx->Btv.p, ctx->F0.p, ctx->inv_nnW.p, g, g + half, st));
+        CK(launch_ph_update(M, D, ctx->Btv.p, ctx->F0.p, ctx->inv_nnW.p, g, g + half, ctx->Afold.p, st));
         s = anderson_step();
         if (s != EPHB_OK) return s;
       } else {
-        CK(launch_ph_update(M, D, B, ctx->Btv.p, ctx->F0.p, ctx->inv_nnW.p, ctx->F.p, ctx->G.p, st));
+        CK(launch_ph_update(M, D, ctx->Btv.p, ctx->F0.p, ctx->inv_nnW.p, ctx->F.p, ctx->G.p, ctx->Afold.p, st));
       }
       if (ph32) CK(launch_pack6_f32(nph, ctx->F.p, ctx->G.p, ctx->FG32.p, st));
       else if (ph32_allowed) CK(launch_pack6_ff(nph, ctx->F.p, ctx->G.p, ctx->FGff.p, st));

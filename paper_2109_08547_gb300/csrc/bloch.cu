@@ -93,13 +93,16 @@ __global__ void __launch_bounds__(128) k_electron_bands(ModelDev M, Mesh km, con
   rmask[k] = rot;
 }
 
-// One thread per q point: D(q), eigen-decomposition, hbar w = sqrt(max(lambda,0)), velocities.
+// One thread per listed q point: D(q), eigen-decomposition, hbar w = sqrt(max(lambda,0)),
+// velocities.
 template <int NB>
-__global__ void __launch_bounds__(128) k_phonon_modes(ModelDev M, Mesh qm, const double2 *__restrict__ qtab,
+__global__ void __launch_bounds__(128) k_phonon_modes(ModelDev M, Mesh qm, const int *__restrict__ list, int64_t n,
+                                                      const double2 *__restrict__ qtab,
                                                       double degen_tol, double omega_min, double *w, double2 *u,
                                                       double *vph, uint8_t *pgrp) {
-  int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= qm.size()) return;
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= n) return;
+  const int q = list[t];
   const int nb = M.nbr;
   int i0, i1, i2;
   qm.unflat(q, i0, i1, i2);
@@ -158,6 +161,55 @@ __global__ void __launch_bounds__(128) k_phonon_modes(ModelDev M, Mesh qm, const
     pgrp[(size_t(q) * nb + s) * 2 + 1] = grp[2 * s + 1];
     for (int i = 0; i < nb; ++i) u[(size_t(q) * nb + i) * nb + s] = V[i * NB + s];
   }
+}
+
+// Phonons of every q that is not the representative of its star, from the representative's
+// (Eq. D_ss'(q) is covariant): with q = S <q> and the atom map S tau_a = tau_{p(a)} + L_a,
+// D(S q)_{p(a) p(b)} = e^{i q.(L_b - L_a)} S D(<q>)_{ab} S^T, so
+//   u_{p(a) x, s}(q) = e^{-i q.L_a} sum_y S_xy u_{a y, s}(<q>)
+// is an eigenvector set of D(q) (a gauge of the degenerate subspaces, which every |g|^2 average
+// leaves invariant); hbar w and the degenerate groups are the representative's and
+// v_s(q) = S v_s(<q>).
+__global__ void k_phonons_from_rep(ModelDev M, Mesh qm, const double2 *__restrict__ qtab, const int *qrep,
+                                   const int *qop, double *w, double2 *u, double *vph, uint8_t *pgrp) {
+  const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (q >= qm.size()) return;
+  const int r = qrep[q];
+  if (r == int(q)) return;
+  const int nbr = M.nbr, nat = M.nat, o = qop[q];
+  const double *S = M.sym_cart + 9 * o;
+  int b0, b1, b2;
+  qm.unflat(int(q), b0, b1, b2);
+  for (int s = 0; s < nbr; ++s) {
+    w[q * nbr + s] = w[size_t(r) * nbr + s];
+    pgrp[(q * nbr + s) * 2] = pgrp[(size_t(r) * nbr + s) * 2];
+    pgrp[(q * nbr + s) * 2 + 1] = pgrp[(size_t(r) * nbr + s) * 2 + 1];
+    const double *v = vph + (size_t(r) * nbr + s) * 3;
+    for (int x = 0; x < 3; ++x)
+      vph[(q * nbr + s) * 3 + x] = S[3 * x] * v[0] + S[3 * x + 1] * v[1] + S[3 * x + 2] * v[2];
+  }
+  for (int a = 0; a < nat; ++a) {
+    const int pa = M.atom_perm[o * nat + a];
+    const int *L = M.atom_shift + (o * nat + a) * 3;
+    const double2 ph = mesh_phase(qtab, qm, b0, b1, b2, L[0], L[1], L[2]);   // e^{i q.L_a}
+    const double2 phc = make_double2(ph.x, -ph.y);
+    for (int s = 0; s < nbr; ++s)
+      for (int x = 0; x < 3; ++x) {
+        double2 acc = cmk(0, 0);
+        for (int y = 0; y < 3; ++y) {
+          const double2 v = u[(size_t(r) * nbr + 3 * a + y) * nbr + s];
+          acc.x += S[3 * x + y] * v.x;
+          acc.y += S[3 * x + y] * v.y;
+        }
+        u[(q * nbr + 3 * pa + x) * nbr + s] = cmul(phc, acc);
+      }
+  }
+}
+
+// of[list[j]] = j
+__global__ void k_rep_index(int64_t nlist, const int *list, int *of) {
+  const int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (j < nlist) of[list[j]] = int(j);
 }
 
 // Irreducible wedge: representative = smallest image index, first op S with S<k> = k,
@@ -409,16 +461,31 @@ cudaError_t launch_compact(int64_t n, const int *flag, const int64_t *pos, int *
   return cudaGetLastError();
 }
 
-cudaError_t launch_phonon_modes(const ModelDev &M, Mesh qm, const double2 *qtab, double degen_tol, double omega_min,
-                                double *w, double2 *u, double *vph, uint8_t *pgrp, cudaStream_t st) {
-  int64_t n = qm.size();
+cudaError_t launch_phonon_modes(const ModelDev &M, Mesh qm, const int *list, int64_t n, const double2 *qtab,
+                                double degen_tol, double omega_min, double *w, double2 *u, double *vph, uint8_t *pgrp,
+                                cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
   int grid = int((n + 127) / 128);
   if (M.nbr <= 3)
-    EPHB_LAUNCH(k_phonon_modes<3>, grid, 128, 0, st, M, qm, qtab, degen_tol, omega_min, w, u, vph, pgrp);
+    EPHB_LAUNCH(k_phonon_modes<3>, grid, 128, 0, st, M, qm, list, n, qtab, degen_tol, omega_min, w, u, vph, pgrp);
   else if (M.nbr <= 6)
-    EPHB_LAUNCH(k_phonon_modes<6>, grid, 128, 0, st, M, qm, qtab, degen_tol, omega_min, w, u, vph, pgrp);
+    EPHB_LAUNCH(k_phonon_modes<6>, grid, 128, 0, st, M, qm, list, n, qtab, degen_tol, omega_min, w, u, vph, pgrp);
   else
-    EPHB_LAUNCH(k_phonon_modes<12>, grid, 128, 0, st, M, qm, qtab, degen_tol, omega_min, w, u, vph, pgrp);
+    EPHB_LAUNCH(k_phonon_modes<12>, grid, 128, 0, st, M, qm, list, n, qtab, degen_tol, omega_min, w, u, vph, pgrp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phonons_from_rep(const ModelDev &M, Mesh qm, const double2 *qtab, const int *qrep, const int *qop,
+                                    double *w, double2 *u, double *vph, uint8_t *pgrp, cudaStream_t st) {
+  const int64_t n = qm.size();
+  EPHB_LAUNCH(k_phonons_from_rep, int((n + 127) / 128), 128, 0, st, M, qm, qtab, qrep, qop, w, u, vph, pgrp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rep_index(int64_t n, const int *list, int64_t nlist, int *of, cudaStream_t st) {
+  (void)n;
+  if (nlist <= 0) return cudaSuccess;
+  EPHB_LAUNCH(k_rep_index, int((nlist + 255) / 256), 256, 0, st, nlist, list, of);
   return cudaGetLastError();
 }
 

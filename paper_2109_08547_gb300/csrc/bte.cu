@@ -420,7 +420,7 @@ __global__ void k_drag_finalize(int64_t nst, SweepSegs S, const double *part, do
 // One warp per phonon row (q,s): Btv = sum Y/|stab| (S_k' I_<k'>n - I_km), fields I and J.
 // Float-float form of the phonon drag scatter (mixed iteration once the outer residual is
 // small), from float-float copies of Y and of the responses (IJff: [state][I0 I1 I2 J0 J1 J2]).
-template <bool SYM>
+template <bool SYM, int LANES>
 __global__ void __launch_bounds__(256) k_ph_sweepff(ModelDev M, BteDev B, const int2 *__restrict__ kinfo,
                                                     const float2 *__restrict__ Yff,
                                                     const float2 *__restrict__ IJff, double *Btv) {
@@ -429,11 +429,11 @@ __global__ void __launch_bounds__(256) k_ph_sweepff(ModelDev M, BteDev B, const 
     for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) C[t] = ff_from_double(M.sym_cart[t]);
     __syncthreads();
   }
-  const int64_t row = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  const int64_t row = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) / LANES;
+  const int lane = LANES == 1 ? 0 : (threadIdx.x & 31);
   if (row >= B.nq * B.nbr) return;
   FFAcc a[6];
-  for (int64_t e = B.ph_row_ptr[row] + lane; e < B.ph_row_ptr[row + 1]; e += 32) {
+  for (int64_t e = B.ph_row_ptr[row] + lane; e < B.ph_row_ptr[row + 1]; e += LANES) {
     const int st = B.ph_st[e];
     const uint32_t pk = B.ph_kpn[e];
     const float2 y = Yff[e];
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(256) k_ph_sweepff(ModelDev M, BteDev B, const 
     for (int c = 0; c < 6; ++c) ff_acc_mul(a[c], y, ff_sub(r[c], own[c]));
   }
   for (int c = 0; c < 6; ++c) {
-    const double v = warp_sum(ff_to_double(a[c]));
+    const double v = LANES == 32 ? warp_sum(ff_to_double(a[c])) : ff_to_double(a[c]);
     if (lane == 0) Btv[row * 6 + c] = v;
   }
 }
@@ -481,7 +481,7 @@ __global__ void k_pack6_ff(int64_t n, const double *A, const double *Bv, float2 
 
 // FP32 form of the phonon drag scatter (mixed iteration while the outer residual is large),
 // from FP32 copies of Y and of the responses (IJ32: [state][I0 I1 I2 J0 J1 J2]).
-template <bool SYM>
+template <bool SYM, int LANES>
 __global__ void __launch_bounds__(256) k_ph_sweep32(ModelDev M, BteDev B, const int2 *__restrict__ kinfo,
                                                     const float *__restrict__ Y32, const float *__restrict__ IJ32,
                                                     double *Btv) {
@@ -490,11 +490,11 @@ __global__ void __launch_bounds__(256) k_ph_sweep32(ModelDev M, BteDev B, const 
     for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) C[t] = float(M.sym_cart[t]);
     __syncthreads();
   }
-  const int64_t row = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  const int64_t row = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) / LANES;
+  const int lane = LANES == 1 ? 0 : (threadIdx.x & 31);
   if (row >= B.nq * B.nbr) return;
   float a[6] = {0, 0, 0, 0, 0, 0};
-  for (int64_t e = B.ph_row_ptr[row] + lane; e < B.ph_row_ptr[row + 1]; e += 32) {
+  for (int64_t e = B.ph_row_ptr[row] + lane; e < B.ph_row_ptr[row + 1]; e += LANES) {
     const int st = B.ph_st[e];
     const uint32_t pk = B.ph_kpn[e];
     const float y = Y32[e];
@@ -514,8 +514,9 @@ __global__ void __launch_bounds__(256) k_ph_sweep32(ModelDev M, BteDev B, const 
     }
     for (int c = 0; c < 6; ++c) a[c] = fmaf(y, r[c] - own[c], a[c]);
   }
-  for (int c = 0; c < 6; ++c)
-    for (int o = 16; o > 0; o >>= 1) a[c] += __shfl_down_sync(0xffffffffu, a[c], o);
+  if (LANES == 32)
+    for (int c = 0; c < 6; ++c)
+      for (int o = 16; o > 0; o >>= 1) a[c] += __shfl_down_sync(0xffffffffu, a[c], o);
   if (lane == 0)
     for (int c = 0; c < 6; ++c) Btv[row * 6 + c] = double(a[c]);
 }
@@ -535,7 +536,9 @@ __global__ void k_copy_f32(int64_t n, const double *a, float *b) {
   if (i < n) b[i] = float(a[i]);
 }
 
-template <bool SYM>
+// LANES threads per phonon row: 32 (a warp) for long rows, 1 when rows hold a few entries (fine
+// meshes with symmetry leave most rows short or empty)
+template <bool SYM, int LANES>
 __global__ void __launch_bounds__(256) k_ph_sweep(ModelDev M, MeshDev D, BteDev B, const int2 *__restrict__ kinfo,
                                                   const double *__restrict__ I, const double *__restrict__ J,
                                                   double *Btv) {
@@ -544,11 +547,11 @@ __global__ void __launch_bounds__(256) k_ph_sweep(ModelDev M, MeshDev D, BteDev 
     for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) C[t] = M.sym_cart[t];
     __syncthreads();
   }
-  int64_t row = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
+  int64_t row = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) / LANES;
+  int lane = LANES == 1 ? 0 : (threadIdx.x & 31);
   if (row >= B.nq * B.nbr) return;
   double aI[3] = {0, 0, 0}, aJ[3] = {0, 0, 0};
-  for (int64_t e = B.ph_row_ptr[row] + lane; e < B.ph_row_ptr[row + 1]; e += 32) {
+  for (int64_t e = B.ph_row_ptr[row] + lane; e < B.ph_row_ptr[row + 1]; e += LANES) {
     int st = B.ph_st[e];
     uint32_t pk = B.ph_kpn[e];
     double y = B.ph_Y[e];
@@ -572,10 +575,11 @@ __global__ void __launch_bounds__(256) k_ph_sweep(ModelDev M, MeshDev D, BteDev 
     }
     for (int a = 0; a < 3; ++a) aJ[a] += y * (r[a] - J[int64_t(st) * 3 + a]);
   }
-  for (int a = 0; a < 3; ++a) {
-    aI[a] = warp_sum(aI[a]);
-    aJ[a] = warp_sum(aJ[a]);
-  }
+  if (LANES == 32)
+    for (int a = 0; a < 3; ++a) {
+      aI[a] = warp_sum(aI[a]);
+      aJ[a] = warp_sum(aJ[a]);
+    }
   if (lane == 0)
     for (int a = 0; a < 3; ++a) {
       Btv[row * 6 + a] = aI[a];
@@ -583,9 +587,11 @@ __global__ void __launch_bounds__(256) k_ph_sweep(ModelDev M, MeshDev D, BteDev 
     }
 }
 
-// F = F0 + d_s/(n(1+n)W) sum_S C_S Btv_I(S^-1 q); G = d_s/(n(1+n)W) sum_S C_S Btv_J(S^-1 q)   (Eq. dF^D)
-__global__ void k_ph_update(ModelDev M, MeshDev D, BteDev B, const double *Btv, const double *F0,
-                            const double *inv_nnW, double *F, double *G) {
+// The full-zone k sum of the phonon drag term from the irreducible rows (reading [A13]):
+// A(q) = sum_S C_S Btv(S^-1 q).  It is covariant, A(S q) = C_S A(q) (rearranging the group sum),
+// so the 48-term sum runs on the representatives of the q wedge only and every other q takes
+// its representative's A rotated by the operation that maps the representative onto it.
+__global__ void k_ph_fold_rep(ModelDev M, MeshDev D, const double *Btv, double *Afold) {
   __shared__ int rot[kMaxSym * 9];
   __shared__ int inv[kMaxSym];
   __shared__ double C[kMaxSym * 9];
@@ -595,23 +601,39 @@ __global__ void k_ph_update(ModelDev M, MeshDev D, BteDev B, const double *Btv, 
   }
   for (int t = threadIdx.x; t < M.nsym; t += blockDim.x) inv[t] = M.sym_inv[t];
   __syncthreads();
-  int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   const int nbr = M.nbr;
-  if (t >= D.nq * nbr) return;
-  int q = int(t / nbr), s = int(t % nbr);
-  double aI[3] = {0, 0, 0}, aJ[3] = {0, 0, 0};
+  if (t >= D.n_qrep * nbr) return;
+  const int j = int(t / nbr), s = int(t % nbr);
+  const int q = D.qlist[j];
+  double a[6] = {0, 0, 0, 0, 0, 0};
   for (int o = 0; o < M.nsym; ++o) {
-    int64_t src = int64_t(q_image(D.qm, rot + 9 * inv[o], q)) * nbr + s;
+    const int64_t src = int64_t(q_image(D.qm, rot + 9 * inv[o], q)) * nbr + s;
     double r[3];
     rot3(C + 9 * o, Btv + src * 6, r);
-    for (int a = 0; a < 3; ++a) aI[a] += r[a];
+    for (int x = 0; x < 3; ++x) a[x] += r[x];
     rot3(C + 9 * o, Btv + src * 6 + 3, r);
-    for (int a = 0; a < 3; ++a) aJ[a] += r[a];
+    for (int x = 0; x < 3; ++x) a[3 + x] += r[x];
   }
-  double c = M.spin_deg * inv_nnW[t];
-  for (int a = 0; a < 3; ++a) {
-    F[t * 3 + a] = F0[t * 3 + a] + c * aI[a];
-    G[t * 3 + a] = c * aJ[a];
+  for (int c = 0; c < 6; ++c) Afold[t * 6 + c] = a[c];
+}
+
+// F = F0 + d_s/(n(1+n)W) A_I(q); G = d_s/(n(1+n)W) A_J(q)   (Eq. dF^D), A(q) = C_S A(<q>)
+__global__ void k_ph_update(ModelDev M, MeshDev D, const double *Afold, const double *F0, const double *inv_nnW,
+                            double *F, double *G) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int nbr = M.nbr;
+  if (t >= D.nq * nbr) return;
+  const int q = int(t / nbr), s = int(t % nbr);
+  const double *A = Afold + (int64_t(D.qrep_of[D.qrep[q]]) * nbr + s) * 6;
+  const double *Cs = M.sym_cart + 9 * D.qop[q];
+  double aI[3], aJ[3];
+  rot3(Cs, A, aI);
+  rot3(Cs, A + 3, aJ);
+  const double c = M.spin_deg * inv_nnW[t];
+  for (int x = 0; x < 3; ++x) {
+    F[t * 3 + x] = F0[t * 3 + x] + c * aI[x];
+    G[t * 3 + x] = c * aJ[x];
   }
 }
 
@@ -1258,12 +1280,16 @@ cudaError_t launch_drag_termff(const MeshDev &D, const BteDev &B, const SweepSeg
 }
 
 cudaError_t launch_ph_sweepff(const ModelDev &M, const BteDev &B, const int2 *kinfo, const float2 *Yff,
-                              const float2 *IJff, double *Btv, cudaStream_t st) {
-  const unsigned g = unsigned((B.nq * B.nbr * 32 + 255) / 256);
+                              const float2 *IJff, double *Btv, int64_t n_ph_entries, cudaStream_t st) {
+  // rows of a few entries: one thread per row; longer rows: one warp
+  const bool wide = B.nq * B.nbr > 0 && n_ph_entries / (B.nq * B.nbr) >= 4;
+  const unsigned g = unsigned((B.nq * B.nbr * (wide ? 32 : 1) + 255) / 256);
   if (M.nsym > 1)
-    EPHB_LAUNCH(k_ph_sweepff<true>, g, 256, 0, st, M, B, kinfo, Yff, IJff, Btv);
+    wide ? EPHB_LAUNCH((k_ph_sweepff<true, 32>), g, 256, 0, st, M, B, kinfo, Yff, IJff, Btv)
+         : EPHB_LAUNCH((k_ph_sweepff<true, 1>), g, 256, 0, st, M, B, kinfo, Yff, IJff, Btv);
   else
-    EPHB_LAUNCH(k_ph_sweepff<false>, g, 256, 0, st, M, B, kinfo, Yff, IJff, Btv);
+    wide ? EPHB_LAUNCH((k_ph_sweepff<false, 32>), g, 256, 0, st, M, B, kinfo, Yff, IJff, Btv)
+         : EPHB_LAUNCH((k_ph_sweepff<false, 1>), g, 256, 0, st, M, B, kinfo, Yff, IJff, Btv);
   return cudaGetLastError();
 }
 
@@ -1289,12 +1315,16 @@ cudaError_t launch_drag_term32(const MeshDev &D, const BteDev &B, const SweepSeg
 }
 
 cudaError_t launch_ph_sweep32(const ModelDev &M, const BteDev &B, const int2 *kinfo, const float *Y32,
-                              const float *IJ32, double *Btv, cudaStream_t st) {
-  const unsigned g = unsigned((B.nq * B.nbr * 32 + 255) / 256);
+                              const float *IJ32, double *Btv, int64_t n_ph_entries, cudaStream_t st) {
+  // rows of a few entries: one thread per row; longer rows: one warp
+  const bool wide = B.nq * B.nbr > 0 && n_ph_entries / (B.nq * B.nbr) >= 4;
+  const unsigned g = unsigned((B.nq * B.nbr * (wide ? 32 : 1) + 255) / 256);
   if (M.nsym > 1)
-    EPHB_LAUNCH(k_ph_sweep32<true>, g, 256, 0, st, M, B, kinfo, Y32, IJ32, Btv);
+    wide ? EPHB_LAUNCH((k_ph_sweep32<true, 32>), g, 256, 0, st, M, B, kinfo, Y32, IJ32, Btv)
+         : EPHB_LAUNCH((k_ph_sweep32<true, 1>), g, 256, 0, st, M, B, kinfo, Y32, IJ32, Btv);
   else
-    EPHB_LAUNCH(k_ph_sweep32<false>, g, 256, 0, st, M, B, kinfo, Y32, IJ32, Btv);
+    wide ? EPHB_LAUNCH((k_ph_sweep32<false, 32>), g, 256, 0, st, M, B, kinfo, Y32, IJ32, Btv)
+         : EPHB_LAUNCH((k_ph_sweep32<false, 1>), g, 256, 0, st, M, B, kinfo, Y32, IJ32, Btv);
   return cudaGetLastError();
 }
 
@@ -1319,18 +1349,25 @@ cudaError_t launch_drag_term(const MeshDev &D, const BteDev &B, const SweepSegs 
 }
 
 cudaError_t launch_ph_sweep(const ModelDev &M, const MeshDev &D, const BteDev &B, const int2 *kinfo, const double *I,
-                            const double *J, double *Btv, cudaStream_t st) {
-  const unsigned g = unsigned((B.nq * B.nbr * 32 + 255) / 256);
+                            const double *J, double *Btv, int64_t n_ph_entries, cudaStream_t st) {
+  // rows of a few entries: one thread per row; longer rows: one warp
+  const bool wide = B.nq * B.nbr > 0 && n_ph_entries / (B.nq * B.nbr) >= 4;
+  const unsigned g = unsigned((B.nq * B.nbr * (wide ? 32 : 1) + 255) / 256);
   if (M.nsym > 1)
-    EPHB_LAUNCH(k_ph_sweep<true>, g, 256, 0, st, M, D, B, kinfo, I, J, Btv);
+    wide ? EPHB_LAUNCH((k_ph_sweep<true, 32>), g, 256, 0, st, M, D, B, kinfo, I, J, Btv)
+         : EPHB_LAUNCH((k_ph_sweep<true, 1>), g, 256, 0, st, M, D, B, kinfo, I, J, Btv);
   else
-    EPHB_LAUNCH(k_ph_sweep<false>, g, 256, 0, st, M, D, B, kinfo, I, J, Btv);
+    wide ? EPHB_LAUNCH((k_ph_sweep<false, 32>), g, 256, 0, st, M, D, B, kinfo, I, J, Btv)
+         : EPHB_LAUNCH((k_ph_sweep<false, 1>), g, 256, 0, st, M, D, B, kinfo, I, J, Btv);
   return cudaGetLastError();
 }
 
-cudaError_t launch_ph_update(const ModelDev &M, const MeshDev &D, const BteDev &B, const double *Btv,
-                             const double *F0, const double *inv_nnW, double *F, double *G, cudaStream_t st) {
-  EPHB_LAUNCH(k_ph_update, unsigned((D.nq * M.nbr + 255) / 256), 256, 0, st, M, D, B, Btv, F0, inv_nnW, F, G);
+cudaError_t launch_ph_update(const ModelDev &M, const MeshDev &D, const double *Btv, const double *F0,
+                             const double *inv_nnW, double *F, double *G, double *Afold, cudaStream_t st) {
+  EPHB_LAUNCH(k_ph_fold_rep, unsigned((D.n_qrep * M.nbr + 255) / 256), 256, 0, st, M, D, Btv, Afold);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  EPHB_LAUNCH(k_ph_update, unsigned((D.nq * M.nbr + 255) / 256), 256, 0, st, M, D, Afold, F0, inv_nnW, F, G);
   return cudaGetLastError();
 }
 

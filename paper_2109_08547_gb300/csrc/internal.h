@@ -21,6 +21,9 @@ struct ModelDev {
   const int *sym_rot = nullptr;       // [nsym][9]
   const double *sym_cart = nullptr;   // [nsym][9]
   const int *sym_inv = nullptr;       // [nsym]
+  // atom maps of the operations: S tau_a = tau_{perm[s][a]} + shift[s][a] (crystal coordinates)
+  const int *atom_perm = nullptr;     // [nsym][nat]
+  const int *atom_shift = nullptr;    // [nsym][nat][3]
 };
 
 // Views of the mesh-level arrays.
@@ -40,6 +43,10 @@ struct MeshDev {
   const double2 *u;                   // [nq][nbr][nbr]
   const double *vph;                  // [nq][nbr][3]
   const uint8_t *pgrp;                // [nq][nbr][2]
+  const int *qrep, *qop;              // [nq] representative of the q star and S with S <q> = q
+  const int *qrep_of;                 // [nq] index of a representative in the representative list
+  const int *qlist;                   // [n_qrep] the representatives
+  int64_t n_qrep;
   const int *rep, *op, *stab;         // [nk]
   const int *ibzw_of;                 // [nk] index in the irreducible-window list or -1
   const int *ibzw_list;               // [n_ibzw]
@@ -69,9 +76,13 @@ cudaError_t launch_bands_from_rep(const ModelDev &M, Mesh km, const int *rep, co
                                   uint8_t *egrp, uint32_t *amask, uint32_t *rmask, int *flag, cudaStream_t st);
 cudaError_t launch_ibzw_flag(int64_t nk, const int *rep, const uint32_t *amask, int *flag, cudaStream_t st);
 cudaError_t launch_compact(int64_t n, const int *flag, const int64_t *pos, int *list, cudaStream_t st);
-cudaError_t launch_phonon_modes(const ModelDev &M, Mesh qm, const double2 *qtab, double degen_tol, double omega_min,
-                                double *w, double2 *u, double *vph, uint8_t *pgrp, cudaStream_t st);
+cudaError_t launch_phonon_modes(const ModelDev &M, Mesh qm, const int *list, int64_t n, const double2 *qtab,
+                                double degen_tol, double omega_min, double *w, double2 *u, double *vph, uint8_t *pgrp,
+                                cudaStream_t st);
 cudaError_t launch_ibz(const ModelDev &M, Mesh km, int *rep, int *op, int *stab, int *flag, cudaStream_t st);
+cudaError_t launch_phonons_from_rep(const ModelDev &M, Mesh qm, const double2 *qtab, const int *qrep, const int *qop,
+                                    double *w, double2 *u, double *vph, uint8_t *pgrp, cudaStream_t st);
+cudaError_t launch_rep_index(int64_t n, const int *list, int64_t nlist, int *of, cudaStream_t st);
 cudaError_t launch_ibzw_fill(int64_t nk, const int *flag, const int64_t *pos, int *ibzw_list, int *ibzw_of,
                              cudaStream_t st);
 cudaError_t launch_pair_count(const MeshDev &D, int *npairs, cudaStream_t st);
@@ -122,7 +133,8 @@ cudaError_t launch_vertex_epilogue(const ModelDev &M, const MeshDev &D, RatePara
 // ---- vertex_tc.cu (tcgen05 R_ph contraction with exact BF16 fixed-point slices)
 int tc_kp(const ModelDev &M);     // padded K = 2 nRgp rounded up to the K block
 int tc_nmax(const ModelDev &M);   // column stride of B' = 2 nb^2 nbr rounded up to 16
-cudaError_t launch_phase_slices(const ModelDev &M, const MeshDev &D, int ns, __nv_bfloat16 *phis, cudaStream_t st);
+cudaError_t launch_phase_slices(const ModelDev &M, const MeshDev &D, int ns, __nv_bfloat16 *phis,
+                                __nv_bfloat16 *angle_tab, cudaStream_t st);
 cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_t i0, int64_t nkc, int64_t pair_base,
                              const double2 *A, const __nv_bfloat16 *phis, __nv_bfloat16 *bs, double *bscale,
                              int *nitem, int64_t *item_ptr, int64_t *scratch, int64_t scratch_elems,
@@ -245,9 +257,9 @@ cudaError_t launch_pack_ij(int64_t nst, const double *I, const double *J, double
 cudaError_t launch_drag_term(const MeshDev &D, const BteDev &B, const SweepSegs &S, const double *F, const double *G,
                              double *part, double *Dterm, cudaStream_t st);
 cudaError_t launch_ph_sweep(const ModelDev &M, const MeshDev &D, const BteDev &B, const int2 *kinfo, const double *I,
-                            const double *J, double *Btv, cudaStream_t st);
-cudaError_t launch_ph_update(const ModelDev &M, const MeshDev &D, const BteDev &B, const double *Btv,
-                             const double *F0, const double *inv_nnW, double *F, double *G, cudaStream_t st);
+                            const double *J, double *Btv, int64_t n_ph_entries, cudaStream_t st);
+cudaError_t launch_ph_update(const ModelDev &M, const MeshDev &D, const double *Btv, const double *F0,
+                             const double *inv_nnW, double *F, double *G, double *Afold, cudaStream_t st);
 // Coefficient tensors: fixed-count partial sums (electron: 36 per block, phonon: 18 per
 // block) and a single-block finalisation into `res`.
 //   res layout: [0] sigma [9] sigmaS [18] alpha_el [27] kappa0_el [36] alpha_ph [45] kappa_ph
@@ -273,7 +285,7 @@ cudaError_t launch_corr_apply(int64_t nst, const float *dI, const float *dJ, dou
 cudaError_t launch_drag_term32(const MeshDev &D, const BteDev &B, const SweepSegs &S, const float2 *X32,
                                const float *FG32, double *part, double *Dterm, cudaStream_t st);
 cudaError_t launch_ph_sweep32(const ModelDev &M, const BteDev &B, const int2 *kinfo, const float *Y32,
-                              const float *IJ32, double *Btv, cudaStream_t st);
+                              const float *IJ32, double *Btv, int64_t n_ph_entries, cudaStream_t st);
 cudaError_t launch_pack6_f32(int64_t n, const double *A, const double *Bv, float *out, cudaStream_t st);
 // Float-float forms of the same two terms for the later outer iterations of the mixed
 // iteration: Xff (X+ hi, lo, X- hi, lo per entry), Yff, IJff ([state][6] pairs), FGff
@@ -281,7 +293,7 @@ cudaError_t launch_pack6_f32(int64_t n, const double *A, const double *Bv, float
 cudaError_t launch_drag_termff(const MeshDev &D, const BteDev &B, const SweepSegs &S, const float4 *Xff,
                                const float2 *FGff, double *part, double *Dterm, cudaStream_t st);
 cudaError_t launch_ph_sweepff(const ModelDev &M, const BteDev &B, const int2 *kinfo, const float2 *Yff,
-                              const float2 *IJff, double *Btv, cudaStream_t st);
+                              const float2 *IJff, double *Btv, int64_t n_ph_entries, cudaStream_t st);
 cudaError_t launch_copy_ff(int64_t n, const double *a, float2 *out, cudaStream_t st);
 cudaError_t launch_pack6_ff(int64_t n, const double *A, const double *Bv, float2 *out, cudaStream_t st);
 cudaError_t launch_copy_f32(int64_t n, const double *a, float *b, cudaStream_t st);

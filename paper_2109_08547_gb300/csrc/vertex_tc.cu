@@ -114,6 +114,38 @@ __global__ void k_phase_slices(ModelDev M, MeshDev D, int ns, int Kp, __nv_bfloa
   fixed_slices(x, ns, phis + (size_t(q) * ns) * Kp + r, size_t(Kp));
 }
 
+// On an n x n x n mesh every phase 2 pi q.R is 2 pi j / n with j = (q.R) mod n: the slices of
+// cos and sin of the n angles once (table [j][cos, sin][slice]), then every phase slice is a
+// lookup.  The angles' cosines and sines are FP64 library values of 2 pi j / n.
+__global__ void k_phase_angle_table(int n, int ns, __nv_bfloat16 *tab) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * n) return;
+  const int j = t >> 1, part = t & 1;
+  double sv, cv;
+  sincospi(2.0 * double(j) / double(n), &sv, &cv);
+  fixed_slices(part == 0 ? cv : sv, ns, tab + size_t(t) * ns, 1);
+}
+
+__global__ void k_phase_slices_cubic(ModelDev M, MeshDev D, int ns, int Kp, const __nv_bfloat16 *__restrict__ tab,
+                                     __nv_bfloat16 *phis) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int R = M.nRgp, n = D.qm.n[0];
+  if (t >= D.nq * int64_t(Kp)) return;
+  const int q = int(t / Kp), r = int(t % Kp);
+  __nv_bfloat16 *dst = phis + (size_t(q) * ns) * Kp + r;
+  if (r >= 2 * R) {
+    for (int sl = 0; sl < ns; ++sl) dst[sl * size_t(Kp)] = __float2bfloat16_rn(0.f);
+    return;
+  }
+  const int rr = r < R ? r : r - R;
+  int b0, b1, b2;
+  D.qm.unflat(q, b0, b1, b2);
+  const int *Rv = M.Rgp + 3 * rr;
+  const int j = pmod((long long)b0 * Rv[0] + (long long)b1 * Rv[1] + (long long)b2 * Rv[2], n);
+  const __nv_bfloat16 *src = tab + (size_t(j) * 2 + (r < R ? 0 : 1)) * ns;
+  for (int sl = 0; sl < ns; ++sl) dst[sl * size_t(Kp)] = src[sl];
+}
+
 // B' slices of the k points of a chunk: BS[kc][slice][Nmax][Kp] (BF16) and column scales.
 // Column j' = ml*(2 nb nbr) + part*(nb nbr) + n'*nbr + a.  One block per (k, ml, column group):
 // the stage-A rows of that initial band for the group's (n', a) range (R x h complex values,
@@ -974,10 +1006,17 @@ cudaError_t launch_stage_a_tc(const ModelDev &M, const MeshDev &D, int ns, int64
   return e;
 }
 
-cudaError_t launch_phase_slices(const ModelDev &M, const MeshDev &D, int ns, __nv_bfloat16 *phis, cudaStream_t st) {
+cudaError_t launch_phase_slices(const ModelDev &M, const MeshDev &D, int ns, __nv_bfloat16 *phis,
+                                __nv_bfloat16 *angle_tab, cudaStream_t st) {
   const int Kp = tc_kp(M);
   const int64_t n = D.nq * int64_t(Kp);
-  EPHB_LAUNCH(k_phase_slices, unsigned((n + 255) / 256), 256, 0, st, M, D, ns, Kp, phis);
+  const Mesh &q = D.qm;
+  if (angle_tab && q.n[0] == q.n[1] && q.n[1] == q.n[2]) {
+    EPHB_LAUNCH(k_phase_angle_table, unsigned((2 * q.n[0] + 127) / 128), 128, 0, st, q.n[0], ns, angle_tab);
+    EPHB_LAUNCH(k_phase_slices_cubic, unsigned((n + 255) / 256), 256, 0, st, M, D, ns, Kp, angle_tab, phis);
+  } else {
+    EPHB_LAUNCH(k_phase_slices, unsigned((n + 255) / 256), 256, 0, st, M, D, ns, Kp, phis);
+  }
   return cudaGetLastError();
 }
 
