@@ -89,8 +89,9 @@ def parse():
                    help="Anderson history depth of the outer iteration (0: the plain iteration)")
     p.add_argument("--instances", type=int, default=8,
                    help="(T, mu, window) instances of the batched-vs-sequential comparison (0: skip it)")
-    p.add_argument("--warm", type=int, default=12,
-                   help="mesh size of the learned-warm-start report (40 training + 10 held-out instances; 0: skip)")
+    p.add_argument("--warm-train", type=int, default=200,
+                   help="(T, mu) training points of the learned-warm-start report (0: skip it)")
+    p.add_argument("--warm-held", type=int, default=40, help="held-out points of the learned-warm-start report")
     return p.parse_args()
 
 
@@ -287,39 +288,53 @@ def batched_block(B, ctx, wl, args, flush, torch, np):
     return out
 
 
-def warm_block(B, args, torch, np):
-    """The learned warm start: train the network on converged solutions of 40 (T, mu, window)
-    instances of the 4-band model on args.warm^3 meshes, then solve 10 held-out instances from
-    the RTA start and from the network's start (tolerance 1e-8): sweeps, outer iterations,
-    solve time and the worst coefficient difference between the two."""
+def warm_block(B, wl, args, torch, np):
+    """The learned warm start on the fine-mesh drag workload: train the network on converged
+    solutions of 200 seeded (T, mu) points (T in [100, 500] K, mu in mu0 +- 0.2 eV, the workload's
+    window), then solve 40 held-out points to tol 1e-8 from the RTA start, from the network's start
+    and from each point's own converged coordinates (the best this parametrisation allows):
+    sweeps, outer iterations, solve time, and the largest coefficient difference from the
+    RTA-started answers."""
     from paper_2109_08547_gb300 import synthetic as S
     from paper_2109_08547_gb300 import warmstart as WS
-    wl = S.workload_cscl4(args.warm)
-    grid = S.instance_grid(50, wl.mu_eV, seed=S.SEED_BASE + 6)
-    train, held = grid[:40], grid[40:]
-    union = (min(i[2] for i in grid), max(i[3] for i in grid))
+    train, held = WS.thermo_points(wl, args.warm_train, args.warm_held, seed=S.SEED_BASE + 7)
     dev = torch.device("cuda", torch.cuda.current_device())
     tol = 1e-8
+    prec = B.PRECISIONS[args.precision]
     with B.Context(dev.index) as ctx:
         B.set_wannier_model(ctx, wl.model)
-        B.build_meshes_ibz(ctx, wl.kmesh, wl.qmesh, union, wl.degen_tol_eV, wl.omega_min_eV)
-        B.compute_transition_rates(ctx, 0.0, 0.0, wl.sigma_eV, wl.cutoff_sigmas, instances=train)
-        B.solve_coupled_bte(ctx, "dragged", tol)
-        X, T = WS.instance_data(ctx, range(len(train)), dev)
-        net = B.MLP(seed=11)
+        B.build_meshes_ibz(ctx, wl.kmesh, wl.qmesh, wl.window, wl.degen_tol_eV, wl.omega_min_eV)
         torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xs, ts = [], []
+        for b0 in range(0, len(train), 64):
+            batch = train[b0:b0 + 64]
+            B.compute_transition_rates(ctx, 0.0, 0.0, wl.sigma_eV, wl.cutoff_sigmas, prec, instances=batch)
+            B.solve_coupled_bte(ctx, "dragged", tol, solve_precision=args.solve)
+            X, T = WS.instance_data(ctx, range(len(batch)), dev)
+            xs.append(X)
+            ts.append(T)
+        X, T = torch.cat(xs), torch.cat(ts)
+        torch.cuda.synchronize()
+        data_s = time.perf_counter() - t0
+        net = B.MLP(seed=11)
         t0 = time.perf_counter()
         losses = WS.train(net, X, T, steps=600, lr=2e-3)
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
-        B.compute_transition_rates(ctx, 0.0, 0.0, wl.sigma_eV, wl.cutoff_sigmas, instances=held)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        plain = B.solve_coupled_bte(ctx, "dragged", tol)
-        torch.cuda.synchronize()
-        plain_s = time.perf_counter() - t0
+
+        def held_solve(start):
+            B.compute_transition_rates(ctx, 0.0, 0.0, wl.sigma_eV, wl.cutoff_sigmas, prec, instances=held)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            if start is not None:
+                start()
+            r = B.solve_coupled_bte(ctx, "dragged", tol, solve_precision=args.solve, warm_start=start is not None)
+            torch.cuda.synchronize()
+            return r, time.perf_counter() - t1
+
+        plain, plain_s = held_solve(None)
         base = [B.transport_coefficients(ctx, i) for i in range(len(held))]
-        # the best this parametrisation can do: each instance's own converged coordinates
         nst = B.num_states(ctx)
         ideal_a = []
         for i in range(len(held)):
@@ -327,17 +342,18 @@ def warm_block(B, args, torch, np):
             torch.cuda.synchronize()
             B.state_targets(ctx, i, a.data_ptr())
             ideal_a.append(a)
-        for i in range(len(held)):
-            B.set_warm_start(ctx, i, ideal_a[i].data_ptr())
-        ideal = B.solve_coupled_bte(ctx, "dragged", tol, warm_start=True)
-        B.compute_transition_rates(ctx, 0.0, 0.0, wl.sigma_eV, wl.cutoff_sigmas, instances=held)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for i in range(len(held)):
-            WS.apply(ctx, net, i, dev)
-        warm = B.solve_coupled_bte(ctx, "dragged", tol, warm_start=True)
-        torch.cuda.synchronize()
-        warm_s = time.perf_counter() - t0
+
+        def set_ideal():
+            for i in range(len(held)):
+                B.set_warm_start(ctx, i, ideal_a[i].data_ptr())
+
+        ideal, _ = held_solve(set_ideal)
+
+        def set_net():
+            for i in range(len(held)):
+                WS.apply(ctx, net, i, dev)
+
+        warm, warm_s = held_solve(set_net)
         worst = 0.0
         for i in range(len(held)):
             c = B.transport_coefficients(ctx, i)
@@ -346,13 +362,16 @@ def warm_block(B, args, torch, np):
                 if nrm > 0:
                     worst = max(worst, float(np.linalg.norm(c[key] - v) / nrm))
         net.close()
-    return {"mesh": args.warm, "train_instances": len(train), "held_out": len(held), "samples": int(X.shape[0]),
-            "train_steps": len(losses), "train_s": train_s, "loss_first": losses[0], "loss_last": losses[-1],
-            "tol": tol, "rta_start": {"sweeps": plain["n_sweeps"], "outer": plain["outer_iters"], "s": plain_s},
-            "warm_start": {"sweeps": warm["n_sweeps"], "outer": warm["outer_iters"], "s": warm_s,
-                           "includes": "network inference for every held-out instance"},
-            "ideal_projection_start": {"sweeps": ideal["n_sweeps"], "outer": ideal["outer_iters"],
-                                       "note": "each instance started from its own converged coordinates"},
+    return {"workload": wl.name, "train_points": len(train), "held_out": len(held), "samples": int(X.shape[0]),
+            "training_data_s": data_s, "train_steps": len(losses), "train_s": train_s, "loss_first": losses[0],
+            "loss_last": losses[-1], "tol": tol,
+            "rta_start": {"fp64_sweeps": plain["n_sweeps"], "fp32_sweeps": plain["n_sweeps32"],
+                          "outer": plain["outer_iters"], "s": plain_s},
+            "network_start": {"fp64_sweeps": warm["n_sweeps"], "fp32_sweeps": warm["n_sweeps32"],
+                              "outer": warm["outer_iters"], "s": warm_s,
+                              "includes": "network inference for every held-out point"},
+            "own_converged_coordinates_start": {"fp64_sweeps": ideal["n_sweeps"], "fp32_sweeps": ideal["n_sweeps32"],
+                                                "outer": ideal["outer_iters"]},
             "max_coeff_rel_diff": worst}
 
 
@@ -634,7 +653,7 @@ def main():
         from paper_2109_08547_gb300 import synthetic as S
         with B.Context(local, stream=stream.cuda_stream) as bctx:
             batched = batched_block(B, bctx, S.workload_cscl4(24), args, flush, torch, np)
-    warm = warm_block(B, args, torch, np) if args.warm > 0 else None
+    warm = warm_block(B, wl, args, torch, np) if args.warm_train > 0 else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -154,7 +154,19 @@ typedef struct {
   double window_lo_eV, window_hi_eV;   /* instance window; lo >= hi: the mesh window           */
 } ephb_thermo;
 #define EPHB_MAX_INSTANCES 64
-typedef struct { double sigma_eV, cutoff_sigmas; } ephb_delta;
+/* Energy-conserving delta of Eq. X^e-ph.  kind EPHB_DELTA_GAUSS: Gaussian of standard deviation
+ * sigma_eV, zero beyond cutoff_sigmas standard deviations (readings [A10], [A11]).  kind
+ * EPHB_DELTA_TETRA: the analytic (linear) tetrahedron method of "Workflow and structure": the
+ * energy balance eps_n(k + q) - eps_m(k) -/+ hbar w_s(q) is interpolated linearly in the six
+ * tetrahedra of every cube of the q mesh and (1/N_q) delta becomes the weight of the mesh point
+ * q in that zone integral (reading [A22]); sigma_eV and cutoff_sigmas are ignored.  A zeroed
+ * struct's kind is the Gaussian. */
+#define EPHB_DELTA_GAUSS 0
+#define EPHB_DELTA_TETRA 1
+typedef struct {
+  double sigma_eV, cutoff_sigmas;
+  int kind;
+} ephb_delta;
 /* Precision of the R_ph contraction of the vertex (the largest part of the work):
  *   EPHB_FP64         FP64 on the CUDA cores.
  *   EPHB_FP64_SLICED  tensor cores (tcgen05, BF16 in, FP32 accumulate) on exact fixed-point

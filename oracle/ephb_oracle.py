@@ -37,6 +37,7 @@ __all__ = [
     "transition_rates", "Rates", "BTEResult", "solve_coupled_bte", "coefficients_from_responses",
     "prepare", "Prepared", "gaussian_delta", "fermi", "bose", "StateSpace", "ibz_window_points",
     "kplusq", "minus_q", "TENSORS", "inverse_ops", "ANGSTROM", "ibz_window_rows", "prepare_rows",
+    "tetra_corner_weights", "tetra_point_weights", "CUBE_TETRAHEDRA", "CUBE_SUBDIVISIONS",
 ]
 
 
@@ -164,6 +165,115 @@ def gaussian_delta(x, sigma, cutoff):
     """delta(x) = exp(-x^2/(2 sigma^2)) / (sigma sqrt(2 pi)); exactly 0 beyond cutoff*sigma."""
     d = np.exp(-0.5 * (x / sigma) ** 2) / (sigma * np.sqrt(2.0 * np.pi))
     return np.where(np.abs(x) <= cutoff * sigma, d, 0.0)
+
+
+# ----------------------------------------------------------------------------------------
+# linear tetrahedron delta ("Workflow and structure": the analytic tetrahedron method)
+# ----------------------------------------------------------------------------------------
+
+# The six tetrahedra of a mesh cube around one of its body diagonals (corner c has the offset
+# (c&1, c>>1&1, c>>2&1)): the diagonal 0-7 and its images a^c, a = 1, 2, 4, for the other three.
+# One diagonal's subdivision is not invariant under the cubic group; the average over the four
+# is (reading [A22]).
+CUBE_TETRAHEDRA = ((0, 1, 3, 7), (0, 1, 5, 7), (0, 2, 3, 7), (0, 2, 6, 7), (0, 4, 5, 7), (0, 4, 6, 7))
+CUBE_SUBDIVISIONS = tuple(tuple(tuple(a ^ c for c in tet) for tet in CUBE_TETRAHEDRA) for a in (0, 1, 2, 4))
+
+
+def tetra_corner_weights(e, E):
+    """Delta weights of the four corners of one tetrahedron: W_c = (1/V) int_T delta(E - e(r)) lam_c(r) dr
+    for e linear in the barycentric coordinates lam (e(r) = sum_c lam_c(r) e_c).  The level set
+    e = E is a triangle or a quadrilateral whose vertices lie on the edges (i, j) with
+    e_i < E < e_j; int_S lam_c dA / |grad e| over it, with the reference simplex of volume 1/6 in
+    the coordinates (lam_2, lam_3, lam_4) of the corners sorted by energy.  Zero unless
+    e_min < E < e_max."""
+    e = np.asarray(e, dtype=np.float64)
+    order = np.argsort(e, kind="stable")
+    es = e[order]
+    W = np.zeros(4)
+    if not (es[0] < E < es[3]):
+        return W
+    if E < es[1]:
+        edges = ((0, 1), (0, 2), (0, 3))
+    elif E < es[2]:
+        edges = ((0, 2), (0, 3), (1, 3), (1, 2))
+    else:
+        edges = ((0, 3), (1, 3), (2, 3))
+    pts = []
+    for i, j in edges:
+        t = (E - es[i]) / (es[j] - es[i])
+        lam = np.zeros(4)
+        lam[i], lam[j] = 1.0 - t, t
+        pts.append(lam)
+    tris = [(0, 1, 2)] if len(pts) == 3 else [(0, 1, 2), (0, 2, 3)]
+    grad = np.array([es[1] - es[0], es[2] - es[0], es[3] - es[0]])
+    acc = np.zeros(4)
+    for a, b, c in tris:
+        x = [pts[a][1:], pts[b][1:], pts[c][1:]]
+        area = 0.5 * np.linalg.norm(np.cross(x[1] - x[0], x[2] - x[0]))
+        acc += area * (pts[a] + pts[b] + pts[c]) / 3.0
+    W[order] = acc / (np.linalg.norm(grad) / 6.0)
+    return W
+
+
+def _tetra_weights_batch(e, corner):
+    """tetra_corner_weights for many tetrahedra at E = 0, the weight of one corner each:
+    e (m, 4) corner values, corner (m,) the corner's position in e.  Same construction, array
+    by array: the three energy ranges are evaluated for every tetrahedron and selected."""
+    m = e.shape[0]
+    order = np.argsort(e, axis=1, kind="stable")
+    es = np.take_along_axis(e, order, axis=1)
+    pc = np.argmax(order == corner[:, None], axis=1)           # sorted position of the corner
+    out = np.zeros(m)
+    cases = (((0, 1), (0, 2), (0, 3)), ((0, 2), (0, 3), (1, 3), (1, 2)), ((0, 3), (1, 3), (2, 3)))
+    sel = [(0.0 < es[:, 1]), (es[:, 1] <= 0.0) & (0.0 < es[:, 2]), (es[:, 2] <= 0.0)]
+    valid = (es[:, 0] < 0.0) & (0.0 < es[:, 3])
+    gnorm = np.linalg.norm(es[:, 1:] - es[:, :1], axis=1)
+    for edges, mask in zip(cases, sel):
+        rows = np.nonzero(valid & mask)[0]
+        if len(rows) == 0:
+            continue
+        esr = es[rows]
+        lam = np.zeros((len(rows), len(edges), 4))
+        for p, (i, j) in enumerate(edges):
+            t = (0.0 - esr[:, i]) / (esr[:, j] - esr[:, i])
+            lam[:, p, i] = 1.0 - t
+            lam[:, p, j] = t
+        lc = lam[np.arange(len(rows)), :, pc[rows]]                 # (r, npts): lambda of the corner
+        x = lam[:, :, 1:]
+        tris = [(0, 1, 2)] if len(edges) == 3 else [(0, 1, 2), (0, 2, 3)]
+        acc = np.zeros(len(rows))
+        for a, b, c in tris:
+            area = 0.5 * np.linalg.norm(np.cross(x[:, b] - x[:, a], x[:, c] - x[:, a]), axis=1)
+            acc += area * (lc[:, a] + lc[:, b] + lc[:, c]) / 3.0
+        out[rows] = acc / (gnorm[rows] / 6.0)
+    return out
+
+
+def tetra_point_weights(values, n, pts):
+    """w(p) = (1 / (6 N)) sum over the tetrahedra containing mesh point p of p's corner weight at
+    E = 0, averaged over the four body-diagonal subdivisions of the mesh cubes, for a function
+    `values` on the n1 x n2 x n3 mesh linearly interpolated in every tetrahedron
+    (sum_p w(p) F(p) approximates the zone average of F delta(values))."""
+    nn = np.array(n)
+    N = int(np.prod(nn))
+    vals = np.asarray(values).reshape(N)
+    pts = np.asarray(pts, dtype=np.int64)
+    idx = mesh_indices(n)
+    # every (point, cube it is a corner of, subdivision, tetrahedron holding that corner)
+    combos = []
+    for cb in range(8):
+        shift = np.array([cb & 1, (cb >> 1) & 1, (cb >> 2) & 1])
+        for sub in CUBE_SUBDIVISIONS:
+            for tet in sub:
+                if cb in tet:
+                    combos.append((shift, tet, tet.index(cb)))
+    out = np.zeros(len(pts))
+    for shift, tet, pos in combos:
+        origin = idx[pts] - shift
+        corners = np.stack([flat_index(np.mod(origin + np.array([c & 1, (c >> 1) & 1, (c >> 2) & 1]), nn), n)
+                            for c in tet], axis=1)
+        out += 0.25 * _tetra_weights_batch(vals[corners], np.full(len(pts), pos))
+    return out / (6.0 * N)
 
 
 # ----------------------------------------------------------------------------------------
@@ -342,8 +452,11 @@ def transition_rates(P: Prepared, ks=None, q_chunk: int = 256) -> Rates:
     """X^{+/-}_{m<k> n k'|sq} = (2 pi / (hbar N_q)) |g|^2 f_mk (1 - f_nk') {n_sq, 1 + n_sq}
     delta(eps_nk' - eps_mk -/+ hbar w_sq) for every IBZ representative <k> with an active
     band, every q of the phonon mesh with k' = [<k> + q] holding an active band, and every
-    branch above omega_min.  An entry is kept when either delta argument lies within the
-    cut.  ``ks`` restricts the rows to a subset of IBZ representatives (sampling)."""
+    branch above omega_min.  Gaussian delta: an entry is kept when either delta argument lies
+    within the cut.  Tetrahedron delta: (1/N_q) delta is replaced by the weight of q in the
+    linear tetrahedron integral over the q mesh of delta(eps_n(<k>+q) - eps_mk -/+ w_s(q)), and an
+    entry is kept when either weight is positive.  ``ks`` restricts the rows to a subset of IBZ
+    representatives (sampling)."""
     wl = P.wl
     nb, nbr = wl.model.nb, wl.model.nbranch
     T, mu = wl.T_K, wl.mu_eV
@@ -357,11 +470,25 @@ def transition_rates(P: Prepared, ks=None, q_chunk: int = 256) -> Rates:
     n_tuples = 0
     n_pairs = 0
     allq = np.arange(P.Nq)
+    tetra = getattr(wl, "delta", "gauss") == "tetra"
     for k in rows:
         kps_all = kplusq(P, k, allq)
         sel = P.active[kps_all].any(axis=1)
         qs_k = allq[sel]
         n_pairs += len(qs_k)
+        if tetra:
+            # weights of every pair q of the row, per (m, n, s, +/-): the zone integral over q of
+            # delta(eps_n(k+q) - eps_m(k) -/+ w_s(q)), linear in every tetrahedron of the q mesh
+            # (modes at or below omega_min enter with w = 0)
+            tw = {}
+            ws_all = np.where(P.w > wl.omega_min_eV, P.w, 0.0)
+            for mm in np.nonzero(P.active[k])[0]:
+                for nn in range(nb):
+                    base = P.eps[kps_all, nn] - P.eps[k, mm]
+                    for s in range(nbr):
+                        tw[(mm, nn, s)] = (tetra_point_weights(base - ws_all[:, s], wl.qmesh, qs_k) * P.Nq,
+                                           tetra_point_weights(base + ws_all[:, s], wl.qmesh, qs_k) * P.Nq)
+            qpos = {int(q): j for j, q in enumerate(qs_k)}
         for c0 in range(0, len(qs_k), q_chunk):
             qs = qs_k[c0:c0 + q_chunk]
             kps = kps_all[qs]
@@ -373,10 +500,17 @@ def transition_rates(P: Prepared, ks=None, q_chunk: int = 256) -> Rates:
                             if P.w[q, s] <= wl.omega_min_eV:
                                 continue
                             n_tuples += 1
-                            xp = P.eps[kp, nn] - P.eps[k, mm] - P.w[q, s]
-                            xm = P.eps[kp, nn] - P.eps[k, mm] + P.w[q, s]
-                            if abs(xp) > cut * sig and abs(xm) > cut * sig:
-                                continue
+                            if tetra:
+                                wpa, wma = tw[(mm, nn, s)]
+                                dp, dm = wpa[qpos[int(q)]], wma[qpos[int(q)]]
+                                if dp <= 0.0 and dm <= 0.0:
+                                    continue
+                            else:
+                                xp = P.eps[kp, nn] - P.eps[k, mm] - P.w[q, s]
+                                xm = P.eps[kp, nn] - P.eps[k, mm] + P.w[q, s]
+                                if abs(xp) > cut * sig and abs(xm) > cut * sig:
+                                    continue
+                                dp, dm = gaussian_delta(xp, sig, cut), gaussian_delta(xm, sig, cut)
                             occ = C * g2[i, mm, nn, s] * fk[k, mm] * (1.0 - fk[kp, nn])
                             cols["ik"].append(k)
                             cols["m"].append(mm)
@@ -384,8 +518,8 @@ def transition_rates(P: Prepared, ks=None, q_chunk: int = 256) -> Rates:
                             cols["n"].append(nn)
                             cols["s"].append(s)
                             cols["ikp"].append(kp)
-                            cols["Xp"].append(occ * nq[q, s] * gaussian_delta(xp, sig, cut))
-                            cols["Xm"].append(occ * (1.0 + nq[q, s]) * gaussian_delta(xm, sig, cut))
+                            cols["Xp"].append(occ * nq[q, s] * dp)
+                            cols["Xm"].append(occ * (1.0 + nq[q, s]) * dm)
     arr = {key: np.array(v, dtype=np.float64 if key in ("Xp", "Xm") else np.int64) for key, v in cols.items()}
     order = np.lexsort((arr["s"], arr["n"], arr["iq"], arr["m"], arr["ik"]))
     arr = {key: v[order] for key, v in arr.items()}

@@ -71,7 +71,11 @@ class ThermoC(C.Structure):
 
 
 class DeltaC(C.Structure):
-    _fields_ = [("sigma_eV", C.c_double), ("cutoff_sigmas", C.c_double)]
+    _fields_ = [("sigma_eV", C.c_double), ("cutoff_sigmas", C.c_double), ("kind", C.c_int)]
+
+
+DELTA_GAUSS, DELTA_TETRA = 0, 1   # EPHB_DELTA_*
+DELTAS = {"gauss": DELTA_GAUSS, "tetra": DELTA_TETRA}
 
 
 class RatesInfoC(C.Structure):
@@ -278,7 +282,7 @@ def build_meshes_ibz(ctx: Context, kmesh, qmesh, window, degen_tol_eV=1e-6, omeg
 
 
 def compute_transition_rates(ctx: Context, T_K, mu_eV, sigma_eV=0.01, cutoff_sigmas=8.0, precision=FP64,
-                             instances=None) -> dict:
+                             instances=None, delta="gauss") -> dict:
     """One (T_K, mu_eV) instance on the mesh window, or ``instances``: a list of
     (T_K, mu_eV) or (T_K, mu_eV, window_lo_eV, window_hi_eV) tuples (T_K, mu_eV ignored)."""
     if instances is None:
@@ -287,7 +291,7 @@ def compute_transition_rates(ctx: Context, T_K, mu_eV, sigma_eV=0.01, cutoff_sig
     for i, t in enumerate(instances):
         lo, hi = (t[2], t[3]) if len(t) > 2 else (0.0, 0.0)
         arr[i] = ThermoC(float(t[0]), float(t[1]), float(lo), float(hi))
-    de = DeltaC(float(sigma_eV), float(cutoff_sigmas))
+    de = DeltaC(float(sigma_eV), float(cutoff_sigmas), DELTAS[delta] if isinstance(delta, str) else int(delta))
     info = RatesInfoC()
     _check(ctx, _lib.ephb_compute_transition_rates(ctx.handle, arr, len(instances), C.byref(de), int(precision),
                                                    C.byref(info)))
@@ -403,7 +407,8 @@ def run_path(ctx: Context, wl, level="dragged", ko_correction=True, tol=None, ma
              precision=FP64, allow_noconv=False, solve_precision="fp64", accel=0) -> PathResult:
     """The whole hot path for one workload on an existing context whose model is set."""
     mesh = build_meshes_ibz(ctx, wl.kmesh, wl.qmesh, wl.window, wl.degen_tol_eV, wl.omega_min_eV)
-    rates = compute_transition_rates(ctx, wl.T_K, wl.mu_eV, wl.sigma_eV, wl.cutoff_sigmas, precision)
+    rates = compute_transition_rates(ctx, wl.T_K, wl.mu_eV, wl.sigma_eV, wl.cutoff_sigmas, precision,
+                                     delta=getattr(wl, "delta", "gauss"))
     solve = solve_coupled_bte(ctx, level, wl.tol if tol is None else tol, 0.0, max_outer, max_inner, ko_correction,
                               allow_noconv, solve_precision=solve_precision, accel=accel)
     return PathResult(mesh, rates, solve, transport_coefficients(ctx))

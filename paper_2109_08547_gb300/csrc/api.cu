@@ -764,7 +764,9 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
   if (ninst < 1 || ninst > EPHB_MAX_INSTANCES) return fail(ctx, EPHB_EINVAL, "ninst out of range");
   if (precision != EPHB_FP64 && precision != EPHB_FP64_SLICED && precision != EPHB_SPLIT_BF16)
     return fail(ctx, EPHB_EINVAL, "precision must be EPHB_FP64, EPHB_FP64_SLICED or EPHB_SPLIT_BF16");
-  if (!(delta->sigma_eV > 0) || !(delta->cutoff_sigmas > 0))
+  if (delta->kind != EPHB_DELTA_GAUSS && delta->kind != EPHB_DELTA_TETRA)
+    return fail(ctx, EPHB_EINVAL, "delta kind must be EPHB_DELTA_GAUSS or EPHB_DELTA_TETRA");
+  if (delta->kind == EPHB_DELTA_GAUSS && (!(delta->sigma_eV > 0) || !(delta->cutoff_sigmas > 0)))
     return fail(ctx, EPHB_EINVAL, "sigma and cutoff must be positive");
   // exact FP32 sums of the accumulated slice diagonals bound the contraction length
   if (precision == EPHB_FP64_SLICED && tc_slices_for(tc_kp(ctx->M), true) == 0)
@@ -798,10 +800,12 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
   RateParams rp;
   rp.T = inst->T_K;
   rp.mu = inst->mu_eV;
-  rp.sigma = delta->sigma_eV;
-  rp.cut = delta->cutoff_sigmas * delta->sigma_eV;
-  rp.inv_sigma = 1.0 / delta->sigma_eV;
-  rp.gnorm = 1.0 / (delta->sigma_eV * std::sqrt(2.0 * kPi));
+  rp.tetra = delta->kind == EPHB_DELTA_TETRA ? 1 : 0;
+  const double sig = rp.tetra ? 1.0 : delta->sigma_eV;   // unused with the tetrahedron weights
+  rp.sigma = sig;
+  rp.cut = rp.tetra ? 0.0 : delta->cutoff_sigmas * sig;
+  rp.inv_sigma = 1.0 / sig;
+  rp.gnorm = 1.0 / (sig * std::sqrt(2.0 * kPi));
   auto ff_split = [](double v) {
     const float h = float(v);
     return make_float2(h, float(v - double(h)));

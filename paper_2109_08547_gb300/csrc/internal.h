@@ -100,6 +100,7 @@ struct RateParams {
   double y_scale;                          // N_q / N_k
   int vertex_only;                         // 1: store V+- = 2pi/(hbar N_q)|g|^2 delta (no occupations)
   int rot_fp32;                            // 1: band/branch rotations in FP32 (mixed mode)
+  int tetra = 0;                           // 1: linear tetrahedron delta weights instead of the Gaussian
   const float *eps32 = nullptr, *w32 = nullptr;   // FP32 copies of eps [nk][nb] and w [nq][nbr]
 };
 cudaError_t launch_rate_count(const ModelDev &M, const MeshDev &D, RateParams rp, int *cntE, int *cntPh,

@@ -120,6 +120,110 @@ __device__ inline int cut_flags(double ekpn, double ekm, double wqs, float fkpn,
   return (fabs(dxp) <= cut ? 1 : 0) | (fabs(dxm) <= cut ? 2 : 0);
 }
 
+// ------------------------------------------------------------------------ tetrahedron delta
+// The analytic (linear) tetrahedron method of "Workflow and structure" for the energy-conserving
+// delta (reading [A22]): for the process <k>m -> k'n with k' = <k> + r q, the function
+// Delta+-(q') = eps_n(<k> + r q') - eps_m(<k>) -/+ hbar w_s(q') is interpolated linearly in the six
+// tetrahedra of every cube of the q mesh, and (1/N_q) delta(Delta) at mesh point q becomes the
+// weight of q in that integral: the sum over the 24 tetrahedra containing q of q's corner weight
+// W_c = (1/V) int_T delta(Delta) lambda_c, divided by 6 N_q.  Modes at or below omega_min enter
+// Delta with w = 0.  The six tetrahedra of a cube lie around one body diagonal; that subdivision
+// is not invariant under the cubic group, so the weights are averaged over the four diagonals
+// (the diagonal 0-7 and its images: corners c -> c ^ a, a = 1, 2, 4).  No width and no cutoff:
+// an entry exists where a weight is positive.
+__constant__ unsigned char kCubeTets[6][4] = {{0, 1, 3, 7}, {0, 1, 5, 7}, {0, 2, 3, 7},
+                                              {0, 2, 6, 7}, {0, 4, 5, 7}, {0, 4, 6, 7}};
+
+// weight W_c of corner c of one tetrahedron with corner values e at the level 0: the level set is
+// a triangle or a quadrilateral on the edges (i, j) of the energy-sorted corners with
+// e_i < 0 < e_j; int lambda_c dA / |grad e| over it in the coordinates (lambda_2, lambda_3,
+// lambda_4) of the sorted corners, where the simplex has volume 1/6
+__device__ inline double tetra_corner_weight(const double e[4], int c) {
+  int o[4] = {0, 1, 2, 3};
+  for (int i = 1; i < 4; ++i) {   // stable sort of the corners by value
+    const int x = o[i];
+    int j = i - 1;
+    while (j >= 0 && e[o[j]] > e[x]) {
+      o[j + 1] = o[j];
+      --j;
+    }
+    o[j + 1] = x;
+  }
+  const double es[4] = {e[o[0]], e[o[1]], e[o[2]], e[o[3]]};
+  if (!(es[0] < 0.0 && 0.0 < es[3])) return 0.0;
+  int pc = 0;
+  for (int i = 0; i < 4; ++i)
+    if (o[i] == c) pc = i;
+  int ei[4], ej[4], np;
+  if (0.0 < es[1]) {
+    np = 3; ei[0] = 0; ej[0] = 1; ei[1] = 0; ej[1] = 2; ei[2] = 0; ej[2] = 3;
+  } else if (0.0 < es[2]) {
+    np = 4; ei[0] = 0; ej[0] = 2; ei[1] = 0; ej[1] = 3; ei[2] = 1; ej[2] = 3; ei[3] = 1; ej[3] = 2;
+  } else {
+    np = 3; ei[0] = 0; ej[0] = 3; ei[1] = 1; ej[1] = 3; ei[2] = 2; ej[2] = 3;
+  }
+  double x[4][3], lc[4];
+  for (int p = 0; p < np; ++p) {
+    const double t = (0.0 - es[ei[p]]) / (es[ej[p]] - es[ei[p]]);
+    double lam[4] = {0.0, 0.0, 0.0, 0.0};
+    lam[ei[p]] = 1.0 - t;
+    lam[ej[p]] = t;
+    x[p][0] = lam[1];
+    x[p][1] = lam[2];
+    x[p][2] = lam[3];
+    lc[p] = lam[pc];
+  }
+  auto tri = [&](int a, int b, int d) {
+    const double u0 = x[b][0] - x[a][0], u1 = x[b][1] - x[a][1], u2 = x[b][2] - x[a][2];
+    const double v0 = x[d][0] - x[a][0], v1 = x[d][1] - x[a][1], v2 = x[d][2] - x[a][2];
+    const double c0 = u1 * v2 - u2 * v1, c1 = u2 * v0 - u0 * v2, c2 = u0 * v1 - u1 * v0;
+    return 0.5 * sqrt(c0 * c0 + c1 * c1 + c2 * c2) * (lc[a] + lc[b] + lc[d]) / 3.0;
+  };
+  double acc = tri(0, 1, 2);
+  if (np == 4) acc += tri(0, 2, 3);
+  const double g0 = es[1] - es[0], g1 = es[2] - es[0], g2 = es[3] - es[0];
+  return acc / (sqrt(g0 * g0 + g1 * g1 + g2 * g2) / 6.0);
+}
+
+// N_q times the tetrahedron weights of mesh point q for both processes: wp for
+// Delta+ = eps_n(k + r q') - eps_m(k) - w_s(q') and wm for Delta- (+ w_s)
+__device__ inline void tetra_pair_weights(const MeshDev &D, int nb, int nbr, int k, int m, int n, int s, int q,
+                                          double &wp, double &wm) {
+  int a0, a1, a2, b0, b1, b2;
+  D.km.unflat(k, a0, a1, a2);
+  D.qm.unflat(q, b0, b1, b2);
+  const double em = D.eps[size_t(k) * nb + m];
+  double accp = 0.0, accm = 0.0;
+  for (int cb = 0; cb < 8; ++cb) {
+    const int o0 = b0 - (cb & 1), o1 = b1 - ((cb >> 1) & 1), o2 = b2 - ((cb >> 2) & 1);
+    for (int dt = 0; dt < 24; ++dt) {
+      const int t = dt % 6, flip = dt < 6 ? 0 : (1 << (dt / 6 - 1));   // diagonal images c ^ 1, 2, 4
+      int c = -1;
+      for (int i = 0; i < 4; ++i)
+        if ((kCubeTets[t][i] ^ flip) == cb) c = i;
+      if (c < 0) continue;
+      double ep[4], en[4];
+      for (int i = 0; i < 4; ++i) {
+        const int cr = kCubeTets[t][i] ^ flip;
+        const int q0 = pmod(o0 + (cr & 1), D.qm.n[0]), q1 = pmod(o1 + ((cr >> 1) & 1), D.qm.n[1]),
+                  q2 = pmod(o2 + ((cr >> 2) & 1), D.qm.n[2]);
+        const int qq = D.qm.flat(q0, q1, q2);
+        const int kk = D.km.flat(pmod(a0 + D.ratio[0] * q0, D.km.n[0]), pmod(a1 + D.ratio[1] * q1, D.km.n[1]),
+                                 pmod(a2 + D.ratio[2] * q2, D.km.n[2]));
+        const double wv = D.w[size_t(qq) * nbr + s];
+        const double w = wv > D.omega_min ? wv : 0.0;
+        const double d = D.eps[size_t(kk) * nb + n] - em;
+        ep[i] = d - w;
+        en[i] = d + w;
+      }
+      accp += tetra_corner_weight(ep, c);
+      accm += tetra_corner_weight(en, c);
+    }
+  }
+  wp = accp / 24.0;   // 1/6 per tetrahedron, 1/4 per subdivision
+  wm = accm / 24.0;
+}
+
 // ------------------------------------------------------------------------ count pass
 __global__ void k_rate_count(ModelDev M, MeshDev D, RateParams rp, int *cntE, int *cntPh,
                              unsigned long long *n_tuples) {
@@ -153,7 +257,14 @@ __global__ void k_rate_count(ModelDev M, MeshDev D, RateParams rp, int *cntE, in
           for (int s = 0; s < nbr; ++s) {
             if (!(wq[s] > D.omega_min)) continue;
             ++nt;
-            const int f = cut_flags(ekp[n], ek[m], wq[s], fkp[n], fk[m], fw[s], rp.cut);
+            int f;
+            if (rp.tetra) {
+              double wpt, wmt;
+              tetra_pair_weights(D, nb, nbr, k, m, n, s, q, wpt, wmt);
+              f = (wpt > 0.0 ? 1 : 0) | (wmt > 0.0 ? 2 : 0);
+            } else {
+              f = cut_flags(ekp[n], ek[m], wq[s], fkp[n], fk[m], fw[s], rp.cut);
+            }
             c += f != 0;
             cph[s] += f & 1;
           }
@@ -347,19 +458,27 @@ __device__ void pair_epilogue(const ModelDev &M, const MeshDev &D, const RatePar
       double g2 = cnt == 1 ? sum : sum / double(cnt);
       double dxp = ekp[n] - ek[m] - wq[s];
       double dxm = ekp[n] - ek[m] + wq[s];
+      double dp, dm;   // N_q times the (1/N_q) delta weights
+      if (rp.tetra) {
+        tetra_pair_weights(D, nb, nbr, k, m, n, s, q, dp, dm);
+      } else {
+        dp = gauss_d(dxp, rp);
+        dm = gauss_d(dxm, rp);
+      }
       if (rp.vertex_only) {   // T-independent vertex weights V+-: occupation factors left out
         const double v = rp.inv_Nq_pref * g2;
-        xp = v * gauss_d(dxp, rp);
-        xm = v * gauss_d(dxm, rp);
+        xp = v * dp;
+        xm = v * dm;
       } else {
         double fm = fermi_d(ek[m], rp.mu, kT), fn = fermi_d(ekp[n], rp.mu, kT), nq = bose_d(wq[s], kT);
         double occ = rp.inv_Nq_pref * g2 * fm * (1.0 - fn);
-        xp = occ * nq * gauss_d(dxp, rp);
-        xm = occ * (1.0 + nq) * gauss_d(dxm, rp);
+        xp = occ * nq * dp;
+        xm = occ * (1.0 + nq) * dm;
       }
       Xps[t] = xp;
       Xms[t] = xm;
-      flg[t] = (fabs(dxp) <= rp.cut ? 1 : 0) | (fabs(dxm) <= rp.cut ? 2 : 0);
+      flg[t] = rp.tetra ? ((dp > 0.0 ? 1 : 0) | (dm > 0.0 ? 2 : 0))
+                        : ((fabs(dxp) <= rp.cut ? 1 : 0) | (fabs(dxm) <= rp.cut ? 2 : 0));
     } else {
       Xps[t] = 0.0;
       Xms[t] = 0.0;
@@ -662,7 +781,14 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
     flg[t] = 0;
     if (!(wq[s] > D.omega_min)) continue;
     // the cutoff test first: tuples with neither delta inside it need no average or occupation
-    const int f = cut_flags(ekp[n], ek[m], wq[s], fkp32[n], fk32[m], fw32[s], rp.cut);
+    double tp = 0.0, tm = 0.0;
+    int f;
+    if (rp.tetra) {
+      tetra_pair_weights(D, nb, nbr, k, m, n, s, q, tp, tm);
+      f = (tp > 0.0 ? 1 : 0) | (tm > 0.0 ? 2 : 0);
+    } else {
+      f = cut_flags(ekp[n], ek[m], wq[s], fkp32[n], fk32[m], fw32[s], rp.cut);
+    }
     if (!f) continue;
     const bool inp = f & 1, inm = f & 2;
     flg[t] = uint8_t(f);
@@ -682,7 +808,8 @@ __global__ void __launch_bounds__(128) k_rate_epilogue(ModelDev M, MeshDev D, Ra
         }
       }
     }
-    const double gp = inp ? gauss_ff(dxp, rp) : 0.0, gm = inm ? gauss_ff(dxm, rp) : 0.0;
+    const double gp = rp.tetra ? tp : (inp ? gauss_ff(dxp, rp) : 0.0);
+    const double gm = rp.tetra ? tm : (inm ? gauss_ff(dxm, rp) : 0.0);
     if (rp.vertex_only) {   // T-independent vertex weights V+-: occupation factors left out
       const double v = rp.inv_Nq_pref * (cnt == 1 ? sum : sum / double(cnt));
       Xp[t] = v * gp;

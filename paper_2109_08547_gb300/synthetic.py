@@ -73,6 +73,7 @@ class Workload:
     omega_min_eV: float = 1.0e-4
     degen_tol_eV: float = 1.0e-6
     tol: float = 1.0e-10
+    delta: str = "gauss"           # energy-conserving delta: "gauss" (sigma_eV) or "tetra" (no width)
 
 
 def oh_group() -> np.ndarray:

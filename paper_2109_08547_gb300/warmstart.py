@@ -18,6 +18,15 @@ def _sync():
     torch.cuda.synchronize()
 
 
+def thermo_points(wl, n_train: int, n_held: int, seed: int):
+    """Seeded (T, mu, window) points uniform over T in [100, 500] K and mu in mu0 +- 0.2 eV, all on
+    the workload's window: (training points, held-out points)."""
+    rng = np.random.default_rng(seed)
+    pts = [(float(rng.uniform(100.0, 500.0)), float(wl.mu_eV + rng.uniform(-0.2, 0.2)), float(wl.window[0]),
+            float(wl.window[1])) for _ in range(n_train + n_held)]
+    return pts[:n_train], pts[n_train:]
+
+
 def instance_data(ctx: B.Context, insts, device, targets: bool = True):
     """Features (and targets) of the active states of the given solved instances, stacked on
     the device.  The kernels fill per-instance buffers; the active rows (inactive states have

@@ -710,3 +710,114 @@ def test_cscl8_detailed_balance():
         np.testing.assert_allclose(R.Xp[i] / R.Xm[j], np.exp(beta * x), rtol=1e-9)
         n += 1
     assert n > 500
+
+
+# ------------------------------------------------------------------ tetrahedron delta ([A22])
+
+def test_tetra_corner_weights_closed_forms():
+    """Corner weights of one linear tetrahedron: their sum is the tetrahedron density of
+    states in closed form in each of the three energy ranges (Bloechl's expressions), it
+    integrates to 1 over [e_min, e_max], every corner's weight integrates to 1/4 (the mean of its
+    barycentric coordinate), and its first moment is (e_c + sum_j e_j) / 20 (the mean of
+    lambda_c e over the tetrahedron)."""
+    e = np.array([0.3, -0.2, 1.1, 0.5])
+    es = np.sort(e)
+    e21, e31, e41 = es[1] - es[0], es[2] - es[0], es[3] - es[0]
+    e32, e42, e43 = es[2] - es[1], es[3] - es[1], es[3] - es[2]
+    for E in (-0.1, 0.05, 0.2):
+        np.testing.assert_allclose(O.tetra_corner_weights(e, E).sum(), 3 * (E - es[0]) ** 2 / (e21 * e31 * e41),
+                                   rtol=1e-13)
+    for E in (0.31, 0.4, 0.49):
+        D = (3 * e21 + 6 * (E - es[1]) - 3 * (e31 + e42) * (E - es[1]) ** 2 / (e32 * e42)) / (e31 * e41)
+        np.testing.assert_allclose(O.tetra_corner_weights(e, E).sum(), D, rtol=1e-13)
+    for E in (0.6, 0.9, 1.05):
+        np.testing.assert_allclose(O.tetra_corner_weights(e, E).sum(), 3 * (es[3] - E) ** 2 / (e41 * e42 * e43),
+                                   rtol=1e-13)
+    Es = np.linspace(es[0], es[3], 200001)
+    W = np.array([O.tetra_corner_weights(e, E) for E in Es])
+    h = Es[1] - Es[0]
+    trap = lambda y: h * (y.sum(axis=0) - 0.5 * (y[0] + y[-1]))
+    np.testing.assert_allclose(trap(W).sum(), 1.0, rtol=1e-8)
+    np.testing.assert_allclose(trap(W), 0.25, rtol=1e-7)
+    np.testing.assert_allclose(trap(W * Es[:, None]), (e + e.sum()) / 20.0, rtol=1e-7, atol=1e-9)
+    assert np.all(O.tetra_corner_weights(e, es[0] - 1e-9) == 0) and np.all(O.tetra_corner_weights(e, es[3]) == 0)
+
+
+def test_tetra_point_weights_give_the_density_of_states():
+    """sum_q w(q) over a 12^3 mesh of eps(q) - E, eps the nearest-neighbour band, is the zone
+    average of delta(E - eps): the density of states per cell, here against a histogram of the
+    band on a 240^3 half-shifted mesh (bins of +-0.05 eV) within 3 % (the linear tetrahedron
+    error on the coarse mesh; a wrong normalisation would be off by a factor 4, 6 or N).  The
+    weights are invariant under the cubic operations (four-diagonal average)."""
+    n = 12
+    idx = O.mesh_indices((n, n, n))
+    eps = -2.0 * np.cos(2 * np.pi * idx / n).sum(axis=1)
+    nf = 240
+    c = np.cos(2 * np.pi * (np.arange(nf) + 0.5) / nf)
+    ef = -2.0 * (c[:, None, None] + c[None, :, None] + c[None, None, :])
+    ops = S.oh_group()
+    for E in (-3.1, 0.83):
+        w = O.tetra_point_weights(eps - E, (n, n, n), np.arange(n ** 3))
+        ref = np.count_nonzero(np.abs(ef - E) < 0.05) / (nf ** 3 * 0.1)
+        np.testing.assert_allclose(w.sum(), ref, rtol=0.03)
+        for Sop in ops[::5]:
+            img = O.flat_index(np.mod(idx @ Sop.T, n), (n, n, n))
+            np.testing.assert_allclose(w[img], w, rtol=1e-12, atol=1e-15 * w.max())
+
+
+def test_tetra_rates_ibz_path_equals_full_bz():
+    """Tetrahedron delta on the one-band cubic model: the irreducible-wedge rates and RTA and
+    dragged coefficients equal the full-zone ones (the four-diagonal weights are cubic
+    invariant)."""
+    res = []
+    for full in (True, False):
+        wl = dataclasses.replace(S.workload_sc1(8, nsym_full=full), delta="tetra")
+        P = O.prepare(wl)
+        R = O.transition_rates(P)
+        res.append([O.solve_coupled_bte(P, R, level=lv) for lv in ("rta", "dragged")])
+    for a, b in zip(*res):
+        assert a.converged and b.converged
+        for key in ("sigma", "sigmaS", "alpha_el", "kappa0_el", "alpha_ph", "kappa_ph"):
+            assert np.linalg.norm(a.coeffs[key] - b.coeffs[key]) <= 1e-9 * np.linalg.norm(b.coeffs[key]), key
+
+
+@pytest.mark.parametrize("n_k,n_q", [(8, 8), (8, 4)])
+def test_tetra_rate_sums_equal_brute_force(n_k, n_q):
+    """Rates with the tetrahedron delta on equal and ratio-2 meshes: with the constant coupling
+    of the one-band model (R = 0 only) every irreducible state's summed X+ and X- equal a direct
+    loop over all q of the phonon mesh and the three energy-sorted closed-form branches of
+    (2 pi / hbar) |g_s|^2 f_k (1 - f_k+q) {n, 1+n} w(q), w the tetrahedron weight of q for
+    eps(k + r q') - eps(k) -/+ w_s(q') built from the closed-form band and frequencies (zero below
+    omega_min) -- neither the oracle's bands nor its pair tables.  A wrong 2 pi / hbar, N_q or
+    weight normalisation, or a weight for the wrong point, fails."""
+    wl, g2 = _sc1_r0_workload(n_k, n_q)
+    wl = dataclasses.replace(wl, delta="tetra")
+    P = O.prepare(wl)
+    R = O.transition_rates(P)
+    eps, wq = _sc1_closed(wl)
+    T, mu = wl.T_K, wl.mu_eV
+    kT = O.KB_EVK * T
+    lo, hi = wl.window
+    qall = O.mesh_indices(wl.qmesh)
+    r = n_k // n_q
+    wsorted = np.sort(wq(qall), axis=1)
+    wz = np.where(wsorted > wl.omega_min_eV, wsorted, 0.0)
+    for k in R.ibz_win:
+        ki = P.kidx[k]
+        e = eps(ki)
+        ep = eps(ki[None, :] + r * qall)
+        act = (ep >= lo) & (ep <= hi)
+        f, fp = 1 / (np.exp((e - mu) / kT) + 1), 1 / (np.exp((ep - mu) / kT) + 1)
+        sp = sm = 0.0
+        for s in range(3):
+            wp = O.tetra_point_weights(ep - e - wz[:, s], wl.qmesh, np.arange(len(qall)))
+            wm = O.tetra_point_weights(ep - e + wz[:, s], wl.qmesh, np.arange(len(qall)))
+            ok = act & (wsorted[:, s] > wl.omega_min_eV)
+            w = wsorted[ok, s]
+            n = 1.0 / np.expm1(w / kT)
+            base = (2 * np.pi / HB) * g2 * (wl.model.omega_ref_eV / w) * f * (1 - fp[ok])
+            sp += np.sum(base * n * wp[ok])
+            sm += np.sum(base * (1 + n) * wm[ok])
+        sel = R.ik == k
+        np.testing.assert_allclose(R.Xp[sel].sum(), sp, rtol=1e-10)
+        np.testing.assert_allclose(R.Xm[sel].sum(), sm, rtol=1e-10)
