@@ -87,8 +87,12 @@ def parse():
     p.add_argument("--no-variants", action="store_true", help="skip the one-step timings of the other modes")
     p.add_argument("--accel", type=int, default=0,
                    help="Anderson history depth of the outer iteration (0: the plain iteration)")
-    p.add_argument("--instances", type=int, default=8,
+    p.add_argument("--instances", type=int, default=32,
                    help="(T, mu, window) instances of the batched-vs-sequential comparison (0: skip it)")
+    p.add_argument("--batch-nk", type=int, default=48, help="k mesh of the batched comparison (4-band model)")
+    p.add_argument("--batch-nq", type=int, default=24, help="q mesh of the batched comparison")
+    p.add_argument("--seq-sample", type=int, default=4,
+                   help="instances of the sequential plain-FP64 baseline actually run (the rest extrapolated)")
     p.add_argument("--warm-train", type=int, default=200,
                    help="(T, mu) training points of the learned-warm-start report (0: skip it)")
     p.add_argument("--warm-held", type=int, default=40, help="held-out points of the learned-warm-start report")
@@ -230,60 +234,66 @@ def oracle_sample(P, row, n_pairs=None):
 
 
 def batched_block(B, ctx, wl, args, flush, torch, np):
-    """The batched form against sequential plain FP64 runs on the same meshes.
+    """The batched form (32 (T, mu, window) instances of the 4-band model on 48^3 k / 24^3 q, the
+    union window mu0 +- 0.45 eV) against sequential plain FP64 runs.
 
     Instances: synthetic.instance_grid (T in [100, 500] K, mu0 +- 0.2 eV, windows mu +- 0.25 eV).
-    Sequential: for each instance the whole FP64 path on its own window (meshes, rates, solve,
-    coefficients).  Batched: meshes on the union window, one rates call for all instances in
-    this run's precision (the vertex interpolated once), one solve, the coefficients.  Both are
-    wall times between device synchronisations; errors are per-coefficient relative Frobenius
-    differences of the batched result from the sequential FP64 one."""
+    Sequential: for each instance the whole plain FP64 path on its own window (meshes, FP64
+    vertex, plain FP64 iteration, coefficients); args.seq_sample instances spread over the grid
+    are run and the total is extrapolated to all instances (stated in the block).  Batched:
+    meshes on the union window, one rates call for all instances (the vertex interpolated
+    once), one solve, the coefficients.  Both are wall times between device synchronisations;
+    errors are per-coefficient relative Frobenius differences of the batched result from the
+    sequential FP64 one on the sampled instances."""
     import dataclasses
     from paper_2109_08547_gb300 import synthetic as S
     insts = S.instance_grid(args.instances, wl.mu_eV)
-    B.set_wannier_model(ctx, wl.model)
     union = (min(i[2] for i in insts), max(i[3] for i in insts))
-    seq_coeffs, seq_s = [], 0.0
-    for T, mu, lo, hi in insts:
+    B.set_wannier_model(ctx, wl.model)
+    pick = sorted(set(int(round(x)) for x in np.linspace(0, len(insts) - 1, args.seq_sample)))
+    seq_coeffs, seq_times = {}, []
+    for j in pick:
+        T, mu, lo, hi = insts[j]
         w1 = dataclasses.replace(wl, T_K=T, mu_eV=mu, window=(lo, hi))
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        r = B.run_path(ctx, w1, level="dragged", ko_correction=True, precision=B.FP64)
+        r = B.run_path(ctx, w1, level="dragged", ko_correction=True, precision=B.FP64, tol=args.tol)
         torch.cuda.synchronize()
-        seq_s += time.perf_counter() - t0
-        seq_coeffs.append(r.coeffs)
+        seq_times.append(time.perf_counter() - t0)
+        seq_coeffs[j] = r.coeffs
+    seq_s = statistics.mean(seq_times) * len(insts)
 
     def batched_run(prec, solve_prec):
-        B.build_meshes_ibz(ctx, wl.kmesh, wl.qmesh, union, wl.degen_tol_eV, wl.omega_min_eV)
+        mesh = B.build_meshes_ibz(ctx, wl.kmesh, wl.qmesh, union, wl.degen_tol_eV, wl.omega_min_eV)
         rates = B.compute_transition_rates(ctx, 0.0, 0.0, wl.sigma_eV, wl.cutoff_sigmas, B.PRECISIONS[prec],
                                            instances=insts)
-        solve = B.solve_coupled_bte(ctx, "dragged", wl.tol, solve_precision=solve_prec, accel=args.accel)
-        return rates, solve, [B.transport_coefficients(ctx, i) for i in range(len(insts))]
+        solve = B.solve_coupled_bte(ctx, "dragged", args.tol, solve_precision=solve_prec)
+        return mesh, rates, solve, [B.transport_coefficients(ctx, i) for i in range(len(insts))]
 
-    out = {"workload": wl.name, "instances": len(insts), "union_window_eV": list(union), "T_K_range": [100.0, 500.0],
-           "s_sequential_fp64": seq_s}
-    # FP64-grade batch (exact-slice vertex, FP64 iteration) and mixed batch (split-BF16 vertex,
-    # mixed-precision iteration)
-    for tag, prec, sp in (("fp64_grade", args.precision, "fp64"), ("mixed", "split-bf16", "mixed")):
-        flush.zero_()
-        batched_run(prec, sp)             # warm-up (allocations, tile tuning)
+    out = {"workload": wl.name, "instances": len(insts), "rhs": 2 * len(insts), "union_window_eV": list(union),
+           "T_K_range": [100.0, 500.0], "tol": args.tol,
+           "s_sequential_fp64": seq_s, "sequential_measured": len(pick),
+           "sequential_note": f"plain FP64 path timed on {len(pick)} instances spread over the grid "
+                              f"(mean {statistics.mean(seq_times):.3f} s), times {len(insts)}"}
+    for tag, prec, sp in (("fp64_grade", "fp64-sliced", "fp64"), ("mixed", "split-bf16", "mixed")):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rates, solve, coeffs = batched_run(prec, sp)
+        mesh, rates, solve, coeffs = batched_run(prec, sp)
         torch.cuda.synchronize()
         bat_s = time.perf_counter() - t0
         worst = {}
-        for c, ref in zip(coeffs, seq_coeffs):
+        for j, ref in seq_coeffs.items():
             for key, v in ref.items():
                 nrm = float(np.linalg.norm(v))
-                e = float(np.linalg.norm(c[key] - v) / nrm) if nrm > 0 else 0.0
+                e = float(np.linalg.norm(coeffs[j][key] - v) / nrm) if nrm > 0 else 0.0
                 worst[key] = max(worst.get(key, 0.0), e)
         out[tag] = {"vertex_precision": prec, "solve_precision": sp, "s_batched": bat_s,
                     "speedup_vs_sequential_fp64": seq_s / bat_s, "rates_ms": rates["ms"], "solve_ms": solve["ms"],
                     "fp64_sweeps": solve["n_sweeps"], "fp32_sweeps": solve["n_sweeps32"],
-                    "union_tuples": rates["n_tuples"], "converged": solve["converged"],
+                    "union_pairs": mesh["n_pairs"], "union_tuples": rates["n_tuples"],
+                    "union_entries": rates["n_entries"], "converged": solve["converged"],
                     "max_coeff_rel_err_vs_sequential_fp64": worst}
     return out
 
@@ -659,7 +669,9 @@ def main():
     if args.instances > 0:
         from paper_2109_08547_gb300 import synthetic as S
         with B.Context(local, stream=stream.cuda_stream) as bctx:
-            batched = batched_block(B, bctx, S.workload_cscl4(24), args, flush, torch, np)
+            bwl = dataclasses.replace(S.workload_cscl4(args.batch_nk), qmesh=(args.batch_nq,) * 3,
+                                      name=f"cscl4-{args.batch_nk}^3/{args.batch_nq}^3")
+            batched = batched_block(B, bctx, bwl, args, flush, torch, np)
     warm = warm_block(B, wl, args, torch, np) if args.warm_train > 0 else None
 
     cpu = None

@@ -400,6 +400,12 @@ typedef enum {
  * EPHB_ETIMEOUT with the context still usable.  It exists to check that failure path; value 0
  * restores normal operation. */
 #define EPHB_TUNE_WITHHOLD_MMA 1
+/* EPHB_TUNE_DEFER_INSTANCES, value 1: with several instances, compute_transition_rates keeps the
+ * union lists only and every instance derives its own lists when the solve reaches it, releasing
+ * them (and its sweep arrays) after its solve; the responses, RTA rates and coefficient inputs
+ * stay.  This is what the library does by itself when the instances' lists would exceed half of
+ * the free device memory; the key forces it (the results are the same).  Value 0: automatic. */
+#define EPHB_TUNE_DEFER_INSTANCES 2
 ephb_status ephb_set_tuning(ephb_ctx *ctx, int key, int value);
 
 /* Make instance inst the one whose arrays the views and copies below return (and the one

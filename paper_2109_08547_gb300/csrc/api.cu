@@ -110,7 +110,24 @@ struct InstState {
   bool have_f32 = false;
   DBuf<unsigned> vmaxb;
   bool bte_ready = false, has_warm = false, solved = false;
+  bool lists_pending = false;   // the instance's lists are to be derived from the union lists
   ephb_solve_info last{};       // the instance's last solve
+
+  // after a deferred instance's solve: the lists and the sweep arrays go, the responses, the
+  // RTA rates and the state tables (the coefficients' inputs) stay
+  void release_lists() {
+    row_ptr.release(); ph_row_ptr.release(); e_kpns.release(); ph_kpn.release(); e_X.release(); ph_st.release();
+    ph_Y.release();
+    seg_part.release(); Dterm.release(); run_w.release(); I2.release(); J2.release(); Btv.release();
+    nseg_row.release(); eseg_row.release(); rseg_row.release(); run_flag.release(); eseg_ptr.release();
+    eseg_begin.release(); rseg_ptr.release(); rseg_begin.release(); run_ptr.release(); run_idx.release();
+    run_col.release();
+    for (auto *b : {&run_w32, &rI, &rJ, &dI, &dJ, &dI2, &dJ2, &part32}) b->release();
+    IJ.release();
+    IJ2.release();
+    have_f32 = false;
+    lists_pending = true;
+  }
 
   void release_all() {
     row_ptr.release(); ph_row_ptr.release(); e_kpns.release(); ph_kpn.release(); e_X.release(); ph_st.release();
@@ -127,7 +144,7 @@ struct InstState {
     IJ.release();
     IJ2.release();
     fuse_ctr.release();
-    bte_ready = has_warm = solved = have_f32 = false;
+    bte_ready = has_warm = solved = have_f32 = lists_pending = false;
   }
 };
 
@@ -187,7 +204,8 @@ struct ephb_ctx : InstState {
   DBuf<unsigned long long> ucount;
 
   // T-independent vertex lists over the union of the instance windows (several instances)
-  int64_t u_entries = 0, u_ph_entries = 0;
+  int64_t u_entries = 0, u_ph_entries = 0, u_tuples = 0;
+  bool deferred = false;        // instances derive their lists when solved (memory bound)
   DBuf<int64_t> u_row_ptr, u_ph_row_ptr;
   DBuf<uint32_t> u_kpns, u_ph_kpn;
   DBuf<double2> u_X;
@@ -213,6 +231,7 @@ struct ephb_ctx : InstState {
   int tune_st[3] = {2, 2, 2};
   int force_cols = 0;
   int withhold_mma = 0;   // failure-path check (EPHB_TUNE_WITHHOLD_MMA)
+  int force_defer = 0;    // EPHB_TUNE_DEFER_INSTANCES: derive instance lists at solve time always
   double *host_res = nullptr;   // pinned: kResLen doubles, then the sweep-loop control (4 ints)
 };
 
@@ -694,8 +713,49 @@ void set_instances(ephb_ctx *ctx, int n) {
 
 // The lists just computed (vertex-only) become the union lists; each instance then takes the
 // entries of its window with its occupation factors.
-ephb_status derive_instances(ephb_ctx *ctx, const ephb_thermo *inst, int ninst) {
+// The lists of the instance in the base from the union lists: its window, T and mu are set.
+ephb_status derive_one(ephb_ctx *ctx) {
   cudaStream_t st = ctx->stream;
+  const ModelDev &M = ctx->M;
+  const int64_t nst = ctx->n_ibzw * M.nb, nph = ctx->qm.size() * M.nbr;
+  ctx->n_tuples = ctx->u_tuples;
+  ctx->bte_ready = false;
+  MeshDev D = mesh_view(ctx);
+  const InstWindow w{ctx->win_lo, ctx->win_hi};
+  CK(launch_epi_tables(M, D, ctx->T, ctx->mu, ctx->fk.p, ctx->nbq.p, ctx->wr.p, ctx->ut.p, st));
+  CK(launch_inst_count(M, D, w, ctx->u_row_ptr.p, ctx->u_kpns.p, ctx->u_ph_row_ptr.p, ctx->u_ph_st.p,
+                       ctx->u_ph_kpn.p, ctx->cntE.p, ctx->cntPh.p, st));
+  CK(ctx->row_ptr.ensure(nst + 1));
+  CK(ctx->ph_row_ptr.ensure(nph + 1));
+  CK(exclusive_scan<int>(ctx->cntE.p, ctx->row_ptr.p, nst, ctx->scal.p + 3, ctx->scratch.p, ctx->scratch.n, st));
+  CK(exclusive_scan<int>(ctx->cntPh.p, ctx->ph_row_ptr.p, nph, ctx->scal.p + 4, ctx->scratch.p, ctx->scratch.n,
+                         st));
+  CK(cudaMemcpyAsync(ctx->row_ptr.p + nst, ctx->scal.p + 3, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(ctx->ph_row_ptr.p + nph, ctx->scal.p + 4, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+  int64_t hs[2];
+  CK(cudaMemcpyAsync(hs, ctx->scal.p + 3, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  ctx->n_entries = hs[0];
+  ctx->n_ph_entries = hs[1];
+  CK(ctx->e_kpns.ensure(ctx->n_entries));
+  CK(ctx->e_X.ensure(ctx->n_entries));
+  CK(ctx->ph_st.ensure(ctx->n_ph_entries));
+  CK(ctx->ph_kpn.ensure(ctx->n_ph_entries));
+  CK(ctx->ph_Y.ensure(ctx->n_ph_entries));
+  CK(launch_inst_fill(M, D, w, ctx->fk.p, ctx->nbq.p, ctx->u_row_ptr.p, ctx->u_kpns.p, ctx->u_X.p,
+                      ctx->u_ph_row_ptr.p, ctx->u_ph_st.p, ctx->u_ph_kpn.p, ctx->u_ph_V.p, ctx->row_ptr.p,
+                      ctx->ph_row_ptr.p, ctx->e_kpns.p, ctx->e_X.p, ctx->ph_st.p, ctx->ph_kpn.p, ctx->ph_Y.p, st));
+  ctx->lists_pending = false;
+  return EPHB_OK;
+}
+
+// The lists just computed (vertex-only) become the union lists; each instance then takes the
+// entries of its window with its occupation factors.  When the instances' lists together would
+// not fit the free device memory (the union lists x the instance count, with the solve's
+// working arrays), each instance keeps only its window, T and mu here and derives its lists
+// when it is solved; after its solve the lists and sweep arrays are released again (the
+// responses, rates and coefficient inputs stay).
+ephb_status derive_instances(ephb_ctx *ctx, const ephb_thermo *inst, int ninst) {
   const ModelDev &M = ctx->M;
   const int64_t nst = ctx->n_ibzw * M.nb, nph = ctx->qm.size() * M.nbr;
   std::swap(ctx->u_row_ptr, ctx->row_ptr);
@@ -707,7 +767,7 @@ ephb_status derive_instances(ephb_ctx *ctx, const ephb_thermo *inst, int ninst) 
   std::swap(ctx->u_ph_V, ctx->ph_Y);
   ctx->u_entries = ctx->n_entries;
   ctx->u_ph_entries = ctx->n_ph_entries;
-  const int64_t n_tuples = ctx->n_tuples;
+  ctx->u_tuples = ctx->n_tuples;
   CK(ctx->cntE.ensure(nst > 0 ? nst : 1));
   CK(ctx->cntPh.ensure(nph > 0 ? nph : 1));
   CK(ctx->scratch.ensure(scan_scratch_elems(nst > nph ? nst : nph)));
@@ -715,6 +775,11 @@ ephb_status derive_instances(ephb_ctx *ctx, const ephb_thermo *inst, int ninst) 
   CK(ctx->nbq.ensure(size_t(nph)));
   CK(ctx->wr.ensure(size_t(nph)));
   CK(ctx->ut.ensure(size_t(nph) * M.nbr));
+  // lists (20 B per electron entry, 16 B per phonon entry) and sweep arrays (~28 B per entry)
+  size_t free_b = 0, total_b = 0;
+  CK(cudaMemGetInfo(&free_b, &total_b));
+  const double per_inst = 48.0 * double(ctx->u_entries) + 24.0 * double(ctx->u_ph_entries);
+  const bool defer = ninst > 1 && (ctx->force_defer || double(ninst) * per_inst > 0.5 * double(free_b));
   for (int i = 0; i < ninst; ++i) {
     select_instance(ctx, i);
     ctx->T = inst[i].T_K;
@@ -722,34 +787,15 @@ ephb_status derive_instances(ephb_ctx *ctx, const ephb_thermo *inst, int ninst) 
     const bool own = inst[i].window_lo_eV < inst[i].window_hi_eV;
     ctx->win_lo = own ? std::max(inst[i].window_lo_eV, ctx->lo) : ctx->lo;
     ctx->win_hi = own ? std::min(inst[i].window_hi_eV, ctx->hi) : ctx->hi;
-    ctx->n_tuples = n_tuples;
+    ctx->n_tuples = ctx->u_tuples;
     ctx->bte_ready = false;
-    MeshDev D = mesh_view(ctx);
-    const InstWindow w{ctx->win_lo, ctx->win_hi};
-    CK(launch_epi_tables(M, D, ctx->T, ctx->mu, ctx->fk.p, ctx->nbq.p, ctx->wr.p, ctx->ut.p, st));
-    CK(launch_inst_count(M, D, w, ctx->u_row_ptr.p, ctx->u_kpns.p, ctx->u_ph_row_ptr.p, ctx->u_ph_st.p,
-                         ctx->u_ph_kpn.p, ctx->cntE.p, ctx->cntPh.p, st));
-    CK(ctx->row_ptr.ensure(nst + 1));
-    CK(ctx->ph_row_ptr.ensure(nph + 1));
-    CK(exclusive_scan<int>(ctx->cntE.p, ctx->row_ptr.p, nst, ctx->scal.p + 3, ctx->scratch.p, ctx->scratch.n, st));
-    CK(exclusive_scan<int>(ctx->cntPh.p, ctx->ph_row_ptr.p, nph, ctx->scal.p + 4, ctx->scratch.p, ctx->scratch.n,
-                           st));
-    CK(cudaMemcpyAsync(ctx->row_ptr.p + nst, ctx->scal.p + 3, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(ctx->ph_row_ptr.p + nph, ctx->scal.p + 4, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
-    int64_t hs[2];
-    CK(cudaMemcpyAsync(hs, ctx->scal.p + 3, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    ctx->n_entries = hs[0];
-    ctx->n_ph_entries = hs[1];
-    CK(ctx->e_kpns.ensure(ctx->n_entries));
-    CK(ctx->e_X.ensure(ctx->n_entries));
-    CK(ctx->ph_st.ensure(ctx->n_ph_entries));
-    CK(ctx->ph_kpn.ensure(ctx->n_ph_entries));
-    CK(ctx->ph_Y.ensure(ctx->n_ph_entries));
-    CK(launch_inst_fill(M, D, w, ctx->fk.p, ctx->nbq.p, ctx->u_row_ptr.p, ctx->u_kpns.p, ctx->u_X.p,
-                        ctx->u_ph_row_ptr.p, ctx->u_ph_st.p, ctx->u_ph_kpn.p, ctx->u_ph_V.p, ctx->row_ptr.p,
-                        ctx->ph_row_ptr.p, ctx->e_kpns.p, ctx->e_X.p, ctx->ph_st.p, ctx->ph_kpn.p, ctx->ph_Y.p, st));
+    ctx->lists_pending = true;
+    if (!defer) {
+      ephb_status r = derive_one(ctx);
+      if (r != EPHB_OK) return r;
+    }
   }
+  ctx->deferred = defer;
   select_instance(ctx, 0);
   return EPHB_OK;
 }
@@ -788,6 +834,7 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
   // several instances (or a window narrower than the meshes'): one T-independent vertex pass
   // over the mesh window, then the rate lists of every instance from it
   const bool multi = ninst > 1 || windowed;
+  ctx->deferred = false;
   set_instances(ctx, ninst);
   ctx->T = inst->T_K;
   ctx->mu = inst->mu_eV;
@@ -1592,6 +1639,10 @@ ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb
   bool noconv = false;
   for (int i = 0; i < ctx->ninst; ++i) {
     select_instance(ctx, i);
+    if (ctx->lists_pending) {
+      ephb_status d = derive_one(ctx);
+      if (d != EPHB_OK) return d;
+    }
     ephb_solve_info one{};
     ephb_status r = solve_one(ctx, o, &one);
     if (r == EPHB_ENOCONV && o->warm_start && ctx->has_warm) {
@@ -1608,6 +1659,10 @@ ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb
     if (r != EPHB_OK && r != EPHB_ENOCONV) return r;
     noconv = noconv || r == EPHB_ENOCONV;
     ctx->last = one;
+    if (ctx->deferred) {
+      CK(cudaStreamSynchronize(ctx->stream));
+      ctx->release_lists();
+    }
     sum.outer_iters = std::max(sum.outer_iters, one.outer_iters);
     sum.inner_iters_total += one.inner_iters_total;
     sum.converged = sum.converged && one.converged;
@@ -1665,6 +1720,10 @@ ephb_status ephb_state_features(ephb_ctx *ctx, int inst, float *feat_dev, int64_
   if (n_states != ctx->n_ibzw * ctx->M.nb) return fail(ctx, EPHB_EINVAL, "n_states must be ephb_num_states()");
   CK(cudaSetDevice(ctx->device));
   select_instance(ctx, inst);
+  if (ctx->lists_pending) {
+    ephb_status d = derive_one(ctx);
+    if (d != EPHB_OK) return d;
+  }
   if (!ctx->bte_ready) {
     ephb_status s = bte_setup(ctx);
     if (s != EPHB_OK) return s;
@@ -1718,6 +1777,10 @@ ephb_status ephb_set_tuning(ephb_ctx *ctx, int key, int value) {
   if (!ctx) return EPHB_EINVAL;
   if (key == EPHB_TUNE_WITHHOLD_MMA) {
     ctx->withhold_mma = value ? 1 : 0;
+    return EPHB_OK;
+  }
+  if (key == EPHB_TUNE_DEFER_INSTANCES) {
+    ctx->force_defer = value ? 1 : 0;
     return EPHB_OK;
   }
   if (key != EPHB_TUNE_TC_COLS) return fail(ctx, EPHB_EINVAL, "unknown tuning key");

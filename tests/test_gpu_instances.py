@@ -112,3 +112,30 @@ def test_shared_vertex_equals_direct_path():
             g2 = B.transport_coefficients(c2, i)
             for key in TENSORS:
                 assert rel_fro(g2[key], g1[key]) <= 1e-10, key
+
+
+def test_deferred_instances_give_the_same_answers(batched, standalone):
+    """Instances whose lists are derived only when the solve reaches them (what the library does
+    when all instances' lists would not fit the device memory; forced here): every instance's
+    coefficients bit-identical to the eagerly derived ones and within 1e-8 of the oracle on the
+    instance alone; a second solve (lists derived again) and the warm-start features still work."""
+    wl = batched["wl"]
+    with B.Context(0) as ctx:
+        B.set_wannier_model(ctx, wl.model)
+        B.set_tuning(ctx, B.TUNE_DEFER_INSTANCES, 1)
+        B.build_meshes_ibz(ctx, wl.kmesh, wl.qmesh, wl.window, wl.degen_tol_eV, wl.omega_min_eV)
+        B.compute_transition_rates(ctx, 0.0, 0.0, wl.sigma_eV, wl.cutoff_sigmas, instances=INSTANCES)
+        B.solve_coupled_bte(ctx, "dragged", wl.tol)
+        for i, (_, _, _, ref) in enumerate(standalone):
+            c = B.transport_coefficients(ctx, i)
+            for key in TENSORS:
+                np.testing.assert_array_equal(c[key], batched["coeffs"][i][key])
+                assert rel_fro(c[key], ref.coeffs[key]) <= COEFF_RTOL, (i, key)
+        again = B.solve_coupled_bte(ctx, "dragged", wl.tol)
+        assert again["converged"] == 1
+        np.testing.assert_array_equal(B.transport_coefficients(ctx, 1)["sigma"], batched["coeffs"][1]["sigma"])
+        import torch
+        f = torch.empty((B.num_states(ctx), B.NFEAT), dtype=torch.float32, device="cuda")
+        B.state_features(ctx, 2, f.data_ptr())
+        torch.cuda.synchronize()
+        assert torch.isfinite(f).all()
