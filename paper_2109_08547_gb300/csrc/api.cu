@@ -983,10 +983,9 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
       const int64_t na = a_end - a0;
       CK(ta.start(st));
       if (tensor_a) {
-        const int width_a = ctx->force_cols ? std::min(ctx->force_cols, tc_nc_max(ns_a)) : tc_nc_max(ns_a);
         CK(launch_stage_a_tc(M, D, ns_a, a0, na, ctx->phik.p, ctx->gslices.p, ctx->gscale.p, ctx->Tbuf.p,
-                             ctx->tc_err.p, width_a, st, &tensor_flops_a));
-        CK(launch_stage_a2(M, D, a0, na, ctx->Tbuf.p, ctx->Abuf.p, st));
+                             ctx->tc_err.p, st, &tensor_flops_a));
+        CK(launch_stage_a2(M, D, a0, na, ctx->Tbuf.p, ctx->Abuf.p, true, st));
       } else {
         CK(launch_stage_a(M, D, a0, na, ctx->Tbuf.p, ctx->Abuf.p, st));
       }

@@ -144,17 +144,20 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
                              int64_t ws_cap);
 // ws_desc: scratch of 4 int64 per work item (descriptors of the persistent form), ws_cap items
 // Stage A on tensor cores: T[kc][col] = sum_Re e^{ik.Re} g[Re][col] for the k of a chunk, as
-// the same exact-slice GEMM with the k phase slices as rows and the model's g slices (made
-// once by launch_g_slices, [ns][tc_ncols_a][tc_kp_a] BF16 + column scales) as B.
+// the same exact-slice GEMM with the model's g slices (made once by launch_g_slices,
+// [ns][tc_ncols_a][tc_kp_a] BF16 + column scales) as the rows and the k phase slices as the
+// columns.  ns: 7 or 8.  T is written as float-float pairs (two FP32 numbers per real value,
+// in the place of one double), read by launch_stage_a2 with t_ff set.
 int tc_kp_a(const ModelDev &M);
 int tc_ncols_a(const ModelDev &M);
 cudaError_t launch_g_slices(const ModelDev &M, int ns, __nv_bfloat16 *gs, double *gscale, cudaStream_t st);
 cudaError_t launch_stage_a_tc(const ModelDev &M, const MeshDev &D, int ns, int64_t i0, int64_t nkc,
                               __nv_bfloat16 *phik, const __nv_bfloat16 *gs, const double *gscale, double2 *T, int *err,
-                              int ncm, cudaStream_t st, double *flops_acc);
-// The band rotation of stage A: A[kc][rp][(m,n',a)] = sum_m' c_{m'm}(k) T[kc][rp][m'][n'][a].
+                              cudaStream_t st, double *flops_acc);
+// The band rotation of stage A: A[kc][rp][(m,n',a)] = sum_m' c_{m'm}(k) T[kc][rp][m'][n'][a]
+// (T in FP64, or as float-float pairs when t_ff).
 cudaError_t launch_stage_a2(const ModelDev &M, const MeshDev &D, int64_t i0, int64_t nkc, const double2 *T, double2 *A,
-                            cudaStream_t st);
+                            bool t_ff, cudaStream_t st);
 // Tile shape of the contraction: column-chunk width and K per shared-memory stage (16: two CTAs
 // per SM).  The result does not depend on it: every column is summed in the same order.
 struct TcShape {

@@ -343,6 +343,8 @@ __global__ void __launch_bounds__(256) k_stage_a1(ModelDev M, MeshDev D, int64_t
 // A[kc][rp][j], j = ml*(nb*nbr) + n'*nbr + a over the rotation bands m of k (the active bands
 // and their degenerate partners):
 //   A = sum_m' c_{m'm}(k) T[kc][rp][m'][n'][a]
+// FF: T holds float-float pairs (hi, lo) per real value, each read as the FP64 value hi + lo.
+template <bool FF>
 __global__ void k_stage_a2(ModelDev M, MeshDev D, int64_t i0, int64_t nkc, const double2 *T, double2 *A) {
   const int nb = M.nb, nbr = M.nbr;
   const int64_t jmax = int64_t(nb) * nb * nbr;
@@ -357,9 +359,19 @@ __global__ void k_stage_a2(ModelDev M, MeshDev D, int64_t i0, int64_t nkc, const
   double2 acc = cmk(0, 0);
   if (ml < __popc(rm)) {
     int m = nth_bit(rm, ml);
-    const double2 *Tk = T + kc * per_k + int64_t(rp) * jmax;
+    const int64_t t0 = kc * per_k + int64_t(rp) * jmax;
     const double2 *ck = D.cvec + size_t(k) * nb * nb;
-    for (int mp = 0; mp < nb; ++mp) cfma(acc, ck[mp * nb + m], Tk[mp * nb * nbr + na]);
+    for (int mp = 0; mp < nb; ++mp) {
+      const int64_t idx = t0 + mp * nb * nbr + na;
+      double2 tv;
+      if (FF) {
+        const float4 f = reinterpret_cast<const float4 *>(T)[idx];
+        tv = cmk(double(f.x) + double(f.y), double(f.z) + double(f.w));
+      } else {
+        tv = T[idx];
+      }
+      cfma(acc, ck[mp * nb + m], tv);
+    }
   }
   A[t] = acc;
 }
@@ -935,15 +947,18 @@ cudaError_t launch_stage_a(const ModelDev &M, const MeshDev &D, int64_t i0, int6
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int64_t n2 = nkc * ncol;
-  EPHB_LAUNCH(k_stage_a2, unsigned((n2 + 255) / 256), 256, 0, st, M, D, i0, nkc, T, A);
+  EPHB_LAUNCH(k_stage_a2<false>, unsigned((n2 + 255) / 256), 256, 0, st, M, D, i0, nkc, T, A);
   return cudaGetLastError();
 }
 
 cudaError_t launch_stage_a2(const ModelDev &M, const MeshDev &D, int64_t i0, int64_t nkc, const double2 *T, double2 *A,
-                            cudaStream_t st) {
+                            bool t_ff, cudaStream_t st) {
   const int64_t n2 = nkc * int64_t(M.nRgp) * M.nb * M.nb * M.nbr;
   if (n2 == 0) return cudaSuccess;
-  EPHB_LAUNCH(k_stage_a2, unsigned((n2 + 255) / 256), 256, 0, st, M, D, i0, nkc, T, A);
+  if (t_ff)
+    EPHB_LAUNCH(k_stage_a2<true>, unsigned((n2 + 255) / 256), 256, 0, st, M, D, i0, nkc, T, A);
+  else
+    EPHB_LAUNCH(k_stage_a2<false>, unsigned((n2 + 255) / 256), 256, 0, st, M, D, i0, nkc, T, A);
   return cudaGetLastError();
 }
 

@@ -403,22 +403,17 @@ __device__ __forceinline__ void store_ff16(const float *s, const float *e, const
     }
 }
 
-// Rows of a contraction: (k,q) pairs of each k (stage B: A rows are the phase slices of the
-// pair's q, B and the column scales belong to the pair's k) or k points of a chunk (stage A:
-// A rows are the k phase slices, B = the model's g slices shared by every k).
-enum { kRowsPairs = 0, kRowsK = 1 };
-
 struct TcParams {
   int ns, nacc, Kp, Nmax, nc_max;   // Nmax: B rows per slice (columns of the real GEMM)
   int64_t i0, nkc, pair_base;       // stage B: first pair of the chunk
-  int ncols, out_stride;            // stage A: live columns and the output row stride (doubles)
+  int ncols, out_stride;            // stage A: live columns and the output row stride (float2)
   int withhold;                     // failure-path check: issue no MMA (so no barrier completes)
 };
 
 // KC: K per shared-memory stage (32: one CTA per SM; 16: two CTAs per SM share the SM's
 // shared memory and tensor memory, one's epilogue overlapping the other's products).
 // ST: shared-memory stages (copies run up to ST - 1 K blocks ahead of the MMAs).
-template <int NS, int NACC, int ROWS, int KC, int ST>
+template <int NS, int NACC, int KC, int ST>
 __global__ void __launch_bounds__(kTcThreads, (KC == 16 && ST == 2) ? 2 : 1) k_vertex_gemm(ModelDev M, MeshDev D, TcParams P,
                                                                const int64_t *__restrict__ item_ptr,
                                                                const __nv_bfloat16 *__restrict__ phis,
@@ -437,46 +432,30 @@ __global__ void __launch_bounds__(kTcThreads, (KC == 16 && ST == 2) ? 2 : 1) k_v
   const __nv_bfloat16 *bsk;      // B slices of this item
   const double *sc;              // column scales from n0
   double *crow;                  // this thread's output row from n0
-  if (ROWS == kRowsPairs) {
-    // which (k, 128-pair tile, column chunk)
-    int64_t lo = 0, hi = P.nkc;
-    while (hi - lo > 1) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (item_ptr[mid] <= item) lo = mid; else hi = mid;
-    }
-    const int64_t kc = lo;
-    const int64_t i = P.i0 + kc;
-    const int k = D.ibzw_list[i];
-    const int nk = round_up(2 * __popc(D.rmask[k]) * M.nb * M.nbr, 16);
-    const int nch = (nk + P.nc_max - 1) / P.nc_max;
-    nc = round_up((nk + nch - 1) / nch, 16);                   // balanced chunk width
-    const int64_t local = item - item_ptr[kc];
-    const int tile = int(local / nch), chunk = int(local % nch);
-    n0 = chunk * nc;
-    ncw = nk - n0 < nc ? nk - n0 : nc;                        // columns of this chunk (multiple of 16)
-    const int64_t p0 = D.pair_ptr[i];
-    const int64_t npl = D.pair_ptr[i + 1] - p0;
-    const int64_t t0 = int64_t(tile) * kTcM;
-    npt = int(npl - t0 < kTcM ? npl - t0 : kTcM);
-    a_row = tid < npt ? D.pair_q[p0 + t0 + tid] : -1;
-    bsk = bs + size_t(kc) * NS * P.Nmax * P.Kp;
-    sc = bscale + kc * P.Nmax + n0;
-    crow = Cbuf + (p0 + t0 + tid - P.pair_base) * P.Nmax + n0;
-  } else {
-    // which (128-k tile, column chunk)
-    const int nch = (P.Nmax + P.nc_max - 1) / P.nc_max;
-    nc = round_up((P.Nmax + nch - 1) / nch, 16);
-    const int tile = int(item / nch), chunk = int(item % nch);
-    n0 = chunk * nc;
-    ncw = P.Nmax - n0 < nc ? P.Nmax - n0 : nc;
-    const int64_t t0 = int64_t(tile) * kTcM;
-    npt = int(P.nkc - t0 < kTcM ? P.nkc - t0 : kTcM);
-    a_row = tid < npt ? int(t0 + tid) : -1;
-    bsk = bs;
-    sc = bscale + n0;
-    crow = Cbuf + (t0 + tid) * P.out_stride + n0;
+  // which (k, 128-pair tile, column chunk)
+  int64_t lo = 0, hi = P.nkc;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (item_ptr[mid] <= item) lo = mid; else hi = mid;
   }
-
+  const int64_t kc = lo;
+  const int64_t i = P.i0 + kc;
+  const int k = D.ibzw_list[i];
+  const int nk = round_up(2 * __popc(D.rmask[k]) * M.nb * M.nbr, 16);
+  const int nch = (nk + P.nc_max - 1) / P.nc_max;
+  nc = round_up((nk + nch - 1) / nch, 16);                   // balanced chunk width
+  const int64_t local = item - item_ptr[kc];
+  const int tile = int(local / nch), chunk = int(local % nch);
+  n0 = chunk * nc;
+  ncw = nk - n0 < nc ? nk - n0 : nc;                        // columns of this chunk (multiple of 16)
+  const int64_t p0 = D.pair_ptr[i];
+  const int64_t npl = D.pair_ptr[i + 1] - p0;
+  const int64_t t0 = int64_t(tile) * kTcM;
+  npt = int(npl - t0 < kTcM ? npl - t0 : kTcM);
+  a_row = tid < npt ? D.pair_q[p0 + t0 + tid] : -1;
+  bsk = bs + size_t(kc) * NS * P.Nmax * P.Kp;
+  sc = bscale + kc * P.Nmax + n0;
+  crow = Cbuf + (p0 + t0 + tid - P.pair_base) * P.Nmax + n0;
   // ST shared-memory stages, each NS x [128 x KC] (A) followed by NS x [nc_max x KC] (B)
   const size_t a_slice = size_t(kTcM) * KC * 2, b_slice = size_t(P.nc_max) * KC * 2;
   const size_t stage_bytes = size_t(NS) * (a_slice + b_slice);
@@ -588,45 +567,13 @@ __global__ void __launch_bounds__(kTcThreads, (KC == 16 && ST == 2) ? 2 : 1) k_v
   if (!ok) {
     if (tid == 0) atomicExch(err, 1);
   } else {
-    // accumulators -> FP64 combination -> C'[row][n0 + j]
+    // accumulators -> float-float pairs -> C'[row][n0 + j]
     const int row = warp * 32 + lane;
-    const int nlive = ROWS == kRowsPairs ? ncw : (P.ncols - n0 < ncw ? P.ncols - n0 : ncw);
-    // Exact accumulators (diagonals d = 0..NACC-2) hold integer multiples of 2^-(2(B-1)+Bd)
-    // below 2^24 of that unit; the tail is rounded to 2^-48.  All of them go into one 64-bit
-    // integer in units of 2^-48 (at most 2^60), converted to FP64 once.
-    if (ROWS == kRowsPairs) {   // C' as float-float pairs
-      float2 *frow = reinterpret_cast<float2 *>(Cbuf) + (crow - Cbuf);
-      for (int c0 = 0; c0 < ncw; c0 += 16) {
-        float sm[16], er[16];
-        tmem_ff16<NACC>(taddr + (uint32_t(warp * 32) << 16) + uint32_t(c0), nc, sm, er);
-        if (row < npt) store_ff16(sm, er, sc + c0, frow + c0, nlive - c0);
-      }
-    } else
+    float2 *frow = reinterpret_cast<float2 *>(Cbuf) + (crow - Cbuf);
     for (int c0 = 0; c0 < ncw; c0 += 16) {
-      long long sum[16];
-      for (int j = 0; j < 16; ++j) sum[j] = 0;
-      for (int a = 0; a < NACC; ++a) {
-        uint32_t v[16];
-        const uint32_t ta = taddr + (uint32_t(warp * 32) << 16) + uint32_t(a * nc + c0);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(ta));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (a < NACC - 1) {
-          // diagonal a: integer multiples of 2^-(2(B-1) + B a), B the digit width
-          constexpr int B = digit_bits(NS);
-          const float up = __int_as_float((127 + 2 * (B - 1) + B * a) << 23);
-          for (int j = 0; j < 16; ++j)
-            sum[j] += (long long)__float2int_rn(__uint_as_float(v[j]) * up) << (48 - 2 * (B - 1) - B * a);
-        } else {
-          for (int j = 0; j < 16; ++j) sum[j] += __float2ll_rn(ldexpf(__uint_as_float(v[j]), 48));
-        }
-      }
-      if (row < npt)
-        for (int j = 0; j < 16; ++j)
-          if (c0 + j < nlive) crow[c0 + j] = (sc[c0 + j] * 0x1p-48) * double(sum[j]);
+      float sm[16], er[16];
+      tmem_ff16<NACC>(taddr + (uint32_t(warp * 32) << 16) + uint32_t(c0), nc, sm, er);
+      if (row < npt) store_ff16(sm, er, sc + c0, frow + c0, ncw - c0);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -909,6 +856,223 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_vertex_gemm_ws(ModelDev M, Me
   if (warp == 4) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(taddr));
 }
 
+// ---- stage A, persistent and warp-specialised, operand roles swapped ---------------------
+// T[k][j'] = sum_r GS[j'][r] PhiK[k][r] with the rows of the contraction (tensor-memory
+// lanes) on 128 columns j' of the model's g slices and its N dimension on a chunk of up to
+// nw k points of the group.  The g slices (NS x Ncols x Kp, the large operand) then move from
+// DRAM once per k chunk, and consecutive work items -- taken by neighbouring CTAs at the same
+// time -- are the k chunks of one column tile, which share that tile through L2; the k phase
+// slices of the group (NS x nkc x Kp) stay in L2.  No row of a tile is padding except the
+// last column tile's, and a chunk's N is its k count rounded up to 16.  One accumulator set
+// of NACC x nw (<= 480) tensor-memory columns; its epilogue (the diagonals summed by TwoSum
+// into a float-float pair, scaled by the column's power of two, stored as two FP32 numbers)
+// runs under the next item's copies.  Roles and barriers as in k_vertex_gemm_ws with a single
+// accumulator buffer: accf completes once per item, acce once the 128 epilogue threads have
+// read it.  All waits bounded.
+template <int NS, int NACC, int ST>
+__global__ void __launch_bounds__(kWsThreads, 1) k_stage_a_ws(TcParams P, int64_t nitems, int nkch,
+                                                              const __nv_bfloat16 *__restrict__ gs,
+                                                              const __nv_bfloat16 *__restrict__ phik,
+                                                              const double *__restrict__ gscale, float2 *T,
+                                                              int *err) {
+  constexpr int KC = 16;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[ST], empty[ST], accf, acce;
+  __shared__ uint32_t tslot;
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (*reinterpret_cast<volatile int *>(err)) return;   // the whole CTA returns, before any barrier
+  const int nw = P.nc_max;
+  const size_t a_slice = size_t(kTcM) * KC * 2, b_slice = size_t(nw) * KC * 2;
+  const size_t stage_bytes = size_t(NS) * (a_slice + b_slice);
+  const size_t gs_slice = size_t(P.Nmax) * P.Kp;   // GS[slice][Ncols][Kp]
+  const int nkb = P.Kp / KC;
+  const int nkc = int(P.nkc);
+  if (tid == 0) {
+    for (int i = 0; i < ST; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&full[i])), "r"(kWsCopyThreads));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&empty[i])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&accf)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&acce)), "r"(kTcM));
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 4) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" :: "r"(smem_u32(&tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t taddr = tslot;
+  auto give_up = [&]() {
+    abort_flag = 1;
+    atomicExch(err, 1);
+  };
+  // item -> first column j0 of its tile, first k k0 of its chunk, live k count nk, MMA width ncw
+  auto decode = [&](int64_t item, int &j0, int &k0, int &nk, int &ncw) {
+    const int64_t ct = item / nkch;
+    const int kch = int(item - ct * nkch);
+    j0 = int(ct * kTcM);
+    k0 = kch * nw;
+    nk = nkc - k0 < nw ? nkc - k0 : nw;
+    ncw = round_up(nk, 16);
+  };
+
+  if (warp >= 5) {
+    // ---------------- copies
+    const int ct = tid - 5 * 32;               // 0..127
+    const int g = ct & 1, r0 = ct >> 1;        // this thread's 16-byte piece and A rows r0, r0 + 64
+    uint32_t it = 0;
+    bool ok = true;
+    auto complete = [&](uint32_t j) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(smem_u32(&full[j % ST]));
+    };
+    for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+      int j0, k0, nk, ncw;
+      decode(item, j0, k0, nk, ncw);
+      const bool live0 = j0 + r0 < P.Nmax, live1 = j0 + r0 + 64 < P.Nmax;
+      const __nv_bfloat16 *a0 = gs + (live0 ? size_t(j0 + r0) * P.Kp : 0);
+      const __nv_bfloat16 *a1 = gs + (live1 ? size_t(j0 + r0 + 64) * P.Kp : 0);
+      for (int kb = 0; kb < nkb; ++kb) {
+        const uint32_t slot = it % ST;
+        if (it >= ST && !mbar_wait(smem_u32(&empty[slot]), ((it / ST) - 1) & 1)) {
+          give_up();
+          ok = false;
+          break;
+        }
+        if (abort_flag) {
+          ok = false;
+          break;
+        }
+        unsigned char *sA = smem + slot * stage_bytes;
+        unsigned char *sB = sA + NS * a_slice;
+        const int kk = kb * KC + g * 8;
+        for (int sl = 0; sl < NS; ++sl) {
+          cp_async16(smem_u32(sA + sl * a_slice + core_off<KC>(r0, g)), a0 + sl * gs_slice + kk, live0 ? 16u : 0u);
+          cp_async16(smem_u32(sA + sl * a_slice + core_off<KC>(r0 + 64, g)), a1 + sl * gs_slice + kk,
+                     live1 ? 16u : 0u);
+        }
+        for (int rem = r0; rem < NS * ncw; rem += 64) {
+          const int sl = rem / ncw, row = rem - sl * ncw;
+          const bool lv = row < nk;
+          const __nv_bfloat16 *src = phik + (lv ? (size_t(k0 + row) * NS + sl) * P.Kp : 0) + kk;
+          cp_async16(smem_u32(sB + sl * b_slice + core_off<KC>(row, g)), src, lv ? 16u : 0u);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        if (it >= ST - 2) {
+          asm volatile("cp.async.wait_group %0;" :: "n"(ST - 2) : "memory");
+          complete(it - (ST - 2));
+        }
+        ++it;
+      }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (ok)
+      for (uint32_t j = it >= ST - 2 ? it - (ST - 2) : 0; j < it; ++j) complete(j);
+  } else if (warp == 4) {
+    // ---------------- tensor-core products (one thread)
+    if (lane == 0) {
+      uint32_t it = 0, tcount = 0, last_bar = 0, last_par = 0;
+      bool any = false;
+      for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        if (abort_flag) break;
+        int j0, k0, nk, ncw;
+        decode(item, j0, k0, nk, ncw);
+        if (tcount >= 1 && !mbar_wait(smem_u32(&acce), (tcount - 1) & 1)) {
+          give_up();
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(ncw >> 3) << 17) |
+                               (uint32_t(kTcM >> 4) << 24);
+        bool ok = true;
+        for (int kb = 0; kb < nkb; ++kb) {
+          const uint32_t slot = it % ST;
+          if (!mbar_wait(smem_u32(&full[slot]), (it / ST) & 1) || abort_flag) {
+            if (!abort_flag) give_up();
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          if (!P.withhold) {
+            const unsigned char *sA = smem + slot * stage_bytes;
+            const unsigned char *sB = sA + NS * a_slice;
+            for (int is = 0; is < NS; ++is)
+              for (int ls = 0; ls < NS - is; ++ls) {
+                const int d = is + ls;
+                const int acc = d < NACC - 1 ? d : NACC - 1;
+                const uint64_t ad = smem_desc(smem_u32(sA + is * a_slice), 128u, (KC / 8) * 128u);
+                const uint64_t bd = smem_desc(smem_u32(sB + ls * b_slice), 128u, (KC / 8) * 128u);
+                const bool first = kb == 0 && (acc < NACC - 1 ? (is == 0) : (is == 0 && ls == NACC - 1));
+                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                             :: "r"(taddr + uint32_t(acc * nw)), "l"(ad), "l"(bd), "r"(idesc), "r"(first ? 0u : 1u));
+              }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(&empty[slot])) : "memory");
+            any = true;
+            last_bar = smem_u32(&empty[slot]);
+            last_par = (it / ST) & 1;
+          }
+          ++it;
+        }
+        if (!ok) break;
+        if (!P.withhold) {
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                       :: "r"(smem_u32(&accf)) : "memory");
+          last_bar = smem_u32(&accf);
+          last_par = tcount & 1;
+        }
+        ++tcount;
+      }
+      if (any && !mbar_wait(last_bar, last_par)) give_up();
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue (warps 0-3: tensor-memory lanes 32w .. 32w + 31 = columns j0 + row)
+    const int row = warp * 32 + lane;
+    uint32_t tcount = 0;
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+      int j0, k0, nk, ncw;
+      decode(item, j0, k0, nk, ncw);
+      const int j = j0 + row;
+      const bool live = j < P.ncols;
+      const float f = live ? pow2_float(gscale[j]) : 0.f;
+      const bool waited = mbar_wait(smem_u32(&accf), tcount & 1);
+      const bool ok = epi_sync_and(waited && !abort_flag);
+      if (!ok) {
+        if (!waited && !abort_flag) give_up();
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      float2 *out = T + size_t(k0) * P.out_stride + j;
+      const uint32_t tb = taddr + (uint32_t(warp * 32) << 16);
+      for (int c0 = 0; c0 < ncw; c0 += 16) {
+        float sm[16], er[16];
+        tmem_ff16<NACC>(tb + uint32_t(c0), nw, sm, er);
+        if (c0 + 16 >= ncw) {   // the last reads of the accumulators: hand them back
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          mbar_arrive(smem_u32(&acce));
+        }
+        if (live)
+          for (int c = 0; c < 16; ++c)
+            if (c0 + c < nk) {
+              float h, l;
+              ff_two_sum(sm[c], er[c], h, l);
+              out[size_t(c0 + c) * P.out_stride] = make_float2(__fmul_rn(h, f), __fmul_rn(l, f));
+            }
+      }
+      ++tcount;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 4) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(taddr));
+}
+
 }  // namespace
 
 int tc_kp(const ModelDev &M) { return round_up(2 * M.nRgp, kTcKc); }
@@ -957,52 +1121,64 @@ cudaError_t launch_g_slices(const ModelDev &M, int ns, __nv_bfloat16 *gs, double
   return cudaGetLastError();
 }
 
+// Stage A on the tensor cores: the k phase slices of the group, then the persistent
+// swapped-role contraction (k_stage_a_ws) into T[k][j'] as float-float pairs.  The k chunk
+// width: the fewest chunks of at most (512 / NACC rounded down to 16) k points, balanced and
+// rounded up to 16.
+static int stage_a_chunk(int ns, int64_t nkc, int *nkch) {
+  const int cap = (512 / nacc_of(ns)) / 16 * 16;
+  const int64_t n = (nkc + cap - 1) / cap;
+  *nkch = int(n);
+  return round_up(int((nkc + n - 1) / n), 16);
+}
+constexpr int kStageASt = 4;   // shared-memory stages of the stage-A pipeline
+
 cudaError_t launch_stage_a_tc(const ModelDev &M, const MeshDev &D, int ns, int64_t i0, int64_t nkc,
                               __nv_bfloat16 *phik, const __nv_bfloat16 *gs, const double *gscale, double2 *T, int *err,
-                              int ncm, cudaStream_t st, double *flops_acc) {
+                              cudaStream_t st, double *flops_acc) {
   if (nkc <= 0) return cudaSuccess;
-  if (!tc_nc_valid(ns, ncm, 32, 2)) return cudaErrorInvalidValue;
+  if (ns != 7 && ns != 8) return cudaErrorInvalidValue;
   const int Kp = tc_kp_a(M), Ncols = tc_ncols_a(M);
   const int64_t n = nkc * int64_t(Kp);
   EPHB_LAUNCH(k_phase_slices_k, unsigned((n + 255) / 256), 256, 0, st, M, D, i0, nkc, ns, Kp, phik);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  int nkch = 0;
+  const int nw = stage_a_chunk(ns, nkc, &nkch);
   TcParams P;
   P.ns = ns;
   P.nacc = nacc_of(ns);
   P.Kp = Kp;
   P.Nmax = Ncols;
-  P.nc_max = ncm;
+  P.nc_max = nw;
   P.i0 = i0;
   P.nkc = nkc;
   P.pair_base = 0;
   P.ncols = 2 * M.nRgp * M.nb * M.nb * M.nbr;
   P.out_stride = P.ncols;
   P.withhold = 0;
-  const int nch = (Ncols + ncm - 1) / ncm;
-  const int64_t ntile = (nkc + kTcM - 1) / kTcM;
-  const int64_t nitems = ntile * nch;
-  const size_t smem = tc_smem_bytes(ns, ncm, 32, 2);
-  double *out = reinterpret_cast<double *>(T);
-  if (ns == 8) {
-    e = cudaFuncSetAttribute(k_vertex_gemm<8, 6, kRowsK, 32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    EPHB_LAUNCH((k_vertex_gemm<8, 6, kRowsK, 32, 2>), unsigned(nitems), kTcThreads, smem, st, M, D, P, nullptr, phik, gs,
-                gscale, out, err);
-  } else if (ns == 7) {
-    e = cudaFuncSetAttribute(k_vertex_gemm<7, 5, kRowsK, 32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    EPHB_LAUNCH((k_vertex_gemm<7, 5, kRowsK, 32, 2>), unsigned(nitems), kTcThreads, smem, st, M, D, P, nullptr, phik, gs,
-                gscale, out, err);
-  } else {
-    e = cudaFuncSetAttribute(k_vertex_gemm<3, 2, kRowsK, 32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    EPHB_LAUNCH((k_vertex_gemm<3, 2, kRowsK, 32, 2>), unsigned(nitems), kTcThreads, smem, st, M, D, P, nullptr, phik, gs,
-                gscale, out, err);
+  const int64_t nct = (Ncols + kTcM - 1) / kTcM;
+  const int64_t nitems = nct * nkch;
+  const size_t smem = size_t(kStageASt) * ns * (size_t(kTcM) * 16 * 2 + size_t(nw) * 16 * 2);
+  int dev = 0, nsm = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = unsigned(nitems < nsm ? nitems : nsm);
+  float2 *out = reinterpret_cast<float2 *>(T);
+  auto go = [&](auto kern) -> cudaError_t {
+    cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (r != cudaSuccess) return r;
+    EPHB_LAUNCH(kern, grid, kWsThreads, smem, st, P, nitems, nkch, gs, phik, gscale, out, err);
+    return cudaGetLastError();
+  };
+  e = ns == 8 ? go(k_stage_a_ws<8, 6, kStageASt>) : go(k_stage_a_ws<7, 5, kStageASt>);
+  // issued MMA work: 128 columns x each chunk's width x Kp per slice product and column tile
+  if (flops_acc) {
+    double width = 0.0;
+    for (int c = 0; c < nkch; ++c) width += round_up(int(std::min<int64_t>(nw, nkc - int64_t(c) * nw)), 16);
+    *flops_acc += 2.0 * kTcM * width * Kp * (ns * (ns + 1) / 2) * double(nct);
   }
-  e = cudaGetLastError();
-  // issued MMA work: every item runs 128 rows x its chunk width x Kp for each slice product
-  if (flops_acc) *flops_acc += 2.0 * kTcM * double(Ncols) * Kp * (ns * (ns + 1) / 2) * double(ntile);
   return e;
 }
 
@@ -1089,17 +1265,17 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
                 : (ns == 7 ? go_ws(k_vertex_gemm_ws<7, 5, 5>)
                            : (ns == 4 ? go_ws(k_vertex_gemm_ws<4, 2, 5>) : go_ws(k_vertex_gemm_ws<3, 2, 5>)));
   else if (ns == 4)
-    e = kc == 32 ? go(k_vertex_gemm<4, 2, kRowsPairs, 32, 2>)
-                 : (stages == 4 ? go(k_vertex_gemm<4, 2, kRowsPairs, 16, 4>) : go(k_vertex_gemm<4, 2, kRowsPairs, 16, 2>));
+    e = kc == 32 ? go(k_vertex_gemm<4, 2, 32, 2>)
+                 : (stages == 4 ? go(k_vertex_gemm<4, 2, 16, 4>) : go(k_vertex_gemm<4, 2, 16, 2>));
   else if (ns == 8)
-    e = kc == 32 ? go(k_vertex_gemm<8, 6, kRowsPairs, 32, 2>)
-                 : (stages == 4 ? go(k_vertex_gemm<8, 6, kRowsPairs, 16, 4>) : go(k_vertex_gemm<8, 6, kRowsPairs, 16, 2>));
+    e = kc == 32 ? go(k_vertex_gemm<8, 6, 32, 2>)
+                 : (stages == 4 ? go(k_vertex_gemm<8, 6, 16, 4>) : go(k_vertex_gemm<8, 6, 16, 2>));
   else if (ns == 7)
-    e = kc == 32 ? go(k_vertex_gemm<7, 5, kRowsPairs, 32, 2>)
-                 : (stages == 4 ? go(k_vertex_gemm<7, 5, kRowsPairs, 16, 4>) : go(k_vertex_gemm<7, 5, kRowsPairs, 16, 2>));
+    e = kc == 32 ? go(k_vertex_gemm<7, 5, 32, 2>)
+                 : (stages == 4 ? go(k_vertex_gemm<7, 5, 16, 4>) : go(k_vertex_gemm<7, 5, 16, 2>));
   else
-    e = kc == 32 ? go(k_vertex_gemm<3, 2, kRowsPairs, 32, 2>)
-                 : (stages == 4 ? go(k_vertex_gemm<3, 2, kRowsPairs, 16, 4>) : go(k_vertex_gemm<3, 2, kRowsPairs, 16, 2>));
+    e = kc == 32 ? go(k_vertex_gemm<3, 2, 32, 2>)
+                 : (stages == 4 ? go(k_vertex_gemm<3, 2, 16, 4>) : go(k_vertex_gemm<3, 2, 16, 2>));
   if (e != cudaSuccess) return e;
   e = cudaGetLastError();
   if (e == cudaSuccess && gemm1) e = cudaEventRecord(gemm1, st);
