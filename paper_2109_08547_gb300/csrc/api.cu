@@ -160,7 +160,7 @@ struct ephb_ctx : InstState {
   ModelDev M;
   DBuf<int> Re, Rd, Rge, Rgp, sym_rot, sym_inv;
   DBuf<double2> H_R, D_R, g_R;
-  DBuf<double> sym_cart;
+  DBuf<double> sym_cart, sym_pair;
 
   // meshes
   Mesh km{}, qm{};
@@ -381,6 +381,7 @@ void ephb_destroy(ephb_ctx *ctx) {
   cudaStreamSynchronize(ctx->stream);
   ctx->Re.release(); ctx->Rd.release(); ctx->Rge.release(); ctx->Rgp.release(); ctx->sym_rot.release();
   ctx->sym_inv.release(); ctx->H_R.release(); ctx->D_R.release(); ctx->g_R.release(); ctx->sym_cart.release();
+  ctx->sym_pair.release();
   ctx->ktab.release(); ctx->qtab.release(); ctx->cvec.release(); ctx->u.release(); ctx->eps.release();
   ctx->vel.release(); ctx->w.release(); ctx->vph.release(); ctx->egrp.release(); ctx->pgrp.release();
   ctx->qrep.release(); ctx->qop.release(); ctx->qstab.release(); ctx->qflag.release(); ctx->qlist.release();
@@ -522,6 +523,15 @@ ephb_status ephb_set_wannier_model(ephb_ctx *ctx, const ephb_model *m) {
   CK(upload(ctx->g_R, reinterpret_cast<const double2 *>(m->g_R), size_t(m->nRge) * m->nRgp * nb2 * M.nbr, st));
   CK(upload(ctx->sym_rot, m->sym_rot, size_t(m->nsym) * 9, st));
   CK(upload(ctx->sym_cart, m->sym_cart, size_t(m->nsym) * 9, st));
+  {
+    std::vector<double> pair(81, 0.0);
+    for (int o = 0; o < m->nsym; ++o) {
+      const double *S = m->sym_cart + 9 * o;
+      for (int ab = 0; ab < 9; ++ab)
+        for (int ef = 0; ef < 9; ++ef) pair[ab * 9 + ef] += S[(ab / 3) * 3 + ef / 3] * S[(ab % 3) * 3 + ef % 3];
+    }
+    CK(upload(ctx->sym_pair, pair.data(), pair.size(), st));
+  }
   CK(upload(ctx->sym_inv, inv.data(), inv.size(), st));
   CK(upload(ctx->atom_perm, aperm.data(), aperm.size(), st));
   CK(upload(ctx->atom_shift, ashift.data(), ashift.size(), st));
@@ -534,6 +544,7 @@ ephb_status ephb_set_wannier_model(ephb_ctx *ctx, const ephb_model *m) {
   M.g_R = ctx->g_R.p;
   M.sym_rot = ctx->sym_rot.p;
   M.sym_cart = ctx->sym_cart.p;
+  M.sym_pair = ctx->sym_pair.p;
   M.sym_inv = ctx->sym_inv.p;
   M.atom_perm = ctx->atom_perm.p;
   M.atom_shift = ctx->atom_shift.p;
@@ -948,14 +959,14 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     CK(ctx->ws_desc.ensure(size_t(ctx->ws_cap) * 4));
     CK(ctx->tc_err.ensure(1));
     if (tensor_a) {   // g slices once per model; k phase slices per chunk
-      const size_t gsz = size_t(ns_a) * tc_ncols_a(M) * tc_kp_a(M);
+      const size_t gsz = tc_gs_elems_a(M, ns_a);
       if (ctx->gslices_ns != ns_a || ctx->gslices.n < gsz) {
         CK(ctx->gslices.ensure(gsz));
         CK(ctx->gscale.ensure(tc_ncols_a(M)));
         CK(launch_g_slices(M, ns_a, ctx->gslices.p, ctx->gscale.p, st));
         ctx->gslices_ns = ns_a;
       }
-      CK(ctx->phik.ensure(size_t(chunk) * ns_a * tc_kp_a(M)));
+      CK(ctx->phik.ensure(stage_a_phik_elems(M, ns_a, chunk)));
     }
     CK(cudaMemsetAsync(ctx->tc_err.p, 0, sizeof(int), st));
     CK(cudaMemsetAsync(ctx->scal.p + 7, 0, sizeof(int64_t), st));

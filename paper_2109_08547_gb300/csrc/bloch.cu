@@ -21,7 +21,7 @@ __global__ void k_phase_tables(double2 *tab, Mesh m) {
 
 // One thread per listed k point: H(k), grad_k H(k), eigen-decomposition, velocities.
 template <int NB>
-__global__ void __launch_bounds__(128) k_electron_bands(ModelDev M, Mesh km, const int *__restrict__ list, int64_t n,
+__global__ void __launch_bounds__(32) k_electron_bands(ModelDev M, Mesh km, const int *__restrict__ list, int64_t n,
                                                         const double2 *__restrict__ ktab,
                                                         double degen_tol, double lo, double hi, double *eps,
                                                         double2 *cvec, double *vel, uint8_t *egrp,
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(128) k_electron_bands(ModelDev M, Mesh km, con
 // One thread per listed q point: D(q), eigen-decomposition, hbar w = sqrt(max(lambda,0)),
 // velocities.
 template <int NB>
-__global__ void __launch_bounds__(128) k_phonon_modes(ModelDev M, Mesh qm, const int *__restrict__ list, int64_t n,
+__global__ void __launch_bounds__(32) k_phonon_modes(ModelDev M, Mesh qm, const int *__restrict__ list, int64_t n,
                                                       const double2 *__restrict__ qtab,
                                                       double degen_tol, double omega_min, double *w, double2 *u,
                                                       double *vph, uint8_t *pgrp) {
@@ -431,15 +431,17 @@ cudaError_t launch_electron_bands(const ModelDev &M, Mesh km, const int *list, i
                                   double degen_tol, double lo, double hi, double *eps, double2 *cvec, double *vel,
                                   uint8_t *egrp, uint32_t *amask, uint32_t *rmask, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  int grid = int((n + 127) / 128);
+  // one warp per block: the decomposition is FP64-bound per thread, so the warps are spread
+  // over every SM instead of filling a few
+  const int grid = int((n + 31) / 32), bs = 32;
   if (M.nb <= 1)
-    EPHB_LAUNCH(k_electron_bands<1>, grid, 128, 0, st, M, km, list, n, ktab, degen_tol, lo, hi, eps, cvec, vel, egrp,
+    EPHB_LAUNCH(k_electron_bands<1>, grid, bs, 0, st, M, km, list, n, ktab, degen_tol, lo, hi, eps, cvec, vel, egrp,
                 amask, rmask);
   else if (M.nb <= 4)
-    EPHB_LAUNCH(k_electron_bands<4>, grid, 128, 0, st, M, km, list, n, ktab, degen_tol, lo, hi, eps, cvec, vel, egrp,
+    EPHB_LAUNCH(k_electron_bands<4>, grid, bs, 0, st, M, km, list, n, ktab, degen_tol, lo, hi, eps, cvec, vel, egrp,
                 amask, rmask);
   else
-    EPHB_LAUNCH(k_electron_bands<8>, grid, 128, 0, st, M, km, list, n, ktab, degen_tol, lo, hi, eps, cvec, vel, egrp,
+    EPHB_LAUNCH(k_electron_bands<8>, grid, bs, 0, st, M, km, list, n, ktab, degen_tol, lo, hi, eps, cvec, vel, egrp,
                 amask, rmask);
   return cudaGetLastError();
 }
@@ -465,13 +467,13 @@ cudaError_t launch_phonon_modes(const ModelDev &M, Mesh qm, const int *list, int
                                 double degen_tol, double omega_min, double *w, double2 *u, double *vph, uint8_t *pgrp,
                                 cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  int grid = int((n + 127) / 128);
+  const int grid = int((n + 31) / 32), bs = 32;   // one warp per block, as for the bands
   if (M.nbr <= 3)
-    EPHB_LAUNCH(k_phonon_modes<3>, grid, 128, 0, st, M, qm, list, n, qtab, degen_tol, omega_min, w, u, vph, pgrp);
+    EPHB_LAUNCH(k_phonon_modes<3>, grid, bs, 0, st, M, qm, list, n, qtab, degen_tol, omega_min, w, u, vph, pgrp);
   else if (M.nbr <= 6)
-    EPHB_LAUNCH(k_phonon_modes<6>, grid, 128, 0, st, M, qm, list, n, qtab, degen_tol, omega_min, w, u, vph, pgrp);
+    EPHB_LAUNCH(k_phonon_modes<6>, grid, bs, 0, st, M, qm, list, n, qtab, degen_tol, omega_min, w, u, vph, pgrp);
   else
-    EPHB_LAUNCH(k_phonon_modes<12>, grid, 128, 0, st, M, qm, list, n, qtab, degen_tol, omega_min, w, u, vph, pgrp);
+    EPHB_LAUNCH(k_phonon_modes<12>, grid, bs, 0, st, M, qm, list, n, qtab, degen_tol, omega_min, w, u, vph, pgrp);
   return cudaGetLastError();
 }
 

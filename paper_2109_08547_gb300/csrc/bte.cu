@@ -591,6 +591,8 @@ __global__ void __launch_bounds__(256) k_ph_sweep(ModelDev M, MeshDev D, BteDev 
 // A(q) = sum_S C_S Btv(S^-1 q).  It is covariant, A(S q) = C_S A(q) (rearranging the group sum),
 // so the 48-term sum runs on the representatives of the q wedge only and every other q takes
 // its representative's A rotated by the operation that maps the representative onto it.
+// Eight lanes per (representative, branch): lane l sums the operations l, l + 8, ...; the eight
+// partial sums are added by shuffles (a fixed order: the result is reproducible).
 __global__ void k_ph_fold_rep(ModelDev M, MeshDev D, const double *Btv, double *Afold) {
   __shared__ int rot[kMaxSym * 9];
   __shared__ int inv[kMaxSym];
@@ -601,21 +603,27 @@ __global__ void k_ph_fold_rep(ModelDev M, MeshDev D, const double *Btv, double *
   }
   for (int t = threadIdx.x; t < M.nsym; t += blockDim.x) inv[t] = M.sym_inv[t];
   __syncthreads();
-  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int64_t t = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 3;
+  const int l = threadIdx.x & 7;
   const int nbr = M.nbr;
-  if (t >= D.n_qrep * nbr) return;
-  const int j = int(t / nbr), s = int(t % nbr);
-  const int q = D.qlist[j];
+  const bool live = t < D.n_qrep * nbr;
   double a[6] = {0, 0, 0, 0, 0, 0};
-  for (int o = 0; o < M.nsym; ++o) {
-    const int64_t src = int64_t(q_image(D.qm, rot + 9 * inv[o], q)) * nbr + s;
-    double r[3];
-    rot3(C + 9 * o, Btv + src * 6, r);
-    for (int x = 0; x < 3; ++x) a[x] += r[x];
-    rot3(C + 9 * o, Btv + src * 6 + 3, r);
-    for (int x = 0; x < 3; ++x) a[3 + x] += r[x];
+  if (live) {
+    const int j = int(t / nbr), s = int(t % nbr);
+    const int q = D.qlist[j];
+    for (int o = l; o < M.nsym; o += 8) {
+      const int64_t src = int64_t(q_image(D.qm, rot + 9 * inv[o], q)) * nbr + s;
+      double r[3];
+      rot3(C + 9 * o, Btv + src * 6, r);
+      for (int x = 0; x < 3; ++x) a[x] += r[x];
+      rot3(C + 9 * o, Btv + src * 6 + 3, r);
+      for (int x = 0; x < 3; ++x) a[3 + x] += r[x];
+    }
   }
-  for (int c = 0; c < 6; ++c) Afold[t * 6 + c] = a[c];
+  for (int off = 4; off > 0; off >>= 1)
+    for (int c = 0; c < 6; ++c) a[c] += __shfl_xor_sync(0xffffffffu, a[c], off);
+  if (live && l == 0)
+    for (int c = 0; c < 6; ++c) Afold[t * 6 + c] = a[c];
 }
 
 // F = F0 + d_s/(n(1+n)W) A_I(q); G = d_s/(n(1+n)W) A_J(q)   (Eq. dF^D), A(q) = C_S A(<q>)
@@ -696,15 +704,11 @@ __device__ void coeff_final_body(const ModelDev &M, const BteDev &B, const doubl
   }
   __syncthreads();
   const int t = threadIdx.x;
-  if (t < 36) {   // symmetrised electron tensors: sum_S S M S^T
-    const int c = t / 9, a = (t % 9) / 3, b = t % 3;
+  if (t < 36) {   // symmetrised electron tensors: sum_S S M S^T = sum_ef sym_pair[ab][ef] M_ef
+    const int c = t / 9, ab = t % 9;
     const double *Mc = Ms + 9 * c;
     double s = 0.0;
-    for (int o = 0; o < M.nsym; ++o) {
-      const double *S = M.sym_cart + 9 * o;
-      for (int e = 0; e < 3; ++e)
-        for (int f = 0; f < 3; ++f) s += S[a * 3 + e] * Mc[e * 3 + f] * S[b * 3 + f];
-    }
+    for (int ef = 0; ef < 9; ++ef) s += M.sym_pair[ab * 9 + ef] * Mc[ef];
     R[t] = (c < 2 ? 1.0 : -1.0) * B.Pe * s;
   } else if (t < 54) {
     R[t] = B.Pph * Ms[t];
@@ -886,13 +890,8 @@ __global__ void k_ko_final(ModelDev M, BteDev B, const double *kpart, int npart,
   __syncthreads();
   const int t = threadIdx.x;
   if (t < 9) {
-    const int a = t / 3, b = t % 3;
     double s = 0.0;
-    for (int o = 0; o < M.nsym; ++o) {
-      const double *S = M.sym_cart + 9 * o;
-      for (int e = 0; e < 3; ++e)
-        for (int f = 0; f < 3; ++f) s += S[a * 3 + e] * Ms[e * 3 + f] * S[b * 3 + f];
-    }
+    for (int ef = 0; ef < 9; ++ef) s += M.sym_pair[t * 9 + ef] * Ms[ef];
     Bt[t] = B.Pe * s;
   }
   __syncthreads();
@@ -1364,7 +1363,7 @@ cudaError_t launch_ph_sweep(const ModelDev &M, const MeshDev &D, const BteDev &B
 
 cudaError_t launch_ph_update(const ModelDev &M, const MeshDev &D, const double *Btv, const double *F0,
                              const double *inv_nnW, double *F, double *G, double *Afold, cudaStream_t st) {
-  EPHB_LAUNCH(k_ph_fold_rep, unsigned((D.n_qrep * M.nbr + 255) / 256), 256, 0, st, M, D, Btv, Afold);
+  EPHB_LAUNCH(k_ph_fold_rep, unsigned((D.n_qrep * M.nbr * 8 + 255) / 256), 256, 0, st, M, D, Btv, Afold);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   EPHB_LAUNCH(k_ph_update, unsigned((D.nq * M.nbr + 255) / 256), 256, 0, st, M, D, Afold, F0, inv_nnW, F, G);

@@ -21,6 +21,9 @@ struct ModelDev {
   const int *sym_rot = nullptr;       // [nsym][9]
   const double *sym_cart = nullptr;   // [nsym][9]
   const int *sym_inv = nullptr;       // [nsym]
+  // sum over the operations of S_ae S_bf, at [(a*3+b)*9 + e*3+f]: the symmetrised tensor
+  // sum_S S M S^T is then sum_ef sym_pair[ab][ef] M_ef
+  const double *sym_pair = nullptr;   // [81]
   // atom maps of the operations: S tau_a = tau_{perm[s][a]} + shift[s][a] (crystal coordinates)
   const int *atom_perm = nullptr;     // [nsym][nat]
   const int *atom_shift = nullptr;    // [nsym][nat][3]
@@ -144,12 +147,15 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
                              int64_t ws_cap);
 // ws_desc: scratch of 4 int64 per work item (descriptors of the persistent form), ws_cap items
 // Stage A on tensor cores: T[kc][col] = sum_Re e^{ik.Re} g[Re][col] for the k of a chunk, as
-// the same exact-slice GEMM with the model's g slices (made once by launch_g_slices,
-// [ns][tc_ncols_a][tc_kp_a] BF16 + column scales) as the rows and the k phase slices as the
-// columns.  ns: 7 or 8.  T is written as float-float pairs (two FP32 numbers per real value,
+// the same exact-slice GEMM with the model's g slices (made once by launch_g_slices, BF16,
+// pre-tiled by 128 columns and K blocks of 16, + column scales) as the rows and the k phase
+// slices as the columns.  ns: 7 or 8.  T is written as float-float pairs (two FP32 numbers per real value,
 // in the place of one double), read by launch_stage_a2 with t_ff set.
 int tc_kp_a(const ModelDev &M);
 int tc_ncols_a(const ModelDev &M);
+// elements of the pre-tiled g slices and of the phase-slice operand of a group of <= chunk k
+size_t tc_gs_elems_a(const ModelDev &M, int ns);
+size_t stage_a_phik_elems(const ModelDev &M, int ns, int64_t chunk);
 cudaError_t launch_g_slices(const ModelDev &M, int ns, __nv_bfloat16 *gs, double *gscale, cudaStream_t st);
 cudaError_t launch_stage_a_tc(const ModelDev &M, const MeshDev &D, int ns, int64_t i0, int64_t nkc,
                               __nv_bfloat16 *phik, const __nv_bfloat16 *gs, const double *gscale, double2 *T, int *err,

@@ -1,7 +1,10 @@
 // Small dense complex-Hermitian eigen-decomposition by the cyclic Jacobi method, one
 // matrix per thread.  Used for H(k) (<= 8 bands) and D(q) (<= 12 branches) in FP64.
 // Each rotation J = D R D^dagger combines a diagonal phase D = diag(1, e^{-i phi}) that
-// makes a_pq real with the classic real Jacobi rotation R of the (p,q) plane.
+// makes a_pq real with the classic real Jacobi rotation R of the (p,q) plane (t = tan of its
+// angle from theta = (a_qq - a_pp) / (2 |a_pq|), the smaller root of t^2 + 2 t theta = 1).
+// Only the off-block entries are rotated; the Hermitian mirror is copied and the 2 x 2 block
+// takes its closed form, which halves the FP64 work of a rotation.
 #pragma once
 #include "common.cuh"
 
@@ -10,7 +13,7 @@ namespace ephb {
 // A: NMAX x NMAX row-major, Hermitian in its leading n x n block (destroyed).
 // On return e[0..n) ascending and V columns the matching orthonormal eigenvectors.
 template <int NMAX>
-__host__ __device__ inline void herm_jacobi(double2 *A, double2 *V, double *e, int n) {
+__device__ inline void herm_jacobi(double2 *A, double2 *V, double *e, int n) {
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) V[i * NMAX + j] = cmk(i == j ? 1.0 : 0.0, 0.0);
   double norm2 = 0.0;
@@ -23,35 +26,36 @@ __host__ __device__ inline void herm_jacobi(double2 *A, double2 *V, double *e, i
     if (off <= 1e-36 * norm2) break;
     for (int p = 0; p < n - 1; ++p) {
       for (int q = p + 1; q < n; ++q) {
-        double2 apq = A[p * NMAX + q];
-        double b = sqrt(cabs2(apq));
-        if (b == 0.0) continue;
-        double2 ph = cscale(apq, 1.0 / b);   // e^{i phi}
-        double app = A[p * NMAX + p].x, aqq = A[q * NMAX + q].x;
-        double theta = (aqq - app) / (2.0 * b);
-        double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-        double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-        double2 sph = cscale(ph, s);          // s e^{i phi}
-        double2 sphc = cconj(sph);            // s e^{-i phi}
-        // A <- A J : columns p, q
+        const double2 apq = A[p * NMAX + q];
+        const double b2 = cabs2(apq);
+        if (b2 == 0.0) continue;
+        const double ib = rsqrt(b2), b = b2 * ib;   // 1 / |a_pq| and |a_pq|
+        const double2 ph = cscale(apq, ib);          // e^{i phi}
+        const double app = A[p * NMAX + p].x, aqq = A[q * NMAX + q].x;
+        const double theta = (aqq - app) * 0.5 * ib;
+        const double t = copysign(1.0, theta) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = rsqrt(t * t + 1.0), s = t * c;
+        const double2 sph = cscale(ph, s);          // s e^{i phi}
+        const double2 sphc = cconj(sph);            // s e^{-i phi}
+        // A <- J^dagger A J.  Columns p, q of every other row r; rows p, q are their conjugates
+        // (A stays Hermitian), and the (p, q) block becomes diag(a_pp - t |a_pq|, a_qq + t |a_pq|).
         for (int r = 0; r < n; ++r) {
-          double2 tp = A[r * NMAX + p], tq = A[r * NMAX + q];
-          A[r * NMAX + p] = csub(cscale(tp, c), cmul(sphc, tq));
-          A[r * NMAX + q] = cadd(cmul(sph, tp), cscale(tq, c));
+          if (r == p || r == q) continue;
+          const double2 tp = A[r * NMAX + p], tq = A[r * NMAX + q];
+          const double2 np = csub(cscale(tp, c), cmul(sphc, tq));
+          const double2 nq = cadd(cmul(sph, tp), cscale(tq, c));
+          A[r * NMAX + p] = np;
+          A[r * NMAX + q] = nq;
+          A[p * NMAX + r] = cconj(np);
+          A[q * NMAX + r] = cconj(nq);
         }
-        // A <- J^dagger A : rows p, q
-        for (int r = 0; r < n; ++r) {
-          double2 tp = A[p * NMAX + r], tq = A[q * NMAX + r];
-          A[p * NMAX + r] = csub(cscale(tp, c), cmul(sph, tq));
-          A[q * NMAX + r] = cadd(cmul(sphc, tp), cscale(tq, c));
-        }
+        A[p * NMAX + p] = cmk(app - t * b, 0.0);
+        A[q * NMAX + q] = cmk(aqq + t * b, 0.0);
         A[p * NMAX + q] = cmk(0.0, 0.0);
         A[q * NMAX + p] = cmk(0.0, 0.0);
-        A[p * NMAX + p].y = 0.0;
-        A[q * NMAX + q].y = 0.0;
         // V <- V J
         for (int r = 0; r < n; ++r) {
-          double2 tp = V[r * NMAX + p], tq = V[r * NMAX + q];
+          const double2 tp = V[r * NMAX + p], tq = V[r * NMAX + q];
           V[r * NMAX + p] = csub(cscale(tp, c), cmul(sphc, tq));
           V[r * NMAX + q] = cadd(cmul(sph, tp), cscale(tq, c));
         }

@@ -242,58 +242,109 @@ static size_t b_slices_smem(const ModelDev &M) {
   return size_t(M.nRgp) * ((nbnbr + g - 1) / g) * sizeof(double2);
 }
 
-// Phase slices of the k points of a chunk (stage A rows): PhiK[kc][slice][Kp] with the
-// (cos, sin) of 2 pi k.Re for r < nRe and nRe <= r < 2 nRe.
-__global__ void k_phase_slices_k(ModelDev M, MeshDev D, int64_t i0, int64_t nkc, int ns, int Kp,
-                                 __nv_bfloat16 *phik) {
-  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  const int R = M.nRge;
-  if (t >= nkc * int64_t(Kp)) return;
-  const int64_t kc = t / Kp;
-  const int r = int(t % Kp);
-  double x = 0.0;
-  if (r < 2 * R) {
-    const int rr = r < R ? r : r - R;
-    int a0, a1, a2;
-    D.km.unflat(D.ibzw_list[i0 + kc], a0, a1, a2);
-    const int *Rv = M.Rge + 3 * rr;
-    const double2 ph = mesh_phase(D.ktab, D.km, a0, a1, a2, Rv[0], Rv[1], Rv[2]);
-    x = r < R ? ph.x : ph.y;
-  }
-  fixed_slices(x, ns, phik + (size_t(kc) * ns) * Kp + r, size_t(Kp));
+// ---- stage-A operands, pre-tiled ---------------------------------------------------------
+// Both operands of the stage-A contraction are stored in HBM in the order the pipeline
+// consumes them: for each (tile of rows, K block of 16) the NS slices' [rows x 16] K-major
+// core-matrix tiles (8 rows x 16 bytes per core matrix, the two K halves of a row group
+// 128 bytes apart, row groups 256 bytes apart) lie back to back.  One pipeline stage of one
+// operand is then one contiguous block, moved by a single bulk copy.  Row tiles: 128 columns
+// of the model's g (A) and chunks of nw k points (B).
+
+// element offset of (row, k-in-block kk) within one [rows x 16] core-matrix tile
+__host__ __device__ __forceinline__ int tile16_off(int row, int kk) {
+  return ((row >> 3) * 2 + (kk >> 3)) * 64 + (row & 7) * 8 + (kk & 7);
 }
 
-// Slices of the model's g as the B operand of stage A: column j' = 2 col + part of
-// T[k][col] = sum_Re e^{ik.Re} g[Re][col], col = (rp, m', n', alpha):
+// ns slices of 8 consecutive values into ns 16-byte vectors (8 BF16 each)
+__device__ inline void slices8(const double *x, int ns, uint4 *out) {
+  __nv_bfloat16 v[8][8];
+  for (int e = 0; e < 8; ++e) fixed_slices(x[e], ns, &v[e][0], 1);
+  for (int sl = 0; sl < ns; ++sl) {
+    __nv_bfloat16 w[8];
+    for (int e = 0; e < 8; ++e) w[e] = v[e][sl];
+    out[sl] = *reinterpret_cast<const uint4 *>(w);
+  }
+}
+
+// Phase slices of the k points of a group as the B operand of stage A: rows k (chunks of nw,
+// rows past nkc zero), (cos, sin) of 2 pi k.Re for r < nRe and nRe <= r < 2 nRe, K padded to
+// Kp with zeros.  One thread per (k, 8 consecutive r).
+__global__ void k_phase_slices_k(ModelDev M, MeshDev D, int64_t i0, int64_t nkc, int nrows, int nw, int ns, int Kp,
+                                 __nv_bfloat16 *phik) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int R = M.nRge, n8 = Kp / 8, nkb = Kp / 16;
+  if (t >= int64_t(nrows) * n8) return;
+  const int k = int(t / n8), r0 = int(t % n8) * 8;
+  double x[8];
+  int a0 = 0, a1 = 0, a2 = 0;
+  if (k < nkc) D.km.unflat(D.ibzw_list[i0 + k], a0, a1, a2);
+  for (int e = 0; e < 8; ++e) {
+    const int r = r0 + e;
+    x[e] = 0.0;
+    if (k < nkc && r < 2 * R) {
+      const int rr = r < R ? r : r - R;
+      const int *Rv = M.Rge + 3 * rr;
+      const double2 ph = mesh_phase(D.ktab, D.km, a0, a1, a2, Rv[0], Rv[1], Rv[2]);
+      x[e] = r < R ? ph.x : ph.y;
+    }
+  }
+  uint4 o[8];
+  slices8(x, ns, o);
+  const int kch = k / nw, row = k % nw, kb = r0 / 16;
+  const size_t base = (size_t(kch) * nkb + kb) * ns;
+  for (int sl = 0; sl < ns; ++sl)
+    *reinterpret_cast<uint4 *>(phik + (base + sl) * (size_t(nw) * 16) + tile16_off(row, r0 % 16)) = o[sl];
+}
+
+// column j' = 2 col + part of T[k][col] = sum_Re e^{ik.Re} g[Re][col], col = (rp, m', n', alpha):
 //   part 0 (real): rows r < nRe: Re g[r][col];  r >= nRe: -Im g[r-nRe][col]
 //   part 1 (imag): rows r < nRe: Im g[r][col];  r >= nRe:  Re g[r-nRe][col]
-// GS[slice][Ncols][Kp] (BF16) and power-of-two column scales; one warp per column.
-__global__ void k_g_slices(ModelDev M, int ns, int Kp, int Ncols, __nv_bfloat16 *gs, double *gscale) {
+__device__ __forceinline__ double g_operand(const ModelDev &M, int64_t ncol, int jp, int r) {
+  const int R = M.nRge;
+  const int64_t col = jp / 2;
+  const double2 g = M.g_R[size_t(r < R ? r : r - R) * ncol + col];
+  return r < R ? ((jp & 1) == 0 ? g.x : g.y) : ((jp & 1) == 0 ? -g.y : g.x);
+}
+
+// power-of-two scale of each g column j' (>= its largest entry; 1 for a zero column); one warp
+// per column
+__global__ void k_g_scales(ModelDev M, int Ncols, double *gscale) {
   const int64_t w = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= Ncols) return;
   const int jp = int(w);
   const int64_t ncol = int64_t(M.nRgp) * M.nb * M.nb * M.nbr;
-  const int R = M.nRge;
-  const int64_t col = jp / 2;
-  const int part = jp & 1;
-  const bool live = col < ncol;
-  auto value = [&](int r) -> double {
-    const double2 g = M.g_R[size_t(r < R ? r : r - R) * ncol + col];
-    return r < R ? (part == 0 ? g.x : g.y) : (part == 0 ? -g.y : g.x);
-  };
+  const bool live = jp / 2 < ncol;
   double mx = 0.0;
-  for (int r = lane; r < 2 * R; r += 32)
-    if (live) mx = fmax(mx, fabs(value(r)));
+  for (int r = lane; r < 2 * M.nRge; r += 32)
+    if (live) mx = fmax(mx, fabs(g_operand(M, ncol, jp, r)));
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   int ex = 0;
   if (mx > 0.0) frexp(mx, &ex);
-  const double inv_sigma = mx > 0.0 ? ldexp(1.0, -ex) : 1.0;
   if (lane == 0) gscale[jp] = mx > 0.0 ? ldexp(1.0, ex) : 1.0;
-  for (int r = lane; r < Kp; r += 32) {
-    const double v = live && r < 2 * R ? value(r) : 0.0;
-    fixed_slices(v * inv_sigma, ns, gs + size_t(jp) * Kp + r, size_t(Ncols) * Kp);
-  }
+}
+
+// Slices of the model's g as the A operand of stage A, pre-tiled by 128 columns: one thread per
+// (column tile, K block, K half, row), 8 values each.  Columns past Ncols are zero rows.
+__global__ void k_g_slices(ModelDev M, int ns, int Kp, int Ncols, int nct, const double *gscale, __nv_bfloat16 *gs) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int nkb = Kp / 16;
+  if (t >= int64_t(nct) * nkb * 256) return;
+  const int row = int(t & 127), half = int((t >> 7) & 1);
+  const int64_t tk = t >> 8;
+  const int kb = int(tk % nkb), ct = int(tk / nkb);
+  const int jp = ct * kTcM + row;
+  const int64_t ncol = int64_t(M.nRgp) * M.nb * M.nb * M.nbr;
+  const bool live = jp < Ncols && jp / 2 < ncol;
+  const double inv = live ? 1.0 / gscale[jp] : 0.0;   // a power of two: exact
+  const int r0 = kb * 16 + half * 8;
+  double x[8];
+  for (int e = 0; e < 8; ++e) x[e] = live && r0 + e < 2 * M.nRge ? g_operand(M, ncol, jp, r0 + e) * inv : 0.0;
+  uint4 o[8];
+  slices8(x, ns, o);
+  const size_t base = (size_t(ct) * nkb + kb) * ns;
+  for (int sl = 0; sl < ns; ++sl)
+    *reinterpret_cast<uint4 *>(gs + (base + sl) * (size_t(kTcM) * 16) + tile16_off(row, half * 8)) = o[sl];
 }
 
 // work items of a chunk: (k, 128-pair tile, column chunk); per k: ceil(npl/128) * nchunk(k)
@@ -330,16 +381,47 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// wait for the completion of phase `phase` of an mbarrier; gives up after kWaitNs
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t phase) {
+  uint32_t done = 0;
+  asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(done) : "r"(mbar), "r"(phase) : "memory");
+  return done != 0;
+}
+
+// wait for the completion of phase `phase` of an mbarrier; gives up after kWaitNs (the timer is
+// read only once the first test has failed)
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+  if (mbar_try(mbar, phase)) return true;
   const uint64_t t0 = global_ns();
   for (;;) {
-    uint32_t done = 0;
-    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(done) : "r"(mbar), "r"(phase) : "memory");
-    if (done) return true;
+    if (mbar_try(mbar, phase)) return true;
     if (global_ns() - t0 > kWaitNs) return false;
   }
+}
+
+// The slice products of one K step of 16: A slice is (0-based) times B slice ls for every
+// is + ls <= NS - 1, diagonal d = is + ls into accumulator min(d, NACC - 1) (NACC == 1: all into
+// one), is-major.  ad0 / bd0: descriptors of slice 0 of A and B at this K step; slice i lies
+// i * a16 (b16) 16-byte units further (the descriptor's address field counts 16-byte units and
+// the shared window stays below 2^18 bytes, so adding to the descriptor moves the address).
+// FIRST: the first K step, whose first product into each accumulator overwrites it.  Fully
+// unrolled: a product costs the MMA and two 64-bit adds.
+template <int NS, int NACC, bool FIRST>
+__device__ __forceinline__ void slice_products(uint32_t tacc, uint32_t acc_cols, uint64_t ad0, uint64_t bd0,
+                                               uint32_t a16, uint32_t b16, uint32_t idesc) {
+#pragma unroll
+  for (int is = 0; is < NS; ++is)
+#pragma unroll
+    for (int ls = 0; ls < NS - is; ++ls) {
+      const int d = is + ls;
+      const int acc = NACC == 1 ? 0 : (d < NACC - 1 ? d : NACC - 1);
+      const bool first = FIRST && (NACC == 1 ? (is == 0 && ls == 0) :
+                                   (acc < NACC - 1 ? (is == 0) : (is == 0 && ls == NACC - 1)));
+      asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                   "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                   :: "r"(tacc + uint32_t(acc) * acc_cols), "l"(ad0 + uint64_t(is) * a16),
+                      "l"(bd0 + uint64_t(ls) * b16), "r"(idesc), "r"(first ? 0u : 1u));
+    }
 }
 
 // 16-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros
@@ -524,23 +606,16 @@ __global__ void __launch_bounds__(kTcThreads, (KC == 16 && ST == 2) ? 2 : 1) k_v
       // K-step-major order: every accumulator receives its products in the same sequence
       // whatever KC is, so the rounded tail accumulator (and the result) does not depend on
       // the tile shape
-      for (int ks = 0; ks < KC / 16; ++ks)
-        for (int is = 0; is < NS; ++is)
-          for (int ls = 0; ls < NS - is; ++ls) {   // diagonal d = is + ls <= NS - 1 (i + l <= NS + 1)
-            const int d = is + ls;
-            const int acc = NACC == 1 ? 0 : (d < NACC - 1 ? d : NACC - 1);
-            const uint32_t dtm = taddr + uint32_t(acc * nc);
-            const uint64_t ad = smem_desc(smem_u32(sA + is * a_slice) + ks * 256, 128u, (KC / 8) * 128u);
-            const uint64_t bd = smem_desc(smem_u32(sB + ls * b_slice) + ks * 256, 128u, (KC / 8) * 128u);
-            // the first product into each accumulator (first K block, first K step) overwrites it
-            const bool first = b == 0 && ks == 0 &&
-                               (NACC == 1 ? (is == 0 && ls == 0) :
-                                (acc < NACC - 1 ? (is == 0) : (is == 0 && ls == NACC - 1)));
-            const uint32_t en = first ? 0u : 1u;
-            asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                         :: "r"(dtm), "l"(ad), "l"(bd), "r"(idesc), "r"(en));
-          }
+      const uint64_t ad0 = smem_desc(smem_u32(sA), 128u, (KC / 8) * 128u);
+      const uint64_t bd0 = smem_desc(smem_u32(sB), 128u, (KC / 8) * 128u);
+      const uint32_t a16 = uint32_t(a_slice >> 4), b16 = uint32_t(b_slice >> 4);
+#pragma unroll
+      for (int ks = 0; ks < KC / 16; ++ks) {   // K step ks: 256 bytes (16 units) into each slice
+        if (b == 0 && ks == 0)
+          slice_products<NS, NACC, true>(taddr, uint32_t(nc), ad0, bd0, a16, b16, idesc);
+        else
+          slice_products<NS, NACC, false>(taddr, uint32_t(nc), ad0 + 16u * ks, bd0 + 16u * ks, a16, b16, idesc);
+      }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                    :: "r"(smem_u32(&mbar[buf])) : "memory");
     }
@@ -785,19 +860,14 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_vertex_gemm_ws(ModelDev M, Me
           if (!P.withhold) {
             const unsigned char *sA = smem + slot * stage_bytes;
             const unsigned char *sB = sA + NS * a_slice;
-            for (int is = 0; is < NS; ++is)
-              for (int ls = 0; ls < NS - is; ++ls) {
-                const int d = is + ls;
-                const int acc = NACC == 1 ? 0 : (d < NACC - 1 ? d : NACC - 1);
-                const uint32_t dtm = tbase + uint32_t(acc * w.nc);
-                const uint64_t ad = smem_desc(smem_u32(sA + is * a_slice), 128u, (KC / 8) * 128u);
-                const uint64_t bd = smem_desc(smem_u32(sB + ls * b_slice), 128u, (KC / 8) * 128u);
-                const bool first = kb == 0 && (NACC == 1 ? (is == 0 && ls == 0) :
-                                               (acc < NACC - 1 ? (is == 0) : (is == 0 && ls == NACC - 1)));
-                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                             :: "r"(dtm), "l"(ad), "l"(bd), "r"(idesc), "r"(first ? 0u : 1u));
-              }
+            const uint64_t ad0 = smem_desc(smem_u32(sA), 128u, (KC / 8) * 128u);
+            const uint64_t bd0 = smem_desc(smem_u32(sB), 128u, (KC / 8) * 128u);
+            if (kb == 0)
+              slice_products<NS, NACC, true>(tbase, uint32_t(w.nc), ad0, bd0, uint32_t(a_slice >> 4),
+                                             uint32_t(b_slice >> 4), idesc);
+            else
+              slice_products<NS, NACC, false>(tbase, uint32_t(w.nc), ad0, bd0, uint32_t(a_slice >> 4),
+                                              uint32_t(b_slice >> 4), idesc);
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          :: "r"(smem_u32(&empty[slot])) : "memory");
             any = true;
@@ -862,15 +932,35 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_vertex_gemm_ws(ModelDev M, Me
 // nw k points of the group.  The g slices (NS x Ncols x Kp, the large operand) then move from
 // DRAM once per k chunk, and consecutive work items -- taken by neighbouring CTAs at the same
 // time -- are the k chunks of one column tile, which share that tile through L2; the k phase
-// slices of the group (NS x nkc x Kp) stay in L2.  No row of a tile is padding except the
-// last column tile's, and a chunk's N is its k count rounded up to 16.  One accumulator set
-// of NACC x nw (<= 480) tensor-memory columns; its epilogue (the diagonals summed by TwoSum
-// into a float-float pair, scaled by the column's power of two, stored as two FP32 numbers)
-// runs under the next item's copies.  Roles and barriers as in k_vertex_gemm_ws with a single
-// accumulator buffer: accf completes once per item, acce once the 128 epilogue threads have
-// read it.  All waits bounded.
+// slices of the group stay in L2.  Both operands are pre-tiled (k_g_slices,
+// k_phase_slices_k), so a stage is two contiguous blocks: one thread moves them with two
+// cp.async.bulk copies that complete on the stage's mbarrier (expect_tx), all ST stages in
+// flight.  One accumulator set of NACC x nw (<= 480) tensor-memory columns; its epilogue (the
+// diagonals summed by TwoSum into a float-float pair, scaled by the column's power of two,
+// stored as two FP32 numbers) runs while the producer refills the stages.
+// Roles: warps 0-3 epilogue (tensor-memory lane quadrant w), warp 4 tensor-memory allocation
+// and (lane 0) every tcgen05.mma and commit, warp 5 lane 0 the bulk copies.  Barriers: full[s]
+// (the producer's expect_tx arrival plus the bytes of its two copies), empty[s] (the MMA commit
+// after the products that read stage s), accf (commit after an item's last products), acce
+// (128 epilogue threads have read the accumulators).  Every wait is bounded; on a timeout the
+// roles leave their loops, the producer waits (bounded) for its copies still in flight, the
+// MMA thread for its last commit, and the tensor memory is freed.
+constexpr int kSaThreads = 192;
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n"
+               :: "r"(mbar), "r"(bytes) : "memory");
+}
+
+// bulk global -> shared copy of `bytes` (16-byte aligned addresses, a multiple of 16 bytes)
+// completing on mbarrier `mbar`
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+
 template <int NS, int NACC, int ST>
-__global__ void __launch_bounds__(kWsThreads, 1) k_stage_a_ws(TcParams P, int64_t nitems, int nkch,
+__global__ void __launch_bounds__(kSaThreads, 1) k_stage_a_ws(TcParams P, int64_t nitems, int nkch,
                                                               const __nv_bfloat16 *__restrict__ gs,
                                                               const __nv_bfloat16 *__restrict__ phik,
                                                               const double *__restrict__ gscale, float2 *T,
@@ -883,14 +973,14 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_stage_a_ws(TcParams P, int64_
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (*reinterpret_cast<volatile int *>(err)) return;   // the whole CTA returns, before any barrier
   const int nw = P.nc_max;
-  const size_t a_slice = size_t(kTcM) * KC * 2, b_slice = size_t(nw) * KC * 2;
-  const size_t stage_bytes = size_t(NS) * (a_slice + b_slice);
-  const size_t gs_slice = size_t(P.Nmax) * P.Kp;   // GS[slice][Ncols][Kp]
+  const uint32_t a_slice = uint32_t(kTcM) * KC * 2, b_slice = uint32_t(nw) * KC * 2;
+  const uint32_t a_bytes = NS * a_slice, b_bytes = NS * b_slice;
+  const uint32_t stage_bytes = a_bytes + b_bytes;
   const int nkb = P.Kp / KC;
   const int nkc = int(P.nkc);
   if (tid == 0) {
     for (int i = 0; i < ST; ++i) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&full[i])), "r"(kWsCopyThreads));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&full[i])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&empty[i])));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&accf)));
@@ -910,68 +1000,52 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_stage_a_ws(TcParams P, int64_
     abort_flag = 1;
     atomicExch(err, 1);
   };
-  // item -> first column j0 of its tile, first k k0 of its chunk, live k count nk, MMA width ncw
-  auto decode = [&](int64_t item, int &j0, int &k0, int &nk, int &ncw) {
-    const int64_t ct = item / nkch;
-    const int kch = int(item - ct * nkch);
-    j0 = int(ct * kTcM);
+  // item -> column tile ct, k chunk kch, first k k0, live k count nk, MMA width ncw
+  auto decode = [&](int64_t item, int &ct, int &kch, int &k0, int &nk, int &ncw) {
+    ct = int(item / nkch);
+    kch = int(item - int64_t(ct) * nkch);
     k0 = kch * nw;
     nk = nkc - k0 < nw ? nkc - k0 : nw;
     ncw = round_up(nk, 16);
   };
 
-  if (warp >= 5) {
-    // ---------------- copies
-    const int ct = tid - 5 * 32;               // 0..127
-    const int g = ct & 1, r0 = ct >> 1;        // this thread's 16-byte piece and A rows r0, r0 + 64
-    uint32_t it = 0;
-    bool ok = true;
-    auto complete = [&](uint32_t j) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(smem_u32(&full[j % ST]));
-    };
-    for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-      int j0, k0, nk, ncw;
-      decode(item, j0, k0, nk, ncw);
-      const bool live0 = j0 + r0 < P.Nmax, live1 = j0 + r0 + 64 < P.Nmax;
-      const __nv_bfloat16 *a0 = gs + (live0 ? size_t(j0 + r0) * P.Kp : 0);
-      const __nv_bfloat16 *a1 = gs + (live1 ? size_t(j0 + r0 + 64) * P.Kp : 0);
-      for (int kb = 0; kb < nkb; ++kb) {
-        const uint32_t slot = it % ST;
-        if (it >= ST && !mbar_wait(smem_u32(&empty[slot]), ((it / ST) - 1) & 1)) {
-          give_up();
-          ok = false;
-          break;
+  if (warp == 5) {
+    // ---------------- bulk copies (one thread)
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      const unsigned char *gsb = reinterpret_cast<const unsigned char *>(gs);
+      const unsigned char *pkb = reinterpret_cast<const unsigned char *>(phik);
+      for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+        int ct, kch, k0, nk, ncw;
+        decode(item, ct, kch, k0, nk, ncw);
+        const unsigned char *asrc = gsb + size_t(ct) * nkb * a_bytes;
+        const unsigned char *bsrc = pkb + size_t(kch) * nkb * b_bytes;
+        for (int kb = 0; kb < nkb; ++kb) {
+          const uint32_t slot = it % ST;
+          if (it >= ST && !mbar_wait(smem_u32(&empty[slot]), ((it / ST) - 1) & 1)) {
+            give_up();
+            ok = false;
+            break;
+          }
+          if (abort_flag) {
+            ok = false;
+            break;
+          }
+          const uint32_t sA = smem_u32(smem + slot * stage_bytes);
+          const uint32_t fb = smem_u32(&full[slot]);
+          mbar_expect_tx(fb, stage_bytes);
+          bulk_g2s(sA, asrc + size_t(kb) * a_bytes, a_bytes, fb);
+          bulk_g2s(sA + a_bytes, bsrc + size_t(kb) * b_bytes, b_bytes, fb);
+          ++it;
         }
-        if (abort_flag) {
-          ok = false;
-          break;
-        }
-        unsigned char *sA = smem + slot * stage_bytes;
-        unsigned char *sB = sA + NS * a_slice;
-        const int kk = kb * KC + g * 8;
-        for (int sl = 0; sl < NS; ++sl) {
-          cp_async16(smem_u32(sA + sl * a_slice + core_off<KC>(r0, g)), a0 + sl * gs_slice + kk, live0 ? 16u : 0u);
-          cp_async16(smem_u32(sA + sl * a_slice + core_off<KC>(r0 + 64, g)), a1 + sl * gs_slice + kk,
-                     live1 ? 16u : 0u);
-        }
-        for (int rem = r0; rem < NS * ncw; rem += 64) {
-          const int sl = rem / ncw, row = rem - sl * ncw;
-          const bool lv = row < nk;
-          const __nv_bfloat16 *src = phik + (lv ? (size_t(k0 + row) * NS + sl) * P.Kp : 0) + kk;
-          cp_async16(smem_u32(sB + sl * b_slice + core_off<KC>(row, g)), src, lv ? 16u : 0u);
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        if (it >= ST - 2) {
-          asm volatile("cp.async.wait_group %0;" :: "n"(ST - 2) : "memory");
-          complete(it - (ST - 2));
-        }
-        ++it;
       }
+      // no copy may still be writing shared memory when the CTA leaves: wait (bounded) for the
+      // stages issued last (on the normal path the MMA thread has consumed them already)
+      for (uint32_t j = it >= ST ? it - ST : 0; j < it; ++j)
+        if (!mbar_wait(smem_u32(&full[j % ST]), (j / ST) & 1)) give_up();
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    if (ok)
-      for (uint32_t j = it >= ST - 2 ? it - (ST - 2) : 0; j < it; ++j) complete(j);
+    __syncwarp();
   } else if (warp == 4) {
     // ---------------- tensor-core products (one thread)
     if (lane == 0) {
@@ -979,8 +1053,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_stage_a_ws(TcParams P, int64_
       bool any = false;
       for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
         if (abort_flag) break;
-        int j0, k0, nk, ncw;
-        decode(item, j0, k0, nk, ncw);
+        int ct, kch, k0, nk, ncw;
+        decode(item, ct, kch, k0, nk, ncw);
         if (tcount >= 1 && !mbar_wait(smem_u32(&acce), (tcount - 1) & 1)) {
           give_up();
           break;
@@ -999,18 +1073,13 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_stage_a_ws(TcParams P, int64_
           asm volatile("tcgen05.fence::after_thread_sync;");
           if (!P.withhold) {
             const unsigned char *sA = smem + slot * stage_bytes;
-            const unsigned char *sB = sA + NS * a_slice;
-            for (int is = 0; is < NS; ++is)
-              for (int ls = 0; ls < NS - is; ++ls) {
-                const int d = is + ls;
-                const int acc = d < NACC - 1 ? d : NACC - 1;
-                const uint64_t ad = smem_desc(smem_u32(sA + is * a_slice), 128u, (KC / 8) * 128u);
-                const uint64_t bd = smem_desc(smem_u32(sB + ls * b_slice), 128u, (KC / 8) * 128u);
-                const bool first = kb == 0 && (acc < NACC - 1 ? (is == 0) : (is == 0 && ls == NACC - 1));
-                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                             :: "r"(taddr + uint32_t(acc * nw)), "l"(ad), "l"(bd), "r"(idesc), "r"(first ? 0u : 1u));
-              }
+            const unsigned char *sB = sA + a_bytes;
+            const uint64_t ad0 = smem_desc(smem_u32(sA), 128u, (KC / 8) * 128u);
+            const uint64_t bd0 = smem_desc(smem_u32(sB), 128u, (KC / 8) * 128u);
+            if (kb == 0)
+              slice_products<NS, NACC, true>(taddr, uint32_t(nw), ad0, bd0, a_slice >> 4, b_slice >> 4, idesc);
+            else
+              slice_products<NS, NACC, false>(taddr, uint32_t(nw), ad0, bd0, a_slice >> 4, b_slice >> 4, idesc);
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          :: "r"(smem_u32(&empty[slot])) : "memory");
             any = true;
@@ -1036,9 +1105,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_stage_a_ws(TcParams P, int64_
     const int row = warp * 32 + lane;
     uint32_t tcount = 0;
     for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
-      int j0, k0, nk, ncw;
-      decode(item, j0, k0, nk, ncw);
-      const int j = j0 + row;
+      int ct, kch, k0, nk, ncw;
+      decode(item, ct, kch, k0, nk, ncw);
+      const int j = ct * kTcM + row;
       const bool live = j < P.ncols;
       const float f = live ? pow2_float(gscale[j]) : 0.f;
       const bool waited = mbar_wait(smem_u32(&accf), tcount & 1);
@@ -1072,7 +1141,6 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_stage_a_ws(TcParams P, int64_
   __syncthreads();
   if (warp == 4) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(taddr));
 }
-
 }  // namespace
 
 int tc_kp(const ModelDev &M) { return round_up(2 * M.nRgp, kTcKc); }
@@ -1114,10 +1182,14 @@ std::vector<TcShape> tc_shape_candidates(int ns) {
 int tc_kp_a(const ModelDev &M) { return round_up(2 * M.nRge, kTcKc); }
 int tc_ncols_a(const ModelDev &M) { return round_up(2 * M.nRgp * M.nb * M.nb * M.nbr, 16); }
 
+static int stage_a_nct(const ModelDev &M) { return (tc_ncols_a(M) + kTcM - 1) / kTcM; }
+size_t tc_gs_elems_a(const ModelDev &M, int ns) { return size_t(ns) * stage_a_nct(M) * kTcM * tc_kp_a(M); }
+
 cudaError_t launch_g_slices(const ModelDev &M, int ns, __nv_bfloat16 *gs, double *gscale, cudaStream_t st) {
-  const int Ncols = tc_ncols_a(M);
-  EPHB_LAUNCH(k_g_slices, unsigned((int64_t(Ncols) * 32 + 255) / 256), 256, 0, st, M, ns, tc_kp_a(M), Ncols, gs,
-              gscale);
+  const int Ncols = tc_ncols_a(M), Kp = tc_kp_a(M), nct = stage_a_nct(M);
+  EPHB_LAUNCH(k_g_scales, unsigned((int64_t(Ncols) * 32 + 255) / 256), 256, 0, st, M, Ncols, gscale);
+  const int64_t n = int64_t(nct) * (Kp / 16) * 256;
+  EPHB_LAUNCH(k_g_slices, unsigned((n + 255) / 256), 256, 0, st, M, ns, Kp, Ncols, nct, gscale, gs);
   return cudaGetLastError();
 }
 
@@ -1131,6 +1203,13 @@ static int stage_a_chunk(int ns, int64_t nkc, int *nkch) {
   *nkch = int(n);
   return round_up(int((nkc + n - 1) / n), 16);
 }
+// rows of the phase-slice operand for any group of at most `chunk` k points: nkch x nw <=
+// chunk + 16 nkch
+size_t stage_a_phik_elems(const ModelDev &M, int ns, int64_t chunk) {
+  const int cap = (512 / nacc_of(ns)) / 16 * 16;
+  const int64_t rows = chunk + 16 * ((chunk + cap - 1) / cap);
+  return size_t(rows) * ns * tc_kp_a(M);
+}
 constexpr int kStageASt = 4;   // shared-memory stages of the stage-A pipeline
 
 cudaError_t launch_stage_a_tc(const ModelDev &M, const MeshDev &D, int ns, int64_t i0, int64_t nkc,
@@ -1139,12 +1218,13 @@ cudaError_t launch_stage_a_tc(const ModelDev &M, const MeshDev &D, int ns, int64
   if (nkc <= 0) return cudaSuccess;
   if (ns != 7 && ns != 8) return cudaErrorInvalidValue;
   const int Kp = tc_kp_a(M), Ncols = tc_ncols_a(M);
-  const int64_t n = nkc * int64_t(Kp);
-  EPHB_LAUNCH(k_phase_slices_k, unsigned((n + 255) / 256), 256, 0, st, M, D, i0, nkc, ns, Kp, phik);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
   int nkch = 0;
   const int nw = stage_a_chunk(ns, nkc, &nkch);
+  const int nrows = nkch * nw;
+  const int64_t n = int64_t(nrows) * (Kp / 8);
+  EPHB_LAUNCH(k_phase_slices_k, unsigned((n + 255) / 256), 256, 0, st, M, D, i0, nkc, nrows, nw, ns, Kp, phik);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   TcParams P;
   P.ns = ns;
   P.nacc = nacc_of(ns);
@@ -1157,7 +1237,7 @@ cudaError_t launch_stage_a_tc(const ModelDev &M, const MeshDev &D, int ns, int64
   P.ncols = 2 * M.nRgp * M.nb * M.nb * M.nbr;
   P.out_stride = P.ncols;
   P.withhold = 0;
-  const int64_t nct = (Ncols + kTcM - 1) / kTcM;
+  const int64_t nct = stage_a_nct(M);
   const int64_t nitems = nct * nkch;
   const size_t smem = size_t(kStageASt) * ns * (size_t(kTcM) * 16 * 2 + size_t(nw) * 16 * 2);
   int dev = 0, nsm = 0;
@@ -1169,7 +1249,7 @@ cudaError_t launch_stage_a_tc(const ModelDev &M, const MeshDev &D, int ns, int64
   auto go = [&](auto kern) -> cudaError_t {
     cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (r != cudaSuccess) return r;
-    EPHB_LAUNCH(kern, grid, kWsThreads, smem, st, P, nitems, nkch, gs, phik, gscale, out, err);
+    EPHB_LAUNCH(kern, grid, kSaThreads, smem, st, P, nitems, nkch, gs, phik, gscale, out, err);
     return cudaGetLastError();
   };
   e = ns == 8 ? go(k_stage_a_ws<8, 6, kStageASt>) : go(k_stage_a_ws<7, 5, kStageASt>);
