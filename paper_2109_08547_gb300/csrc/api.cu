@@ -169,6 +169,7 @@ struct ephb_ctx : InstState {
   int64_t n_ibzw = 0, n_pairs = 0;
   ephb_mesh_info minfo{};
   DBuf<double2> ktab, qtab, cvec, u;
+  DBuf<double2> interp;          // Fourier sums of H / D and their gradients for a list chunk
   DBuf<double> eps, vel, w, vph;
   DBuf<uint8_t> egrp, pgrp;
   DBuf<uint32_t> amask, rmask;
@@ -382,7 +383,7 @@ void ephb_destroy(ephb_ctx *ctx) {
   ctx->Re.release(); ctx->Rd.release(); ctx->Rge.release(); ctx->Rgp.release(); ctx->sym_rot.release();
   ctx->sym_inv.release(); ctx->H_R.release(); ctx->D_R.release(); ctx->g_R.release(); ctx->sym_cart.release();
   ctx->sym_pair.release();
-  ctx->ktab.release(); ctx->qtab.release(); ctx->cvec.release(); ctx->u.release(); ctx->eps.release();
+  ctx->ktab.release(); ctx->interp.release(); ctx->qtab.release(); ctx->cvec.release(); ctx->u.release(); ctx->eps.release();
   ctx->vel.release(); ctx->w.release(); ctx->vph.release(); ctx->egrp.release(); ctx->pgrp.release();
   ctx->qrep.release(); ctx->qop.release(); ctx->qstab.release(); ctx->qflag.release(); ctx->qlist.release();
   ctx->qrep_of.release(); ctx->qpos.release(); ctx->Afold.release(); ctx->atom_perm.release();
@@ -622,8 +623,12 @@ ephb_status ephb_build_meshes_ibz(ephb_ctx *ctx, const ephb_mesh_opts *o, ephb_m
   CK(cudaMemcpyAsync(&ctx->n_qrep, ctx->scal.p + 0, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   CK(launch_rep_index(nq, ctx->qlist.p, ctx->n_qrep, ctx->qrep_of.p, st));
+  auto interp_for = [&](int64_t n, int nmat) {
+    return ctx->interp.ensure(size_t(4) * nmat * nmat * size_t(std::min<int64_t>(n, interp_chunk())));
+  };
+  CK(interp_for(ctx->n_qrep, M.nbr));
   CK(launch_phonon_modes(M, qm, ctx->qlist.p, ctx->n_qrep, ctx->qtab.p, ctx->degen_tol, ctx->omega_min, ctx->w.p,
-                         ctx->u.p, ctx->vph.p, ctx->pgrp.p, st));
+                         ctx->u.p, ctx->vph.p, ctx->pgrp.p, ctx->interp.p, st));
   CK(launch_phonons_from_rep(M, qm, ctx->qtab.p, ctx->qrep.p, ctx->qop.p, ctx->w.p, ctx->u.p, ctx->vph.p,
                              ctx->pgrp.p, st));
   // Electron bands: eigen-decompositions on the representatives of the wedge first; a point whose
@@ -636,16 +641,18 @@ ephb_status ephb_build_meshes_ibz(ephb_ctx *ctx, const ephb_mesh_opts *o, ephb_m
   int64_t n_rep = 0, n_own = 0;
   CK(cudaMemcpyAsync(&n_rep, ctx->scal.p + 0, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  CK(interp_for(n_rep, M.nb));
   CK(launch_electron_bands(M, km, ctx->ibzw_of.p, n_rep, ctx->ktab.p, ctx->degen_tol, ctx->lo, ctx->hi, ctx->eps.p,
-                           ctx->cvec.p, ctx->vel.p, ctx->egrp.p, ctx->amask.p, ctx->rmask.p, st));
+                           ctx->cvec.p, ctx->vel.p, ctx->egrp.p, ctx->amask.p, ctx->rmask.p, ctx->interp.p, st));
   CK(launch_bands_from_rep(M, km, ctx->rep.p, ctx->op.p, ctx->eps.p, ctx->vel.p, ctx->egrp.p, ctx->amask.p,
                            ctx->rmask.p, ctx->flag.p, st));
   CK(exclusive_scan<int>(ctx->flag.p, ctx->pos.p, nk, ctx->scal.p + 0, ctx->scratch.p, ctx->scratch.n, st));
   CK(launch_compact(nk, ctx->flag.p, ctx->pos.p, ctx->ibzw_of.p, st));     // points decomposed themselves
   CK(cudaMemcpyAsync(&n_own, ctx->scal.p + 0, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  CK(interp_for(n_own, M.nb));
   CK(launch_electron_bands(M, km, ctx->ibzw_of.p, n_own, ctx->ktab.p, ctx->degen_tol, ctx->lo, ctx->hi, ctx->eps.p,
-                           ctx->cvec.p, ctx->vel.p, ctx->egrp.p, ctx->amask.p, ctx->rmask.p, st));
+                           ctx->cvec.p, ctx->vel.p, ctx->egrp.p, ctx->amask.p, ctx->rmask.p, ctx->interp.p, st));
   CK(launch_ibzw_flag(nk, ctx->rep.p, ctx->amask.p, ctx->flag.p, st));
   CK(exclusive_scan<int>(ctx->flag.p, ctx->pos.p, nk, ctx->scal.p + 0, ctx->scratch.p, ctx->scratch.n, st));
   CK(launch_count_bits(ctx->amask.p, nk, ctx->scal.p + 1, st));
@@ -1204,7 +1211,8 @@ ephb_status coefficients_to_host(ephb_ctx *ctx, double *prev, bool electron = tr
   MeshDev D = mesh_view(ctx);
   BteDev B = bte_view(ctx);
   if (electron) CK(launch_e_partial(B, ctx->I.p, ctx->J.p, ctx->epart.p, ctx->stream));
-  if (phonon) CK(launch_ph_partial(D, B, ctx->F.p, ctx->G.p, ctx->ppart.p, ctx->stream));
+  if (phonon)
+    CK(launch_ph_partial(D, B, ctx->F.p, ctx->G.p, ctx->W_ph.p, ctx->inv_nnW.p, ctx->ppart.p, ctx->stream));
   CK(launch_coeff_final(ctx->M, B, ctx->epart.p, ctx->ppart.p, ctx->res.p, prev, ctx->stream));
   CK(cudaMemcpyAsync(ctx->host_res, ctx->res.p, kResLen * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));

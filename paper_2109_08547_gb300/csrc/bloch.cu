@@ -19,52 +19,98 @@ __global__ void k_phase_tables(double2 *tab, Mesh m) {
   tab[t] = cmk(c, s);
 }
 
-// One thread per listed k point: H(k), grad_k H(k), eigen-decomposition, velocities.
+// ---- Fourier interpolation, one warp per point ------------------------------------------
+// O(k) = sum_R e^{i k.R} O_R and grad_k O(k) = sum_R i R e^{i k.R} O_R (Eqs. H_mn(k) and
+// D_ss'(q) and the Hellmann-Feynman velocities), for the points of a list.  The lanes share the
+// matrix elements (lane l takes elements l, l + 32, ...); lane l computes the phase and the
+// Cartesian R of the l-th vector of each block of 32, which the loop over R broadcasts by
+// shuffles.  Every element sums over R in the order of the R list, exactly as a thread that did
+// the whole matrix alone.  Output, transposed for the one-thread-per-point decomposition that
+// reads it: out[(v ne + e) ldn + t], v = 0 for O and 1..3 for the components of its gradient.
+constexpr int kInterpWarps = 4;
+
+template <int EPL>
+__global__ void __launch_bounds__(32 * kInterpWarps) k_fourier_interp(ModelDev M, Mesh m, const double2 *__restrict__ tab,
+                                                                   const int *__restrict__ list, int64_t n, int64_t ldn,
+                                                                   const int *__restrict__ Rv, int nR,
+                                                                   const double2 *__restrict__ OR, int ne,
+                                                                   double2 *__restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t t = blockIdx.x * int64_t(kInterpWarps) + (threadIdx.x >> 5);
+  if (t >= n) return;   // whole warps leave together
+  int i0, i1, i2;
+  m.unflat(list[t], i0, i1, i2);
+  double2 acc[EPL], grad[EPL][3];
+  for (int k = 0; k < EPL; ++k) {
+    acc[k] = cmk(0, 0);
+    grad[k][0] = grad[k][1] = grad[k][2] = cmk(0, 0);
+  }
+  for (int r0 = 0; r0 < nR; r0 += 32) {
+    double2 myph = cmk(0, 0);
+    double myR[3] = {0, 0, 0};
+    if (r0 + lane < nR) {
+      const int *R = Rv + 3 * (r0 + lane);
+      myph = mesh_phase(tab, m, i0, i1, i2, R[0], R[1], R[2]);
+      for (int a = 0; a < 3; ++a) myR[a] = R[0] * M.lattice[a] + R[1] * M.lattice[3 + a] + R[2] * M.lattice[6 + a];
+    }
+    const int nr = nR - r0 < 32 ? nR - r0 : 32;
+    for (int rr = 0; rr < nr; ++rr) {
+      const double2 ph = cmk(__shfl_sync(0xffffffffu, myph.x, rr), __shfl_sync(0xffffffffu, myph.y, rr));
+      double Rc[3];
+      for (int a = 0; a < 3; ++a) Rc[a] = __shfl_sync(0xffffffffu, myR[a], rr);
+      const double2 *h = OR + size_t(r0 + rr) * ne;
+      for (int k = 0; k < EPL; ++k) {
+        const int e = lane + 32 * k;
+        if (e < ne) {
+          const double2 tt = cmul(ph, h[e]);
+          acc[k] = cadd(acc[k], tt);
+          for (int a = 0; a < 3; ++a) {   // i R_a t
+            grad[k][a].x -= Rc[a] * tt.y;
+            grad[k][a].y += Rc[a] * tt.x;
+          }
+        }
+      }
+    }
+  }
+  for (int k = 0; k < EPL; ++k) {
+    const int e = lane + 32 * k;
+    if (e < ne) {
+      out[size_t(e) * ldn + t] = acc[k];
+      for (int a = 0; a < 3; ++a) out[size_t((1 + a) * ne + e) * ldn + t] = grad[k][a];
+    }
+  }
+}
+
+// One thread per listed k point: eigen-decomposition of H(k) (read from the interpolation),
+// velocities <m| grad H |m> averaged over degenerate groups, the window masks.
 template <int NB>
-__global__ void __launch_bounds__(32) k_electron_bands(ModelDev M, Mesh km, const int *__restrict__ list, int64_t n,
-                                                        const double2 *__restrict__ ktab,
-                                                        double degen_tol, double lo, double hi, double *eps,
-                                                        double2 *cvec, double *vel, uint8_t *egrp,
-                                                        uint32_t *amask, uint32_t *rmask) {
+__global__ void __launch_bounds__(64) k_electron_bands(ModelDev M, Mesh km, const int *__restrict__ list, int64_t n,
+                                                       const double2 *__restrict__ HdH, int64_t ldn,
+                                                       double degen_tol, double lo, double hi, double *eps,
+                                                       double2 *cvec, double *vel, uint8_t *egrp,
+                                                       uint32_t *amask, uint32_t *rmask) {
   const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (t >= n) return;
   const int k = list[t];
-  const int nb = M.nb;
-  int i0, i1, i2;
-  km.unflat(k, i0, i1, i2);
-  double2 H[NB * NB], dH[3][NB * NB], V[NB * NB];
+  const int nb = M.nb, ne = nb * nb;
+  double2 H[NB * NB], V[NB * NB];
   double e[NB];
-  for (int t = 0; t < NB * NB; ++t) {
-    H[t] = cmk(0, 0);
-    dH[0][t] = dH[1][t] = dH[2][t] = cmk(0, 0);
-  }
-  for (int r = 0; r < M.nRe; ++r) {
-    const int r0 = M.Re[3 * r], r1 = M.Re[3 * r + 1], r2 = M.Re[3 * r + 2];
-    double2 ph = mesh_phase(ktab, km, i0, i1, i2, r0, r1, r2);
-    double Rc[3];
-    for (int a = 0; a < 3; ++a) Rc[a] = r0 * M.lattice[a] + r1 * M.lattice[3 + a] + r2 * M.lattice[6 + a];
-    const double2 *h = M.H_R + size_t(r) * nb * nb;
-    for (int i = 0; i < nb; ++i)
-      for (int j = 0; j < nb; ++j) {
-        double2 t = cmul(ph, h[i * nb + j]);
-        H[i * NB + j] = cadd(H[i * NB + j], t);
-        for (int a = 0; a < 3; ++a) {  // i R_a t
-          dH[a][i * NB + j].x -= Rc[a] * t.y;
-          dH[a][i * NB + j].y += Rc[a] * t.x;
-        }
-      }
-  }
+  for (int i = 0; i < nb; ++i)
+    for (int j = 0; j < nb; ++j) H[i * NB + j] = HdH[size_t(i * nb + j) * ldn + t];
   herm_jacobi<NB>(H, V, e, nb);
+  // v_m = <m| grad H |m>: for each component and row i, w_m = sum_j dH_ij V_jm, then
+  // v_m += Re(conj(V_im) w_m); every gradient element is read once
   double vd[NB][3];
-  for (int m = 0; m < nb; ++m)
-    for (int a = 0; a < 3; ++a) {
-      double acc = 0.0;
-      for (int i = 0; i < nb; ++i) {
-        double2 row = cmk(0, 0);
-        for (int j = 0; j < nb; ++j) cfma(row, dH[a][i * NB + j], V[j * NB + m]);
-        acc += V[i * NB + m].x * row.x + V[i * NB + m].y * row.y;   // Re(conj(V_im) row_i)
+  for (int m = 0; m < nb; ++m) vd[m][0] = vd[m][1] = vd[m][2] = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int i = 0; i < nb; ++i) {
+      double2 w[NB];
+      for (int m = 0; m < nb; ++m) w[m] = cmk(0, 0);
+      for (int j = 0; j < nb; ++j) {
+        const double2 d = HdH[size_t((1 + a) * ne + i * nb + j) * ldn + t];
+        for (int m = 0; m < nb; ++m) cfma(w[m], d, V[j * NB + m]);
       }
-      vd[m][a] = acc;
+      for (int m = 0; m < nb; ++m) vd[m][a] += V[i * NB + m].x * w[m].x + V[i * NB + m].y * w[m].y;
     }
   uint8_t grp[2 * NB];
   degenerate_groups(e, nb, degen_tol, grp);
@@ -93,54 +139,35 @@ __global__ void __launch_bounds__(32) k_electron_bands(ModelDev M, Mesh km, cons
   rmask[k] = rot;
 }
 
-// One thread per listed q point: D(q), eigen-decomposition, hbar w = sqrt(max(lambda,0)),
-// velocities.
+// One thread per listed q point: eigen-decomposition of D(q) (read from the interpolation),
+// hbar w = sqrt(max(lambda, 0)), velocities.
 template <int NB>
-__global__ void __launch_bounds__(32) k_phonon_modes(ModelDev M, Mesh qm, const int *__restrict__ list, int64_t n,
-                                                      const double2 *__restrict__ qtab,
-                                                      double degen_tol, double omega_min, double *w, double2 *u,
-                                                      double *vph, uint8_t *pgrp) {
+__global__ void __launch_bounds__(64) k_phonon_modes(ModelDev M, Mesh qm, const int *__restrict__ list, int64_t n,
+                                                     const double2 *__restrict__ DdD, int64_t ldn,
+                                                     double degen_tol, double omega_min, double *w, double2 *u,
+                                                     double *vph, uint8_t *pgrp) {
   const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (t >= n) return;
   const int q = list[t];
-  const int nb = M.nbr;
-  int i0, i1, i2;
-  qm.unflat(q, i0, i1, i2);
-  double2 D[NB * NB], dD[3][NB * NB], V[NB * NB];
+  const int nb = M.nbr, ne = nb * nb;
+  double2 D[NB * NB], V[NB * NB];
   double e[NB];
-  for (int t = 0; t < NB * NB; ++t) {
-    D[t] = cmk(0, 0);
-    dD[0][t] = dD[1][t] = dD[2][t] = cmk(0, 0);
-  }
-  for (int r = 0; r < M.nRd; ++r) {
-    const int r0 = M.Rd[3 * r], r1 = M.Rd[3 * r + 1], r2 = M.Rd[3 * r + 2];
-    double2 ph = mesh_phase(qtab, qm, i0, i1, i2, r0, r1, r2);
-    double Rc[3];
-    for (int a = 0; a < 3; ++a) Rc[a] = r0 * M.lattice[a] + r1 * M.lattice[3 + a] + r2 * M.lattice[6 + a];
-    const double2 *h = M.D_R + size_t(r) * nb * nb;
-    for (int i = 0; i < nb; ++i)
-      for (int j = 0; j < nb; ++j) {
-        double2 t = cmul(ph, h[i * nb + j]);
-        D[i * NB + j] = cadd(D[i * NB + j], t);
-        for (int a = 0; a < 3; ++a) {
-          dD[a][i * NB + j].x -= Rc[a] * t.y;
-          dD[a][i * NB + j].y += Rc[a] * t.x;
-        }
-      }
-  }
+  for (int i = 0; i < nb; ++i)
+    for (int j = 0; j < nb; ++j) D[i * NB + j] = DdD[size_t(i * nb + j) * ldn + t];
   herm_jacobi<NB>(D, V, e, nb);
   double om[NB];
   for (int s = 0; s < nb; ++s) om[s] = sqrt(fmax(e[s], 0.0));
   double vd[NB][3];
-  for (int s = 0; s < nb; ++s)
-    for (int a = 0; a < 3; ++a) {
-      double acc = 0.0;
-      for (int i = 0; i < nb; ++i) {
-        double2 row = cmk(0, 0);
-        for (int j = 0; j < nb; ++j) cfma(row, dD[a][i * NB + j], V[j * NB + s]);
-        acc += V[i * NB + s].x * row.x + V[i * NB + s].y * row.y;
+  for (int s = 0; s < nb; ++s) vd[s][0] = vd[s][1] = vd[s][2] = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int i = 0; i < nb; ++i) {
+      double2 ws[NB];
+      for (int s = 0; s < nb; ++s) ws[s] = cmk(0, 0);
+      for (int j = 0; j < nb; ++j) {
+        const double2 d = DdD[size_t((1 + a) * ne + i * nb + j) * ldn + t];
+        for (int s = 0; s < nb; ++s) cfma(ws[s], d, V[j * NB + s]);
       }
-      vd[s][a] = acc;
+      for (int s = 0; s < nb; ++s) vd[s][a] += V[i * NB + s].x * ws[s].x + V[i * NB + s].y * ws[s].y;
     }
   uint8_t grp[2 * NB];
   degenerate_groups(om, nb, degen_tol, grp);
@@ -427,23 +454,47 @@ cudaError_t launch_phase_tables(double2 *tab, Mesh m, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// the interpolation of a list, in chunks of at most interp_chunk() points (scratch: 4 ne x chunk)
+int64_t interp_chunk() { return 65536; }
+
+static cudaError_t fourier_interp(const ModelDev &M, Mesh m, const double2 *tab, const int *list, int64_t n,
+                                  int64_t ldn, const int *Rv, int nR, const double2 *OR, int ne, double2 *out,
+                                  cudaStream_t st) {
+  const unsigned grid = unsigned((n + kInterpWarps - 1) / kInterpWarps);
+  if (ne <= 32)
+    EPHB_LAUNCH(k_fourier_interp<1>, grid, 32 * kInterpWarps, 0, st, M, m, tab, list, n, ldn, Rv, nR, OR, ne, out);
+  else if (ne <= 64)
+    EPHB_LAUNCH(k_fourier_interp<2>, grid, 32 * kInterpWarps, 0, st, M, m, tab, list, n, ldn, Rv, nR, OR, ne, out);
+  else
+    EPHB_LAUNCH(k_fourier_interp<5>, grid, 32 * kInterpWarps, 0, st, M, m, tab, list, n, ldn, Rv, nR, OR, ne, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_electron_bands(const ModelDev &M, Mesh km, const int *list, int64_t n, const double2 *ktab,
                                   double degen_tol, double lo, double hi, double *eps, double2 *cvec, double *vel,
-                                  uint8_t *egrp, uint32_t *amask, uint32_t *rmask, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  // one warp per block: the decomposition is FP64-bound per thread, so the warps are spread
-  // over every SM instead of filling a few
-  const int grid = int((n + 31) / 32), bs = 32;
-  if (M.nb <= 1)
-    EPHB_LAUNCH(k_electron_bands<1>, grid, bs, 0, st, M, km, list, n, ktab, degen_tol, lo, hi, eps, cvec, vel, egrp,
-                amask, rmask);
-  else if (M.nb <= 4)
-    EPHB_LAUNCH(k_electron_bands<4>, grid, bs, 0, st, M, km, list, n, ktab, degen_tol, lo, hi, eps, cvec, vel, egrp,
-                amask, rmask);
-  else
-    EPHB_LAUNCH(k_electron_bands<8>, grid, bs, 0, st, M, km, list, n, ktab, degen_tol, lo, hi, eps, cvec, vel, egrp,
-                amask, rmask);
-  return cudaGetLastError();
+                                  uint8_t *egrp, uint32_t *amask, uint32_t *rmask, double2 *scratch,
+                                  cudaStream_t st) {
+  const int ne = M.nb * M.nb;
+  for (int64_t c0 = 0; c0 < n; c0 += interp_chunk()) {
+    const int64_t nc = n - c0 < interp_chunk() ? n - c0 : interp_chunk();
+    cudaError_t e = fourier_interp(M, km, ktab, list + c0, nc, nc, M.Re, M.nRe, M.H_R, ne, scratch, st);
+    if (e != cudaSuccess) return e;
+    // two warps per block: the decomposition is FP64-bound per thread, so the warps are spread
+    // over every SM instead of filling a few
+    const int grid = int((nc + 63) / 64), bs = 64;
+    if (M.nb <= 1)
+      EPHB_LAUNCH(k_electron_bands<1>, grid, bs, 0, st, M, km, list + c0, nc, scratch, nc, degen_tol, lo, hi, eps, cvec,
+                  vel, egrp, amask, rmask);
+    else if (M.nb <= 4)
+      EPHB_LAUNCH(k_electron_bands<4>, grid, bs, 0, st, M, km, list + c0, nc, scratch, nc, degen_tol, lo, hi, eps, cvec,
+                  vel, egrp, amask, rmask);
+    else
+      EPHB_LAUNCH(k_electron_bands<8>, grid, bs, 0, st, M, km, list + c0, nc, scratch, nc, degen_tol, lo, hi, eps, cvec,
+                  vel, egrp, amask, rmask);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_bands_from_rep(const ModelDev &M, Mesh km, const int *rep, const int *op, double *eps, double *vel,
@@ -465,16 +516,26 @@ cudaError_t launch_compact(int64_t n, const int *flag, const int64_t *pos, int *
 
 cudaError_t launch_phonon_modes(const ModelDev &M, Mesh qm, const int *list, int64_t n, const double2 *qtab,
                                 double degen_tol, double omega_min, double *w, double2 *u, double *vph, uint8_t *pgrp,
-                                cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  const int grid = int((n + 31) / 32), bs = 32;   // one warp per block, as for the bands
-  if (M.nbr <= 3)
-    EPHB_LAUNCH(k_phonon_modes<3>, grid, bs, 0, st, M, qm, list, n, qtab, degen_tol, omega_min, w, u, vph, pgrp);
-  else if (M.nbr <= 6)
-    EPHB_LAUNCH(k_phonon_modes<6>, grid, bs, 0, st, M, qm, list, n, qtab, degen_tol, omega_min, w, u, vph, pgrp);
-  else
-    EPHB_LAUNCH(k_phonon_modes<12>, grid, bs, 0, st, M, qm, list, n, qtab, degen_tol, omega_min, w, u, vph, pgrp);
-  return cudaGetLastError();
+                                double2 *scratch, cudaStream_t st) {
+  const int ne = M.nbr * M.nbr;
+  for (int64_t c0 = 0; c0 < n; c0 += interp_chunk()) {
+    const int64_t nc = n - c0 < interp_chunk() ? n - c0 : interp_chunk();
+    cudaError_t e = fourier_interp(M, qm, qtab, list + c0, nc, nc, M.Rd, M.nRd, M.D_R, ne, scratch, st);
+    if (e != cudaSuccess) return e;
+    const int grid = int((nc + 63) / 64), bs = 64;
+    if (M.nbr <= 3)
+      EPHB_LAUNCH(k_phonon_modes<3>, grid, bs, 0, st, M, qm, list + c0, nc, scratch, nc, degen_tol, omega_min, w, u, vph,
+                  pgrp);
+    else if (M.nbr <= 6)
+      EPHB_LAUNCH(k_phonon_modes<6>, grid, bs, 0, st, M, qm, list + c0, nc, scratch, nc, degen_tol, omega_min, w, u, vph,
+                  pgrp);
+    else
+      EPHB_LAUNCH(k_phonon_modes<12>, grid, bs, 0, st, M, qm, list + c0, nc, scratch, nc, degen_tol, omega_min, w, u,
+                  vph, pgrp);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_phonons_from_rep(const ModelDev &M, Mesh qm, const double2 *qtab, const int *qrep, const int *qop,

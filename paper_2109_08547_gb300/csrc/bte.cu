@@ -834,23 +834,26 @@ __global__ void __launch_bounds__(kCT) k_e_partial(BteDev B, const double *I, co
   block_reduce_store(acc, kNE, epart + size_t(blockIdx.x) * kNE);
 }
 
+// w n(1+n) of a mode from the RTA tables of the solve (n(1+n) = 1 / (inv_nnW W)), instead of
+// the Bose factor's exponential per call
 __global__ void __launch_bounds__(kCT) k_ph_partial(MeshDev D, BteDev B, const double *F, const double *G,
-                                                    double *ppart) {
+                                                    const double *__restrict__ W_ph,
+                                                    const double *__restrict__ inv_nnW, double *ppart) {
   double acc[kNP];
   for (int j = 0; j < kNP; ++j) acc[j] = 0.0;
   const int64_t stride = int64_t(gridDim.x) * kCT;
-  const double kT = kKbEVK * B.T;
   for (int64_t t = blockIdx.x * int64_t(kCT) + threadIdx.x; t < B.nq * B.nbr; t += stride) {
-    double w = D.w[t];
-    if (!(w > D.omega_min)) continue;
-    double n = bose_b(w, kT);
-    double wt = w * n * (1.0 + n);
+    const double w = D.w[t], W = W_ph[t];
+    if (!(w > D.omega_min) || !(W > 0.0)) continue;
+    const double wt = w / (inv_nnW[t] * W);
     const double *v = D.vph + t * 3;
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < 3; ++a) {
+      const double u = wt * v[a];
       for (int b = 0; b < 3; ++b) {
-        acc[a * 3 + b] += -wt * v[a] * G[t * 3 + b];
-        acc[9 + a * 3 + b] += wt * v[a] * F[t * 3 + b];
+        acc[a * 3 + b] -= u * G[t * 3 + b];
+        acc[9 + a * 3 + b] += u * F[t * 3 + b];
       }
+    }
   }
   block_reduce_store(acc, kNP, ppart + size_t(blockIdx.x) * kNP);
 }
@@ -1375,9 +1378,9 @@ cudaError_t launch_e_partial(const BteDev &B, const double *I, const double *J, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_ph_partial(const MeshDev &D, const BteDev &B, const double *F, const double *G, double *ppart,
-                              cudaStream_t st) {
-  EPHB_LAUNCH(k_ph_partial, kNPart, kCT, 0, st, D, B, F, G, ppart);
+cudaError_t launch_ph_partial(const MeshDev &D, const BteDev &B, const double *F, const double *G, const double *W_ph,
+                              const double *inv_nnW, double *ppart, cudaStream_t st) {
+  EPHB_LAUNCH(k_ph_partial, kNPart, kCT, 0, st, D, B, F, G, W_ph, inv_nnW, ppart);
   return cudaGetLastError();
 }
 

@@ -72,16 +72,21 @@ int64_t scan_scratch_elems(int64_t n);
 
 // ---- bloch.cu
 cudaError_t launch_phase_tables(double2 *tab, Mesh m, cudaStream_t st);
+// Bands / phonons of the points of a list: the Fourier sums of H (D) and its gradient by
+// k_fourier_interp into scratch (4 nb^2 x min(n, interp_chunk()) complex), then the
+// eigen-decompositions.
+int64_t interp_chunk();
 cudaError_t launch_electron_bands(const ModelDev &M, Mesh km, const int *list, int64_t n, const double2 *ktab,
                                   double degen_tol, double lo, double hi, double *eps, double2 *cvec, double *vel,
-                                  uint8_t *egrp, uint32_t *amask, uint32_t *rmask, cudaStream_t st);
+                                  uint8_t *egrp, uint32_t *amask, uint32_t *rmask, double2 *scratch,
+                                  cudaStream_t st);
 cudaError_t launch_bands_from_rep(const ModelDev &M, Mesh km, const int *rep, const int *op, double *eps, double *vel,
                                   uint8_t *egrp, uint32_t *amask, uint32_t *rmask, int *flag, cudaStream_t st);
 cudaError_t launch_ibzw_flag(int64_t nk, const int *rep, const uint32_t *amask, int *flag, cudaStream_t st);
 cudaError_t launch_compact(int64_t n, const int *flag, const int64_t *pos, int *list, cudaStream_t st);
 cudaError_t launch_phonon_modes(const ModelDev &M, Mesh qm, const int *list, int64_t n, const double2 *qtab,
                                 double degen_tol, double omega_min, double *w, double2 *u, double *vph, uint8_t *pgrp,
-                                cudaStream_t st);
+                                double2 *scratch, cudaStream_t st);
 cudaError_t launch_ibz(const ModelDev &M, Mesh km, int *rep, int *op, int *stab, int *flag, cudaStream_t st);
 cudaError_t launch_phonons_from_rep(const ModelDev &M, Mesh qm, const double2 *qtab, const int *qrep, const int *qop,
                                     double *w, double2 *u, double *vph, uint8_t *pgrp, cudaStream_t st);
@@ -277,8 +282,8 @@ cudaError_t launch_ph_update(const ModelDev &M, const MeshDev &D, const double *
 constexpr int kResLen = 80;
 int coeff_partials();
 cudaError_t launch_e_partial(const BteDev &B, const double *I, const double *J, double *epart, cudaStream_t st);
-cudaError_t launch_ph_partial(const MeshDev &D, const BteDev &B, const double *F, const double *G, double *ppart,
-                              cudaStream_t st);
+cudaError_t launch_ph_partial(const MeshDev &D, const BteDev &B, const double *F, const double *G, const double *W_ph,
+                              const double *inv_nnW, double *ppart, cudaStream_t st);
 // Mixed-precision electron loop: FP32 copies, the correction start r = x' - x (d = r), one FP32
 // correction sweep d_out = r + (1/(f(1-f)W)) sum_runs w d[partner], and x += d.
 cudaError_t launch_to_f32(int64_t n, const double *a, float *b, cudaStream_t st);
