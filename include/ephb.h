@@ -406,6 +406,12 @@ typedef enum {
  * stay.  This is what the library does by itself when the instances' lists would exceed half of
  * the free device memory; the key forces it (the results are the same).  Value 0: automatic. */
 #define EPHB_TUNE_DEFER_INSTANCES 2
+/* EPHB_TUNE_STAGE_A_TMEM_A, value 1: the tensor-core stage A (R_e contraction) copies its A
+ * slices into tensor memory once per K step (tcgen05.cp) and the products read them there
+ * instead of from shared memory; before overwriting an A buffer it waits for the products that
+ * read it.  Value 0 (default): every product reads its A slice from shared memory, which
+ * measured faster.  The results are bit-identical. */
+#define EPHB_TUNE_STAGE_A_TMEM_A 3
 ephb_status ephb_set_tuning(ephb_ctx *ctx, int key, int value);
 
 /* Make instance inst the one whose arrays the views and copies below return (and the one

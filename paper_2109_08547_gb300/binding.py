@@ -301,6 +301,7 @@ def compute_transition_rates(ctx: Context, T_K, mu_eV, sigma_eV=0.01, cutoff_sig
 TUNE_TC_COLS = 0
 TUNE_WITHHOLD_MMA = 1
 TUNE_DEFER_INSTANCES = 2
+TUNE_STAGE_A_TMEM_A = 3
 
 
 def set_tuning(ctx: Context, key: int, value: int) -> None:

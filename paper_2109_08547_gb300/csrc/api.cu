@@ -233,6 +233,7 @@ struct ephb_ctx : InstState {
   int force_cols = 0;
   int withhold_mma = 0;   // failure-path check (EPHB_TUNE_WITHHOLD_MMA)
   int force_defer = 0;    // EPHB_TUNE_DEFER_INSTANCES: derive instance lists at solve time always
+  int stage_a_tmem = 0;   // EPHB_TUNE_STAGE_A_TMEM_A: stage A's A slices through tensor memory
   double *host_res = nullptr;   // pinned: kResLen doubles, then the sweep-loop control (4 ints)
 };
 
@@ -287,6 +288,7 @@ MeshDev mesh_view(ephb_ctx *c) {
   D.qop = c->qop.p;
   D.qrep_of = c->qrep_of.p;
   D.qlist = c->qlist.p;
+  D.qstab = c->qstab.p;
   D.n_qrep = c->n_qrep;
   D.w = c->w.p;
   D.u = c->u.p;
@@ -1002,7 +1004,7 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
       CK(ta.start(st));
       if (tensor_a) {
         CK(launch_stage_a_tc(M, D, ns_a, a0, na, ctx->phik.p, ctx->gslices.p, ctx->gscale.p, ctx->Tbuf.p,
-                             ctx->tc_err.p, st, &tensor_flops_a));
+                             ctx->tc_err.p, ctx->stage_a_tmem != 0, st, &tensor_flops_a));
         CK(launch_stage_a2(M, D, a0, na, ctx->Tbuf.p, ctx->Abuf.p, true, st));
       } else {
         CK(launch_stage_a(M, D, a0, na, ctx->Tbuf.p, ctx->Abuf.p, st));
@@ -1799,6 +1801,10 @@ ephb_status ephb_set_tuning(ephb_ctx *ctx, int key, int value) {
   }
   if (key == EPHB_TUNE_DEFER_INSTANCES) {
     ctx->force_defer = value ? 1 : 0;
+    return EPHB_OK;
+  }
+  if (key == EPHB_TUNE_STAGE_A_TMEM_A) {
+    ctx->stage_a_tmem = value ? 1 : 0;
     return EPHB_OK;
   }
   if (key != EPHB_TUNE_TC_COLS) return fail(ctx, EPHB_EINVAL, "unknown tuning key");

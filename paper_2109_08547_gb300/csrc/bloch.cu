@@ -241,38 +241,41 @@ __global__ void k_rep_index(int64_t nlist, const int *list, int *of) {
 
 // Irreducible wedge: representative = smallest image index, first op S with S<k> = k,
 // stabiliser size.  flag = 1 for the representatives.
+// Representative <k> of each mesh point (the smallest flat index of its star), the first
+// operation S with S <k> = k and the order of the stabiliser of <k>, in one pass over the
+// group.  With img_s = S_s k and <k> = min_s img_s, the set H = {s : img_s = <k>} is a coset
+// of the stabiliser of <k> (so |H| = |stab(<k>)|), and S_s <k> = k exactly when s^-1 is in H:
+// the operation sought is the first s whose inverse lies in H.
 __global__ void k_ibz(ModelDev M, Mesh km, int *rep, int *op, int *stab, int *flag) {
   __shared__ int rot[kMaxSym * 9];
+  __shared__ int inv[kMaxSym];
   for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) rot[t] = M.sym_rot[t];
+  for (int t = threadIdx.x; t < M.nsym; t += blockDim.x) inv[t] = M.sym_inv[t];
   __syncthreads();
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= km.size()) return;
   int i[3];
   km.unflat(k, i[0], i[1], i[2]);
   int best = k;
+  uint64_t hit = 0;   // operations s with img_s == best
   for (int s = 0; s < M.nsym; ++s) {
     const int *S = rot + 9 * s;
     int j0 = pmod(S[0] * i[0] + S[1] * i[1] + S[2] * i[2], km.n[0]);
     int j1 = pmod(S[3] * i[0] + S[4] * i[1] + S[5] * i[2], km.n[1]);
     int j2 = pmod(S[6] * i[0] + S[7] * i[1] + S[8] * i[2], km.n[2]);
     int img = km.flat(j0, j1, j2);
-    best = img < best ? img : best;
+    if (img < best) {
+      best = img;
+      hit = 0;
+    }
+    if (img == best) hit |= 1ull << s;
   }
-  int r[3];
-  km.unflat(best, r[0], r[1], r[2]);
-  int first = -1, ns = 0;
-  for (int s = 0; s < M.nsym; ++s) {
-    const int *S = rot + 9 * s;
-    int j0 = pmod(S[0] * r[0] + S[1] * r[1] + S[2] * r[2], km.n[0]);
-    int j1 = pmod(S[3] * r[0] + S[4] * r[1] + S[5] * r[2], km.n[1]);
-    int j2 = pmod(S[6] * r[0] + S[7] * r[1] + S[8] * r[2], km.n[2]);
-    int img = km.flat(j0, j1, j2);
-    if (img == k && first < 0) first = s;
-    if (img == best) ++ns;
-  }
+  int first = -1;
+  for (int s = 0; s < M.nsym && first < 0; ++s)
+    if ((hit >> inv[s]) & 1ull) first = s;
   rep[k] = best;
   op[k] = first;
-  stab[k] = ns;
+  stab[k] = __popcll(hit);
   flag[k] = best == k ? 1 : 0;
 }
 

@@ -710,8 +710,12 @@ __device__ void coeff_final_body(const ModelDev &M, const BteDev &B, const doubl
     double s = 0.0;
     for (int ef = 0; ef < 9; ++ef) s += M.sym_pair[ab * 9 + ef] * Mc[ef];
     R[t] = (c < 2 ? 1.0 : -1.0) * B.Pe * s;
-  } else if (t < 54) {
-    R[t] = B.Pph * Ms[t];
+  } else if (t < 54) {   // phonon tensors: the group sum of the wedge sums
+    const int c = (t - 36) / 9, ab = (t - 36) % 9;
+    const double *Mc = Ms + 36 + 9 * c;
+    double s = 0.0;
+    for (int ef = 0; ef < 9; ++ef) s += M.sym_pair[ab * 9 + ef] * Mc[ef];
+    R[t] = B.Pph * s;
   }
   __syncthreads();
   if (t < 9) {    // adjugate of sigma
@@ -834,18 +838,23 @@ __global__ void __launch_bounds__(kCT) k_e_partial(BteDev B, const double *I, co
   block_reduce_store(acc, kNE, epart + size_t(blockIdx.x) * kNE);
 }
 
-// w n(1+n) of a mode from the RTA tables of the solve (n(1+n) = 1 / (inv_nnW W)), instead of
-// the Bose factor's exponential per call
+// Phonon coefficient sums over the representatives of the q wedge, each weighted by
+// 1/|stabiliser|: the responses, velocities and weights are covariant (F(S q) = C_S F(q)), so
+// the sum over a star is (1/|stab|) sum_S C_S M(<q>) C_S^T, and the assembly applies the group
+// sum.  w n(1+n) comes from the solve's RTA tables (n(1+n) = 1 / (inv_nnW W)) instead of the
+// Bose factor's exponential.
 __global__ void __launch_bounds__(kCT) k_ph_partial(MeshDev D, BteDev B, const double *F, const double *G,
                                                     const double *__restrict__ W_ph,
                                                     const double *__restrict__ inv_nnW, double *ppart) {
   double acc[kNP];
   for (int j = 0; j < kNP; ++j) acc[j] = 0.0;
   const int64_t stride = int64_t(gridDim.x) * kCT;
-  for (int64_t t = blockIdx.x * int64_t(kCT) + threadIdx.x; t < B.nq * B.nbr; t += stride) {
+  for (int64_t r = blockIdx.x * int64_t(kCT) + threadIdx.x; r < D.n_qrep * B.nbr; r += stride) {
+    const int q = D.qlist[r / B.nbr];
+    const int64_t t = int64_t(q) * B.nbr + r % B.nbr;
     const double w = D.w[t], W = W_ph[t];
     if (!(w > D.omega_min) || !(W > 0.0)) continue;
-    const double wt = w / (inv_nnW[t] * W);
+    const double wt = w / (inv_nnW[t] * W * double(D.qstab[q]));
     const double *v = D.vph + t * 3;
     for (int a = 0; a < 3; ++a) {
       const double u = wt * v[a];

@@ -49,6 +49,7 @@ struct MeshDev {
   const int *qrep, *qop;              // [nq] representative of the q star and S with S <q> = q
   const int *qrep_of;                 // [nq] index of a representative in the representative list
   const int *qlist;                   // [n_qrep] the representatives
+  const int *qstab;                   // [nq] order of the stabiliser of q's representative
   int64_t n_qrep;
   const int *rep, *op, *stab;         // [nk]
   const int *ibzw_of;                 // [nk] index in the irreducible-window list or -1
@@ -162,9 +163,12 @@ int tc_ncols_a(const ModelDev &M);
 size_t tc_gs_elems_a(const ModelDev &M, int ns);
 size_t stage_a_phik_elems(const ModelDev &M, int ns, int64_t chunk);
 cudaError_t launch_g_slices(const ModelDev &M, int ns, __nv_bfloat16 *gs, double *gscale, cudaStream_t st);
+// a_tmem: the A slices are copied into tensor memory once per K step (tcgen05.cp) and the
+// products read them there; otherwise every product reads its A slice from shared memory.
+// The two forms give bit-identical results.
 cudaError_t launch_stage_a_tc(const ModelDev &M, const MeshDev &D, int ns, int64_t i0, int64_t nkc,
                               __nv_bfloat16 *phik, const __nv_bfloat16 *gs, const double *gscale, double2 *T, int *err,
-                              cudaStream_t st, double *flops_acc);
+                              bool a_tmem, cudaStream_t st, double *flops_acc);
 // The band rotation of stage A: A[kc][rp][(m,n',a)] = sum_m' c_{m'm}(k) T[kc][rp][m'][n'][a]
 // (T in FP64, or as float-float pairs when t_ff).
 cudaError_t launch_stage_a2(const ModelDev &M, const MeshDev &D, int64_t i0, int64_t nkc, const double2 *T, double2 *A,

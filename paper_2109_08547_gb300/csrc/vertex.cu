@@ -642,7 +642,9 @@ __global__ void k_epi_tables(ModelDev M, MeshDev D, double T, double mu, double 
   const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   const int nb = M.nb, nbr = M.nbr;
   const double kT = kKbEVK * T;
-  if (t < D.nk * nb) fk[t] = fermi_d(D.eps[t], mu, kT);
+  // occupations are read only at the end points of pairs, whose bands rotate (rmask != 0);
+  // the rest are set to 0 without the exponential
+  if (t < D.nk * nb) fk[t] = D.rmask[t / nb] ? fermi_d(D.eps[t], mu, kT) : 0.0;
   if (t < D.nq * nbr) {
     const double w = D.w[t];
     nbq[t] = bose_d(w, kT);
@@ -655,11 +657,13 @@ __global__ void k_epi_tables(ModelDev M, MeshDev D, double T, double mu, double 
 }
 
 // Float-float copies of the final-band eigenvectors c(k) ([k][n'][n]) and of the mass-scaled
-// phonon eigenvectors ([q][a][s]) for the FP64-grade epilogue: (re hi, re lo, im hi, im lo)
-__global__ void k_ff_tables(int64_t nc, const double2 *cvec, int64_t nu, const double2 *ut, float4 *cff,
-                            float4 *uff) {
+// phonon eigenvectors ([q][a][s]) for the FP64-grade epilogue: (re hi, re lo, im hi, im lo).
+// c(k) is read only for k' = k + q of a pair, which has an active band: points without one
+// (rmask 0) are not written.
+__global__ void k_ff_tables(int64_t nc, int nb2, const uint32_t *__restrict__ rmask, const double2 *cvec, int64_t nu,
+                            const double2 *ut, float4 *cff, float4 *uff) {
   const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (t < nc) {
+  if (t < nc && rmask[t / nb2]) {
     const float2 r = ff_from_double(cvec[t].x), i = ff_from_double(cvec[t].y);
     cff[t] = make_float4(r.x, r.y, i.x, i.y);
   }
@@ -881,7 +885,8 @@ cudaError_t launch_ff_tables(const ModelDev &M, const MeshDev &D, const double2 
   const int64_t nc = D.nk * M.nb * M.nb, nu = D.nq * M.nbr * M.nbr;
   const int64_t n = nc > nu ? nc : nu;
   if (n == 0) return cudaSuccess;
-  EPHB_LAUNCH(k_ff_tables, unsigned((n + 255) / 256), 256, 0, st, nc, D.cvec, nu, ut, cff, uff);
+  EPHB_LAUNCH(k_ff_tables, unsigned((n + 255) / 256), 256, 0, st, nc, M.nb * M.nb, D.rmask, D.cvec, nu, ut, cff,
+              uff);
   return cudaGetLastError();
 }
 

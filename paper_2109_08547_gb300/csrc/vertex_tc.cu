@@ -424,6 +424,26 @@ __device__ __forceinline__ void slice_products(uint32_t tacc, uint32_t acc_cols,
     }
 }
 
+// The same products with the A slices in tensor memory: slice is at column a_tm + 8 is (a
+// 128 x 16 BF16 tile takes 8 columns of the 128 lanes).
+template <int NS, int NACC, bool FIRST>
+__device__ __forceinline__ void slice_products_tm(uint32_t tacc, uint32_t acc_cols, uint32_t a_tm, uint64_t bd0,
+                                                  uint32_t b16, uint32_t idesc) {
+#pragma unroll
+  for (int is = 0; is < NS; ++is)
+#pragma unroll
+    for (int ls = 0; ls < NS - is; ++ls) {
+      const int d = is + ls;
+      const int acc = NACC == 1 ? 0 : (d < NACC - 1 ? d : NACC - 1);
+      const bool first = FIRST && (NACC == 1 ? (is == 0 && ls == 0) :
+                                   (acc < NACC - 1 ? (is == 0) : (is == 0 && ls == NACC - 1)));
+      asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                   "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n"
+                   :: "r"(tacc + uint32_t(acc) * acc_cols), "r"(a_tm + uint32_t(8 * is)),
+                      "l"(bd0 + uint64_t(ls) * b16), "r"(idesc), "r"(first ? 0u : 1u));
+    }
+}
+
 // 16-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(src_bytes) : "memory");
@@ -959,7 +979,7 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                :: "r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
 }
 
-template <int NS, int NACC, int ST>
+template <int NS, int NACC, int ST, bool ATM>
 __global__ void __launch_bounds__(kSaThreads, 1) k_stage_a_ws(TcParams P, int64_t nitems, int nkch,
                                                               const __nv_bfloat16 *__restrict__ gs,
                                                               const __nv_bfloat16 *__restrict__ phik,
@@ -975,6 +995,7 @@ __global__ void __launch_bounds__(kSaThreads, 1) k_stage_a_ws(TcParams P, int64_
   const int nw = P.nc_max;
   const uint32_t a_slice = uint32_t(kTcM) * KC * 2, b_slice = uint32_t(nw) * KC * 2;
   const uint32_t a_bytes = NS * a_slice, b_bytes = NS * b_slice;
+  const uint32_t a_col0 = uint32_t(NACC * nw);   // ATM: two A buffers of 8 NS columns after the accumulators
   const uint32_t stage_bytes = a_bytes + b_bytes;
   const int nkb = P.Kp / KC;
   const int nkc = int(P.nkc);
@@ -1076,10 +1097,29 @@ __global__ void __launch_bounds__(kSaThreads, 1) k_stage_a_ws(TcParams P, int64_
             const unsigned char *sB = sA + a_bytes;
             const uint64_t ad0 = smem_desc(smem_u32(sA), 128u, (KC / 8) * 128u);
             const uint64_t bd0 = smem_desc(smem_u32(sB), 128u, (KC / 8) * 128u);
-            if (kb == 0)
+            if (ATM) {
+              // A slices into tensor-memory buffer it & 1 (each read once from shared memory
+              // instead of once per product); the products of stage it - 2, the buffer's last
+              // readers, have completed first
+              if (it >= 2 && !mbar_wait(smem_u32(&empty[(it - 2) % ST]), ((it - 2) / ST) & 1)) {
+                give_up();
+                ok = false;
+                break;
+              }
+              const uint32_t a_tm = taddr + a_col0 + (it & 1u) * uint32_t(8 * NS);
+#pragma unroll
+              for (int is = 0; is < NS; ++is)
+                asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;"
+                             :: "r"(a_tm + uint32_t(8 * is)), "l"(ad0 + uint64_t(is) * (a_slice >> 4)));
+              if (kb == 0)
+                slice_products_tm<NS, NACC, true>(taddr, uint32_t(nw), a_tm, bd0, b_slice >> 4, idesc);
+              else
+                slice_products_tm<NS, NACC, false>(taddr, uint32_t(nw), a_tm, bd0, b_slice >> 4, idesc);
+            } else if (kb == 0) {
               slice_products<NS, NACC, true>(taddr, uint32_t(nw), ad0, bd0, a_slice >> 4, b_slice >> 4, idesc);
-            else
+            } else {
               slice_products<NS, NACC, false>(taddr, uint32_t(nw), ad0, bd0, a_slice >> 4, b_slice >> 4, idesc);
+            }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          :: "r"(smem_u32(&empty[slot])) : "memory");
             any = true;
@@ -1197,8 +1237,11 @@ cudaError_t launch_g_slices(const ModelDev &M, int ns, __nv_bfloat16 *gs, double
 // swapped-role contraction (k_stage_a_ws) into T[k][j'] as float-float pairs.  The k chunk
 // width: the fewest chunks of at most (512 / NACC rounded down to 16) k points, balanced and
 // rounded up to 16.
+// chunk cap: the accumulators and (tensor-memory A form) two A buffers of 8 ns columns fit the
+// 512 columns; both forms use the same chunks
+static int stage_a_cap(int ns) { return ((512 - 16 * ns) / nacc_of(ns)) / 16 * 16; }
 static int stage_a_chunk(int ns, int64_t nkc, int *nkch) {
-  const int cap = (512 / nacc_of(ns)) / 16 * 16;
+  const int cap = stage_a_cap(ns);
   const int64_t n = (nkc + cap - 1) / cap;
   *nkch = int(n);
   return round_up(int((nkc + n - 1) / n), 16);
@@ -1206,7 +1249,7 @@ static int stage_a_chunk(int ns, int64_t nkc, int *nkch) {
 // rows of the phase-slice operand for any group of at most `chunk` k points: nkch x nw <=
 // chunk + 16 nkch
 size_t stage_a_phik_elems(const ModelDev &M, int ns, int64_t chunk) {
-  const int cap = (512 / nacc_of(ns)) / 16 * 16;
+  const int cap = stage_a_cap(ns);
   const int64_t rows = chunk + 16 * ((chunk + cap - 1) / cap);
   return size_t(rows) * ns * tc_kp_a(M);
 }
@@ -1214,7 +1257,7 @@ constexpr int kStageASt = 4;   // shared-memory stages of the stage-A pipeline
 
 cudaError_t launch_stage_a_tc(const ModelDev &M, const MeshDev &D, int ns, int64_t i0, int64_t nkc,
                               __nv_bfloat16 *phik, const __nv_bfloat16 *gs, const double *gscale, double2 *T, int *err,
-                              cudaStream_t st, double *flops_acc) {
+                              bool a_tmem, cudaStream_t st, double *flops_acc) {
   if (nkc <= 0) return cudaSuccess;
   if (ns != 7 && ns != 8) return cudaErrorInvalidValue;
   const int Kp = tc_kp_a(M), Ncols = tc_ncols_a(M);
@@ -1252,7 +1295,10 @@ cudaError_t launch_stage_a_tc(const ModelDev &M, const MeshDev &D, int ns, int64
     EPHB_LAUNCH(kern, grid, kSaThreads, smem, st, P, nitems, nkch, gs, phik, gscale, out, err);
     return cudaGetLastError();
   };
-  e = ns == 8 ? go(k_stage_a_ws<8, 6, kStageASt>) : go(k_stage_a_ws<7, 5, kStageASt>);
+  if (a_tmem)
+    e = ns == 8 ? go(k_stage_a_ws<8, 6, kStageASt, true>) : go(k_stage_a_ws<7, 5, kStageASt, true>);
+  else
+    e = ns == 8 ? go(k_stage_a_ws<8, 6, kStageASt, false>) : go(k_stage_a_ws<7, 5, kStageASt, false>);
   // issued MMA work: 128 columns x each chunk's width x Kp per slice product and column tile
   if (flops_acc) {
     double width = 0.0;

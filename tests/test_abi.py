@@ -57,7 +57,8 @@ def test_binding_constants_match_header():
     for name, value in (("EPHB_MAX_ACCEL_DEPTH", B.MAX_ACCEL_DEPTH), ("EPHB_NFEAT", B.NFEAT),
                         ("EPHB_TUNE_TC_COLS", B.TUNE_TC_COLS), ("EPHB_TUNE_WITHHOLD_MMA", B.TUNE_WITHHOLD_MMA),
                         ("EPHB_NOALLOC_MAX_ITEMS", B.NOALLOC_MAX_ITEMS),
-                        ("EPHB_TUNE_DEFER_INSTANCES", B.TUNE_DEFER_INSTANCES), ("EPHB_DELTA_TETRA", B.DELTA_TETRA)):
+                        ("EPHB_TUNE_DEFER_INSTANCES", B.TUNE_DEFER_INSTANCES), ("EPHB_DELTA_TETRA", B.DELTA_TETRA),
+                        ("EPHB_TUNE_STAGE_A_TMEM_A", B.TUNE_STAGE_A_TMEM_A)):
         m = re.search(r"#define\s+%s\s+(\d+)" % name, text)
         assert m and int(m.group(1)) == value, name
 

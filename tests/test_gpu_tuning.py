@@ -58,3 +58,23 @@ def test_wait_timeout_is_reported_and_the_context_recovers():
         B.compute_transition_rates(ctx, wl.T_K, wl.mu_eV, wl.sigma_eV, wl.cutoff_sigmas, B.FP64_SLICED)
         B.compute_transition_rates(ref, wl.T_K, wl.mu_eV, wl.sigma_eV, wl.cutoff_sigmas, B.FP64_SLICED)
         assert np.array_equal(B.get_array(ctx, "entry_x"), B.get_array(ref, "entry_x"))
+
+
+@pytest.mark.parametrize("name", ["cscl4-6", "cscl8-k12-q6"])
+def test_stage_a_tensor_memory_form_is_bit_identical(name):
+    """Stage A with every product reading its A slice from shared memory (the default) and with
+    the A slices copied into tensor memory once per K step: the same products in the same
+    order, so the rates are bit-identical (7 slices on the 4-band model, 8 on the 7^3-grid
+    model)."""
+    wl = SY.workload_cscl4(n=6) if name == "cscl4-6" else SY.workload_cscl8(12, 6)
+    outs = []
+    for tmem_a in (0, 1):
+        with B.Context(0) as ctx:
+            B.set_wannier_model(ctx, wl.model)
+            B.set_tuning(ctx, B.TUNE_STAGE_A_TMEM_A, tmem_a)
+            B.build_meshes_ibz(ctx, wl.kmesh, wl.qmesh, wl.window, wl.degen_tol_eV, wl.omega_min_eV)
+            B.compute_transition_rates(ctx, wl.T_K, wl.mu_eV, wl.sigma_eV, wl.cutoff_sigmas, B.FP64_SLICED)
+            outs.append((B.get_array(ctx, "entry_x"), B.get_array(ctx, "entry_kpns")))
+    assert outs[0][0].size > 0
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][0], outs[1][0])
