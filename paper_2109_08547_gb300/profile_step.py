@@ -24,7 +24,7 @@ def main(argv=None):
     p.add_argument("--solve", default="mixed", choices=["fp64", "mixed"])
     p.add_argument("--delta", default="gauss", choices=["gauss", "tetra"])
     p.add_argument("--warm", type=int, default=2)
-    p.add_argument("--out", default="gpurun_out")
+    p.add_argument("--out", default=".", help="directory of step_window.txt")
     a = p.parse_args(argv)
     wl = S.workload_cscl8(a.nk, a.nq)
     wl = dataclasses.replace(wl, delta=a.delta)
