@@ -493,6 +493,10 @@ ephb_status ephb_set_wannier_model(ephb_ctx *ctx, const ephb_model *m) {
     }
   }
   ModelDev &M = ctx->M;
+  // the tile shapes tuned for the previous model stay valid while the contraction's shape is
+  // the same (a model of equal dimensions with new values)
+  const bool same_shape = ctx->stage >= 1 && M.nb == m->nb && M.nat == m->nat && M.nRge == m->nRge &&
+                          M.nRgp == m->nRgp;
   M = ModelDev();
   M.nat = m->nat;
   M.nb = m->nb;
@@ -552,7 +556,7 @@ ephb_status ephb_set_wannier_model(ephb_ctx *ctx, const ephb_model *m) {
   M.atom_perm = ctx->atom_perm.p;
   M.atom_shift = ctx->atom_shift.p;
   ctx->stage = 1;
-  ctx->tune_cols[0] = ctx->tune_cols[1] = ctx->tune_cols[2] = 0;   // a new model shape is tuned again
+  if (!same_shape) ctx->tune_cols[0] = ctx->tune_cols[1] = ctx->tune_cols[2] = 0;   // a new shape is tuned again
   ctx->gslices_ns = 0;                          // and its g slices are made again
   ctx->bte_ready = false;
   return EPHB_OK;

@@ -647,22 +647,34 @@ __global__ void k_ph_update(ModelDev M, MeshDev D, const double *Afold, const do
 
 // ---------------------------------------------------------------- coefficient reductions
 constexpr int kNPart = 152;     // fixed number of partial-sum blocks (one per SM)
-constexpr int kCT = 256;
+// Threads of the partial-sum kernels (three warps: the coefficient assembly fused into the
+// last block needs at least 72).  An FP64 warp instruction holds the SM's FP64 pipe ~16 cycles
+// whatever its active lanes, so these kernels keep few warps per SM and few FP64 instructions
+// per warp.
+constexpr int kCT = 96;
 constexpr int kNE = 36;         // electron sums: sigma, sigmaS, alpha_el, kappa0_el (3x3 each)
 constexpr int kNP = 18;         // phonon sums: alpha_ph, kappa_ph
 
+// Block sums of nacc (<= kNE) per-thread values into out[0..nacc).  Within a warp the values go
+// through shared memory and lane l adds value l (and l + 32) over the 32 lanes: 2 FP64
+// instructions per lane-column instead of 5 shuffle-adds per value; then the warps' sums are
+// added in a fixed order (reproducible).
 __device__ inline void block_reduce_store(double *acc, int nacc, double *out) {
+  __shared__ double tr[kCT / 32][32][kNE + 1];   // +1: column reads without bank conflicts
   __shared__ double wsum[kCT / 32][kNE];
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int j = 0; j < nacc; ++j) {
-    double v = warp_sum(acc[j]);
-    if (lane == 0) wsum[wid][j] = v;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int j = 0; j < nacc; ++j) tr[wid][lane][j] = acc[j];
+  __syncwarp();
+  for (int v = lane; v < nacc; v += 32) {
+    double sum = 0.0;
+    for (int r = 0; r < 32; ++r) sum += tr[wid][r][v];
+    wsum[wid][v] = sum;
   }
   __syncthreads();
   if (threadIdx.x < nacc) {
-    double s = 0.0;
-    for (int w = 0; w < kCT / 32; ++w) s += wsum[w][threadIdx.x];
-    out[threadIdx.x] = s;
+    double sum = 0.0;
+    for (int w = 0; w < kCT / 32; ++w) sum += wsum[w][threadIdx.x];
+    out[threadIdx.x] = sum;
   }
 }
 
