@@ -68,6 +68,17 @@ __device__ inline void int_slices(long long N, int ns, __nv_bfloat16 *out, size_
   out[0] = __float2bfloat16_rn(ldexpf(float(N), -(B - 1)));
 }
 
+// ns slices of 8 fixed-point integers into ns 16-byte vectors (8 BF16 each)
+__device__ inline void int_slices8(const long long *N, int ns, uint4 *out) {
+  __nv_bfloat16 v[8][8];
+  for (int e = 0; e < 8; ++e) int_slices(N[e], ns, &v[e][0], 1);
+  for (int sl = 0; sl < ns; ++sl) {
+    __nv_bfloat16 w[8];
+    for (int e = 0; e < 8; ++e) w[e] = v[e][sl];
+    out[sl] = *reinterpret_cast<const uint4 *>(w);
+  }
+}
+
 // Split x in [-1,1] into ns exact BF16 fixed-point slices: x is rounded once to the 64-bit
 // integer N = rint(x 2^slice_top(ns)) (2^55 in every FP64-grade form); the rest is integer.
 __device__ inline void fixed_slices(double x, int ns, __nv_bfloat16 *out, size_t stride) {
@@ -128,22 +139,28 @@ __global__ void k_phase_angle_table(int n, int ns, __nv_bfloat16 *tab) {
 
 __global__ void k_phase_slices_cubic(ModelDev M, MeshDev D, int ns, int Kp, const __nv_bfloat16 *__restrict__ tab,
                                      __nv_bfloat16 *phis) {
+  // one thread per (q, 8 consecutive r): 16-byte stores of each slice
   const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  const int R = M.nRgp, n = D.qm.n[0];
-  if (t >= D.nq * int64_t(Kp)) return;
-  const int q = int(t / Kp), r = int(t % Kp);
-  __nv_bfloat16 *dst = phis + (size_t(q) * ns) * Kp + r;
-  if (r >= 2 * R) {
-    for (int sl = 0; sl < ns; ++sl) dst[sl * size_t(Kp)] = __float2bfloat16_rn(0.f);
-    return;
-  }
-  const int rr = r < R ? r : r - R;
+  const int R = M.nRgp, n = D.qm.n[0], n8 = Kp / 8;
+  if (t >= D.nq * int64_t(n8)) return;
+  const int q = int(t / n8), r0 = int(t % n8) * 8;
   int b0, b1, b2;
   D.qm.unflat(q, b0, b1, b2);
-  const int *Rv = M.Rgp + 3 * rr;
-  const int j = pmod((long long)b0 * Rv[0] + (long long)b1 * Rv[1] + (long long)b2 * Rv[2], n);
-  const __nv_bfloat16 *src = tab + (size_t(j) * 2 + (r < R ? 0 : 1)) * ns;
-  for (int sl = 0; sl < ns; ++sl) dst[sl * size_t(Kp)] = src[sl];
+  __nv_bfloat16 v[8][8];
+  for (int e = 0; e < 8; ++e) {
+    const int r = r0 + e;
+    if (r >= 2 * R) {
+      for (int sl = 0; sl < ns; ++sl) v[sl][e] = __float2bfloat16_rn(0.f);
+      continue;
+    }
+    const int rr = r < R ? r : r - R;
+    const int *Rv = M.Rgp + 3 * rr;
+    const int j = pmod((long long)b0 * Rv[0] + (long long)b1 * Rv[1] + (long long)b2 * Rv[2], n);
+    const __nv_bfloat16 *src = tab + (size_t(j) * 2 + (r < R ? 0 : 1)) * ns;
+    for (int sl = 0; sl < ns; ++sl) v[sl][e] = src[sl];
+  }
+  __nv_bfloat16 *dst = phis + (size_t(q) * ns) * Kp + r0;
+  for (int sl = 0; sl < ns; ++sl) *reinterpret_cast<uint4 *>(dst + sl * size_t(Kp)) = *reinterpret_cast<const uint4 *>(v[sl]);
 }
 
 // B' slices of the k points of a chunk: BS[kc][slice][Nmax][Kp] (BF16) and column scales.
@@ -219,12 +236,20 @@ __global__ void __launch_bounds__(256) k_b_slices(ModelDev M, MeshDev D, int64_t
     bscale[kc * Nmax + c0 + gcol(lc)] = __longlong_as_double((long long)(ex + 1023) << 52);
   }
   __syncthreads();
-  const int top = slice_top(ns);
-  for (int t = threadIdx.x; t < ncol * Kp; t += blockDim.x) {
-    const int lc = t / Kp, r = t - lc * Kp;
-    long long N = 0;
-    if (r < 2 * R && sh_ex[lc] != -2000) N = fixed_round(__longlong_as_double(value_bits(lc, r)), top - sh_ex[lc]);
-    int_slices(N, ns, dstk + size_t(c0 + gcol(lc)) * Kp + r, sstride);
+  // one thread per (column, 8 consecutive r): 16-byte stores of each slice
+  const int top = slice_top(ns), n8 = Kp / 8;
+  for (int t = threadIdx.x; t < ncol * n8; t += blockDim.x) {
+    const int lc = t / n8, r0 = (t - lc * n8) * 8;
+    long long N[8];
+    for (int e = 0; e < 8; ++e) {
+      const int r = r0 + e;
+      N[e] = r < 2 * R && sh_ex[lc] != -2000 ? fixed_round(__longlong_as_double(value_bits(lc, r)), top - sh_ex[lc])
+                                             : 0;
+    }
+    uint4 o[8];
+    int_slices8(N, ns, o);
+    __nv_bfloat16 *dst = dstk + size_t(c0 + gcol(lc)) * Kp + r0;
+    for (int sl = 0; sl < ns; ++sl) *reinterpret_cast<uint4 *>(dst + sl * sstride) = o[sl];
   }
 }
 
@@ -255,17 +280,6 @@ __host__ __device__ __forceinline__ int tile16_off(int row, int kk) {
   return ((row >> 3) * 2 + (kk >> 3)) * 64 + (row & 7) * 8 + (kk & 7);
 }
 
-// ns slices of 8 consecutive values into ns 16-byte vectors (8 BF16 each)
-__device__ inline void slices8(const double *x, int ns, uint4 *out) {
-  __nv_bfloat16 v[8][8];
-  for (int e = 0; e < 8; ++e) fixed_slices(x[e], ns, &v[e][0], 1);
-  for (int sl = 0; sl < ns; ++sl) {
-    __nv_bfloat16 w[8];
-    for (int e = 0; e < 8; ++e) w[e] = v[e][sl];
-    out[sl] = *reinterpret_cast<const uint4 *>(w);
-  }
-}
-
 // Phase slices of the k points of a group as the B operand of stage A: rows k (chunks of nw,
 // rows past nkc zero), (cos, sin) of 2 pi k.Re for r < nRe and nRe <= r < 2 nRe, K padded to
 // Kp with zeros.  One thread per (k, 8 consecutive r).
@@ -275,21 +289,21 @@ __global__ void k_phase_slices_k(ModelDev M, MeshDev D, int64_t i0, int64_t nkc,
   const int R = M.nRge, n8 = Kp / 8, nkb = Kp / 16;
   if (t >= int64_t(nrows) * n8) return;
   const int k = int(t / n8), r0 = int(t % n8) * 8;
-  double x[8];
+  long long N[8];
   int a0 = 0, a1 = 0, a2 = 0;
   if (k < nkc) D.km.unflat(D.ibzw_list[i0 + k], a0, a1, a2);
   for (int e = 0; e < 8; ++e) {
     const int r = r0 + e;
-    x[e] = 0.0;
+    N[e] = 0;
     if (k < nkc && r < 2 * R) {
       const int rr = r < R ? r : r - R;
       const int *Rv = M.Rge + 3 * rr;
       const double2 ph = mesh_phase(D.ktab, D.km, a0, a1, a2, Rv[0], Rv[1], Rv[2]);
-      x[e] = r < R ? ph.x : ph.y;
+      N[e] = fixed_round(r < R ? ph.x : ph.y, slice_top(ns));
     }
   }
   uint4 o[8];
-  slices8(x, ns, o);
+  int_slices8(N, ns, o);
   const int kch = k / nw, row = k % nw, kb = r0 / 16;
   const size_t base = (size_t(kch) * nkb + kb) * ns;
   for (int sl = 0; sl < ns; ++sl)
@@ -306,22 +320,19 @@ __device__ __forceinline__ double g_operand(const ModelDev &M, int64_t ncol, int
   return r < R ? ((jp & 1) == 0 ? g.x : g.y) : ((jp & 1) == 0 ? -g.y : g.x);
 }
 
-// power-of-two scale of each g column j' (>= its largest entry; 1 for a zero column); one warp
-// per column
+// power-of-two scale of each g column j' (>= its largest entry; 1 for a zero column); one thread
+// per column, so a warp reads 32 consecutive columns of each row of g (coalesced)
 __global__ void k_g_scales(ModelDev M, int Ncols, double *gscale) {
-  const int64_t w = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= Ncols) return;
-  const int jp = int(w);
+  const int64_t jp64 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (jp64 >= Ncols) return;
+  const int jp = int(jp64);
   const int64_t ncol = int64_t(M.nRgp) * M.nb * M.nb * M.nbr;
-  const bool live = jp / 2 < ncol;
   double mx = 0.0;
-  for (int r = lane; r < 2 * M.nRge; r += 32)
-    if (live) mx = fmax(mx, fabs(g_operand(M, ncol, jp, r)));
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (jp / 2 < ncol)
+    for (int r = 0; r < 2 * M.nRge; ++r) mx = fmax(mx, fabs(g_operand(M, ncol, jp, r)));
   int ex = 0;
   if (mx > 0.0) frexp(mx, &ex);
-  if (lane == 0) gscale[jp] = mx > 0.0 ? ldexp(1.0, ex) : 1.0;
+  gscale[jp] = mx > 0.0 ? ldexp(1.0, ex) : 1.0;
 }
 
 // Slices of the model's g as the A operand of stage A, pre-tiled by 128 columns: one thread per
@@ -336,12 +347,15 @@ __global__ void k_g_slices(ModelDev M, int ns, int Kp, int Ncols, int nct, const
   const int jp = ct * kTcM + row;
   const int64_t ncol = int64_t(M.nRgp) * M.nb * M.nb * M.nbr;
   const bool live = jp < Ncols && jp / 2 < ncol;
-  const double inv = live ? 1.0 / gscale[jp] : 0.0;   // a power of two: exact
+  // rint(x 2^top / sigma) by integer operations (sigma = 2^ex, a power of two): the same integers
+  // as the FP64 division, scaling and conversion, with no FP64 instruction
+  const int ex = live ? int((__double_as_longlong(gscale[jp]) >> 52) & 0x7ff) - 1023 : 0;
   const int r0 = kb * 16 + half * 8;
-  double x[8];
-  for (int e = 0; e < 8; ++e) x[e] = live && r0 + e < 2 * M.nRge ? g_operand(M, ncol, jp, r0 + e) * inv : 0.0;
+  long long N[8];
+  for (int e = 0; e < 8; ++e)
+    N[e] = live && r0 + e < 2 * M.nRge ? fixed_round(g_operand(M, ncol, jp, r0 + e), slice_top(ns) - ex) : 0;
   uint4 o[8];
-  slices8(x, ns, o);
+  int_slices8(N, ns, o);
   const size_t base = (size_t(ct) * nkb + kb) * ns;
   for (int sl = 0; sl < ns; ++sl)
     *reinterpret_cast<uint4 *>(gs + (base + sl) * (size_t(kTcM) * 16) + tile16_off(row, half * 8)) = o[sl];
@@ -1227,7 +1241,7 @@ size_t tc_gs_elems_a(const ModelDev &M, int ns) { return size_t(ns) * stage_a_nc
 
 cudaError_t launch_g_slices(const ModelDev &M, int ns, __nv_bfloat16 *gs, double *gscale, cudaStream_t st) {
   const int Ncols = tc_ncols_a(M), Kp = tc_kp_a(M), nct = stage_a_nct(M);
-  EPHB_LAUNCH(k_g_scales, unsigned((int64_t(Ncols) * 32 + 255) / 256), 256, 0, st, M, Ncols, gscale);
+  EPHB_LAUNCH(k_g_scales, unsigned((int64_t(Ncols) + 127) / 128), 128, 0, st, M, Ncols, gscale);
   const int64_t n = int64_t(nct) * (Kp / 16) * 256;
   EPHB_LAUNCH(k_g_slices, unsigned((n + 255) / 256), 256, 0, st, M, ns, Kp, Ncols, nct, gscale, gs);
   return cudaGetLastError();
@@ -1315,7 +1329,7 @@ cudaError_t launch_phase_slices(const ModelDev &M, const MeshDev &D, int ns, __n
   const Mesh &q = D.qm;
   if (angle_tab && q.n[0] == q.n[1] && q.n[1] == q.n[2]) {
     EPHB_LAUNCH(k_phase_angle_table, unsigned((2 * q.n[0] + 127) / 128), 128, 0, st, q.n[0], ns, angle_tab);
-    EPHB_LAUNCH(k_phase_slices_cubic, unsigned((n + 255) / 256), 256, 0, st, M, D, ns, Kp, angle_tab, phis);
+    EPHB_LAUNCH(k_phase_slices_cubic, unsigned((n / 8 + 255) / 256), 256, 0, st, M, D, ns, Kp, angle_tab, phis);
   } else {
     EPHB_LAUNCH(k_phase_slices, unsigned((n + 255) / 256), 256, 0, st, M, D, ns, Kp, phis);
   }
