@@ -97,7 +97,9 @@ typedef struct {
   double bg_T_ref;
 } ephb_model;
 
-/* Validate and copy the model to the device.  Resets meshes, rates and solutions. */
+/* Validate and copy the model to the device.  Resets meshes, rates and solutions.
+ * EPHB_EINVAL for an out-of-range size, a non-group operation list, non-positive masses or
+ * scalars, or a lattice-vector component (Re, Rd, Rge, Rgp) outside +-65535. */
 ephb_status ephb_set_wannier_model(ephb_ctx *ctx, const ephb_model *model);
 
 /* ----------------------------------------------------------------------------------

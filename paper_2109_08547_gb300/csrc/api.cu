@@ -180,7 +180,7 @@ struct ephb_ctx : InstState {
   DBuf<__nv_bfloat16> angle_tab;      // slices of cos, sin of the 2 pi j / n angles of a cubic q mesh
   DBuf<int> atom_perm, atom_shift;
   DBuf<int> rep, op, stab, flag, ibzw_list, ibzw_of, npairs, pair_q, pair_i, qcount, pq_rank;
-  DBuf<int64_t> pos, pair_ptr, qpair_ptr, scratch, scal;
+  DBuf<int64_t> pos, pair_ptr, pair_off, qpair_ptr, scratch, scal;
 
   // rates (scratch shared by the instances)
   DBuf<int> cntE, cntPh;
@@ -393,7 +393,7 @@ void ephb_destroy(ephb_ctx *ctx) {
   ctx->amask.release(); ctx->rmask.release(); ctx->rep.release(); ctx->op.release(); ctx->stab.release(); ctx->flag.release();
   ctx->ibzw_list.release(); ctx->ibzw_of.release(); ctx->npairs.release(); ctx->pair_q.release();
   ctx->pair_i.release(); ctx->qcount.release(); ctx->pq_rank.release(); ctx->pos.release();
-  ctx->pair_ptr.release(); ctx->qpair_ptr.release(); ctx->scratch.release(); ctx->scal.release();
+  ctx->pair_ptr.release(); ctx->pair_off.release(); ctx->qpair_ptr.release(); ctx->scratch.release(); ctx->scal.release();
   ctx->cntE.release(); ctx->cntPh.release(); ctx->escan.release(); ctx->phscan.release();
   ctx->Tbuf.release(); ctx->Abuf.release();
   ctx->phik.release(); ctx->gslices.release(); ctx->gscale.release();
@@ -432,6 +432,15 @@ ephb_status ephb_set_wannier_model(ephb_ctx *ctx, const ephb_model *m) {
     return fail(ctx, EPHB_EINVAL, "bad scalar model parameter");
   for (int a = 0; a < m->nat; ++a)
     if (!(m->mass_amu[a] > 0)) return fail(ctx, EPHB_EINVAL, "masses must be positive");
+  // lattice-vector components stay below 2^16, so mesh index x component sums fit 32 bits
+  {
+    const std::pair<const int32_t *, int> lists[4] = {{m->Re, m->nRe}, {m->Rd, m->nRd}, {m->Rge, m->nRge},
+                                                      {m->Rgp, m->nRgp}};
+    for (const auto &l : lists)
+      for (int64_t i = 0; i < 3 * int64_t(l.second); ++i)
+        if (l.first[i] > 65535 || l.first[i] < -65535)
+          return fail(ctx, EPHB_EINVAL, "lattice-vector components must lie within +-65535");
+  }
   // the operation list must be a group closed under inversion: find S^-1 for each S
   std::vector<int> inv(m->nsym, -1);
   for (int s = 0; s < m->nsym; ++s) {
@@ -670,13 +679,17 @@ ephb_status ephb_build_meshes_ibz(ephb_ctx *ctx, const ephb_mesh_opts *o, ephb_m
   CK(ctx->ibzw_list.ensure(ctx->n_ibzw));
   CK(launch_ibzw_fill(nk, ctx->flag.p, ctx->pos.p, ctx->ibzw_list.p, ctx->ibzw_of.p, st));
   // pairs (k, q) with an active band at k+q, sorted by q within each k
-  CK(ctx->npairs.ensure(ctx->n_ibzw));
+  const int nch = pair_chunks(nq);
+  const int64_t ncnt = ctx->n_ibzw * nch;
+  CK(ctx->npairs.ensure(ncnt));
+  CK(ctx->pair_off.ensure(ncnt + 1));
   CK(ctx->pair_ptr.ensure(ctx->n_ibzw + 1));
   MeshDev D = mesh_view(ctx);
   CK(launch_pair_count(D, ctx->npairs.p, st));
-  CK(ctx->scratch.ensure(scan_scratch_elems(ctx->n_ibzw > nk ? ctx->n_ibzw : nk)));
-  CK(exclusive_scan<int>(ctx->npairs.p, ctx->pair_ptr.p, ctx->n_ibzw, ctx->pair_ptr.p + ctx->n_ibzw,
-                         ctx->scratch.p, ctx->scratch.n, st));
+  CK(ctx->scratch.ensure(scan_scratch_elems(std::max<int64_t>(ncnt, nk))));
+  CK(exclusive_scan<int>(ctx->npairs.p, ctx->pair_off.p, ncnt, ctx->pair_off.p + ncnt, ctx->scratch.p,
+                         ctx->scratch.n, st));
+  CK(launch_pair_ptr(ctx->n_ibzw, nch, ctx->pair_off.p, ctx->pair_ptr.p, st));
   cudaError_t e;
   ctx->n_pairs = read_i64(ctx, ctx->pair_ptr.p + ctx->n_ibzw, e);
   CK(e);
@@ -684,7 +697,7 @@ ephb_status ephb_build_meshes_ibz(ephb_ctx *ctx, const ephb_mesh_opts *o, ephb_m
   CK(ctx->pair_i.ensure(ctx->n_pairs));
   CK(ctx->pq_rank.ensure(ctx->n_pairs));
   D = mesh_view(ctx);
-  CK(launch_pair_fill(D, ctx->pair_q.p, ctx->pair_i.p, st));
+  CK(launch_pair_fill(D, ctx->pair_off.p, ctx->pair_q.p, ctx->pair_i.p, st));
   CK(ctx->qcount.ensure(nq));
   CK(ctx->qpair_ptr.ensure(nq + 1));
   CK(launch_qpair_count(D, ctx->qcount.p, st));

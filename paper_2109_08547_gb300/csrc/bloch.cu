@@ -343,19 +343,26 @@ __device__ inline int kplusq(const MeshDev &D, int k, int q) {
 }
 
 // block per irreducible-window k: number of q with an active band at k+q
-__global__ void k_pair_count(MeshDev D, int *npairs) {
+// Pairs (k, q) of the irreducible window points with an active band at k + q, k-major and in
+// increasing q within each k.  The q range of each k is cut into chunks of kPairChunk: block
+// (c, i) counts (then writes) the pairs of chunk c of point i, so that a scan over the counts in
+// (i, c) order gives every block its output offset and the pair pointers of each i.
+constexpr int kPairChunk = 4096;
+
+__global__ void k_pair_count(MeshDev D, int nch, int *cnt) {
   __shared__ int red[32];
-  int i = blockIdx.x;
-  int k = D.ibzw_list[i];
-  int c = 0;
-  for (int q = threadIdx.x; q < D.nq; q += blockDim.x) c += D.amask[kplusq(D, k, q)] != 0u;
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+  const int c = blockIdx.x, i = blockIdx.y;
+  const int k = D.ibzw_list[i];
+  const int q1 = int(D.nq - int64_t(c) * kPairChunk < kPairChunk ? D.nq : int64_t(c + 1) * kPairChunk);
+  int n = 0;
+  for (int q = c * kPairChunk + threadIdx.x; q < q1; q += blockDim.x) n += D.amask[kplusq(D, k, q)] != 0u;
+  for (int o = 16; o > 0; o >>= 1) n += __shfl_down_sync(0xffffffffu, n, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = n;
   __syncthreads();
   if (threadIdx.x < 32) {
     int v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) npairs[i] = v;
+    if (threadIdx.x == 0) cnt[int64_t(i) * nch + c] = v;
   }
 }
 
@@ -376,16 +383,19 @@ __device__ inline int block_rank(int flag, int *warp_tot, int &total) {
   return off + r;
 }
 
-__global__ void k_pair_fill(MeshDev D, int *pair_q, int *pair_i) {
+// off: exclusive scan of the chunk counts in (i, c) order
+__global__ void k_pair_fill(MeshDev D, int nch, const int64_t *__restrict__ off, int *pair_q, int *pair_i) {
   __shared__ int wt[32];
-  int i = blockIdx.x;
-  int k = D.ibzw_list[i];
-  int64_t base = D.pair_ptr[i];
-  for (int q0 = 0; q0 < D.nq; q0 += blockDim.x) {
-    int q = q0 + threadIdx.x;
-    int f = q < D.nq ? (D.amask[kplusq(D, k, q)] != 0u) : 0;
+  const int c = blockIdx.x, i = blockIdx.y;
+  const int k = D.ibzw_list[i];
+  const int q0 = c * kPairChunk;
+  const int q1 = int(D.nq - int64_t(c) * kPairChunk < kPairChunk ? D.nq : int64_t(c + 1) * kPairChunk);
+  int64_t base = off[int64_t(i) * nch + c];
+  for (int qb = q0; qb < q1; qb += blockDim.x) {
+    const int q = qb + threadIdx.x;
+    const int f = q < q1 ? (D.amask[kplusq(D, k, q)] != 0u) : 0;
     int total;
-    int r = block_rank(f, wt, total);
+    const int r = block_rank(f, wt, total);
     if (f) {
       pair_q[base + r] = q;
       pair_i[base + r] = i;
@@ -394,42 +404,44 @@ __global__ void k_pair_fill(MeshDev D, int *pair_q, int *pair_i) {
   }
 }
 
-// block per q: how many irreducible-window k pair with it
-__global__ void k_qpair_count(MeshDev D, int *qcount) {
-  __shared__ int red[32];
-  int q = blockIdx.x;
-  int c = 0;
-  for (int i = threadIdx.x; i < D.n_ibzw; i += blockDim.x) c += D.amask[kplusq(D, D.ibzw_list[i], q)] != 0u;
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    int v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) qcount[q] = v;
-  }
+// pair pointers of each irreducible window point from the chunk offsets
+__global__ void k_pair_ptr(int64_t n_ibzw, int nch, const int64_t *__restrict__ off, int64_t *pair_ptr) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i <= n_ibzw) pair_ptr[i] = off[i * nch];
 }
 
-// block per q: rank of each pair (i, q) among the pairs of q, in increasing i
+// one warp per q: how many irreducible-window k pair with it
+__global__ void k_qpair_count(MeshDev D, int *qcount) {
+  const int64_t q = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (q >= D.nq) return;
+  int n = 0;
+  for (int i = lane; i < D.n_ibzw; i += 32) n += D.amask[kplusq(D, D.ibzw_list[i], int(q))] != 0u;
+  for (int o = 16; o > 0; o >>= 1) n += __shfl_down_sync(0xffffffffu, n, o);
+  if (lane == 0) qcount[q] = n;
+}
+
+// one warp per q: rank of each pair (i, q) among the pairs of q, in increasing i
 __global__ void k_qpair_fill(MeshDev D, int *pq_rank) {
-  __shared__ int wt[32];
-  int q = blockIdx.x;
+  const int64_t q64 = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (q64 >= D.nq) return;
+  const int q = int(q64);
   int base = 0;
-  for (int i0 = 0; i0 < D.n_ibzw; i0 += blockDim.x) {
-    int i = i0 + threadIdx.x;
-    int f = i < D.n_ibzw ? (D.amask[kplusq(D, D.ibzw_list[i], q)] != 0u) : 0;
-    int total;
-    int r = block_rank(f, wt, total);
+  for (int i0 = 0; i0 < D.n_ibzw; i0 += 32) {
+    const int i = i0 + lane;
+    const int f = i < D.n_ibzw ? (D.amask[kplusq(D, D.ibzw_list[i], q)] != 0u) : 0;
+    const unsigned b = __ballot_sync(0xffffffffu, f);
     if (f) {
       // pair index of (i, q): binary search in the q-sorted list of i
       int64_t lo = D.pair_ptr[i], hi = D.pair_ptr[i + 1];
       while (hi - lo > 1) {
-        int64_t mid = (lo + hi) >> 1;
+        const int64_t mid = (lo + hi) >> 1;
         if (D.pair_q[mid] <= q) lo = mid; else hi = mid;
       }
-      pq_rank[lo] = base + r;
+      pq_rank[lo] = base + __popc(b & ((1u << lane) - 1u));
     }
-    base += total;
+    base += __popc(b);
   }
 }
 
@@ -566,25 +578,34 @@ cudaError_t launch_ibzw_fill(int64_t nk, const int *flag, const int64_t *pos, in
   return cudaGetLastError();
 }
 
-cudaError_t launch_pair_count(const MeshDev &D, int *npairs, cudaStream_t st) {
+int pair_chunks(int64_t nq) { return int((nq + kPairChunk - 1) / kPairChunk); }
+
+cudaError_t launch_pair_count(const MeshDev &D, int *cnt, cudaStream_t st) {
   if (D.n_ibzw == 0) return cudaSuccess;
-  EPHB_LAUNCH(k_pair_count, int(D.n_ibzw), 256, 0, st, D, npairs);
+  EPHB_LAUNCH(k_pair_count, dim3(unsigned(pair_chunks(D.nq)), unsigned(D.n_ibzw)), 256, 0, st, D, pair_chunks(D.nq),
+              cnt);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pair_fill(const MeshDev &D, int *pair_q, int *pair_i, cudaStream_t st) {
+cudaError_t launch_pair_ptr(int64_t n_ibzw, int nch, const int64_t *off, int64_t *pair_ptr, cudaStream_t st) {
+  EPHB_LAUNCH(k_pair_ptr, unsigned((n_ibzw + 1 + 255) / 256), 256, 0, st, n_ibzw, nch, off, pair_ptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_fill(const MeshDev &D, const int64_t *off, int *pair_q, int *pair_i, cudaStream_t st) {
   if (D.n_ibzw == 0) return cudaSuccess;
-  EPHB_LAUNCH(k_pair_fill, int(D.n_ibzw), 256, 0, st, D, pair_q, pair_i);
+  EPHB_LAUNCH(k_pair_fill, dim3(unsigned(pair_chunks(D.nq)), unsigned(D.n_ibzw)), 256, 0, st, D, pair_chunks(D.nq),
+              off, pair_q, pair_i);
   return cudaGetLastError();
 }
 
 cudaError_t launch_qpair_count(const MeshDev &D, int *qcount, cudaStream_t st) {
-  EPHB_LAUNCH(k_qpair_count, int(D.nq), 256, 0, st, D, qcount);
+  EPHB_LAUNCH(k_qpair_count, unsigned((D.nq * 32 + 255) / 256), 256, 0, st, D, qcount);
   return cudaGetLastError();
 }
 
 cudaError_t launch_qpair_fill(const MeshDev &D, int *pq_rank, cudaStream_t st) {
-  EPHB_LAUNCH(k_qpair_fill, int(D.nq), 256, 0, st, D, pq_rank);
+  EPHB_LAUNCH(k_qpair_fill, unsigned((D.nq * 32 + 255) / 256), 256, 0, st, D, pq_rank);
   return cudaGetLastError();
 }
 

@@ -646,7 +646,7 @@ __global__ void k_ph_update(ModelDev M, MeshDev D, const double *Afold, const do
 }
 
 // ---------------------------------------------------------------- coefficient reductions
-constexpr int kNPart = 152;     // fixed number of partial-sum blocks (one per SM)
+constexpr int kNPart = 48;      // fixed number of partial-sum blocks (few: the assembly adds them)
 // Threads of the partial-sum kernels (three warps: the coefficient assembly fused into the
 // last block needs at least 72).  An FP64 warp instruction holds the SM's FP64 pipe ~16 cycles
 // whatever its active lanes, so these kernels keep few warps per SM and few FP64 instructions

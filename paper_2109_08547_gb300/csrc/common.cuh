@@ -146,17 +146,19 @@ struct Mesh {
   }
 };
 
-__host__ __device__ inline int pmod(long long a, int n) {
-  long long r = a % n;
-  return int(r < 0 ? r + n : r);
+// a mod n in [0, n), 32-bit: every argument is a small mesh-index expression (mesh sizes
+// below 1024, lattice-vector components below 2^16, checked when the model is set)
+__host__ __device__ inline int pmod(int a, int n) {
+  const int r = a % n;
+  return r < 0 ? r + n : r;
 }
 
 // exp(i 2 pi sum_d i_d R_d / n_d) from per-dimension tables tab[off_d + j] = exp(i 2 pi j / n_d)
 __device__ inline double2 mesh_phase(const double2 *__restrict__ tab, const Mesh &m, int i0, int i1, int i2,
                                      int r0, int r1, int r2) {
-  double2 p0 = tab[pmod((long long)i0 * r0, m.n[0])];
-  double2 p1 = tab[m.n[0] + pmod((long long)i1 * r1, m.n[1])];
-  double2 p2 = tab[m.n[0] + m.n[1] + pmod((long long)i2 * r2, m.n[2])];
+  double2 p0 = tab[pmod(i0 * r0, m.n[0])];
+  double2 p1 = tab[m.n[0] + pmod(i1 * r1, m.n[1])];
+  double2 p2 = tab[m.n[0] + m.n[1] + pmod(i2 * r2, m.n[2])];
   return cmul(cmul(p0, p1), p2);
 }
 

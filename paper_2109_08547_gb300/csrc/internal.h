@@ -94,8 +94,12 @@ cudaError_t launch_phonons_from_rep(const ModelDev &M, Mesh qm, const double2 *q
 cudaError_t launch_rep_index(int64_t n, const int *list, int64_t nlist, int *of, cudaStream_t st);
 cudaError_t launch_ibzw_fill(int64_t nk, const int *flag, const int64_t *pos, int *ibzw_list, int *ibzw_of,
                              cudaStream_t st);
-cudaError_t launch_pair_count(const MeshDev &D, int *npairs, cudaStream_t st);
-cudaError_t launch_pair_fill(const MeshDev &D, int *pair_q, int *pair_i, cudaStream_t st);
+// pair lists: chunk counts cnt[n_ibzw][pair_chunks(nq)], their exclusive scan off (n_ibzw x
+// nch + 1 entries), the pair pointers from it, then the k-major, q-ascending fill
+int pair_chunks(int64_t nq);
+cudaError_t launch_pair_count(const MeshDev &D, int *cnt, cudaStream_t st);
+cudaError_t launch_pair_ptr(int64_t n_ibzw, int nch, const int64_t *off, int64_t *pair_ptr, cudaStream_t st);
+cudaError_t launch_pair_fill(const MeshDev &D, const int64_t *off, int *pair_q, int *pair_i, cudaStream_t st);
 cudaError_t launch_qpair_count(const MeshDev &D, int *qcount, cudaStream_t st);
 cudaError_t launch_qpair_fill(const MeshDev &D, int *pq_rank, cudaStream_t st);
 cudaError_t launch_count_bits(const uint32_t *amask, int64_t n, int64_t *out, cudaStream_t st);

@@ -356,6 +356,9 @@ __global__ void k_stage_a2(ModelDev M, MeshDev D, int64_t i0, int64_t nkc, const
   int ml = j / (nb * nbr), na = j % (nb * nbr);
   int k = D.ibzw_list[i0 + kc];
   uint32_t rm = D.rmask[k];
+  // the tensor-core path's B' slicing reads only the rows of rotating bands (it writes zero
+  // slices for the others), so there the rest is not written at all
+  if (FF && ml >= __popc(rm)) return;
   double2 acc = cmk(0, 0);
   if (ml < __popc(rm)) {
     int m = nth_bit(rm, ml);

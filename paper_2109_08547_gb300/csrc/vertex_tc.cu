@@ -155,7 +155,7 @@ __global__ void k_phase_slices_cubic(ModelDev M, MeshDev D, int ns, int Kp, cons
     }
     const int rr = r < R ? r : r - R;
     const int *Rv = M.Rgp + 3 * rr;
-    const int j = pmod((long long)b0 * Rv[0] + (long long)b1 * Rv[1] + (long long)b2 * Rv[2], n);
+    const int j = pmod(b0 * Rv[0] + b1 * Rv[1] + b2 * Rv[2], n);
     const __nv_bfloat16 *src = tab + (size_t(j) * 2 + (r < R ? 0 : 1)) * ns;
     for (int sl = 0; sl < ns; ++sl) v[sl][e] = src[sl];
   }

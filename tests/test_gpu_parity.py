@@ -330,6 +330,13 @@ def test_call_order_and_arguments():
     B.compute_transition_rates(ctx, wl.T_K, wl.mu_eV)
     info = B.solve_coupled_bte(ctx, "dragged", 1e-14, max_outer=2, max_inner=3, allow_noconv=True)
     assert info["status"] == B.ENOCONV and info["converged"] == 0
+    # a lattice vector beyond the 32-bit mesh-index arithmetic is refused
+    import dataclasses
+    far = wl.model.Re.copy()
+    far[0, 0] = 70000
+    with pytest.raises(B.EphbError) as e:
+        B.set_wannier_model(ctx, dataclasses.replace(wl.model, Re=far))
+    assert e.value.status == B.EINVAL
     ctx.close()
 
 
