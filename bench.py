@@ -184,13 +184,13 @@ def measured_peaks():
         return {}
 
 
-def profile_traffic(kernel_tag, source_file):
-    """dram bytes per unit from a committed ncu summary, if it was taken on the current source."""
-    import glob
-    paths = sorted(glob.glob(os.path.join(ROOT, "profiles", f"ncu_{kernel_tag}*.txt")))
-    if not paths:
+def profile_traffic(summary, source_file):
+    """DRAM bytes per unit (and the unit) from the committed ncu summary profiles/<summary>, if
+    its counters were taken on the current source of the kernel: lines `source_sha256_16: h`,
+    `dram_bytes_per_unit: b` and `unit: u`."""
+    path = os.path.join(ROOT, "profiles", summary)
+    if not os.path.exists(path):
         return None
-    path = paths[0]
     kv = {}
     for ln in open(path):
         if ":" in ln:
@@ -538,9 +538,12 @@ def main():
             alg = ra["stage_a_flops"]     # 8 N_Re ncol per irreducible-window k, plus the band rotation
             if ra["tensor_flops_a"] > 0:
                 ach = alg / (ms_a * 1e-3) / 1e12
+                # DRAM bytes of the contraction kernel (one launch per step on this workload)
+                tra = profile_traffic("ncu_stage_a_traffic_cscl8-80-40.txt", "vertex_tc.cu") \
+                    if wl.name == "cscl8-80^3/40^3" else None
                 roof = {"kernel": "stage A (k phase slices + tcgen05 R_e contraction + band rotation)",
                         "bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
-                        "peak_source": bf16_src, "traffic": None, "algorithmic_flops": alg,
+                        "peak_source": bf16_src, "traffic": tra[0] if tra else None, "algorithmic_flops": alg,
                         "issued_mma_tflops": ra["tensor_flops_a"] / (ms_a * 1e-3) / 1e12,
                         "issued_frac": ra["tensor_flops_a"] / (ms_a * 1e-3) / 1e12 / bf16}
             else:
@@ -552,7 +555,8 @@ def main():
         elif name == "gemm":
             alg = ra["stage_b_flops"] - ra["rot_flops"]   # 8 N_Rp nwin N_b 3N_at per (k,q) pair
             ach = alg / (ms_g * 1e-3) / 1e12
-            tr = profile_traffic("vertex_gemm", "vertex_tc.cu")
+            tr = profile_traffic("ncu_vertex_gemm_traffic_cscl8-80-40.txt", "vertex_tc.cu") \
+                if wl.name == "cscl8-80^3/40^3" else None
             roof = {"kernel": f"k_vertex_gemm* (tcgen05 R_ph contraction, {args.precision})", "bound": "tensor",
                     "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16, "peak_source": bf16_src,
                     "traffic": (tr[0] * ra["n_pairs"]) if tr else None, "algorithmic_flops": alg,

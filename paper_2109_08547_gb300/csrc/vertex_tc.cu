@@ -128,13 +128,16 @@ __global__ void k_phase_slices(ModelDev M, MeshDev D, int ns, int Kp, __nv_bfloa
 // On an n x n x n mesh every phase 2 pi q.R is 2 pi j / n with j = (q.R) mod n: the slices of
 // cos and sin of the n angles once (table [j][cos, sin][slice]), then every phase slice is a
 // lookup.  The angles' cosines and sines are FP64 library values of 2 pi j / n.
+// tab[2 j + part][8]: the ns slices of cos (part 0) or sin (part 1) of 2 pi j / n, padded to 8
+// BF16 (16 bytes) per entry so that one vector load fetches them
 __global__ void k_phase_angle_table(int n, int ns, __nv_bfloat16 *tab) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * n) return;
   const int j = t >> 1, part = t & 1;
   double sv, cv;
   sincospi(2.0 * double(j) / double(n), &sv, &cv);
-  fixed_slices(part == 0 ? cv : sv, ns, tab + size_t(t) * ns, 1);
+  for (int sl = ns; sl < 8; ++sl) tab[size_t(t) * 8 + sl] = __float2bfloat16_rn(0.f);
+  fixed_slices(part == 0 ? cv : sv, ns, tab + size_t(t) * 8, 1);
 }
 
 __global__ void k_phase_slices_cubic(ModelDev M, MeshDev D, int ns, int Kp, const __nv_bfloat16 *__restrict__ tab,
@@ -146,19 +149,22 @@ __global__ void k_phase_slices_cubic(ModelDev M, MeshDev D, int ns, int Kp, cons
   const int q = int(t / n8), r0 = int(t % n8) * 8;
   int b0, b1, b2;
   D.qm.unflat(q, b0, b1, b2);
-  __nv_bfloat16 v[8][8];
+  // the 8 slices of each of the 8 elements with one 16-byte load, then transposed to 8
+  // elements of each slice
+  __nv_bfloat16 in[8][8], v[8][8];
   for (int e = 0; e < 8; ++e) {
     const int r = r0 + e;
-    if (r >= 2 * R) {
-      for (int sl = 0; sl < ns; ++sl) v[sl][e] = __float2bfloat16_rn(0.f);
-      continue;
+    uint4 x = make_uint4(0u, 0u, 0u, 0u);
+    if (r < 2 * R) {
+      const int rr = r < R ? r : r - R;
+      const int *Rv = M.Rgp + 3 * rr;
+      const int j = pmod(b0 * Rv[0] + b1 * Rv[1] + b2 * Rv[2], n);
+      x = *reinterpret_cast<const uint4 *>(tab + (size_t(j) * 2 + (r < R ? 0 : 1)) * 8);
     }
-    const int rr = r < R ? r : r - R;
-    const int *Rv = M.Rgp + 3 * rr;
-    const int j = pmod(b0 * Rv[0] + b1 * Rv[1] + b2 * Rv[2], n);
-    const __nv_bfloat16 *src = tab + (size_t(j) * 2 + (r < R ? 0 : 1)) * ns;
-    for (int sl = 0; sl < ns; ++sl) v[sl][e] = src[sl];
+    *reinterpret_cast<uint4 *>(in[e]) = x;
   }
+  for (int sl = 0; sl < 8; ++sl)
+    for (int e = 0; e < 8; ++e) v[sl][e] = in[e][sl];
   __nv_bfloat16 *dst = phis + (size_t(q) * ns) * Kp + r0;
   for (int sl = 0; sl < ns; ++sl) *reinterpret_cast<uint4 *>(dst + sl * size_t(Kp)) = *reinterpret_cast<const uint4 *>(v[sl]);
 }
