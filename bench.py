@@ -87,6 +87,9 @@ def parse():
     p.add_argument("--no-variants", action="store_true", help="skip the one-step timings of the other modes")
     p.add_argument("--accel", type=int, default=0,
                    help="Anderson history depth of the outer iteration (0: the plain iteration)")
+    p.add_argument("--device-loop", type=int, default=1, choices=[0, 1],
+                   help="1: the solve as one CUDA graph launch with device-driven loops (plain outer iteration "
+                        "only); 0: host-driven loops")
     p.add_argument("--instances", type=int, default=32,
                    help="(T, mu, window) instances of the batched-vs-sequential comparison (0: skip it)")
     p.add_argument("--batch-nk", type=int, default=48, help="k mesh of the batched comparison (4-band model)")
@@ -268,7 +271,8 @@ def batched_block(B, ctx, wl, args, flush, torch, np):
         mesh = B.build_meshes_ibz(ctx, wl.kmesh, wl.qmesh, union, wl.degen_tol_eV, wl.omega_min_eV)
         rates = B.compute_transition_rates(ctx, 0.0, 0.0, wl.sigma_eV, wl.cutoff_sigmas, B.PRECISIONS[prec],
                                            instances=insts)
-        solve = B.solve_coupled_bte(ctx, "dragged", args.tol, solve_precision=solve_prec)
+        solve = B.solve_coupled_bte(ctx, "dragged", args.tol, solve_precision=solve_prec,
+                                    device_loop=bool(args.device_loop))
         return mesh, rates, solve, [B.transport_coefficients(ctx, i) for i in range(len(insts))]
 
     out = {"workload": wl.name, "instances": len(insts), "rhs": 2 * len(insts), "union_window_eV": list(union),
@@ -294,6 +298,7 @@ def batched_block(B, ctx, wl, args, flush, torch, np):
                     "fp64_sweeps": solve["n_sweeps"], "fp32_sweeps": solve["n_sweeps32"],
                     "union_pairs": mesh["n_pairs"], "union_tuples": rates["n_tuples"],
                     "union_entries": rates["n_entries"], "converged": solve["converged"],
+                    "graph_launches": solve["graph_launches"],
                     "max_coeff_rel_err_vs_sequential_fp64": worst}
     return out
 
@@ -450,10 +455,11 @@ def main():
 
     prec = B.PRECISIONS[args.precision]
 
-    def step(p=prec, sp=args.solve, acc=args.accel, tol=args.tol, delta="gauss"):
+    def step(p=prec, sp=args.solve, acc=args.accel, tol=args.tol, delta="gauss", dl=None):
         w = wl if delta == "gauss" else dataclasses.replace(wl, delta=delta)
+        dl = bool(args.device_loop) and acc == 0 if dl is None else dl
         return B.run_path(ctx, w, level="dragged", ko_correction=True, precision=p, solve_precision=sp, accel=acc,
-                          tol=tol)
+                          tol=tol, device_loop=dl)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -487,13 +493,13 @@ def main():
     # FP64 GPU path at this run's tolerance, timed the same way (its time to converged
     # coefficients is the metric's comparator)
     flush.zero_()
-    ref = step(B.FP64, "fp64", 0, REF_TOL)
+    ref = step(B.FP64, "fp64", 0, REF_TOL, dl=False)
     fp64_times = []
     for i in range(3):
         flush.zero_()
         torch.cuda.synchronize()
         tv = time.perf_counter()
-        rf = step(B.FP64, "fp64", 0, args.tol)
+        rf = step(B.FP64, "fp64", 0, args.tol, dl=False)
         torch.cuda.synchronize()
         if i > 0:
             fp64_times.append(time.perf_counter() - tv)
@@ -503,20 +509,29 @@ def main():
     accuracy = {"reference": f"FP64 vertex + plain FP64 iteration, tol {REF_TOL:g}",
                 "max_coeff_rel_err": max(err.values()), "coeff_rel_err": err,
                 "within_1e-6": max(err.values()) <= METRIC_RTOL}
-    fp64_block = {"mode": "FP64 vertex (CUDA cores) + plain FP64 iteration + no outer acceleration",
+    fp64_block = {"mode": "FP64 vertex (CUDA cores) + plain FP64 iteration + no outer acceleration "
+                          "(host-driven loops)",
                   "tol": args.tol, "s_to_converged": s_fp64, "value": rf.rates["n_tuples"] / s_fp64,
                   "rates_ms": rf.rates["ms"], "solve_ms": rf.solve["ms"], "outer_iters": rf.solve["outer_iters"],
                   "fp64_sweeps": rf.solve["n_sweeps"], "max_coeff_rel_err": max(fp64_err.values()),
                   "speedup_of_default": s_fp64 / s_step}
 
-    # dominant kernels and their rooflines (device time from CUDA events in this run)
+    # dominant kernels and their rooflines (device time from CUDA events in this run); the
+    # device-driven solve times no single kernel, so the sweep kernels are timed in one
+    # host-driven step of the same mode
     mean = lambda f: statistics.mean(f(r) for r in results)
     ms_a = mean(lambda r: r.rates["ms_stage_a"])
     ms_b = mean(lambda r: r.rates["ms_stage_b"])
     ms_g = mean(lambda r: r.rates["ms_gemm"])
     ms_ep = mean(lambda r: r.rates["ms_epilogue"])
-    ms_self = mean(lambda r: r.solve["ms_self_kernel"])
-    ms_corr = mean(lambda r: r.solve["ms_corr"])
+    host_loop = r0
+    if r0.solve["graph_launches"] > 0:
+        flush.zero_()
+        step(dl=False)
+        flush.zero_()
+        host_loop = step(dl=False)
+    ms_self = host_loop.solve["ms_self_kernel"]
+    ms_corr = host_loop.solve["ms_corr"]
     peaks = measured_peaks()
     bf16 = peaks.get("bf16_tflops", 1900.0)
     bf16_src = "MEASURED_PEAKS.json bf16_tflops (measured burst)" if "bf16_tflops" in peaks else "fallback"
@@ -532,7 +547,7 @@ def main():
         cands.append(("corr", ms_corr))
 
     def roof_of(name):
-        ra, so = r0.rates, r0.solve
+        ra, so = r0.rates, host_loop.solve
         base = {"ms_per_step": None, "share_of_step": None}
         if name == "stage_a":
             alg = ra["stage_a_flops"]     # 8 N_Re ncol per irreducible-window k, plus the band rotation
@@ -620,8 +635,9 @@ def main():
         h2d = int(sum(v.numel() * v.element_size() for v in pinned.values()))
         ctx2 = B.Context(local, stream=stream.cuda_stream)
         B.set_wannier_model(ctx2, mp)
+        dl = bool(args.device_loop) and args.accel == 0
         B.run_path(ctx2, wl, level="dragged", ko_correction=True, precision=prec, solve_precision=args.solve,
-                   accel=args.accel, tol=args.tol)       # warm-up (allocations, tile tuning)
+                   accel=args.accel, tol=args.tol, device_loop=dl)       # warm-up (allocations, tile tuning)
         barrier()
         torch.cuda.synchronize()
         t1 = time.perf_counter()
@@ -633,7 +649,7 @@ def main():
             B.set_wannier_model(ctx2, mp)      # returns once the arrays are on the device
             t_model += time.perf_counter() - tm
             rr = B.run_path(ctx2, wl, level="dragged", ko_correction=True, precision=prec,
-                            solve_precision=args.solve, accel=args.accel, tol=args.tol)
+                            solve_precision=args.solve, accel=args.accel, tol=args.tol, device_loop=dl)
             tup += rr.rates["n_tuples"]
         torch.cuda.synchronize()
         barrier()
@@ -654,16 +670,19 @@ def main():
                  for sp in ("fp64", "mixed") if (name, sp) != (args.precision, args.solve)]
         cases.append((f"{args.precision}+{args.solve}-solve+outer-accel-{3 if args.accel == 0 else 0}", prec,
                       args.solve, 3 if args.accel == 0 else 0, "gauss"))
+        if args.device_loop and args.accel == 0:
+            cases.append((f"{args.precision}+{args.solve}-solve+host-driven-loops", prec, args.solve, 0, "gauss"))
         # the paper's default delta: the analytic tetrahedron method (no width); its rates differ
         # from the Gaussian's, so its coefficient difference from the reference is physics, not error
         cases.append((f"{args.precision}+{args.solve}-solve+tetrahedron-delta", prec, args.solve, args.accel, "tetra"))
         for name, p, sp, acc, dk in cases:
+            dlv = False if name.endswith("host-driven-loops") else None
             flush.zero_()
-            step(p, sp, acc, delta=dk)    # warm-up of this mode
+            step(p, sp, acc, delta=dk, dl=dlv)    # warm-up of this mode
             flush.zero_()
             torch.cuda.synchronize()
             tv = time.perf_counter()
-            rv = step(p, sp, acc, delta=dk)
+            rv = step(p, sp, acc, delta=dk, dl=dlv)
             torch.cuda.synchronize()
             sv = time.perf_counter() - tv
             e = coeff_errors(rv.coeffs, ref.coeffs)
@@ -672,6 +691,7 @@ def main():
                               "stage_b_ms": rv.rates["ms_stage_b"], "solve_ms": rv.solve["ms"],
                               "fp64_sweeps": rv.solve["n_sweeps"], "fp32_sweeps": rv.solve["n_sweeps32"],
                               "outer_iters": rv.solve["outer_iters"], "outer_accel": acc, "delta": dk,
+                              "device_loop": rv.solve["graph_launches"] > 0,
                               "tuples": rv.rates["n_tuples"], "entries": rv.rates["n_entries"],
                               "max_coeff_rel_err": max(e.values()), "coeff_rel_err": e}
 
@@ -702,6 +722,7 @@ def main():
                        "kmesh": list(wl.kmesh), "qmesh": list(wl.qmesh), "T_K": wl.T_K, "mu_eV": wl.mu_eV,
                        "window_eV": list(wl.window), "sigma_eV": wl.sigma_eV, "level": "dragged+KO",
                        "tol": args.tol, "precision": args.precision, "solve": args.solve, "outer_accel": args.accel,
+                       "device_loop": r0.solve["graph_launches"] > 0,
                        "tc_tile": {"cols": r0.rates["tc_cols"], "kblock": r0.rates["tc_kblock"],
                                    "stages": r0.rates["tc_stages"]},
                        "l2": "256 MB buffer written before every step",
@@ -714,12 +735,15 @@ def main():
             "phases_ms": {"mesh": r0.mesh.get("ms"), "rates": r0.rates["ms"], "stage_a": r0.rates["ms_stage_a"],
                           "stage_b": r0.rates["ms_stage_b"], "tensor_gemm": r0.rates["ms_gemm"],
                           "rate_epilogue": r0.rates["ms_epilogue"],
-                          "solve": r0.solve["ms"], "e_sweeps": r0.solve["ms_e_sweep"],
-                          "self_sweep_kernel": r0.solve["ms_self_kernel"], "n_runs": r0.solve["n_runs"],
-                          "drag_terms": r0.solve["ms_drag"], "ph_sweeps": r0.solve["ms_ph_sweep"],
+                          "solve": r0.solve["ms"], "n_runs": r0.solve["n_runs"],
+                          "kernel_times_from": "host-driven step" if host_loop is not r0 else "timed step",
+                          "e_sweeps": host_loop.solve["ms_e_sweep"], "self_sweep_kernel": ms_self,
+                          "drag_terms": host_loop.solve["ms_drag"], "ph_sweeps": host_loop.solve["ms_ph_sweep"],
                           "n_sweeps": r0.solve["n_sweeps"], "outer_iters": r0.solve["outer_iters"],
                           "outer_iters32": r0.solve["outer_iters32"], "fp32_corrections": ms_corr,
-                          "n_sweeps32": r0.solve["n_sweeps32"]},
+                          "n_sweeps32": r0.solve["n_sweeps32"], "graph_launches": r0.solve["graph_launches"],
+                          "graph_reused": r0.solve["graph_reused"],
+                          "solve_host_driven_loops": host_loop.solve["ms"]},
             "variants": variants, "batched": batched, "warm_start": warm,
             "roofline": roof, "rooflines": rooflines, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks,

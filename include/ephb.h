@@ -261,6 +261,24 @@ typedef struct {
                                   ill-bounded system falls back to the newest g alone.  Same
                                   fixed point and convergence test as the plain iteration.
                                   Outside 0..EPHB_MAX_ACCEL_DEPTH: EPHB_EINVAL.              */
+  int device_loop;             /* 0: the host drives the loops (a residual read back after
+                                  every FP64 sweep and every outer iteration).  1: the whole
+                                  solve of every instance is ONE CUDA graph launch: the outer
+                                  iteration and the electron loop are conditional WHILE nodes
+                                  and the choices (phonon-side arithmetic, converged or
+                                  correct) SWITCH nodes, whose conditions one-thread kernels
+                                  set from the residuals on the device; each instance is an
+                                  independent branch, so all instances' sweeps are in flight
+                                  together.  Same kernels in the same order per instance:
+                                  bit-identical answers and counts.  Needs accel_depth 0 and
+                                  a level other than EPHB_RTA (otherwise EPHB_EINVAL).  The
+                                  graph is kept and launched again while the instances'
+                                  buffers, sizes and options are unchanged.  The per-kernel
+                                  times of ephb_solve_info are not measured in this mode (0);
+                                  ms is the device time of the launch.  A loop that runs past
+                                  600 s on the device stops and the call returns
+                                  EPHB_ETIMEOUT.  When the instances derive their lists at
+                                  solve time (memory bound), each instance is one launch.   */
 } ephb_solve_opts;
 #define EPHB_MAX_ACCEL_DEPTH 8
 
@@ -285,6 +303,8 @@ typedef struct {
   int outer_iters32;           /* outer iterations whose phonon scatter and drag term ran in
                                   FP32 (EPHB_SOLVE_MIXED, dragged level: those begun with the
                                   outer residual at or above 1e-5; never the last one)      */
+  int graph_launches;          /* device_loop: graph launches of the call (0: host-driven)   */
+  int graph_reused;            /* device_loop: 1 if the graph of the previous call was reused */
 } ephb_solve_info;
 
 /* Solves every instance.  `out` (optional) sums the counts and device times over the

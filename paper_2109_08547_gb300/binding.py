@@ -90,7 +90,7 @@ class RatesInfoC(C.Structure):
 class SolveOptsC(C.Structure):
     _fields_ = [("level", C.c_int), ("tol", C.c_double), ("inner_tol", C.c_double), ("max_outer", C.c_int),
                 ("max_inner", C.c_int), ("ko_correction", C.c_int), ("warm_start", C.c_int),
-                ("precision", C.c_int), ("accel_depth", C.c_int)]
+                ("precision", C.c_int), ("accel_depth", C.c_int), ("device_loop", C.c_int)]
 
 
 class SolveInfoC(C.Structure):
@@ -99,7 +99,8 @@ class SolveInfoC(C.Structure):
                 ("n_sweeps", C.c_int64), ("ms", C.c_double), ("ms_e_sweep", C.c_double),
                 ("ms_ph_sweep", C.c_double), ("e_sweep_bytes", C.c_double), ("ms_drag", C.c_double),
                 ("n_runs", C.c_int64), ("ms_self_kernel", C.c_double), ("e_sweep_flops", C.c_double),
-                ("n_sweeps32", C.c_int64), ("ms_corr", C.c_double), ("outer_iters32", C.c_int)]
+                ("n_sweeps32", C.c_int64), ("ms_corr", C.c_double), ("outer_iters32", C.c_int),
+                ("graph_launches", C.c_int), ("graph_reused", C.c_int)]
 
 
 class CoeffsC(C.Structure):
@@ -326,11 +327,12 @@ def instance_solve_info(ctx: Context, inst: int) -> dict:
 
 def solve_coupled_bte(ctx: Context, level="dragged", tol=1e-10, inner_tol=0.0, max_outer=500, max_inner=5000,
                       ko_correction=True, allow_noconv=False, warm_start=False, solve_precision="fp64",
-                      accel=0) -> dict:
-    """accel: Anderson history depth of the outer iteration (0: the plain iteration)."""
+                      accel=0, device_loop=False) -> dict:
+    """accel: Anderson history depth of the outer iteration (0: the plain iteration).
+    device_loop: the whole solve of every instance as one CUDA graph launch (device-driven loops)."""
     o = SolveOptsC(LEVELS[level] if isinstance(level, str) else int(level), float(tol), float(inner_tol),
                    int(max_outer), int(max_inner), 1 if ko_correction else 0, 1 if warm_start else 0,
-                   SOLVE_PRECISIONS[solve_precision], int(accel))
+                   SOLVE_PRECISIONS[solve_precision], int(accel), 1 if device_loop else 0)
     info = SolveInfoC()
     st = _check(ctx, _lib.ephb_solve_coupled_bte(ctx.handle, C.byref(o), C.byref(info)),
                 allow=(ENOCONV,) if allow_noconv else ())
@@ -406,13 +408,14 @@ class PathResult:
 
 
 def run_path(ctx: Context, wl, level="dragged", ko_correction=True, tol=None, max_outer=500, max_inner=5000,
-             precision=FP64, allow_noconv=False, solve_precision="fp64", accel=0) -> PathResult:
+             precision=FP64, allow_noconv=False, solve_precision="fp64", accel=0,
+             device_loop=False) -> PathResult:
     """The whole hot path for one workload on an existing context whose model is set."""
     mesh = build_meshes_ibz(ctx, wl.kmesh, wl.qmesh, wl.window, wl.degen_tol_eV, wl.omega_min_eV)
     rates = compute_transition_rates(ctx, wl.T_K, wl.mu_eV, wl.sigma_eV, wl.cutoff_sigmas, precision,
                                      delta=getattr(wl, "delta", "gauss"))
     solve = solve_coupled_bte(ctx, level, wl.tol if tol is None else tol, 0.0, max_outer, max_inner, ko_correction,
-                              allow_noconv, solve_precision=solve_precision, accel=accel)
+                              allow_noconv, solve_precision=solve_precision, accel=accel, device_loop=device_loop)
     return PathResult(mesh, rates, solve, transport_coefficients(ctx))
 
 

@@ -17,7 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libephb.so")
-SOURCES = ["api.cu", "bloch.cu", "vertex.cu", "vertex_tc.cu", "bte.cu", "scan.cu", "noalloc.cu", "batch.cu", "mlp.cu"]
+SOURCES = ["api.cu", "bloch.cu", "vertex.cu", "vertex_tc.cu", "bte.cu", "scan.cu", "noalloc.cu", "batch.cu", "mlp.cu",
+           "solve_graph.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing",
          "--expt-relaxed-constexpr"]

@@ -20,6 +20,7 @@ std::atomic<long long> g_launches{0};
 }
 
 void ephb::note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long ephb::launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
@@ -109,6 +110,14 @@ struct InstState {
   DBuf<unsigned> fuse_ctr;      // blocks done in the fused finalisation
   bool have_f32 = false;
   DBuf<unsigned> vmaxb;
+  DBuf<double> Afold;           // phonon fold at the q representatives [n_qrep][nbr][6]
+  // mixed iteration, early outer iterations: FP32 copies of the instance's rates (X, Y) and of
+  // the responses ([state][I | J]) and phonon deviations ([mode][F | G]); rebuilt per solve
+  DBuf<float2> X32;
+  DBuf<float> Y32, IJ32, FG32;
+  // later outer iterations: float-float copies of the same (FP64-grade on the FP32 pipe)
+  DBuf<float4> Xff;
+  DBuf<float2> Yff, IJff, FGff;
   bool bte_ready = false, has_warm = false, solved = false;
   bool lists_pending = false;   // the instance's lists are to be derived from the union lists
   ephb_solve_info last{};       // the instance's last solve
@@ -125,6 +134,8 @@ struct InstState {
     for (auto *b : {&run_w32, &rI, &rJ, &dI, &dJ, &dI2, &dJ2, &part32}) b->release();
     IJ.release();
     IJ2.release();
+    X32.release(); Y32.release(); IJ32.release(); FG32.release();
+    Xff.release(); Yff.release(); IJff.release(); FGff.release();
     have_f32 = false;
     lists_pending = true;
   }
@@ -144,6 +155,9 @@ struct InstState {
     IJ.release();
     IJ2.release();
     fuse_ctr.release();
+    Afold.release();
+    X32.release(); Y32.release(); IJ32.release(); FG32.release();
+    Xff.release(); Yff.release(); IJff.release(); FGff.release();
     bte_ready = has_warm = solved = have_f32 = lists_pending = false;
   }
 };
@@ -176,7 +190,6 @@ struct ephb_ctx : InstState {
   DBuf<int> qrep, qop, qstab, qflag, qlist, qrep_of;
   DBuf<int64_t> qpos;
   int64_t n_qrep = 0;
-  DBuf<double> Afold;                 // phonon fold at the q representatives [n_qrep][nbr][6]
   DBuf<__nv_bfloat16> angle_tab;      // slices of cos, sin of the 2 pi j / n angles of a cubic q mesh
   DBuf<int> atom_perm, atom_shift;
   DBuf<int> rep, op, stab, flag, ibzw_list, ibzw_of, npairs, pair_q, pair_i, qcount, pq_rank;
@@ -212,13 +225,6 @@ struct ephb_ctx : InstState {
   DBuf<double2> u_X;
   DBuf<int> u_ph_st;
   DBuf<double> u_ph_V;
-  // mixed iteration, early outer iterations: FP32 copies of the instance's rates (X, Y) and of
-  // the responses ([state][I | J]) and phonon deviations ([mode][F | G]); rebuilt per solve
-  DBuf<float2> X32;
-  DBuf<float> Y32, IJ32, FG32;
-  // later outer iterations: float-float copies of the same (FP64-grade on the FP32 pipe)
-  DBuf<float4> Xff;
-  DBuf<float2> Yff, IJff, FGff;
   // Anderson acceleration of the outer iteration: ring of phonon updates g and residuals f
   DBuf<double> and_g, and_f, and_part, and_dots;
 
@@ -235,6 +241,21 @@ struct ephb_ctx : InstState {
   int force_defer = 0;    // EPHB_TUNE_DEFER_INSTANCES: derive instance lists at solve time always
   int stage_a_tmem = 0;   // EPHB_TUNE_STAGE_A_TMEM_A: stage A's A slices through tensor memory
   double *host_res = nullptr;   // pinned: kResLen doubles, then the sweep-loop control (4 ints)
+  // device-driven solve: the instantiated graph, the signature of what it was built from, the
+  // kernels per body (launch counts), the capture stream and the per-instance control blocks
+  cudaGraph_t sg_graph = nullptr;
+  cudaGraphExec_t sg_exec = nullptr;
+  std::vector<unsigned char> sg_sig;
+  std::vector<GraphKernels> sg_kernels;
+  cudaStream_t sg_cs = nullptr;
+  DBuf<GraphCtl> sg_ctl;
+  void drop_graph() {
+    if (sg_exec) cudaGraphExecDestroy(sg_exec);
+    if (sg_graph) cudaGraphDestroy(sg_graph);
+    sg_exec = nullptr;
+    sg_graph = nullptr;
+    sg_sig.clear();
+  }
 };
 
 namespace {
@@ -271,6 +292,7 @@ int64_t read_i64(ephb_ctx *ctx, const int64_t *dptr, cudaError_t &e) {
 
 MeshDev mesh_view(ephb_ctx *c) {
   MeshDev D;
+  std::memset(&D, 0, sizeof(D));
   D.km = c->km;
   D.qm = c->qm;
   for (int d = 0; d < 3; ++d) D.ratio[d] = c->ratio[d];
@@ -313,6 +335,7 @@ MeshDev mesh_view(ephb_ctx *c) {
 
 BteDev bte_view(ephb_ctx *c) {
   BteDev B;
+  std::memset(&B, 0, sizeof(B));
   B.nb = c->M.nb;
   B.nbr = c->M.nbr;
   B.nsym = c->M.nsym;
@@ -388,7 +411,7 @@ void ephb_destroy(ephb_ctx *ctx) {
   ctx->ktab.release(); ctx->interp.release(); ctx->qtab.release(); ctx->cvec.release(); ctx->u.release(); ctx->eps.release();
   ctx->vel.release(); ctx->w.release(); ctx->vph.release(); ctx->egrp.release(); ctx->pgrp.release();
   ctx->qrep.release(); ctx->qop.release(); ctx->qstab.release(); ctx->qflag.release(); ctx->qlist.release();
-  ctx->qrep_of.release(); ctx->qpos.release(); ctx->Afold.release(); ctx->atom_perm.release();
+  ctx->qrep_of.release(); ctx->qpos.release(); ctx->atom_perm.release();
   ctx->atom_shift.release(); ctx->angle_tab.release();
   ctx->amask.release(); ctx->rmask.release(); ctx->rep.release(); ctx->op.release(); ctx->stab.release(); ctx->flag.release();
   ctx->ibzw_list.release(); ctx->ibzw_of.release(); ctx->npairs.release(); ctx->pair_q.release();
@@ -403,6 +426,9 @@ void ephb_destroy(ephb_ctx *ctx) {
   ctx->w32.release();
   ctx->u_row_ptr.release(); ctx->u_ph_row_ptr.release(); ctx->u_kpns.release(); ctx->u_ph_kpn.release();
   ctx->u_X.release(); ctx->u_ph_st.release(); ctx->u_ph_V.release();
+  ctx->drop_graph();
+  ctx->sg_ctl.release();
+  if (ctx->sg_cs) cudaStreamDestroy(ctx->sg_cs);
   ctx->release_all();
   for (auto &sl : ctx->slots) sl.release_all();
   if (ctx->host_res) cudaFreeHost(ctx->host_res);
@@ -786,12 +812,34 @@ ephb_status derive_one(ephb_ctx *ctx) {
   return EPHB_OK;
 }
 
+// Entries of the electron and phonon lists of the instance in the base (its window), counted
+// from the union lists without writing them.
+ephb_status count_one(ephb_ctx *ctx, int64_t &ne, int64_t &nphe) {
+  cudaStream_t st = ctx->stream;
+  const ModelDev &M = ctx->M;
+  const int64_t nst = ctx->n_ibzw * M.nb, nph = ctx->qm.size() * M.nbr;
+  MeshDev D = mesh_view(ctx);
+  const InstWindow w{ctx->win_lo, ctx->win_hi};
+  CK(launch_inst_count(M, D, w, ctx->u_row_ptr.p, ctx->u_kpns.p, ctx->u_ph_row_ptr.p, ctx->u_ph_st.p,
+                       ctx->u_ph_kpn.p, ctx->cntE.p, ctx->cntPh.p, st));
+  CK(ctx->escan.ensure(nst + 1));
+  CK(ctx->phscan.ensure(nph + 1));
+  CK(exclusive_scan<int>(ctx->cntE.p, ctx->escan.p, nst, ctx->scal.p + 3, ctx->scratch.p, ctx->scratch.n, st));
+  CK(exclusive_scan<int>(ctx->cntPh.p, ctx->phscan.p, nph, ctx->scal.p + 4, ctx->scratch.p, ctx->scratch.n, st));
+  int64_t hs[2];
+  CK(cudaMemcpyAsync(hs, ctx->scal.p + 3, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  ne = hs[0];
+  nphe = hs[1];
+  return EPHB_OK;
+}
+
 // The lists just computed (vertex-only) become the union lists; each instance then takes the
 // entries of its window with its occupation factors.  When the instances' lists together would
-// not fit the free device memory (the union lists x the instance count, with the solve's
-// working arrays), each instance keeps only its window, T and mu here and derives its lists
-// when it is solved; after its solve the lists and sweep arrays are released again (the
-// responses, rates and coefficient inputs stay).
+// not fit the free device memory (their entry counts with the solve's working arrays), each
+// instance keeps only its window, T and mu here and derives its lists when it is solved; after
+// its solve the lists and sweep arrays are released again (the responses, rates and
+// coefficient inputs stay).
 ephb_status derive_instances(ephb_ctx *ctx, const ephb_thermo *inst, int ninst) {
   const ModelDev &M = ctx->M;
   const int64_t nst = ctx->n_ibzw * M.nb, nph = ctx->qm.size() * M.nbr;
@@ -812,11 +860,12 @@ ephb_status derive_instances(ephb_ctx *ctx, const ephb_thermo *inst, int ninst) 
   CK(ctx->nbq.ensure(size_t(nph)));
   CK(ctx->wr.ensure(size_t(nph)));
   CK(ctx->ut.ensure(size_t(nph) * M.nbr));
-  // lists (20 B per electron entry, 16 B per phonon entry) and sweep arrays (~28 B per entry)
+  // per instance: lists (20 B per electron entry, 16 B per phonon entry), sweep arrays and
+  // run scratch (~28 B per electron entry) and the mixed iteration's FP32 and float-float
+  // copies of the rates (24 B per electron entry, 12 B per phonon entry)
   size_t free_b = 0, total_b = 0;
   CK(cudaMemGetInfo(&free_b, &total_b));
-  const double per_inst = 48.0 * double(ctx->u_entries) + 24.0 * double(ctx->u_ph_entries);
-  const bool defer = ninst > 1 && (ctx->force_defer || double(ninst) * per_inst > 0.5 * double(free_b));
+  double need = 0.0;
   for (int i = 0; i < ninst; ++i) {
     select_instance(ctx, i);
     ctx->T = inst[i].T_K;
@@ -827,6 +876,16 @@ ephb_status derive_instances(ephb_ctx *ctx, const ephb_thermo *inst, int ninst) 
     ctx->n_tuples = ctx->u_tuples;
     ctx->bte_ready = false;
     ctx->lists_pending = true;
+    if (ninst > 1 && !ctx->force_defer) {
+      int64_t ne = 0, nphe = 0;
+      ephb_status r = count_one(ctx, ne, nphe);
+      if (r != EPHB_OK) return r;
+      need += 72.0 * double(ne) + 36.0 * double(nphe);
+    }
+  }
+  const bool defer = ninst > 1 && (ctx->force_defer || need > 0.5 * double(free_b));
+  for (int i = 0; i < ninst; ++i) {
+    select_instance(ctx, i);
     if (!defer) {
       ephb_status r = derive_one(ctx);
       if (r != EPHB_OK) return r;
@@ -1207,6 +1266,7 @@ ephb_status bte_setup(ephb_ctx *ctx) {
 
 SweepSegs entry_segs(ephb_ctx *c) {
   SweepSegs S;
+  std::memset(&S, 0, sizeof(S));
   S.nseg = c->neseg;
   S.seg_row = c->eseg_row.p;
   S.seg_begin = c->eseg_begin.p;
@@ -1217,6 +1277,7 @@ SweepSegs entry_segs(ephb_ctx *c) {
 
 SweepSegs run_segs(ephb_ctx *c) {
   SweepSegs S;
+  std::memset(&S, 0, sizeof(S));
   S.nseg = c->nrseg;
   S.seg_row = c->rseg_row.p;
   S.seg_begin = c->rseg_begin.p;
@@ -1241,9 +1302,7 @@ ephb_status coefficients_to_host(ephb_ctx *ctx, double *prev, bool electron = tr
 }  // namespace
 
 constexpr int kSweepBatch = 8;   // electron sweeps queued per host round trip
-constexpr int kCorrSweeps = 12;  // FP32 correction sweeps per FP64 sweep (mixed precision)
 static_assert(kAndMaxSlots == EPHB_MAX_ACCEL_DEPTH + 1, "Anderson ring size");
-constexpr double kPh32Until = 1e-5;  // outer residual below which the phonon-side terms are FP64
 
 namespace {
 
@@ -1656,6 +1715,286 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
   return EPHB_OK;
 }
 
+// ---- device-driven solve: every instance's coupled iteration in one CUDA graph launch
+
+constexpr double kGraphTimeLimitS = 600.0;   // a device loop running longer stops (EPHB_ETIMEOUT)
+
+void sig_bytes(std::vector<unsigned char> &sig, const void *v, size_t n) {
+  const unsigned char *p = static_cast<const unsigned char *>(v);
+  sig.insert(sig.end(), p, p + n);
+}
+#define sig_add(sig, v) sig_bytes((sig), &(v), sizeof(v))
+
+// The buffers of the instance in the base sized for the device-driven solve, and everything
+// its capture reads gathered into one record.
+ephb_status graph_prepare(ephb_ctx *ctx, const GraphOpts &go, int slot, GraphInst &g) {
+  if (!ctx->bte_ready) {
+    ephb_status s = bte_setup(ctx);
+    if (s != EPHB_OK) return s;
+  }
+  const ModelDev &M = ctx->M;
+  const int64_t nst = ctx->n_ibzw * M.nb, nph = ctx->qm.size() * M.nbr;
+  const bool mixed = go.precision == EPHB_SOLVE_MIXED;
+  if (mixed) {
+    CK(ctx->run_w32.ensure(ctx->nruns));
+    for (auto *b : {&ctx->rI, &ctx->rJ, &ctx->dI, &ctx->dJ, &ctx->dI2, &ctx->dJ2}) CK(b->ensure(nst * 3));
+    CK(ctx->part32.ensure(size_t(ctx->nrseg) * 6));
+  } else {
+    CK(ctx->IJ.ensure(nst * 3));
+    CK(ctx->IJ2.ensure(nst * 3));
+    CK(ctx->fuse_ctr.ensure(1));
+  }
+  if (go.ph32_allowed) {
+    CK(ctx->X32.ensure(ctx->n_entries));
+    CK(ctx->Y32.ensure(ctx->n_ph_entries));
+    CK(ctx->IJ32.ensure(nst * 6));
+    CK(ctx->FG32.ensure(nph * 6));
+    CK(ctx->Xff.ensure(ctx->n_entries));
+    CK(ctx->Yff.ensure(ctx->n_ph_entries));
+    CK(ctx->IJff.ensure(nst * 6));
+    CK(ctx->FGff.ensure(nph * 6));
+  }
+  std::memset(&g, 0, sizeof(g));
+  const BteDev B = bte_view(ctx);
+  const SweepSegs Sr = run_segs(ctx), Se = entry_segs(ctx);
+  std::memcpy(&g.B, &B, sizeof(B));
+  std::memcpy(&g.Sr, &Sr, sizeof(Sr));
+  std::memcpy(&g.Se, &Se, sizeof(Se));
+  g.nst = nst;
+  g.nph = nph;
+  g.n_entries = ctx->n_entries;
+  g.n_ph_entries = ctx->n_ph_entries;
+  g.nruns = ctx->nruns;
+  g.kinfo = ctx->kinfo.p;
+  g.run_col = ctx->run_col.p;
+  g.run_w = ctx->run_w.p;
+  g.I0 = ctx->I0.p;
+  g.J0 = ctx->J0.p;
+  g.inv_ffW = ctx->inv_ffW.p;
+  g.W_ph = ctx->W_ph.p;
+  g.inv_nnW = ctx->inv_nnW.p;
+  g.F0 = ctx->F0.p;
+  g.ph_Y = ctx->ph_Y.p;
+  g.e_X = ctx->e_X.p;
+  g.I = ctx->I.p;
+  g.J = ctx->J.p;
+  g.I2 = ctx->I2.p;
+  g.J2 = ctx->J2.p;
+  g.F = ctx->F.p;
+  g.G = ctx->G.p;
+  g.Btv = ctx->Btv.p;
+  g.Afold = ctx->Afold.p;
+  g.Dterm = ctx->Dterm.p;
+  g.seg_part = ctx->seg_part.p;
+  g.epart = ctx->epart.p;
+  g.ppart = ctx->ppart.p;
+  g.kpart = ctx->kpart.p;
+  g.res = ctx->res.p;
+  g.prev_in = ctx->prev_in.p;
+  g.prev_out = ctx->prev_out.p;
+  if (mixed) {
+    g.run_w32 = ctx->run_w32.p;
+    g.rI = ctx->rI.p;
+    g.rJ = ctx->rJ.p;
+    g.dI = ctx->dI.p;
+    g.dJ = ctx->dJ.p;
+    g.dI2 = ctx->dI2.p;
+    g.dJ2 = ctx->dJ2.p;
+    g.part32 = ctx->part32.p;
+  } else {
+    g.sctl = ctx->sctl.p;
+    g.fuse_ctr = ctx->fuse_ctr.p;
+    g.IJ = ctx->IJ.p;
+    g.IJ2 = ctx->IJ2.p;
+  }
+  if (go.ph32_allowed) {
+    g.X32 = ctx->X32.p;
+    g.Y32 = ctx->Y32.p;
+    g.IJ32 = ctx->IJ32.p;
+    g.FG32 = ctx->FG32.p;
+    g.Xff = ctx->Xff.p;
+    g.Yff = ctx->Yff.p;
+    g.IJff = ctx->IJff.p;
+    g.FGff = ctx->FGff.p;
+  }
+  g.warm = ctx->has_warm ? ctx->warm.p : nullptr;
+  g.ctl = ctx->sg_ctl.p + slot;
+  return EPHB_OK;
+}
+
+// Solves the instances `which` (their lists present) in one graph launch; infos[j] gets
+// instance which[j]'s summary.  The graph is reused when everything it was built from is
+// unchanged.
+ephb_status graph_solve_set(ephb_ctx *ctx, const ephb_solve_opts *o, const std::vector<int> &which,
+                            std::vector<ephb_solve_info> &infos, double &ms_launch, bool &reused) {
+  GraphOpts go;
+  std::memset(&go, 0, sizeof(go));
+  go.level = o->level;
+  go.precision = o->precision;
+  go.ko = o->ko_correction ? 1 : 0;
+  go.max_outer = o->max_outer;
+  go.max_inner = o->max_inner;
+  go.ph32_allowed = o->precision == EPHB_SOLVE_MIXED && o->level == EPHB_DRAGGED;
+  go.tol = o->tol;
+  go.inner_tol = o->inner_tol > 0 ? o->inner_tol : 0.1 * o->tol;
+  go.time_limit_s = kGraphTimeLimitS;
+  CK(ctx->sg_ctl.ensure(size_t(ctx->ninst)));
+  std::vector<GraphInst> gi(which.size());
+  std::vector<unsigned char> sig;
+  sig_add(sig, go);
+  sig_add(sig, ctx->M);
+  const MeshDev D = mesh_view(ctx);
+  sig_add(sig, D);
+  for (size_t j = 0; j < which.size(); ++j) {
+    select_instance(ctx, which[j]);
+    GraphInst &g = gi[j];
+    ephb_status s = graph_prepare(ctx, go, which[j], g);
+    if (s != EPHB_OK) return s;
+    // the warm start is applied only where asked for
+    if (!o->warm_start) g.warm = nullptr;
+    sig_add(sig, g);
+  }
+  reused = ctx->sg_exec && sig == ctx->sg_sig;
+  if (!reused) {
+    ctx->drop_graph();
+    if (!ctx->sg_cs) CK(cudaStreamCreateWithFlags(&ctx->sg_cs, cudaStreamNonBlocking));
+    cudaError_t e = build_solve_graph(ctx->M, D, gi, go, ctx->sg_cs, &ctx->sg_graph, &ctx->sg_exec, ctx->sg_kernels);
+    if (e != cudaSuccess) {
+      ctx->drop_graph();
+      return fail(ctx, EPHB_ECUDA, std::string("building the solve graph: ") + cudaGetErrorString(e));
+    }
+    ctx->sg_sig = sig;
+  }
+  const cudaStream_t st = ctx->stream;
+  cudaEvent_t ev0, ev1;
+  CK(cudaEventCreate(&ev0));
+  CK(cudaEventCreate(&ev1));
+  CK(cudaEventRecord(ev0, st));
+  CK(cudaGraphLaunch(ctx->sg_exec, st));
+  CK(cudaEventRecord(ev1, st));
+  std::vector<GraphCtl> hc(ctx->ninst);
+  CK(cudaMemcpyAsync(hc.data(), ctx->sg_ctl.p, sizeof(GraphCtl) * ctx->ninst, cudaMemcpyDeviceToHost, st));
+  std::vector<unsigned long long> nzero(which.size(), 0ull);
+  for (size_t j = 0; j < which.size(); ++j) {
+    select_instance(ctx, which[j]);
+    CK(cudaMemcpyAsync(&nzero[j], ctx->nzero.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, ev0, ev1));
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  ms_launch = ms;
+  infos.assign(which.size(), ephb_solve_info{});
+  long long kernels = 0;
+  bool late = false;
+  for (size_t j = 0; j < which.size(); ++j) {
+    const GraphCtl &c = hc[which[j]];
+    const GraphKernels &k = ctx->sg_kernels[j];
+    kernels += k.prologue + c.n_outer_body * k.outer_fixed + c.n_inner_body * k.inner_fixed;
+    for (int m = 0; m < 3; ++m) kernels += c.n_ph_body[m] * k.ph[m];
+    for (int b = 0; b < 2; ++b) kernels += c.n_in_body[b] * k.in[b];
+    late = late || c.timed_out;
+    select_instance(ctx, which[j]);
+    ephb_solve_info &f = infos[j];
+    f.outer_iters = c.outer;
+    f.inner_iters_total = int(c.inner_total);
+    f.converged = c.converged;
+    f.n_zero_rate_states = int(nzero[j]);
+    f.residual = c.residual;
+    f.lambda = c.lambda;
+    f.n_sweeps = c.sweeps;
+    f.ms = ms;
+    f.e_sweep_flops = double(ctx->nruns) * (ctx->M.nsym > 1 ? 12.0 + 36.0 : 12.0);
+    f.e_sweep_bytes = 12.0 * double(ctx->nruns) + double(ctx->n_ibzw * ctx->M.nb) * (8.0 + 20.0 * 8.0);
+    f.n_runs = ctx->nruns;
+    f.n_sweeps32 = c.sweeps32;
+    f.outer_iters32 = c.outer32;
+    f.graph_launches = 1;
+    f.graph_reused = reused ? 1 : 0;
+    ctx->have_f32 = go.precision == EPHB_SOLVE_MIXED;
+    ctx->solved = true;
+  }
+  note_launches(int(kernels));
+  if (late) return fail(ctx, EPHB_ETIMEOUT, "a device-driven loop ran past its time limit");
+  return EPHB_OK;
+}
+
+// ephb_solve_coupled_bte with opts->device_loop set.
+ephb_status solve_graph(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *out) {
+  ephb_solve_info sum{};
+  sum.converged = 1;
+  sum.lambda = 1.0;
+  bool noconv = false;
+  std::vector<std::vector<int>> sets;
+  if (ctx->deferred) {
+    for (int i = 0; i < ctx->ninst; ++i) sets.push_back({i});
+  } else {
+    sets.emplace_back();
+    for (int i = 0; i < ctx->ninst; ++i) sets.back().push_back(i);
+  }
+  for (const auto &which : sets) {
+    if (ctx->deferred) {
+      select_instance(ctx, which[0]);
+      if (ctx->lists_pending) {
+        ephb_status d = derive_one(ctx);
+        if (d != EPHB_OK) return d;
+      }
+    }
+    std::vector<ephb_solve_info> infos;
+    double ms = 0.0;
+    bool reused = false;
+    ephb_status r = graph_solve_set(ctx, o, which, infos, ms, reused);
+    if (r != EPHB_OK) return r;
+    sum.ms += ms;
+    sum.graph_launches += 1;
+    sum.graph_reused = reused ? 1 : 0;
+    for (size_t j = 0; j < which.size(); ++j) {
+      select_instance(ctx, which[j]);
+      ephb_solve_info one = infos[j];
+      if (!one.converged && o->warm_start && ctx->has_warm) {
+        // the learned start did not converge: the plain RTA start decides (host-driven)
+        ephb_solve_opts plain = *o;
+        plain.warm_start = 0;
+        plain.device_loop = 0;
+        ephb_solve_info again{};
+        ephb_status r2 = solve_one(ctx, &plain, &again);
+        if (r2 != EPHB_OK && r2 != EPHB_ENOCONV) return r2;
+        again.n_sweeps += one.n_sweeps;
+        again.n_sweeps32 += one.n_sweeps32;
+        again.inner_iters_total += one.inner_iters_total;
+        again.ms += one.ms;
+        sum.ms += again.ms - one.ms;
+        one = again;
+      }
+      noconv = noconv || !one.converged;
+      ctx->last = one;
+      sum.outer_iters = std::max(sum.outer_iters, one.outer_iters);
+      sum.inner_iters_total += one.inner_iters_total;
+      sum.converged = sum.converged && one.converged;
+      sum.n_zero_rate_states += one.n_zero_rate_states;
+      sum.residual = std::max(sum.residual, one.residual);
+      sum.lambda = one.lambda;
+      sum.n_sweeps += one.n_sweeps;
+      sum.e_sweep_bytes += one.e_sweep_bytes;
+      sum.n_runs += one.n_runs;
+      sum.n_sweeps32 += one.n_sweeps32;
+      sum.outer_iters32 = std::max(sum.outer_iters32, one.outer_iters32);
+      sum.e_sweep_flops += one.e_sweep_flops;
+    }
+    if (ctx->deferred) {
+      CK(cudaStreamSynchronize(ctx->stream));
+      ctx->release_lists();
+      ctx->drop_graph();   // its buffers are gone
+    }
+  }
+  select_instance(ctx, 0);
+  if (out) *out = sum;
+  ctx->stage = 4;
+  if (noconv) return fail(ctx, EPHB_ENOCONV, "iteration limit reached before the tolerance");
+  return EPHB_OK;
+}
+
 }  // namespace
 
 ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *out) {
@@ -1668,7 +2007,11 @@ ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb
     return fail(ctx, EPHB_EINVAL, "bad solve precision");
   if (o->accel_depth < 0 || o->accel_depth > EPHB_MAX_ACCEL_DEPTH)
     return fail(ctx, EPHB_EINVAL, "accel_depth outside 0..EPHB_MAX_ACCEL_DEPTH");
+  if (o->device_loop != 0 && o->device_loop != 1) return fail(ctx, EPHB_EINVAL, "device_loop must be 0 or 1");
+  if (o->device_loop && (o->accel_depth != 0 || o->level == EPHB_RTA))
+    return fail(ctx, EPHB_EINVAL, "device_loop needs accel_depth 0 and a level other than EPHB_RTA");
   CK(cudaSetDevice(ctx->device));
+  if (o->device_loop) return solve_graph(ctx, o, out);
   // every instance in turn; the summary adds up counts and times and keeps the worst residual
   ephb_solve_info sum{};
   sum.converged = 1;

@@ -348,4 +348,60 @@ cudaError_t launch_coeff_final(const ModelDev &M, const BteDev &B, const double 
 cudaError_t launch_ko(const ModelDev &M, const MeshDev &D, const BteDev &B, double *I, const double *J,
                       double *kpart, double *res, cudaStream_t st);
 
+// Mixed-precision iteration constants shared by the host-driven and graph-driven loops.
+constexpr int kCorrSweeps = 12;       // FP32 correction sweeps per FP64 sweep
+constexpr double kPh32Until = 1e-5;   // outer residual below which the phonon-side terms are FP64-grade
+
+// ---- solve_graph.cu: the coupled iteration of several instances as ONE CUDA graph launch.
+// The loops of "Coupled and decoupled BTEs" (the outer phonon/electron iteration, the inner
+// electron loop) run on the device: conditional graph nodes (WHILE for the loops, SWITCH for
+// the choice of the phonon-side arithmetic and for "converged / correct") whose conditions are
+// set by one-thread control kernels reading the residuals.  Every instance is an independent
+// branch of the graph, so the instances' kernels overlap on the GPU.  Kernels and their order
+// within an instance are those of the host-driven loop, so the results are bit-identical.
+struct GraphCtl {                       // per instance, device memory, read back after the launch
+  int outer, outer32, outer_seen, ph_mode;   // ph_mode: 0 FP32, 1 float-float, 2 FP64 phonon-side terms
+  int inner_it, inner_ok, converged, timed_out;
+  long long sweeps, sweeps32, inner_total;
+  long long n_outer_body, n_inner_body, n_ph_body[3], n_in_body[2];   // body executions
+  double residual, tol_k, last_tol_k, lambda;
+  unsigned long long t0;                // %globaltimer at the start of the instance
+};
+struct GraphOpts {
+  int level, precision, ko, max_outer, max_inner, ph32_allowed;
+  double tol, inner_tol, time_limit_s;
+};
+// Everything the capture of one instance reads (device pointers, counts, views).
+struct GraphInst {
+  BteDev B;
+  SweepSegs Sr, Se;                     // segments of the partner runs and of the entry stream
+  int64_t nst, nph, n_entries, n_ph_entries, nruns;
+  const int2 *kinfo;
+  const uint32_t *run_col;
+  const double *run_w, *I0, *J0, *inv_ffW, *W_ph, *inv_nnW, *F0, *ph_Y;
+  const double2 *e_X;
+  double *I, *J, *I2, *J2, *F, *G, *Btv, *Afold, *Dterm, *seg_part, *epart, *ppart, *kpart, *res, *prev_in, *prev_out;
+  float *run_w32, *rI, *rJ, *dI, *dJ, *dI2, *dJ2, *part32;     // mixed electron loop
+  float2 *X32;                                                 // mixed, FP32 phonon-side terms
+  float *Y32, *IJ32, *FG32;
+  float4 *Xff;                                                 // mixed, float-float phonon-side terms
+  float2 *Yff, *IJff, *FGff;
+  int *sctl;                                                   // FP64 electron loop (fused finalisation)
+  unsigned *fuse_ctr;
+  double2 *IJ, *IJ2;
+  const float *warm;                                           // warm-start factors, or nullptr (RTA start)
+  GraphCtl *ctl;
+};
+// Kernels captured per body, for the launch count of an execution.
+struct GraphKernels {
+  long long prologue = 0, outer_fixed = 0, ph[3] = {0, 0, 0}, inner_fixed = 0, in[2] = {0, 0};
+};
+// Builds and instantiates the graph of all instances (levels partial, dragless, dragged;
+// accel_depth 0).  cs: a stream used only for capture.  The kernel count of every body is
+// returned per instance; the library's launch counter is left unchanged by the capture.
+cudaError_t build_solve_graph(const ModelDev &M, const MeshDev &D, const std::vector<GraphInst> &insts,
+                              const GraphOpts &o, cudaStream_t cs, cudaGraph_t *graph, cudaGraphExec_t *exec,
+                              std::vector<GraphKernels> &kernels);
+long long launch_count();
+
 }  // namespace ephb
