@@ -42,7 +42,7 @@ FP64_PEAK_TFLOPS = 1.188  # lower of two measurements (1.188, 1.255)
 FP64_PEAK_SRC = "measured FP64 FMA rate (profiles/fp64_peak_gb300.txt)"
 # arithmetic of the vertex contraction per precision mode (everything else is FP64)
 DTYPES = {"fp64": "f64", "fp64-sliced": "f64 (tcgen05 bf16 exact fixed-point slices, f32 accumulate)",
-          "split-bf16": "bf16 x3 slices (x4 for contractions longer than 256), f32 accumulate (mixed)"}
+          "split-bf16": "bf16 x4 slices, f32 accumulate (mixed)"}
 SOLVE_DTYPES = {"fp64": "; iteration f64",
                 "mixed": "; iteration f64 residual sweeps + f32 correction sweeps (same fixed point)"}
 COEFFS = ("sigma", "sigmaS", "S", "alpha_el", "kappa0_el", "kappa_el", "alpha_ph", "kappa_ph")

@@ -176,7 +176,7 @@ typedef struct {
  *                     of 8 bits, the 28 slice products of the leading diagonals, the four
  *                     largest diagonals each kept in an accumulator where the FP32 sums are
  *                     exact; FP64-grade results.  Needs 2 nRgp <= 256 (EPHB_EINVAL otherwise).
- *   EPHB_SPLIT_BF16   3 slices, the leading diagonal exact, the rest in one FP32 accumulator,
+ *   EPHB_SPLIT_BF16   4 slices, the leading diagonal exact, the rest in one FP32 accumulator,
  *                     and the band/branch rotations of the epilogue in FP32 (mixed precision,
  *                     ~1e-7 relative).  Needs 2 nRgp <= 1024.
  *   EPHB_SPLIT_TF32   not available (EPHB_EINVAL).

@@ -233,7 +233,7 @@ struct ephb_ctx : InstState {
   std::vector<InstState> slots = std::vector<InstState>(1);
   // tuning: column-chunk width of the tensor-core contraction (FP64-grade, mixed); 0 = not
   // tuned yet.  force_cols != 0 overrides the tuner.
-  int tune_cols[3] = {0, 0, 0};   // [7 slices, 3 slices, 8 slices]
+  int tune_cols[3] = {0, 0, 0};   // [7 slices, 4 slices, 8 slices]
   int tune_kc[3] = {32, 32, 32};
   int tune_st[3] = {2, 2, 2};
   int force_cols = 0;
@@ -1012,7 +1012,7 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
   CK(tg.init());
   const bool tensor = precision != EPHB_FP64;
   const int ns = tensor ? tc_slices_for(tc_kp(M), precision == EPHB_FP64_SLICED) : 0;
-  const int tslot = ns == 8 ? 2 : (ns == 7 ? 0 : 1);   // tuned tile shape per slicing (3 or 4 slices: 1)
+  const int tslot = ns == 8 ? 2 : (ns == 7 ? 0 : 1);   // tuned tile shape per slicing (4 slices: 1)
   const int ncm = tensor && ctx->force_cols ? std::min(ctx->force_cols, tc_nc_max(ns)) : 0;   // 0: tuned width
   int autotuned = 0;
   // stage A on the tensor cores too, always in the FP64-grade form (its error would add to the

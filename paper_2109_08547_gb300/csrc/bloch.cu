@@ -3,6 +3,7 @@
 // window, the irreducible wedge of the k mesh and the (k, q) pair lists.
 #include "internal.h"
 #include "jacobi.cuh"
+#include "jacobi_warp.cuh"
 
 namespace ephb {
 
@@ -81,7 +82,8 @@ __global__ void __launch_bounds__(32 * kInterpWarps) k_fourier_interp(ModelDev M
   }
 }
 
-// One thread per listed k point: eigen-decomposition of H(k) (read from the interpolation),
+// One thread per listed k point (launches of many points: every FP64 instruction serves 32
+// matrices): eigen-decomposition of H(k) (read from the interpolation),
 // velocities <m| grad H |m> averaged over degenerate groups, the window masks.
 template <int NB>
 __global__ void __launch_bounds__(64) k_electron_bands(ModelDev M, Mesh km, const int *__restrict__ list, int64_t n,
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(64) k_electron_bands(ModelDev M, Mesh km, cons
   rmask[k] = rot;
 }
 
-// One thread per listed q point: eigen-decomposition of D(q) (read from the interpolation),
+// One thread per listed q point (launches of many points): eigen-decomposition of D(q) (read from the interpolation),
 // hbar w = sqrt(max(lambda, 0)), velocities.
 template <int NB>
 __global__ void __launch_bounds__(64) k_phonon_modes(ModelDev M, Mesh qm, const int *__restrict__ list, int64_t n,
@@ -187,6 +189,141 @@ __global__ void __launch_bounds__(64) k_phonon_modes(ModelDev M, Mesh qm, const 
     pgrp[(size_t(q) * nb + s) * 2] = grp[2 * s];
     pgrp[(size_t(q) * nb + s) * 2 + 1] = grp[2 * s + 1];
     for (int i = 0; i < nb; ++i) u[(size_t(q) * nb + i) * nb + s] = V[i * NB + s];
+  }
+}
+
+constexpr int kDecompWarps = 4;   // points (one warp each) per block of the warp form
+// Launches of fewer points take the warp form: one thread per matrix leaves most SMs idle and
+// each busy one waiting on a single thread's dependency chain (the time of a launch is that
+// chain, ~0.8 ms, whatever its size), while the warp form keeps ~16 of 32 lanes of each FP64
+// instruction busy and so costs about twice the FP64 work (~0.13 us per point on the FP64 pipe).
+constexpr int64_t kWarpDecompMax = 4096;
+
+// One warp per listed k point (launches of few points): eigen-decomposition of H(k) (read from the interpolation) by
+// the warp-cooperative Jacobi, velocities <m| grad H |m> averaged over degenerate groups, the
+// window masks.
+template <int NB>
+__global__ void __launch_bounds__(32 * kDecompWarps) k_electron_bands_warp(ModelDev M, Mesh km, const int *__restrict__ list,
+                                                                      int64_t n, const double2 *__restrict__ HdH,
+                                                                      int64_t ldn, double degen_tol, double lo,
+                                                                      double hi, double *eps, double2 *cvec,
+                                                                      double *vel, uint8_t *egrp, uint32_t *amask,
+                                                                      uint32_t *rmask) {
+  __shared__ JacobiWarpSmem<NB> sm[kDecompWarps];
+  __shared__ double vds[kDecompWarps][NB * 3];
+  __shared__ uint8_t grps[kDecompWarps][2 * NB];
+  const int wq = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t t = int64_t(blockIdx.x) * kDecompWarps + wq;
+  if (t >= n) return;   // the whole warp
+  JacobiWarpSmem<NB> &S = sm[wq];
+  const int k = list[t];
+  const int nb = M.nb, ne = nb * nb;
+  for (int x = lane; x < ne; x += 32) S.A[(x / nb) * NB + x % nb] = HdH[size_t(x) * ldn + t];
+  __syncwarp();
+  herm_jacobi_warp<NB>(S, nb);
+  // v_m = <m| grad H |m>: for component a and row i, w = sum_j dH_ij V_jm, v += Re(conj(V_im) w)
+  for (int x = lane; x < nb * 3; x += 32) {
+    const int m = x / 3, a = x % 3, col = S.perm[m];
+    double acc = 0.0;
+    for (int i = 0; i < nb; ++i) {
+      double2 w = cmk(0.0, 0.0);
+      for (int j = 0; j < nb; ++j) cfma(w, HdH[size_t((1 + a) * ne + i * nb + j) * ldn + t], S.V[j * NB + col]);
+      const double2 vi = S.V[i * NB + col];
+      acc += vi.x * w.x + vi.y * w.y;
+    }
+    vds[wq][x] = acc;
+  }
+  if (lane == 0) degenerate_groups(S.e, nb, degen_tol, grps[wq]);
+  __syncwarp();
+  const uint8_t *grp = grps[wq];
+  const double conv = kAngstrom / kHbarEVs;
+  for (int x = lane; x < nb * 3; x += 32) {
+    const int m = x / 3, a = x % 3, g0 = grp[2 * m], g1 = grp[2 * m + 1];
+    double s = 0.0;
+    for (int j = g0; j < g1; ++j) s += vds[wq][j * 3 + a];
+    vel[(size_t(k) * nb + m) * 3 + a] = s / double(g1 - g0) * conv;
+  }
+  for (int m = lane; m < nb; m += 32) {
+    eps[size_t(k) * nb + m] = S.e[m];
+    egrp[(size_t(k) * nb + m) * 2] = grp[2 * m];
+    egrp[(size_t(k) * nb + m) * 2 + 1] = grp[2 * m + 1];
+  }
+  for (int x = lane; x < ne; x += 32) {
+    const int i = x / nb, m = x % nb;
+    cvec[(size_t(k) * nb + i) * nb + m] = S.V[i * NB + S.perm[m]];
+  }
+  if (lane == 0) {
+    uint32_t mask = 0;
+    for (int m = 0; m < nb; ++m)
+      if (S.e[m] >= lo && S.e[m] <= hi) mask |= 1u << m;
+    amask[k] = mask;
+    // the degenerate subspaces of the active bands, whole ([A9]: a subspace cut by a window
+    // edge still averages |g|^2 over all its bands)
+    uint32_t rot = 0;
+    for (int m = 0; m < nb; ++m)
+      if ((mask >> m) & 1u)
+        for (int a = grp[2 * m]; a < grp[2 * m + 1]; ++a) rot |= 1u << a;
+    rmask[k] = rot;
+  }
+}
+
+// One warp per listed q point: eigen-decomposition of D(q) (read from the interpolation),
+// hbar w = sqrt(max(lambda, 0)), velocities.
+template <int NB>
+__global__ void __launch_bounds__(32 * kDecompWarps) k_phonon_modes_warp(ModelDev M, Mesh qm, const int *__restrict__ list,
+                                                                    int64_t n, const double2 *__restrict__ DdD,
+                                                                    int64_t ldn, double degen_tol, double omega_min,
+                                                                    double *w, double2 *u, double *vph,
+                                                                    uint8_t *pgrp) {
+  __shared__ JacobiWarpSmem<NB> sm[kDecompWarps];
+  __shared__ double vds[kDecompWarps][NB * 3];
+  __shared__ double oms[kDecompWarps][NB];
+  __shared__ uint8_t grps[kDecompWarps][2 * NB];
+  const int wq = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t t = int64_t(blockIdx.x) * kDecompWarps + wq;
+  if (t >= n) return;   // the whole warp
+  JacobiWarpSmem<NB> &S = sm[wq];
+  const int q = list[t];
+  const int nb = M.nbr, ne = nb * nb;
+  for (int x = lane; x < ne; x += 32) S.A[(x / nb) * NB + x % nb] = DdD[size_t(x) * ldn + t];
+  __syncwarp();
+  herm_jacobi_warp<NB>(S, nb);
+  for (int s = lane; s < nb; s += 32) oms[wq][s] = sqrt(fmax(S.e[s], 0.0));
+  for (int x = lane; x < nb * 3; x += 32) {
+    const int s = x / 3, a = x % 3, col = S.perm[s];
+    double acc = 0.0;
+    for (int i = 0; i < nb; ++i) {
+      double2 ws = cmk(0.0, 0.0);
+      for (int j = 0; j < nb; ++j) cfma(ws, DdD[size_t((1 + a) * ne + i * nb + j) * ldn + t], S.V[j * NB + col]);
+      const double2 vi = S.V[i * NB + col];
+      acc += vi.x * ws.x + vi.y * ws.y;
+    }
+    vds[wq][x] = acc;
+  }
+  __syncwarp();
+  if (lane == 0) degenerate_groups(oms[wq], nb, degen_tol, grps[wq]);
+  __syncwarp();
+  const uint8_t *grp = grps[wq];
+  const double conv = kAngstrom / kHbarEVs;
+  for (int x = lane; x < nb * 3; x += 32) {
+    const int s = x / 3, a = x % 3, g0 = grp[2 * s], g1 = grp[2 * s + 1];
+    const double om = oms[wq][s];
+    double v = 0.0;
+    if (om > omega_min) {
+      double acc = 0.0;
+      for (int j = g0; j < g1; ++j) acc += vds[wq][j * 3 + a];
+      v = acc / double(g1 - g0) / (2.0 * om) * conv;
+    }
+    vph[(size_t(q) * nb + s) * 3 + a] = v;
+  }
+  for (int s = lane; s < nb; s += 32) {
+    w[size_t(q) * nb + s] = oms[wq][s];
+    pgrp[(size_t(q) * nb + s) * 2] = grp[2 * s];
+    pgrp[(size_t(q) * nb + s) * 2 + 1] = grp[2 * s + 1];
+  }
+  for (int x = lane; x < ne; x += 32) {
+    const int i = x / nb, s = x % nb;
+    u[(size_t(q) * nb + i) * nb + s] = S.V[i * NB + S.perm[s]];
   }
 }
 
@@ -494,18 +631,29 @@ cudaError_t launch_electron_bands(const ModelDev &M, Mesh km, const int *list, i
     const int64_t nc = n - c0 < interp_chunk() ? n - c0 : interp_chunk();
     cudaError_t e = fourier_interp(M, km, ktab, list + c0, nc, nc, M.Re, M.nRe, M.H_R, ne, scratch, st);
     if (e != cudaSuccess) return e;
-    // two warps per block: the decomposition is FP64-bound per thread, so the warps are spread
-    // over every SM instead of filling a few
-    const int grid = int((nc + 63) / 64), bs = 64;
-    if (M.nb <= 1)
-      EPHB_LAUNCH(k_electron_bands<1>, grid, bs, 0, st, M, km, list + c0, nc, scratch, nc, degen_tol, lo, hi, eps, cvec,
-                  vel, egrp, amask, rmask);
-    else if (M.nb <= 4)
-      EPHB_LAUNCH(k_electron_bands<4>, grid, bs, 0, st, M, km, list + c0, nc, scratch, nc, degen_tol, lo, hi, eps, cvec,
-                  vel, egrp, amask, rmask);
-    else
-      EPHB_LAUNCH(k_electron_bands<8>, grid, bs, 0, st, M, km, list + c0, nc, scratch, nc, degen_tol, lo, hi, eps, cvec,
-                  vel, egrp, amask, rmask);
+    if (nc >= kWarpDecompMax) {   // one thread per point, two warps per block
+      const int grid = int((nc + 63) / 64), bs = 64;
+      if (M.nb <= 1)
+        EPHB_LAUNCH(k_electron_bands<1>, grid, bs, 0, st, M, km, list + c0, nc, scratch, nc, degen_tol, lo, hi, eps,
+                    cvec, vel, egrp, amask, rmask);
+      else if (M.nb <= 4)
+        EPHB_LAUNCH(k_electron_bands<4>, grid, bs, 0, st, M, km, list + c0, nc, scratch, nc, degen_tol, lo, hi, eps,
+                    cvec, vel, egrp, amask, rmask);
+      else
+        EPHB_LAUNCH(k_electron_bands<8>, grid, bs, 0, st, M, km, list + c0, nc, scratch, nc, degen_tol, lo, hi, eps,
+                    cvec, vel, egrp, amask, rmask);
+    } else {   // one warp per point, four points per block
+      const int grid = int((nc + kDecompWarps - 1) / kDecompWarps), bs = 32 * kDecompWarps;
+      if (M.nb <= 1)
+        EPHB_LAUNCH(k_electron_bands_warp<1>, grid, bs, 0, st, M, km, list + c0, nc, scratch, nc, degen_tol, lo, hi,
+                    eps, cvec, vel, egrp, amask, rmask);
+      else if (M.nb <= 4)
+        EPHB_LAUNCH(k_electron_bands_warp<4>, grid, bs, 0, st, M, km, list + c0, nc, scratch, nc, degen_tol, lo, hi,
+                    eps, cvec, vel, egrp, amask, rmask);
+      else
+        EPHB_LAUNCH(k_electron_bands_warp<8>, grid, bs, 0, st, M, km, list + c0, nc, scratch, nc, degen_tol, lo, hi,
+                    eps, cvec, vel, egrp, amask, rmask);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -537,16 +685,29 @@ cudaError_t launch_phonon_modes(const ModelDev &M, Mesh qm, const int *list, int
     const int64_t nc = n - c0 < interp_chunk() ? n - c0 : interp_chunk();
     cudaError_t e = fourier_interp(M, qm, qtab, list + c0, nc, nc, M.Rd, M.nRd, M.D_R, ne, scratch, st);
     if (e != cudaSuccess) return e;
-    const int grid = int((nc + 63) / 64), bs = 64;
-    if (M.nbr <= 3)
-      EPHB_LAUNCH(k_phonon_modes<3>, grid, bs, 0, st, M, qm, list + c0, nc, scratch, nc, degen_tol, omega_min, w, u, vph,
-                  pgrp);
-    else if (M.nbr <= 6)
-      EPHB_LAUNCH(k_phonon_modes<6>, grid, bs, 0, st, M, qm, list + c0, nc, scratch, nc, degen_tol, omega_min, w, u, vph,
-                  pgrp);
-    else
-      EPHB_LAUNCH(k_phonon_modes<12>, grid, bs, 0, st, M, qm, list + c0, nc, scratch, nc, degen_tol, omega_min, w, u,
-                  vph, pgrp);
+    if (nc >= kWarpDecompMax) {   // one thread per point
+      const int grid = int((nc + 63) / 64), bs = 64;
+      if (M.nbr <= 3)
+        EPHB_LAUNCH(k_phonon_modes<3>, grid, bs, 0, st, M, qm, list + c0, nc, scratch, nc, degen_tol, omega_min, w, u,
+                    vph, pgrp);
+      else if (M.nbr <= 6)
+        EPHB_LAUNCH(k_phonon_modes<6>, grid, bs, 0, st, M, qm, list + c0, nc, scratch, nc, degen_tol, omega_min, w, u,
+                    vph, pgrp);
+      else
+        EPHB_LAUNCH(k_phonon_modes<12>, grid, bs, 0, st, M, qm, list + c0, nc, scratch, nc, degen_tol, omega_min, w, u,
+                    vph, pgrp);
+    } else {   // one warp per point
+      const int grid = int((nc + kDecompWarps - 1) / kDecompWarps), bs = 32 * kDecompWarps;
+      if (M.nbr <= 3)
+        EPHB_LAUNCH(k_phonon_modes_warp<3>, grid, bs, 0, st, M, qm, list + c0, nc, scratch, nc, degen_tol, omega_min,
+                    w, u, vph, pgrp);
+      else if (M.nbr <= 6)
+        EPHB_LAUNCH(k_phonon_modes_warp<6>, grid, bs, 0, st, M, qm, list + c0, nc, scratch, nc, degen_tol, omega_min,
+                    w, u, vph, pgrp);
+      else
+        EPHB_LAUNCH(k_phonon_modes_warp<12>, grid, bs, 0, st, M, qm, list + c0, nc, scratch, nc, degen_tol, omega_min,
+                    w, u, vph, pgrp);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -17,9 +17,8 @@
 // products with i + l <= 8, accumulators (i+l = 2), (3), (4), (5) -- each summed exactly --
 // and (i+l >= 6), which rounds at 2^-24 of a sum below 2^-30 of the column scale.  (With
 // the fourth diagonal in the tail, its rounding, ~2^-42 of the column scale, reached 1.2e-10
-// relative on the smallest rates; with the third there too, 1e-8.)  Mixed mode: 3 slices, the
-// 6 products with i + l <= 4, accumulators (i+l = 2) (exact) and (i+l >= 3); for contraction
-// lengths above 256, 4 slices and the 10 products with i + l <= 5 in the same two accumulators.
+// relative on the smallest rates; with the third there too, 1e-8.)  Mixed mode: 4 slices, the
+// 10 products with i + l <= 5, accumulators (i+l = 2) (exact) and (i+l >= 3).
 // Wide-K FP64-grade mode (contraction lengths 256 < K <= 816, e.g. 7^3 R grids): 8 slices of
 // balanced base-128 digits (|n_i| <= 64, s_i = n_i 2^(-6-7(i-1)), the same 2^-55 input
 // resolution), the 36 products with i + l <= 9, accumulators (i+l = 2) .. (6) -- a diagonal of
@@ -1210,10 +1209,11 @@ int tc_nmax(const ModelDev &M) { return round_up(2 * M.nb * M.nb * M.nbr, 16); }
 // shared memory.  Two CTAs per SM: K blocks of 16 in two stages.
 int tc_nc_max(int ns) { return ns == 8 ? 64 : (ns == 7 ? 96 : 256); }
 static int nacc_of(int ns) { return ns == 8 ? 6 : (ns == 7 ? 5 : 2); }
-// Mixed mode: 3 slices (24-bit inputs) up to K = 256; longer contractions sum more rounded
-// terms and take a fourth slice (32-bit inputs, 10 products, the same two accumulators).
+// Mixed mode: 4 slices (32-bit inputs, 10 products, two accumulators).  With 3 slices (24-bit
+// inputs, 6 products) the Seebeck tensor of a 4-band case already missed the 1e-6 coefficient
+// bound (1.06e-6), as did a contraction of length 686.
 int tc_slices_for(int kp, bool fp64_grade) {
-  if (!fp64_grade) return kp <= 256 ? 3 : (kp <= 1024 ? 4 : 0);
+  if (!fp64_grade) return kp <= 1024 ? 4 : 0;
   return kp <= 256 ? 7 : (kp <= 816 ? 8 : 0);
 }
 static bool two_ctas(int kc, int st) { return kc == 16 && st == 2; }
@@ -1408,11 +1408,7 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
   };
   if (warp_specialised(kc, stages))
     e = ns == 8 ? go_ws(k_vertex_gemm_ws<8, 6, 5>)
-                : (ns == 7 ? go_ws(k_vertex_gemm_ws<7, 5, 5>)
-                           : (ns == 4 ? go_ws(k_vertex_gemm_ws<4, 2, 5>) : go_ws(k_vertex_gemm_ws<3, 2, 5>)));
-  else if (ns == 4)
-    e = kc == 32 ? go(k_vertex_gemm<4, 2, 32, 2>)
-                 : (stages == 4 ? go(k_vertex_gemm<4, 2, 16, 4>) : go(k_vertex_gemm<4, 2, 16, 2>));
+                : (ns == 7 ? go_ws(k_vertex_gemm_ws<7, 5, 5>) : go_ws(k_vertex_gemm_ws<4, 2, 5>));
   else if (ns == 8)
     e = kc == 32 ? go(k_vertex_gemm<8, 6, 32, 2>)
                  : (stages == 4 ? go(k_vertex_gemm<8, 6, 16, 4>) : go(k_vertex_gemm<8, 6, 16, 2>));
@@ -1420,8 +1416,8 @@ cudaError_t launch_vertex_tc(const ModelDev &M, const MeshDev &D, int ns, int64_
     e = kc == 32 ? go(k_vertex_gemm<7, 5, 32, 2>)
                  : (stages == 4 ? go(k_vertex_gemm<7, 5, 16, 4>) : go(k_vertex_gemm<7, 5, 16, 2>));
   else
-    e = kc == 32 ? go(k_vertex_gemm<3, 2, 32, 2>)
-                 : (stages == 4 ? go(k_vertex_gemm<3, 2, 16, 4>) : go(k_vertex_gemm<3, 2, 16, 2>));
+    e = kc == 32 ? go(k_vertex_gemm<4, 2, 32, 2>)
+                 : (stages == 4 ? go(k_vertex_gemm<4, 2, 16, 4>) : go(k_vertex_gemm<4, 2, 16, 2>));
   if (e != cudaSuccess) return e;
   e = cudaGetLastError();
   if (e == cudaSuccess && gemm1) e = cudaEventRecord(gemm1, st);

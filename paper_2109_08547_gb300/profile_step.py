@@ -24,6 +24,8 @@ def main(argv=None):
     p.add_argument("--solve", default="mixed", choices=["fp64", "mixed"])
     p.add_argument("--delta", default="gauss", choices=["gauss", "tetra"])
     p.add_argument("--warm", type=int, default=2)
+    p.add_argument("--device-loop", type=int, default=1, choices=[0, 1],
+                   help="1: the solve as one graph launch with device-driven loops (the bench default)")
     p.add_argument("--out", default=".", help="directory of step_window.txt")
     a = p.parse_args(argv)
     wl = S.workload_cscl8(a.nk, a.nq)
@@ -37,7 +39,8 @@ def main(argv=None):
                                            delta=wl.delta)
             print(json.dumps({"rates_ms": r["ms"], "stage_a_ms": r["ms_stage_a"], "pairs": r["n_pairs"]}))
             return
-        kw = dict(level="dragged", precision=prec, solve_precision=a.solve, accel=0, tol=1e-8)
+        kw = dict(level="dragged", precision=prec, solve_precision=a.solve, accel=0, tol=1e-8,
+                  device_loop=bool(a.device_loop))
         for _ in range(a.warm):
             B.run_path(ctx, wl, **kw)
         l0 = B.kernel_launches()
