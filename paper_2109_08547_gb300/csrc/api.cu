@@ -99,6 +99,11 @@ struct InstState {
   DBuf<int64_t> eseg_ptr, eseg_begin, rseg_ptr, rseg_begin, run_ptr, run_idx;
   DBuf<uint32_t> run_col;
   int64_t neseg = 0, nrseg = 0, nruns = 0;
+  // segments of the phonon entry stream (phonon drag scatter) and their partial sums
+  DBuf<int> pnseg_row, pseg_row;
+  DBuf<int64_t> pseg_ptr, pseg_begin;
+  DBuf<double> pseg_part;
+  int64_t npseg = 0;
   DBuf<uint32_t> kcrd;
   DBuf<int2> kinfo;
   DBuf<int> sctl;               // device-driven sweep loop: stop flag, sweeps done, converged
@@ -136,6 +141,7 @@ struct InstState {
     IJ2.release();
     X32.release(); Y32.release(); IJ32.release(); FG32.release();
     Xff.release(); Yff.release(); IJff.release(); FGff.release();
+    pnseg_row.release(); pseg_row.release(); pseg_ptr.release(); pseg_begin.release(); pseg_part.release();
     have_f32 = false;
     lists_pending = true;
   }
@@ -158,6 +164,7 @@ struct InstState {
     Afold.release();
     X32.release(); Y32.release(); IJ32.release(); FG32.release();
     Xff.release(); Yff.release(); IJff.release(); FGff.release();
+    pnseg_row.release(); pseg_row.release(); pseg_ptr.release(); pseg_begin.release(); pseg_part.release();
     bte_ready = has_warm = solved = have_f32 = lists_pending = false;
   }
 };
@@ -1256,6 +1263,15 @@ ephb_status bte_setup(ephb_ctx *ctx) {
   CK(ctx->rseg_row.ensure(ctx->nrseg));
   CK(ctx->rseg_begin.ensure(ctx->nrseg));
   CK(launch_fill_segments(nst, ctx->run_ptr.p, ctx->rseg_ptr.p, ctx->rseg_row.p, ctx->rseg_begin.p, st));
+  CK(ctx->pnseg_row.ensure(nph));
+  CK(ctx->pseg_ptr.ensure(nph + 1));
+  CK(ctx->scratch.ensure(scan_scratch_elems(nph)));
+  CK(launch_build_segments(nph, ctx->ph_row_ptr.p, ctx->pnseg_row.p, ctx->pseg_ptr.p, ctx->scratch.p,
+                           ctx->scratch.n, ctx->npseg, st));
+  CK(ctx->pseg_row.ensure(ctx->npseg));
+  CK(ctx->pseg_begin.ensure(ctx->npseg));
+  CK(launch_fill_segments(nph, ctx->ph_row_ptr.p, ctx->pseg_ptr.p, ctx->pseg_row.p, ctx->pseg_begin.p, st));
+  CK(ctx->pseg_part.ensure(size_t(ctx->npseg) * 6));
   CK(ctx->seg_part.ensure(size_t(ctx->neseg > ctx->nrseg ? ctx->neseg : ctx->nrseg) * 6));
   CK(ctx->Dterm.ensure(nst * 6));
   CK(cudaMemsetAsync(ctx->Dterm.p, 0, nst * 6 * sizeof(double), st));
@@ -1283,6 +1299,17 @@ SweepSegs run_segs(ephb_ctx *c) {
   S.seg_begin = c->rseg_begin.p;
   S.seg_ptr = c->rseg_ptr.p;
   S.row_ptr = c->run_ptr.p;
+  return S;
+}
+
+SweepSegs ph_segs(ephb_ctx *c) {
+  SweepSegs S;
+  std::memset(&S, 0, sizeof(S));
+  S.nseg = c->npseg;
+  S.seg_row = c->pseg_row.p;
+  S.seg_begin = c->pseg_begin.p;
+  S.seg_ptr = c->pseg_ptr.p;
+  S.row_ptr = c->ph_row_ptr.p;
   return S;
 }
 
@@ -1638,12 +1665,14 @@ ephb_status solve_one(ephb_ctx *ctx, const ephb_solve_opts *o, ephb_solve_info *
       CK(tp.start(st));
       if (ph32) {
         CK(launch_pack6_f32(nst, ctx->I.p, ctx->J.p, ctx->IJ32.p, st));
-        CK(launch_ph_sweep32(M, B, ctx->kinfo.p, ctx->Y32.p, ctx->IJ32.p, ctx->Btv.p, ctx->n_ph_entries, st));
+        CK(launch_ph_sweep32(M, B, ph_segs(ctx), ctx->kinfo.p, ctx->Y32.p, ctx->IJ32.p, ctx->pseg_part.p, ctx->Btv.p,
+                             st));
       } else if (ph32_allowed) {
         CK(launch_pack6_ff(nst, ctx->I.p, ctx->J.p, ctx->IJff.p, st));
-        CK(launch_ph_sweepff(M, B, ctx->kinfo.p, ctx->Yff.p, ctx->IJff.p, ctx->Btv.p, ctx->n_ph_entries, st));
+        CK(launch_ph_sweepff(M, B, ph_segs(ctx), ctx->kinfo.p, ctx->Yff.p, ctx->IJff.p, ctx->pseg_part.p, ctx->Btv.p,
+                             st));
       } else {
-        CK(launch_ph_sweep(M, D, B, ctx->kinfo.p, ctx->I.p, ctx->J.p, ctx->Btv.p, ctx->n_ph_entries, st));
+        CK(launch_ph_sweep(M, B, ph_segs(ctx), ctx->kinfo.p, ctx->I.p, ctx->J.p, ctx->pseg_part.p, ctx->Btv.p, st));
       }
       CK(tp.stop(st));
       if (and_m > 0 && outer >= 2) {   // the update goes to the ring, the mix to (F, G)
@@ -1760,6 +1789,9 @@ ephb_status graph_prepare(ephb_ctx *ctx, const GraphOpts &go, int slot, GraphIns
   std::memcpy(&g.B, &B, sizeof(B));
   std::memcpy(&g.Sr, &Sr, sizeof(Sr));
   std::memcpy(&g.Se, &Se, sizeof(Se));
+  const SweepSegs Sp = ph_segs(ctx);
+  std::memcpy(&g.Sp, &Sp, sizeof(Sp));
+  g.ph_part = ctx->pseg_part.p;
   g.nst = nst;
   g.nph = nph;
   g.n_entries = ctx->n_entries;

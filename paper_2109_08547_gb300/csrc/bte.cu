@@ -417,23 +417,30 @@ __global__ void k_drag_finalize(int64_t nst, SweepSegs S, const double *part, do
   for (int c = 0; c < 6; ++c) Dterm[st * 6 + c] = s[c];
 }
 
-// One warp per phonon row (q,s): Btv = sum Y/|stab| (S_k' I_<k'>n - I_km), fields I and J.
-// Float-float form of the phonon drag scatter (mixed iteration once the outer residual is
-// small), from float-float copies of Y and of the responses (IJff: [state][I0 I1 I2 J0 J1 J2]).
-template <bool SYM, int LANES>
-__global__ void __launch_bounds__(256) k_ph_sweepff(ModelDev M, BteDev B, const int2 *__restrict__ kinfo,
+// The phonon drag scatter Btv(q,s) = sum Y/|stab| (S_k' I_<k'>n - I_km), fields I and J, over
+// the entries of each phonon row.  Rows are cut into segments of at most kSeg entries, one warp
+// per segment (lanes strided over its entries, a fixed-order warp sum into part[seg][6]); the
+// rows of a fine q mesh are very uneven (those near q = 0 and at the inter-valley q gather
+// every irreducible window k, most hold none), which one thread per row turned into a few long
+// serial chains of gathers.  k_ph_seg_finalize adds each row's segments in order.
+// Float-float form (mixed iteration once the outer residual is small), from float-float
+// copies of Y and of the responses (IJff: [state][I0 I1 I2 J0 J1 J2]).
+template <bool SYM>
+__global__ void __launch_bounds__(256) k_ph_sweepff(ModelDev M, BteDev B, SweepSegs S, const int2 *__restrict__ kinfo,
                                                     const float2 *__restrict__ Yff,
-                                                    const float2 *__restrict__ IJff, double *Btv) {
+                                                    const float2 *__restrict__ IJff, double *part) {
   __shared__ float2 C[kMaxSym * 9];
   if (SYM) {
     for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) C[t] = ff_from_double(M.sym_cart[t]);
     __syncthreads();
   }
-  const int64_t row = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) / LANES;
-  const int lane = LANES == 1 ? 0 : (threadIdx.x & 31);
-  if (row >= B.nq * B.nbr) return;
+  const int64_t g = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= S.nseg) return;
+  const int64_t b = S.seg_begin[g], rend = S.row_ptr[S.seg_row[g] + 1];
+  const int64_t e_end = b + kSeg < rend ? b + kSeg : rend;
   FFAcc a[6];
-  for (int64_t e = B.ph_row_ptr[row] + lane; e < B.ph_row_ptr[row + 1]; e += LANES) {
+  for (int64_t e = b + lane; e < e_end; e += 32) {
     const int st = B.ph_st[e];
     const uint32_t pk = B.ph_kpn[e];
     const float2 y = Yff[e];
@@ -458,9 +465,19 @@ __global__ void __launch_bounds__(256) k_ph_sweepff(ModelDev M, BteDev B, const 
     for (int c = 0; c < 6; ++c) ff_acc_mul(a[c], y, ff_sub(r[c], own[c]));
   }
   for (int c = 0; c < 6; ++c) {
-    const double v = LANES == 32 ? warp_sum(ff_to_double(a[c])) : ff_to_double(a[c]);
-    if (lane == 0) Btv[row * 6 + c] = v;
+    const double v = warp_sum(ff_to_double(a[c]));
+    if (lane == 0) part[g * 6 + c] = v;
   }
+}
+
+// Btv[row] = the sum of the row's segment partials, in order (zero for rows without entries)
+__global__ void k_ph_seg_finalize(int64_t nrow, SweepSegs S, const double *__restrict__ part, double *Btv) {
+  const int64_t row = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (row >= nrow) return;
+  double sum[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t g = S.seg_ptr[row]; g < S.seg_ptr[row + 1]; ++g)
+    for (int c = 0; c < 6; ++c) sum[c] += part[g * 6 + c];
+  for (int c = 0; c < 6; ++c) Btv[row * 6 + c] = sum[c];
 }
 
 // float-float copies: out[i] = ff(a[i]) (n values); pack: out[i][0..2] = ff(A[i][..]),
@@ -481,20 +498,24 @@ __global__ void k_pack6_ff(int64_t n, const double *A, const double *Bv, float2 
 
 // FP32 form of the phonon drag scatter (mixed iteration while the outer residual is large),
 // from FP32 copies of Y and of the responses (IJ32: [state][I0 I1 I2 J0 J1 J2]).
-template <bool SYM, int LANES>
-__global__ void __launch_bounds__(256) k_ph_sweep32(ModelDev M, BteDev B, const int2 *__restrict__ kinfo,
+// FP32 form of the phonon drag scatter (early outer iterations of the mixed iteration), the
+// segments as in k_ph_sweepff; lane sums in FP32, the warp sum in FP32, partials stored FP64.
+template <bool SYM>
+__global__ void __launch_bounds__(256) k_ph_sweep32(ModelDev M, BteDev B, SweepSegs S, const int2 *__restrict__ kinfo,
                                                     const float *__restrict__ Y32, const float *__restrict__ IJ32,
-                                                    double *Btv) {
+                                                    double *part) {
   __shared__ float C[kMaxSym * 9];
   if (SYM) {
     for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) C[t] = float(M.sym_cart[t]);
     __syncthreads();
   }
-  const int64_t row = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) / LANES;
-  const int lane = LANES == 1 ? 0 : (threadIdx.x & 31);
-  if (row >= B.nq * B.nbr) return;
+  const int64_t g = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= S.nseg) return;
+  const int64_t b = S.seg_begin[g], rend = S.row_ptr[S.seg_row[g] + 1];
+  const int64_t e_end = b + kSeg < rend ? b + kSeg : rend;
   float a[6] = {0, 0, 0, 0, 0, 0};
-  for (int64_t e = B.ph_row_ptr[row] + lane; e < B.ph_row_ptr[row + 1]; e += LANES) {
+  for (int64_t e = b + lane; e < e_end; e += 32) {
     const int st = B.ph_st[e];
     const uint32_t pk = B.ph_kpn[e];
     const float y = Y32[e];
@@ -514,11 +535,10 @@ __global__ void __launch_bounds__(256) k_ph_sweep32(ModelDev M, BteDev B, const 
     }
     for (int c = 0; c < 6; ++c) a[c] = fmaf(y, r[c] - own[c], a[c]);
   }
-  if (LANES == 32)
-    for (int c = 0; c < 6; ++c)
-      for (int o = 16; o > 0; o >>= 1) a[c] += __shfl_down_sync(0xffffffffu, a[c], o);
+  for (int c = 0; c < 6; ++c)
+    for (int o = 16; o > 0; o >>= 1) a[c] += __shfl_down_sync(0xffffffffu, a[c], o);
   if (lane == 0)
-    for (int c = 0; c < 6; ++c) Btv[row * 6 + c] = double(a[c]);
+    for (int c = 0; c < 6; ++c) part[g * 6 + c] = double(a[c]);
 }
 
 // FP32 copies: out[i][0..2] = A[i][0..2], out[i][3..5] = B[i][0..2]; and plain element copies
@@ -536,22 +556,23 @@ __global__ void k_copy_f32(int64_t n, const double *a, float *b) {
   if (i < n) b[i] = float(a[i]);
 }
 
-// LANES threads per phonon row: 32 (a warp) for long rows, 1 when rows hold a few entries (fine
-// meshes with symmetry leave most rows short or empty)
-template <bool SYM, int LANES>
-__global__ void __launch_bounds__(256) k_ph_sweep(ModelDev M, MeshDev D, BteDev B, const int2 *__restrict__ kinfo,
+// FP64 form of the phonon drag scatter, the segments as in k_ph_sweepff.
+template <bool SYM>
+__global__ void __launch_bounds__(256) k_ph_sweep(ModelDev M, BteDev B, SweepSegs S, const int2 *__restrict__ kinfo,
                                                   const double *__restrict__ I, const double *__restrict__ J,
-                                                  double *Btv) {
+                                                  double *part) {
   __shared__ double C[kMaxSym * 9];
   if (SYM) {
     for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) C[t] = M.sym_cart[t];
     __syncthreads();
   }
-  int64_t row = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) / LANES;
-  int lane = LANES == 1 ? 0 : (threadIdx.x & 31);
-  if (row >= B.nq * B.nbr) return;
+  const int64_t g = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= S.nseg) return;
+  const int64_t b = S.seg_begin[g], rend = S.row_ptr[S.seg_row[g] + 1];
+  const int64_t e_end = b + kSeg < rend ? b + kSeg : rend;
   double aI[3] = {0, 0, 0}, aJ[3] = {0, 0, 0};
-  for (int64_t e = B.ph_row_ptr[row] + lane; e < B.ph_row_ptr[row + 1]; e += LANES) {
+  for (int64_t e = b + lane; e < e_end; e += 32) {
     int st = B.ph_st[e];
     uint32_t pk = B.ph_kpn[e];
     double y = B.ph_Y[e];
@@ -575,15 +596,14 @@ __global__ void __launch_bounds__(256) k_ph_sweep(ModelDev M, MeshDev D, BteDev 
     }
     for (int a = 0; a < 3; ++a) aJ[a] += y * (r[a] - J[int64_t(st) * 3 + a]);
   }
-  if (LANES == 32)
-    for (int a = 0; a < 3; ++a) {
-      aI[a] = warp_sum(aI[a]);
-      aJ[a] = warp_sum(aJ[a]);
-    }
+  for (int a = 0; a < 3; ++a) {
+    aI[a] = warp_sum(aI[a]);
+    aJ[a] = warp_sum(aJ[a]);
+  }
   if (lane == 0)
     for (int a = 0; a < 3; ++a) {
-      Btv[row * 6 + a] = aI[a];
-      Btv[row * 6 + 3 + a] = aJ[a];
+      part[g * 6 + a] = aI[a];
+      part[g * 6 + 3 + a] = aJ[a];
     }
 }
 
@@ -1302,17 +1322,17 @@ cudaError_t launch_drag_termff(const MeshDev &D, const BteDev &B, const SweepSeg
   return cudaGetLastError();
 }
 
-cudaError_t launch_ph_sweepff(const ModelDev &M, const BteDev &B, const int2 *kinfo, const float2 *Yff,
-                              const float2 *IJff, double *Btv, int64_t n_ph_entries, cudaStream_t st) {
-  // rows of a few entries: one thread per row; longer rows: one warp
-  const bool wide = B.nq * B.nbr > 0 && n_ph_entries / (B.nq * B.nbr) >= 4;
-  const unsigned g = unsigned((B.nq * B.nbr * (wide ? 32 : 1) + 255) / 256);
-  if (M.nsym > 1)
-    wide ? EPHB_LAUNCH((k_ph_sweepff<true, 32>), g, 256, 0, st, M, B, kinfo, Yff, IJff, Btv)
-         : EPHB_LAUNCH((k_ph_sweepff<true, 1>), g, 256, 0, st, M, B, kinfo, Yff, IJff, Btv);
-  else
-    wide ? EPHB_LAUNCH((k_ph_sweepff<false, 32>), g, 256, 0, st, M, B, kinfo, Yff, IJff, Btv)
-         : EPHB_LAUNCH((k_ph_sweepff<false, 1>), g, 256, 0, st, M, B, kinfo, Yff, IJff, Btv);
+cudaError_t launch_ph_sweepff(const ModelDev &M, const BteDev &B, const SweepSegs &S, const int2 *kinfo,
+                              const float2 *Yff, const float2 *IJff, double *part, double *Btv, cudaStream_t st) {
+  const int64_t nrow = B.nq * B.nbr;
+  if (S.nseg > 0) {
+    const unsigned g = unsigned((S.nseg * 32 + 255) / 256);
+    if (M.nsym > 1)
+      EPHB_LAUNCH(k_ph_sweepff<true>, g, 256, 0, st, M, B, S, kinfo, Yff, IJff, part);
+    else
+      EPHB_LAUNCH(k_ph_sweepff<false>, g, 256, 0, st, M, B, S, kinfo, Yff, IJff, part);
+  }
+  if (nrow > 0) EPHB_LAUNCH(k_ph_seg_finalize, unsigned((nrow + 255) / 256), 256, 0, st, nrow, S, part, Btv);
   return cudaGetLastError();
 }
 
@@ -1337,17 +1357,17 @@ cudaError_t launch_drag_term32(const MeshDev &D, const BteDev &B, const SweepSeg
   return cudaGetLastError();
 }
 
-cudaError_t launch_ph_sweep32(const ModelDev &M, const BteDev &B, const int2 *kinfo, const float *Y32,
-                              const float *IJ32, double *Btv, int64_t n_ph_entries, cudaStream_t st) {
-  // rows of a few entries: one thread per row; longer rows: one warp
-  const bool wide = B.nq * B.nbr > 0 && n_ph_entries / (B.nq * B.nbr) >= 4;
-  const unsigned g = unsigned((B.nq * B.nbr * (wide ? 32 : 1) + 255) / 256);
-  if (M.nsym > 1)
-    wide ? EPHB_LAUNCH((k_ph_sweep32<true, 32>), g, 256, 0, st, M, B, kinfo, Y32, IJ32, Btv)
-         : EPHB_LAUNCH((k_ph_sweep32<true, 1>), g, 256, 0, st, M, B, kinfo, Y32, IJ32, Btv);
-  else
-    wide ? EPHB_LAUNCH((k_ph_sweep32<false, 32>), g, 256, 0, st, M, B, kinfo, Y32, IJ32, Btv)
-         : EPHB_LAUNCH((k_ph_sweep32<false, 1>), g, 256, 0, st, M, B, kinfo, Y32, IJ32, Btv);
+cudaError_t launch_ph_sweep32(const ModelDev &M, const BteDev &B, const SweepSegs &S, const int2 *kinfo,
+                              const float *Y32, const float *IJ32, double *part, double *Btv, cudaStream_t st) {
+  const int64_t nrow = B.nq * B.nbr;
+  if (S.nseg > 0) {
+    const unsigned g = unsigned((S.nseg * 32 + 255) / 256);
+    if (M.nsym > 1)
+      EPHB_LAUNCH(k_ph_sweep32<true>, g, 256, 0, st, M, B, S, kinfo, Y32, IJ32, part);
+    else
+      EPHB_LAUNCH(k_ph_sweep32<false>, g, 256, 0, st, M, B, S, kinfo, Y32, IJ32, part);
+  }
+  if (nrow > 0) EPHB_LAUNCH(k_ph_seg_finalize, unsigned((nrow + 255) / 256), 256, 0, st, nrow, S, part, Btv);
   return cudaGetLastError();
 }
 
@@ -1371,17 +1391,17 @@ cudaError_t launch_drag_term(const MeshDev &D, const BteDev &B, const SweepSegs 
   return cudaGetLastError();
 }
 
-cudaError_t launch_ph_sweep(const ModelDev &M, const MeshDev &D, const BteDev &B, const int2 *kinfo, const double *I,
-                            const double *J, double *Btv, int64_t n_ph_entries, cudaStream_t st) {
-  // rows of a few entries: one thread per row; longer rows: one warp
-  const bool wide = B.nq * B.nbr > 0 && n_ph_entries / (B.nq * B.nbr) >= 4;
-  const unsigned g = unsigned((B.nq * B.nbr * (wide ? 32 : 1) + 255) / 256);
-  if (M.nsym > 1)
-    wide ? EPHB_LAUNCH((k_ph_sweep<true, 32>), g, 256, 0, st, M, D, B, kinfo, I, J, Btv)
-         : EPHB_LAUNCH((k_ph_sweep<true, 1>), g, 256, 0, st, M, D, B, kinfo, I, J, Btv);
-  else
-    wide ? EPHB_LAUNCH((k_ph_sweep<false, 32>), g, 256, 0, st, M, D, B, kinfo, I, J, Btv)
-         : EPHB_LAUNCH((k_ph_sweep<false, 1>), g, 256, 0, st, M, D, B, kinfo, I, J, Btv);
+cudaError_t launch_ph_sweep(const ModelDev &M, const BteDev &B, const SweepSegs &S, const int2 *kinfo,
+                            const double *I, const double *J, double *part, double *Btv, cudaStream_t st) {
+  const int64_t nrow = B.nq * B.nbr;
+  if (S.nseg > 0) {
+    const unsigned g = unsigned((S.nseg * 32 + 255) / 256);
+    if (M.nsym > 1)
+      EPHB_LAUNCH(k_ph_sweep<true>, g, 256, 0, st, M, B, S, kinfo, I, J, part);
+    else
+      EPHB_LAUNCH(k_ph_sweep<false>, g, 256, 0, st, M, B, S, kinfo, I, J, part);
+  }
+  if (nrow > 0) EPHB_LAUNCH(k_ph_seg_finalize, unsigned((nrow + 255) / 256), 256, 0, st, nrow, S, part, Btv);
   return cudaGetLastError();
 }
 

@@ -279,8 +279,10 @@ cudaError_t launch_pack_ij(int64_t nst, const double *I, const double *J, double
 // Drag term of every row for the current F, G: Dterm[st][6].
 cudaError_t launch_drag_term(const MeshDev &D, const BteDev &B, const SweepSegs &S, const double *F, const double *G,
                              double *part, double *Dterm, cudaStream_t st);
-cudaError_t launch_ph_sweep(const ModelDev &M, const MeshDev &D, const BteDev &B, const int2 *kinfo, const double *I,
-                            const double *J, double *Btv, int64_t n_ph_entries, cudaStream_t st);
+// Phonon drag scatter over the phonon rows (q, s) cut into segments S (built over ph_row_ptr
+// like the electron segments): per-segment partials into part[nseg][6], then Btv[row][6].
+cudaError_t launch_ph_sweep(const ModelDev &M, const BteDev &B, const SweepSegs &S, const int2 *kinfo,
+                            const double *I, const double *J, double *part, double *Btv, cudaStream_t st);
 cudaError_t launch_ph_update(const ModelDev &M, const MeshDev &D, const double *Btv, const double *F0,
                              const double *inv_nnW, double *F, double *G, double *Afold, cudaStream_t st);
 // Coefficient tensors: fixed-count partial sums (electron: 36 per block, phonon: 18 per
@@ -307,16 +309,16 @@ cudaError_t launch_corr_apply(int64_t nst, const float *dI, const float *dJ, dou
 // Y32 (float per phonon entry) and IJ32 ([state][I | J] floats); pack6: out[i] = (A[i], B[i]).
 cudaError_t launch_drag_term32(const MeshDev &D, const BteDev &B, const SweepSegs &S, const float2 *X32,
                                const float *FG32, double *part, double *Dterm, cudaStream_t st);
-cudaError_t launch_ph_sweep32(const ModelDev &M, const BteDev &B, const int2 *kinfo, const float *Y32,
-                              const float *IJ32, double *Btv, int64_t n_ph_entries, cudaStream_t st);
+cudaError_t launch_ph_sweep32(const ModelDev &M, const BteDev &B, const SweepSegs &S, const int2 *kinfo,
+                              const float *Y32, const float *IJ32, double *part, double *Btv, cudaStream_t st);
 cudaError_t launch_pack6_f32(int64_t n, const double *A, const double *Bv, float *out, cudaStream_t st);
 // Float-float forms of the same two terms for the later outer iterations of the mixed
 // iteration: Xff (X+ hi, lo, X- hi, lo per entry), Yff, IJff ([state][6] pairs), FGff
 // ([mode][6] pairs); partial sums converted to FP64 per lane and reduced in FP64.
 cudaError_t launch_drag_termff(const MeshDev &D, const BteDev &B, const SweepSegs &S, const float4 *Xff,
                                const float2 *FGff, double *part, double *Dterm, cudaStream_t st);
-cudaError_t launch_ph_sweepff(const ModelDev &M, const BteDev &B, const int2 *kinfo, const float2 *Yff,
-                              const float2 *IJff, double *Btv, int64_t n_ph_entries, cudaStream_t st);
+cudaError_t launch_ph_sweepff(const ModelDev &M, const BteDev &B, const SweepSegs &S, const int2 *kinfo,
+                              const float2 *Yff, const float2 *IJff, double *part, double *Btv, cudaStream_t st);
 cudaError_t launch_copy_ff(int64_t n, const double *a, float2 *out, cudaStream_t st);
 cudaError_t launch_pack6_ff(int64_t n, const double *A, const double *Bv, float2 *out, cudaStream_t st);
 cudaError_t launch_copy_f32(int64_t n, const double *a, float *b, cudaStream_t st);
@@ -374,13 +376,14 @@ struct GraphOpts {
 // Everything the capture of one instance reads (device pointers, counts, views).
 struct GraphInst {
   BteDev B;
-  SweepSegs Sr, Se;                     // segments of the partner runs and of the entry stream
+  SweepSegs Sr, Se, Sp;                 // segments of the partner runs, the entry stream, the phonon entries
   int64_t nst, nph, n_entries, n_ph_entries, nruns;
   const int2 *kinfo;
   const uint32_t *run_col;
   const double *run_w, *I0, *J0, *inv_ffW, *W_ph, *inv_nnW, *F0, *ph_Y;
   const double2 *e_X;
-  double *I, *J, *I2, *J2, *F, *G, *Btv, *Afold, *Dterm, *seg_part, *epart, *ppart, *kpart, *res, *prev_in, *prev_out;
+  double *I, *J, *I2, *J2, *F, *G, *Btv, *Afold, *Dterm, *seg_part, *ph_part, *epart, *ppart, *kpart, *res, *prev_in,
+      *prev_out;
   float *run_w32, *rI, *rJ, *dI, *dJ, *dI2, *dJ2, *part32;     // mixed electron loop
   float2 *X32;                                                 // mixed, FP32 phonon-side terms
   float *Y32, *IJ32, *FG32;

@@ -291,12 +291,12 @@ struct InstBuilder {
   cudaError_t phonon_half(int mode, cudaStream_t st) {
     if (mode == 0) {
       GS_CK(launch_pack6_f32(g.nst, g.I, g.J, g.IJ32, st));
-      GS_CK(launch_ph_sweep32(M, g.B, g.kinfo, g.Y32, g.IJ32, g.Btv, g.n_ph_entries, st));
+      GS_CK(launch_ph_sweep32(M, g.B, g.Sp, g.kinfo, g.Y32, g.IJ32, g.ph_part, g.Btv, st));
     } else if (mode == 1) {
       GS_CK(launch_pack6_ff(g.nst, g.I, g.J, g.IJff, st));
-      GS_CK(launch_ph_sweepff(M, g.B, g.kinfo, g.Yff, g.IJff, g.Btv, g.n_ph_entries, st));
+      GS_CK(launch_ph_sweepff(M, g.B, g.Sp, g.kinfo, g.Yff, g.IJff, g.ph_part, g.Btv, st));
     } else {
-      GS_CK(launch_ph_sweep(M, D, g.B, g.kinfo, g.I, g.J, g.Btv, g.n_ph_entries, st));
+      GS_CK(launch_ph_sweep(M, g.B, g.Sp, g.kinfo, g.I, g.J, g.ph_part, g.Btv, st));
     }
     GS_CK(launch_ph_update(M, D, g.Btv, g.F0, g.inv_nnW, g.F, g.G, g.Afold, st));
     if (mode == 0) GS_CK(launch_pack6_f32(g.nph, g.F, g.G, g.FG32, st));
