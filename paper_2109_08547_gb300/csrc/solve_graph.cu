@@ -165,8 +165,8 @@ unsigned grid_for(int64_t n) {
   return unsigned(g < 1 ? 1 : (g > 4096 ? 4096 : g));
 }
 
+// launched also for n = 0, so that a switch body made of it alone is never empty
 cudaError_t copy2(int64_t n, const double *a, const double *b, double *ao, double *bo, cudaStream_t st) {
-  if (n == 0) return cudaSuccess;
   EPHB_LAUNCH(k_gs_copy2, grid_for(n), 256, 0, st, n, a, b, ao, bo);
   return cudaGetLastError();
 }

@@ -130,3 +130,19 @@ def test_device_loop_arguments():
             B.solve_coupled_bte(ctx, "rta", 1e-10, device_loop=True)
         r = B.solve_coupled_bte(ctx, "dragged", 1e-10, device_loop=True)
         assert r["converged"] == 1
+
+
+@pytest.mark.parametrize("solve_precision", ["mixed", "fp64"])
+def test_device_loop_on_an_empty_window(solve_precision):
+    """No state in the window: the graph still builds and runs (every conditional body holds a
+    kernel) and gives the host loop's zero electron tensors."""
+    wl = dataclasses.replace(SY.workload_sc1(), window=(50.0, 60.0))
+    with B.Context(0) as ctx:
+        B.set_wannier_model(ctx, wl.model)
+        B.build_meshes_ibz(ctx, wl.kmesh, wl.qmesh, wl.window, wl.degen_tol_eV, wl.omega_min_eV)
+        B.compute_transition_rates(ctx, wl.T_K, wl.mu_eV, wl.sigma_eV, wl.cutoff_sigmas)
+        host, hc, dev, dc = _solve_both(ctx, "dragged", wl.tol, solve_precision)
+        assert dev["graph_launches"] == 1
+        _assert_identical(host, hc, dev, dc)
+        for key in ("sigma", "sigmaS", "alpha_el", "kappa0_el"):
+            assert np.all(dc[0][key] == 0.0)
