@@ -4,6 +4,7 @@ Plain, slow, readable double-precision restatement of arXiv 2109.08547:
   * Wannier-to-Bloch interpolation of H, D and g            (Eqs. H_mn(k), D_ss'(q), g^smn_kq)
   * Hellmann-Feynman electron and phonon velocities         (Eqs. v_mk, v_sq)
   * e-ph transition rates X^+ / X^- over IBZ k x FBZ k'     (Eq. X^e-ph)
+  * e-chimp rates (screened Coulomb, Born)                  (Eqs. |g^e-chimp_q|^2, q_TF^2, X^e-chimp)
   * ph-e rates Y (the same + process seen from the phonon)  (Eq. Y^ph-e)
   * RTA terms and rates, self and drag terms                (Eqs. I0/J0, W^RTA, dI^S, dI^D, F0/G0, dF^D)
   * unified single-iterator coupled solution                ("Coupled and decoupled BTEs")
@@ -38,6 +39,7 @@ __all__ = [
     "prepare", "Prepared", "gaussian_delta", "fermi", "bose", "StateSpace", "ibz_window_points",
     "kplusq", "minus_q", "TENSORS", "inverse_ops", "ANGSTROM", "ibz_window_rows", "prepare_rows",
     "tetra_corner_weights", "tetra_point_weights", "CUBE_TETRAHEDRA", "CUBE_SUBDIVISIONS",
+    "EPS0", "centred", "reciprocal_si", "thomas_fermi_q2", "chimp_g2", "chimp_kernel", "chimp_rates",
 ]
 
 
@@ -533,6 +535,80 @@ def transition_rates(P: Prepared, ks=None, q_chunk: int = 256) -> Rates:
 TENSORS = ("sigma", "sigmaS", "alpha_el", "kappa0_el", "alpha_ph", "kappa_ph")
 
 
+# ----------------------------------------------------------------------------------------
+# electron-charged-impurity scattering (e-chimp): Eqs. |g^e-chimp_q|^2, q_TF^2, X^e-chimp
+# ----------------------------------------------------------------------------------------
+
+EPS0 = 8.8541878128e-12        # F / m
+
+
+def centred(frac: np.ndarray) -> np.ndarray:
+    """Crystal coordinates reduced to [-1/2, 1/2) (for a cubic lattice: the nearest zone centre)."""
+    return frac - np.floor(frac + 0.5)
+
+
+def reciprocal_si(lattice_A: np.ndarray) -> np.ndarray:
+    """Reciprocal lattice vectors (rows, 1/m) of lattice vectors given as rows in Angstrom."""
+    return 2.0 * np.pi * np.linalg.inv(lattice_A).T / ANGSTROM
+
+
+def thomas_fermi_q2(P: Prepared, imp) -> float:
+    """Squared Thomas-Fermi wave vector (1/m^2), Eq. q_TF^2:
+    d_s e^2 beta / (N_k V eps0 eps) sum_{mk} f(1 - f), over every band on the full k mesh."""
+    wl = P.wl
+    m = wl.model
+    V = abs(np.linalg.det(m.lattice)) * ANGSTROM ** 3
+    f = fermi(P.eps, wl.mu_eV, wl.T_K)
+    beta = 1.0 / (KB_EVK * E_CHARGE * wl.T_K)          # 1/J
+    return m.spin_deg * E_CHARGE ** 2 * beta * float(np.sum(f * (1.0 - f))) / (P.Nk * V * EPS0 * imp.eps_r)
+
+
+def chimp_g2(q2: np.ndarray, q_tf2: float, imp, V: float) -> np.ndarray:
+    """|g^e-chimp_q|^2 (eV^2) for squared wave vectors q2 (1/m^2), Eq. |g^e-chimp_q|^2:
+    (1/V) sum_i n_i [Z_i e / (eps0 eps (q^2 + q_TF^2))]^2.  The bracket is in V m^3; with n_i in
+    1/m^3 and V the cell volume in m^3 the result is in V^2, numerically eV^2 per carrier charge."""
+    out = np.zeros_like(q2, dtype=np.float64)
+    for n, Z in zip(imp.n_cm3, imp.Z):
+        out = out + (n * 1e6) * (Z * E_CHARGE / (EPS0 * imp.eps_r * (q2 + q_tf2))) ** 2
+    return out / V
+
+
+def chimp_kernel(P: Prepared, states: np.ndarray):
+    """Elastic e-chimp rates of Eq. X^e-chimp divided by the initial state's f(1 - f):
+    K[a, b] = 2 pi / (hbar N_k) |g_q|^2 (1 - k.k' / (k k')) delta(eps_b - eps_a)
+    for the initial states a = (k, m) (rows of `states`) and every active final state
+    b = (k', n) of the full k mesh, q = [k' - k].  Readings: k, k' and q are Cartesian vectors of
+    the centred crystal coordinates; a zero-length k or k' has transport factor 1; the final
+    states are those of the window, as for the e-ph rates; delta is the e-ph Gaussian.
+    Returns (K, final k indices, final bands)."""
+    wl = P.wl
+    m = wl.model
+    imp = wl.chimp
+    V = abs(np.linalg.det(m.lattice)) * ANGSTROM ** 3
+    Bm = reciprocal_si(m.lattice)
+    frac = P.kidx / np.array(wl.kmesh, dtype=np.float64)
+    kc = centred(frac) @ Bm
+    fk, fb = np.nonzero(P.active)
+    ka, ma = states[:, 0], states[:, 1]
+    dq = centred(frac[fk][None, :, :] - frac[ka][:, None, :]) @ Bm
+    g2 = chimp_g2(np.sum(dq * dq, axis=-1), thomas_fermi_q2(P, imp), imp, V)
+    na = np.linalg.norm(kc[ka], axis=1)
+    nb = np.linalg.norm(kc[fk], axis=1)
+    den = na[:, None] * nb[None, :]
+    cos = np.where(den > 0.0, (kc[ka] @ kc[fk].T) / np.where(den > 0.0, den, 1.0), 0.0)
+    cos = np.clip(cos, -1.0, 1.0)   # rounding must not make 1 - cos (k' = k: zero) negative
+    delta = gaussian_delta(P.eps[fk, fb][None, :] - P.eps[ka, ma][:, None], wl.sigma_eV, wl.cutoff_sigmas)
+    K = 2.0 * np.pi / (HBAR_EVS * P.Nk) * g2 * (1.0 - cos) * delta
+    return K, fk, fb
+
+
+def chimp_rates(P: Prepared, states: np.ndarray) -> np.ndarray:
+    """The e-chimp part of W^RTA of each state (Eq. W^RTA_mk, Matthiessen's rule):
+    sum_{nk'} X^e-chimp / (f (1 - f))."""
+    K, _, _ = chimp_kernel(P, states)
+    return K.sum(axis=1)
+
+
 @dataclasses.dataclass
 class BTEResult:
     coeffs: dict
@@ -669,6 +745,8 @@ def solve_coupled_bte(P: Prepared, R: Rates, level: str = "dragged", ko: bool = 
     W_e = np.zeros(nst)
     np.add.at(W_e, sy.row, X)
     W_e = W_e / sy.ff
+    if getattr(wl, "chimp", None) is not None:   # e-chimp enters the RTA rate only (Matthiessen's rule)
+        W_e = W_e + chimp_rates(P, sy.states)
     ok_e = W_e > 0.0
     inv_ffW = np.zeros(nst)
     inv_ffW[ok_e] = 1.0 / (sy.ff[ok_e] * W_e[ok_e])

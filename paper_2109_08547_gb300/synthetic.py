@@ -59,6 +59,16 @@ class WannierModel:
         return 3 * self.nat
 
 
+@dataclasses.dataclass(frozen=True)
+class Impurities:
+    """Charged dopants of the electron-charged-impurity (e-chimp) channel: one entry per dopant
+    species (concentration in cm^-3 and ionization Z), and the zero-frequency dielectric
+    constant of the host."""
+    n_cm3: tuple
+    Z: tuple
+    eps_r: float
+
+
 @dataclasses.dataclass
 class Workload:
     name: str
@@ -74,6 +84,7 @@ class Workload:
     degen_tol_eV: float = 1.0e-6
     tol: float = 1.0e-10
     delta: str = "gauss"           # energy-conserving delta: "gauss" (sigma_eV) or "tetra" (no width)
+    chimp: Impurities = None       # charged impurities (e-chimp channel), or none
 
 
 def oh_group() -> np.ndarray:
