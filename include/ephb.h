@@ -311,6 +311,33 @@ typedef struct {
  * instances and keeps the largest residual and outer-iteration count; converged is 1 only if
  * every instance converged, else the call returns EPHB_ENOCONV after solving all of them. */
 ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *opts, ephb_solve_info *out);
+
+/* ---- Electron-charged-impurity (e-chimp) scattering -----------------------------------
+ * "Electrons, phonons, and interactions", Eqs. |g^e-chimp_q|^2, q_TF^2 and X^e-chimp: the
+ * dopants' screened Coulomb potential in the first Born approximation,
+ *   |g_q|^2 = (1/V) sum_i n_i [Z_i e / (eps0 eps (q^2 + q_TF^2))]^2,
+ *   q_TF^2  = d_s e^2 / (k_B T N_k V eps0 eps) sum_{mk} f (1 - f)   (every band, full k mesh),
+ *   X^e-chimp_{mk -> nk'} = 2 pi/(hbar N_k) |g_q|^2 (1 - k.k'/(k k')) f (1 - f) delta(eps' - eps),
+ * q = [k' - k], V the cell volume.  It enters the electron RTA rate W^RTA only (Matthiessen's
+ * rule, Eq. W^RTA_mk): its transport factor stands for the elastic in-scattering, so the self
+ * term keeps the e-ph rates alone.  Readings: k, k' and q are the Cartesian vectors of the
+ * centred crystal coordinates (each in [-1/2, 1/2); for a cubic lattice q is then measured from
+ * the nearest zone centre); a zero-length k or k' has transport factor 1; the final states are
+ * the window's, as for the e-ph rates; delta is the rates call's Gaussian (its sigma_eV and
+ * cutoff_sigmas, also with the tetrahedron kind).  The rates are made at each instance's next
+ * solve, one warp per state over every k' of the mesh.  Errors: EPHB_EINVAL for n_species
+ * outside 0..EPHB_MAX_DOPANTS, a negative concentration or eps_r <= 0; a solve returns
+ * EPHB_EINVAL if the rates call had no positive sigma_eV and cutoff_sigmas. */
+#define EPHB_MAX_DOPANTS 4
+typedef struct {
+  int n_species;                   /* 0: no charged impurities (the default)                */
+  double n_cm3[EPHB_MAX_DOPANTS];  /* dopant concentrations n_i, cm^-3                       */
+  double Z[EPHB_MAX_DOPANTS];      /* their ionizations Z_i                                  */
+  double eps_r;                    /* zero-frequency dielectric constant of the host         */
+} ephb_impurities;
+/* Sets (NULL or n_species = 0: clears) the charged impurities; every instance's RTA terms are
+ * made again at its next solve. */
+ephb_status ephb_set_impurities(ephb_ctx *ctx, const ephb_impurities *imp);
 /* The last solve of one instance. */
 ephb_status ephb_instance_solve_info(ephb_ctx *ctx, int inst, ephb_solve_info *out);
 

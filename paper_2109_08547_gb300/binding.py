@@ -38,7 +38,8 @@ EXPORTED = ["ephb_create", "ephb_destroy", "ephb_last_error", "ephb_set_wannier_
             "ephb_set_warm_start", "ephb_mlp_create", "ephb_mlp_destroy", "ephb_mlp_last_error",
             "ephb_mlp_num_params", "ephb_mlp_set_bf16", "ephb_mlp_get_params", "ephb_mlp_set_params",
             "ephb_mlp_forward", "ephb_mlp_loss_grad", "ephb_mlp_train_step", "ephb_set_tuning",
-            "ephb_selftest_exp_ff"]
+            "ephb_selftest_exp_ff", "ephb_set_impurities"]
+MAX_DOPANTS = 4   # EPHB_MAX_DOPANTS
 NFEAT = 6
 MAX_ACCEL_DEPTH = 8   # EPHB_MAX_ACCEL_DEPTH
 
@@ -108,6 +109,10 @@ class CoeffsC(C.Structure):
                 ("sigma", "sigmaS", "S", "alpha_el", "kappa0_el", "kappa_el", "alpha_ph", "kappa_ph")]
 
 
+class ImpuritiesC(C.Structure):
+    _fields_ = [("n_species", C.c_int), ("n_cm3", C.c_double * 4), ("Z", C.c_double * 4), ("eps_r", C.c_double)]
+
+
 class CoeffInputsC(C.Structure):
     _fields_ = [("n_states", C.c_int64), ("eps", C.c_void_p), ("vel", C.c_void_p), ("weight", C.c_void_p),
                 ("I", C.c_void_p), ("J", C.c_void_p), ("n_modes", C.c_int64), ("omega", C.c_void_p),
@@ -141,6 +146,7 @@ def load(path: str = None):
                                                   C.c_int, C.POINTER(RatesInfoC)]
     lib.ephb_solve_coupled_bte.argtypes = [C.c_void_p, C.POINTER(SolveOptsC), C.POINTER(SolveInfoC)]
     lib.ephb_transport_coefficients.argtypes = [C.c_void_p, C.c_int, C.POINTER(CoeffsC)]
+    lib.ephb_set_impurities.argtypes = [C.c_void_p, C.POINTER(ImpuritiesC)]
     lib.ephb_get_device_array.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
                                           C.POINTER(C.c_int)]
     lib.ephb_copy_array_to_host.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]
@@ -342,6 +348,21 @@ def solve_coupled_bte(ctx: Context, level="dragged", tol=1e-10, inner_tol=0.0, m
     return d
 
 
+def set_impurities(ctx: Context, imp=None) -> None:
+    """Charged impurities of the e-chimp channel (an object with n_cm3, Z, eps_r, e.g.
+    synthetic.Impurities), or None to clear them."""
+    if imp is None or len(imp.n_cm3) == 0:
+        _check(ctx, _lib.ephb_set_impurities(ctx.handle, None))
+        return
+    c = ImpuritiesC()
+    c.n_species = len(imp.n_cm3)      # the library rejects more than MAX_DOPANTS
+    for i, (n, z) in enumerate(list(zip(imp.n_cm3, imp.Z))[:MAX_DOPANTS]):
+        c.n_cm3[i] = float(n)
+        c.Z[i] = float(z)
+    c.eps_r = float(imp.eps_r)
+    _check(ctx, _lib.ephb_set_impurities(ctx.handle, C.byref(c)))
+
+
 def transport_coefficients(ctx: Context, inst: int = 0) -> dict:
     c = CoeffsC()
     _check(ctx, _lib.ephb_transport_coefficients(ctx.handle, int(inst), C.byref(c)))
@@ -411,6 +432,7 @@ def run_path(ctx: Context, wl, level="dragged", ko_correction=True, tol=None, ma
              precision=FP64, allow_noconv=False, solve_precision="fp64", accel=0,
              device_loop=False) -> PathResult:
     """The whole hot path for one workload on an existing context whose model is set."""
+    set_impurities(ctx, getattr(wl, "chimp", None))
     mesh = build_meshes_ibz(ctx, wl.kmesh, wl.qmesh, wl.window, wl.degen_tol_eV, wl.omega_min_eV)
     rates = compute_transition_rates(ctx, wl.T_K, wl.mu_eV, wl.sigma_eV, wl.cutoff_sigmas, precision,
                                      delta=getattr(wl, "delta", "gauss"))

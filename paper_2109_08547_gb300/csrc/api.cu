@@ -104,6 +104,7 @@ struct InstState {
   DBuf<int64_t> pseg_ptr, pseg_begin;
   DBuf<double> pseg_part;
   int64_t npseg = 0;
+  DBuf<double> W_chimp;         // e-chimp part of the electron RTA rates [nst]
   DBuf<uint32_t> kcrd;
   DBuf<int2> kinfo;
   DBuf<int> sctl;               // device-driven sweep loop: stop flag, sweeps done, converged
@@ -165,6 +166,7 @@ struct InstState {
     X32.release(); Y32.release(); IJ32.release(); FG32.release();
     Xff.release(); Yff.release(); IJff.release(); FGff.release();
     pnseg_row.release(); pseg_row.release(); pseg_ptr.release(); pseg_begin.release(); pseg_part.release();
+    W_chimp.release();
     bte_ready = has_warm = solved = have_f32 = lists_pending = false;
   }
 };
@@ -248,6 +250,10 @@ struct ephb_ctx : InstState {
   int force_defer = 0;    // EPHB_TUNE_DEFER_INSTANCES: derive instance lists at solve time always
   int stage_a_tmem = 0;   // EPHB_TUNE_STAGE_A_TMEM_A: stage A's A slices through tensor memory
   double *host_res = nullptr;   // pinned: kResLen doubles, then the sweep-loop control (4 ints)
+  // charged impurities (e-chimp) and the Gaussian of the last rates call (their delta)
+  ephb_impurities imp{};
+  double delta_sigma = 0.0, delta_cut = 0.0;
+  DBuf<double> chimp_part, chimp_qtf;
   // device-driven solve: the instantiated graph, the signature of what it was built from, the
   // kernels per body (launch counts), the capture stream and the per-instance control blocks
   cudaGraph_t sg_graph = nullptr;
@@ -435,6 +441,8 @@ void ephb_destroy(ephb_ctx *ctx) {
   ctx->u_X.release(); ctx->u_ph_st.release(); ctx->u_ph_V.release();
   ctx->drop_graph();
   ctx->sg_ctl.release();
+  ctx->chimp_part.release();
+  ctx->chimp_qtf.release();
   if (ctx->sg_cs) cudaStreamDestroy(ctx->sg_cs);
   ctx->release_all();
   for (auto &sl : ctx->slots) sl.release_all();
@@ -917,6 +925,8 @@ ephb_status ephb_compute_transition_rates(ephb_ctx *ctx, const ephb_thermo *inst
     return fail(ctx, EPHB_EINVAL, "delta kind must be EPHB_DELTA_GAUSS or EPHB_DELTA_TETRA");
   if (delta->kind == EPHB_DELTA_GAUSS && (!(delta->sigma_eV > 0) || !(delta->cutoff_sigmas > 0)))
     return fail(ctx, EPHB_EINVAL, "sigma and cutoff must be positive");
+  ctx->delta_sigma = delta->sigma_eV;
+  ctx->delta_cut = delta->cutoff_sigmas;
   // exact FP32 sums of the accumulated slice diagonals bound the contraction length
   if (precision == EPHB_FP64_SLICED && tc_slices_for(tc_kp(ctx->M), true) == 0)
     return fail(ctx, EPHB_EINVAL, "EPHB_FP64_SLICED needs 2 nRgp <= 816");
@@ -1234,7 +1244,46 @@ ephb_status bte_setup(ephb_ctx *ctx) {
   BteDev B = bte_view(ctx);
   CK(ctx->nzero.ensure(1));
   CK(cudaMemsetAsync(ctx->nzero.p, 0, sizeof(unsigned long long), st));
-  CK(launch_rta_electron(B, ctx->W_e.p, ctx->inv_ffW.p, ctx->I0.p, ctx->J0.p, ctx->nzero.p, st));
+  const double *W_add = nullptr;
+  if (ctx->imp.n_species > 0) {   // e-chimp rates join W^RTA (Matthiessen's rule)
+    if (!(ctx->delta_sigma > 0) || !(ctx->delta_cut > 0))
+      return fail(ctx, EPHB_EINVAL, "charged impurities need the Gaussian width of the rates call");
+    CK(ctx->W_chimp.ensure(nst));
+    CK(ctx->chimp_part.ensure(size_t(chimp_partials())));
+    CK(ctx->chimp_qtf.ensure(1));
+    const double *L = M.lattice;   // rows: the lattice vectors (Angstrom)
+    const double det3 = L[0] * (L[4] * L[8] - L[5] * L[7]) - L[1] * (L[3] * L[8] - L[5] * L[6]) +
+                        L[2] * (L[3] * L[7] - L[4] * L[6]);
+    const double V = fabs(det3) * kAngstrom * kAngstrom * kAngstrom;
+    ChimpParams cp;
+    std::memset(&cp, 0, sizeof(cp));
+    cp.nspec = ctx->imp.n_species;
+    for (int i = 0; i < cp.nspec; ++i) {
+      cp.n_m3[i] = ctx->imp.n_cm3[i] * 1e6;
+      cp.Z[i] = ctx->imp.Z[i];
+    }
+    cp.eps_r = ctx->imp.eps_r;
+    cp.V = V;
+    // reciprocal vectors (1/m): the rows of 2 pi (L^-1)^T, (L^-1)^T[r][c] = cofactor(r, c) / det L
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) {
+        const int r1 = (r + 1) % 3, r2 = (r + 2) % 3, c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+        const double cof = L[r1 * 3 + c1] * L[r2 * 3 + c2] - L[r1 * 3 + c2] * L[r2 * 3 + c1];
+        cp.rec[r][c] = 2.0 * kPi * cof / det3 / kAngstrom;
+      }
+    cp.sigma = ctx->delta_sigma;
+    cp.cut_sigmas = ctx->delta_cut;
+    cp.gnorm = 1.0 / (ctx->delta_sigma * sqrt(2.0 * kPi));
+    cp.pref = 2.0 * kPi / (kHbarEVs * double(nk));
+    cp.win_lo = ctx->win_lo;
+    cp.win_hi = ctx->win_hi;
+    const double kT_J = kKbEVK * kECharge * ctx->T;
+    const double ff_scale = M.spin_deg * kECharge * kECharge / (kT_J * double(nk) * V * 8.8541878128e-12 * cp.eps_r);
+    CK(launch_chimp_rates(D, B, cp, ctx->eps.p, nk * M.nb, ff_scale, ctx->chimp_part.p, ctx->chimp_qtf.p,
+                          ctx->W_chimp.p, st));
+    W_add = ctx->W_chimp.p;
+  }
+  CK(launch_rta_electron(B, ctx->W_e.p, ctx->inv_ffW.p, ctx->I0.p, ctx->J0.p, ctx->nzero.p, st, W_add));
   CK(launch_ph_rowsum(B, ctx->Bt.p, st));
   CK(launch_rta_phonon(M, D, B, ctx->Bt.p, ctx->W_ph.p, ctx->inv_nnW.p, ctx->F0.p, st));
   // partner runs of the electron rows (self term), then segments of the entry stream
@@ -2098,6 +2147,25 @@ ephb_status ephb_solve_coupled_bte(ephb_ctx *ctx, const ephb_solve_opts *o, ephb
   if (out) *out = sum;
   ctx->stage = 4;
   if (noconv) return fail(ctx, EPHB_ENOCONV, "iteration limit reached before the tolerance");
+  return EPHB_OK;
+}
+
+ephb_status ephb_set_impurities(ephb_ctx *ctx, const ephb_impurities *imp) {
+  if (!ctx) return EPHB_EINVAL;
+  ephb_impurities v{};
+  if (imp && imp->n_species != 0) {
+    if (imp->n_species < 0 || imp->n_species > EPHB_MAX_DOPANTS)
+      return fail(ctx, EPHB_EINVAL, "n_species outside 0..EPHB_MAX_DOPANTS");
+    if (!(imp->eps_r > 0)) return fail(ctx, EPHB_EINVAL, "eps_r must be positive");
+    for (int i = 0; i < imp->n_species; ++i)
+      if (!(imp->n_cm3[i] >= 0) || !std::isfinite(imp->Z[i]))
+        return fail(ctx, EPHB_EINVAL, "concentrations must be non-negative and charges finite");
+    v = *imp;
+  }
+  ctx->imp = v;
+  // the RTA terms of every instance change
+  ctx->bte_ready = false;
+  for (auto &sl : ctx->slots) sl.bte_ready = false;
   return EPHB_OK;
 }
 

@@ -58,9 +58,10 @@ __global__ void k_state_setup(ModelDev M, MeshDev D, double T, double mu, double
   }
 }
 
-// W_e = sum_row (X+ + X-) / (f(1-f)); I0 = (eps-mu)/T v/W; J0 = v/W   (Eqs. W^RTA_mk, I0/J0)
+// W_e = sum_row (X+ + X-) / (f(1-f)) (+ W_add, other channels by Matthiessen's rule);
+// I0 = (eps-mu)/T v/W; J0 = v/W   (Eqs. W^RTA_mk, I0/J0)
 __global__ void k_rta_electron(BteDev B, double *W_e, double *inv_ffW, double *I0, double *J0,
-                               unsigned long long *n_zero) {
+                               unsigned long long *n_zero, const double *__restrict__ W_add) {
   int64_t st = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (st >= B.nst) return;
@@ -73,8 +74,9 @@ __global__ void k_rta_electron(BteDev B, double *W_e, double *inv_ffW, double *I
   if (lane == 0) {
     double ff = B.st_ff[st];
     double W = 0.0, inv = 0.0;
-    if (ff > 0.0 && s > 0.0) {
-      W = s / ff;
+    const double add = ff > 0.0 && W_add ? W_add[st] : 0.0;
+    if (ff > 0.0 && (s > 0.0 || add > 0.0)) {
+      W = s / ff + add;
       inv = 1.0 / (ff * W);
     } else if (ff > 0.0) {
       atomicAdd(n_zero, 1ull);
@@ -980,12 +982,134 @@ cudaError_t launch_state_setup(const ModelDev &M, const MeshDev &D, double T, do
 }
 
 cudaError_t launch_rta_electron(const BteDev &B, double *W_e, double *inv_ffW, double *I0, double *J0,
-                                unsigned long long *n_zero, cudaStream_t st) {
+                                unsigned long long *n_zero, cudaStream_t st, const double *W_add) {
   cudaError_t e = cudaMemsetAsync(n_zero, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess || B.nst == 0) return e;
-  EPHB_LAUNCH(k_rta_electron, unsigned((B.nst * 32 + 255) / 256), 256, 0, st, B, W_e, inv_ffW, I0, J0, n_zero);
+  EPHB_LAUNCH(k_rta_electron, unsigned((B.nst * 32 + 255) / 256), 256, 0, st, B, W_e, inv_ffW, I0, J0, n_zero,
+              W_add);
   return cudaGetLastError();
 }
+
+namespace {
+
+// ---- electron-charged-impurity scattering (e-chimp): Eqs. |g^e-chimp_q|^2, q_TF^2, X^e-chimp
+
+constexpr int kChimpSumBlocks = 152;
+constexpr double kEps0 = 8.8541878128e-12;   // F / m
+
+// partial sums of f(1 - f) over every band of every k point (fixed grid: reproducible)
+__global__ void __launch_bounds__(256) k_ff_sum(int64_t n, const double *__restrict__ eps, double mu, double kT,
+                                                double *part) {
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const double f = fermi_b(eps[i], mu, kT);
+    s += f * (1.0 - f);
+  }
+  s = warp_sum(s);
+  __shared__ double w[8];
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) t += w[i];
+    part[blockIdx.x] = t;
+  }
+}
+
+// q_TF^2 = ff_scale * sum f(1 - f) (1/m^2)
+__global__ void k_tf_final(const double *part, int nparts, double ff_scale, double *q_tf2) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double t = 0.0;
+  for (int i = 0; i < nparts; ++i) t += part[i];
+  *q_tf2 = ff_scale * t;
+}
+
+__device__ inline double centred_frac(int i, int n) {
+  const double f = double(i) / double(n);
+  return f - floor(f + 0.5);
+}
+
+// One warp per state (irreducible window k, band): W^chimp = 2 pi/(hbar N_k) sum over the
+// window states (k', n) of the full mesh of |g_q|^2 (1 - k.k'/(k k')) delta(eps' - eps), with
+// q = [k' - k] and k, k', q Cartesian vectors of the centred crystal coordinates (a zero-length
+// k or k' has transport factor 1, the cosine is clipped to [-1, 1]); |g_q|^2 = (1/V) sum_i n_i
+// [Z_i e / (eps0 eps (q^2 + q_TF^2))]^2 (numerically eV^2); Gaussian delta with the e-ph cut.
+__global__ void __launch_bounds__(256) k_chimp_rates(MeshDev D, BteDev B, ChimpParams P, const double *q_tf2_dev,
+                                                     double *W) {
+  const int64_t st = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (st >= B.nst) return;
+  if (!(B.st_ff[st] > 0.0)) {
+    if (lane == 0) W[st] = 0.0;
+    return;
+  }
+  const int nb = B.nb;
+  const int k = D.ibzw_list[st / nb];
+  const double e0 = B.st_eps[st];
+  const double q_tf2 = *q_tf2_dev;
+  int a0, a1, a2;
+  D.km.unflat(k, a0, a1, a2);
+  const double fk[3] = {centred_frac(a0, D.km.n[0]), centred_frac(a1, D.km.n[1]), centred_frac(a2, D.km.n[2])};
+  double kv[3];
+  for (int x = 0; x < 3; ++x) kv[x] = fk[0] * P.rec[0][x] + fk[1] * P.rec[1][x] + fk[2] * P.rec[2][x];
+  const double kn = sqrt(kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2]);
+  const double cut = P.cut_sigmas * P.sigma, inv2s2 = 0.5 / (P.sigma * P.sigma);
+  double acc = 0.0;
+  for (int64_t kp = lane; kp < D.nk; kp += 32) {
+    const uint32_t mask = D.amask[kp];
+    if (!mask) continue;
+    int b0, b1, b2;
+    D.km.unflat(int(kp), b0, b1, b2);
+    double g2 = -1.0, tf = 0.0;   // computed at the first band inside the cut
+    for (int n = 0; n < nb; ++n) {
+      if (!((mask >> n) & 1u)) continue;
+      const double e1 = D.eps[size_t(kp) * nb + n];
+      if (e1 < P.win_lo || e1 > P.win_hi) continue;
+      const double x = e1 - e0;
+      if (fabs(x) > cut) continue;
+      if (g2 < 0.0) {
+        const double fp[3] = {centred_frac(b0, D.km.n[0]), centred_frac(b1, D.km.n[1]), centred_frac(b2, D.km.n[2])};
+        double fq[3], qv[3], pv[3];
+        for (int y = 0; y < 3; ++y) {
+          const double d = fp[y] - fk[y];
+          fq[y] = d - floor(d + 0.5);
+        }
+        for (int y = 0; y < 3; ++y) {
+          qv[y] = fq[0] * P.rec[0][y] + fq[1] * P.rec[1][y] + fq[2] * P.rec[2][y];
+          pv[y] = fp[0] * P.rec[0][y] + fp[1] * P.rec[1][y] + fp[2] * P.rec[2][y];
+        }
+        const double q2 = qv[0] * qv[0] + qv[1] * qv[1] + qv[2] * qv[2];
+        g2 = 0.0;
+        for (int i = 0; i < P.nspec; ++i) {
+          const double u = P.Z[i] * kECharge / (kEps0 * P.eps_r * (q2 + q_tf2));
+          g2 += P.n_m3[i] * u * u;
+        }
+        g2 /= P.V;
+        const double pn = sqrt(pv[0] * pv[0] + pv[1] * pv[1] + pv[2] * pv[2]);
+        const double den = kn * pn;
+        double c = den > 0.0 ? (kv[0] * pv[0] + kv[1] * pv[1] + kv[2] * pv[2]) / den : 0.0;
+        c = fmin(fmax(c, -1.0), 1.0);
+        tf = 1.0 - c;
+      }
+      acc += g2 * tf * exp(-x * x * inv2s2) * P.gnorm;
+    }
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) W[st] = P.pref * acc;
+}
+
+}  // namespace
+
+cudaError_t launch_chimp_rates(const MeshDev &D, const BteDev &B, const ChimpParams &P, const double *eps_all,
+                               int64_t n_eps, double ff_scale, double *part, double *q_tf2, double *W,
+                               cudaStream_t st) {
+  EPHB_LAUNCH(k_ff_sum, kChimpSumBlocks, 256, 0, st, n_eps, eps_all, B.mu, kKbEVK * B.T, part);
+  EPHB_LAUNCH(k_tf_final, 1, 32, 0, st, part, kChimpSumBlocks, ff_scale, q_tf2);
+  if (B.nst > 0) EPHB_LAUNCH(k_chimp_rates, unsigned((B.nst * 32 + 255) / 256), 256, 0, st, D, B, P, q_tf2, W);
+  return cudaGetLastError();
+}
+
+int chimp_partials() { return kChimpSumBlocks; }
 
 cudaError_t launch_ph_rowsum(const BteDev &B, double *Bt, cudaStream_t st) {
   EPHB_LAUNCH(k_ph_rowsum, unsigned((B.nq * B.nbr * 32 + 255) / 256), 256, 0, st, B, Bt);

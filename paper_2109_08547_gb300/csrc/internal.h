@@ -226,8 +226,25 @@ cudaError_t launch_inst_fill(const ModelDev &M, const MeshDev &D, InstWindow w, 
                              const double *u_ph_V, const int64_t *row_ptr, const int64_t *ph_row_ptr,
                              uint32_t *e_kpns, double2 *e_X, int *ph_st, uint32_t *ph_kpn, double *ph_Y,
                              cudaStream_t st);
+// W_add (optional, per state): rates of other channels added to W^RTA (Matthiessen's rule)
 cudaError_t launch_rta_electron(const BteDev &B, double *W_e, double *inv_ffW, double *I0, double *J0,
-                                unsigned long long *n_zero, cudaStream_t st);
+                                unsigned long long *n_zero, cudaStream_t st, const double *W_add = nullptr);
+// Electron-charged-impurity scattering: the e-chimp part of W^RTA of every state.
+struct ChimpParams {
+  int nspec;
+  double n_m3[4], Z[4];             // dopant concentrations (1/m^3) and ionizations
+  double eps_r, V;                  // dielectric constant, cell volume (m^3)
+  double rec[3][3];                 // reciprocal lattice vectors (rows, 1/m)
+  double sigma, cut_sigmas, gnorm;  // Gaussian delta: width, cut, 1/(sigma sqrt(2 pi))
+  double pref;                      // 2 pi / (hbar N_k)
+  double win_lo, win_hi;            // window of the final states
+};
+int chimp_partials();
+// q_TF^2 = ff_scale * sum over the n_eps energies eps_all of f(1 - f) (into q_tf2, device), then
+// W[state] (part: chimp_partials() doubles of scratch)
+cudaError_t launch_chimp_rates(const MeshDev &D, const BteDev &B, const ChimpParams &P, const double *eps_all,
+                               int64_t n_eps, double ff_scale, double *part, double *q_tf2, double *W,
+                               cudaStream_t st);
 cudaError_t launch_ph_rowsum(const BteDev &B, double *Bt, cudaStream_t st);
 cudaError_t launch_rta_phonon(const ModelDev &M, const MeshDev &D, const BteDev &B, const double *Bt, double *W_ph,
                               double *inv_nnW, double *F0, cudaStream_t st);

@@ -38,7 +38,7 @@ def test_struct_layouts_match_header(tmp_path):
     structs = {"ephb_model": B.ModelC, "ephb_mesh_opts": B.MeshOptsC, "ephb_mesh_info": B.MeshInfoC,
                "ephb_thermo": B.ThermoC, "ephb_delta": B.DeltaC, "ephb_rates_info": B.RatesInfoC,
                "ephb_solve_opts": B.SolveOptsC, "ephb_solve_info": B.SolveInfoC, "ephb_coeffs": B.CoeffsC,
-               "ephb_coeff_inputs": B.CoeffInputsC}
+               "ephb_coeff_inputs": B.CoeffInputsC, "ephb_impurities": B.ImpuritiesC}
     src = tmp_path / "sz.c"
     lines = ['#include <stdio.h>', '#include "ephb.h"', "int main(void){"]
     for n in structs:
@@ -58,7 +58,7 @@ def test_binding_constants_match_header():
                         ("EPHB_TUNE_TC_COLS", B.TUNE_TC_COLS), ("EPHB_TUNE_WITHHOLD_MMA", B.TUNE_WITHHOLD_MMA),
                         ("EPHB_NOALLOC_MAX_ITEMS", B.NOALLOC_MAX_ITEMS),
                         ("EPHB_TUNE_DEFER_INSTANCES", B.TUNE_DEFER_INSTANCES), ("EPHB_DELTA_TETRA", B.DELTA_TETRA),
-                        ("EPHB_TUNE_STAGE_A_TMEM_A", B.TUNE_STAGE_A_TMEM_A)):
+                        ("EPHB_TUNE_STAGE_A_TMEM_A", B.TUNE_STAGE_A_TMEM_A), ("EPHB_MAX_DOPANTS", B.MAX_DOPANTS)):
         m = re.search(r"#define\s+%s\s+(\d+)" % name, text)
         assert m and int(m.group(1)) == value, name
 
