@@ -338,6 +338,22 @@ typedef struct {
 /* Sets (NULL or n_species = 0: clears) the charged impurities; every instance's RTA terms are
  * made again at its next solve. */
 ephb_status ephb_set_impurities(ephb_ctx *ctx, const ephb_impurities *imp);
+
+/* ---- Phonon-isotope (Tamura) scattering ----------------------------------------------
+ * "Electrons, phonons, and interactions", Eq. W^ph-x: on-site mass defects in the first Born
+ * approximation.  Its part of the phonon RTA rate (Eq. W^RTA_sq, Matthiessen's rule; the paper's
+ * phonon self term sums the ph-ph rates alone) is
+ *   W^iso_sq = pi (hbar w_sq)^2 / (2 hbar N_q) sum_tau g_tau sum_{s'q'} |xi*_{tau,sq} . xi_{tau,s'q'}|^2
+ *              delta(hbar w_s'q' - hbar w_sq),
+ * xi the eigenvectors of the mass-scaled dynamical matrix, g_tau the mass-variance parameter of
+ * atom tau.  Readings: the rate carries 1/N_q (the printed formula omits it; a mesh sum needs
+ * it, as Eq. X^e-ph has it); modes at or below omega_min take no part; delta is the rates call's
+ * Gaussian; the rate is averaged over the degenerate group of sq.  Computed at each instance's
+ * next solve, one block per q representative over every q' of the mesh, the other q taking
+ * their representative's rates.  g: nat values (nat = the model's atoms, at most 4; NULL or
+ * nat = 0 clears).  Errors: EPHB_EINVAL for nat outside 0..4 or a negative g; a solve returns
+ * EPHB_EINVAL if nat differs from the model's or the rates call had no positive Gaussian. */
+ephb_status ephb_set_isotopes(ephb_ctx *ctx, const double *g, int nat);
 /* The last solve of one instance. */
 ephb_status ephb_instance_solve_info(ephb_ctx *ctx, int inst, ephb_solve_info *out);
 

@@ -5,6 +5,7 @@ Plain, slow, readable double-precision restatement of arXiv 2109.08547:
   * Hellmann-Feynman electron and phonon velocities         (Eqs. v_mk, v_sq)
   * e-ph transition rates X^+ / X^- over IBZ k x FBZ k'     (Eq. X^e-ph)
   * e-chimp rates (screened Coulomb, Born)                  (Eqs. |g^e-chimp_q|^2, q_TF^2, X^e-chimp)
+  * ph-isotope rates (Tamura)                               (Eq. W^ph-x)
   * ph-e rates Y (the same + process seen from the phonon)  (Eq. Y^ph-e)
   * RTA terms and rates, self and drag terms                (Eqs. I0/J0, W^RTA, dI^S, dI^D, F0/G0, dF^D)
   * unified single-iterator coupled solution                ("Coupled and decoupled BTEs")
@@ -16,7 +17,7 @@ design notes): Wigner-Seitz weights and 1/N factors absorbed into the Wannier
 arrays; g prefactor sqrt(w_ref/w_sq) with the mass inside the Cartesian sum;
 |g|^2 and velocities averaged over degenerate subspaces; Gaussian delta with an
 8-sigma cut; modes with hbar*w < omega_min excluded; X normalised by 1/N_q and Y by
-1/N_k; phonon background rate W_bg replacing ph-ph/ph-isotope scattering; Jacobi
+1/N_k; phonon background rate W_bg replacing ph-ph scattering; Jacobi
 iteration without mixing; residual = max relative Frobenius change of the
 coefficient tensors; Kelvin-Onsager scalar by least squares; coefficient sums
 carry 1/N_k and 1/N_q.
@@ -40,6 +41,7 @@ __all__ = [
     "kplusq", "minus_q", "TENSORS", "inverse_ops", "ANGSTROM", "ibz_window_rows", "prepare_rows",
     "tetra_corner_weights", "tetra_point_weights", "CUBE_TETRAHEDRA", "CUBE_SUBDIVISIONS",
     "EPS0", "centred", "reciprocal_si", "thomas_fermi_q2", "chimp_g2", "chimp_kernel", "chimp_rates",
+    "isotope_rates",
 ]
 
 
@@ -609,6 +611,37 @@ def chimp_rates(P: Prepared, states: np.ndarray) -> np.ndarray:
     return K.sum(axis=1)
 
 
+# ----------------------------------------------------------------------------------------
+# phonon-isotope scattering (Tamura): Eq. W^ph-x and its entry into W^RTA_sq
+# ----------------------------------------------------------------------------------------
+
+def isotope_rates(P: Prepared, g_atoms) -> np.ndarray:
+    """The ph-isotope part of W^RTA_sq (Eq. W^ph-x summed over s'q' and divided by n(1+n)), on the
+    full q mesh: pi w_sq^2 / (2 N_q) sum_tau g_tau sum_{s'q'} |xi*_{tau,sq} . xi_{tau,s'q'}|^2
+    delta(w_s'q' - w_sq).  With energies E = hbar w in eV and delta(w) = hbar delta(E) this is
+    pi E^2 / (2 hbar N_q) sum ... delta(E' - E).  Readings: the printed rate carries no 1/N_q,
+    which a mesh sum needs (as X^e-ph does); modes at or below omega_min take no part, on either
+    side; delta is the e-ph Gaussian; the rate is averaged over the degenerate group of sq (the
+    gauge inside a degenerate subspace is arbitrary).  g_atoms: mass-variance parameter g_tau of
+    each atom of the basis."""
+    wl = P.wl
+    w, u = P.w, P.u
+    Nq, nbr = w.shape
+    ok = w > wl.omega_min_eV
+    ov = np.zeros((Nq, nbr, Nq, nbr))
+    for tau, g in enumerate(g_atoms):
+        A = u[:, 3 * tau:3 * tau + 3, :]
+        ov += g * np.abs(np.einsum("qxs,pxt->qspt", A.conj(), A)) ** 2
+    d = gaussian_delta(w[None, None, :, :] - w[:, :, None, None], wl.sigma_eV, wl.cutoff_sigmas)
+    d = d * ok[None, None, :, :]
+    raw = np.pi * w ** 2 / (2.0 * HBAR_EVS * Nq) * np.einsum("qspt,qspt->qs", ov, d)
+    raw = np.where(ok, raw, 0.0)
+    W = np.empty_like(raw)
+    for q in range(Nq):
+        W[q] = _group_average_matrix(w[q], wl.degen_tol_eV) @ raw[q]
+    return W
+
+
 @dataclasses.dataclass
 class BTEResult:
     coeffs: dict
@@ -760,6 +793,8 @@ def solve_coupled_bte(P: Prepared, R: Rates, level: str = "dragged", ko: bool = 
     W_ph = np.zeros_like(P.w)
     okp = sy.ph_ok
     W_ph[okp] = ds * sumY[okp] / sy.nn1[okp] + W_bg[okp]
+    if getattr(wl, "isotopes", None) is not None:   # ph-isotope enters the RTA rate only
+        W_ph[okp] = W_ph[okp] + isotope_rates(P, wl.isotopes)[okp]
     inv_nnW = np.zeros_like(P.w)
     inv_nnW[okp] = 1.0 / (sy.nn1[okp] * W_ph[okp])
     # RTA terms (Eqs. I0/J0, F0/G0)

@@ -38,7 +38,7 @@ EXPORTED = ["ephb_create", "ephb_destroy", "ephb_last_error", "ephb_set_wannier_
             "ephb_set_warm_start", "ephb_mlp_create", "ephb_mlp_destroy", "ephb_mlp_last_error",
             "ephb_mlp_num_params", "ephb_mlp_set_bf16", "ephb_mlp_get_params", "ephb_mlp_set_params",
             "ephb_mlp_forward", "ephb_mlp_loss_grad", "ephb_mlp_train_step", "ephb_set_tuning",
-            "ephb_selftest_exp_ff", "ephb_set_impurities"]
+            "ephb_selftest_exp_ff", "ephb_set_impurities", "ephb_set_isotopes"]
 MAX_DOPANTS = 4   # EPHB_MAX_DOPANTS
 NFEAT = 6
 MAX_ACCEL_DEPTH = 8   # EPHB_MAX_ACCEL_DEPTH
@@ -147,6 +147,7 @@ def load(path: str = None):
     lib.ephb_solve_coupled_bte.argtypes = [C.c_void_p, C.POINTER(SolveOptsC), C.POINTER(SolveInfoC)]
     lib.ephb_transport_coefficients.argtypes = [C.c_void_p, C.c_int, C.POINTER(CoeffsC)]
     lib.ephb_set_impurities.argtypes = [C.c_void_p, C.POINTER(ImpuritiesC)]
+    lib.ephb_set_isotopes.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.c_int]
     lib.ephb_get_device_array.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
                                           C.POINTER(C.c_int)]
     lib.ephb_copy_array_to_host.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]
@@ -363,6 +364,15 @@ def set_impurities(ctx: Context, imp=None) -> None:
     _check(ctx, _lib.ephb_set_impurities(ctx.handle, C.byref(c)))
 
 
+def set_isotopes(ctx: Context, g=None) -> None:
+    """Mass-variance parameter of each atom for the ph-isotope channel, or None to clear it."""
+    if g is None or len(g) == 0:
+        _check(ctx, _lib.ephb_set_isotopes(ctx.handle, None, 0))
+        return
+    arr = (C.c_double * len(g))(*[float(x) for x in g])
+    _check(ctx, _lib.ephb_set_isotopes(ctx.handle, arr, len(g)))
+
+
 def transport_coefficients(ctx: Context, inst: int = 0) -> dict:
     c = CoeffsC()
     _check(ctx, _lib.ephb_transport_coefficients(ctx.handle, int(inst), C.byref(c)))
@@ -433,6 +443,7 @@ def run_path(ctx: Context, wl, level="dragged", ko_correction=True, tol=None, ma
              device_loop=False) -> PathResult:
     """The whole hot path for one workload on an existing context whose model is set."""
     set_impurities(ctx, getattr(wl, "chimp", None))
+    set_isotopes(ctx, getattr(wl, "isotopes", None))
     mesh = build_meshes_ibz(ctx, wl.kmesh, wl.qmesh, wl.window, wl.degen_tol_eV, wl.omega_min_eV)
     rates = compute_transition_rates(ctx, wl.T_K, wl.mu_eV, wl.sigma_eV, wl.cutoff_sigmas, precision,
                                      delta=getattr(wl, "delta", "gauss"))

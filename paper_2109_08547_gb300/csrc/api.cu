@@ -105,6 +105,7 @@ struct InstState {
   DBuf<double> pseg_part;
   int64_t npseg = 0;
   DBuf<double> W_chimp;         // e-chimp part of the electron RTA rates [nst]
+  DBuf<double> W_iso, W_iso_rep;   // ph-isotope part of the phonon RTA rates [nq][nbr], [n_qrep][nbr]
   DBuf<uint32_t> kcrd;
   DBuf<int2> kinfo;
   DBuf<int> sctl;               // device-driven sweep loop: stop flag, sweeps done, converged
@@ -167,6 +168,8 @@ struct InstState {
     Xff.release(); Yff.release(); IJff.release(); FGff.release();
     pnseg_row.release(); pseg_row.release(); pseg_ptr.release(); pseg_begin.release(); pseg_part.release();
     W_chimp.release();
+    W_iso.release();
+    W_iso_rep.release();
     bte_ready = has_warm = solved = have_f32 = lists_pending = false;
   }
 };
@@ -252,6 +255,8 @@ struct ephb_ctx : InstState {
   double *host_res = nullptr;   // pinned: kResLen doubles, then the sweep-loop control (4 ints)
   // charged impurities (e-chimp) and the Gaussian of the last rates call (their delta)
   ephb_impurities imp{};
+  int iso_nat = 0;               // phonon-isotope channel: mass-variance parameter per atom
+  double iso_g[4] = {0, 0, 0, 0};
   double delta_sigma = 0.0, delta_cut = 0.0;
   DBuf<double> chimp_part, chimp_qtf;
   // device-driven solve: the instantiated graph, the signature of what it was built from, the
@@ -1285,7 +1290,24 @@ ephb_status bte_setup(ephb_ctx *ctx) {
   }
   CK(launch_rta_electron(B, ctx->W_e.p, ctx->inv_ffW.p, ctx->I0.p, ctx->J0.p, ctx->nzero.p, st, W_add));
   CK(launch_ph_rowsum(B, ctx->Bt.p, st));
-  CK(launch_rta_phonon(M, D, B, ctx->Bt.p, ctx->W_ph.p, ctx->inv_nnW.p, ctx->F0.p, st));
+  const double *W_ph_add = nullptr;
+  if (ctx->iso_nat > 0) {   // ph-isotope rates join W^RTA_sq (Matthiessen's rule)
+    if (ctx->iso_nat != M.nat) return fail(ctx, EPHB_EINVAL, "isotope parameters for a different number of atoms");
+    if (!(ctx->delta_sigma > 0) || !(ctx->delta_cut > 0))
+      return fail(ctx, EPHB_EINVAL, "isotope scattering needs the Gaussian width of the rates call");
+    CK(ctx->W_iso.ensure(nph));
+    CK(ctx->W_iso_rep.ensure(size_t(ctx->n_qrep > 0 ? ctx->n_qrep : 1) * M.nbr));
+    IsoParams ip;
+    std::memset(&ip, 0, sizeof(ip));
+    for (int a = 0; a < ctx->iso_nat; ++a) ip.g[a] = ctx->iso_g[a];
+    ip.sigma = ctx->delta_sigma;
+    ip.cut_sigmas = ctx->delta_cut;
+    ip.gnorm = 1.0 / (ctx->delta_sigma * sqrt(2.0 * kPi));
+    ip.pref = kPi / (2.0 * kHbarEVs * double(ctx->qm.size()));
+    CK(launch_iso_rates(M, D, ip, ctx->W_iso_rep.p, ctx->W_iso.p, st));
+    W_ph_add = ctx->W_iso.p;
+  }
+  CK(launch_rta_phonon(M, D, B, ctx->Bt.p, ctx->W_ph.p, ctx->inv_nnW.p, ctx->F0.p, st, W_ph_add));
   // partner runs of the electron rows (self term), then segments of the entry stream
   // (drag term) and of the run stream (self term)
   const int64_t ne = ctx->n_entries;
@@ -2164,6 +2186,22 @@ ephb_status ephb_set_impurities(ephb_ctx *ctx, const ephb_impurities *imp) {
   }
   ctx->imp = v;
   // the RTA terms of every instance change
+  ctx->bte_ready = false;
+  for (auto &sl : ctx->slots) sl.bte_ready = false;
+  return EPHB_OK;
+}
+
+ephb_status ephb_set_isotopes(ephb_ctx *ctx, const double *g, int nat) {
+  if (!ctx) return EPHB_EINVAL;
+  if (!g || nat == 0) {
+    ctx->iso_nat = 0;
+  } else {
+    if (nat < 0 || nat > 4) return fail(ctx, EPHB_EINVAL, "nat outside 0..4");
+    for (int a = 0; a < nat; ++a)
+      if (!(g[a] >= 0) || !std::isfinite(g[a])) return fail(ctx, EPHB_EINVAL, "mass variances must be >= 0");
+    ctx->iso_nat = nat;
+    for (int a = 0; a < 4; ++a) ctx->iso_g[a] = a < nat ? g[a] : 0.0;
+  }
   ctx->bte_ready = false;
   for (auto &sl : ctx->slots) sl.bte_ready = false;
   return EPHB_OK;

@@ -105,7 +105,7 @@ __global__ void k_ph_rowsum(BteDev B, double *Bt) {
 
 // W_ph = d_s sum_S Bt(S^-1 q) / (n(1+n)) + W_bg; F0 = (hbar w/T) v / W   (Eqs. W^RTA_sq, F0/G0)
 __global__ void k_rta_phonon(ModelDev M, MeshDev D, BteDev B, const double *Bt, double *W_ph, double *inv_nnW,
-                             double *F0) {
+                             double *F0, const double *__restrict__ W_add) {
   __shared__ int rot[kMaxSym * 9];
   __shared__ int inv[kMaxSym];
   for (int t = threadIdx.x; t < M.nsym * 9; t += blockDim.x) rot[t] = M.sym_rot[t];
@@ -124,7 +124,7 @@ __global__ void k_rta_phonon(ModelDev M, MeshDev D, BteDev B, const double *Bt, 
     double n = bose_b(w, kT);
     double nn1 = n * (1.0 + n);
     double wr = w / M.bg_w;
-    W = M.spin_deg * sum / nn1 + M.bg_coeff * wr * wr * (B.T / M.bg_T);
+    W = M.spin_deg * sum / nn1 + M.bg_coeff * wr * wr * (B.T / M.bg_T) + (W_add ? W_add[t] : 0.0);
     invw = 1.0 / (nn1 * W);
   }
   W_ph[t] = W;
@@ -1117,8 +1117,91 @@ cudaError_t launch_ph_rowsum(const BteDev &B, double *Bt, cudaStream_t st) {
 }
 
 cudaError_t launch_rta_phonon(const ModelDev &M, const MeshDev &D, const BteDev &B, const double *Bt, double *W_ph,
-                              double *inv_nnW, double *F0, cudaStream_t st) {
-  EPHB_LAUNCH(k_rta_phonon, unsigned((D.nq * M.nbr + 255) / 256), 256, 0, st, M, D, B, Bt, W_ph, inv_nnW, F0);
+                              double *inv_nnW, double *F0, cudaStream_t st, const double *W_add) {
+  EPHB_LAUNCH(k_rta_phonon, unsigned((D.nq * M.nbr + 255) / 256), 256, 0, st, M, D, B, Bt, W_ph, inv_nnW, F0,
+              W_add);
+  return cudaGetLastError();
+}
+
+namespace {
+
+// ---- phonon-isotope scattering (Tamura): Eq. W^ph-x, its part of W^RTA_sq
+
+constexpr int kIsoThreads = 256;
+
+// One block per representative q of the q wedge, all its branches s: threads strided over q'
+// sum g_tau |xi*_{tau,sq} . xi_{tau,s'q'}|^2 delta(E' - E) over the branches s' above omega_min
+// (the Gaussian of the rates call), then the warps' and the block's sums in a fixed order;
+// W = pi E^2 / (2 hbar N_q) x sum, averaged over the degenerate group of s, zero for modes at or
+// below omega_min.  Wrep[rep][s].
+__global__ void __launch_bounds__(kIsoThreads) k_iso_rates(ModelDev M, MeshDev D, IsoParams P, double *Wrep) {
+  const int nbr = M.nbr;
+  const int r = blockIdx.x;
+  const int q = D.qlist[r];
+  __shared__ double2 xi[kMaxBranches * kMaxBranches];
+  __shared__ double wq[kMaxBranches];
+  __shared__ double part[kIsoThreads / 32][kMaxBranches];
+  __shared__ double raw[kMaxBranches];
+  for (int t = threadIdx.x; t < nbr * nbr; t += blockDim.x) xi[t] = D.u[size_t(q) * nbr * nbr + t];
+  for (int t = threadIdx.x; t < nbr; t += blockDim.x) wq[t] = D.w[size_t(q) * nbr + t];
+  __syncthreads();
+  double acc[kMaxBranches];
+  for (int s = 0; s < kMaxBranches; ++s) acc[s] = 0.0;
+  const double cut = P.cut_sigmas * P.sigma, inv2s2 = 0.5 / (P.sigma * P.sigma);
+  for (int64_t qp = threadIdx.x; qp < D.nq; qp += blockDim.x) {
+    const double2 *up = D.u + size_t(qp) * nbr * nbr;
+    for (int sp = 0; sp < nbr; ++sp) {
+      const double wp = D.w[size_t(qp) * nbr + sp];
+      if (!(wp > D.omega_min)) continue;
+      for (int s = 0; s < nbr; ++s) {
+        const double x = wp - wq[s];
+        if (fabs(x) > cut) continue;
+        double ov = 0.0;
+        for (int a = 0; a < M.nat; ++a) {
+          double2 d = cmk(0.0, 0.0);
+          for (int c = 0; c < 3; ++c) cfma_conj(d, xi[(3 * a + c) * nbr + s], up[(3 * a + c) * nbr + sp]);
+          ov += P.g[a] * (d.x * d.x + d.y * d.y);
+        }
+        acc[s] += ov * exp(-x * x * inv2s2) * P.gnorm;
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int s = 0; s < nbr; ++s) {
+    const double v = warp_sum(acc[s]);
+    if (lane == 0) part[wid][s] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nbr) {
+    const int s = threadIdx.x;
+    double t = 0.0;
+    for (int w = 0; w < kIsoThreads / 32; ++w) t += part[w][s];
+    raw[s] = wq[s] > D.omega_min ? P.pref * wq[s] * wq[s] * t : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x < nbr) {
+    const int s = threadIdx.x;
+    const int g0 = D.pgrp[(size_t(q) * nbr + s) * 2], g1 = D.pgrp[(size_t(q) * nbr + s) * 2 + 1];
+    double t = 0.0;
+    for (int j = g0; j < g1; ++j) t += raw[j];
+    Wrep[size_t(r) * nbr + s] = t / double(g1 - g0);
+  }
+}
+
+// every q takes its representative's rates (W^ph-x is invariant under the point group)
+__global__ void k_iso_spread(MeshDev D, int nbr, const double *Wrep, double *W) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= D.nq * nbr) return;
+  const int q = int(t / nbr), s = int(t % nbr);
+  W[t] = Wrep[size_t(D.qrep_of[D.qrep[q]]) * nbr + s];
+}
+
+}  // namespace
+
+cudaError_t launch_iso_rates(const ModelDev &M, const MeshDev &D, const IsoParams &P, double *Wrep, double *W,
+                             cudaStream_t st) {
+  if (D.n_qrep > 0) EPHB_LAUNCH(k_iso_rates, unsigned(D.n_qrep), kIsoThreads, 0, st, M, D, P, Wrep);
+  if (D.nq * M.nbr > 0) EPHB_LAUNCH(k_iso_spread, unsigned((D.nq * M.nbr + 255) / 256), 256, 0, st, D, M.nbr, Wrep, W);
   return cudaGetLastError();
 }
 

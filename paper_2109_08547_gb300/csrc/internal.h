@@ -247,7 +247,16 @@ cudaError_t launch_chimp_rates(const MeshDev &D, const BteDev &B, const ChimpPar
                                cudaStream_t st);
 cudaError_t launch_ph_rowsum(const BteDev &B, double *Bt, cudaStream_t st);
 cudaError_t launch_rta_phonon(const ModelDev &M, const MeshDev &D, const BteDev &B, const double *Bt, double *W_ph,
-                              double *inv_nnW, double *F0, cudaStream_t st);
+                              double *inv_nnW, double *F0, cudaStream_t st, const double *W_add = nullptr);
+// Phonon-isotope (Tamura) scattering: its part of W^RTA_sq on the q representatives (Wrep
+// [n_qrep][nbr]), then on every q (W [nq][nbr]).
+struct IsoParams {
+  double g[4];                      // mass-variance parameter of each atom
+  double sigma, cut_sigmas, gnorm;  // Gaussian delta: width, cut, 1/(sigma sqrt(2 pi))
+  double pref;                      // pi / (2 hbar N_q)
+};
+cudaError_t launch_iso_rates(const ModelDev &M, const MeshDev &D, const IsoParams &P, double *Wrep, double *W,
+                             cudaStream_t st);
 // Segments of a row-structured stream (at most sweep_segment_len() items, within one row).
 struct SweepSegs {
   int64_t nseg = 0;

@@ -85,6 +85,7 @@ class Workload:
     tol: float = 1.0e-10
     delta: str = "gauss"           # energy-conserving delta: "gauss" (sigma_eV) or "tetra" (no width)
     chimp: Impurities = None       # charged impurities (e-chimp channel), or none
+    isotopes: tuple = None         # mass-variance parameter g of each atom (ph-isotope channel), or none
 
 
 def oh_group() -> np.ndarray:
